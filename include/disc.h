@@ -1,0 +1,187 @@
+/*
+ * libdisc -- the per-frame integration step of DISC (Dense Integrated Semantic
+ * Context, arxiv 2603.03935) as a C ABI over hand-written sm_103a kernels.
+ *
+ * One map = one sparse voxel hash table (voxel key -> instance id) plus an
+ * instance table (union-find parent, voxel count, view quality Q, embedding),
+ * all resident on one GPU.  Each integrated frame runs the paper's per-frame
+ * pipeline:
+ *   - distinctiveness map D over the frame's patch tokens (Sec. III-C, Eq. 1),
+ *   - D-weighted pooling of the tokens inside each mask (Sec. III-C),
+ *   - view quality Q = S_size * S_angle * S_sem * S_dist (Sec. III-C, Eq. 2-3),
+ *   - back-projection of the masked depth into per-segment voxel sets
+ *     (Sec. III-A),
+ *   - exact voxel overlap of each segment with the map, the cosine gate, and
+ *     on-the-fly merging of instances (Sec. III-B),
+ *   - Q-replacement fusion of the instance embeddings (Sec. III-C).
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes only; nothing throws across the ABI.  A frame is all or
+ *     nothing: when integration fails the map keeps its pre-frame state.
+ *   - The caller owns every buffer it passes; the map owns its device state.
+ *     Inputs must stay valid until the call returns.
+ *   - Work is ordered on the map's CUDA stream (config.cuda_stream, or a
+ *     stream the map creates).  Every call returns after its results are on
+ *     the host unless stated otherwise.
+ *   - One host thread per map at a time; different maps are independent.
+ *   - Instance ids are resolved roots (the smallest id of a merged group);
+ *     -1 means "none".
+ *   - Camera: OpenCV pinhole (x right, y down, z forward), pixel centres at
+ *     (u + 0.5, v + 0.5); pose camera->world, row-major 4x4 doubles, rounded
+ *     once to fp32 on the host.
+ */
+#ifndef DISC_H
+#define DISC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DISC_OK = 0,
+    DISC_ERR_INVALID_ARG = -1, /* bad pointer, size or configuration */
+    DISC_ERR_OOM = -2,         /* a device or host allocation failed */
+    DISC_ERR_TABLE_FULL = -3,  /* hash probe limit reached */
+    DISC_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    DISC_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    DISC_ERR_BUDGET = -6,      /* reserved for admission under a memory budget */
+    DISC_ERR_RANGE = -7,       /* a token is non-finite or |value| > 1024 */
+    DISC_ERR_CAPACITY = -8     /* more association edges/pairs than a frame may hold */
+} disc_status;
+
+typedef struct disc_map disc_map; /* opaque; owns all device state of one map */
+
+typedef enum { DISC_FP32 = 0, DISC_BF16 = 1, DISC_FP8_E4M3 = 2 } disc_precision;
+typedef enum { DISC_TOKENS_F32 = 0, DISC_TOKENS_BF16 = 1 } disc_token_dtype;
+
+typedef struct {
+    float voxel_size;        /* metres per voxel edge (> 0) */
+    float z_min, z_max;      /* depth range that counts as valid, metres */
+    float eps;               /* epsilon of Eq. 1 */
+    float tau_cos;           /* association gate: cosine >= tau_cos (Sec. III-B) */
+    float lambda_size;       /* lambda of S_size, 3.3 in the paper */
+    int32_t ov_num, ov_den;  /* geometry gate: overlap * ov_den >= ov_num * |V_m| */
+    int32_t embed_dim;       /* D, <= 4096 */
+    int32_t patch_h, patch_w;/* token grid; Ph * Pw <= 16384 */
+    int32_t max_width, max_height; /* largest frame this map accepts (H*W <= 2^24) */
+    int32_t max_masks;       /* largest num_masks per frame, <= 256 */
+    int32_t min_mask_pixels; /* masks with fewer pixels are ignored (Sec. III-A filter) */
+    int64_t voxel_capacity;  /* initial hash slots (rounded up to a power of two) */
+    float max_load;          /* the table doubles before its load would pass this */
+    int32_t instance_capacity; /* initial instance slots (grows on demand) */
+    int32_t precision;       /* disc_precision of the fast pooling/scoring path */
+    void* cuda_stream;       /* cudaStream_t, or NULL: the map creates one */
+    int32_t device;          /* CUDA device ordinal */
+} disc_map_config;
+
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    double T_world_cam[16];  /* row-major camera -> world */
+    const float* depth;      /* [H][W] metres; invalid = outside [z_min, z_max] or NaN */
+    const uint16_t* labels;  /* [H][W] mask label, 0 = none, 1..num_masks */
+    const void* tokens;      /* [Ph*Pw][D] row-major patch tokens (token_dtype) */
+    int32_t token_dtype;     /* disc_token_dtype */
+    int32_t num_masks;       /* labels above num_masks count as background */
+    const float* global_embed; /* [D] global image embedding, or NULL -> mean token */
+    int32_t inputs_on_device;  /* 1: pointers are device memory; 0: host memory */
+} disc_frame;
+
+typedef struct {
+    int32_t valid_pixels;       /* masked pixels with valid depth and in-range keys */
+    int32_t dropped_pixels;     /* valid depth but voxel key out of range */
+    int32_t unique_seg_voxels;  /* unique (segment, voxel) pairs = voxel updates */
+    int32_t new_voxels;         /* voxels inserted into the map */
+    int32_t active_instances;   /* distinct instances the segments overlap */
+    int32_t overlap_pairs;      /* distinct (segment, instance) overlaps */
+    int32_t new_instances;
+    int32_t merges;             /* instances merged into another */
+    int32_t live_segments;      /* masks that produced at least one voxel */
+    int32_t borderline_rescored;/* fast cosines re-scored exactly near tau_cos */
+    int32_t max_probe;          /* longest hash probe of the frame */
+    int32_t status;             /* disc_status of the frame */
+} disc_frame_stats;
+
+/* Intermediates of the most recent frame, copied to caller host buffers (any
+ * pointer may be NULL).  Rows over masks: label m in row m - 1. */
+typedef struct {
+    float* fbar;      /* [D] mean token (Eq. 1) */
+    float* Dp;        /* [P] distinctiveness (Eq. 1) */
+    float* cosg;      /* [P] cosine of each token with the global embedding */
+    int32_t* cov;     /* [M][P] pixels of mask m inside patch p */
+    int32_t* npix;    /* [M] |M_m| */
+    float* W;         /* [M][P] pooling weights (sum to 1 per valid mask) */
+    float* E;         /* [M][D] pooled embeddings, exact path */
+    float* E_fast;    /* [M][D] pooled embeddings, tensor-core path */
+    float* S;         /* [M][5] S_size, S_angle, S_sem, S_dist, Q */
+    int32_t* nvox;    /* [M] |V_m| */
+    int32_t* rep;     /* [M] instance each segment joined, -1 if none */
+    uint64_t* seg_keys; /* [seg_cap] unique (segment, voxel) pairs, unordered */
+    int32_t* seg_m;     /* [seg_cap] their mask label */
+    int64_t seg_cap;
+    int64_t n_seg;      /* out: number of pairs */
+    int32_t num_masks;  /* out */
+} disc_frame_report;
+
+/* Fills a config with the defaults used throughout (eps 1e-6, tau_cos 0.75,
+ * lambda 3.3, overlap 1/5, depth 0.1..10 m, 640x480, 24x24x768, 40 masks). */
+void disc_config_default(disc_map_config* cfg);
+
+/* Creates a map on cfg->device.  Returns DISC_ERR_INVALID_ARG for an invalid
+ * config and DISC_ERR_OOM when the resident state does not fit. */
+disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolved, disc_map** out_map);
+
+/* Integrates one frame (all steps above).  stats may be NULL. */
+disc_status disc_integrate_frame(disc_map* map, const disc_frame* frame, disc_frame_stats* stats);
+
+/* Integrates n frames in order with one host synchronisation at the end.
+ * stats (nullable) receives one entry per frame.  On an error the frames
+ * before the failing one stay integrated; *n_done (nullable) says how many. */
+disc_status disc_integrate_frames(disc_map* map, const disc_frame* frames, int32_t n,
+                                  disc_frame_stats* stats, int32_t* n_done);
+
+/* Copies the intermediates of the most recent frame (see disc_frame_report). */
+disc_status disc_map_last_frame(disc_map* map, disc_frame_report* report);
+
+/* Open-vocabulary query (Sec. IV retrieval): cosine of each query vector
+ * [nq][D] (host) against every live instance embedding; per query the k best
+ * ids and scores (descending score, ascending id on ties; -1 / -inf pad). */
+disc_status disc_query_topk(disc_map* map, const float* queries, int32_t nq, int32_t k, int32_t* ids,
+                            float* scores);
+
+/* Instance id of the voxel containing each world point [n][3] (host), -1 if
+ * the voxel is not mapped. */
+disc_status disc_query_points(disc_map* map, const float* xyz, int64_t n, int32_t* ids);
+
+/* Map export.  Voxels come sorted by key with resolved instance ids; instance
+ * arrays cover ids 0..num_ids-1 (parent[i] == i marks a live instance). */
+disc_status disc_map_counts(disc_map* map, int64_t* num_voxels, int32_t* num_ids);
+disc_status disc_map_export_voxels(disc_map* map, uint64_t* keys, int32_t* ids, int64_t cap);
+disc_status disc_map_export_instances(disc_map* map, int32_t* parent, int64_t* count, float* Q,
+                                      float* E, int32_t* n_obs, int32_t cap);
+
+/* Checkpoint: a host file holding the config, the voxel table and the
+ * instance table.  disc_map_load creates a new map (stream and device taken
+ * from cfg_override when it is not NULL). */
+disc_status disc_map_save(disc_map* map, const char* path);
+disc_status disc_map_load(const char* path, const disc_map_config* cfg_override, disc_map** out_map);
+
+/* Voxel key packing: three signed 18-bit voxel coordinates (x, y, z), each
+ * biased by 2^17, in bits 36..53, 18..35 and 0..17. */
+uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz);
+
+/* The map's resolved configuration (capacities after rounding/growth). */
+disc_status disc_map_get_config(disc_map* map, disc_map_config* out);
+
+/* Device memory held by the map, bytes. */
+int64_t disc_map_device_bytes(disc_map* map);
+
+void disc_map_destroy(disc_map* map); /* NULL-safe */
+const char* disc_status_str(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

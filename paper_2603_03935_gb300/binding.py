@@ -1,0 +1,301 @@
+"""ctypes binding of libdisc (include/disc.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdisc.so")
+
+c_i32, c_i64, c_f32, c_f64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+
+STATUS = {0: "DISC_OK", -1: "DISC_ERR_INVALID_ARG", -2: "DISC_ERR_OOM", -3: "DISC_ERR_TABLE_FULL",
+          -4: "DISC_ERR_CUDA", -5: "DISC_ERR_TIMEOUT", -6: "DISC_ERR_BUDGET", -7: "DISC_ERR_RANGE",
+          -8: "DISC_ERR_CAPACITY"}
+
+
+class DiscError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = int(code)
+        super().__init__(f"{what}: {STATUS.get(self.code, self.code)}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("voxel_size", c_f32), ("z_min", c_f32), ("z_max", c_f32), ("eps", c_f32),
+                ("tau_cos", c_f32), ("lambda_size", c_f32), ("ov_num", c_i32), ("ov_den", c_i32),
+                ("embed_dim", c_i32), ("patch_h", c_i32), ("patch_w", c_i32),
+                ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
+                ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
+                ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
+                ("device", c_i32)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32),
+                ("cy", c_f32), ("T_world_cam", c_f64 * 16), ("depth", c_vp), ("labels", c_vp),
+                ("tokens", c_vp), ("token_dtype", c_i32), ("num_masks", c_i32),
+                ("global_embed", c_vp), ("inputs_on_device", c_i32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, c_i32) for k in ("valid_pixels", "dropped_pixels", "unique_seg_voxels", "new_voxels",
+                                     "active_instances", "overlap_pairs", "new_instances", "merges",
+                                     "live_segments", "borderline_rescored", "max_probe", "status")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
+                ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
+                ("seg_keys", c_vp), ("seg_m", c_vp), ("seg_cap", c_i64), ("n_seg", c_i64),
+                ("num_masks", c_i32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdisc.so; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdisc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.disc_config_default.argtypes = [P(Config)]
+        L.disc_config_default.restype = None
+        L.disc_map_create.argtypes = [P(Config), P(Config), P(c_vp)]
+        L.disc_integrate_frame.argtypes = [c_vp, P(Frame), P(Stats)]
+        L.disc_integrate_frames.argtypes = [c_vp, P(Frame), c_i32, P(Stats), P(c_i32)]
+        L.disc_map_last_frame.argtypes = [c_vp, P(Report)]
+        L.disc_query_topk.argtypes = [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp]
+        L.disc_query_points.argtypes = [c_vp, c_vp, c_i64, c_vp]
+        L.disc_map_counts.argtypes = [c_vp, P(c_i64), P(c_i32)]
+        L.disc_map_export_voxels.argtypes = [c_vp, c_vp, c_vp, c_i64]
+        L.disc_map_export_instances.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i32]
+        L.disc_map_save.argtypes = [c_vp, ctypes.c_char_p]
+        L.disc_map_load.argtypes = [ctypes.c_char_p, P(Config), P(c_vp)]
+        L.disc_pack_key.argtypes = [c_i32, c_i32, c_i32]
+        L.disc_pack_key.restype = ctypes.c_uint64
+        L.disc_map_get_config.argtypes = [c_vp, P(Config)]
+        L.disc_map_get_config.restype = ctypes.c_int
+        L.disc_map_device_bytes.argtypes = [c_vp]
+        L.disc_map_device_bytes.restype = c_i64
+        L.disc_map_destroy.argtypes = [c_vp]
+        L.disc_map_destroy.restype = None
+        L.disc_status_str.argtypes = [c_i32]
+        L.disc_status_str.restype = ctypes.c_char_p
+        for f in ("disc_map_create", "disc_integrate_frame", "disc_integrate_frames", "disc_map_last_frame",
+                  "disc_query_topk", "disc_query_points", "disc_map_counts", "disc_map_export_voxels",
+                  "disc_map_export_instances", "disc_map_save", "disc_map_load"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    return lib().disc_status_str(int(code)).decode()
+
+
+def pack_key(kx: int, ky: int, kz: int) -> int:
+    return int(lib().disc_pack_key(kx, ky, kz))
+
+
+def config_default(**overrides) -> dict:
+    c = Config()
+    lib().disc_config_default(ctypes.byref(c))
+    d = {k: getattr(c, k) for k, _ in Config._fields_}
+    d.update(overrides)
+    return d
+
+
+def _check(code, what):
+    if code != 0:
+        raise DiscError(code, what)
+
+
+def _fill_frame(fr: Frame, width, height, intr, pose):
+    fr.width, fr.height = int(width), int(height)
+    fr.fx, fr.fy, fr.cx, fr.cy = (float(x) for x in intr)
+    for i, v in enumerate(np.asarray(pose, np.float64).reshape(16)):
+        fr.T_world_cam[i] = float(v)
+
+
+def host_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None):
+    """A disc_frame over host numpy arrays (kept alive by the returned tuple)."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    labels = np.ascontiguousarray(labels, np.uint16)
+    if tokens.dtype == np.float32:
+        tokens = np.ascontiguousarray(tokens)
+        tdt = 0
+    else:  # bfloat16 bits as uint16
+        tokens = np.ascontiguousarray(tokens, np.uint16)
+        tdt = 1
+    g = None if global_embed is None else np.ascontiguousarray(global_embed, np.float32)
+    fr = Frame()
+    _fill_frame(fr, depth.shape[1], depth.shape[0], intr, pose)
+    fr.depth, fr.labels, fr.tokens = depth.ctypes.data, labels.ctypes.data, tokens.ctypes.data
+    fr.token_dtype = tdt
+    fr.num_masks = int(num_masks)
+    fr.global_embed = None if g is None else g.ctypes.data
+    fr.inputs_on_device = 0
+    return fr, (depth, labels, tokens, g)
+
+
+def device_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None):
+    """A disc_frame over device tensors (torch CUDA tensors or raw pointers).
+
+    depth: float32 [H, W]; labels: int16/uint16 [H, W]; tokens: float32 or
+    bfloat16 [P, D]; all contiguous on the map's device."""
+    import torch
+    H, W = depth.shape
+    fr = Frame()
+    _fill_frame(fr, W, H, intr, pose)
+    fr.depth, fr.labels, fr.tokens = depth.data_ptr(), labels.data_ptr(), tokens.data_ptr()
+    fr.token_dtype = 1 if tokens.dtype == torch.bfloat16 else 0
+    fr.num_masks = int(num_masks)
+    fr.global_embed = None if global_embed is None else global_embed.data_ptr()
+    fr.inputs_on_device = 1
+    return fr, (depth, labels, tokens, global_embed)
+
+
+class DiscMap:
+    """One map resident on one GPU (disc_map_create ... disc_map_destroy)."""
+
+    def __init__(self, **cfg):
+        c = Config(**config_default(**cfg))
+        resolved = Config()
+        h = c_vp()
+        _check(lib().disc_map_create(ctypes.byref(c), ctypes.byref(resolved), ctypes.byref(h)),
+               "disc_map_create")
+        self._h = h
+        self.cfg = {k: getattr(resolved, k) for k, _ in Config._fields_}
+        self.D = int(resolved.embed_dim)
+        self.P = int(resolved.patch_h * resolved.patch_w)
+
+    @classmethod
+    def _from_handle(cls, h):
+        self = cls.__new__(cls)
+        self._h = h
+        c = Config()
+        _check(lib().disc_map_get_config(h, ctypes.byref(c)), "disc_map_get_config")
+        self.cfg = {k: getattr(c, k) for k, _ in Config._fields_}
+        self.D = int(c.embed_dim)
+        self.P = int(c.patch_h * c.patch_w)
+        return self
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().disc_map_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def integrate(self, frame, check: bool = True) -> dict:
+        """frame: (Frame, keepalive) from host_frame/device_frame."""
+        fr, _keep = frame
+        st = Stats()
+        rc = lib().disc_integrate_frame(self._h, ctypes.byref(fr), ctypes.byref(st))
+        if check:
+            _check(rc, "disc_integrate_frame")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def integrate_frames(self, frames, check: bool = True):
+        n = len(frames)
+        arr = (Frame * n)()
+        for i, (fr, _k) in enumerate(frames):
+            arr[i] = fr
+        st = (Stats * n)()
+        done = c_i32(0)
+        rc = lib().disc_integrate_frames(self._h, arr, n, st, ctypes.byref(done))
+        if check:
+            _check(rc, "disc_integrate_frames")
+        return [s.as_dict() for s in st], int(done.value), rc
+
+    def integrate_frames_raw(self, arr, n, stats):
+        """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
+        return lib().disc_integrate_frames(self._h, arr, n, stats, None)
+
+    def last_frame(self) -> dict:
+        M_cap = int(self.cfg["max_masks"])
+        P, D = self.P, self.D
+        npx = int(self.cfg["max_width"]) * int(self.cfg["max_height"])
+        out = dict(fbar=np.zeros(D, np.float32), Dp=np.zeros(P, np.float32), cosg=np.zeros(P, np.float32),
+                   cov=np.zeros((max(M_cap, 1), P), np.int32), npix=np.zeros(max(M_cap, 1), np.int32),
+                   W=np.zeros((max(M_cap, 1), P), np.float32), E=np.zeros((max(M_cap, 1), D), np.float32),
+                   E_fast=np.zeros((max(M_cap, 1), D), np.float32), S=np.zeros((max(M_cap, 1), 5), np.float32),
+                   nvox=np.zeros(max(M_cap, 1), np.int32), rep=np.zeros(max(M_cap, 1), np.int32),
+                   seg_keys=np.zeros(npx, np.uint64), seg_m=np.zeros(npx, np.int32))
+        r = Report()
+        for k in ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "seg_keys", "seg_m"):
+            setattr(r, k, out[k].ctypes.data)
+        r.seg_cap = npx
+        _check(lib().disc_map_last_frame(self._h, ctypes.byref(r)), "disc_map_last_frame")
+        M = int(r.num_masks)
+        n = int(r.n_seg)
+        for k in ("cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep"):
+            out[k] = out[k][:M]
+        order = np.lexsort((out["seg_keys"][:n], out["seg_m"][:n]))
+        out["seg_keys"] = out["seg_keys"][:n][order]
+        out["seg_m"] = out["seg_m"][:n][order]
+        out["n_seg"] = n
+        out["num_masks"] = M
+        return out
+
+    def counts(self):
+        nv, nid = c_i64(0), c_i32(0)
+        _check(lib().disc_map_counts(self._h, ctypes.byref(nv), ctypes.byref(nid)), "disc_map_counts")
+        return int(nv.value), int(nid.value)
+
+    def voxels(self):
+        nv, _ = self.counts()
+        keys = np.zeros(max(nv, 1), np.uint64)
+        ids = np.zeros(max(nv, 1), np.int32)
+        _check(lib().disc_map_export_voxels(self._h, keys.ctypes.data, ids.ctypes.data, nv), "export_voxels")
+        return keys[:nv], ids[:nv]
+
+    def instances(self):
+        _, n = self.counts()
+        parent = np.zeros(max(n, 1), np.int32)
+        count = np.zeros(max(n, 1), np.int64)
+        Q = np.zeros(max(n, 1), np.float32)
+        E = np.zeros((max(n, 1), self.D), np.float32)
+        obs = np.zeros(max(n, 1), np.int32)
+        _check(lib().disc_map_export_instances(self._h, parent.ctypes.data, count.ctypes.data, Q.ctypes.data,
+                                                E.ctypes.data, obs.ctypes.data, n), "export_instances")
+        return dict(parent=parent[:n], count=count[:n], Q=Q[:n], E=E[:n], n_obs=obs[:n])
+
+    def query_topk(self, queries, k):
+        q = np.ascontiguousarray(queries, np.float32).reshape(-1, self.D)
+        ids = np.zeros((q.shape[0], k), np.int32)
+        sc = np.zeros((q.shape[0], k), np.float32)
+        _check(lib().disc_query_topk(self._h, q.ctypes.data, q.shape[0], k, ids.ctypes.data, sc.ctypes.data),
+               "disc_query_topk")
+        return ids, sc
+
+    def query_points(self, xyz):
+        x = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+        ids = np.zeros(x.shape[0], np.int32)
+        _check(lib().disc_query_points(self._h, x.ctypes.data, x.shape[0], ids.ctypes.data), "disc_query_points")
+        return ids
+
+    def device_bytes(self) -> int:
+        return int(lib().disc_map_device_bytes(self._h))
+
+    def save(self, path):
+        _check(lib().disc_map_save(self._h, str(path).encode()), "disc_map_save")
+
+    @classmethod
+    def load(cls, path, **override):
+        c = Config(**config_default(**override)) if override else None
+        h = c_vp()
+        _check(lib().disc_map_load(str(path).encode(), ctypes.byref(c) if c is not None else None,
+                                   ctypes.byref(h)), "disc_map_load")
+        return cls._from_handle(h)

@@ -1,0 +1,187 @@
+// Shared device-side definitions of libdisc: the exact fixed-point arithmetic,
+// voxel keys, hash probing, and the per-map / per-frame device state.
+//
+// Numerical contract (identical on every GPU run, independent of thread order):
+//   * element-wise arithmetic is IEEE fp32 in a fixed operation order; the
+//     library is compiled with -fmad=false so no multiply-add is fused;
+//   * sums that decide labels are exact: each term is scaled by 2^S, rounded
+//     to the nearest integer (ties to even) and added in int64 with atomics or
+//     shuffles -- integer addition is associative, so any order gives the
+//     same bits;
+//   * scalar quotients/square roots of those sums are taken in fp64 and
+//     rounded once to fp32.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/disc.h"
+
+namespace disc {
+
+// fixed-point scales (bits after the binary point) of the exact sums
+constexpr int S_TOK = 32;   // token sums (mean token, Eq. 1)
+constexpr int S_SQ = 28;    // sums over the embedding dimension
+constexpr int S_NRM = 28;   // sum of residual norms (Eq. 1)
+constexpr int S_A = 24;     // coverage x distinctiveness sums
+constexpr int S_SEM = 32;   // coverage x ReLU(cosine) sums
+constexpr int S_EMB = 40;   // pooled embedding sums
+constexpr int S_VEC = 32;   // voxel normal and S_angle sums
+
+constexpr float TOKEN_LIMIT = 1024.0f;
+constexpr int KEY_BITS = 18;
+constexpr int32_t KEY_BIAS = 1 << (KEY_BITS - 1);
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+constexpr int MAX_MASKS = 256;
+constexpr int GEMM_MT = 128;    // token-dimension rows per GEMM tile
+constexpr int GEMM_KC = 32;     // patches per GEMM pipeline chunk
+
+__device__ __forceinline__ long long fix32f(float x, int S)
+{
+    return __float2ll_rn(__fmul_rn(x, __int_as_float((127 + S) << 23)));
+}
+__device__ __forceinline__ double unfix(long long n, int S)
+{
+    return __dmul_rn(__ll2double_rn(n), __longlong_as_double((long long)(1023 - S) << 52));
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// floor(p / s) per axis, packed as three biased 18-bit fields; false when a
+// coordinate is out of range.
+__device__ __forceinline__ bool voxel_key(float px, float py, float pz, float s,
+                                          unsigned long long* key)
+{
+    float k[3] = {floorf(__fdiv_rn(px, s)), floorf(__fdiv_rn(py, s)), floorf(__fdiv_rn(pz, s))};
+    unsigned long long out = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (!(k[a] >= -(float)KEY_BIAS && k[a] <= (float)(KEY_BIAS - 1))) return false;
+        out = (out << KEY_BITS) | (unsigned long long)((int)k[a] + KEY_BIAS);
+    }
+    *key = out;
+    return true;
+}
+
+__device__ __forceinline__ void unpack_key(unsigned long long key, int k[3])
+{
+    const unsigned long long mask = (1ull << KEY_BITS) - 1;
+    k[0] = (int)((key >> (2 * KEY_BITS)) & mask) - KEY_BIAS;
+    k[1] = (int)((key >> KEY_BITS) & mask) - KEY_BIAS;
+    k[2] = (int)(key & mask) - KEY_BIAS;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Device state.  Plain structs of device pointers, passed to kernels by value.
+
+struct VoxelTable {              // open addressing, linear probing
+    unsigned long long* keys;    // EMPTY_KEY = free
+    int32_t* labels;             // instance id at insertion (resolve via parent)
+    unsigned long long mask;     // capacity - 1 (capacity is a power of two)
+    unsigned long long* used;    // number of occupied slots
+};
+
+struct Instances {
+    int32_t* parent;             // flat: parent[i] is always a root
+    long long* count;            // voxels per root
+    float* Q;
+    float* E;                    // [cap][D] stored embedding
+    int32_t* n_obs;
+    int32_t cap;
+};
+
+// counters of one frame, written on the device and copied back to the host
+struct FrameCounters {
+    int32_t n_entries;           // unique (segment, voxel) pairs
+    int32_t n_pairs;             // distinct (segment, root) overlaps
+    int32_t n_new;               // distinct absent voxels
+    int32_t valid_pixels;
+    int32_t dropped_pixels;
+    int32_t active_instances;
+    int32_t new_instances;
+    int32_t merges;
+    int32_t live_segments;
+    int32_t borderline;
+    int32_t max_probe;
+    int32_t err;                 // disc_status of the frame (0 = ok)
+    int32_t next_id;             // instance ids handed out so far
+    int32_t num_masks;           // of the frame
+    int32_t n_edges;
+    int32_t pad;
+};
+
+struct Scratch {
+    // Eq. 1
+    long long* sumF;    // [D]
+    float* fbar;        // [D]
+    float* gvec;        // [D]
+    long long* gg;      // [1]
+    long long* nsum;    // [1]
+    long long* dotg;    // [P]
+    long long* ffp;     // [P]
+    float* nrm;         // [P]
+    float* Dp;          // [P]
+    float* cosg;        // [P]
+    float* fnorm;       // [P]
+    // coverage / weights / pooling
+    int32_t* cov;       // [MAX_MASKS][P]
+    int32_t* npix;      // [MAX_MASKS]
+    float* W;           // [Npad_max][Kpad] GEMM operand, zero padded
+    float* S;           // [MAX_MASKS][5]
+    float* Bm;          // [MAX_MASKS] sum_p w ||f_p|| (error-bound scale)
+    float* Ecan;        // [MAX_MASKS][D]
+    float* Efast;       // [MAX_MASKS][D]
+    long long* ang;     // [MAX_MASKS]
+    int32_t* nvox;      // [MAX_MASKS]
+    int32_t* segrep;    // [MAX_MASKS]
+    // per-frame hashes (cleared slot by slot at the start of the next frame)
+    unsigned long long* skeys;  // (mask << 54 | voxel key) -> slot; EMPTY = 0
+    int32_t* snpx;              // pixels per slot
+    long long* snrm;            // [3][scap] normal sums per slot
+    int32_t* slist;             // used slots
+    unsigned long long smask;
+    unsigned long long* okeys;  // (mask << 32 | root) ; EMPTY = ~0
+    int32_t* ocnt;
+    int32_t* olist;
+    unsigned long long omask;
+    unsigned long long* nkeys;  // absent voxel key ; EMPTY = ~0
+    int32_t* nown;              // lowest mask label containing it
+    int32_t* nlist;
+    unsigned long long nmask;
+    // association
+    int32_t* edge_m;    // [edge_cap]
+    int32_t* edge_k;
+    int32_t edge_cap;
+    FrameCounters* ctr;
+};
+
+// frame parameters passed by value
+struct FrameParams {
+    int32_t H, W, M, P, D, Ph, Pw, Kpad, Npad;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float voxel, z_min, z_max, eps, tau, lambda_size;
+    int32_t ov_num, ov_den, min_px;
+    int32_t token_bf16;
+    const float* depth;
+    const uint16_t* labels;
+    const void* tokens;
+    const float* gembed;   // nullable
+};
+
+}  // namespace disc

@@ -1,0 +1,277 @@
+// D-weighted mask pooling as a tensor-core GEMM (Sec. III-C: "aggregating the
+// patch features within the segmentation mask, weighted by D").
+//
+//   E[m][d] = sum_p W[m][p] * F[p][d]      (W: pooling weights, F: tokens)
+//
+// computed as E^T = F^T W^T so the long token dimension D fills the 128 rows
+// of one tcgen05 MMA and the masks (<= 256) form its N dimension:
+//   A (128 x 32, K-major) = F^T tile  -- transposed while staged into shared memory
+//   B (N   x 32, K-major) = W tile    -- W rows are already K-contiguous
+// The fp32 operands are split as x = hi + lo with hi, lo TF32 and three
+// kind::tf32 MMAs (hi*hi + hi*lo + lo*hi) accumulate in fp32 in TMEM, which
+// keeps the fp32-level accuracy of the product (relative error ~1e-6).
+//
+// One CTA = one 128-row tile of D; one elected thread issues the MMAs; a
+// two-stage shared-memory ring is recycled through mbarriers that
+// tcgen05.commit arrives on.  Every wait is bounded by a global-timer limit
+// after which the kernel records DISC_ERR_TIMEOUT and returns.
+#include <cuda_bf16.h>
+
+#include "disc_common.cuh"
+#include "kernels.h"
+
+namespace disc {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor, SWIZZLE_NONE, K-major canonical layout:
+// core matrices of 8 rows x 16 bytes stored contiguously (128 B); LBO = byte
+// distance between core matrices adjacent along K, SBO = along M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the tcgen05 family
+    return d;                // base offset 0, absolute LBO mode, no swizzle
+}
+
+// Instruction descriptor of kind::tf32: D fp32, A/B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity; false after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ float ldtok(const T* F, size_t i);
+template <>
+__device__ __forceinline__ float ldtok<float>(const float* F, size_t i) { return __ldg(F + i); }
+template <>
+__device__ __forceinline__ float ldtok<__nv_bfloat16>(const __nv_bfloat16* F, size_t i) { return __bfloat162float(F[i]); }
+
+}  // namespace
+
+constexpr uint32_t A_TILE_BYTES = GEMM_MT * GEMM_KC * 4;  // 16 KB
+constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 4-wide K group
+
+// two pipeline stages + barriers; the trailing guard keeps every address an
+// MMA descriptor of this kernel can form inside the allocation
+constexpr size_t GEMM_SMEM_GUARD = 48 * 1024;
+__host__ size_t gemm_smem_bytes(int NT)
+{
+    return 2 * (2 * A_TILE_BYTES + 2 * (size_t)NT * GEMM_KC * 4) + 64 + GEMM_SMEM_GUARD;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, 1) k_pool_gemm(FrameParams fp, Scratch sc, int NT)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const T* F = (const T*)fp.tokens;
+    const int D = fp.D, P = fp.P, M = fp.M;
+    const int d0 = blockIdx.x * GEMM_MT;
+    if (sc.ctr->err) return;  // uniform for the block
+
+    const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * 4;
+    const uint32_t B_LBO = (uint32_t)NT * 16;
+    const uint32_t STAGE = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
+    uint64_t* mbar = (uint64_t*)(smem + 2 * STAGE);
+    uint32_t* tmem_slot = (uint32_t*)(mbar + 2);
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)NT) ncols <<= 1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = idesc_tf32(GEMM_MT, NT);
+    const int nchunks = (P + GEMM_KC - 1) / GEMM_KC;
+    bool failed = false;
+    int last_commit = -1;  // chunk of the most recent commit (same on all threads)
+
+    for (int c = 0; c < nchunks && !failed; c++) {
+        const int s = c & 1;
+        uint8_t* st = smem + s * STAGE;
+        if (c >= 2) {
+            // the MMAs of chunk c-2 read this stage: wait for their commit
+            bool ok = mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1));
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+        }
+        const int p0 = c * GEMM_KC;
+        // A: F^T tile. Thread tid owns row r = tid (token dimension d0 + tid).
+        {
+            const int d = d0 + tid;
+            float* Ahi = (float*)st;
+            float* Alo = (float*)(st + A_TILE_BYTES);
+#pragma unroll
+            for (int kq = 0; kq < GEMM_KC / 4; kq++) {
+                float x[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int p = p0 + 4 * kq + j;
+                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
+                }
+                float4 hi, lo;
+                hi.x = tf32_rna(x[0]); lo.x = tf32_rna(x[0] - hi.x);
+                hi.y = tf32_rna(x[1]); lo.y = tf32_rna(x[1] - hi.y);
+                hi.z = tf32_rna(x[2]); lo.z = tf32_rna(x[2] - hi.z);
+                hi.w = tf32_rna(x[3]); lo.w = tf32_rna(x[3] - hi.w);
+                const uint32_t off = kq * A_LBO + tid * 16;
+                *(float4*)((uint8_t*)Ahi + off) = hi;
+                *(float4*)((uint8_t*)Alo + off) = lo;
+            }
+        }
+        // B: W tile, NT rows x 32 patches, 16-byte granules
+        {
+            uint8_t* Bhi = st + 2 * A_TILE_BYTES;
+            uint8_t* Blo = Bhi + B_TILE_BYTES;
+            for (int g = tid; g < NT * (GEMM_KC / 4); g += 128) {
+                const int n = g >> 3, kq = g & 7;
+                float4 x = *(const float4*)(sc.W + (size_t)n * fp.Kpad + p0 + 4 * kq);
+                float4 hi, lo;
+                hi.x = tf32_rna(x.x); lo.x = tf32_rna(x.x - hi.x);
+                hi.y = tf32_rna(x.y); lo.y = tf32_rna(x.y - hi.y);
+                hi.z = tf32_rna(x.z); lo.z = tf32_rna(x.z - hi.z);
+                hi.w = tf32_rna(x.w); lo.w = tf32_rna(x.w - hi.w);
+                const uint32_t off = kq * B_LBO + n * 16;
+                *(float4*)(Bhi + off) = hi;
+                *(float4*)(Blo + off) = lo;
+            }
+        }
+        // make the generic-proxy stores visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_TILE_BYTES;
+            const uint32_t b_hi = a_hi + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < GEMM_KC / 8; ks++) {
+                const uint32_t ao = ks * 2 * A_LBO, bo = ks * 2 * B_LBO;
+                const uint64_t dah = smem_desc(a_hi + ao, A_LBO, 128), dal = smem_desc(a_lo + ao, A_LBO, 128);
+                const uint64_t dbh = smem_desc(b_hi + bo, B_LBO, 128), dbl = smem_desc(b_lo + bo, B_LBO, 128);
+                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            mma_commit(smem_u32(&mbar[s]));
+        }
+        last_commit = c;
+    }
+    if (!failed && nchunks > 0) {
+        const int c = nchunks - 1;
+        bool ok = mbar_wait(smem_u32(&mbar[c & 1]), (uint32_t)((c >> 1) & 1));
+        failed = __syncthreads_or(!ok);
+    }
+    fence_after();
+    if (!failed && nchunks > 0) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows d0 + 32w + lane)
+        const int d = d0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int m = c0 + j;
+                if (m < M && d < D) sc.Efast[(size_t)m * D + d] = __uint_as_float(r[j]);
+            }
+        }
+    } else if (failed) {
+        // give MMAs still in flight one more bounded wait before TMEM is freed
+        if (last_commit >= 0 && tid == 0)
+            mbar_wait(smem_u32(&mbar[last_commit & 1]), (uint32_t)((last_commit >> 1) & 1));
+        if (tid == 0) atomicCAS(&sc.ctr->err, 0, DISC_ERR_TIMEOUT);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+void launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+{
+    if (fp.M <= 0) return;
+    const int NT = fp.Npad;
+    const size_t smem = gemm_smem_bytes(NT);
+    dim3 g((fp.D + GEMM_MT - 1) / GEMM_MT);
+    if (fp.token_bf16) k_pool_gemm<__nv_bfloat16><<<g, 128, smem, st>>>(fp, sc, NT);
+    else k_pool_gemm<float><<<g, 128, smem, st>>>(fp, sc, NT);
+}
+
+void set_gemm_kernel_attrs()
+{
+    const int mx = (int)gemm_smem_bytes(MAX_MASKS);
+    cudaFuncSetAttribute(k_pool_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
+}  // namespace disc

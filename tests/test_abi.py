@@ -1,0 +1,69 @@
+"""The C ABI library builds, loads and exports every entry point of
+include/disc.h (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libdisc():
+    from paper_2603_03935_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "disc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**(disc_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("disc_map_create", "disc_integrate_frame", "disc_integrate_frames", "disc_query_topk",
+                     "disc_query_points", "disc_map_destroy", "disc_map_export_voxels", "disc_map_save",
+                     "disc_map_load"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libdisc):
+    missing = [n for n in declared_functions() if not hasattr(libdisc, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(libdisc):
+    import paper_2603_03935_gb300 as pkg
+    cfg = pkg.config_default()
+    assert cfg["lambda_size"] == pytest.approx(3.3)
+    assert cfg["tau_cos"] == pytest.approx(0.75)
+    assert (cfg["ov_num"], cfg["ov_den"]) == (1, 5)
+    assert pkg.status_str(0) == "ok"
+    assert pkg.status_str(-7) == "token out of range"
+    # key packing agrees with the oracle's independent packing
+    import oracle
+    for k in [(0, 0, 0), (-1, 2, -3), (131071, -131072, 5)]:
+        key = pkg.pack_key(*k)
+        assert oracle.unpack_key(key) == k
+    assert pkg.pack_key(1, 2, 3) == oracle.point_key(1.01, 2.01, 3.01, 1.0)
+
+
+def test_product_path_refuses_to_run_without_the_library(tmp_path, monkeypatch):
+    import paper_2603_03935_gb300.binding as b
+    monkeypatch.setattr(b, "_lib", None)
+    monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        b.lib()
+
+
+def test_create_without_device_fails_cleanly(libdisc):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    import paper_2603_03935_gb300 as pkg
+    with pytest.raises(pkg.DiscError):
+        pkg.DiscMap()

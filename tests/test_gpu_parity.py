@@ -1,0 +1,237 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+Bit-exact: voxel keys, coverage counts, labels, overlap/instance counters,
+and every quantity the method computes with exact sums (D, weights, Q terms,
+the exact pooled embedding, stored instance embeddings).  The tensor-core
+pooled embedding is held to 1e-5 relative error per vector.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import common, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2603_03935_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    return torch, dev
+
+
+def _dframe(torch, dev, fr, i):
+    from paper_2603_03935_gb300 import device_frame
+    sc = fr.scene
+    d = torch.from_numpy(fr.depth[i]).to(dev)
+    l = torch.from_numpy(fr.labels[i].view(np.int16)).to(dev)
+    t = torch.from_numpy(fr.tokens[i]).to(dev)
+    return device_frame(d, l, t, fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy), fr.num_masks[i])
+
+
+def _hframe(fr, i):
+    from paper_2603_03935_gb300 import host_frame
+    sc = fr.scene
+    return host_frame(fr.depth[i], fr.labels[i], fr.tokens[i], fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy),
+                      fr.num_masks[i])
+
+
+def run_parity(torch_dev, scene, frames, host=False, **cfg_kw):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    fr = scene.render(frames)
+    cfg = common.disc_cfg(scene, **cfg_kw)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    stats = []
+    for i in range(len(fr)):
+        st = gmap.integrate(_hframe(fr, i) if host else _dframe(torch, dev, fr, i))
+        o = omap.integrate(*oracle.frame_args(fr, i))
+        common.compare_frame(st, gmap.last_frame(), o, ctx=f"{scene.name} frame {i}")
+        stats.append(st)
+    common.compare_maps(gmap, omap, ctx=scene.name)
+    return gmap, omap, stats
+
+
+def test_tiny_trajectory_parity(torch_dev):
+    run_parity(torch_dev, synth.tiny_scene(), range(20))
+
+
+def test_tiny_parity_with_host_inputs(torch_dev):
+    run_parity(torch_dev, synth.tiny_scene(), range(0, 20, 3), host=True)
+
+
+def test_tiny_parity_with_growth_of_both_tables(torch_dev):
+    # tiny initial capacities force rehashing and instance-table growth
+    run_parity(torch_dev, synth.tiny_scene(), range(20), voxel_capacity=256, instance_capacity=2)
+
+
+def test_room_scale_frames_parity(torch_dev):
+    # full 640x480 frames, 24x24x768 tokens, 40 masks, 2.5 cm voxels
+    sc = synth.room_scene(num_frames=2000)
+    run_parity(torch_dev, sc, [0, 1, 2, 3, 250, 251], voxel_capacity=1 << 22, instance_capacity=1024)
+
+
+def test_ragged_token_grid_and_odd_frame(torch_dev):
+    # P = 7 x 5 = 35 (ragged last GEMM chunk), D = 200 (ragged last tile),
+    # 50 x 37 pixels (patch bands of uneven height)
+    prims = [(0, 1, (0.013, 0.013, 0.213), (0.3, 0.25, 0.2)),
+             (1, 2, (0.6, 0.5, 0.25), (0.2, 0.2, 0.25))]
+    sc = scenes.custom_scene(prims, scenes.orbit((0.2, 0.2, 0.2), 1.6, 0.9, 6, sweep=np.deg2rad(60)),
+                             width=50, height=37, f=40.0, dim=200, patch=(7, 5), voxel=0.04, max_masks=5)
+    run_parity(torch_dev, sc, range(6))
+
+
+def test_equal_results_alone_and_batched(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(20))
+    cfg = common.disc_cfg(sc)
+    a, b = DiscMap(**cfg), DiscMap(**cfg)
+    for i in range(20):
+        a.integrate(_dframe(torch, dev, fr, i))
+    frames = [_dframe(torch, dev, fr, i) for i in range(20)]
+    stats, done, rc = b.integrate_frames(frames)
+    assert rc == 0 and done == 20
+    ka, ia = a.voxels()
+    kb, ib = b.voxels()
+    assert np.array_equal(ka, kb) and np.array_equal(ia, ib)
+    ea, eb = a.instances(), b.instances()
+    for k in ("parent", "count", "n_obs"):
+        assert np.array_equal(ea[k], eb[k])
+    assert np.array_equal(ea["E"], eb["E"])
+
+
+def test_empty_and_degenerate_frames(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    sc = synth.tiny_scene()
+    cfg = common.disc_cfg(sc)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    H, W, P, D = sc.height, sc.width, sc.patch_h * sc.patch_w, sc.dim
+    rng = np.random.default_rng(3)
+    tok = rng.standard_normal((P, D)).astype(np.float32)
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    pose = sc.poses[0]
+    cases = [
+        ("no masks", np.full((H, W), 2.0, np.float32), np.zeros((H, W), np.uint16), 0),
+        ("all depth invalid", np.full((H, W), np.nan, np.float32), np.ones((H, W), np.uint16), 1),
+        ("labels above num_masks", np.full((H, W), 2.0, np.float32), np.full((H, W), 5, np.uint16), 2),
+        ("masks below the size filter", np.full((H, W), 2.0, np.float32),
+         np.pad(np.ones((1, 2), np.uint16), ((0, H - 1), (0, W - 2))), 1),
+        ("constant tokens", np.full((H, W), 2.0, np.float32), np.ones((H, W), np.uint16), 1),
+    ]
+    for name, depth, lab, M in cases:
+        t = np.full_like(tok, 0.5) if name == "constant tokens" else tok
+        st = gmap.integrate(host_frame(depth, lab, t, pose, intr, M))
+        o = omap.integrate(depth, lab, t, pose, intr, M)
+        common.compare_frame(st, gmap.last_frame(), o, ctx=name)
+    common.compare_maps(gmap, omap, ctx="degenerate")
+
+
+def test_token_range_error_leaves_the_map_unchanged(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    sc = synth.tiny_scene()
+    fr = sc.render(range(3))
+    gmap = DiscMap(**common.disc_cfg(sc))
+    gmap.integrate(_hframe(fr, 0))
+    k0, i0 = gmap.voxels()
+    bad = fr.tokens[1].copy()
+    bad[3, 7] = np.inf
+    st = gmap.integrate(host_frame(fr.depth[1], fr.labels[1], bad, fr.poses[1], (sc.fx, sc.fy, sc.cx, sc.cy),
+                                   fr.num_masks[1]), check=False)
+    assert st["rc"] == -7 and st["status"] == -7
+    k1, i1 = gmap.voxels()
+    assert np.array_equal(k0, k1) and np.array_equal(i0, i1)
+    # and a batch stops at the failing frame
+    frames = [_hframe(fr, 2), host_frame(fr.depth[1], fr.labels[1], bad, fr.poses[1],
+                                         (sc.fx, sc.fy, sc.cx, sc.cy), fr.num_masks[1]), _hframe(fr, 0)]
+    stats, done, rc = gmap.integrate_frames(frames, check=False)
+    assert rc == -7 and done == 1
+
+
+def test_borderline_cosines_are_rescored_exactly(torch_dev):
+    # put tau_cos exactly on a cosine the oracle computes for a real
+    # (segment, instance) pair: the fast tensor-core score lands inside the
+    # error band and the exact re-score must reproduce the oracle's decision
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(3))
+    probe = oracle.OracleMap(**oracle.config_for_scene(sc))
+    probe.integrate(*oracle.frame_args(fr, 0))
+    E0 = probe.instances()["E"]
+    r1 = probe.integrate(*oracle.frame_args(fr, 1))
+    m = int(np.argmax(r1["nvox"]))
+    k = int(r1["rep"][m]) if r1["rep"][m] < len(E0) else 0
+    tau = oracle.cosine(r1["E"][m], E0[k])
+    for t in (tau, np.nextafter(np.float32(tau), np.float32(2))):
+        cfg = common.disc_cfg(sc, tau_cos=float(t))
+        gmap = DiscMap(**cfg)
+        omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+        border = 0
+        for i in range(3):
+            st = gmap.integrate(_dframe(torch, dev, fr, i))
+            o = omap.integrate(*oracle.frame_args(fr, i))
+            common.compare_frame(st, gmap.last_frame(), o, ctx=f"tau={t} frame {i}")
+            border += st["borderline_rescored"]
+        common.compare_maps(gmap, omap, ctx=f"tau={t}")
+        assert border >= 1
+
+
+def test_checkpoint_resume_equals_uninterrupted(torch_dev, tmp_path):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(12))
+    cfg = common.disc_cfg(sc)
+    full = DiscMap(**cfg)
+    for i in range(12):
+        full.integrate(_dframe(torch, dev, fr, i))
+    part = DiscMap(**cfg)
+    for i in range(6):
+        part.integrate(_dframe(torch, dev, fr, i))
+    part.save(tmp_path / "map.bin")
+    part.close()
+    res = DiscMap.load(tmp_path / "map.bin")
+    for i in range(6, 12):
+        res.integrate(_dframe(torch, dev, fr, i))
+    ka, ia = full.voxels()
+    kb, ib = res.voxels()
+    assert np.array_equal(ka, kb) and np.array_equal(ia, ib)
+    ea, eb = full.instances(), res.instances()
+    for k in ("parent", "count", "n_obs", "Q", "E"):
+        assert np.array_equal(ea[k], eb[k])
+
+
+def test_queries(torch_dev):
+    torch, dev = torch_dev
+    sc = synth.tiny_scene()
+    gmap, omap, _ = run_parity(torch_dev, sc, range(8))
+    inst = omap.instances()
+    live = np.nonzero(inst["parent"] == np.arange(len(inst["parent"])))[0]
+    # query = an instance's own embedding -> that instance first, cosine 1
+    q = inst["E"][live[:4]]
+    ids, scores = gmap.query_topk(q, 3)
+    assert np.array_equal(ids[:, 0], live[:4])
+    np.testing.assert_allclose(scores[:, 0], 1.0, atol=1e-5)
+    # scores against an fp64 recomputation
+    E = inst["E"][live].astype(np.float64)
+    for qi in range(len(q)):
+        c = E @ q[qi].astype(np.float64) / (np.linalg.norm(E, axis=1) * np.linalg.norm(q[qi]))
+        order = np.lexsort((live, -c))[:3]
+        np.testing.assert_allclose(scores[qi], c[order], atol=1e-5)
+    # point queries: voxel centres map to their instance, far points to -1
+    keys, vids = omap.voxels()
+    ks = np.array([oracle.unpack_key(k) for k in keys[:200]], np.float64)
+    pts = ((ks + 0.5) * sc.voxel_size).astype(np.float32)
+    got = gmap.query_points(np.vstack([pts, [[100.0, 100.0, 100.0]]]))
+    assert np.array_equal(got[:-1], vids[:200]) and got[-1] == -1
