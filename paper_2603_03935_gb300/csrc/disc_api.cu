@@ -419,8 +419,14 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     }
     static bool attrs_set = false;
     if (!attrs_set) {
-        set_feature_kernel_attrs(100 * 1024);
-        set_gemm_kernel_attrs();
+        cudaError_t e = set_feature_kernel_attrs(100 * 1024);
+        if (e == cudaSuccess) e = set_gemm_kernel_attrs();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (m->own_stream) cudaStreamDestroy(m->stream);
+            delete m;
+            return DISC_ERR_CUDA;
+        }
         attrs_set = true;
     }
     const int D = m->D, P = m->P, MM = MAX_MASKS;

@@ -263,11 +263,15 @@ void launch_features(const FrameParams& fp, const Scratch& sc, cudaStream_t st, 
     }
 }
 
-void set_feature_kernel_attrs(int max_dyn_smem)
+cudaError_t set_feature_kernel_attrs(int max_dyn_smem)
 {
-    cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
-    cudaFuncSetAttribute(k_pool_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
-    cudaFuncSetAttribute(k_pool_exact<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pool_exact<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pool_exact<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_dyn_smem);
+    return e;
 }
 
 }  // namespace disc

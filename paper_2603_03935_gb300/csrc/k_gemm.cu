@@ -17,6 +17,8 @@
 // after which the kernel records DISC_ERR_TIMEOUT and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "disc_common.cuh"
 #include "kernels.h"
 
@@ -107,9 +109,11 @@ constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 4-wide K
 // two pipeline stages + barriers; the trailing guard keeps every address an
 // MMA descriptor of this kernel can form inside the allocation
 constexpr size_t GEMM_SMEM_GUARD = 48 * 1024;
+constexpr size_t SMEM_MAX = 227 * 1024;
 __host__ size_t gemm_smem_bytes(int NT)
 {
-    return 2 * (2 * A_TILE_BYTES + 2 * (size_t)NT * GEMM_KC * 4) + 64 + GEMM_SMEM_GUARD;
+    const size_t base = 2 * (2 * A_TILE_BYTES + 2 * (size_t)NT * GEMM_KC * 4) + 64;
+    return std::min(base + GEMM_SMEM_GUARD, std::max(base, SMEM_MAX));
 }
 
 template <typename T>
@@ -267,11 +271,13 @@ void launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
     else k_pool_gemm<float><<<g, 128, smem, st>>>(fp, sc, NT);
 }
 
-void set_gemm_kernel_attrs()
+cudaError_t set_gemm_kernel_attrs()
 {
     const int mx = (int)gemm_smem_bytes(MAX_MASKS);
-    cudaFuncSetAttribute(k_pool_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = cudaFuncSetAttribute(k_pool_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
 }
 
 }  // namespace disc

@@ -9,11 +9,11 @@ namespace disc {
 
 // Eq. 1, coverage, weights + image quality terms, exact pooling
 void launch_features(const FrameParams& fp, const Scratch& sc, cudaStream_t st, int cov_smem_limit);
-void set_feature_kernel_attrs(int max_dyn_smem);
+cudaError_t set_feature_kernel_attrs(int max_dyn_smem);
 
 // tensor-core pooling GEMM (fast embedding used by the association gate)
 void launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-void set_gemm_kernel_attrs();
+cudaError_t set_gemm_kernel_attrs();
 size_t gemm_smem_bytes(int NT);
 
 // map side
