@@ -1,0 +1,395 @@
+"""Benchmark of the DISC per-frame integration step on GB300.
+
+Workload (the Room-scale configuration): a 10x8x3 m synthetic room with 80
+random boxes/ellipsoids, a 2000-frame closed camera path, 640x480 fp32 depth
+with 1 % noise, 40 masks per frame, 24x24x768 fp32 patch tokens, 2.5 cm
+voxels.  A step integrates B consecutive frames of the trajectory into one
+resident map through disc_integrate_frames (all steps a1-a10 per frame).
+
+Reported: frames/s (whole job, all ranks), voxel-updates/s, p50/p99 single-
+frame latency, the roofline of the dominant kernel (per-phase CUDA events on
+the map's stream), an end-to-end figure through the same C ABI with pinned
+host buffers (H2D inside the timed region), and the CPU oracle's throughput on
+a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & voxel-updates/s on 1 GB300 (plain vs batched/served); p50/p99 frame ms"
+WORKLOAD = "Room-scale plain: 10x8x3 m room, 80 boxes/ellipsoids, 640x480 fp32 depth (1% noise), " \
+           "40 masks/frame, tokens 24x24x768 fp32, voxel 2.5 cm, FP32"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames-per-step", type=int, default=32)
+    ap.add_argument("--latency-frames", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def room_cfg(scene):
+    from tests import common
+    return common.disc_cfg(scene, voxel_capacity=1 << 24, instance_capacity=1 << 16)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.path = None
+        self.idx = device_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(phase, st, H, W, P, D, M, Kpad):
+    """Bytes one launch of a phase must move for one frame.
+
+    backproject: depth (4 B) + labels (2 B) per pixel, plus for every unique
+    (segment, voxel) pair its 8 B key, 4 B pixel count and 3 x 8 B normal sums.
+    """
+    ne = st["unique_seg_voxels"]
+    if phase == "backproject":
+        return 6 * H * W + 36 * ne
+    if phase == "entries":
+        return ne * (8 + 4 + 24) + ne * 12 + st["new_voxels"] * 12 + st["overlap_pairs"] * 12
+    if phase == "token_stats":
+        return 4 * P * D
+    if phase == "pool_gemm":
+        return 4 * P * D + 4 * M * Kpad + 4 * M * D
+    if phase == "coverage":
+        return 2 * H * W + 4 * M * P
+    if phase == "insert":
+        return 24 * st["new_voxels"]
+    return 0
+
+
+def run_reference(args, rank):
+    """The oracle, as it stands, on the host cores: same workload and metric."""
+    import oracle
+    import synth
+    if rank != 0:
+        return
+    scene = synth.room_scene()
+    per_step = 2
+    n = (args.warmup + args.steps) * per_step
+    fr = scene.render(range(n))
+    m = oracle.OracleMap(**oracle.config_for_scene(scene))
+    k = 0
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            m.integrate(*oracle.frame_args(fr, k), report=False)
+            k += 1
+    t0 = time.perf_counter()
+    upd = 0
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            r = m.integrate(*oracle.frame_args(fr, k), report=True)
+            upd += r["n_seg"]
+            k += 1
+    dt = time.perf_counter() - t0
+    fps = args.steps * per_step / dt
+    out = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded room trajectory)",
+           "config": {"workload": WORKLOAD, "frames_per_step": per_step, "l2": "n/a (CPU)"},
+           "voxel_updates_per_s": upd / dt,
+           "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                            "sample": f"frames {args.warmup * per_step}..{k - 1} of the Room trajectory"},
+           "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline(scene, fr, budget_s):
+    import oracle
+    m = oracle.OracleMap(**oracle.config_for_scene(scene))
+    t0 = time.perf_counter()
+    n = 0
+    upd = 0
+    while n < len(fr) and time.perf_counter() - t0 < budget_s:
+        r = m.integrate(*oracle.frame_args(fr, n), report=True)
+        upd += r["n_seg"]
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} frames of the Room trajectory, fresh map ({upd / dt:.3g} voxel-updates/s)"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2603_03935_gb300 import DiscMap, binding
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if not os.path.exists(binding.LIB_PATH):
+        if rank == 0:
+            import __graft_entry__
+            __graft_entry__.build()
+        if world > 1:
+            dist.barrier()
+
+    B, K, Wm = args.frames_per_step, args.steps, args.warmup
+    # replicas only: every rank integrates its own map of its own scene
+    scene = synth.room_scene(seed=1 + rank)
+    n_main = (Wm + K) * B
+    n_extra = 2 * B + args.latency_frames
+    fr = scene.render(range(n_main + n_extra))
+    H, W_, P, D = scene.height, scene.width, scene.patch_h * scene.patch_w, scene.dim
+    Kpad = (P + 31) // 32 * 32
+    intr = (scene.fx, scene.fy, scene.cx, scene.cy)
+
+    # a dedicated stream: the map enqueues on it, the timing events are
+    # recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    cfg = room_cfg(scene)
+    cfg["cuda_stream"] = stream.cuda_stream
+    cfg["device"] = local
+    depth = torch.from_numpy(fr.depth).to(dev)
+    labels = torch.from_numpy(fr.labels.view(np.int16)).to(dev)
+    tokens = torch.from_numpy(fr.tokens).to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def frame_array(lo, hi, on_device=True, host=None):
+        n = hi - lo
+        arr = (binding.Frame * n)()
+        for j in range(n):
+            i = lo + j
+            f = arr[j]
+            f.width, f.height = W_, H
+            f.fx, f.fy, f.cx, f.cy = intr
+            for q, v in enumerate(fr.poses[i].reshape(16)):
+                f.T_world_cam[q] = float(v)
+            if on_device:
+                f.depth, f.labels, f.tokens = depth[i].data_ptr(), labels[i].data_ptr(), tokens[i].data_ptr()
+            else:
+                hd, hl, ht = host
+                f.depth, f.labels, f.tokens = hd[i].data_ptr(), hl[i].data_ptr(), ht[i].data_ptr()
+            f.token_dtype = 0
+            f.num_masks = int(fr.num_masks[i])
+            f.global_embed = None
+            f.inputs_on_device = 1 if on_device else 0
+        return arr
+
+    steps = [frame_array(s * B, (s + 1) * B) for s in range(Wm + K)]
+    stats = (binding.Stats * B)()
+
+    gmap = DiscMap(**cfg)
+    for s in range(Wm):
+        rc = gmap.integrate_frames_raw(steps[s], B, stats)
+        assert rc == 0, rc
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = gmap.kernel_launches()
+    times = []
+    updates = 0
+    new_vox = 0
+    for s in range(Wm, Wm + K):
+        flush.fill_(float(s))           # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = gmap.integrate_frames_raw(steps[s], B, stats)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        times.append(e0.elapsed_time(e1))
+        updates += sum(stats[j].unique_seg_voxels for j in range(B))
+        new_vox += sum(stats[j].new_voxels for j in range(B))
+    launches = gmap.kernel_launches() - launches0
+    total_ms = float(np.sum(times))
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    frames_all = K * B * world
+
+    # per-phase device time on the following frames (events around each phase)
+    lo = n_main
+    gmap.set_phase_timing(True)
+    ph_stats = (binding.Stats * B)()
+    rc = gmap.integrate_frames_raw(frame_array(lo, lo + B), B, ph_stats)
+    assert rc == 0, rc
+    phases = gmap.phase_times()
+    gmap.set_phase_timing(False)
+    lo += B
+
+    # single-frame latency (disc_integrate_frame, one synchronisation per frame)
+    lat = []
+    for i in range(lo, lo + args.latency_frames):
+        a = frame_array(i, i + 1)
+        st1 = binding.Stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = binding.lib().disc_integrate_frame(gmap._h, a, ctypes.byref(st1))
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        lat.append(e0.elapsed_time(e1))
+    gmap.close()
+
+    # dominant single-kernel phase and its roofline
+    peak, peak_kind = peaks()
+    per_frame = {k: v["ms"] / max(v["calls"], 1) for k, v in phases.items()}
+    single = ("backproject", "entries", "pool_gemm", "coverage", "insert", "associate", "pool_exact", "weights")
+    dom = max(single, key=lambda k: phases[k]["ms"])
+    st_list = [{k: getattr(ph_stats[j], k) for k, _ in binding.Stats._fields_} for j in range(B)]
+    alg = np.mean([algorithmic_bytes(dom, s_, H, W_, P, D, int(fr.num_masks[lo - B + j]), Kpad)
+                   for j, s_ in enumerate(st_list)])
+    dur_s = per_frame[dom] / 1e3
+    achieved = alg / dur_s / 1e9 if dur_s > 0 and alg > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": float(alg), "launch_us": per_frame[dom] * 1e3}
+
+    # end to end through the C ABI with pinned host buffers (H2D inside)
+    e2e = None
+    if not args.no_e2e:
+        hd = torch.from_numpy(fr.depth[:n_main]).pin_memory()
+        hl = torch.from_numpy(fr.labels[:n_main].view(np.int16)).pin_memory()
+        ht = torch.from_numpy(fr.tokens[:n_main]).pin_memory()
+        hsteps = [frame_array(s * B, (s + 1) * B, on_device=False, host=(hd, hl, ht)) for s in range(Wm + K)]
+        m2 = DiscMap(**cfg)
+        for s in range(Wm):
+            assert m2.integrate_frames_raw(hsteps[s], B, stats) == 0
+        torch.cuda.synchronize()
+        et = []
+        for s in range(Wm, Wm + K):
+            flush.fill_(float(s))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = m2.integrate_frames_raw(hsteps[s], B, stats)
+            e1.record(stream)
+            e1.synchronize()
+            assert rc == 0, rc
+            et.append(e0.elapsed_time(e1))
+        m2.close()
+        tt = torch.tensor([float(np.sum(et))], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": frames_all / (tt.item() / 1e3), "unit": "frames/s",
+               "h2d_bytes_per_step": B * (H * W_ * 6 + P * D * 4),
+               "d2h_bytes_per_step": B * 64}
+
+    if rank == 0:
+        cpu = cpu_baseline(scene, fr, args.cpu_seconds) if world == 1 else None
+        out = {"metric": METRIC, "value": frames_all / (total_ms / 1e3), "unit": "frames/s",
+               "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": total_ms / K,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded room trajectory; stands in for the paper's HM3D/Replica trajectories)",
+               "config": {"workload": WORKLOAD, "frames_per_step": B, "frames_timed": K * B,
+                          "l2": "flushed between timed steps (258 MB write)", "replicas": world},
+               "voxel_updates_per_s": updates * world / (total_ms / 1e3),
+               "new_voxels_per_s": new_vox * world / (total_ms / 1e3),
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"},
+               "frame_ms_batched": total_ms / (K * B),
+               "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
+               "gpu_launches": int(launches),
+               "roofline": roofline,
+               "cpu_baseline": cpu,
+               "e2e": e2e,
+               "clocks": clk}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,19 @@ uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz);
 /* The map's resolved configuration (capacities after rounding/growth). */
 disc_status disc_map_get_config(disc_map* map, disc_map_config* out);
 
+/* Kernels this map has enqueued since creation (every kernel of every phase). */
+int64_t disc_map_kernel_launches(disc_map* map);
+
+/* Per-phase timing with CUDA events recorded on the map's stream around each
+ * phase of every frame (off by default; enabling resets the totals).  Phases:
+ * 0 frame_begin, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
+ * 5 pool_gemm, 6 backproject, 7 entries (S_angle terms, map lookup), 8
+ * associate, 9 insert.  ms/launches/calls: [n] accumulated device time,
+ * kernels launched and timed intervals per phase (any may be NULL). */
+disc_status disc_map_set_phase_timing(disc_map* map, int32_t enable);
+disc_status disc_map_phase_times(disc_map* map, double* ms, int64_t* launches, int64_t* calls, int32_t n);
+const char* disc_phase_name(int32_t phase);
+
 /* Device memory held by the map, bytes. */
 int64_t disc_map_device_bytes(disc_map* map);
 

@@ -370,7 +370,10 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
     for (int m = 0; m < M; m++) {
         if (nvox[m] == 0) continue;
         for (auto& kv : ov[m]) {
-            bool geo = kv.second * (int64_t)cfg.ov_den >= (int64_t)cfg.ov_num * nvox[m];
+            // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) against ov_num/ov_den
+            int64_t vk = map->count[kv.first];
+            int64_t denom = std::min<int64_t>(nvox[m], vk);
+            bool geo = kv.second * (int64_t)cfg.ov_den >= (int64_t)cfg.ov_num * denom;
             if (!geo) continue;
             float c = cosine_exact(&Em[(size_t)m * D], map->E[kv.first].data(), D);
             if (c >= cfg.tau_cos) edges[m].push_back(kv.first);

@@ -83,6 +83,14 @@ def lib():
         L.disc_pack_key.restype = ctypes.c_uint64
         L.disc_map_get_config.argtypes = [c_vp, P(Config)]
         L.disc_map_get_config.restype = ctypes.c_int
+        L.disc_map_kernel_launches.argtypes = [c_vp]
+        L.disc_map_kernel_launches.restype = c_i64
+        L.disc_map_set_phase_timing.argtypes = [c_vp, c_i32]
+        L.disc_map_set_phase_timing.restype = ctypes.c_int
+        L.disc_map_phase_times.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
+        L.disc_map_phase_times.restype = ctypes.c_int
+        L.disc_phase_name.argtypes = [c_i32]
+        L.disc_phase_name.restype = ctypes.c_char_p
         L.disc_map_device_bytes.argtypes = [c_vp]
         L.disc_map_device_bytes.restype = c_i64
         L.disc_map_destroy.argtypes = [c_vp]
@@ -285,6 +293,22 @@ class DiscMap:
         ids = np.zeros(x.shape[0], np.int32)
         _check(lib().disc_query_points(self._h, x.ctypes.data, x.shape[0], ids.ctypes.data), "disc_query_points")
         return ids
+
+    def kernel_launches(self) -> int:
+        return int(lib().disc_map_kernel_launches(self._h))
+
+    def set_phase_timing(self, enable: bool):
+        _check(lib().disc_map_set_phase_timing(self._h, 1 if enable else 0), "disc_map_set_phase_timing")
+
+    def phase_times(self) -> dict:
+        n = 10
+        ms = np.zeros(n, np.float64)
+        la = np.zeros(n, np.int64)
+        ca = np.zeros(n, np.int64)
+        _check(lib().disc_map_phase_times(self._h, ms.ctypes.data, la.ctypes.data, ca.ctypes.data, n),
+               "disc_map_phase_times")
+        return {lib().disc_phase_name(i).decode(): dict(ms=float(ms[i]), launches=int(la[i]), calls=int(ca[i]))
+                for i in range(n)}
 
     def device_bytes(self) -> int:
         return int(lib().disc_map_device_bytes(self._h))

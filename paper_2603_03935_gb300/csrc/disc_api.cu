@@ -88,6 +88,19 @@ struct disc_map {
     void* d_tokens = nullptr;
     float* d_gembed = nullptr;
     int cov_smem_limit = 96 * 1024;
+    // kernel accounting and optional per-phase CUDA-event timing
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    double phase_ms[PH_COUNT] = {};
+    int64_t phase_launches[PH_COUNT] = {};
+    int64_t phase_calls[PH_COUNT] = {};
 };
 
 namespace {
@@ -237,6 +250,50 @@ disc_status ensure_instance_room(disc_map* m, int incoming)
     return DISC_OK;
 }
 
+cudaEvent_t take_event(disc_map* m)
+{
+    if (m->ev_used == m->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        m->ev_pool.push_back(e);
+    }
+    return m->ev_pool[m->ev_used++];
+}
+
+// Enqueue one phase; with timing on, bracket it with events on the map's stream.
+template <class F>
+void run_phase(disc_map* m, int ph, F&& launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (m->timing && (a = take_event(m))) cudaEventRecord(a, m->stream);
+    const int n = launch();
+    m->launches += n;
+    m->phase_launches[ph] += n;
+    if (a && (b = take_event(m))) {
+        cudaEventRecord(b, m->stream);
+        if (n > 0) m->marks.push_back({ph, a, b});
+    }
+}
+
+// After a synchronisation: fold the recorded phase intervals into the totals.
+void collect_timing(disc_map* m)
+{
+    for (auto& mk : m->marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
+            m->phase_ms[mk.phase] += ms;
+            m->phase_calls[mk.phase] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    m->marks.clear();
+    m->ev_used = 0;
+}
+
 disc_status check_frame(const disc_map* m, const disc_frame* f)
 {
     if (!f || !f->depth || !f->labels || !f->tokens) return DISC_ERR_INVALID_ARG;
@@ -311,14 +368,22 @@ disc_status enqueue_frame(disc_map* m, const disc_frame* f, int sticky, FrameCou
     Scratch sc = m->sc;
     sc.ctr = m->d_ctr + m->cur;
     FrameCounters* prev = m->d_ctr + (m->cur ^ 1);
-    launch_frame_begin(sc, prev, m->d_next_id, D, sticky, m->stream);
-    launch_features(fp, sc, m->stream, m->cov_smem_limit);
-    launch_pool_gemm(fp, sc, m->stream);
-    launch_geometry(fp, sc, m->vt, m->inst, m->stream);
+    cudaStream_t st = m->stream;
+    // error bound of the tensor-core pooled embedding relative to
+    // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
+    // 3 K products; and of a warp-level fp32 cosine
     const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * m->Kpad * std::ldexp(1.0, -24));
     const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
-    launch_associate(fp, sc, m->inst, m->d_next_id, eta, dot_err, m->stream);
-    if (M > 0) launch_insert(sc, m->vt, m->inst, m->stream);
+    run_phase(m, PH_BEGIN, [&] { return launch_frame_begin(sc, prev, m->d_next_id, D, sticky, st); });
+    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(fp, sc, st); });
+    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(fp, sc, st, m->cov_smem_limit); });
+    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(fp, sc, st); });
+    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(fp, sc, st); });
+    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(fp, sc, st); });
+    run_phase(m, PH_BACKPROJECT, [&] { return launch_backproject(fp, sc, st); });
+    run_phase(m, PH_ENTRIES, [&] { return launch_entries(fp, sc, m->vt, m->inst, st); });
+    run_phase(m, PH_ASSOCIATE, [&] { return launch_associate(fp, sc, m->inst, m->d_next_id, eta, dot_err, st); });
+    run_phase(m, PH_INSERT, [&] { return launch_insert(fp, sc, m->vt, m->inst, st); });
     if (hist) CK(cudaMemcpyAsync(hist, sc.ctr, sizeof(FrameCounters), cudaMemcpyDeviceToDevice, m->stream));
     CK(cudaGetLastError());
     m->cur ^= 1;
@@ -421,6 +486,7 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     if (!attrs_set) {
         cudaError_t e = set_feature_kernel_attrs(100 * 1024);
         if (e == cudaSuccess) e = set_gemm_kernel_attrs();
+        if (e == cudaSuccess) e = set_map_kernel_attrs();
         if (e != cudaSuccess) {
             cudaGetLastError();
             if (m->own_stream) cudaStreamDestroy(m->stream);
@@ -521,6 +587,7 @@ void disc_map_destroy(disc_map* m)
     if (!m) return;
     cudaSetDevice(m->cfg.device);
     cudaStreamSynchronize(m->stream);
+    for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     m->mem.free_all();
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -535,6 +602,7 @@ disc_status disc_integrate_frame(disc_map* m, const disc_frame* f, disc_frame_st
     FrameCounters c{};
     CK(cudaMemcpyAsync(&c, m->d_ctr + (m->cur ^ 1), sizeof(c), cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
+    collect_timing(m);
     if (stats) to_stats(c, stats);
     if (c.err == 0) m->next_id_upper = c.next_id;
     return (disc_status)c.err;
@@ -558,6 +626,7 @@ disc_status disc_integrate_frames(disc_map* m, const disc_frame* frames, int32_t
     std::vector<FrameCounters> c(std::max(enq, 1));
     if (enq > 0) CK(cudaMemcpyAsync(c.data(), m->d_hist, sizeof(FrameCounters) * enq, cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
+    collect_timing(m);
     int done = 0;
     disc_status fs = DISC_OK;
     for (int i = 0; i < enq; i++) {
@@ -850,6 +919,41 @@ uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz)
 }
 
 int64_t disc_map_device_bytes(disc_map* m) { return m ? m->mem.bytes : 0; }
+
+int64_t disc_map_kernel_launches(disc_map* m) { return m ? m->launches : 0; }
+
+disc_status disc_map_set_phase_timing(disc_map* m, int32_t enable)
+{
+    if (!m) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    CK(cudaStreamSynchronize(m->stream));
+    collect_timing(m);
+    m->timing = enable != 0;
+    for (int i = 0; i < PH_COUNT; i++) {
+        m->phase_ms[i] = 0.0;
+        m->phase_launches[i] = 0;
+        m->phase_calls[i] = 0;
+    }
+    return DISC_OK;
+}
+
+disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int64_t* calls, int32_t n)
+{
+    if (!m || n < 0) return DISC_ERR_INVALID_ARG;
+    for (int i = 0; i < n && i < PH_COUNT; i++) {
+        if (ms) ms[i] = m->phase_ms[i];
+        if (launches) launches[i] = m->phase_launches[i];
+        if (calls) calls[i] = m->phase_calls[i];
+    }
+    return DISC_OK;
+}
+
+const char* disc_phase_name(int32_t i)
+{
+    static const char* names[PH_COUNT] = {"frame_begin", "token_stats", "coverage", "weights", "pool_exact",
+                                          "pool_gemm", "backproject", "entries", "associate", "insert"};
+    return (i >= 0 && i < PH_COUNT) ? names[i] : "";
+}
 
 disc_status disc_map_get_config(disc_map* m, disc_map_config* out)
 {

@@ -236,8 +236,8 @@ __global__ void k_pool_exact(FrameParams fp, Scratch sc)
     sc.Ecan[(size_t)m * fp.D + d] = __double2float_rn(unfix(acc, S_EMB));
 }
 
-// ---- host launchers -------------------------------------------------------------
-void launch_features(const FrameParams& fp, const Scratch& sc, cudaStream_t st, int cov_smem_limit)
+// ---- host launchers (each returns the number of kernels it enqueued) ----------
+int launch_token_stats(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
 {
     const dim3 b256(256);
     dim3 gcol((fp.D + 255) / 256, (fp.P + 63) / 64);
@@ -247,20 +247,37 @@ void launch_features(const FrameParams& fp, const Scratch& sc, cudaStream_t st, 
     if (fp.token_bf16) k_tok_rows<__nv_bfloat16><<<(fp.P + 7) / 8, b256, 0, st>>>(fp, sc);
     else k_tok_rows<float><<<(fp.P + 7) / 8, b256, 0, st>>>(fp, sc);
     k_tok_finish<<<(fp.P + 255) / 256, b256, 0, st>>>(fp, sc);
-    if (fp.M > 0) {
-        size_t hsm = sizeof(int32_t) * (size_t)fp.M * fp.Pw;
-        if ((int)hsm <= cov_smem_limit) {
-            k_coverage<<<fp.Ph, b256, hsm, st>>>(fp, sc);
-        } else {
-            cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)fp.M * fp.P, st);
-            k_coverage_global<<<608, b256, 0, st>>>(fp, sc);
-        }
-        k_weights<<<fp.M, b256, 0, st>>>(fp, sc);
-        dim3 gp(fp.M, (fp.D + 255) / 256);
-        size_t psm = sizeof(float) * (size_t)fp.P;
-        if (fp.token_bf16) k_pool_exact<__nv_bfloat16><<<gp, b256, psm, st>>>(fp, sc);
-        else k_pool_exact<float><<<gp, b256, psm, st>>>(fp, sc);
+    return 4;
+}
+
+int launch_coverage(const FrameParams& fp, const Scratch& sc, cudaStream_t st, int cov_smem_limit)
+{
+    if (fp.M <= 0) return 0;
+    size_t hsm = sizeof(int32_t) * (size_t)fp.M * fp.Pw;
+    if ((int)hsm <= cov_smem_limit) {
+        k_coverage<<<fp.Ph, 256, hsm, st>>>(fp, sc);
+    } else {
+        cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)fp.M * fp.P, st);
+        k_coverage_global<<<608, 256, 0, st>>>(fp, sc);
     }
+    return 1;
+}
+
+int launch_weights(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+{
+    if (fp.M <= 0) return 0;
+    k_weights<<<fp.M, 256, 0, st>>>(fp, sc);
+    return 1;
+}
+
+int launch_pool_exact(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+{
+    if (fp.M <= 0) return 0;
+    dim3 gp(fp.M, (fp.D + 255) / 256);
+    size_t psm = sizeof(float) * (size_t)fp.P;
+    if (fp.token_bf16) k_pool_exact<__nv_bfloat16><<<gp, 256, psm, st>>>(fp, sc);
+    else k_pool_exact<float><<<gp, 256, psm, st>>>(fp, sc);
+    return 1;
 }
 
 cudaError_t set_feature_kernel_attrs(int max_dyn_smem)

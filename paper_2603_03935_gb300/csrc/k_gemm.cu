@@ -261,14 +261,15 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(FrameParams fp, Scratch sc
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-void launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+int launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
 {
-    if (fp.M <= 0) return;
+    if (fp.M <= 0) return 0;
     const int NT = fp.Npad;
     const size_t smem = gemm_smem_bytes(NT);
     dim3 g((fp.D + GEMM_MT - 1) / GEMM_MT);
     if (fp.token_bf16) k_pool_gemm<__nv_bfloat16><<<g, 128, smem, st>>>(fp, sc, NT);
     else k_pool_gemm<float><<<g, 128, smem, st>>>(fp, sc, NT);
+    return 1;
 }
 
 cudaError_t set_gemm_kernel_attrs()

@@ -286,8 +286,8 @@ __global__ void k_entries(FrameParams fp, Scratch sc, VoxelTable vt, Instances i
 
 // ---- association, union, new ids, merging and fusion (one block) ---------------
 constexpr int ASSOC_THREADS = 1024;
-constexpr int PAIR_CAP = 4096;   // distinct (segment, instance) overlaps per frame
-constexpr int COMP_CAP = 1024;   // distinct active instances whose component changes
+constexpr int PAIR_CAP = 8192;   // distinct (segment, instance) overlaps per frame
+constexpr size_t ASSOC_SMEM = (size_t)PAIR_CAP * 16;  // roots, uf, best_src, best_q
 
 struct AssocParams {
     float eta;      // relative error bound of the tensor-core pooled embedding
@@ -313,8 +313,11 @@ __device__ int uf_find(int* uf, int x)
 __global__ void __launch_bounds__(ASSOC_THREADS, 1)
 k_associate(FrameParams fp, Scratch sc, Instances inst, int* next_id, AssocParams ap)
 {
-    __shared__ unsigned roots[PAIR_CAP];   // sorted distinct roots (active set)
-    __shared__ int uf[PAIR_CAP];
+    extern __shared__ __align__(16) unsigned char assoc_smem[];
+    unsigned* roots = (unsigned*)assoc_smem;            // sorted distinct roots (active set)
+    int* uf = (int*)(roots + PAIR_CAP);                  // union-find over local indices
+    int* best_src = uf + PAIR_CAP;                       // fusion winner per component
+    float* best_q = (float*)(best_src + PAIR_CAP);
     __shared__ int first[MAX_MASKS];
     __shared__ int s_nroots, s_nedge, s_live, s_border, s_merges, s_new;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = ASSOC_THREADS / 32;
@@ -367,12 +370,6 @@ k_associate(FrameParams fp, Scratch sc, Instances inst, int* next_id, AssocParam
     }
     __syncthreads();
     const int nroots = s_nroots;
-    if (nroots > COMP_CAP) {
-        // more active instances than this block tracks: refuse the frame
-        // before anything in the map changes
-        if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
-        return;
-    }
     for (int i = tid; i < nroots; i += ASSOC_THREADS) uf[i] = i;
     // (3) edges: overlap gate (exact) and cosine gate (fast score, exact re-score
     //     inside the error band), one warp per overlap pair
@@ -382,7 +379,9 @@ k_associate(FrameParams fp, Scratch sc, Instances inst, int* next_id, AssocParam
         const int m = (int)(okey >> 32) - 1;
         const int k = (int)(okey & 0xffffffffu);
         const long long ov = sc.ocnt[slot];
-        if (ov * (long long)fp.ov_den < (long long)fp.ov_num * sc.nvox[m]) continue;
+        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
+        const long long denom = min((long long)sc.nvox[m], inst.count[k]);
+        if (ov * (long long)fp.ov_den < (long long)fp.ov_num * denom) continue;
         const float* a = sc.Efast + (size_t)m * D;
         const float* b = inst.E + (size_t)k * D;
         float dt = 0.0f, na = 0.0f, nb = 0.0f;
@@ -469,8 +468,6 @@ k_associate(FrameParams fp, Scratch sc, Instances inst, int* next_id, AssocParam
     // (6) fusion per component: candidates in the order (members by ascending
     //     id, then segments by ascending mask); the first strictly larger Q wins
     //     (Sec. III-C).  best_src >= 0: an instance id; < 0: segment -(m+1).
-    __shared__ int best_src[COMP_CAP];
-    __shared__ float best_q[COMP_CAP];
     // compress every chain to its root (concurrent writes only store roots)
     for (int x = tid; x < nroots; x += ASSOC_THREADS) uf[x] = uf_find(uf, x);
     __syncthreads();
@@ -684,33 +681,50 @@ __global__ void k_load_voxels(const unsigned long long* keys, const int* labels,
     }
 }
 
-// ---- host launchers ------------------------------------------------------------------
-void launch_frame_begin(const Scratch& sc, FrameCounters* prev, const int* next_id, int D, int sticky,
-                        cudaStream_t st)
+// ---- host launchers (each returns the number of kernels it enqueued) ---------------
+int launch_frame_begin(const Scratch& sc, FrameCounters* prev, const int* next_id, int D, int sticky,
+                       cudaStream_t st)
 {
     k_frame_begin<<<304, 256, 0, st>>>(sc, prev, next_id, D, MAX_MASKS, sticky);
+    return 1;
 }
 
-void launch_geometry(const FrameParams& fp, const Scratch& sc, const VoxelTable& vt, const Instances& inst,
-                     cudaStream_t st)
+int launch_backproject(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
 {
-    if (fp.M <= 0) return;
+    if (fp.M <= 0) return 0;
     dim3 b(32, 8), g((fp.W + 31) / 32, (fp.H + 7) / 8);
     k_backproject<<<g, b, 0, st>>>(fp, sc);
+    return 1;
+}
+
+int launch_entries(const FrameParams& fp, const Scratch& sc, const VoxelTable& vt, const Instances& inst,
+                   cudaStream_t st)
+{
+    if (fp.M <= 0) return 0;
     k_entries<<<152 * 4, 256, 0, st>>>(fp, sc, vt, inst);
+    return 1;
 }
 
-void launch_associate(const FrameParams& fp, const Scratch& sc, const Instances& inst, int* next_id,
-                      float eta, float dot_err, cudaStream_t st)
+int launch_associate(const FrameParams& fp, const Scratch& sc, const Instances& inst, int* next_id,
+                     float eta, float dot_err, cudaStream_t st)
 {
-    if (fp.M <= 0) return;
+    if (fp.M <= 0) return 0;
     AssocParams ap{eta, dot_err};
-    k_associate<<<1, ASSOC_THREADS, 0, st>>>(fp, sc, inst, next_id, ap);
+    k_associate<<<1, ASSOC_THREADS, ASSOC_SMEM, st>>>(fp, sc, inst, next_id, ap);
+    return 1;
 }
 
-void launch_insert(const Scratch& sc, const VoxelTable& vt, const Instances& inst, cudaStream_t st)
+int launch_insert(const FrameParams& fp, const Scratch& sc, const VoxelTable& vt, const Instances& inst,
+                  cudaStream_t st)
 {
+    if (fp.M <= 0) return 0;
     k_insert<<<152 * 2, 256, 0, st>>>(sc, vt, inst);
+    return 1;
+}
+
+cudaError_t set_map_kernel_attrs()
+{
+    return cudaFuncSetAttribute(k_associate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ASSOC_SMEM);
 }
 
 void launch_rehash(const VoxelTable& from, const VoxelTable& to, int* err, cudaStream_t st)

@@ -77,6 +77,27 @@ def test_room_scale_frames_parity(torch_dev):
     run_parity(torch_dev, sc, [0, 1, 2, 3, 250, 251], voxel_capacity=1 << 22, instance_capacity=1024)
 
 
+def test_room_trajectory_batched_parity(torch_dev):
+    # the launch configuration the benchmark times: 32 consecutive full-size
+    # frames per disc_integrate_frames call, device-resident inputs
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.room_scene(num_frames=2000)
+    fr = sc.render(range(64))
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 24, instance_capacity=1 << 16)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    for lo in (0, 32):
+        frames = [_dframe(torch, dev, fr, i) for i in range(lo, lo + 32)]
+        stats, done, rc = gmap.integrate_frames(frames)
+        assert rc == 0 and done == 32
+        for j, st in enumerate(stats):
+            o = omap.integrate(*oracle.frame_args(fr, lo + j), report=True)
+            for gk, ok in common.COUNT_FIELDS:
+                assert st[gk] == o[ok], f"frame {lo + j} {gk}: {st[gk]} vs {o[ok]}"
+    common.compare_maps(gmap, omap, ctx="room batched")
+
+
 def test_ragged_token_grid_and_odd_frame(torch_dev):
     # P = 7 x 5 = 35 (ragged last GEMM chunk), D = 200 (ragged last tile),
     # 50 x 37 pixels (patch bands of uneven height)

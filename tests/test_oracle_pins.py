@@ -373,6 +373,22 @@ def test_overlap_gate_is_an_exact_rational_test():
         assert r["new_voxels"] == 80
 
 
+def test_overlap_is_normalised_by_the_smaller_set():
+    # a 2 x 5 fragment lies entirely inside a new 10 x 10 segment: 10 shared
+    # voxels are 1/10 of the segment but all of the fragment -> merged
+    H, W, s, z0 = 10, 10, 0.05, 1.013
+    fx = z0 / s
+    depth = np.full((H, W), z0, np.float32)
+    F = np.ones((4, 8), np.float32)
+    frag = np.zeros((H, W), np.uint16)
+    frag[:5, :2] = 1
+    m = oracle.OracleMap(**oracle.default_config(8, 2, 2, s))
+    m.integrate(depth, frag, F, np.eye(4), (fx, fx, W // 2, H // 2), 1)
+    r = m.integrate(depth, np.ones((H, W), np.uint16), F, np.eye(4), (fx, fx, W // 2, H // 2), 1)
+    assert r["rep"][0] == 0 and r["new_instances"] == 0 and r["new_voxels"] == 90
+    assert m.instances()["count"][0] == 100
+
+
 def test_transitive_merge_keeps_the_smallest_id():
     # frame 1: the wall split into two disjoint masks -> instances 0 and 1;
     # frame 2: one mask covering both -> merged into 0 (Sec. III-B refinement)
