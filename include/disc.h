@@ -168,6 +168,28 @@ disc_status disc_map_export_instances(disc_map* map, int32_t* parent, int64_t* c
 disc_status disc_map_save(disc_map* map, const char* path);
 disc_status disc_map_load(const char* path, const disc_map_config* cfg_override, disc_map** out_map);
 
+/* Token statistics without device allocation.  The paper has no counterpart
+ * of this entry point: it serves callers that cannot call cudaMalloc (code
+ * whose device memory footprint must stay fixed after start-up, or hosts that
+ * hand the library only buffers they registered themselves).  It computes the
+ * same distinctiveness D_p (Eq. 1) and token/global-embedding cosine as one
+ * frame of disc_integrate_frame, bit for bit, for one token grid:
+ *   tokens       [P][D] device memory, disc_token_dtype;
+ *   global_embed [D] device memory or NULL (then the mean token);
+ *   Dp, cosg     [P] device memory, written;
+ *   cuda_stream  cudaStream_t of the current device (NULL = default stream).
+ * Limits: P <= 16384, D <= 4096; larger sizes return DISC_ERR_INVALID_ARG.
+ * Its working set (~450 KB) is a file-scope __device__ array that every GPU
+ * loading the library holds until the process exits; every call on a GPU
+ * shares it, so calls whose GPU work overlaps race.  The first call on each
+ * device looks up that array's device address (the current device must be
+ * the one the stream and pointers belong to); make that first call before any
+ * stream capture.  Returns after the results are complete; DISC_ERR_RANGE for
+ * a non-finite token or |token| > 1024. */
+disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
+                                    const float* global_embed, float eps, float* Dp, float* cosg,
+                                    void* cuda_stream);
+
 /* Voxel key packing: three signed 18-bit voxel coordinates (x, y, z), each
  * biased by 2^17, in bits 36..53, 18..35 and 0..17. */
 uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz);

@@ -91,6 +91,8 @@ def lib():
         L.disc_map_phase_times.restype = ctypes.c_int
         L.disc_phase_name.argtypes = [c_i32]
         L.disc_phase_name.restype = ctypes.c_char_p
+        L.disc_token_stats_static.argtypes = [c_vp, c_i32, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp, c_vp]
+        L.disc_token_stats_static.restype = ctypes.c_int
         L.disc_map_device_bytes.argtypes = [c_vp]
         L.disc_map_device_bytes.restype = c_i64
         L.disc_map_destroy.argtypes = [c_vp]
@@ -169,6 +171,22 @@ def device_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None
     fr.global_embed = None if global_embed is None else global_embed.data_ptr()
     fr.inputs_on_device = 1
     return fr, (depth, labels, tokens, global_embed)
+
+
+def token_stats_static(tokens, global_embed=None, eps=1e-6, stream=None):
+    """Eq. 1 distinctiveness and cosine to the global embedding for one token
+    grid (torch CUDA tensor [P, D], fp32 or bf16) with no device allocation.
+    Returns (Dp, cosg) as new CUDA tensors allocated by the caller here."""
+    import torch
+    P, D = tokens.shape
+    Dp = torch.empty(P, dtype=torch.float32, device=tokens.device)
+    cosg = torch.empty(P, dtype=torch.float32, device=tokens.device)
+    s = torch.cuda.current_stream(tokens.device) if stream is None else stream
+    rc = lib().disc_token_stats_static(tokens.data_ptr(), 1 if tokens.dtype == torch.bfloat16 else 0, P, D,
+                                       None if global_embed is None else global_embed.data_ptr(), float(eps),
+                                       Dp.data_ptr(), cosg.data_ptr(), s.cuda_stream)
+    _check(rc, "disc_token_stats_static")
+    return Dp, cosg
 
 
 class DiscMap:
