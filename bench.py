@@ -116,26 +116,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(phase, st, H, W, P, D, M, Kpad):
-    """Bytes one launch of a phase must move for one frame.
-
-    backproject: depth (4 B) + labels (2 B) per pixel, plus for every unique
-    (segment, voxel) pair its 8 B key, 4 B pixel count and 3 x 8 B normal sums.
-    """
-    ne = st["unique_seg_voxels"]
-    if phase == "backproject":
-        return 6 * H * W + 36 * ne
-    if phase == "entries":
-        return ne * (8 + 4 + 24) + ne * 12 + st["new_voxels"] * 12 + st["overlap_pairs"] * 12
-    if phase == "token_stats":
-        return 4 * P * D
-    if phase == "pool_gemm":
-        return 4 * P * D + 4 * M * Kpad + 4 * M * D
-    if phase == "coverage":
-        return 2 * H * W + 4 * M * P
-    if phase == "insert":
-        return 24 * st["new_voxels"]
-    return 0
+def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
+    """Bytes one launch of a phase must move.  Batched phases
+    cover every frame of the batch in one launch; serial phases one frame
+    (the mean over the batch is returned for those).  sts: per-frame stats."""
+    batched = {
+        "backproject": lambda s, M: 6 * H * W + 36 * s["unique_seg_voxels"],
+        "entries": lambda s, M: 52 * s["unique_seg_voxels"],
+        "token_stats": lambda s, M: 4 * P * D,
+        "pool_gemm": lambda s, M: 4 * P * D + 4 * M * Kpad + 4 * M * D,
+        "pool_exact": lambda s, M: 4 * P * D + 4 * M * D,
+        "coverage": lambda s, M: 2 * H * W + 4 * M * P,
+        "weights": lambda s, M: 8 * M * P,
+    }
+    serial = {
+        "overlap": lambda s, M: 16 * s["unique_seg_voxels"] + 12 * s["new_voxels"],
+        "score": lambda s, M: 8 * D * s["overlap_pairs"],
+        "apply": lambda s, M: 24 * s["new_voxels"] + 8 * D * (s["new_instances"] + s["merges"]),
+    }
+    if phase in batched:
+        return float(sum(batched[phase](s_, M) for s_, M in zip(sts, Ms)))
+    if phase in serial:
+        return float(np.mean([serial[phase](s_, M) for s_, M in zip(sts, Ms)]))
+    return 0.0
 
 
 def run_reference(args, rank):
@@ -324,17 +327,18 @@ def main():
 
     # dominant single-kernel phase and its roofline
     peak, peak_kind = peaks()
-    per_frame = {k: v["ms"] / max(v["calls"], 1) for k, v in phases.items()}
-    single = ("backproject", "entries", "pool_gemm", "coverage", "insert", "associate", "pool_exact", "weights")
+    per_frame = {k: v["ms"] / B for k, v in phases.items()}
+    single = ("backproject", "coverage", "pool_gemm", "pool_exact", "weights", "overlap", "score", "union")
     dom = max(single, key=lambda k: phases[k]["ms"])
     st_list = [{k: getattr(ph_stats[j], k) for k, _ in binding.Stats._fields_} for j in range(B)]
-    alg = np.mean([algorithmic_bytes(dom, s_, H, W_, P, D, int(fr.num_masks[lo - B + j]), Kpad)
-                   for j, s_ in enumerate(st_list)])
-    dur_s = per_frame[dom] / 1e3
-    achieved = alg / dur_s / 1e9 if dur_s > 0 and alg > 0 else 0.0
+    Ms = [int(fr.num_masks[lo - B + j]) for j in range(B)]
+    alg = algorithmic_bytes(dom, st_list, H, W_, P, D, Ms, Kpad)
+    launch_ms = phases[dom]["ms"] / max(phases[dom]["calls"], 1)
+    achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 and alg > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "alg_bytes_per_launch": float(alg), "launch_us": per_frame[dom] * 1e3}
+                "alg_bytes_per_launch": float(alg), "launch_us": launch_ms * 1e3,
+                "launches_per_frame": phases[dom]["calls"] / B}
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None

@@ -74,6 +74,7 @@ typedef struct {
     int32_t precision;       /* disc_precision of the fast pooling/scoring path */
     void* cuda_stream;       /* cudaStream_t, or NULL: the map creates one */
     int32_t device;          /* CUDA device ordinal */
+    int32_t batch_frames;    /* frames whose stateless phases share one launch (1..256) */
 } disc_map_config;
 
 typedef struct {
@@ -136,9 +137,15 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
 /* Integrates one frame (all steps above).  stats may be NULL. */
 disc_status disc_integrate_frame(disc_map* map, const disc_frame* frame, disc_frame_stats* stats);
 
-/* Integrates n frames in order with one host synchronisation at the end.
- * stats (nullable) receives one entry per frame.  On an error the frames
- * before the failing one stay integrated; *n_done (nullable) says how many. */
+/* Integrates n frames in order.  Frames are processed in batches of
+ * config.batch_frames: the steps that do not touch the map (Eq. 1, coverage,
+ * pooling, back-projection, S_angle, Q, the lookup of every voxel in the map
+ * as it stood when the batch started) run for the whole batch in one launch
+ * each; overlap, association, merging, fusion and insertion then run frame
+ * after frame on the device with no host round trip.  The result is the same
+ * as n calls of disc_integrate_frame.  stats (nullable) receives one entry per
+ * frame.  On an error the frames before the failing one stay integrated;
+ * *n_done (nullable) says how many. */
 disc_status disc_integrate_frames(disc_map* map, const disc_frame* frames, int32_t n,
                                   disc_frame_stats* stats, int32_t* n_done);
 
@@ -202,10 +209,11 @@ int64_t disc_map_kernel_launches(disc_map* map);
 
 /* Per-phase timing with CUDA events recorded on the map's stream around each
  * phase of every frame (off by default; enabling resets the totals).  Phases:
- * 0 frame_begin, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
- * 5 pool_gemm, 6 backproject, 7 entries (S_angle terms, map lookup), 8
- * associate, 9 insert.  ms/launches/calls: [n] accumulated device time,
- * kernels launched and timed intervals per phase (any may be NULL). */
+ * 0 clear, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
+ * 5 pool_gemm, 6 backproject, 7 entries (S_angle, |V_m|, lookup, Q) -- one
+ * interval per batch each -- and 8 overlap, 9 score, 10 union, 11 apply --
+ * one interval per frame each.  ms/launches/calls: [n] accumulated device
+ * time, kernels launched and timed intervals per phase (any may be NULL). */
 disc_status disc_map_set_phase_timing(disc_map* map, int32_t enable);
 disc_status disc_map_phase_times(disc_map* map, double* ms, int64_t* launches, int64_t* calls, int32_t n);
 const char* disc_phase_name(int32_t phase);

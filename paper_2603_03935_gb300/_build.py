@@ -10,7 +10,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdisc.so")
-SOURCES = ["k_features.cu", "k_gemm.cu", "k_map.cu", "disc_api.cu", "disc_static.cu"]
+SOURCES = ["k_features.cu", "k_gemm.cu", "k_geometry.cu", "k_serial.cu", "k_maint.cu", "disc_api.cu",
+           "disc_static.cu"]
 HEADERS = ["disc_common.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no fused multiply-add anywhere, so every fp32 expression is

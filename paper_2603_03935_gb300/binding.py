@@ -29,7 +29,7 @@ class Config(ctypes.Structure):
                 ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
                 ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
                 ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
-                ("device", c_i32)]
+                ("device", c_i32), ("batch_frames", c_i32)]
 
 
 class Frame(ctypes.Structure):
@@ -319,7 +319,7 @@ class DiscMap:
         _check(lib().disc_map_set_phase_timing(self._h, 1 if enable else 0), "disc_map_set_phase_timing")
 
     def phase_times(self) -> dict:
-        n = 10
+        n = 12
         ms = np.zeros(n, np.float64)
         la = np.zeros(n, np.int64)
         ca = np.zeros(n, np.int64)

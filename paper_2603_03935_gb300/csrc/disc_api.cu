@@ -1,7 +1,7 @@
 // C ABI of libdisc (declared in include/disc.h): map lifetime, frame
 // integration, queries, export and checkpoints.  Host code only orchestrates:
-// every step of a frame runs in the kernels of k_features.cu, k_gemm.cu and
-// k_map.cu, enqueued on the map's stream.
+// every step of a frame runs in the kernels of k_features.cu, k_gemm.cu,
+// k_geometry.cu and k_serial.cu, enqueued on the map's stream.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -16,7 +16,8 @@ using namespace disc;
 
 namespace {
 
-constexpr int SLOT_FACTOR = 2;  // per-frame hashes: slots >= 2 x pixels
+constexpr int SLOT_FACTOR = 2;   // per-frame hashes: slots >= 2 x pixels
+constexpr int PAIR_CAP = 8192;   // distinct (segment, instance) overlaps per frame (k_serial.cu)
 
 struct DevAlloc {
     std::vector<void*> ptrs;
@@ -71,23 +72,25 @@ struct disc_map {
     Instances inst{};
     int* d_next_id = nullptr;
     int* d_flag = nullptr;
-    Scratch sc{};
-    FrameCounters* d_ctr = nullptr;       // [2], alternating per frame
-    FrameCounters* d_hist = nullptr;      // [hist_cap] per-frame counters of a batch
+    BatchScratch bs{};
+    SerialScratch ss{};
+    FrameParams* d_fps = nullptr;         // [Bmax] parameters of the batch's frames
+    FrameCounters* d_hist = nullptr;      // [hist_cap] per-frame counters of one call
     int hist_cap = 0;
-    int cur = 0;                          // counter block of the next frame
-    int P = 0, Kpad = 0, D = 0;
+    int Bmax = 1;
+    int MM = 1;                           // mask rows per frame slot
+    int P = 0, Kpad = 0, D = 0, Npad_max = 16;
     // host-side bounds that avoid a synchronisation per frame
     uint64_t used_upper = 0;
     int64_t next_id_upper = 0;
-    int last_M = 0;
+    int last_slot = 0, last_M = 0;
     bool have_frame = false;
-    // staging for host inputs
+    // staging of host inputs, one slot per frame of a batch
     float* d_depth = nullptr;
     uint16_t* d_labels = nullptr;
-    void* d_tokens = nullptr;
+    unsigned char* d_tokens = nullptr;
     float* d_gembed = nullptr;
-    int cov_smem_limit = 96 * 1024;
+    size_t px_cap = 0;
     // kernel accounting and optional per-phase CUDA-event timing
     int64_t launches = 0;
     bool timing = false;
@@ -126,8 +129,10 @@ bool config_ok(const disc_map_config& c)
     if (c.patch_h <= 0 || c.patch_w <= 0 || (int64_t)c.patch_h * c.patch_w > 16384) return false;
     if (c.max_width <= 0 || c.max_height <= 0 || (int64_t)c.max_width * c.max_height > (1 << 24)) return false;
     if (c.max_masks < 0 || c.max_masks > MAX_MASKS) return false;
+    if (coverage_smem_bytes(c.max_masks, c.patch_w) > 200 * 1024) return false;
     if (c.voxel_capacity <= 0 || !(c.max_load > 0.0f && c.max_load < 1.0f)) return false;
     if (c.instance_capacity <= 0) return false;
+    if (c.batch_frames < 0 || c.batch_frames > 256) return false;
     if (c.precision != DISC_FP32) return false;  // only the fp32 fast path is built
     return true;
 }
@@ -219,7 +224,7 @@ disc_status ensure_voxel_room(disc_map* m, uint64_t incoming)
     return DISC_OK;
 }
 
-disc_status ensure_instance_room(disc_map* m, int incoming)
+disc_status ensure_instance_room(disc_map* m, int64_t incoming)
 {
     if (m->next_id_upper + incoming <= m->inst.cap) return DISC_OK;
     CK(cudaStreamSynchronize(m->stream));
@@ -305,91 +310,125 @@ disc_status check_frame(const disc_map* m, const disc_frame* f)
     return DISC_OK;
 }
 
-// Enqueue one frame.  `sticky`: an error of the previous frame of the same
-// batch skips this one.  `hist` (nullable): device slot for its counters.
-disc_status enqueue_frame(disc_map* m, const disc_frame* f, int sticky, FrameCounters* hist)
+// Enqueue frames[0..B) (B <= Bmax, all valid) as one batch; counters of frame
+// j are copied to hist[j].  prev: counters of the frame before this batch in
+// the same call (an error there stops this batch), or NULL.
+disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCounters* hist,
+                          const FrameCounters* prev)
 {
-    disc_status s = check_frame(m, f);
+    const int D = m->D, P = m->P;
+    uint64_t px = 0;
+    int64_t masks = 0;
+    int Hmax = 0, Wmax = 0, Mmax = 0;
+    bool any_bf16 = false, any_f32 = false;
+    for (int j = 0; j < B; j++) {
+        px += (uint64_t)frames[j].width * frames[j].height;
+        masks += frames[j].num_masks;
+        Hmax = std::max(Hmax, frames[j].height);
+        Wmax = std::max(Wmax, frames[j].width);
+        Mmax = std::max(Mmax, frames[j].num_masks);
+        any_bf16 |= frames[j].token_dtype == DISC_TOKENS_BF16;
+        any_f32 |= frames[j].token_dtype == DISC_TOKENS_F32;
+    }
+    disc_status s = ensure_voxel_room(m, px);
     if (s != DISC_OK) return s;
-    const int H = f->height, W = f->width, M = f->num_masks, D = m->D, P = m->P;
-    s = ensure_voxel_room(m, (uint64_t)H * W);
-    if (s != DISC_OK) return s;
-    s = ensure_instance_room(m, M);
+    s = ensure_instance_room(m, masks);
     if (s != DISC_OK) return s;
 
-    FrameParams fp{};
-    fp.H = H;
-    fp.W = W;
-    fp.M = M;
-    fp.P = P;
-    fp.D = D;
-    fp.Ph = m->cfg.patch_h;
-    fp.Pw = m->cfg.patch_w;
-    fp.Kpad = m->Kpad;
-    fp.Npad = std::max(16, (M + 15) / 16 * 16);
-    fp.fx = f->fx;
-    fp.fy = f->fy;
-    fp.cx = f->cx;
-    fp.cy = f->cy;
-    for (int r = 0; r < 3; r++) {
-        for (int c = 0; c < 3; c++) fp.R[3 * r + c] = (float)f->T_world_cam[4 * r + c];
-        fp.t[r] = (float)f->T_world_cam[4 * r + 3];
-    }
-    fp.voxel = m->cfg.voxel_size;
-    fp.z_min = m->cfg.z_min;
-    fp.z_max = m->cfg.z_max;
-    fp.eps = m->cfg.eps;
-    fp.tau = m->cfg.tau_cos;
-    fp.lambda_size = m->cfg.lambda_size;
-    fp.ov_num = m->cfg.ov_num;
-    fp.ov_den = m->cfg.ov_den;
-    fp.min_px = std::max(1, m->cfg.min_mask_pixels);
-    fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
-    const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
-    if (f->inputs_on_device) {
-        fp.depth = f->depth;
-        fp.labels = f->labels;
-        fp.tokens = f->tokens;
-        fp.gembed = f->global_embed;
-    } else {
-        CK(cudaMemcpyAsync(m->d_depth, f->depth, sizeof(float) * H * W, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->d_labels, f->labels, sizeof(uint16_t) * H * W, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->d_tokens, f->tokens, tok_bytes, cudaMemcpyHostToDevice, m->stream));
-        fp.depth = m->d_depth;
-        fp.labels = m->d_labels;
-        fp.tokens = m->d_tokens;
-        fp.gembed = nullptr;
-        if (f->global_embed) {
-            CK(cudaMemcpyAsync(m->d_gembed, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, m->stream));
-            fp.gembed = m->d_gembed;
+    std::vector<FrameParams> fps(B);
+    for (int j = 0; j < B; j++) {
+        const disc_frame* f = frames + j;
+        FrameParams& fp = fps[j];
+        fp.H = f->height;
+        fp.W = f->width;
+        fp.M = f->num_masks;
+        fp.P = P;
+        fp.D = D;
+        fp.Ph = m->cfg.patch_h;
+        fp.Pw = m->cfg.patch_w;
+        fp.Kpad = m->Kpad;
+        fp.Npad = std::max(16, (fp.M + 15) / 16 * 16);
+        fp.fx = f->fx;
+        fp.fy = f->fy;
+        fp.cx = f->cx;
+        fp.cy = f->cy;
+        for (int r = 0; r < 3; r++) {
+            for (int c = 0; c < 3; c++) fp.R[3 * r + c] = (float)f->T_world_cam[4 * r + c];
+            fp.t[r] = (float)f->T_world_cam[4 * r + 3];
+        }
+        fp.voxel = m->cfg.voxel_size;
+        fp.z_min = m->cfg.z_min;
+        fp.z_max = m->cfg.z_max;
+        fp.eps = m->cfg.eps;
+        fp.tau = m->cfg.tau_cos;
+        fp.lambda_size = m->cfg.lambda_size;
+        fp.ov_num = m->cfg.ov_num;
+        fp.ov_den = m->cfg.ov_den;
+        fp.min_px = std::max(1, m->cfg.min_mask_pixels);
+        fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
+        const size_t npx = (size_t)fp.H * fp.W;
+        const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
+        if (f->inputs_on_device) {
+            fp.depth = f->depth;
+            fp.labels = f->labels;
+            fp.tokens = f->tokens;
+            fp.gembed = f->global_embed;
+        } else {
+            float* dd = m->d_depth + (size_t)j * m->px_cap;
+            uint16_t* dl = m->d_labels + (size_t)j * m->px_cap;
+            unsigned char* dt = m->d_tokens + (size_t)j * P * D * 4;
+            CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, m->stream));
+            CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, m->stream));
+            CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, m->stream));
+            fp.depth = dd;
+            fp.labels = dl;
+            fp.tokens = dt;
+            fp.gembed = nullptr;
+            if (f->global_embed) {
+                float* dg = m->d_gembed + (size_t)j * D;
+                CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, m->stream));
+                fp.gembed = dg;
+            }
         }
     }
+    // pageable source: the call returns once the parameters are staged
+    CK(cudaMemcpyAsync(m->d_fps, fps.data(), sizeof(FrameParams) * B, cudaMemcpyHostToDevice, m->stream));
 
-    Scratch sc = m->sc;
-    sc.ctr = m->d_ctr + m->cur;
-    FrameCounters* prev = m->d_ctr + (m->cur ^ 1);
     cudaStream_t st = m->stream;
+    const BatchScratch& bs = m->bs;
+    const FrameParams* dfp = m->d_fps;
+    run_phase(m, PH_CLEAR, [&] { return launch_slot_clear(bs, B, D, m->MM, st); });
+    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, B, P, D, any_bf16, any_f32, st); });
+    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, B, m->cfg.patch_h, m->cfg.patch_w, Mmax, st); });
+    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, B, Mmax, st); });
+    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, B, P, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, B, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(m, PH_BACKPROJECT, [&] { return Mmax > 0 ? launch_backproject(dfp, bs, B, Hmax, Wmax, st) : 0; });
+    run_phase(m, PH_ENTRIES, [&] { return launch_entries(dfp, bs, m->vt, B, Mmax, st); });
+
     // error bound of the tensor-core pooled embedding relative to
     // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
     // 3 K products; and of a warp-level fp32 cosine
     const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * m->Kpad * std::ldexp(1.0, -24));
     const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
-    run_phase(m, PH_BEGIN, [&] { return launch_frame_begin(sc, prev, m->d_next_id, D, sticky, st); });
-    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(fp, sc, st); });
-    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(fp, sc, st, m->cov_smem_limit); });
-    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(fp, sc, st); });
-    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(fp, sc, st); });
-    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(fp, sc, st); });
-    run_phase(m, PH_BACKPROJECT, [&] { return launch_backproject(fp, sc, st); });
-    run_phase(m, PH_ENTRIES, [&] { return launch_entries(fp, sc, m->vt, m->inst, st); });
-    run_phase(m, PH_ASSOCIATE, [&] { return launch_associate(fp, sc, m->inst, m->d_next_id, eta, dot_err, st); });
-    run_phase(m, PH_INSERT, [&] { return launch_insert(fp, sc, m->vt, m->inst, st); });
-    if (hist) CK(cudaMemcpyAsync(hist, sc.ctr, sizeof(FrameCounters), cudaMemcpyDeviceToDevice, m->stream));
+    SerialScratch ss = m->ss;
+    ss.prev = prev;
+    for (int j = 0; j < B; j++) {
+        if (fps[j].M > 0) {
+            run_phase(m, PH_OVERLAP, [&] { return launch_overlap(bs, j, ss, m->vt, m->inst, st); });
+            run_phase(m, PH_SCORE, [&] { return launch_score(fps[j], bs, j, ss, m->inst, eta, dot_err, st); });
+            run_phase(m, PH_UNION, [&] { return launch_union(fps[j], bs, j, ss, m->inst, m->d_next_id, st); });
+            run_phase(m, PH_APPLY,
+                      [&] { return launch_apply(fps[j], bs, j, ss, m->vt, m->inst, m->d_next_id, st); });
+        }
+        ss.prev = nullptr;
+        CK(cudaMemcpyAsync(hist + j, bs.frame(j).ctr, sizeof(FrameCounters), cudaMemcpyDeviceToDevice, st));
+    }
     CK(cudaGetLastError());
-    m->cur ^= 1;
-    m->used_upper += (uint64_t)H * W;
-    m->next_id_upper += M;
-    m->last_M = M;
+    m->used_upper += px;
+    m->next_id_upper += masks;
+    m->last_slot = B - 1;
+    m->last_M = frames[B - 1].num_masks;
     m->have_frame = true;
     return DISC_OK;
 }
@@ -425,6 +464,46 @@ disc_status ensure_hist(disc_map* m, int n)
     return DISC_OK;
 }
 
+// Integrate frames[0..n): batches of Bmax; stops at the first invalid frame
+// (host check) or the first frame that fails on the device.
+disc_status integrate(disc_map* m, const disc_frame* frames, int n, disc_frame_stats* stats, int* n_done)
+{
+    if (n_done) *n_done = 0;
+    disc_status s = ensure_hist(m, std::max(n, 1));
+    if (s != DISC_OK) return s;
+    int valid = 0;
+    while (valid < n && check_frame(m, frames + valid) == DISC_OK) valid++;
+    int enq = 0;
+    for (int lo = 0; lo < valid; lo += m->Bmax) {
+        const int B = std::min(m->Bmax, valid - lo);
+        s = enqueue_batch(m, frames + lo, B, m->d_hist + lo, lo > 0 ? m->d_hist + lo - 1 : nullptr);
+        if (s != DISC_OK) break;
+        enq += B;
+    }
+    std::vector<FrameCounters> c(std::max(enq, 1));
+    if (enq > 0) CK(cudaMemcpyAsync(c.data(), m->d_hist, sizeof(FrameCounters) * enq, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    collect_timing(m);
+    int done = 0;
+    disc_status fs = DISC_OK;
+    int exact_next_id = -1;  // frames without masks skip the kernel that records it
+    for (int i = 0; i < enq; i++) {
+        if (stats) to_stats(c[i], stats + i);
+        if (c[i].err != 0) {
+            fs = (disc_status)c[i].err;
+            break;
+        }
+        exact_next_id = std::max(exact_next_id, c[i].next_id);
+        done++;
+    }
+    if (exact_next_id > 0) m->next_id_upper = std::max<int64_t>(exact_next_id, 0);
+    if (n_done) *n_done = done;
+    if (fs != DISC_OK) return fs;
+    if (s != DISC_OK) return s;
+    if (valid < n) return DISC_ERR_INVALID_ARG;
+    return DISC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -454,6 +533,7 @@ void disc_config_default(disc_map_config* c)
     c->precision = DISC_FP32;
     c->cuda_stream = nullptr;
     c->device = 0;
+    c->batch_frames = 32;
 }
 
 disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolved, disc_map** out_map)
@@ -470,13 +550,18 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     disc_map* m = new disc_map();
     m->cfg = *cfg;
     m->cfg.voxel_capacity = (int64_t)next_pow2((uint64_t)cfg->voxel_capacity);
+    if (m->cfg.batch_frames == 0) m->cfg.batch_frames = 32;
+    m->Bmax = m->cfg.batch_frames;
     m->D = cfg->embed_dim;
     m->P = cfg->patch_h * cfg->patch_w;
     m->Kpad = (m->P + GEMM_KC - 1) / GEMM_KC * GEMM_KC;
+    m->MM = std::max(1, cfg->max_masks);
+    m->Npad_max = std::max(16, (m->MM + 15) / 16 * 16);
     if (cfg->cuda_stream) {
         m->stream = (cudaStream_t)cfg->cuda_stream;
     } else {
         if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
             delete m;
             return DISC_ERR_CUDA;
         }
@@ -484,9 +569,9 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     }
     static bool attrs_set = false;
     if (!attrs_set) {
-        cudaError_t e = set_feature_kernel_attrs(100 * 1024);
+        cudaError_t e = set_feature_kernel_attrs(200 * 1024);
         if (e == cudaSuccess) e = set_gemm_kernel_attrs();
-        if (e == cudaSuccess) e = set_map_kernel_attrs();
+        if (e == cudaSuccess) e = set_serial_kernel_attrs();
         if (e != cudaSuccess) {
             cudaGetLastError();
             if (m->own_stream) cudaStreamDestroy(m->stream);
@@ -495,56 +580,74 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
         }
         attrs_set = true;
     }
-    const int D = m->D, P = m->P, MM = MAX_MASKS;
+    const int D = m->D, P = m->P, MM = m->MM, B = m->Bmax;
     const uint64_t npx = (uint64_t)cfg->max_width * cfg->max_height;
     const uint64_t scap = next_pow2(SLOT_FACTOR * npx);
+    m->px_cap = npx;
     DevAlloc& a = m->mem;
     m->vt.used = a.get<unsigned long long>(1);
     m->d_next_id = a.get<int>(1);
     m->d_flag = a.get<int>(1);
-    m->d_ctr = a.get<FrameCounters>(2);
-    Scratch& sc = m->sc;
-    sc.sumF = a.get<long long>(D);
-    sc.fbar = a.get<float>(D);
-    sc.gvec = a.get<float>(D);
-    sc.gg = a.get<long long>(1);
-    sc.nsum = a.get<long long>(1);
-    sc.dotg = a.get<long long>(P);
-    sc.ffp = a.get<long long>(P);
-    sc.nrm = a.get<float>(P);
-    sc.Dp = a.get<float>(P);
-    sc.cosg = a.get<float>(P);
-    sc.fnorm = a.get<float>(P);
-    sc.cov = a.get<int32_t>((size_t)MM * P);
-    sc.npix = a.get<int32_t>(MM);
-    sc.W = a.get<float>((size_t)MM * m->Kpad);
-    sc.S = a.get<float>(5 * MM);
-    sc.Bm = a.get<float>(MM);
-    sc.Ecan = a.get<float>((size_t)MM * D);
-    sc.Efast = a.get<float>((size_t)MM * D);
-    sc.ang = a.get<long long>(MM);
-    sc.nvox = a.get<int32_t>(MM);
-    sc.segrep = a.get<int32_t>(MM);
-    sc.skeys = a.get<unsigned long long>(scap);
-    sc.snpx = a.get<int32_t>(scap);
-    sc.snrm = a.get<long long>(3 * scap);
-    sc.slist = a.get<int32_t>(scap);
+    m->d_fps = a.get<FrameParams>(B);
+    BatchScratch& bs = m->bs;
+    bs.sD = D;
+    bs.sP = P;
+    bs.sMM = MM;
+    bs.sMMP = (long long)MM * P;
+    bs.sW = (long long)m->Npad_max * m->Kpad;
+    bs.sMMD = (long long)MM * D;
+    bs.sS = 5LL * MM;
+    bs.scap = (long long)scap;
+    Scratch& sc = bs.base;
+    sc.sumF = a.get<long long>((size_t)B * D);
+    sc.fbar = a.get<float>((size_t)B * D);
+    sc.gvec = a.get<float>((size_t)B * D);
+    sc.gg = a.get<long long>(B);
+    sc.nsum = a.get<long long>(B);
+    sc.dotg = a.get<long long>((size_t)B * P);
+    sc.ffp = a.get<long long>((size_t)B * P);
+    sc.nrm = a.get<float>((size_t)B * P);
+    sc.Dp = a.get<float>((size_t)B * P);
+    sc.cosg = a.get<float>((size_t)B * P);
+    sc.fnorm = a.get<float>((size_t)B * P);
+    sc.cov = a.get<int32_t>((size_t)B * MM * P);
+    sc.npix = a.get<int32_t>((size_t)B * MM);
+    sc.W = a.get<float>((size_t)B * bs.sW);
+    sc.S = a.get<float>((size_t)B * 5 * MM);
+    sc.Bm = a.get<float>((size_t)B * MM);
+    sc.Ecan = a.get<float>((size_t)B * MM * D);
+    sc.Efast = a.get<float>((size_t)B * MM * D);
+    sc.ang = a.get<long long>((size_t)B * MM);
+    sc.nvox = a.get<int32_t>((size_t)B * MM);
+    sc.segrep = a.get<int32_t>((size_t)B * MM);
+    sc.sslot = a.get<SegSlot>((size_t)B * scap);
+    sc.sent = a.get<unsigned long long>((size_t)B * scap);
+    sc.slist = a.get<int32_t>((size_t)B * scap);
+    sc.elab = a.get<int32_t>((size_t)B * scap);
     sc.smask = scap - 1;
-    sc.okeys = a.get<unsigned long long>(scap);
-    sc.ocnt = a.get<int32_t>(scap);
-    sc.olist = a.get<int32_t>(scap);
-    sc.omask = scap - 1;
-    sc.nkeys = a.get<unsigned long long>(scap);
-    sc.nown = a.get<int32_t>(scap);
-    sc.nlist = a.get<int32_t>(scap);
-    sc.nmask = scap - 1;
-    sc.edge_cap = 4096;
-    sc.edge_m = a.get<int32_t>(sc.edge_cap);
-    sc.edge_k = a.get<int32_t>(sc.edge_cap);
-    m->d_depth = a.get<float>(npx);
-    m->d_labels = a.get<uint16_t>(npx);
-    m->d_tokens = a.get<float>((size_t)P * D);
-    m->d_gembed = a.get<float>(D);
+    sc.ctr = a.get<FrameCounters>(B);
+    SerialScratch& ss = m->ss;
+    ss.okeys = a.get<unsigned long long>(scap);
+    ss.ocnt = a.get<int32_t>(scap);
+    ss.olist = a.get<int32_t>(scap);
+    ss.omask = scap - 1;
+    ss.nkeys = a.get<unsigned long long>(scap);
+    ss.nown = a.get<int32_t>(scap);
+    ss.nlist = a.get<int32_t>(scap);
+    ss.nmask = scap - 1;
+    ss.edge_cap = PAIR_CAP;
+    ss.edge_m = a.get<int32_t>(PAIR_CAP);
+    ss.edge_k = a.get<int32_t>(PAIR_CAP);
+    ss.edge_n = a.get<int32_t>(1);
+    ss.copy_cap = PAIR_CAP + MAX_MASKS;
+    ss.copy_dst = a.get<int32_t>(ss.copy_cap);
+    ss.copy_src = a.get<int32_t>(ss.copy_cap);
+    ss.copy_n = a.get<int32_t>(1);
+    ss.prev = nullptr;
+    m->d_depth = a.get<float>((size_t)B * npx);
+    m->d_labels = a.get<uint16_t>((size_t)B * npx);
+    m->d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
+    m->d_gembed = a.get<float>((size_t)B * D);
     disc_status st = DISC_OK;
     if (a.failed) st = DISC_ERR_OOM;
     if (st == DISC_OK) {
@@ -557,18 +660,18 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
         cudaStream_t s = m->stream;
         cudaMemsetAsync(m->vt.used, 0, sizeof(unsigned long long), s);
         cudaMemsetAsync(m->d_next_id, 0, sizeof(int), s);
-        cudaMemsetAsync(m->d_ctr, 0, sizeof(FrameCounters) * 2, s);
-        cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)MM * m->Kpad, s);
-        cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)MM * P, s);
-        cudaMemsetAsync(sc.skeys, 0, sizeof(unsigned long long) * scap, s);
-        cudaMemsetAsync(sc.snpx, 0, sizeof(int32_t) * scap, s);
-        cudaMemsetAsync(sc.snrm, 0, sizeof(long long) * 3 * scap, s);
-        cudaMemsetAsync(sc.okeys, 0xFF, sizeof(unsigned long long) * scap, s);
-        cudaMemsetAsync(sc.ocnt, 0, sizeof(int32_t) * scap, s);
-        cudaMemsetAsync(sc.nkeys, 0xFF, sizeof(unsigned long long) * scap, s);
-        cudaMemsetAsync(sc.nown, 0x7F, sizeof(int32_t) * scap, s);  // large positive sentinel
-        cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)MM * D, s);
-        cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)MM * D, s);
+        cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s);
+        cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s);
+        cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s);
+        cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s);
+        cudaMemsetAsync(ss.okeys, 0xFF, sizeof(unsigned long long) * scap, s);
+        cudaMemsetAsync(ss.ocnt, 0, sizeof(int32_t) * scap, s);
+        cudaMemsetAsync(ss.nkeys, 0xFF, sizeof(unsigned long long) * scap, s);
+        cudaMemsetAsync(ss.nown, 0x7F, sizeof(int32_t) * scap, s);  // large positive sentinel
+        cudaMemsetAsync(ss.edge_n, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(ss.copy_n, 0, sizeof(int32_t), s);
+        cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s);
+        cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s);
         st = cuda_status(cudaStreamSynchronize(s));
     }
     if (st != DISC_OK) {
@@ -595,17 +698,11 @@ void disc_map_destroy(disc_map* m)
 
 disc_status disc_integrate_frame(disc_map* m, const disc_frame* f, disc_frame_stats* stats)
 {
-    if (!m) return DISC_ERR_INVALID_ARG;
+    if (!m || !f) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
-    disc_status s = enqueue_frame(m, f, 0, nullptr);
+    disc_status s = check_frame(m, f);
     if (s != DISC_OK) return s;
-    FrameCounters c{};
-    CK(cudaMemcpyAsync(&c, m->d_ctr + (m->cur ^ 1), sizeof(c), cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    collect_timing(m);
-    if (stats) to_stats(c, stats);
-    if (c.err == 0) m->next_id_upper = c.next_id;
-    return (disc_status)c.err;
+    return integrate(m, f, 1, stats, nullptr);
 }
 
 disc_status disc_integrate_frames(disc_map* m, const disc_frame* frames, int32_t n, disc_frame_stats* stats,
@@ -615,32 +712,7 @@ disc_status disc_integrate_frames(disc_map* m, const disc_frame* frames, int32_t
     if (!m || (n > 0 && !frames) || n < 0) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
     if (n == 0) return DISC_OK;
-    disc_status s = ensure_hist(m, n);
-    if (s != DISC_OK) return s;
-    int enq = 0;
-    for (int i = 0; i < n; i++) {
-        s = enqueue_frame(m, frames + i, i > 0 ? 1 : 0, m->d_hist + i);
-        if (s != DISC_OK) break;
-        enq++;
-    }
-    std::vector<FrameCounters> c(std::max(enq, 1));
-    if (enq > 0) CK(cudaMemcpyAsync(c.data(), m->d_hist, sizeof(FrameCounters) * enq, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    collect_timing(m);
-    int done = 0;
-    disc_status fs = DISC_OK;
-    for (int i = 0; i < enq; i++) {
-        if (stats) to_stats(c[i], stats + i);
-        if (c[i].err != 0) {
-            fs = (disc_status)c[i].err;
-            break;
-        }
-        m->next_id_upper = c[i].next_id;
-        done++;
-    }
-    if (n_done) *n_done = done;
-    if (fs != DISC_OK) return fs;
-    return s;
+    return integrate(m, frames, n, stats, n_done);
 }
 
 disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
@@ -649,34 +721,33 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
     const int M = m->have_frame ? m->last_M : 0, P = m->P, D = m->D;
+    const Scratch sc = m->bs.frame(m->last_slot);
     FrameCounters c{};
-    CK(cudaMemcpy(&c, m->d_ctr + (m->cur ^ 1), sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&c, sc.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     r->num_masks = M;
-    if (r->fbar) CK(cudaMemcpy(r->fbar, m->sc.fbar, sizeof(float) * D, cudaMemcpyDeviceToHost));
-    if (r->Dp) CK(cudaMemcpy(r->Dp, m->sc.Dp, sizeof(float) * P, cudaMemcpyDeviceToHost));
-    if (r->cosg) CK(cudaMemcpy(r->cosg, m->sc.cosg, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    if (r->fbar) CK(cudaMemcpy(r->fbar, sc.fbar, sizeof(float) * D, cudaMemcpyDeviceToHost));
+    if (r->Dp) CK(cudaMemcpy(r->Dp, sc.Dp, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    if (r->cosg) CK(cudaMemcpy(r->cosg, sc.cosg, sizeof(float) * P, cudaMemcpyDeviceToHost));
     if (M > 0) {
-        if (r->cov) CK(cudaMemcpy(r->cov, m->sc.cov, sizeof(int32_t) * (size_t)M * P, cudaMemcpyDeviceToHost));
-        if (r->npix) CK(cudaMemcpy(r->npix, m->sc.npix, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
+        if (r->cov) CK(cudaMemcpy(r->cov, sc.cov, sizeof(int32_t) * (size_t)M * P, cudaMemcpyDeviceToHost));
+        if (r->npix) CK(cudaMemcpy(r->npix, sc.npix, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
         if (r->W)
-            CK(cudaMemcpy2D(r->W, sizeof(float) * P, m->sc.W, sizeof(float) * m->Kpad, sizeof(float) * P, M,
+            CK(cudaMemcpy2D(r->W, sizeof(float) * P, sc.W, sizeof(float) * m->Kpad, sizeof(float) * P, M,
                             cudaMemcpyDeviceToHost));
-        if (r->E) CK(cudaMemcpy(r->E, m->sc.Ecan, sizeof(float) * (size_t)M * D, cudaMemcpyDeviceToHost));
-        if (r->E_fast) CK(cudaMemcpy(r->E_fast, m->sc.Efast, sizeof(float) * (size_t)M * D, cudaMemcpyDeviceToHost));
-        if (r->S) CK(cudaMemcpy(r->S, m->sc.S, sizeof(float) * 5 * M, cudaMemcpyDeviceToHost));
-        if (r->nvox) CK(cudaMemcpy(r->nvox, m->sc.nvox, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
-        if (r->rep) CK(cudaMemcpy(r->rep, m->sc.segrep, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
+        if (r->E) CK(cudaMemcpy(r->E, sc.Ecan, sizeof(float) * (size_t)M * D, cudaMemcpyDeviceToHost));
+        if (r->E_fast) CK(cudaMemcpy(r->E_fast, sc.Efast, sizeof(float) * (size_t)M * D, cudaMemcpyDeviceToHost));
+        if (r->S) CK(cudaMemcpy(r->S, sc.S, sizeof(float) * 5 * M, cudaMemcpyDeviceToHost));
+        if (r->nvox) CK(cudaMemcpy(r->nvox, sc.nvox, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
+        if (r->rep) CK(cudaMemcpy(r->rep, sc.segrep, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
     }
     r->n_seg = c.n_entries;
     if (r->seg_keys && r->seg_m && c.n_entries > 0) {
         const int n = c.n_entries;
-        std::vector<int32_t> slots(n);
-        CK(cudaMemcpy(slots.data(), m->sc.slist, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
-        std::vector<unsigned long long> keys(m->sc.smask + 1);
-        CK(cudaMemcpy(keys.data(), m->sc.skeys, sizeof(unsigned long long) * keys.size(), cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> keys(n);
+        CK(cudaMemcpy(keys.data(), sc.sent, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
         const int lim = (int)std::min<int64_t>(n, r->seg_cap);
         for (int i = 0; i < lim; i++) {
-            unsigned long long hk = keys[slots[i]];
+            const unsigned long long hk = keys[i];
             r->seg_m[i] = (int32_t)(hk >> 54);
             r->seg_keys[i] = hk & ((1ull << 54) - 1);
         }
@@ -950,8 +1021,9 @@ disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int
 
 const char* disc_phase_name(int32_t i)
 {
-    static const char* names[PH_COUNT] = {"frame_begin", "token_stats", "coverage", "weights", "pool_exact",
-                                          "pool_gemm", "backproject", "entries", "associate", "insert"};
+    static const char* names[PH_COUNT] = {"clear",    "token_stats", "coverage", "weights", "pool_exact",
+                                          "pool_gemm", "backproject", "entries",  "overlap", "score",
+                                          "union",    "apply"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : "";
 }
 

@@ -124,6 +124,13 @@ struct FrameCounters {
     int32_t pad;
 };
 
+// One slot of the per-frame (segment, voxel) hash: one 32-byte sector.
+struct __align__(32) SegSlot {
+    unsigned long long key;     // (mask << 54 | voxel key); 0 = empty
+    long long n[3];             // exact sums of the pixel normals (2^-32 fixed point)
+};
+
+// Per-frame scratch of one frame slot (pointers already offset to the slot).
 struct Scratch {
     // Eq. 1
     long long* sumF;    // [D]
@@ -138,35 +145,82 @@ struct Scratch {
     float* cosg;        // [P]
     float* fnorm;       // [P]
     // coverage / weights / pooling
-    int32_t* cov;       // [MAX_MASKS][P]
-    int32_t* npix;      // [MAX_MASKS]
+    int32_t* cov;       // [MM][P]
+    int32_t* npix;      // [MM]
     float* W;           // [Npad_max][Kpad] GEMM operand, zero padded
-    float* S;           // [MAX_MASKS][5]
-    float* Bm;          // [MAX_MASKS] sum_p w ||f_p|| (error-bound scale)
-    float* Ecan;        // [MAX_MASKS][D]
-    float* Efast;       // [MAX_MASKS][D]
-    long long* ang;     // [MAX_MASKS]
-    int32_t* nvox;      // [MAX_MASKS]
-    int32_t* segrep;    // [MAX_MASKS]
-    // per-frame hashes (cleared slot by slot at the start of the next frame)
-    unsigned long long* skeys;  // (mask << 54 | voxel key) -> slot; EMPTY = 0
-    int32_t* snpx;              // pixels per slot
-    long long* snrm;            // [3][scap] normal sums per slot
-    int32_t* slist;             // used slots
+    float* S;           // [MM][5]
+    float* Bm;          // [MM] sum_p w ||f_p|| (error-bound scale)
+    float* Ecan;        // [MM][D]
+    float* Efast;       // [MM][D]
+    long long* ang;     // [MM]
+    int32_t* nvox;      // [MM]
+    int32_t* segrep;    // [MM]
+    // per-frame (segment, voxel) hash, cleared slot by slot before reuse
+    SegSlot* sslot;             // [scap] key (mask << 54 | voxel key; EMPTY = 0) + normal sums
+    int32_t* slist;             // [scap] used slots, in claim order (entry i -> slot)
+    unsigned long long* sent;   // [scap] key of entry i (dense copy of the slot key)
+    int32_t* elab;              // [scap] per entry: label at batch start, -1 absent
     unsigned long long smask;
-    unsigned long long* okeys;  // (mask << 32 | root) ; EMPTY = ~0
+    FrameCounters* ctr;
+};
+
+// The frame slots of one batch: base pointers plus the per-frame stride of
+// every array (in elements).
+struct BatchScratch {
+    Scratch base;
+    long long sD, sP, sMM, sMMP, sW, sMMD, sS, scap;
+    __host__ __device__ Scratch frame(int f) const
+    {
+        Scratch s = base;
+        s.sumF += f * sD;
+        s.fbar += f * sD;
+        s.gvec += f * sD;
+        s.gg += f;
+        s.nsum += f;
+        s.dotg += f * sP;
+        s.ffp += f * sP;
+        s.nrm += f * sP;
+        s.Dp += f * sP;
+        s.cosg += f * sP;
+        s.fnorm += f * sP;
+        s.cov += f * sMMP;
+        s.npix += f * sMM;
+        s.W += f * sW;
+        s.S += f * sS;
+        s.Bm += f * sMM;
+        s.Ecan += f * sMMD;
+        s.Efast += f * sMMD;
+        s.ang += f * sMM;
+        s.nvox += f * sMM;
+        s.segrep += f * sMM;
+        s.sslot += f * scap;
+        s.slist += f * scap;
+        s.sent += f * scap;
+        s.elab += f * scap;
+        s.ctr += f;
+        return s;
+    }
+};
+
+// Map-level scratch of the serial (per-frame) phases.
+struct SerialScratch {
+    unsigned long long* okeys;  // (mask << 32 | root); EMPTY = ~0
     int32_t* ocnt;
     int32_t* olist;
     unsigned long long omask;
-    unsigned long long* nkeys;  // absent voxel key ; EMPTY = ~0
+    unsigned long long* nkeys;  // absent voxel key; EMPTY = ~0
     int32_t* nown;              // lowest mask label containing it
     int32_t* nlist;
     unsigned long long nmask;
-    // association
-    int32_t* edge_m;    // [edge_cap]
+    int32_t* edge_m;            // [edge_cap] accepted (segment, local root) edges
     int32_t* edge_k;
+    int32_t* edge_n;            // [1] number of edges
     int32_t edge_cap;
-    FrameCounters* ctr;
+    int32_t* copy_dst;          // [copy_cap] instance id receiving an embedding
+    int32_t* copy_src;          // >= 0 instance id, < 0: segment -(m+1)
+    int32_t* copy_n;            // [1]
+    int32_t copy_cap;
+    const FrameCounters* prev;  // counters of the frame before slot 0 in this call, or NULL
 };
 
 // frame parameters passed by value

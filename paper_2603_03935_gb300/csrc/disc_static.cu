@@ -38,7 +38,8 @@ constexpr size_t OFF_DOTG = align256(OFF_GVEC + 4 * (size_t)STATIC_MAX_D); // lo
 constexpr size_t OFF_FFP = align256(OFF_DOTG + 8 * (size_t)STATIC_MAX_P);  // long long [P]
 constexpr size_t OFF_NRM = align256(OFF_FFP + 8 * (size_t)STATIC_MAX_P);   // float [P]
 constexpr size_t OFF_FNORM = align256(OFF_NRM + 4 * (size_t)STATIC_MAX_P); // float [P]
-constexpr size_t STATIC_BYTES = align256(OFF_FNORM + 4 * (size_t)STATIC_MAX_P);
+constexpr size_t OFF_PARAMS = align256(OFF_FNORM + 4 * (size_t)STATIC_MAX_P); // FrameParams
+constexpr size_t STATIC_BYTES = align256(OFF_PARAMS + sizeof(FrameParams));
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
@@ -86,7 +87,8 @@ extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token
     fp.tokens = tokens;
     fp.token_bf16 = token_dtype == DISC_TOKENS_BF16;
     fp.gembed = global_embed;
-    Scratch sc{};
+    BatchScratch bs{};  // one frame slot: every stride stays zero
+    Scratch& sc = bs.base;
     sc.ctr = (FrameCounters*)(base + OFF_CTR);
     sc.gg = (long long*)(base + OFF_GG);
     sc.nsum = (long long*)(base + OFF_NSUM);
@@ -100,12 +102,17 @@ extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token
     sc.Dp = Dp;
     sc.cosg = cosg;
 
-    // counters, ||g||^2, the residual-norm sum and the column sums start at zero
-    if (cudaMemsetAsync(base, 0, ZERO_BYTES + 8 * (size_t)D, st) != cudaSuccess) {
+    // counters, ||g||^2, the residual-norm sum and the column sums start at
+    // zero; the frame parameters travel to the array as well (pageable
+    // source: staged before the call returns)
+    FrameParams* dfp = (FrameParams*)(base + OFF_PARAMS);
+    if (cudaMemsetAsync(base, 0, ZERO_BYTES + 8 * (size_t)D, st) != cudaSuccess ||
+        cudaMemcpyAsync(dfp, &fp, sizeof(fp), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaGetLastError();
         return DISC_ERR_CUDA;
     }
-    launch_token_stats(fp, sc, st);
+    const bool bf16 = token_dtype == DISC_TOKENS_BF16;
+    launch_token_stats(dfp, bs, 1, P, D, bf16, !bf16, st);
     if (cudaGetLastError() != cudaSuccess) return DISC_ERR_CUDA;
     int err = 0;
     if (cudaMemcpyAsync(&err, &sc.ctr->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -1,7 +1,9 @@
-// Feature-side kernels of the integration step (Sec. III-C):
+// Feature-side kernels of the integration step (Sec. III-C), batched over the
+// frames of a batch (blockIdx.z = frame slot):
 //   Eq. 1 distinctiveness map, mask->patch coverage, pooling weights with the
 //   image-based quality terms (S_size, S_sem, S_dist of Eq. 2), and the exact
-//   D-weighted pooled embedding.
+//   D-weighted pooled embedding.  None of them touches the map, so all frames
+//   of a batch run in one launch.
 #include <cuda_bf16.h>
 
 #include "disc_common.cuh"
@@ -23,12 +25,15 @@ __device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(
 
 // ---- Eq. 1, pass 1: column sums of the tokens (mean token) + range check ----
 template <typename T>
-__global__ void k_tok_colsum(FrameParams fp, Scratch sc)
+__global__ void k_tok_colsum(const FrameParams* fps, BatchScratch bs)
 {
+    const FrameParams& fp = fps[blockIdx.z];
+    if (fp.token_bf16 != (sizeof(T) == 2)) return;
+    const Scratch sc = bs.frame(blockIdx.z);
     const T* F = (const T*)fp.tokens;
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     const int p0 = blockIdx.y * 64, p1 = min(fp.P, p0 + 64);
-    if (d >= fp.D) return;
+    if (d >= fp.D || p0 >= fp.P) return;
     long long s = 0;
     bool bad = false;
     for (int p = p0; p < p1; p++) {
@@ -41,8 +46,10 @@ __global__ void k_tok_colsum(FrameParams fp, Scratch sc)
 }
 
 // ---- mean token, global embedding, ||g||^2 -----------------------------------
-__global__ void k_tok_mean(FrameParams fp, Scratch sc)
+__global__ void k_tok_mean(const FrameParams* fps, BatchScratch bs)
 {
+    const FrameParams& fp = fps[blockIdx.z];
+    const Scratch sc = bs.frame(blockIdx.z);
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     long long gg = 0;
     if (d < fp.D) {
@@ -62,8 +69,11 @@ __global__ void k_tok_mean(FrameParams fp, Scratch sc)
 
 // ---- Eq. 1, pass 2: residual norms, token . g, ||token||^2 (warp per patch) --
 template <typename T>
-__global__ void k_tok_rows(FrameParams fp, Scratch sc)
+__global__ void k_tok_rows(const FrameParams* fps, BatchScratch bs)
 {
+    const FrameParams& fp = fps[blockIdx.z];
+    if (fp.token_bf16 != (sizeof(T) == 2)) return;
+    const Scratch sc = bs.frame(blockIdx.z);
     const T* F = (const T*)fp.tokens;
     const int lane = threadIdx.x & 31;
     const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -90,8 +100,10 @@ __global__ void k_tok_rows(FrameParams fp, Scratch sc)
 }
 
 // ---- Eq. 1, pass 3: D_p and cos(f_p, g) ----------------------------------------
-__global__ void k_tok_finish(FrameParams fp, Scratch sc)
+__global__ void k_tok_finish(const FrameParams* fps, BatchScratch bs)
 {
+    const FrameParams& fp = fps[blockIdx.z];
+    const Scratch sc = bs.frame(blockIdx.z);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= fp.P || sc.ctr->err) return;
     double nbar = __ddiv_rn(unfix(*sc.nsum, S_NRM), (double)fp.P);
@@ -106,11 +118,14 @@ __global__ void k_tok_finish(FrameParams fp, Scratch sc)
 
 // ---- mask -> patch coverage: one block per patch row, shared histogram --------
 // Rows v with floor(v * Ph / H) == i form the band of patch row i.
-__global__ void k_coverage(FrameParams fp, Scratch sc)
+__global__ void k_coverage(const FrameParams* fps, BatchScratch bs)
 {
     extern __shared__ int32_t hist[];  // [M][Pw]
+    const FrameParams& fp = fps[blockIdx.z];
+    const Scratch sc = bs.frame(blockIdx.z);
     const int i = blockIdx.x;
     const int M = fp.M, Pw = fp.Pw;
+    if (M <= 0 || i >= fp.Ph) return;
     for (int j = threadIdx.x; j < M * Pw; j += blockDim.x) hist[j] = 0;
     __syncthreads();
     const int v0 = (i * fp.H + fp.Ph - 1) / fp.Ph;
@@ -135,21 +150,6 @@ __global__ void k_coverage(FrameParams fp, Scratch sc)
     }
 }
 
-// Fallback when [M][Pw] does not fit in shared memory: global atomics.
-__global__ void k_coverage_global(FrameParams fp, Scratch sc)
-{
-    const size_t n = (size_t)fp.H * fp.W;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-        int lab = fp.labels[idx];
-        if (lab >= 1 && lab <= fp.M) {
-            int v = (int)(idx / fp.W), u = (int)(idx % fp.W);
-            int p = ((v * fp.Ph) / fp.H) * fp.Pw + (u * fp.Pw) / fp.W;
-            atomicAdd(&sc.cov[(size_t)(lab - 1) * fp.P + p], 1);
-            atomicAdd(&sc.npix[lab - 1], 1);
-        }
-    }
-}
-
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red)
 {
@@ -167,12 +167,14 @@ __device__ __forceinline__ T block_sum(T v, T* red)
 // a_p = c_p * D_p;  w_p = a_p / sum a  (sum a == 0: w_p = c_p / |M|);
 // S_size = min(lambda |M| / (H W), 1);  S_dist = 0.5 + 0.5 * sum a / |M|;
 // S_sem = clamp(sum c_p ReLU(cos(f_p, g)) / |M|, 0, 1).
-__global__ void k_weights(FrameParams fp, Scratch sc)
+__global__ void k_weights(const FrameParams* fps, BatchScratch bs)
 {
     __shared__ long long red_ll[32];
     __shared__ float red_f[32];
+    const FrameParams& fp = fps[blockIdx.z];
+    const Scratch sc = bs.frame(blockIdx.z);
     const int m = blockIdx.x;
-    if (sc.ctr->err) return;
+    if (m >= fp.M || sc.ctr->err) return;
     const int npix = sc.npix[m];
     float* w = sc.W + (size_t)m * fp.Kpad;
     float* S = sc.S + 5 * m;
@@ -214,71 +216,91 @@ __global__ void k_weights(FrameParams fp, Scratch sc)
 }
 
 // ---- exact D-weighted pooled embedding: e_m[d] = sum_p w_p f_p[d] -------------
-// Each product is rounded to fp32 and added exactly in 2^-40 fixed point.
+// Each product is rounded to fp32 and added exactly in 2^-40 fixed point, so
+// the patches can be visited in any order: the block first gathers the
+// patches the mask covers, then every thread (one d) walks only those.
 template <typename T>
-__global__ void k_pool_exact(FrameParams fp, Scratch sc)
+__global__ void k_pool_exact(const FrameParams* fps, BatchScratch bs)
 {
-    extern __shared__ float wrow[];  // [P]
+    extern __shared__ unsigned char pool_smem[];
+    __shared__ int nnz;
+    const FrameParams& fp = fps[blockIdx.z];
+    if (fp.token_bf16 != (sizeof(T) == 2)) return;
+    const Scratch sc = bs.frame(blockIdx.z);
+    int* plist = (int*)pool_smem;                 // [P]
+    float* wlist = (float*)(plist + fp.P);        // [P]
     const T* F = (const T*)fp.tokens;
     const int m = blockIdx.x;
+    if (m >= fp.M || sc.ctr->err) return;
     const int d = blockIdx.y * blockDim.x + threadIdx.x;
-    if (sc.ctr->err) return;
     const bool ok = sc.npix[m] >= fp.min_px;
-    for (int p = threadIdx.x; p < fp.P; p += blockDim.x) wrow[p] = ok ? sc.W[(size_t)m * fp.Kpad + p] : 0.0f;
+    if (threadIdx.x == 0) nnz = 0;
+    __syncthreads();
+    if (ok)
+        for (int p = threadIdx.x; p < fp.P; p += blockDim.x) {
+            float wp = sc.W[(size_t)m * fp.Kpad + p];
+            if (wp != 0.0f) {
+                int at = atomicAdd(&nnz, 1);
+                plist[at] = p;
+                wlist[at] = wp;
+            }
+        }
     __syncthreads();
     if (d >= fp.D) return;
     long long acc = 0;
-    if (ok)
-        for (int p = 0; p < fp.P; p++) {
-            float wp = wrow[p];
-            if (wp != 0.0f) acc += fix32f(__fmul_rn(wp, tok<T>(F, (size_t)p * fp.D + d)), S_EMB);
-        }
+    const int n = nnz;
+    for (int i = 0; i < n; i++)
+        acc += fix32f(__fmul_rn(wlist[i], tok<T>(F, (size_t)plist[i] * fp.D + d)), S_EMB);
     sc.Ecan[(size_t)m * fp.D + d] = __double2float_rn(unfix(acc, S_EMB));
 }
 
 // ---- host launchers (each returns the number of kernels it enqueued) ----------
-int launch_token_stats(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+// Batched launchers cover B frame slots; P, D, Ph, Pw and Mmax bound the grids.
+int launch_token_stats(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, bool any_bf16,
+                       bool any_f32, cudaStream_t st)
 {
     const dim3 b256(256);
-    dim3 gcol((fp.D + 255) / 256, (fp.P + 63) / 64);
-    if (fp.token_bf16) k_tok_colsum<__nv_bfloat16><<<gcol, b256, 0, st>>>(fp, sc);
-    else k_tok_colsum<float><<<gcol, b256, 0, st>>>(fp, sc);
-    k_tok_mean<<<(fp.D + 255) / 256, b256, 0, st>>>(fp, sc);
-    if (fp.token_bf16) k_tok_rows<__nv_bfloat16><<<(fp.P + 7) / 8, b256, 0, st>>>(fp, sc);
-    else k_tok_rows<float><<<(fp.P + 7) / 8, b256, 0, st>>>(fp, sc);
-    k_tok_finish<<<(fp.P + 255) / 256, b256, 0, st>>>(fp, sc);
-    return 4;
+    int n = 0;
+    dim3 gcol((D + 255) / 256, (P + 63) / 64, B);
+    if (any_f32) { k_tok_colsum<float><<<gcol, b256, 0, st>>>(fps, bs); n++; }
+    if (any_bf16) { k_tok_colsum<__nv_bfloat16><<<gcol, b256, 0, st>>>(fps, bs); n++; }
+    k_tok_mean<<<dim3((D + 255) / 256, 1, B), b256, 0, st>>>(fps, bs);
+    n++;
+    dim3 grow((P + 7) / 8, 1, B);
+    if (any_f32) { k_tok_rows<float><<<grow, b256, 0, st>>>(fps, bs); n++; }
+    if (any_bf16) { k_tok_rows<__nv_bfloat16><<<grow, b256, 0, st>>>(fps, bs); n++; }
+    k_tok_finish<<<dim3((P + 255) / 256, 1, B), b256, 0, st>>>(fps, bs);
+    return n + 1;
 }
 
-int launch_coverage(const FrameParams& fp, const Scratch& sc, cudaStream_t st, int cov_smem_limit)
+int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int Ph, int Pw, int Mmax, cudaStream_t st)
 {
-    if (fp.M <= 0) return 0;
-    size_t hsm = sizeof(int32_t) * (size_t)fp.M * fp.Pw;
-    if ((int)hsm <= cov_smem_limit) {
-        k_coverage<<<fp.Ph, 256, hsm, st>>>(fp, sc);
-    } else {
-        cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)fp.M * fp.P, st);
-        k_coverage_global<<<608, 256, 0, st>>>(fp, sc);
-    }
+    if (Mmax <= 0) return 0;
+    k_coverage<<<dim3(Ph, 1, B), 256, coverage_smem_bytes(Mmax, Pw), st>>>(fps, bs);
     return 1;
 }
 
-int launch_weights(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+int launch_weights(const FrameParams* fps, const BatchScratch& bs, int B, int Mmax, cudaStream_t st)
 {
-    if (fp.M <= 0) return 0;
-    k_weights<<<fp.M, 256, 0, st>>>(fp, sc);
+    if (Mmax <= 0) return 0;
+    k_weights<<<dim3(Mmax, 1, B), 256, 0, st>>>(fps, bs);
     return 1;
 }
 
-int launch_pool_exact(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, int Mmax, bool any_bf16,
+                      bool any_f32, cudaStream_t st)
 {
-    if (fp.M <= 0) return 0;
-    dim3 gp(fp.M, (fp.D + 255) / 256);
-    size_t psm = sizeof(float) * (size_t)fp.P;
-    if (fp.token_bf16) k_pool_exact<__nv_bfloat16><<<gp, 256, psm, st>>>(fp, sc);
-    else k_pool_exact<float><<<gp, 256, psm, st>>>(fp, sc);
-    return 1;
+    if (Mmax <= 0) return 0;
+    dim3 gp(Mmax, (D + 255) / 256, B);
+    size_t psm = 8 * (size_t)P;
+    int n = 0;
+    if (any_f32) { k_pool_exact<float><<<gp, 256, psm, st>>>(fps, bs); n++; }
+    if (any_bf16) { k_pool_exact<__nv_bfloat16><<<gp, 256, psm, st>>>(fps, bs); n++; }
+    return n;
 }
+
+// the [M][Pw] coverage histogram of one block
+size_t coverage_smem_bytes(int max_masks, int Pw) { return sizeof(int32_t) * (size_t)max_masks * Pw; }
 
 cudaError_t set_feature_kernel_attrs(int max_dyn_smem)
 {

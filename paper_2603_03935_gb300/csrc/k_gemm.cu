@@ -117,14 +117,17 @@ __host__ size_t gemm_smem_bytes(int NT)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128, 1) k_pool_gemm(FrameParams fp, Scratch sc, int NT)
+__global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
+    const FrameParams& fp = fps[blockIdx.y];
+    const Scratch sc = bs.frame(blockIdx.y);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const T* F = (const T*)fp.tokens;
     const int D = fp.D, P = fp.P, M = fp.M;
     const int d0 = blockIdx.x * GEMM_MT;
-    if (sc.ctr->err) return;  // uniform for the block
+    // uniform for the block: other dtype, no masks, tile past D, failed frame
+    if (fp.token_bf16 != (sizeof(T) == 2) || M <= 0 || d0 >= D || sc.ctr->err) return;
 
     const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * 4;
     const uint32_t B_LBO = (uint32_t)NT * 16;
@@ -261,15 +264,17 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(FrameParams fp, Scratch sc
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-int launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st)
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, bool any_bf16,
+                     bool any_f32, cudaStream_t st)
 {
-    if (fp.M <= 0) return 0;
-    const int NT = fp.Npad;
+    if (Mmax <= 0) return 0;
+    const int NT = std::max(16, (Mmax + 15) / 16 * 16);
     const size_t smem = gemm_smem_bytes(NT);
-    dim3 g((fp.D + GEMM_MT - 1) / GEMM_MT);
-    if (fp.token_bf16) k_pool_gemm<__nv_bfloat16><<<g, 128, smem, st>>>(fp, sc, NT);
-    else k_pool_gemm<float><<<g, 128, smem, st>>>(fp, sc, NT);
-    return 1;
+    dim3 g((D + GEMM_MT - 1) / GEMM_MT, B);
+    int n = 0;
+    if (any_f32) { k_pool_gemm<float><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any_bf16) { k_pool_gemm<__nv_bfloat16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    return n;
 }
 
 cudaError_t set_gemm_kernel_attrs()

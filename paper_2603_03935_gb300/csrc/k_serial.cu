@@ -1,0 +1,486 @@
+// The stateful part of the integration step, run frame after frame in order
+// (each frame sees the map its predecessors left):
+//   k_overlap  Sec. III-B  exact overlap histogram ov[m][k] of every segment
+//                          with the instances of the map before this frame
+//   k_score    Sec. III-B  geometry gate (overlap coefficient) and cosine gate
+//                          per (segment, instance) pair; fast tensor-core
+//                          score, exact re-score inside its error band
+//   k_union    Sec. III-B  union of segments and instances (representative =
+//              Sec. III-C  smallest id), new ids, merges, Q-replacement fusion
+//   k_apply    Sec. III-B  embedding copies, insertion of the new voxels,
+//                          flattening of the parent table, cleanup
+#include <climits>
+
+#include "disc_common.cuh"
+#include "kernels.h"
+
+namespace disc {
+
+__device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(&c->err, 0, code); }
+
+// an error of the previous frame of the same call stops this one
+__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, int f, const FrameCounters* prev)
+{
+    const Scratch sc = bs.frame(f);
+    if (sc.ctr->err) return true;
+    const int pe = f > 0 ? bs.frame(f - 1).ctr->err : (prev ? prev->err : 0);
+    if (pe) {
+        set_err(sc.ctr, pe);
+        return true;
+    }
+    return false;
+}
+
+// ---- overlap histogram -----------------------------------------------------------
+__global__ void k_overlap(BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst)
+{
+    const Scratch sc = bs.frame(f);
+    if (frame_blocked(bs, f, ss.prev)) return;
+    const int ne = sc.ctr->n_entries;
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < ne; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < ne;
+        unsigned long long okey = EMPTY_KEY, key = 0;
+        int m = 0;
+        bool found = false;
+        if (act) {
+            const unsigned long long hk = sc.sent[i];
+            m = (int)(hk >> 54);
+            key = hk & ((1ull << 54) - 1);
+            int lab = sc.elab[i];
+            if (lab < 0) {
+                // absent when the batch started: an earlier frame may have added it
+                unsigned long long h = mix64(key) & vt.mask;
+                for (int pr = 0;; pr++) {
+                    const unsigned long long kk = vt.keys[h];
+                    if (kk == key) { lab = vt.labels[h]; break; }
+                    if (kk == EMPTY_KEY || pr > (int)vt.mask) break;
+                    h = (h + 1) & vt.mask;
+                }
+            }
+            if (lab >= 0) {
+                found = true;
+                okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
+            }
+        }
+        // one hash update per distinct (segment, root) of the warp
+        const unsigned wm = __ballot_sync(0xffffffffu, found);
+        if (found) {
+            const unsigned grp = __match_any_sync(wm, okey);
+            if (lane == __ffs(grp) - 1) {
+                unsigned long long t = mix64(okey) & ss.omask;
+                for (int pr = 0;; pr++) {
+                    const unsigned long long cur = ss.okeys[t];
+                    if (cur == okey) break;
+                    if (cur == EMPTY_KEY) {
+                        const unsigned long long prev = atomicCAS(&ss.okeys[t], EMPTY_KEY, okey);
+                        if (prev == EMPTY_KEY) { ss.olist[atomicAdd(&sc.ctr->n_pairs, 1)] = (int)t; break; }
+                        if (prev == okey) break;
+                    }
+                    t = (t + 1) & ss.omask;
+                    if (pr > (int)ss.omask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
+                }
+                atomicAdd(&ss.ocnt[t], __popc(grp));
+            }
+        } else if (act) {
+            unsigned long long t = mix64(key) & ss.nmask;
+            for (int pr = 0;; pr++) {
+                const unsigned long long cur = ss.nkeys[t];
+                if (cur == key) break;
+                if (cur == EMPTY_KEY) {
+                    const unsigned long long prev = atomicCAS(&ss.nkeys[t], EMPTY_KEY, key);
+                    if (prev == EMPTY_KEY) { ss.nlist[atomicAdd(&sc.ctr->n_new, 1)] = (int)t; break; }
+                    if (prev == key) break;
+                }
+                t = (t + 1) & ss.nmask;
+                if (pr > (int)ss.nmask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
+            }
+            atomicMin(&ss.nown[t], m);
+        }
+    }
+}
+
+// ---- gates per (segment, instance) pair: one warp per pair -----------------------
+struct ScoreParams {
+    float eta;      // error bound of the tensor-core pooled embedding, relative to sum_p w_p ||f_p||
+    float dot_err;  // error bound of an fp32 warp cosine
+};
+
+__global__ void k_score(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst, ScoreParams sp)
+{
+    const Scratch sc = bs.frame(f);
+    if (frame_blocked(bs, f, ss.prev)) return;
+    const int lane = threadIdx.x & 31;
+    const int npairs = sc.ctr->n_pairs;
+    const int D = fp.D;
+    int border = 0;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npairs; i += (gridDim.x * blockDim.x) >> 5) {
+        const int slot = ss.olist[i];
+        const unsigned long long okey = ss.okeys[slot];
+        const int m = (int)(okey >> 32) - 1;
+        const int k = (int)(okey & 0xffffffffu);
+        const long long ov = ss.ocnt[slot];
+        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
+        const long long denom = min((long long)sc.nvox[m], inst.count[k]);
+        if (ov * (long long)fp.ov_den < (long long)fp.ov_num * denom) continue;
+        const float* a = sc.Efast + (size_t)m * D;
+        const float* b = inst.E + (size_t)k * D;
+        float dt = 0.0f, na = 0.0f, nb = 0.0f;
+        if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads
+            const float4* a4 = (const float4*)a;
+            const float4* b4 = (const float4*)b;
+            for (int d = lane; d < (D >> 2); d += 32) {
+                const float4 x = a4[d], y = b4[d];
+                dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+            }
+        } else {
+            for (int d = lane; d < D; d += 32) {
+                const float x = a[d], y = b[d];
+                dt += x * y;
+                na += x * x;
+                nb += y * y;
+            }
+        }
+        dt = warp_sum(dt);
+        na = warp_sum(na);
+        nb = warp_sum(nb);
+        bool edge;
+        const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
+        const float band = (na > 0.0f) ? 2.2f * sp.eta * sc.Bm[m] / sqrtf(na) + sp.dot_err + 1e-6f : 2.0f;
+        if (fabsf(cf - fp.tau) > band) {
+            edge = cf >= fp.tau;
+        } else {
+            // exact re-score with the exact pooled embedding
+            const float* ae = sc.Ecan + (size_t)m * D;
+            long long xd = 0, xa = 0, xb = 0;
+            for (int d = lane; d < D; d += 32) {
+                const float x = ae[d], y = b[d];
+                xd += fix32f(__fmul_rn(x, y), S_SQ);
+                xa += fix32f(__fmul_rn(x, x), S_SQ);
+                xb += fix32f(__fmul_rn(y, y), S_SQ);
+            }
+            xd = warp_sum(xd);
+            xa = warp_sum(xa);
+            xb = warp_sum(xb);
+            float ce = 0.0f;
+            if (xa != 0 && xb != 0)
+                ce = __double2float_rn(__ddiv_rn(unfix(xd, S_SQ),
+                                                 __dmul_rn(__dsqrt_rn(unfix(xa, S_SQ)), __dsqrt_rn(unfix(xb, S_SQ)))));
+            edge = ce >= fp.tau;
+            border++;
+        }
+        if (edge && lane == 0) {
+            const int e = atomicAdd(ss.edge_n, 1);
+            if (e < ss.edge_cap) {
+                ss.edge_m[e] = m;
+                ss.edge_k[e] = k;
+            } else {
+                set_err(sc.ctr, DISC_ERR_CAPACITY);
+            }
+        }
+    }
+    if (lane == 0 && border) atomicAdd(&sc.ctr->borderline, border);
+}
+
+// ---- union, new ids, merges, fusion (one block) ------------------------------------
+// Shared memory: a hash set of the frame's active roots (all overlap pairs)
+// that also hands out local indices to the roots that carry an edge, and
+// per-local-root arrays for the union-find and the fusion winners.
+constexpr int UNION_THREADS = 1024;
+constexpr int PAIR_CAP = 8192;             // distinct (segment, instance) overlaps per frame
+constexpr int EDGE_ROOT_CAP = 4096;        // distinct instances with an accepted edge per frame
+constexpr int UHASH = 2 * PAIR_CAP;        // hash slots (load <= 1/2)
+constexpr unsigned UH_EMPTY = 0xffffffffu;
+constexpr unsigned UH_UNUSED = 0xffffffffu;
+constexpr unsigned UH_LOCAL = 0x80000000u;
+constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 16;
+
+__device__ __forceinline__ unsigned uhash(unsigned k) { return (unsigned)(mix64(k) & (UHASH - 1)); }
+
+__device__ int uf_find(const int* uf, int x)
+{
+    while (uf[x] != x) x = uf[x];
+    return x;
+}
+
+__global__ void __launch_bounds__(UNION_THREADS, 1)
+k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst, int* next_id)
+{
+    extern __shared__ __align__(16) unsigned char union_smem[];
+    unsigned* hkey = (unsigned*)union_smem;           // [UHASH] root id
+    unsigned* hval = hkey + UHASH;                    // [UHASH] claimant edge, then UH_LOCAL | local index
+    int* gid = (int*)(hval + UHASH);                  // [EDGE_ROOT_CAP] local -> instance id
+    int* uf = gid + EDGE_ROOT_CAP;                    // union-find over local indices
+    int* best_src = uf + EDGE_ROOT_CAP;               // fusion winner per component
+    float* best_q = (float*)(best_src + EDGE_ROOT_CAP);
+    __shared__ int first[MAX_MASKS];
+    __shared__ int s_nroots, s_nloc, s_merges, s_new, s_ncopy;
+    const int tid = threadIdx.x;
+    const Scratch sc = bs.frame(f);
+    FrameCounters* ctr = sc.ctr;
+    if (frame_blocked(bs, f, ss.prev)) return;
+    const int M = fp.M;
+    const int npairs = ctr->n_pairs;
+    const int nedge = min(*ss.edge_n, ss.edge_cap);
+    if (npairs > PAIR_CAP) {
+        if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
+        return;
+    }
+    for (int i = tid; i < UHASH; i += UNION_THREADS) {
+        hkey[i] = UH_EMPTY;
+        hval[i] = UH_UNUSED;
+    }
+    for (int m = tid; m < MAX_MASKS; m += UNION_THREADS) first[m] = -1;
+    if (tid == 0) { s_nroots = 0; s_nloc = 0; s_merges = 0; s_new = 0; s_ncopy = 0; }
+    __syncthreads();
+    // (1) active set: distinct roots of all overlap pairs
+    for (int i = tid; i < npairs; i += UNION_THREADS) {
+        const unsigned k = (unsigned)(ss.okeys[ss.olist[i]] & 0xffffffffu);
+        unsigned h = uhash(k);
+        while (true) {
+            const unsigned cur = hkey[h];
+            if (cur == k) break;
+            if (cur == UH_EMPTY) {
+                const unsigned prev = atomicCAS(&hkey[h], UH_EMPTY, k);
+                if (prev == UH_EMPTY) { atomicAdd(&s_nroots, 1); break; }
+                if (prev == k) break;
+            }
+            h = (h + 1) & (UHASH - 1);
+        }
+    }
+    __syncthreads();
+    // (2) local indices for the roots that carry an edge: the first edge to
+    //     claim a root's slot assigns the index
+    for (int e = tid; e < nedge; e += UNION_THREADS) {
+        const unsigned k = (unsigned)ss.edge_k[e];
+        unsigned h = uhash(k);
+        while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+        atomicCAS(&hval[h], UH_UNUSED, (unsigned)e);
+    }
+    __syncthreads();
+    for (int e = tid; e < nedge; e += UNION_THREADS) {
+        const unsigned k = (unsigned)ss.edge_k[e];
+        unsigned h = uhash(k);
+        while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+        if (hval[h] == (unsigned)e) {
+            const int x = atomicAdd(&s_nloc, 1);
+            if (x < EDGE_ROOT_CAP) {
+                gid[x] = (int)k;
+                uf[x] = x;
+            }
+            hval[h] = UH_LOCAL | (unsigned)x;
+        }
+    }
+    __syncthreads();
+    const int nloc = s_nloc;
+    if (nloc > EDGE_ROOT_CAP) {
+        if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
+        return;
+    }
+    // (3) union of the instances one segment joins; the set's root is the
+    //     member with the smallest instance id
+    if (tid == 0) {
+        for (int e = 0; e < nedge; e++) {
+            const int m = ss.edge_m[e];
+            const unsigned k = (unsigned)ss.edge_k[e];
+            unsigned h = uhash(k);
+            while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+            const int x = (int)(hval[h] & ~UH_LOCAL);
+            if (first[m] < 0) { first[m] = x; continue; }
+            const int a = uf_find(uf, first[m]), b = uf_find(uf, x);
+            if (a != b) {
+                if (gid[a] < gid[b]) uf[b] = a; else uf[a] = b;
+            }
+        }
+    }
+    __syncthreads();
+    for (int x = tid; x < nloc; x += UNION_THREADS) uf[x] = uf_find(uf, x);  // stores only roots
+    __syncthreads();
+    for (int m = tid; m < M; m += UNION_THREADS) sc.segrep[m] = first[m] >= 0 ? gid[uf[first[m]]] : -1;
+    __syncthreads();
+    // (4) new instances for live segments without an edge, in mask order
+    if (tid == 0) {
+        int id = *next_id;
+        for (int m = 0; m < M; m++) {
+            if (sc.nvox[m] > 0 && sc.segrep[m] < 0) {
+                if (id >= inst.cap) { set_err(ctr, DISC_ERR_CAPACITY); break; }
+                sc.segrep[m] = id;
+                inst.parent[id] = id;
+                inst.count[id] = 0;
+                inst.Q[id] = sc.S[5 * m + 4];
+                inst.n_obs[id] = 1;
+                const int c = s_ncopy++;
+                ss.copy_dst[c] = id;
+                ss.copy_src[c] = -(m + 1);
+                id++;
+                s_new++;
+            }
+        }
+        if (!ctr->err) *next_id = id;
+    }
+    __syncthreads();
+    if (ctr->err) return;
+    // (5) fusion per component: the candidates in the order (members by
+    //     ascending id, then segments by ascending mask) keep the first one
+    //     whose Q is the component's maximum (strict '>' while scanning)
+    for (int r = tid; r < nloc; r += UNION_THREADS) {
+        best_src[r] = INT_MIN;
+        if (uf[r] != r) continue;
+        const int rep = gid[r];
+        float q = -INFINITY;
+        int obs = 0;
+        for (int x = 0; x < nloc; x++) {
+            if (uf[x] != r) continue;
+            obs += inst.n_obs[gid[x]];
+            q = fmaxf(q, inst.Q[gid[x]]);
+        }
+        for (int m = 0; m < M; m++)
+            if (sc.segrep[m] == rep) {
+                obs++;
+                q = fmaxf(q, sc.S[5 * m + 4]);
+            }
+        int src = INT_MAX;
+        for (int x = 0; x < nloc; x++)
+            if (uf[x] == r && inst.Q[gid[x]] == q) src = min(src, gid[x]);
+        if (src == INT_MAX)
+            for (int m = 0; m < M && src == INT_MAX; m++)
+                if (sc.segrep[m] == rep && sc.S[5 * m + 4] == q) src = -(m + 1);
+        best_src[r] = src;
+        best_q[r] = q;
+        inst.n_obs[rep] = obs;
+    }
+    __syncthreads();
+    for (int r = tid; r < nloc; r += UNION_THREADS) {
+        const int src = best_src[r];
+        if (src == INT_MIN || src == gid[r]) continue;
+        const int c = atomicAdd(&s_ncopy, 1);
+        ss.copy_dst[c] = gid[r];
+        ss.copy_src[c] = src;
+        inst.Q[gid[r]] = best_q[r];
+    }
+    // (6) merge members into their representative
+    for (int x = tid; x < nloc; x += UNION_THREADS) {
+        const int r = uf[x];
+        if (r == x) continue;
+        const int k = gid[x], rep = gid[r];
+        inst.parent[k] = rep;
+        atomicAdd((unsigned long long*)&inst.count[rep], (unsigned long long)inst.count[k]);
+        inst.count[k] = 0;
+        atomicAdd(&s_merges, 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *ss.copy_n = s_ncopy;
+        ctr->active_instances = s_nroots;
+        ctr->new_instances = s_new;
+        ctr->merges = s_merges;
+        ctr->n_edges = nedge;
+        ctr->next_id = *next_id;
+    }
+}
+
+// ---- embeddings, new voxels, parent flattening, cleanup ---------------------------
+__global__ void k_apply(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst,
+                        const int* next_id)
+{
+    const Scratch sc = bs.frame(f);
+    const bool ok = !frame_blocked(bs, f, ss.prev);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gsz = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int D = fp.D;
+    if (ok) {
+        // winning embeddings (the sources are never written in this frame)
+        const int nc = *ss.copy_n;
+        for (int c = gtid >> 5; c < nc; c += gsz >> 5) {
+            const int src = ss.copy_src[c];
+            const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
+            float* to = inst.E + (size_t)ss.copy_dst[c] * D;
+            for (int d = lane; d < D; d += 32) to[d] = from[d];
+        }
+        // new voxels: the lowest segment index owns a voxel
+        const int nn = sc.ctr->n_new;
+        for (int i = gtid; i < nn; i += gsz) {
+            const int t = ss.nlist[i];
+            const unsigned long long key = ss.nkeys[t];
+            const int lab = sc.segrep[ss.nown[t] - 1];
+            unsigned long long h = mix64(key) & vt.mask;
+            for (int pr = 0;; pr++) {
+                const unsigned long long prev = atomicCAS(&vt.keys[h], EMPTY_KEY, key);
+                if (prev == EMPTY_KEY) { vt.labels[h] = lab; break; }
+                h = (h + 1) & vt.mask;
+                if (pr > (int)vt.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
+            }
+            // one count update per distinct instance of the warp
+            const unsigned grp = __match_any_sync(__activemask(), lab);
+            if (lane == __ffs(grp) - 1) atomicAdd((unsigned long long*)&inst.count[lab], (unsigned long long)__popc(grp));
+        }
+        if (gtid == 0) atomicAdd(vt.used, (unsigned long long)nn);
+        // keep the parent table flat (two levels at most after this frame)
+        if (sc.ctr->merges > 0) {
+            const int nid = *next_id;
+            for (int i = gtid; i < nid; i += gsz) inst.parent[i] = inst.parent[inst.parent[i]];
+        }
+    }
+    // cleanup of the serial hashes, whatever happened above
+    const int np = sc.ctr->n_pairs, nn = sc.ctr->n_new;
+    for (int i = gtid; i < np; i += gsz) {
+        const int s = ss.olist[i];
+        ss.okeys[s] = EMPTY_KEY;
+        ss.ocnt[s] = 0;
+    }
+    for (int i = gtid; i < nn; i += gsz) {
+        const int s = ss.nlist[i];
+        // inserted above before this thread reset it: same thread, same i
+        ss.nkeys[s] = EMPTY_KEY;
+        ss.nown[s] = INT_MAX;
+    }
+}
+
+// edge and copy counters of the next frame start at zero
+__global__ void k_serial_reset(SerialScratch ss)
+{
+    *ss.edge_n = 0;
+    *ss.copy_n = 0;
+}
+
+// ---- host launchers (each returns the number of kernels it enqueued) ------------------
+int launch_overlap(const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
+                   const Instances& inst, cudaStream_t st)
+{
+    k_overlap<<<152 * 2, 256, 0, st>>>(bs, f, ss, vt, inst);
+    return 1;
+}
+
+int launch_score(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
+                 float eta, float dot_err, cudaStream_t st)
+{
+    ScoreParams sp{eta, dot_err};
+    k_score<<<152, 256, 0, st>>>(fp, bs, f, ss, inst, sp);
+    return 1;
+}
+
+int launch_union(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
+                 int* next_id, cudaStream_t st)
+{
+    k_union<<<1, UNION_THREADS, UNION_SMEM, st>>>(fp, bs, f, ss, inst, next_id);
+    return 1;
+}
+
+int launch_apply(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
+                 const Instances& inst, const int* next_id, cudaStream_t st)
+{
+    k_apply<<<152 * 2, 256, 0, st>>>(fp, bs, f, ss, vt, inst, next_id);
+    k_serial_reset<<<1, 1, 0, st>>>(ss);
+    return 2;
+}
+
+cudaError_t set_serial_kernel_attrs()
+{
+    return cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+}
+
+}  // namespace disc

@@ -1,5 +1,12 @@
 // Host-side launchers of the libdisc kernels.  Each enqueues on the given
 // stream and returns the number of kernels it launched.
+//
+// A batch of B frames runs in two parts:
+//   batched (one launch covers every frame slot; nothing here writes the map):
+//     slot_clear, token_stats (Eq. 1), coverage, weights, pool_exact,
+//     pool_gemm (tcgen05), backproject, entries (+ Q)
+//   serial (per frame, in order; these read and write the map):
+//     overlap, score, union, apply
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,40 +15,52 @@
 
 namespace disc {
 
-// per-frame phases, in enqueue order
+// phases timed by disc_map_phase_times, in enqueue order
 enum Phase {
-    PH_BEGIN = 0,     // clear the previous frame's scratch
-    PH_TOKENS,        // Eq. 1 (4 kernels)
+    PH_CLEAR = 0,     // clear the frame slots' scratch from their last use
+    PH_TOKENS,        // Eq. 1
     PH_COVERAGE,      // mask -> patch coverage
     PH_WEIGHTS,       // pooling weights, S_size / S_sem / S_dist
     PH_POOL_EXACT,    // exact D-weighted pooled embedding
     PH_POOL_GEMM,     // tcgen05 pooled embedding (fast score)
     PH_BACKPROJECT,   // depth -> voxel keys, normals, per-segment sets
-    PH_ENTRIES,       // S_angle terms, map lookup, overlap histogram
-    PH_ASSOCIATE,     // gates, union, new ids, merges, fusion
-    PH_INSERT,        // new voxels
+    PH_ENTRIES,       // S_angle terms, |V_m|, labels at batch start, Q
+    PH_OVERLAP,       // per frame: overlap histogram against the current map
+    PH_SCORE,         // per frame: geometry and cosine gates
+    PH_UNION,         // per frame: union, new ids, merges, fusion (one CTA)
+    PH_APPLY,         // per frame: embeddings, new voxels, parent flattening
     PH_COUNT
 };
 
-int launch_frame_begin(const Scratch& sc, FrameCounters* prev, const int* next_id, int D, int sticky,
-                       cudaStream_t st);
-int launch_token_stats(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-int launch_coverage(const FrameParams& fp, const Scratch& sc, cudaStream_t st, int cov_smem_limit);
-int launch_weights(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-int launch_pool_exact(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-int launch_pool_gemm(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-int launch_backproject(const FrameParams& fp, const Scratch& sc, cudaStream_t st);
-int launch_entries(const FrameParams& fp, const Scratch& sc, const VoxelTable& vt, const Instances& inst,
+// batched
+int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st);
+int launch_token_stats(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, bool any_bf16,
+                       bool any_f32, cudaStream_t st);
+int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int Ph, int Pw, int Mmax, cudaStream_t st);
+int launch_weights(const FrameParams* fps, const BatchScratch& bs, int B, int Mmax, cudaStream_t st);
+int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, int Mmax, bool any_bf16,
+                      bool any_f32, cudaStream_t st);
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, bool any_bf16,
+                     bool any_f32, cudaStream_t st);
+int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int B, int H, int W, cudaStream_t st);
+int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int B, int Mmax,
                    cudaStream_t st);
-int launch_associate(const FrameParams& fp, const Scratch& sc, const Instances& inst, int* next_id, float eta,
-                     float dot_err, cudaStream_t st);
-int launch_insert(const FrameParams& fp, const Scratch& sc, const VoxelTable& vt, const Instances& inst,
-                  cudaStream_t st);
 
+// serial, one frame slot f
+int launch_overlap(const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
+                   const Instances& inst, cudaStream_t st);
+int launch_score(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
+                 float eta, float dot_err, cudaStream_t st);
+int launch_union(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
+                 int* next_id, cudaStream_t st);
+int launch_apply(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
+                 const Instances& inst, const int* next_id, cudaStream_t st);
+
+size_t coverage_smem_bytes(int max_masks, int Pw);
+size_t gemm_smem_bytes(int NT);
 cudaError_t set_feature_kernel_attrs(int max_dyn_smem);
 cudaError_t set_gemm_kernel_attrs();
-cudaError_t set_map_kernel_attrs();
-size_t gemm_smem_bytes(int NT);
+cudaError_t set_serial_kernel_attrs();
 
 // maintenance and queries
 void launch_rehash(const VoxelTable& from, const VoxelTable& to, int* err, cudaStream_t st);
