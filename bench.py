@@ -117,10 +117,10 @@ class ClockSampler:
 
 
 def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
-    """Bytes one launch of a phase must move.  Batched phases
-    cover every frame of the batch in one launch; serial phases one frame
-    (the mean over the batch is returned for those).  sts: per-frame stats."""
-    batched = {
+    """Bytes a phase must move for all frames of the timed batch together
+    (see the design doc); divided by the phase's launches it gives the bytes per
+    launch.  sts: per-frame stats, Ms: masks per frame."""
+    per_frame = {
         "backproject": lambda s, M: 6 * H * W + 36 * s["unique_seg_voxels"],
         "entries": lambda s, M: 52 * s["unique_seg_voxels"],
         "token_stats": lambda s, M: 4 * P * D,
@@ -128,17 +128,13 @@ def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
         "pool_exact": lambda s, M: 4 * P * D + 4 * M * D,
         "coverage": lambda s, M: 2 * H * W + 4 * M * P,
         "weights": lambda s, M: 8 * M * P,
-    }
-    serial = {
         "overlap": lambda s, M: 16 * s["unique_seg_voxels"] + 12 * s["new_voxels"],
         "score": lambda s, M: 8 * D * s["overlap_pairs"],
         "apply": lambda s, M: 24 * s["new_voxels"] + 8 * D * (s["new_instances"] + s["merges"]),
     }
-    if phase in batched:
-        return float(sum(batched[phase](s_, M) for s_, M in zip(sts, Ms)))
-    if phase in serial:
-        return float(np.mean([serial[phase](s_, M) for s_, M in zip(sts, Ms)]))
-    return 0.0
+    if phase not in per_frame:
+        return 0.0
+    return float(sum(per_frame[phase](s_, M) for s_, M in zip(sts, Ms)))
 
 
 def run_reference(args, rank):
@@ -332,13 +328,14 @@ def main():
     dom = max(single, key=lambda k: phases[k]["ms"])
     st_list = [{k: getattr(ph_stats[j], k) for k, _ in binding.Stats._fields_} for j in range(B)]
     Ms = [int(fr.num_masks[lo - B + j]) for j in range(B)]
-    alg = algorithmic_bytes(dom, st_list, H, W_, P, D, Ms, Kpad)
-    launch_ms = phases[dom]["ms"] / max(phases[dom]["calls"], 1)
-    achieved = alg / (launch_ms / 1e3) / 1e9 if launch_ms > 0 and alg > 0 else 0.0
+    alg_total = algorithmic_bytes(dom, st_list, H, W_, P, D, Ms, Kpad)
+    calls = max(phases[dom]["calls"], 1)
+    launch_ms = phases[dom]["ms"] / calls
+    achieved = alg_total / (phases[dom]["ms"] / 1e3) / 1e9 if phases[dom]["ms"] > 0 and alg_total > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "alg_bytes_per_launch": float(alg), "launch_us": launch_ms * 1e3,
-                "launches_per_frame": phases[dom]["calls"] / B}
+                "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
+                "launches_per_frame": calls / B}
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None

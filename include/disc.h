@@ -210,9 +210,10 @@ int64_t disc_map_kernel_launches(disc_map* map);
 /* Per-phase timing with CUDA events recorded on the map's stream around each
  * phase of every frame (off by default; enabling resets the totals).  Phases:
  * 0 clear, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
- * 5 pool_gemm, 6 backproject, 7 entries (S_angle, |V_m|, lookup, Q) -- one
- * interval per batch each -- and 8 overlap, 9 score, 10 union, 11 apply --
- * one interval per frame each.  ms/launches/calls: [n] accumulated device
+ * 5 pool_gemm -- one interval per batch each --, 6 backproject and 7 entries
+ * (S_angle, |V_m|, lookup; then Q) -- one interval per chunk of 4 frames --,
+ * and 8 overlap, 9 score, 10 union, 11 apply -- one interval per frame each.
+ * With timing on, batches run as plain launches instead of a CUDA graph.  ms/launches/calls: [n] accumulated device
  * time, kernels launched and timed intervals per phase (any may be NULL). */
 disc_status disc_map_set_phase_timing(disc_map* map, int32_t enable);
 disc_status disc_map_phase_times(disc_map* map, double* ms, int64_t* launches, int64_t* calls, int32_t n);

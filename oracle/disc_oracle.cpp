@@ -53,9 +53,12 @@ float cosine_exact(const float* a, const float* b, int D)
     return (float)(unfix(dot, S_SQ) / (std::sqrt(unfix(na, S_SQ)) * std::sqrt(unfix(nb, S_SQ))));
 }
 
+// Voxel of a world point: floor(p * (1/s)) per axis, the reciprocal rounded
+// once to fp32.
 bool key_of(float px, float py, float pz, float s, uint64_t* key)
 {
-    float k[3] = {std::floor(px / s), std::floor(py / s), std::floor(pz / s)};
+    const float is = 1.0f / s;
+    float k[3] = {std::floor(px * is), std::floor(py * is), std::floor(pz * is)};
     uint64_t out = 0;
     for (int a = 0; a < 3; a++) {
         if (!(k[a] >= -(float)KEY_BIAS && k[a] <= (float)(KEY_BIAS - 1))) return false;
@@ -79,12 +82,14 @@ struct Pose {
 };
 
 // Pinhole back-projection of pixel (u, v) at depth z, then camera -> world
-// (Sec. III-A: "projected into a 3D point cloud").  Pixel centres at +0.5.
+// (Sec. III-A: "projected into a 3D point cloud").  Pixel centres at +0.5;
+// the focal lengths enter as reciprocals rounded once to fp32.
 void world_point(const Pose& T, float fx, float fy, float cx, float cy, int u, int v, float z,
                  float p[3])
 {
-    float xc = ((((float)u + 0.5f) - cx) * z) / fx;
-    float yc = ((((float)v + 0.5f) - cy) * z) / fy;
+    const float ifx = 1.0f / fx, ify = 1.0f / fy;
+    float xc = ((((float)u + 0.5f) - cx) * z) * ifx;
+    float yc = ((((float)v + 0.5f) - cy) * z) * ify;
     float zc = z;
     for (int r = 0; r < 3; r++) p[r] = ((T.R[r][0] * xc + T.R[r][1] * yc) + T.R[r][2] * zc) + T.t[r];
 }
@@ -306,7 +311,8 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
                 float l2 = (n[0] * n[0] + n[1] * n[1]) + n[2] * n[2];
                 if (l2 > 0.0f) {
                     float l = std::sqrt(l2);
-                    for (int r = 0; r < 3; r++) n[r] = n[r] / l;
+                    const float il = 1.0f / l;
+                    for (int r = 0; r < 3; r++) n[r] = n[r] * il;
                     // orient toward the camera
                     float vd = ((p0[0] - T.t[0]) * n[0] + (p0[1] - T.t[1]) * n[1]) + (p0[2] - T.t[2]) * n[2];
                     if (vd > 0.0f)

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "disc_common.cuh"
@@ -16,7 +17,6 @@ using namespace disc;
 
 namespace {
 
-constexpr int SLOT_FACTOR = 2;   // per-frame hashes: slots >= 2 x pixels
 constexpr int PAIR_CAP = 8192;   // distinct (segment, instance) overlaps per frame (k_serial.cu)
 
 struct DevAlloc {
@@ -63,6 +63,11 @@ uint64_t next_pow2(uint64_t x)
 
 }  // namespace
 
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+};
+
 struct disc_map {
     disc_map_config cfg;
     cudaStream_t stream = nullptr;
@@ -72,6 +77,11 @@ struct disc_map {
     Instances inst{};
     int* d_next_id = nullptr;
     int* d_flag = nullptr;
+    int* d_prev_err = nullptr;            // status of the frame before the running batch
+    bool graphs_off = false;              // capture failed once: launch directly
+    std::map<int, BatchGraph> graphs;     // captured batch sequences
+    const void* graph_vt_keys = nullptr;
+    const void* graph_inst_parent = nullptr;
     BatchScratch bs{};
     SerialScratch ss{};
     FrameParams* d_fps = nullptr;         // [Bmax] parameters of the batch's frames
@@ -310,6 +320,86 @@ disc_status check_frame(const disc_map* m, const disc_frame* f)
     return DISC_OK;
 }
 
+// Every kernel of one batch of B frame slots, in order.  Grids follow the
+// map's maxima (frames smaller than that return early in their blocks), and
+// per-frame values are read on the device, so the sequence is the same for
+// every batch of B frames and can be replayed as a CUDA graph.
+int enqueue_batch_kernels(disc_map* m, int B, bool any_bf16, bool any_f32)
+{
+    const int D = m->D, P = m->P, Mmax = m->cfg.max_masks;
+    const int Hmax = m->cfg.max_height, Wmax = m->cfg.max_width;
+    cudaStream_t st = m->stream;
+    const BatchScratch& bs = m->bs;
+    const FrameParams* dfp = m->d_fps;
+    const int64_t before = m->launches;
+    run_phase(m, PH_CLEAR, [&] { return launch_slot_clear(bs, B, D, m->MM, st); });
+    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, B, P, D, any_bf16, any_f32, st); });
+    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, B, m->cfg.patch_h, m->cfg.patch_w, Mmax, st); });
+    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, B, Mmax, st); });
+    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, B, P, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, B, D, Mmax, any_bf16, any_f32, st); });
+    if (Mmax > 0) {
+        for (int f0 = 0; f0 < B; f0 += GEOMETRY_CHUNK) {
+            const int nb = std::min(GEOMETRY_CHUNK, B - f0);
+            run_phase(m, PH_BACKPROJECT, [&] { return launch_backproject(dfp, bs, f0, nb, Hmax, Wmax, st); });
+            run_phase(m, PH_ENTRIES, [&] { return launch_entries(dfp, bs, m->vt, f0, nb, Mmax, st); });
+        }
+        run_phase(m, PH_ENTRIES, [&] { return launch_quality(dfp, bs, B, st); });
+    }
+    // error bound of the tensor-core pooled embedding relative to
+    // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
+    // 3 K products; and of a warp-level fp32 cosine
+    const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * m->Kpad * std::ldexp(1.0, -24));
+    const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
+    SerialScratch ss = m->ss;
+    ss.prev_err = m->d_prev_err;
+    for (int j = 0; j < B; j++)
+        for (int ph = 0; ph < 4; ph++)
+            run_phase(m, PH_OVERLAP + ph, [&] {
+                return launch_serial_frame(dfp, bs, j, ss, m->vt, m->inst, m->d_next_id, eta, dot_err, ph, st);
+            });
+    return (int)(m->launches - before);
+}
+
+// The batch's kernel sequence captured once per (B, token dtypes) and
+// replayed; tables that move (growth) invalidate the cache.
+disc_status batch_graph(disc_map* m, int B, bool any_bf16, bool any_f32, BatchGraph** out)
+{
+    const int key = B * 4 + (any_bf16 ? 2 : 0) + (any_f32 ? 1 : 0);
+    if (m->graph_vt_keys != m->vt.keys || m->graph_inst_parent != m->inst.parent) {
+        for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+        m->graphs.clear();
+        m->graph_vt_keys = m->vt.keys;
+        m->graph_inst_parent = m->inst.parent;
+    }
+    auto it = m->graphs.find(key);
+    if (it != m->graphs.end()) {
+        *out = &it->second;
+        return DISC_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = m->launches;
+    const int n = enqueue_batch_kernels(m, B, any_bf16, any_f32);
+    m->launches = before;  // counted when the graph is launched
+    cudaError_t e = cudaStreamEndCapture(m->stream, &graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return DISC_ERR_CUDA;
+    }
+    BatchGraph g;
+    g.kernels = n;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DISC_ERR_CUDA;
+    }
+    *out = &(m->graphs[key] = g);
+    return DISC_OK;
+}
+
 // Enqueue frames[0..B) (B <= Bmax, all valid) as one batch; counters of frame
 // j are copied to hist[j].  prev: counters of the frame before this batch in
 // the same call (an error there stops this batch), or NULL.
@@ -319,14 +409,10 @@ disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCou
     const int D = m->D, P = m->P;
     uint64_t px = 0;
     int64_t masks = 0;
-    int Hmax = 0, Wmax = 0, Mmax = 0;
     bool any_bf16 = false, any_f32 = false;
     for (int j = 0; j < B; j++) {
         px += (uint64_t)frames[j].width * frames[j].height;
         masks += frames[j].num_masks;
-        Hmax = std::max(Hmax, frames[j].height);
-        Wmax = std::max(Wmax, frames[j].width);
-        Mmax = std::max(Mmax, frames[j].num_masks);
         any_bf16 |= frames[j].token_dtype == DISC_TOKENS_BF16;
         any_f32 |= frames[j].token_dtype == DISC_TOKENS_F32;
     }
@@ -357,6 +443,10 @@ disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCou
             fp.t[r] = (float)f->T_world_cam[4 * r + 3];
         }
         fp.voxel = m->cfg.voxel_size;
+        // reciprocals rounded once to fp32 (host fp32 division is IEEE)
+        fp.inv_fx = 1.0f / f->fx;
+        fp.inv_fy = 1.0f / f->fy;
+        fp.inv_voxel = 1.0f / m->cfg.voxel_size;
         fp.z_min = m->cfg.z_min;
         fp.z_max = m->cfg.z_max;
         fp.eps = m->cfg.eps;
@@ -393,37 +483,24 @@ disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCou
     }
     // pageable source: the call returns once the parameters are staged
     CK(cudaMemcpyAsync(m->d_fps, fps.data(), sizeof(FrameParams) * B, cudaMemcpyHostToDevice, m->stream));
+    // status of the frame before this batch (0 when it is the first of the call)
+    if (prev) CK(cudaMemcpyAsync(m->d_prev_err, &prev->err, sizeof(int), cudaMemcpyDeviceToDevice, m->stream));
+    else CK(cudaMemsetAsync(m->d_prev_err, 0, sizeof(int), m->stream));
 
-    cudaStream_t st = m->stream;
-    const BatchScratch& bs = m->bs;
-    const FrameParams* dfp = m->d_fps;
-    run_phase(m, PH_CLEAR, [&] { return launch_slot_clear(bs, B, D, m->MM, st); });
-    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, B, P, D, any_bf16, any_f32, st); });
-    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, B, m->cfg.patch_h, m->cfg.patch_w, Mmax, st); });
-    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, B, Mmax, st); });
-    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, B, P, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, B, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(m, PH_BACKPROJECT, [&] { return Mmax > 0 ? launch_backproject(dfp, bs, B, Hmax, Wmax, st) : 0; });
-    run_phase(m, PH_ENTRIES, [&] { return launch_entries(dfp, bs, m->vt, B, Mmax, st); });
-
-    // error bound of the tensor-core pooled embedding relative to
-    // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
-    // 3 K products; and of a warp-level fp32 cosine
-    const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * m->Kpad * std::ldexp(1.0, -24));
-    const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
-    SerialScratch ss = m->ss;
-    ss.prev = prev;
-    for (int j = 0; j < B; j++) {
-        if (fps[j].M > 0) {
-            run_phase(m, PH_OVERLAP, [&] { return launch_overlap(bs, j, ss, m->vt, m->inst, st); });
-            run_phase(m, PH_SCORE, [&] { return launch_score(fps[j], bs, j, ss, m->inst, eta, dot_err, st); });
-            run_phase(m, PH_UNION, [&] { return launch_union(fps[j], bs, j, ss, m->inst, m->d_next_id, st); });
-            run_phase(m, PH_APPLY,
-                      [&] { return launch_apply(fps[j], bs, j, ss, m->vt, m->inst, m->d_next_id, st); });
-        }
-        ss.prev = nullptr;
-        CK(cudaMemcpyAsync(hist + j, bs.frame(j).ctr, sizeof(FrameCounters), cudaMemcpyDeviceToDevice, st));
+    BatchGraph* g = nullptr;
+    if (!m->timing && !m->graphs_off && batch_graph(m, B, any_bf16, any_f32, &g) != DISC_OK) {
+        m->graphs_off = true;  // this stream or driver cannot capture the sequence
+        g = nullptr;
     }
+    if (g) {
+        CK(cudaGraphLaunch(g->exec, m->stream));
+        m->launches += g->kernels;
+    } else {
+        // per-phase events need plain launches
+        enqueue_batch_kernels(m, B, any_bf16, any_f32);
+    }
+    // the batch's counters, in slot order, to the call's history
+    CK(cudaMemcpyAsync(hist, m->bs.base.ctr, sizeof(FrameCounters) * B, cudaMemcpyDeviceToDevice, m->stream));
     CK(cudaGetLastError());
     m->used_upper += px;
     m->next_id_upper += masks;
@@ -582,12 +659,13 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     }
     const int D = m->D, P = m->P, MM = m->MM, B = m->Bmax;
     const uint64_t npx = (uint64_t)cfg->max_width * cfg->max_height;
-    const uint64_t scap = next_pow2(SLOT_FACTOR * npx);
+    const uint64_t scap = next_pow2(npx + npx / 2);  // per-frame hashes: load <= 2/3
     m->px_cap = npx;
     DevAlloc& a = m->mem;
     m->vt.used = a.get<unsigned long long>(1);
     m->d_next_id = a.get<int>(1);
     m->d_flag = a.get<int>(1);
+    m->d_prev_err = a.get<int>(1);
     m->d_fps = a.get<FrameParams>(B);
     BatchScratch& bs = m->bs;
     bs.sD = D;
@@ -643,7 +721,7 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     ss.copy_dst = a.get<int32_t>(ss.copy_cap);
     ss.copy_src = a.get<int32_t>(ss.copy_cap);
     ss.copy_n = a.get<int32_t>(1);
-    ss.prev = nullptr;
+    ss.prev_err = nullptr;
     m->d_depth = a.get<float>((size_t)B * npx);
     m->d_labels = a.get<uint16_t>((size_t)B * npx);
     m->d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
@@ -691,6 +769,7 @@ void disc_map_destroy(disc_map* m)
     cudaSetDevice(m->cfg.device);
     cudaStreamSynchronize(m->stream);
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
     m->mem.free_all();
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -1021,9 +1100,9 @@ disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int
 
 const char* disc_phase_name(int32_t i)
 {
-    static const char* names[PH_COUNT] = {"clear",    "token_stats", "coverage", "weights", "pool_exact",
+    static const char* names[PH_COUNT] = {"clear",     "token_stats", "coverage", "weights", "pool_exact",
                                           "pool_gemm", "backproject", "entries",  "overlap", "score",
-                                          "union",    "apply"};
+                                          "union",     "apply"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : "";
 }
 

@@ -53,12 +53,12 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-// floor(p / s) per axis, packed as three biased 18-bit fields; false when a
-// coordinate is out of range.
-__device__ __forceinline__ bool voxel_key(float px, float py, float pz, float s,
+// floor(p * inv_s) per axis (inv_s = 1/s rounded once to fp32), packed as
+// three biased 18-bit fields; false when a coordinate is out of range.
+__device__ __forceinline__ bool voxel_key(float px, float py, float pz, float inv_s,
                                           unsigned long long* key)
 {
-    float k[3] = {floorf(__fdiv_rn(px, s)), floorf(__fdiv_rn(py, s)), floorf(__fdiv_rn(pz, s))};
+    float k[3] = {floorf(__fmul_rn(px, inv_s)), floorf(__fmul_rn(py, inv_s)), floorf(__fmul_rn(pz, inv_s))};
     unsigned long long out = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -220,7 +220,7 @@ struct SerialScratch {
     int32_t* copy_src;          // >= 0 instance id, < 0: segment -(m+1)
     int32_t* copy_n;            // [1]
     int32_t copy_cap;
-    const FrameCounters* prev;  // counters of the frame before slot 0 in this call, or NULL
+    const int* prev_err;        // status of the frame before slot 0 in this call (0 for the first)
 };
 
 // frame parameters passed by value
@@ -230,6 +230,7 @@ struct FrameParams {
     float R[9];
     float t[3];
     float voxel, z_min, z_max, eps, tau, lambda_size;
+    float inv_fx, inv_fy, inv_voxel;   // 1/fx, 1/fy, 1/voxel rounded once to fp32
     int32_t ov_num, ov_den, min_px;
     int32_t token_bf16;
     const float* depth;

@@ -7,6 +7,7 @@
 //               the batch (voxels absent then are re-probed by the serial
 //               overlap kernel, which sees the inserts of earlier frames)
 //   Eq. 2       Q = S_size * S_angle * S_sem * S_dist per segment
+#include <algorithm>
 #include <climits>
 
 #include "disc_common.cuh"
@@ -49,8 +50,8 @@ __global__ void k_slot_reset(BatchScratch bs, int B)
 // ---- Sec. III-A: world point of pixel (u, v) at depth z -------------------------
 __device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v, float z, float p[3])
 {
-    float xc = __fdiv_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fp.cx), z), fp.fx);
-    float yc = __fdiv_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), fp.cy), z), fp.fy);
+    float xc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fp.cx), z), fp.inv_fx);
+    float yc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), fp.cy), z), fp.inv_fy);
 #pragma unroll
     for (int r = 0; r < 3; r++)
         p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(fp.R[3 * r], xc), __fmul_rn(fp.R[3 * r + 1], yc)),
@@ -58,69 +59,88 @@ __device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v,
                          fp.t[r]);
 }
 
-__device__ __forceinline__ bool pix_valid(const FrameParams& fp, int u, int v, int lab)
-{
-    if (u < 0 || v < 0 || u >= fp.W || v >= fp.H) return false;
-    size_t i = (size_t)v * fp.W + u;
-    if (fp.labels[i] != lab) return false;
-    float z = fp.depth[i];
-    return z >= fp.z_min && z <= fp.z_max;
-}
 
 // ---- back-projection + per-segment voxel dedupe (one thread per pixel) ----------
-// Block (32, 8): a warp is 32 consecutive pixels of one row; pixel counters are
-// aggregated with ballots before one atomic per warp.
-__global__ void k_backproject(const FrameParams* fps, BatchScratch bs)
+// A block covers a 32 x 16 pixel tile.  The tile and a one-pixel halo are
+// loaded once into shared memory together with each position's world point,
+// so neighbours' points (for the pixel normal) are read, not recomputed.
+// The tile's pixels then meet in a shared hash keyed by (mask, voxel) that
+// sums their normals exactly; only the tile's distinct keys update the frame
+// slot's global hash.
+constexpr int BP_TX = 32, BP_TY = 16, BP_THREADS = BP_TX * BP_TY;
+constexpr int BP_HX = BP_TX + 2, BP_HY = BP_TY + 2, BP_HALO = BP_HX * BP_HY;
+constexpr int BP_SLOTS = 2 * BP_THREADS;
+
+struct __align__(16) TilePoint {
+    float p[3];
+    int lab;   // mask label if the pixel has valid depth (and is inside the image), else 0
+};
+
+__global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* fps, BatchScratch bs, int f0)
 {
-    const FrameParams& fp = fps[blockIdx.z];
-    const Scratch sc = bs.frame(blockIdx.z);
+    __shared__ TilePoint tp[BP_HALO];
+    __shared__ unsigned long long tkey[BP_SLOTS];
+    __shared__ int tn[6][BP_SLOTS];  // per component: sum of (v >> 16) and of (v & 0xffff)
+    __shared__ int tcount[2];
+    const FrameParams& fp = fps[f0 + blockIdx.z];
+    const Scratch sc = bs.frame(f0 + blockIdx.z);
     if (fp.M <= 0) return;  // uniform per block
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool inside = u < fp.W && v < fp.H;
-    int lab = 0;
-    float z = 0.0f;
-    bool active = inside && !sc.ctr->err;
-    if (active) {
-        const size_t idx = (size_t)v * fp.W + u;
-        lab = fp.labels[idx];
-        active = lab >= 1 && lab <= fp.M && sc.npix[lab - 1] >= fp.min_px;
-        if (active) {
-            z = fp.depth[idx];
-            active = z >= fp.z_min && z <= fp.z_max;
+    const int tid = threadIdx.y * BP_TX + threadIdx.x;
+    const int u0 = blockIdx.x * BP_TX - 1, v0 = blockIdx.y * BP_TY - 1;  // halo origin
+    const bool ok_frame = !sc.ctr->err;
+    // tile + halo: label (0 unless the depth is valid) and world point
+    for (int i = tid; i < BP_HALO; i += BP_THREADS) {
+        const int hu = u0 + i % BP_HX, hv = v0 + i / BP_HX;
+        TilePoint t;
+        t.lab = 0;
+        t.p[0] = t.p[1] = t.p[2] = 0.0f;
+        if (ok_frame && hu >= 0 && hv >= 0 && hu < fp.W && hv < fp.H) {
+            const size_t idx = (size_t)hv * fp.W + hu;
+            const int lab = fp.labels[idx];
+            const float z = fp.depth[idx];
+            if (lab >= 1 && lab <= fp.M && z >= fp.z_min && z <= fp.z_max) {
+                t.lab = lab;
+                world_point(fp, hu, hv, z, t.p);
+            }
         }
+        tp[i] = t;
     }
-    float p0[3] = {0.0f, 0.0f, 0.0f};
+    for (int i = tid; i < BP_SLOTS; i += BP_THREADS) {
+        tkey[i] = 0ull;
+#pragma unroll
+        for (int r = 0; r < 6; r++) tn[r][i] = 0;
+    }
+    if (tid < 2) tcount[tid] = 0;
+    __syncthreads();
+    const int hx = threadIdx.x + 1, hy = threadIdx.y + 1;  // own position in the halo tile
+    const TilePoint me = tp[hy * BP_HX + hx];
+    const int lab = me.lab;
+    const bool active = lab > 0 && sc.npix[lab - 1] >= fp.min_px;
     unsigned long long key = 0;
     bool keyed = false;
-    if (active) {
-        world_point(fp, u, v, z, p0);
-        keyed = voxel_key(p0[0], p0[1], p0[2], fp.voxel, &key);
-    }
-    const unsigned wmask = __activemask();
-    const unsigned nvalid = __popc(__ballot_sync(wmask, keyed));
-    const unsigned ndrop = __popc(__ballot_sync(wmask, active && !keyed));
+    if (active) keyed = voxel_key(me.p[0], me.p[1], me.p[2], fp.inv_voxel, &key);
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(wmask) - 1;
-    if (lane == leader) {
-        if (nvalid) atomicAdd(&sc.ctr->valid_pixels, (int)nvalid);
-        if (ndrop) atomicAdd(&sc.ctr->dropped_pixels, (int)ndrop);
+    const unsigned nvalid = __popc(__ballot_sync(0xffffffffu, keyed));
+    const unsigned ndrop = __popc(__ballot_sync(0xffffffffu, active && !keyed));
+    if (lane == 0) {
+        if (nvalid) atomicAdd(&tcount[0], (int)nvalid);
+        if (ndrop) atomicAdd(&tcount[1], (int)ndrop);
     }
     // pixel normal (zero when it has none)
     long long nfix[3] = {0, 0, 0};
     if (keyed) {
-        // image-space tangents: forward differences, backward at the mask's edge
-        int ua = -1, ub = -1, va = -1, vb = -1;
-        if (pix_valid(fp, u + 1, v, lab)) { ua = u + 1; ub = u; }
-        else if (pix_valid(fp, u - 1, v, lab)) { ua = u; ub = u - 1; }
-        if (pix_valid(fp, u, v + 1, lab)) { va = v + 1; vb = v; }
-        else if (pix_valid(fp, u, v - 1, lab)) { va = v; vb = v - 1; }
-        if (ua >= 0 && va >= 0) {
-            float pa[3], pb[3], qa[3], qb[3];
-            world_point(fp, ua, v, fp.depth[(size_t)v * fp.W + ua], pa);
-            world_point(fp, ub, v, fp.depth[(size_t)v * fp.W + ub], pb);
-            world_point(fp, u, va, fp.depth[(size_t)va * fp.W + u], qa);
-            world_point(fp, u, vb, fp.depth[(size_t)vb * fp.W + u], qb);
+        // image-space tangents: forward differences, backward at the mask's
+        // edge; a neighbour counts if it has valid depth and the same label
+        const TilePoint& R = tp[hy * BP_HX + hx + 1];
+        const TilePoint& L = tp[hy * BP_HX + hx - 1];
+        const TilePoint& Dn = tp[(hy + 1) * BP_HX + hx];
+        const TilePoint& Up = tp[(hy - 1) * BP_HX + hx];
+        const float *pa = nullptr, *pb = nullptr, *qa = nullptr, *qb = nullptr;
+        if (R.lab == lab) { pa = R.p; pb = me.p; }
+        else if (L.lab == lab) { pa = me.p; pb = L.p; }
+        if (Dn.lab == lab) { qa = Dn.p; qb = me.p; }
+        else if (Up.lab == lab) { qa = me.p; qb = Up.p; }
+        if (pa && qa) {
             float e1[3], e2[3], n[3];
 #pragma unroll
             for (int r = 0; r < 3; r++) {
@@ -132,13 +152,13 @@ __global__ void k_backproject(const FrameParams* fps, BatchScratch bs)
             n[2] = __fsub_rn(__fmul_rn(e2[0], e1[1]), __fmul_rn(e2[1], e1[0]));
             float l2 = __fadd_rn(__fadd_rn(__fmul_rn(n[0], n[0]), __fmul_rn(n[1], n[1])), __fmul_rn(n[2], n[2]));
             if (l2 > 0.0f) {
-                float l = __fsqrt_rn(l2);
+                const float il = __fdiv_rn(1.0f, __fsqrt_rn(l2));
 #pragma unroll
-                for (int r = 0; r < 3; r++) n[r] = __fdiv_rn(n[r], l);
+                for (int r = 0; r < 3; r++) n[r] = __fmul_rn(n[r], il);
                 // orient toward the camera
-                float vd = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(p0[0], fp.t[0]), n[0]),
-                                               __fmul_rn(__fsub_rn(p0[1], fp.t[1]), n[1])),
-                                     __fmul_rn(__fsub_rn(p0[2], fp.t[2]), n[2]));
+                float vd = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(me.p[0], fp.t[0]), n[0]),
+                                               __fmul_rn(__fsub_rn(me.p[1], fp.t[1]), n[1])),
+                                     __fmul_rn(__fsub_rn(me.p[2], fp.t[2]), n[2]));
                 if (vd > 0.0f) {
 #pragma unroll
                     for (int r = 0; r < 3; r++) n[r] = -n[r];
@@ -148,33 +168,52 @@ __global__ void k_backproject(const FrameParams* fps, BatchScratch bs)
             }
         }
     }
-
-    // Runs of consecutive lanes with the same (mask, voxel) key: a segmented
-    // inclusive scan gives the last lane of each run the run's exact normal
-    // sums; that lane alone updates the hash.  A key that reappears later in
-    // the warp forms a second run (a second, still exact, update).
+    // Pixels of one warp with the same (mask, voxel) key are summed first:
+    // each 2^-32 fixed-point component v (|v| <= 2^32) splits exactly into
+    // v = (v >> 16) * 2^16 + (v & 0xffff), whose parts add in 32-bit integers
+    // for up to a whole tile.  One lane per key then updates the tile hash.
     const unsigned long long hk = keyed ? (((unsigned long long)lab << 54) | key) : 0ull;
-    const unsigned long long hk_prev = __shfl_up_sync(wmask, hk, 1);
-    const unsigned long long hk_next = __shfl_down_sync(wmask, hk, 1);
-    const bool head = lane == 0 || hk_prev != hk;
-    const bool tail = lane == 31 || hk_next != hk;
-    const unsigned heads = __ballot_sync(wmask, head);
-    const int run_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const unsigned grp = __match_any_sync(0xffffffffu, hk);
+    unsigned part[6];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        long long o0 = __shfl_up_sync(wmask, nfix[0], d);
-        long long o1 = __shfl_up_sync(wmask, nfix[1], d);
-        long long o2 = __shfl_up_sync(wmask, nfix[2], d);
-        if (lane - d >= run_start) {
-            nfix[0] += o0;
-            nfix[1] += o1;
-            nfix[2] += o2;
-        }
+    for (int r = 0; r < 3; r++) {
+        part[2 * r] = (unsigned)(int)(nfix[r] >> 16);
+        part[2 * r + 1] = (unsigned)(nfix[r] & 0xffff);
     }
+#pragma unroll
+    for (int r = 0; r < 6; r++) part[r] = __reduce_add_sync(grp, part[r]);
+    if (keyed && lane == __ffs(grp) - 1) {
+        // tile-level dedupe: at most BP_THREADS distinct keys in BP_SLOTS slots
+        unsigned t = (unsigned)(mix64(hk) & (BP_SLOTS - 1));
+        while (true) {
+            const unsigned long long prev = atomicCAS(&tkey[t], 0ull, hk);
+            if (prev == 0ull || prev == hk) break;
+            t = (t + 1) & (BP_SLOTS - 1);
+        }
+#pragma unroll
+        for (int r = 0; r < 6; r++)
+            if (part[r]) atomicAdd((unsigned*)&tn[r][t], part[r]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (tcount[0]) atomicAdd(&sc.ctr->valid_pixels, tcount[0]);
+        if (tcount[1]) atomicAdd(&sc.ctr->dropped_pixels, tcount[1]);
+    }
+    // the tile's distinct keys update the frame slot's hash; the keys this
+    // block claims first are appended to the entry list with one reservation
+    // per block (a single shared counter would serialise every claim)
+    constexpr int PER_THREAD = BP_SLOTS / BP_THREADS;
     int probes = 0;
-    if (keyed && tail) {
-        // insert (mask, voxel) into the slot's hash; the winner of an empty
-        // slot appends it to the entry list
+    int claimed_slot[PER_THREAD];
+    unsigned long long claimed_key[PER_THREAD];
+    int nclaim = 0;
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; j++) {
+        const int i = tid + j * BP_THREADS;
+        const unsigned long long hk = tkey[i];
+        claimed_slot[j] = -1;
+        claimed_key[j] = hk;
+        if (hk == 0ull) continue;
         unsigned long long s = mix64(hk) & sc.smask;
         bool ok = true;
         while (true) {
@@ -183,9 +222,8 @@ __global__ void k_backproject(const FrameParams* fps, BatchScratch bs)
             if (cur == 0ull) {
                 const unsigned long long prev = atomicCAS(&sc.sslot[s].key, 0ull, hk);
                 if (prev == 0ull) {
-                    const int at = atomicAdd(&sc.ctr->n_entries, 1);
-                    sc.slist[at] = (int)s;
-                    sc.sent[at] = hk;
+                    claimed_slot[j] = (int)s;
+                    nclaim++;
                     break;
                 }
                 if (prev == hk) break;
@@ -199,23 +237,55 @@ __global__ void k_backproject(const FrameParams* fps, BatchScratch bs)
         }
         if (ok) {
             SegSlot& slot = sc.sslot[s];
-            if (nfix[0]) atomicAdd((unsigned long long*)&slot.n[0], (unsigned long long)nfix[0]);
-            if (nfix[1]) atomicAdd((unsigned long long*)&slot.n[1], (unsigned long long)nfix[1]);
-            if (nfix[2]) atomicAdd((unsigned long long*)&slot.n[2], (unsigned long long)nfix[2]);
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                const long long v = (long long)tn[2 * r][i] * 65536 + (long long)(unsigned)tn[2 * r + 1][i];
+                if (v) atomicAdd((unsigned long long*)&slot.n[r], (unsigned long long)v);
+            }
         }
     }
-    const int pmax = __reduce_max_sync(wmask, probes);
-    if (lane == leader && pmax > 0) atomicMax(&sc.ctr->max_probe, pmax);
+    // block-wide exclusive scan of the claim counts
+    __shared__ int wsum[BP_THREADS / 32];
+    __shared__ int s_base;
+    int incl = nclaim;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    const int warp = tid >> 5;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < BP_THREADS / 32; w++) {
+            const int c = wsum[w];
+            wsum[w] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(&sc.ctr->n_entries, tot) : 0;
+    }
+    __syncthreads();
+    int at = s_base + wsum[warp] + incl - nclaim;
+#pragma unroll
+    for (int j = 0; j < PER_THREAD; j++) {
+        if (claimed_slot[j] < 0) continue;
+        sc.slist[at] = claimed_slot[j];
+        sc.sent[at] = claimed_key[j];
+        at++;
+    }
+    const int pmax = __reduce_max_sync(0xffffffffu, probes);
+    if (lane == 0 && pmax > 0) atomicMax(&sc.ctr->max_probe, pmax);
 }
 
 // ---- per unique (segment, voxel): Eq. 3 term, |V_m|, label at batch start ------
 // Per-segment sums gather in shared memory first (one global atomic per
 // block and segment).
-__global__ void k_entries(const FrameParams* fps, BatchScratch bs, VoxelTable vt)
+__global__ void k_entries(const FrameParams* fps, BatchScratch bs, VoxelTable vt, int f0)
 {
     extern __shared__ unsigned char ent_smem[];
-    const FrameParams& fp = fps[blockIdx.y];
-    const Scratch sc = bs.frame(blockIdx.y);
+    const FrameParams& fp = fps[f0 + blockIdx.y];
+    const Scratch sc = bs.frame(f0 + blockIdx.y);
     long long* s_ang = (long long*)ent_smem;         // [M]
     int* s_nv = (int*)(s_ang + max(fp.M, 1));         // [M]
     for (int m = threadIdx.x; m < fp.M; m += blockDim.x) {
@@ -309,20 +379,26 @@ int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t
     return 2;
 }
 
-int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int B, int H, int W, cudaStream_t st)
+// launch on frames [f0, f0 + nb) of the batch
+int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st)
 {
-    dim3 b(32, 8), g((W + 31) / 32, (H + 7) / 8, B);
-    k_backproject<<<g, b, 0, st>>>(fps, bs);
+    dim3 b(BP_TX, BP_TY), g((W + BP_TX - 1) / BP_TX, (H + BP_TY - 1) / BP_TY, nb);
+    k_backproject<<<g, b, 0, st>>>(fps, bs, f0);
     return 1;
 }
 
-int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int B, int Mmax,
+int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int f0, int nb, int Mmax,
                    cudaStream_t st)
 {
     const size_t smem = 12 * (size_t)std::max(Mmax, 1) + 16;
-    k_entries<<<dim3(152 * 2, B), 256, smem, st>>>(fps, bs, vt);
+    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, vt, f0);
+    return 1;
+}
+
+int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st)
+{
     k_quality<<<B, 256, 0, st>>>(fps, bs);
-    return 2;
+    return 1;
 }
 
 }  // namespace disc

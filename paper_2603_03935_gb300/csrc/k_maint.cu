@@ -91,7 +91,7 @@ __global__ void k_query_points(const float* xyz, long long n, float voxel, Voxel
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         unsigned long long key;
         int out = -1;
-        if (voxel_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], voxel, &key)) {
+        if (voxel_key(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], __fdiv_rn(1.0f, voxel), &key)) {
             unsigned long long h = mix64(key) & vt.mask;
             for (unsigned long long pr = 0; pr <= vt.mask; pr++) {
                 unsigned long long kk = vt.keys[h];

@@ -1,5 +1,6 @@
 // The stateful part of the integration step, run frame after frame in order
-// (each frame sees the map its predecessors left):
+// (each frame sees the map its predecessors left).  Per frame, four kernels
+// (captured with the rest of the batch in one CUDA graph):
 //   k_overlap  Sec. III-B  exact overlap histogram ov[m][k] of every segment
 //                          with the instances of the map before this frame
 //   k_score    Sec. III-B  geometry gate (overlap coefficient) and cosine gate
@@ -7,8 +8,10 @@
 //                          score, exact re-score inside its error band
 //   k_union    Sec. III-B  union of segments and instances (representative =
 //              Sec. III-C  smallest id), new ids, merges, Q-replacement fusion
+//                          (one CTA)
 //   k_apply    Sec. III-B  embedding copies, insertion of the new voxels,
 //                          flattening of the parent table, cleanup
+#include <algorithm>
 #include <climits>
 
 #include "disc_common.cuh"
@@ -19,11 +22,11 @@ namespace disc {
 __device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(&c->err, 0, code); }
 
 // an error of the previous frame of the same call stops this one
-__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, int f, const FrameCounters* prev)
+__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, int f, const int* prev_err)
 {
     const Scratch sc = bs.frame(f);
     if (sc.ctr->err) return true;
-    const int pe = f > 0 ? bs.frame(f - 1).ctr->err : (prev ? prev->err : 0);
+    const int pe = f > 0 ? bs.frame(f - 1).ctr->err : *prev_err;
     if (pe) {
         set_err(sc.ctr, pe);
         return true;
@@ -32,22 +35,33 @@ __device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, int f, con
 }
 
 // ---- overlap histogram -----------------------------------------------------------
-__global__ void k_overlap(BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst)
+// Each block takes 256 entries at a time.  Their (segment, root) pairs are
+// counted in a shared-memory hash first; only the block's distinct pairs
+// then update the frame's global histogram.  Voxels absent from the map go
+// to the new-voxel hash with the lowest segment that contains them.
+constexpr int SER_THREADS = 1024;
+constexpr int OV_SLOTS = 2 * SER_THREADS;
+
+__device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
+                              unsigned char* smem)
 {
-    const Scratch sc = bs.frame(f);
-    if (frame_blocked(bs, f, ss.prev)) return;
+    unsigned long long* pkey = (unsigned long long*)smem;   // [OV_SLOTS]
+    int* pcnt = (int*)(pkey + OV_SLOTS);                    // [OV_SLOTS]
+    constexpr int OV_THREADS = SER_THREADS;
     const int ne = sc.ctr->n_entries;
+    for (int i = threadIdx.x; i < OV_SLOTS; i += OV_THREADS) {
+        pkey[i] = EMPTY_KEY;
+        pcnt[i] = 0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    for (int i0 = blockIdx.x * blockDim.x; i0 < ne; i0 += gridDim.x * blockDim.x) {
+    for (int i0 = blockIdx.x * OV_THREADS; i0 < ne; i0 += gridDim.x * OV_THREADS) {
         const int i = i0 + threadIdx.x;
-        const bool act = i < ne;
-        unsigned long long okey = EMPTY_KEY, key = 0;
-        int m = 0;
-        bool found = false;
-        if (act) {
+        int new_slot = -1;  // slot of the new-voxel hash this thread claimed
+        if (i < ne) {
             const unsigned long long hk = sc.sent[i];
-            m = (int)(hk >> 54);
-            key = hk & ((1ull << 54) - 1);
+            const int m = (int)(hk >> 54);
+            const unsigned long long key = hk & ((1ull << 54) - 1);
             int lab = sc.elab[i];
             if (lab < 0) {
                 // absent when the batch started: an earlier frame may have added it
@@ -60,44 +74,68 @@ __global__ void k_overlap(BatchScratch bs, int f, SerialScratch ss, VoxelTable v
                 }
             }
             if (lab >= 0) {
-                found = true;
-                okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
+                const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
+                unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
+                while (true) {
+                    const unsigned long long prev = atomicCAS(&pkey[t], EMPTY_KEY, okey);
+                    if (prev == EMPTY_KEY || prev == okey) break;
+                    t = (t + 1) & (OV_SLOTS - 1);
+                }
+                atomicAdd(&pcnt[t], 1);
+            } else {
+                unsigned long long t = mix64(key) & ss.nmask;
+                for (int pr = 0;; pr++) {
+                    const unsigned long long cur = ss.nkeys[t];
+                    if (cur == key) break;
+                    if (cur == EMPTY_KEY) {
+                        const unsigned long long prev = atomicCAS(&ss.nkeys[t], EMPTY_KEY, key);
+                        if (prev == EMPTY_KEY) { new_slot = (int)t; break; }
+                        if (prev == key) break;
+                    }
+                    t = (t + 1) & ss.nmask;
+                    if (pr > (int)ss.nmask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
+                }
+                atomicMin(&ss.nown[t], m);
             }
         }
-        // one hash update per distinct (segment, root) of the warp
-        const unsigned wm = __ballot_sync(0xffffffffu, found);
-        if (found) {
-            const unsigned grp = __match_any_sync(wm, okey);
-            if (lane == __ffs(grp) - 1) {
+        // warp-aggregated append of the claimed new-voxel slots
+        {
+            const unsigned want = __ballot_sync(0xffffffffu, new_slot >= 0);
+            int base = 0;
+            if (lane == 0 && want) base = atomicAdd(&sc.ctr->n_new, __popc(want));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (new_slot >= 0) ss.nlist[base + __popc(want & ((1u << lane) - 1))] = new_slot;
+        }
+        __syncthreads();
+        // flush the block's distinct pairs, then clear them for the next pass
+        for (int j0 = 0; j0 < OV_SLOTS; j0 += OV_THREADS) {
+            const int j = j0 + threadIdx.x;
+            const unsigned long long okey = pkey[j];
+            int pair_slot = -1;
+            if (okey != EMPTY_KEY) {
                 unsigned long long t = mix64(okey) & ss.omask;
                 for (int pr = 0;; pr++) {
                     const unsigned long long cur = ss.okeys[t];
                     if (cur == okey) break;
                     if (cur == EMPTY_KEY) {
                         const unsigned long long prev = atomicCAS(&ss.okeys[t], EMPTY_KEY, okey);
-                        if (prev == EMPTY_KEY) { ss.olist[atomicAdd(&sc.ctr->n_pairs, 1)] = (int)t; break; }
+                        if (prev == EMPTY_KEY) { pair_slot = (int)t; break; }
                         if (prev == okey) break;
                     }
                     t = (t + 1) & ss.omask;
                     if (pr > (int)ss.omask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
                 }
-                atomicAdd(&ss.ocnt[t], __popc(grp));
+                atomicAdd(&ss.ocnt[t], pcnt[j]);
+                pkey[j] = EMPTY_KEY;
+                pcnt[j] = 0;
             }
-        } else if (act) {
-            unsigned long long t = mix64(key) & ss.nmask;
-            for (int pr = 0;; pr++) {
-                const unsigned long long cur = ss.nkeys[t];
-                if (cur == key) break;
-                if (cur == EMPTY_KEY) {
-                    const unsigned long long prev = atomicCAS(&ss.nkeys[t], EMPTY_KEY, key);
-                    if (prev == EMPTY_KEY) { ss.nlist[atomicAdd(&sc.ctr->n_new, 1)] = (int)t; break; }
-                    if (prev == key) break;
-                }
-                t = (t + 1) & ss.nmask;
-                if (pr > (int)ss.nmask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
-            }
-            atomicMin(&ss.nown[t], m);
+            const unsigned want = __ballot_sync(0xffffffffu, pair_slot >= 0);
+            int base = 0;
+            if (lane == 0 && want) base = atomicAdd(&sc.ctr->n_pairs, __popc(want));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (pair_slot >= 0) ss.olist[base + __popc(want & ((1u << lane) - 1))] = pair_slot;
         }
+        __syncthreads();
     }
 }
 
@@ -107,10 +145,9 @@ struct ScoreParams {
     float dot_err;  // error bound of an fp32 warp cosine
 };
 
-__global__ void k_score(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst, ScoreParams sp)
+__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
+                            const ScoreParams& sp)
 {
-    const Scratch sc = bs.frame(f);
-    if (frame_blocked(bs, f, ss.prev)) return;
     const int lane = threadIdx.x & 31;
     const int npairs = sc.ctr->n_pairs;
     const int D = fp.D;
@@ -127,14 +164,25 @@ __global__ void k_score(FrameParams fp, BatchScratch bs, int f, SerialScratch ss
         const float* a = sc.Efast + (size_t)m * D;
         const float* b = inst.E + (size_t)k * D;
         float dt = 0.0f, na = 0.0f, nb = 0.0f;
-        if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads
+        if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads, 8 in flight per lane
             const float4* a4 = (const float4*)a;
             const float4* b4 = (const float4*)b;
-            for (int d = lane; d < (D >> 2); d += 32) {
-                const float4 x = a4[d], y = b4[d];
-                dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
-                na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-                nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+            const int n4 = D >> 2;
+            for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+                float4 xs[4], ys[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int d = d0 + j * 32 + lane;
+                    xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ys[j] = d < n4 ? b4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float4 x = xs[j], y = ys[j];
+                    dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                    nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+                }
             }
         } else {
             for (int d = lane; d < D; d += 32) {
@@ -188,53 +236,85 @@ __global__ void k_score(FrameParams fp, BatchScratch bs, int f, SerialScratch ss
 // ---- union, new ids, merges, fusion (one block) ------------------------------------
 // Shared memory: a hash set of the frame's active roots (all overlap pairs)
 // that also hands out local indices to the roots that carry an edge, and
-// per-local-root arrays for the union-find and the fusion winners.
-constexpr int UNION_THREADS = 1024;
+// per-local-root arrays for the union-find and the fusion.  Every step runs
+// in parallel on shared memory except the new-id scan over the masks.
+constexpr int UNION_THREADS = SER_THREADS;
 constexpr int PAIR_CAP = 8192;             // distinct (segment, instance) overlaps per frame
-constexpr int EDGE_ROOT_CAP = 4096;        // distinct instances with an accepted edge per frame
+constexpr int EDGE_ROOT_CAP = 2048;        // distinct instances with an accepted edge per frame
+constexpr int EDGE_CAP = 4096;             // accepted (segment, instance) edges per frame
 constexpr int UHASH = 2 * PAIR_CAP;        // hash slots (load <= 1/2)
 constexpr unsigned UH_EMPTY = 0xffffffffu;
 constexpr unsigned UH_UNUSED = 0xffffffffu;
 constexpr unsigned UH_LOCAL = 0x80000000u;
-constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 16;
+constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8;
 
 __device__ __forceinline__ unsigned uhash(unsigned k) { return (unsigned)(mix64(k) & (UHASH - 1)); }
 
-__device__ int uf_find(const int* uf, int x)
+__device__ __forceinline__ int uf_find(const int* uf, int x)
 {
-    while (uf[x] != x) x = uf[x];
-    return x;
+    while (true) {
+        const int p = ((volatile const int*)uf)[x];
+        if (p == x) return x;
+        x = p;
+    }
 }
 
-__global__ void __launch_bounds__(UNION_THREADS, 1)
-k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst, int* next_id)
+__device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hval, unsigned k)
 {
-    extern __shared__ __align__(16) unsigned char union_smem[];
+    unsigned h = uhash(k);
+    while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+    return (int)(hval[h] & ~UH_LOCAL);
+}
+
+__device__ void phase_union(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
+                            int* next_id, unsigned char* union_smem)
+{
     unsigned* hkey = (unsigned*)union_smem;           // [UHASH] root id
     unsigned* hval = hkey + UHASH;                    // [UHASH] claimant edge, then UH_LOCAL | local index
     int* gid = (int*)(hval + UHASH);                  // [EDGE_ROOT_CAP] local -> instance id
     int* uf = gid + EDGE_ROOT_CAP;                    // union-find over local indices
     int* best_src = uf + EDGE_ROOT_CAP;               // fusion winner per component
     float* best_q = (float*)(best_src + EDGE_ROOT_CAP);
-    __shared__ int first[MAX_MASKS];
-    __shared__ int s_nroots, s_nloc, s_merges, s_new, s_ncopy;
+    float* qloc = best_q + EDGE_ROOT_CAP;             // Q of the local roots
+    int* oloc = (int*)(qloc + EDGE_ROOT_CAP);         // observations of the local roots
+    int* em = oloc + EDGE_ROOT_CAP;                   // [EDGE_CAP] edge segment
+    int* ek = em + EDGE_CAP;                          // [EDGE_CAP] edge instance id
+    __shared__ int anchor[MAX_MASKS];                 // smallest local root of a segment's edges
+    __shared__ int srep[MAX_MASKS];
+    __shared__ int snv[MAX_MASKS];
+    __shared__ float sq[MAX_MASKS];
+    __shared__ int s_nroots, s_nloc, s_merges, s_new, s_ncopy, s_next;
     const int tid = threadIdx.x;
-    const Scratch sc = bs.frame(f);
     FrameCounters* ctr = sc.ctr;
-    if (frame_blocked(bs, f, ss.prev)) return;
     const int M = fp.M;
     const int npairs = ctr->n_pairs;
     const int nedge = min(*ss.edge_n, ss.edge_cap);
-    if (npairs > PAIR_CAP) {
+    if (npairs > PAIR_CAP || nedge > EDGE_CAP) {
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
         return;
+    }
+    // the edges, once, into shared memory (segment, root)
+    for (int e = tid; e < nedge; e += UNION_THREADS) {
+        em[e] = ss.edge_m[e];
+        ek[e] = ss.edge_k[e];
     }
     for (int i = tid; i < UHASH; i += UNION_THREADS) {
         hkey[i] = UH_EMPTY;
         hval[i] = UH_UNUSED;
     }
-    for (int m = tid; m < MAX_MASKS; m += UNION_THREADS) first[m] = -1;
-    if (tid == 0) { s_nroots = 0; s_nloc = 0; s_merges = 0; s_new = 0; s_ncopy = 0; }
+    for (int m = tid; m < M; m += UNION_THREADS) {
+        anchor[m] = INT_MAX;
+        snv[m] = sc.nvox[m];
+        sq[m] = sc.S[5 * m + 4];
+    }
+    if (tid == 0) {
+        s_nroots = 0;
+        s_nloc = 0;
+        s_merges = 0;
+        s_new = 0;
+        s_ncopy = 0;
+        s_next = *next_id;
+    }
     __syncthreads();
     // (1) active set: distinct roots of all overlap pairs
     for (int i = tid; i < npairs; i += UNION_THREADS) {
@@ -255,14 +335,14 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
     // (2) local indices for the roots that carry an edge: the first edge to
     //     claim a root's slot assigns the index
     for (int e = tid; e < nedge; e += UNION_THREADS) {
-        const unsigned k = (unsigned)ss.edge_k[e];
+        const unsigned k = (unsigned)ek[e];
         unsigned h = uhash(k);
         while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
         atomicCAS(&hval[h], UH_UNUSED, (unsigned)e);
     }
     __syncthreads();
     for (int e = tid; e < nedge; e += UNION_THREADS) {
-        const unsigned k = (unsigned)ss.edge_k[e];
+        const unsigned k = (unsigned)ek[e];
         unsigned h = uhash(k);
         while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
         if (hval[h] == (unsigned)e) {
@@ -270,6 +350,8 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
             if (x < EDGE_ROOT_CAP) {
                 gid[x] = (int)k;
                 uf[x] = x;
+                qloc[x] = inst.Q[k];
+                oloc[x] = inst.n_obs[k];
             }
             hval[h] = UH_LOCAL | (unsigned)x;
         }
@@ -280,37 +362,38 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
         return;
     }
-    // (3) union of the instances one segment joins; the set's root is the
-    //     member with the smallest instance id
-    if (tid == 0) {
-        for (int e = 0; e < nedge; e++) {
-            const int m = ss.edge_m[e];
-            const unsigned k = (unsigned)ss.edge_k[e];
-            unsigned h = uhash(k);
-            while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
-            const int x = (int)(hval[h] & ~UH_LOCAL);
-            if (first[m] < 0) { first[m] = x; continue; }
-            const int a = uf_find(uf, first[m]), b = uf_find(uf, x);
-            if (a != b) {
-                if (gid[a] < gid[b]) uf[b] = a; else uf[a] = b;
-            }
+    // (3) union of the instances one segment joins: every edge hooks its
+    //     root onto the segment's anchor; a hook always links the root with
+    //     the larger instance id under the smaller one, so each set's root is
+    //     its smallest instance id
+    for (int e = tid; e < nedge; e += UNION_THREADS) atomicMin(&anchor[em[e]], local_of(hkey, hval, (unsigned)ek[e]));
+    __syncthreads();
+    for (int e = tid; e < nedge; e += UNION_THREADS) {
+        int x = local_of(hkey, hval, (unsigned)ek[e]);
+        int y = anchor[em[e]];
+        while (true) {
+            x = uf_find(uf, x);
+            y = uf_find(uf, y);
+            if (x == y) break;
+            const int lo = gid[x] < gid[y] ? x : y, hi = lo == x ? y : x;
+            if (atomicCAS(&uf[hi], hi, lo) == hi) break;
         }
     }
     __syncthreads();
     for (int x = tid; x < nloc; x += UNION_THREADS) uf[x] = uf_find(uf, x);  // stores only roots
     __syncthreads();
-    for (int m = tid; m < M; m += UNION_THREADS) sc.segrep[m] = first[m] >= 0 ? gid[uf[first[m]]] : -1;
+    for (int m = tid; m < M; m += UNION_THREADS) srep[m] = anchor[m] != INT_MAX ? gid[uf[anchor[m]]] : -1;
     __syncthreads();
     // (4) new instances for live segments without an edge, in mask order
     if (tid == 0) {
-        int id = *next_id;
+        int id = s_next;
         for (int m = 0; m < M; m++) {
-            if (sc.nvox[m] > 0 && sc.segrep[m] < 0) {
+            if (snv[m] > 0 && srep[m] < 0) {
                 if (id >= inst.cap) { set_err(ctr, DISC_ERR_CAPACITY); break; }
-                sc.segrep[m] = id;
+                srep[m] = id;
                 inst.parent[id] = id;
                 inst.count[id] = 0;
-                inst.Q[id] = sc.S[5 * m + 4];
+                inst.Q[id] = sq[m];
                 inst.n_obs[id] = 1;
                 const int c = s_ncopy++;
                 ss.copy_dst[c] = id;
@@ -319,10 +402,14 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
                 s_new++;
             }
         }
-        if (!ctr->err) *next_id = id;
+        if (!ctr->err) {
+            *next_id = id;
+            s_next = id;
+        }
     }
     __syncthreads();
     if (ctr->err) return;
+    for (int m = tid; m < M; m += UNION_THREADS) sc.segrep[m] = srep[m];
     // (5) fusion per component: the candidates in the order (members by
     //     ascending id, then segments by ascending mask) keep the first one
     //     whose Q is the component's maximum (strict '>' while scanning)
@@ -334,20 +421,20 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
         int obs = 0;
         for (int x = 0; x < nloc; x++) {
             if (uf[x] != r) continue;
-            obs += inst.n_obs[gid[x]];
-            q = fmaxf(q, inst.Q[gid[x]]);
+            obs += oloc[x];
+            q = fmaxf(q, qloc[x]);
         }
         for (int m = 0; m < M; m++)
-            if (sc.segrep[m] == rep) {
+            if (srep[m] == rep) {
                 obs++;
-                q = fmaxf(q, sc.S[5 * m + 4]);
+                q = fmaxf(q, sq[m]);
             }
         int src = INT_MAX;
         for (int x = 0; x < nloc; x++)
-            if (uf[x] == r && inst.Q[gid[x]] == q) src = min(src, gid[x]);
+            if (uf[x] == r && qloc[x] == q) src = min(src, gid[x]);
         if (src == INT_MAX)
             for (int m = 0; m < M && src == INT_MAX; m++)
-                if (sc.segrep[m] == rep && sc.S[5 * m + 4] == q) src = -(m + 1);
+                if (srep[m] == rep && sq[m] == q) src = -(m + 1);
         best_src[r] = src;
         best_q[r] = q;
         inst.n_obs[rep] = obs;
@@ -378,28 +465,46 @@ k_union(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, Instances inst
         ctr->new_instances = s_new;
         ctr->merges = s_merges;
         ctr->n_edges = nedge;
-        ctr->next_id = *next_id;
+        ctr->next_id = s_next;
     }
 }
 
 // ---- embeddings, new voxels, parent flattening, cleanup ---------------------------
-__global__ void k_apply(FrameParams fp, BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst,
-                        const int* next_id)
+__device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt,
+                            const Instances& inst, const int* next_id, bool ok)
 {
-    const Scratch sc = bs.frame(f);
-    const bool ok = !frame_blocked(bs, f, ss.prev);
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gsz = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     const int D = fp.D;
     if (ok) {
-        // winning embeddings (the sources are never written in this frame)
+        // winning embeddings (the sources are never written in this frame):
+        // one warp per vector, all loads in flight before the stores
         const int nc = *ss.copy_n;
         for (int c = gtid >> 5; c < nc; c += gsz >> 5) {
             const int src = ss.copy_src[c];
             const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
             float* to = inst.E + (size_t)ss.copy_dst[c] * D;
-            for (int d = lane; d < D; d += 32) to[d] = from[d];
+            if ((D & 3) == 0) {
+                const float4* f4 = (const float4*)from;
+                float4* t4 = (float4*)to;
+                const int n4 = D >> 2;
+                for (int d0 = 0; d0 < n4; d0 += 32 * 8) {
+                    float4 r[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const int d = d0 + j * 32 + lane;
+                        if (d < n4) r[j] = f4[d];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const int d = d0 + j * 32 + lane;
+                        if (d < n4) t4[d] = r[j];
+                    }
+                }
+            } else {
+                for (int d = lane; d < D; d += 32) to[d] = from[d];
+            }
         }
         // new voxels: the lowest segment index owns a voxel
         const int nn = sc.ctr->n_new;
@@ -440,6 +545,51 @@ __global__ void k_apply(FrameParams fp, BatchScratch bs, int f, SerialScratch ss
     }
 }
 
+// ---- kernels ------------------------------------------------------------------------
+// frame_blocked decided once per block (another block may raise an error
+// while this one reads), so every thread of the block takes the same path
+__device__ bool block_blocked(const BatchScratch& bs, int f, const int* prev_err)
+{
+    __shared__ int s_blocked;
+    if (threadIdx.x == 0) s_blocked = frame_blocked(bs, f, prev_err) ? 1 : 0;
+    __syncthreads();
+    const bool b = s_blocked != 0;
+    __syncthreads();
+    return b;
+}
+
+constexpr size_t OV_SMEM = (size_t)OV_SLOTS * 12;
+
+__global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, int f, SerialScratch ss, VoxelTable vt,
+                                                         Instances inst)
+{
+    extern __shared__ __align__(16) unsigned char ov_smem[];
+    if (block_blocked(bs, f, ss.prev_err)) return;
+    phase_overlap(bs.frame(f), ss, vt, inst, ov_smem);
+}
+
+__global__ void k_score(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, Instances inst,
+                        ScoreParams sp)
+{
+    if (block_blocked(bs, f, ss.prev_err)) return;
+    phase_score(fps[f], bs.frame(f), ss, inst, sp);
+}
+
+__global__ void __launch_bounds__(UNION_THREADS, 1)
+k_union(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, Instances inst, int* next_id)
+{
+    extern __shared__ __align__(16) unsigned char union_smem[];
+    if (block_blocked(bs, f, ss.prev_err)) return;
+    phase_union(fps[f], bs.frame(f), ss, inst, next_id, union_smem);
+}
+
+__global__ void k_apply(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst,
+                        const int* next_id)
+{
+    const bool ok = !block_blocked(bs, f, ss.prev_err);
+    phase_apply(fps[f], bs.frame(f), ss, vt, inst, next_id, ok);
+}
+
 // edge and copy counters of the next frame start at zero
 __global__ void k_serial_reset(SerialScratch ss)
 {
@@ -447,40 +597,33 @@ __global__ void k_serial_reset(SerialScratch ss)
     *ss.copy_n = 0;
 }
 
-// ---- host launchers (each returns the number of kernels it enqueued) ------------------
-int launch_overlap(const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
-                   const Instances& inst, cudaStream_t st)
+// ---- host launcher ----------------------------------------------------------------
+int launch_serial_frame(const FrameParams* fps, const BatchScratch& bs, int f, const SerialScratch& ss,
+                        const VoxelTable& vt, const Instances& inst, int* next_id, float eta, float dot_err, int phase,
+                        cudaStream_t st)
 {
-    k_overlap<<<152 * 2, 256, 0, st>>>(bs, f, ss, vt, inst);
-    return 1;
-}
-
-int launch_score(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
-                 float eta, float dot_err, cudaStream_t st)
-{
-    ScoreParams sp{eta, dot_err};
-    k_score<<<152, 256, 0, st>>>(fp, bs, f, ss, inst, sp);
-    return 1;
-}
-
-int launch_union(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
-                 int* next_id, cudaStream_t st)
-{
-    k_union<<<1, UNION_THREADS, UNION_SMEM, st>>>(fp, bs, f, ss, inst, next_id);
-    return 1;
-}
-
-int launch_apply(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
-                 const Instances& inst, const int* next_id, cudaStream_t st)
-{
-    k_apply<<<152 * 2, 256, 0, st>>>(fp, bs, f, ss, vt, inst, next_id);
-    k_serial_reset<<<1, 1, 0, st>>>(ss);
-    return 2;
+    switch (phase) {
+        case 0:
+            k_overlap<<<152 * 2, SER_THREADS, OV_SMEM, st>>>(bs, f, ss, vt, inst);
+            return 1;
+        case 1:
+            k_score<<<152, 256, 0, st>>>(fps, bs, f, ss, inst, ScoreParams{eta, dot_err});
+            return 1;
+        case 2:
+            k_union<<<1, UNION_THREADS, UNION_SMEM, st>>>(fps, bs, f, ss, inst, next_id);
+            return 1;
+        default:
+            k_apply<<<152 * 2, 256, 0, st>>>(fps, bs, f, ss, vt, inst, next_id);
+            k_serial_reset<<<1, 1, 0, st>>>(ss);
+            return 2;
+    }
 }
 
 cudaError_t set_serial_kernel_attrs()
 {
-    return cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OV_SMEM);
+    return e;
 }
 
 }  // namespace disc

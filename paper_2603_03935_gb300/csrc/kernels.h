@@ -23,8 +23,8 @@ enum Phase {
     PH_WEIGHTS,       // pooling weights, S_size / S_sem / S_dist
     PH_POOL_EXACT,    // exact D-weighted pooled embedding
     PH_POOL_GEMM,     // tcgen05 pooled embedding (fast score)
-    PH_BACKPROJECT,   // depth -> voxel keys, normals, per-segment sets
-    PH_ENTRIES,       // S_angle terms, |V_m|, labels at batch start, Q
+    PH_BACKPROJECT,   // depth -> voxel keys, normals, per-segment sets (chunks of frames)
+    PH_ENTRIES,       // S_angle terms, |V_m|, labels at batch start (chunks), then Q
     PH_OVERLAP,       // per frame: overlap histogram against the current map
     PH_SCORE,         // per frame: geometry and cosine gates
     PH_UNION,         // per frame: union, new ids, merges, fusion (one CTA)
@@ -42,19 +42,19 @@ int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int
                       bool any_f32, cudaStream_t st);
 int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, bool any_bf16,
                      bool any_f32, cudaStream_t st);
-int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int B, int H, int W, cudaStream_t st);
-int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int B, int Mmax,
+// back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
+// batch start) on frames [f0, f0 + nb); then Q of every segment
+int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
+int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int f0, int nb, int Mmax,
                    cudaStream_t st);
+int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);
+// frames per back-projection/entries launch: their per-frame hashes stay in L2
+constexpr int GEOMETRY_CHUNK = 4;
 
-// serial, one frame slot f
-int launch_overlap(const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
-                   const Instances& inst, cudaStream_t st);
-int launch_score(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
-                 float eta, float dot_err, cudaStream_t st);
-int launch_union(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const Instances& inst,
-                 int* next_id, cudaStream_t st);
-int launch_apply(const FrameParams& fp, const BatchScratch& bs, int f, const SerialScratch& ss, const VoxelTable& vt,
-                 const Instances& inst, const int* next_id, cudaStream_t st);
+// serial part, frame slot f: phase 0 overlap, 1 score, 2 union, 3 apply
+int launch_serial_frame(const FrameParams* fps, const BatchScratch& bs, int f, const SerialScratch& ss,
+                        const VoxelTable& vt, const Instances& inst, int* next_id, float eta, float dot_err, int phase,
+                        cudaStream_t st);
 
 size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);
