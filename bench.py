@@ -39,11 +39,12 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames-per-step", type=int, default=32)
     ap.add_argument("--latency-frames", type=int, default=64)
+    ap.add_argument("--timing-batches", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -64,16 +65,19 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples while the timed region runs."""
+    """nvidia-smi clock/throttle samples, started before the warm-up (the tool
+    takes a moment to start) and kept only inside the timed window."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index=0):
+    def __init__(self, device_index=0, period_ms=20):
         self.proc = None
         self.path = None
         self.idx = device_index
+        self.period = period_ms
+        self.window = None
 
     def start(self):
         try:
@@ -81,10 +85,14 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, t0, t1):
+        """The timed window, in time.time() seconds."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -95,25 +103,35 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        samples = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                if "." in parts[0]:
+                    ts += float("0." + parts[0].split(".")[1])
+                samples.append((ts, float(parts[2]), float(parts[3]),
+                                {n for n, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
         os.unlink(self.path)
-        if not sm:
+        if not samples:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = samples
+        if self.window:
+            t0, t1 = self.window
+            inside = [x for x in samples if t0 - 0.02 <= x[0] <= t1 + 0.02]
+            if not inside:  # window shorter than the sampling period: the nearest sample
+                mid = 0.5 * (t0 + t1)
+                inside = [min(samples, key=lambda x: abs(x[0] - mid))]
+        reasons = set()
+        for x in inside:
+            reasons |= x[3]
+        return {"sm_mhz": float(np.median([x[1] for x in inside])), "sm_max_mhz": float(max(x[2] for x in inside)),
+                "reasons": sorted(reasons), "samples": len(inside), "period_ms": self.period}
 
 
 def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
@@ -216,11 +234,13 @@ def main():
             dist.barrier()
 
     B, K, Wm = args.frames_per_step, args.steps, args.warmup
-    # replicas only: every rank integrates its own map of its own scene
+    # replicas only: every rank integrates its own map of its own scene; the
+    # camera path is closed, so frames past its end continue on the next lap
     scene = synth.room_scene(seed=1 + rank)
     n_main = (Wm + K) * B
-    n_extra = 2 * B + args.latency_frames
-    fr = scene.render(range(n_main + n_extra))
+    n_extra = args.timing_batches * B + args.latency_frames
+    n_render = min(scene.num_frames, n_main + n_extra)
+    fr = scene.render(range(n_render))
     H, W_, P, D = scene.height, scene.width, scene.patch_h * scene.patch_w, scene.dim
     Kpad = (P + 31) // 32 * 32
     intr = (scene.fx, scene.fy, scene.cx, scene.cy)
@@ -241,7 +261,7 @@ def main():
         n = hi - lo
         arr = (binding.Frame * n)()
         for j in range(n):
-            i = lo + j
+            i = (lo + j) % n_render
             f = arr[j]
             f.width, f.height = W_, H
             f.fx, f.fy, f.cx, f.cy = intr
@@ -261,6 +281,8 @@ def main():
     steps = [frame_array(s * B, (s + 1) * B) for s in range(Wm + K)]
     stats = (binding.Stats * B)()
 
+    clocks = ClockSampler(local)
+    clocks.start()
     gmap = DiscMap(**cfg)
     for s in range(Wm):
         rc = gmap.integrate_frames_raw(steps[s], B, stats)
@@ -269,9 +291,9 @@ def main():
     if world > 1:
         dist.barrier()
 
-    clocks = ClockSampler(local)
-    clocks.start()
+    time.sleep(0.5)  # the sampler is running by now
     launches0 = gmap.kernel_launches()
+    wall0 = time.time()
     times = []
     updates = 0
     new_vox = 0
@@ -288,6 +310,7 @@ def main():
         updates += sum(stats[j].unique_seg_voxels for j in range(B))
         new_vox += sum(stats[j].new_voxels for j in range(B))
     launches = gmap.kernel_launches() - launches0
+    clocks.mark(wall0, time.time())
     total_ms = float(np.sum(times))
     clk = clocks.stop()
     t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -296,15 +319,17 @@ def main():
     total_ms = float(t.item())
     frames_all = K * B * world
 
-    # per-phase device time on the following frames (events around each phase)
+    # per-phase device time on the following batches (event-record nodes
+    # around each phase, inside the batch's graph)
     lo = n_main
+    TB = args.timing_batches
     gmap.set_phase_timing(True)
-    ph_stats = (binding.Stats * B)()
-    rc = gmap.integrate_frames_raw(frame_array(lo, lo + B), B, ph_stats)
+    ph_stats = (binding.Stats * (TB * B))()
+    rc = gmap.integrate_frames_raw(frame_array(lo, lo + TB * B), TB * B, ph_stats)
     assert rc == 0, rc
     phases = gmap.phase_times()
     gmap.set_phase_timing(False)
-    lo += B
+    lo += TB * B
 
     # single-frame latency (disc_integrate_frame, one synchronisation per frame)
     lat = []
@@ -321,13 +346,14 @@ def main():
         lat.append(e0.elapsed_time(e1))
     gmap.close()
 
-    # dominant single-kernel phase and its roofline
+    # dominant single-kernel phase with a byte model, and its roofline (the
+    # one-CTA union moves a few KB per frame and has none)
     peak, peak_kind = peaks()
-    per_frame = {k: v["ms"] / B for k, v in phases.items()}
-    single = ("backproject", "coverage", "pool_gemm", "pool_exact", "weights", "overlap", "score", "union")
+    per_frame = {k: v["ms"] / (TB * B) for k, v in phases.items()}
+    single = ("backproject", "coverage", "pool_gemm", "pool_exact", "weights", "overlap", "score")
     dom = max(single, key=lambda k: phases[k]["ms"])
-    st_list = [{k: getattr(ph_stats[j], k) for k, _ in binding.Stats._fields_} for j in range(B)]
-    Ms = [int(fr.num_masks[lo - B + j]) for j in range(B)]
+    st_list = [{k: getattr(ph_stats[j], k) for k, _ in binding.Stats._fields_} for j in range(TB * B)]
+    Ms = [int(fr.num_masks[(lo - TB * B + j) % n_render]) for j in range(TB * B)]
     alg_total = algorithmic_bytes(dom, st_list, H, W_, P, D, Ms, Kpad)
     calls = max(phases[dom]["calls"], 1)
     launch_ms = phases[dom]["ms"] / calls
@@ -335,14 +361,14 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
-                "launches_per_frame": calls / B}
+                "launches_per_frame": calls / (TB * B)}
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None
     if not args.no_e2e:
-        hd = torch.from_numpy(fr.depth[:n_main]).pin_memory()
-        hl = torch.from_numpy(fr.labels[:n_main].view(np.int16)).pin_memory()
-        ht = torch.from_numpy(fr.tokens[:n_main]).pin_memory()
+        hd = torch.from_numpy(fr.depth).pin_memory()
+        hl = torch.from_numpy(fr.labels.view(np.int16)).pin_memory()
+        ht = torch.from_numpy(fr.tokens).pin_memory()
         hsteps = [frame_array(s * B, (s + 1) * B, on_device=False, host=(hd, hl, ht)) for s in range(Wm + K)]
         m2 = DiscMap(**cfg)
         for s in range(Wm):
@@ -374,6 +400,7 @@ def main():
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded room trajectory; stands in for the paper's HM3D/Replica trajectories)",
                "config": {"workload": WORKLOAD, "frames_per_step": B, "frames_timed": K * B,
+                          "trajectory_frames": n_render,
                           "l2": "flushed between timed steps (258 MB write)", "replicas": world},
                "voxel_updates_per_s": updates * world / (total_ms / 1e3),
                "new_voxels_per_s": new_vox * world / (total_ms / 1e3),

@@ -278,19 +278,61 @@ cudaEvent_t take_event(disc_map* m)
     return m->ev_pool[m->ev_used++];
 }
 
-// Enqueue one phase; with timing on, bracket it with events on the map's stream.
+// Enqueue one phase; with timing on, bracket it with events on the map's
+// stream (event-record nodes when the stream is being captured).
 template <class F>
 void run_phase(disc_map* m, int ph, F&& launch)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (m->timing && (a = take_event(m))) cudaEventRecord(a, m->stream);
+    if (m->timing && (a = take_event(m))) cudaEventRecordWithFlags(a, m->stream, cudaEventRecordExternal);
     const int n = launch();
     m->launches += n;
     m->phase_launches[ph] += n;
     if (a && (b = take_event(m))) {
-        cudaEventRecord(b, m->stream);
+        cudaEventRecordWithFlags(b, m->stream, cudaEventRecordExternal);
         if (n > 0) m->marks.push_back({ph, a, b});
     }
+}
+
+int enqueue_batch_kernels(disc_map* m, int B, bool any_bf16, bool any_f32);
+
+// Timing run of one batch: the sequence with its phase events is captured and
+// launched as one graph, so the device never waits on the host inside a
+// timed interval.  false: capture is not possible here (plain launches).
+bool launch_timed_graph(disc_map* m, int B, bool any_bf16, bool any_f32)
+{
+    const size_t marks0 = m->marks.size(), ev0 = m->ev_used;
+    const int64_t l0 = m->launches;
+    int64_t pl0[PH_COUNT];
+    for (int i = 0; i < PH_COUNT; i++) pl0[i] = m->phase_launches[i];
+    auto undo = [&] {
+        m->marks.resize(marks0);
+        m->ev_used = ev0;
+        m->launches = l0;
+        for (int i = 0; i < PH_COUNT; i++) m->phase_launches[i] = pl0[i];
+        cudaGetLastError();
+    };
+    if (cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        undo();
+        return false;
+    }
+    enqueue_batch_kernels(m, B, any_bf16, any_f32);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamEndCapture(m->stream, &graph) != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        undo();
+        return false;
+    }
+    cudaGraphDestroy(graph);
+    const bool ok = cudaGraphLaunch(exec, m->stream) == cudaSuccess;
+    cudaGraphExecDestroy(exec);  // freed once the launch completes
+    if (!ok) {
+        undo();
+        return false;
+    }
+    return true;
 }
 
 // After a synchronisation: fold the recorded phase intervals into the totals.
@@ -495,8 +537,7 @@ disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCou
     if (g) {
         CK(cudaGraphLaunch(g->exec, m->stream));
         m->launches += g->kernels;
-    } else {
-        // per-phase events need plain launches
+    } else if (!(m->timing && !m->graphs_off && launch_timed_graph(m, B, any_bf16, any_f32))) {
         enqueue_batch_kernels(m, B, any_bf16, any_f32);
     }
     // the batch's counters, in slot order, to the call's history

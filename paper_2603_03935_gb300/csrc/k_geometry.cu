@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
     __shared__ TilePoint tp[BP_HALO];
     __shared__ unsigned long long tkey[BP_SLOTS];
     __shared__ int tn[6][BP_SLOTS];  // per component: sum of (v >> 16) and of (v & 0xffff)
-    __shared__ int tcount[2];
+    __shared__ unsigned short tlist[BP_THREADS];  // claimed tile slots
+    __shared__ int tcount[3];        // valid pixels, dropped pixels, listed slots
     const FrameParams& fp = fps[f0 + blockIdx.z];
     const Scratch sc = bs.frame(f0 + blockIdx.z);
     if (fp.M <= 0) return;  // uniform per block
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
 #pragma unroll
         for (int r = 0; r < 6; r++) tn[r][i] = 0;
     }
-    if (tid < 2) tcount[tid] = 0;
+    if (tid < 3) tcount[tid] = 0;
     __syncthreads();
     const int hx = threadIdx.x + 1, hy = threadIdx.y + 1;  // own position in the halo tile
     const TilePoint me = tp[hy * BP_HX + hx];
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
             n[2] = __fsub_rn(__fmul_rn(e2[0], e1[1]), __fmul_rn(e2[1], e1[0]));
             float l2 = __fadd_rn(__fadd_rn(__fmul_rn(n[0], n[0]), __fmul_rn(n[1], n[1])), __fmul_rn(n[2], n[2]));
             if (l2 > 0.0f) {
-                const float il = __fdiv_rn(1.0f, __fsqrt_rn(l2));
+                const float il = __frcp_rn(__fsqrt_rn(l2));
 #pragma unroll
                 for (int r = 0; r < 3; r++) n[r] = __fmul_rn(n[r], il);
                 // orient toward the camera
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
     // Pixels of one warp with the same (mask, voxel) key are summed first:
     // each 2^-32 fixed-point component v (|v| <= 2^32) splits exactly into
     // v = (v >> 16) * 2^16 + (v & 0xffff), whose parts add in 32-bit integers
-    // for up to a whole tile.  One lane per key then updates the tile hash.
+    // for up to a whole tile.  One lane per key then updates the tile hash;
+    // the lane that claims a tile slot lists it.
     const unsigned long long hk = keyed ? (((unsigned long long)lab << 54) | key) : 0ull;
     const unsigned grp = __match_any_sync(0xffffffffu, hk);
     unsigned part[6];
@@ -187,7 +189,11 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
         unsigned t = (unsigned)(mix64(hk) & (BP_SLOTS - 1));
         while (true) {
             const unsigned long long prev = atomicCAS(&tkey[t], 0ull, hk);
-            if (prev == 0ull || prev == hk) break;
+            if (prev == 0ull) {
+                tlist[atomicAdd(&tcount[2], 1)] = (unsigned short)t;
+                break;
+            }
+            if (prev == hk) break;
             t = (t + 1) & (BP_SLOTS - 1);
         }
 #pragma unroll
@@ -199,80 +205,60 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
         if (tcount[0]) atomicAdd(&sc.ctr->valid_pixels, tcount[0]);
         if (tcount[1]) atomicAdd(&sc.ctr->dropped_pixels, tcount[1]);
     }
-    // the tile's distinct keys update the frame slot's hash; the keys this
-    // block claims first are appended to the entry list with one reservation
-    // per block (a single shared counter would serialise every claim)
-    constexpr int PER_THREAD = BP_SLOTS / BP_THREADS;
+    // the tile's distinct keys update the frame slot's hash, one lane per key
+    // (whole warps iterate together); each warp appends the keys it claimed
+    // first to the entry list with one reservation
+    const int nkeys = tcount[2];
+    const int warp = tid >> 5;
     int probes = 0;
-    int claimed_slot[PER_THREAD];
-    unsigned long long claimed_key[PER_THREAD];
-    int nclaim = 0;
-#pragma unroll
-    for (int j = 0; j < PER_THREAD; j++) {
-        const int i = tid + j * BP_THREADS;
-        const unsigned long long hk = tkey[i];
-        claimed_slot[j] = -1;
-        claimed_key[j] = hk;
-        if (hk == 0ull) continue;
-        unsigned long long s = mix64(hk) & sc.smask;
-        bool ok = true;
-        while (true) {
-            const unsigned long long cur = sc.sslot[s].key;
-            if (cur == hk) break;
-            if (cur == 0ull) {
-                const unsigned long long prev = atomicCAS(&sc.sslot[s].key, 0ull, hk);
-                if (prev == 0ull) {
-                    claimed_slot[j] = (int)s;
-                    nclaim++;
+    for (int i0 = warp * 32; i0 < nkeys; i0 += BP_THREADS) {
+        const int i = i0 + lane;
+        unsigned long long hk2 = 0ull;
+        long long s = -1;
+        bool claimed = false;
+        if (i < nkeys) {
+            const int t = tlist[i];
+            hk2 = tkey[t];
+            unsigned long long h = mix64(hk2) & sc.smask;
+            while (true) {
+                const unsigned long long cur = sc.sslot[h].key;
+                if (cur == hk2) break;
+                if (cur == 0ull) {
+                    const unsigned long long prev = atomicCAS(&sc.sslot[h].key, 0ull, hk2);
+                    if (prev == 0ull) {
+                        claimed = true;
+                        break;
+                    }
+                    if (prev == hk2) break;
+                }
+                h = (h + 1) & sc.smask;
+                if (++probes > (int)sc.smask) {
+                    set_err(sc.ctr, DISC_ERR_TABLE_FULL);
+                    h = ~0ull;
                     break;
                 }
-                if (prev == hk) break;
             }
-            s = (s + 1) & sc.smask;
-            if (++probes > (int)sc.smask) {
-                set_err(sc.ctr, DISC_ERR_TABLE_FULL);
-                ok = false;
-                break;
-            }
-        }
-        if (ok) {
-            SegSlot& slot = sc.sslot[s];
+            if (h != ~0ull) {
+                s = (long long)h;
+                SegSlot& slot = sc.sslot[h];
 #pragma unroll
-            for (int r = 0; r < 3; r++) {
-                const long long v = (long long)tn[2 * r][i] * 65536 + (long long)(unsigned)tn[2 * r + 1][i];
-                if (v) atomicAdd((unsigned long long*)&slot.n[r], (unsigned long long)v);
+                for (int r = 0; r < 3; r++) {
+                    const long long v = (long long)tn[2 * r][t] * 65536 + (long long)(unsigned)tn[2 * r + 1][t];
+                    if (v) atomicAdd((unsigned long long*)&slot.n[r], (unsigned long long)v);
+                }
             }
         }
-    }
-    // block-wide exclusive scan of the claim counts
-    __shared__ int wsum[BP_THREADS / 32];
-    __shared__ int s_base;
-    int incl = nclaim;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
-    }
-    const int warp = tid >> 5;
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < BP_THREADS / 32; w++) {
-            const int c = wsum[w];
-            wsum[w] = tot;
-            tot += c;
+        const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+        if (cm) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&sc.ctr->n_entries, __popc(cm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (claimed) {
+                const int at = base + __popc(cm & ((1u << lane) - 1));
+                sc.slist[at] = (int)s;
+                sc.sent[at] = hk2;
+            }
         }
-        s_base = tot ? atomicAdd(&sc.ctr->n_entries, tot) : 0;
-    }
-    __syncthreads();
-    int at = s_base + wsum[warp] + incl - nclaim;
-#pragma unroll
-    for (int j = 0; j < PER_THREAD; j++) {
-        if (claimed_slot[j] < 0) continue;
-        sc.slist[at] = claimed_slot[j];
-        sc.sent[at] = claimed_key[j];
-        at++;
     }
     const int pmax = __reduce_max_sync(0xffffffffu, probes);
     if (lane == 0 && pmax > 0) atomicMax(&sc.ctr->max_probe, pmax);
