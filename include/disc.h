@@ -149,7 +149,58 @@ disc_status disc_integrate_frame(disc_map* map, const disc_frame* frame, disc_fr
 disc_status disc_integrate_frames(disc_map* map, const disc_frame* frames, int32_t n,
                                   disc_frame_stats* stats, int32_t* n_done);
 
-/* Copies the intermediates of the most recent frame (see disc_frame_report). */
+/* ---- Groups: many maps integrated side by side --------------------------
+ * A group owns the scratch of one batch over up to max_maps maps with up to
+ * frames_per_map frames each (the paper has no counterpart: it processes one
+ * map; this serves many independent maps on one GPU).  Every launch of a
+ * batch covers the frames of all its maps; the stateful steps (overlap,
+ * association, merging, fusion, insertion) run frame j of every map in one
+ * launch, so maps hide each other's per-frame latency.  Each map's result is
+ * bit for bit the result of integrating its frames alone.  Maps keep their
+ * tables (resident on the device) between calls and may join any group call
+ * whose embed_dim, patch grid and device match theirs. */
+typedef struct disc_group disc_group; /* opaque */
+
+typedef struct {
+    int32_t max_maps;        /* maps per call (1..1024) */
+    int32_t frames_per_map;  /* frames of one map per batch (1..256); max_maps * frames_per_map <= 4096 */
+    int32_t embed_dim;       /* D of every map of the group */
+    int32_t patch_h, patch_w;/* token grid of every map of the group */
+    int32_t max_width, max_height; /* largest frame of any map */
+    int32_t max_masks;       /* largest num_masks of any frame (<= 256) */
+    void* cuda_stream;       /* cudaStream_t, or NULL: the group creates one */
+    int32_t device;
+} disc_group_config;
+
+/* Defaults: 16 maps x 4 frames, 640x480, 24x24x768, 40 masks. */
+void disc_group_config_default(disc_group_config* cfg);
+
+/* Allocates the batch scratch (about 26 MB per frame slot at 640x480).
+ * DISC_ERR_INVALID_ARG for an invalid config, DISC_ERR_OOM when it does not
+ * fit. */
+disc_status disc_group_create(const disc_group_config* cfg, disc_group** out_group);
+
+/* Integrates counts[i] frames (frames[i], in order) into maps[i] for every i,
+ * each map's frames in order and the maps independently: a frame that fails
+ * stops the later frames of its own map only.  stats (nullable; stats[i]
+ * nullable) receives one entry per frame of each map; n_done (nullable)
+ * [n_maps] how many frames of each map were integrated.  A map may appear
+ * once per call.  Returns DISC_OK when every frame was integrated, else the
+ * first failure in map order.  Returns after all results are complete. */
+disc_status disc_group_integrate(disc_group* group, disc_map* const* maps, int32_t n_maps,
+                                 const disc_frame* const* frames, const int32_t* counts,
+                                 disc_frame_stats* const* stats, int32_t* n_done);
+
+/* Per-phase timing of the group's batches (as disc_map_set_phase_timing). */
+disc_status disc_group_set_phase_timing(disc_group* group, int32_t enable);
+disc_status disc_group_phase_times(disc_group* group, double* ms, int64_t* launches, int64_t* calls,
+                                   int32_t n);
+int64_t disc_group_kernel_launches(disc_group* group);
+int64_t disc_group_device_bytes(disc_group* group);
+void disc_group_destroy(disc_group* group); /* NULL-safe */
+
+/* Copies the intermediates of the most recent frame that the map integrated
+ * through disc_integrate_frame(s) (see disc_frame_report). */
 disc_status disc_map_last_frame(disc_map* map, disc_frame_report* report);
 
 /* Open-vocabulary query (Sec. IV retrieval): cosine of each query vector
@@ -212,9 +263,11 @@ int64_t disc_map_kernel_launches(disc_map* map);
  * 0 clear, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
  * 5 pool_gemm -- one interval per batch each --, 6 backproject and 7 entries
  * (S_angle, |V_m|, lookup; then Q) -- one interval per chunk of 4 frames --,
- * and 8 overlap, 9 score, 10 union, 11 apply -- one interval per frame each.
- * With timing on, batches run as plain launches instead of a CUDA graph.  ms/launches/calls: [n] accumulated device
- * time, kernels launched and timed intervals per phase (any may be NULL). */
+ * and 8 overlap, 9 score, 10 union, 11 apply -- one interval per frame step
+ * each.  With timing on, each batch is captured with event-record nodes and
+ * launched once as a graph.  ms/launches/calls: [n] accumulated device time,
+ * kernels launched and timed intervals per phase (any may be NULL).  Kernel
+ * launches count only the map's own calls (not group calls). */
 disc_status disc_map_set_phase_timing(disc_map* map, int32_t enable);
 disc_status disc_map_phase_times(disc_map* map, double* ms, int64_t* launches, int64_t* calls, int32_t n);
 const char* disc_phase_name(int32_t phase);

@@ -48,6 +48,12 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class GroupConfig(ctypes.Structure):
+    _fields_ = [("max_maps", c_i32), ("frames_per_map", c_i32), ("embed_dim", c_i32), ("patch_h", c_i32),
+                ("patch_w", c_i32), ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
+                ("cuda_stream", c_vp), ("device", c_i32)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
                 ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
@@ -99,9 +105,22 @@ def lib():
         L.disc_map_destroy.restype = None
         L.disc_status_str.argtypes = [c_i32]
         L.disc_status_str.restype = ctypes.c_char_p
+        L.disc_group_config_default.argtypes = [P(GroupConfig)]
+        L.disc_group_config_default.restype = None
+        L.disc_group_create.argtypes = [P(GroupConfig), P(c_vp)]
+        L.disc_group_integrate.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]
+        L.disc_group_set_phase_timing.argtypes = [c_vp, c_i32]
+        L.disc_group_phase_times.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
+        L.disc_group_kernel_launches.argtypes = [c_vp]
+        L.disc_group_kernel_launches.restype = c_i64
+        L.disc_group_device_bytes.argtypes = [c_vp]
+        L.disc_group_device_bytes.restype = c_i64
+        L.disc_group_destroy.argtypes = [c_vp]
+        L.disc_group_destroy.restype = None
         for f in ("disc_map_create", "disc_integrate_frame", "disc_integrate_frames", "disc_map_last_frame",
                   "disc_query_topk", "disc_query_points", "disc_map_counts", "disc_map_export_voxels",
-                  "disc_map_export_instances", "disc_map_save", "disc_map_load"):
+                  "disc_map_export_instances", "disc_map_save", "disc_map_load", "disc_group_create",
+                  "disc_group_integrate", "disc_group_set_phase_timing", "disc_group_phase_times"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -341,3 +360,74 @@ class DiscMap:
         _check(lib().disc_map_load(str(path).encode(), ctypes.byref(c) if c is not None else None,
                                    ctypes.byref(h)), "disc_map_load")
         return cls._from_handle(h)
+
+
+class DiscGroup:
+    """Batches over many maps (disc_group_create ... disc_group_destroy)."""
+
+    def __init__(self, **cfg):
+        c = GroupConfig()
+        lib().disc_group_config_default(ctypes.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = c_vp()
+        _check(lib().disc_group_create(ctypes.byref(c), ctypes.byref(h)), "disc_group_create")
+        self._h = h
+        self.cfg = {k: getattr(c, k) for k, _ in GroupConfig._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().disc_group_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def integrate_raw(self, maps, frame_arrays, counts, stats_arrays=None, n_done=None):
+        """maps: [DiscMap]; frame_arrays: [ctypes Frame array]; counts: [int];
+        stats_arrays: [ctypes Stats array] or None; returns the status."""
+        n = len(maps)
+        hm = (c_vp * n)(*[m._h.value for m in maps])
+        hf = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in frame_arrays])
+        hc = (c_i32 * n)(*counts)
+        hs = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in stats_arrays]) \
+            if stats_arrays is not None else None
+        return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
+
+    def integrate(self, maps, frames_per_map, check: bool = True):
+        """frames_per_map: per map a list of (Frame, keepalive).  Returns
+        (per-map list of stats dicts, per-map frames done, status)."""
+        n = len(maps)
+        arrs, sts = [], []
+        for frames in frames_per_map:
+            k = len(frames)
+            a = (Frame * max(k, 1))()
+            for i, (fr, _keep) in enumerate(frames):
+                a[i] = fr
+            arrs.append(a)
+            sts.append((Stats * max(k, 1))())
+        done = (c_i32 * max(n, 1))()
+        rc = self.integrate_raw(maps, arrs, [len(f) for f in frames_per_map], sts, done)
+        if check:
+            _check(rc, "disc_group_integrate")
+        stats = [[sts[g][i].as_dict() for i in range(len(frames_per_map[g]))] for g in range(n)]
+        return stats, [int(done[g]) for g in range(n)], rc
+
+    def kernel_launches(self) -> int:
+        return int(lib().disc_group_kernel_launches(self._h))
+
+    def device_bytes(self) -> int:
+        return int(lib().disc_group_device_bytes(self._h))
+
+    def set_phase_timing(self, enable: bool):
+        _check(lib().disc_group_set_phase_timing(self._h, 1 if enable else 0), "disc_group_set_phase_timing")
+
+    def phase_times(self) -> dict:
+        n = 12
+        ms = np.zeros(n, np.float64)
+        la = np.zeros(n, np.int64)
+        ca = np.zeros(n, np.int64)
+        _check(lib().disc_group_phase_times(self._h, ms.ctypes.data, la.ctypes.data, ca.ctypes.data, n),
+               "disc_group_phase_times")
+        return {lib().disc_phase_name(i).decode(): dict(ms=float(ms[i]), launches=int(la[i]), calls=int(ca[i]))
+                for i in range(n)}

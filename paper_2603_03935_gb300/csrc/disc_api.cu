@@ -1,7 +1,8 @@
-// C ABI of libdisc (declared in include/disc.h): map lifetime, frame
-// integration, queries, export and checkpoints.  Host code only orchestrates:
-// every step of a frame runs in the kernels of k_features.cu, k_gemm.cu,
-// k_geometry.cu and k_serial.cu, enqueued on the map's stream.
+// C ABI of libdisc (declared in include/disc.h): map and group lifetime,
+// frame integration, queries, export and checkpoints.  Host code only
+// orchestrates: every step of a frame runs in the kernels of k_features.cu,
+// k_gemm.cu, k_geometry.cu and k_serial.cu, enqueued on the stream of the
+// map (its own calls) or of the group (batches over many maps).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -68,40 +69,31 @@ struct BatchGraph {
     int kernels = 0;
 };
 
-struct disc_map {
-    disc_map_config cfg;
+// What one batch of frame slots needs besides the maps themselves: the
+// slots' scratch, the per-batch parameter block, input staging, the per-frame
+// counters of the running call, captured launch sequences and phase timing.
+// A map owns one for its own calls (one map per batch); a group owns one for
+// batches that span many maps.
+struct Runner {
+    int device = 0;
     cudaStream_t stream = nullptr;
-    bool own_stream = false;
     DevAlloc mem;
-    VoxelTable vt{};
-    Instances inst{};
-    int* d_next_id = nullptr;
-    int* d_flag = nullptr;
-    int* d_prev_err = nullptr;            // status of the frame before the running batch
-    bool graphs_off = false;              // capture failed once: launch directly
-    std::map<int, BatchGraph> graphs;     // captured batch sequences
-    const void* graph_vt_keys = nullptr;
-    const void* graph_inst_parent = nullptr;
+    int D = 0, P = 0, Ph = 0, Pw = 0, Kpad = 0, MM = 1, Npad_max = 16;
+    int Hmax = 0, Wmax = 0, Mmax = 0;
+    int Gmax = 1, Jmax = 1, S = 1;  // maps per batch, frames per map, slots = Gmax * Jmax
+    size_t px_cap = 0;
     BatchScratch bs{};
-    SerialScratch ss{};
-    FrameParams* d_fps = nullptr;         // [Bmax] parameters of the batch's frames
-    FrameCounters* d_hist = nullptr;      // [hist_cap] per-frame counters of one call
+    // parameter block: FrameParams[S] | MapRefs[Gmax] | slot_of[Gmax * Jmax] | prev_hist[Gmax]
+    unsigned char* d_param = nullptr;
+    size_t off_refs = 0, off_slot = 0, off_prev = 0, param_bytes = 0;
+    FrameCounters* d_hist = nullptr;  // [hist_cap] per-frame counters of one call
     int hist_cap = 0;
-    int Bmax = 1;
-    int MM = 1;                           // mask rows per frame slot
-    int P = 0, Kpad = 0, D = 0, Npad_max = 16;
-    // host-side bounds that avoid a synchronisation per frame
-    uint64_t used_upper = 0;
-    int64_t next_id_upper = 0;
-    int last_slot = 0, last_M = 0;
-    bool have_frame = false;
-    // staging of host inputs, one slot per frame of a batch
-    float* d_depth = nullptr;
+    float* d_depth = nullptr;         // staging of host inputs, one slot per frame of a batch
     uint16_t* d_labels = nullptr;
     unsigned char* d_tokens = nullptr;
     float* d_gembed = nullptr;
-    size_t px_cap = 0;
-    // kernel accounting and optional per-phase CUDA-event timing
+    bool graphs_off = false;
+    std::map<long long, BatchGraph> graphs;
     int64_t launches = 0;
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -114,6 +106,37 @@ struct disc_map {
     double phase_ms[PH_COUNT] = {};
     int64_t phase_launches[PH_COUNT] = {};
     int64_t phase_calls[PH_COUNT] = {};
+    int last_slot = 0, last_M = 0;  // the most recent frame
+    bool have_frame = false;
+
+    const FrameParams* fps() const { return (const FrameParams*)d_param; }
+    const MapRefs* refs() const { return (const MapRefs*)(d_param + off_refs); }
+    const int* slot_of() const { return (const int*)(d_param + off_slot); }
+    const int* prev_hist() const { return (const int*)(d_param + off_prev); }
+};
+
+struct disc_map {
+    disc_map_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevAlloc mem;
+    VoxelTable vt{};
+    Instances inst{};
+    SerialScratch ss{};
+    int* d_next_id = nullptr;
+    int* d_flag = nullptr;
+    int D = 0, P = 0, Kpad = 0, MM = 1;
+    // host-side bounds that avoid a synchronisation per frame
+    uint64_t used_upper = 0;
+    int64_t next_id_upper = 0;
+    Runner* run = nullptr;  // created by the map's first own integration call
+    bool timing_wanted = false;
+};
+
+struct disc_group {
+    disc_group_config cfg;
+    bool own_stream = false;
+    Runner run;
 };
 
 namespace {
@@ -147,7 +170,137 @@ bool config_ok(const disc_map_config& c)
     return true;
 }
 
-disc_status alloc_voxel_table(disc_map* m, uint64_t cap, VoxelTable* out)
+// kernel attributes (dynamic shared memory above 48 KB), once per process
+disc_status set_kernel_attrs()
+{
+    static bool done = false;
+    if (done) return DISC_OK;
+    cudaError_t e = set_feature_kernel_attrs(200 * 1024);
+    if (e == cudaSuccess) e = set_gemm_kernel_attrs();
+    if (e == cudaSuccess) e = set_serial_kernel_attrs();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DISC_ERR_CUDA;
+    }
+    done = true;
+    return DISC_OK;
+}
+
+// ---- runner ----------------------------------------------------------------------
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int Ph, int Pw, int Hmax, int Wmax,
+                        int Mmax, int Gmax, int Jmax)
+{
+    r.device = device;
+    r.stream = stream;
+    r.D = D;
+    r.Ph = Ph;
+    r.Pw = Pw;
+    r.P = Ph * Pw;
+    r.Kpad = (r.P + GEMM_KC - 1) / GEMM_KC * GEMM_KC;
+    r.Hmax = Hmax;
+    r.Wmax = Wmax;
+    r.Mmax = Mmax;
+    r.MM = std::max(1, Mmax);
+    r.Npad_max = std::max(16, (r.MM + 15) / 16 * 16);
+    r.Gmax = Gmax;
+    r.Jmax = Jmax;
+    r.S = Gmax * Jmax;
+    const int P = r.P, MM = r.MM, B = r.S;
+    const uint64_t npx = (uint64_t)Wmax * Hmax;
+    const uint64_t scap = next_pow2(npx + npx / 2);  // per-frame hashes: load <= 2/3
+    r.px_cap = npx;
+    DevAlloc& a = r.mem;
+    r.off_refs = align256(sizeof(FrameParams) * B);
+    r.off_slot = r.off_refs + align256(sizeof(MapRefs) * Gmax);
+    r.off_prev = r.off_slot + align256(sizeof(int) * Gmax * Jmax);
+    r.param_bytes = r.off_prev + align256(sizeof(int) * Gmax);
+    r.d_param = a.get<unsigned char>(r.param_bytes);
+    BatchScratch& bs = r.bs;
+    bs.sD = D;
+    bs.sP = P;
+    bs.sMM = MM;
+    bs.sMMP = (long long)MM * P;
+    bs.sW = (long long)r.Npad_max * r.Kpad;
+    bs.sMMD = (long long)MM * D;
+    bs.sS = 5LL * MM;
+    bs.scap = (long long)scap;
+    Scratch& sc = bs.base;
+    sc.sumF = a.get<long long>((size_t)B * D);
+    sc.fbar = a.get<float>((size_t)B * D);
+    sc.gvec = a.get<float>((size_t)B * D);
+    sc.gg = a.get<long long>(B);
+    sc.nsum = a.get<long long>(B);
+    sc.dotg = a.get<long long>((size_t)B * P);
+    sc.ffp = a.get<long long>((size_t)B * P);
+    sc.nrm = a.get<float>((size_t)B * P);
+    sc.Dp = a.get<float>((size_t)B * P);
+    sc.cosg = a.get<float>((size_t)B * P);
+    sc.fnorm = a.get<float>((size_t)B * P);
+    sc.cov = a.get<int32_t>((size_t)B * MM * P);
+    sc.npix = a.get<int32_t>((size_t)B * MM);
+    sc.W = a.get<float>((size_t)B * bs.sW);
+    sc.S = a.get<float>((size_t)B * 5 * MM);
+    sc.Bm = a.get<float>((size_t)B * MM);
+    sc.Ecan = a.get<float>((size_t)B * MM * D);
+    sc.Efast = a.get<float>((size_t)B * MM * D);
+    sc.ang = a.get<long long>((size_t)B * MM);
+    sc.nvox = a.get<int32_t>((size_t)B * MM);
+    sc.segrep = a.get<int32_t>((size_t)B * MM);
+    sc.sslot = a.get<SegSlot>((size_t)B * scap);
+    sc.sent = a.get<unsigned long long>((size_t)B * scap);
+    sc.slist = a.get<int32_t>((size_t)B * scap);
+    sc.elab = a.get<int32_t>((size_t)B * scap);
+    sc.smask = scap - 1;
+    sc.ctr = a.get<FrameCounters>(B);
+    r.d_depth = a.get<float>((size_t)B * npx);
+    r.d_labels = a.get<uint16_t>((size_t)B * npx);
+    r.d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
+    r.d_gembed = a.get<float>((size_t)B * D);
+    if (a.failed) return DISC_ERR_OOM;
+    cudaStream_t s = r.stream;
+    CK(cudaMemsetAsync(r.d_param, 0, r.param_bytes, s));
+    CK(cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s));
+    CK(cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s));
+    CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
+    CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
+    CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
+    CK(cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s));
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+void runner_release(Runner& r)
+{
+    cudaStreamSynchronize(r.stream);
+    for (cudaEvent_t e : r.ev_pool) cudaEventDestroy(e);
+    r.ev_pool.clear();
+    for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
+    r.graphs.clear();
+    r.mem.free_all();
+}
+
+disc_status ensure_hist(Runner& r, int n)
+{
+    if (n <= r.hist_cap) return DISC_OK;
+    if (r.d_hist) r.mem.release(r.d_hist, sizeof(FrameCounters) * r.hist_cap);
+    // captured sequences hold the old pointer
+    for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
+    r.graphs.clear();
+    const int cap = std::max(n, 2 * r.hist_cap);
+    r.d_hist = r.mem.get<FrameCounters>(cap);
+    if (r.mem.failed) {
+        r.mem.failed = false;
+        r.hist_cap = 0;
+        r.d_hist = nullptr;
+        return DISC_ERR_OOM;
+    }
+    r.hist_cap = cap;
+    return DISC_OK;
+}
+
+// ---- map tables --------------------------------------------------------------------
+disc_status alloc_voxel_table(disc_map* m, uint64_t cap, VoxelTable* out, cudaStream_t st)
 {
     VoxelTable t{};
     t.keys = m->mem.get<unsigned long long>(cap);
@@ -158,7 +311,7 @@ disc_status alloc_voxel_table(disc_map* m, uint64_t cap, VoxelTable* out)
         if (t.labels) m->mem.release(t.labels, sizeof(int32_t) * cap);
         return DISC_ERR_OOM;
     }
-    CK(cudaMemsetAsync(t.keys, 0xFF, sizeof(unsigned long long) * cap, m->stream));
+    CK(cudaMemsetAsync(t.keys, 0xFF, sizeof(unsigned long long) * cap, st));
     t.mask = cap - 1;
     t.used = m->vt.used;
     *out = t;
@@ -187,41 +340,42 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
     return DISC_OK;
 }
 
-int read_next_id(disc_map* m)
+int read_next_id(disc_map* m, cudaStream_t st)
 {
     int v = 0;
-    cudaMemcpyAsync(&v, m->d_next_id, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
-    cudaStreamSynchronize(m->stream);
+    cudaMemcpyAsync(&v, m->d_next_id, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
     return v;
 }
 
-uint64_t read_used(disc_map* m)
+uint64_t read_used(disc_map* m, cudaStream_t st)
 {
     unsigned long long v = 0;
-    cudaMemcpyAsync(&v, m->vt.used, sizeof(v), cudaMemcpyDeviceToHost, m->stream);
-    cudaStreamSynchronize(m->stream);
+    cudaMemcpyAsync(&v, m->vt.used, sizeof(v), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
     return v;
 }
 
 // Grow the voxel table so that `incoming` more voxels keep the load below
-// max_load.  Uses a host bound first; synchronises only when the bound is hit.
-disc_status ensure_voxel_room(disc_map* m, uint64_t incoming)
+// max_load.  Uses a host bound first; synchronises `st` (the stream the map's
+// kernels run on) only when the bound is hit.
+disc_status ensure_voxel_room(disc_map* m, uint64_t incoming, cudaStream_t st)
 {
     const double lim = (double)m->cfg.max_load * (double)(m->vt.mask + 1);
     if ((double)(m->used_upper + incoming) <= lim) return DISC_OK;
-    CK(cudaStreamSynchronize(m->stream));
-    m->used_upper = read_used(m);
+    CK(cudaStreamSynchronize(st));
+    m->used_upper = read_used(m, st);
     uint64_t cap = m->vt.mask + 1;
     while ((double)(m->used_upper + incoming) > (double)m->cfg.max_load * (double)cap) cap <<= 1;
     if (cap == m->vt.mask + 1) return DISC_OK;
     VoxelTable nt{};
-    disc_status s = alloc_voxel_table(m, cap, &nt);
+    disc_status s = alloc_voxel_table(m, cap, &nt, st);
     if (s != DISC_OK) return s;
-    CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), m->stream));
-    launch_rehash(m->vt, nt, m->d_flag, m->stream);
+    CK(cudaMemsetAsync(m->d_flag, 0, sizeof(int), st));
+    launch_rehash(m->vt, nt, m->d_flag, st);
     int flag = 0;
-    CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(&flag, m->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     if (flag != 0) {
         m->mem.release(nt.keys, sizeof(unsigned long long) * cap);
         m->mem.release(nt.labels, sizeof(int32_t) * cap);
@@ -234,11 +388,11 @@ disc_status ensure_voxel_room(disc_map* m, uint64_t incoming)
     return DISC_OK;
 }
 
-disc_status ensure_instance_room(disc_map* m, int64_t incoming)
+disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
 {
     if (m->next_id_upper + incoming <= m->inst.cap) return DISC_OK;
-    CK(cudaStreamSynchronize(m->stream));
-    m->next_id_upper = read_next_id(m);
+    CK(cudaStreamSynchronize(st));
+    m->next_id_upper = read_next_id(m, st);
     if (m->next_id_upper + incoming <= m->inst.cap) return DISC_OK;
     int cap = m->inst.cap;
     while ((int64_t)cap < m->next_id_upper + incoming) {
@@ -249,12 +403,12 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming)
     disc_status s = alloc_instances(m, cap, &ni);
     if (s != DISC_OK) return s;
     const int n = (int)m->next_id_upper;
-    CK(cudaMemcpyAsync(ni.parent, m->inst.parent, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaMemcpyAsync(ni.count, m->inst.count, sizeof(long long) * n, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaMemcpyAsync(ni.Q, m->inst.Q, sizeof(float) * n, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaMemcpyAsync(ni.E, m->inst.E, sizeof(float) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaMemcpyAsync(ni.n_obs, m->inst.n_obs, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(ni.parent, m->inst.parent, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ni.count, m->inst.count, sizeof(long long) * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ni.Q, m->inst.Q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ni.E, m->inst.E, sizeof(float) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ni.n_obs, m->inst.n_obs, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
     const int oc = m->inst.cap;
     m->mem.release(m->inst.parent, sizeof(int32_t) * oc);
     m->mem.release(m->inst.count, sizeof(long long) * oc);
@@ -265,166 +419,143 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming)
     return DISC_OK;
 }
 
-cudaEvent_t take_event(disc_map* m)
+MapRefs map_refs(const disc_map* m)
 {
-    if (m->ev_used == m->ev_pool.size()) {
+    MapRefs r;
+    r.vt = m->vt;
+    r.inst = m->inst;
+    r.ss = m->ss;
+    r.next_id = m->d_next_id;
+    return r;
+}
+
+// ---- phase timing ----------------------------------------------------------------
+cudaEvent_t take_event(Runner& r)
+{
+    if (r.ev_used == r.ev_pool.size()) {
         cudaEvent_t e = nullptr;
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        m->ev_pool.push_back(e);
+        r.ev_pool.push_back(e);
     }
-    return m->ev_pool[m->ev_used++];
+    return r.ev_pool[r.ev_used++];
 }
 
-// Enqueue one phase; with timing on, bracket it with events on the map's
+// Enqueue one phase; with timing on, bracket it with events on the runner's
 // stream (event-record nodes when the stream is being captured).
 template <class F>
-void run_phase(disc_map* m, int ph, F&& launch)
+void run_phase(Runner& r, int ph, F&& launch)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (m->timing && (a = take_event(m))) cudaEventRecordWithFlags(a, m->stream, cudaEventRecordExternal);
+    if (r.timing && (a = take_event(r))) cudaEventRecordWithFlags(a, r.stream, cudaEventRecordExternal);
     const int n = launch();
-    m->launches += n;
-    m->phase_launches[ph] += n;
-    if (a && (b = take_event(m))) {
-        cudaEventRecordWithFlags(b, m->stream, cudaEventRecordExternal);
-        if (n > 0) m->marks.push_back({ph, a, b});
+    r.launches += n;
+    r.phase_launches[ph] += n;
+    if (a && (b = take_event(r))) {
+        cudaEventRecordWithFlags(b, r.stream, cudaEventRecordExternal);
+        if (n > 0) r.marks.push_back({ph, a, b});
     }
-}
-
-int enqueue_batch_kernels(disc_map* m, int B, bool any_bf16, bool any_f32);
-
-// Timing run of one batch: the sequence with its phase events is captured and
-// launched as one graph, so the device never waits on the host inside a
-// timed interval.  false: capture is not possible here (plain launches).
-bool launch_timed_graph(disc_map* m, int B, bool any_bf16, bool any_f32)
-{
-    const size_t marks0 = m->marks.size(), ev0 = m->ev_used;
-    const int64_t l0 = m->launches;
-    int64_t pl0[PH_COUNT];
-    for (int i = 0; i < PH_COUNT; i++) pl0[i] = m->phase_launches[i];
-    auto undo = [&] {
-        m->marks.resize(marks0);
-        m->ev_used = ev0;
-        m->launches = l0;
-        for (int i = 0; i < PH_COUNT; i++) m->phase_launches[i] = pl0[i];
-        cudaGetLastError();
-    };
-    if (cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        undo();
-        return false;
-    }
-    enqueue_batch_kernels(m, B, any_bf16, any_f32);
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    if (cudaStreamEndCapture(m->stream, &graph) != cudaSuccess || !graph ||
-        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        undo();
-        return false;
-    }
-    cudaGraphDestroy(graph);
-    const bool ok = cudaGraphLaunch(exec, m->stream) == cudaSuccess;
-    cudaGraphExecDestroy(exec);  // freed once the launch completes
-    if (!ok) {
-        undo();
-        return false;
-    }
-    return true;
 }
 
 // After a synchronisation: fold the recorded phase intervals into the totals.
-void collect_timing(disc_map* m)
+void collect_timing(Runner& r)
 {
-    for (auto& mk : m->marks) {
+    for (auto& mk : r.marks) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
-            m->phase_ms[mk.phase] += ms;
-            m->phase_calls[mk.phase] += 1;
+            r.phase_ms[mk.phase] += ms;
+            r.phase_calls[mk.phase] += 1;
         } else {
             cudaGetLastError();
         }
     }
-    m->marks.clear();
-    m->ev_used = 0;
+    r.marks.clear();
+    r.ev_used = 0;
 }
 
-disc_status check_frame(const disc_map* m, const disc_frame* f)
+void reset_timing(Runner& r, bool enable)
 {
-    if (!f || !f->depth || !f->labels || !f->tokens) return DISC_ERR_INVALID_ARG;
-    if (f->width <= 0 || f->height <= 0 || f->width > m->cfg.max_width || f->height > m->cfg.max_height)
-        return DISC_ERR_INVALID_ARG;
-    if (f->num_masks < 0 || f->num_masks > m->cfg.max_masks) return DISC_ERR_INVALID_ARG;
-    if (f->token_dtype != DISC_TOKENS_F32 && f->token_dtype != DISC_TOKENS_BF16) return DISC_ERR_INVALID_ARG;
-    if (!(f->fx != 0.0f) || !(f->fy != 0.0f)) return DISC_ERR_INVALID_ARG;
-    return DISC_OK;
+    collect_timing(r);
+    r.timing = enable;
+    for (int i = 0; i < PH_COUNT; i++) {
+        r.phase_ms[i] = 0.0;
+        r.phase_launches[i] = 0;
+        r.phase_calls[i] = 0;
+    }
 }
 
-// Every kernel of one batch of B frame slots, in order.  Grids follow the
-// map's maxima (frames smaller than that return early in their blocks), and
-// per-frame values are read on the device, so the sequence is the same for
-// every batch of B frames and can be replayed as a CUDA graph.
-int enqueue_batch_kernels(disc_map* m, int B, bool any_bf16, bool any_f32)
+// ---- one batch -------------------------------------------------------------------
+// Every kernel of one batch of S frame slots over G maps (J frames per map at
+// most), in order.  Grids follow the runner's maxima (smaller frames return
+// early in their blocks) and per-frame values and map state are read on the
+// device, so the sequence depends on (S, G, J, token dtypes) only and is
+// replayed as a CUDA graph.
+int enqueue_batch_kernels(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32)
 {
-    const int D = m->D, P = m->P, Mmax = m->cfg.max_masks;
-    const int Hmax = m->cfg.max_height, Wmax = m->cfg.max_width;
-    cudaStream_t st = m->stream;
-    const BatchScratch& bs = m->bs;
-    const FrameParams* dfp = m->d_fps;
-    const int64_t before = m->launches;
-    run_phase(m, PH_CLEAR, [&] { return launch_slot_clear(bs, B, D, m->MM, st); });
-    run_phase(m, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, B, P, D, any_bf16, any_f32, st); });
-    run_phase(m, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, B, m->cfg.patch_h, m->cfg.patch_w, Mmax, st); });
-    run_phase(m, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, B, Mmax, st); });
-    run_phase(m, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, B, P, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(m, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, B, D, Mmax, any_bf16, any_f32, st); });
+    const int D = r.D, P = r.P, Mmax = r.Mmax;
+    cudaStream_t st = r.stream;
+    const BatchScratch& bs = r.bs;
+    const FrameParams* dfp = r.fps();
+    const MapRefs* refs = r.refs();
+    const int64_t before = r.launches;
+    run_phase(r, PH_CLEAR, [&] { return launch_slot_clear(bs, S, D, r.MM, refs, G, st); });
+    run_phase(r, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, S, P, D, any_bf16, any_f32, st); });
+    run_phase(r, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, S, r.Ph, r.Pw, Mmax, st); });
+    run_phase(r, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
+    run_phase(r, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(r, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any_bf16, any_f32, st); });
     if (Mmax > 0) {
-        for (int f0 = 0; f0 < B; f0 += GEOMETRY_CHUNK) {
-            const int nb = std::min(GEOMETRY_CHUNK, B - f0);
-            run_phase(m, PH_BACKPROJECT, [&] { return launch_backproject(dfp, bs, f0, nb, Hmax, Wmax, st); });
-            run_phase(m, PH_ENTRIES, [&] { return launch_entries(dfp, bs, m->vt, f0, nb, Mmax, st); });
+        for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
+            const int nb = std::min(GEOMETRY_CHUNK, S - f0);
+            run_phase(r, PH_BACKPROJECT, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
+            run_phase(r, PH_ENTRIES, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
         }
-        run_phase(m, PH_ENTRIES, [&] { return launch_quality(dfp, bs, B, st); });
+        run_phase(r, PH_ENTRIES, [&] { return launch_quality(dfp, bs, S, st); });
     }
     // error bound of the tensor-core pooled embedding relative to
     // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
     // 3 K products; and of a warp-level fp32 cosine
-    const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * m->Kpad * std::ldexp(1.0, -24));
+    const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * r.Kpad * std::ldexp(1.0, -24));
     const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
-    SerialScratch ss = m->ss;
-    ss.prev_err = m->d_prev_err;
-    for (int j = 0; j < B; j++)
+    SerialStep step;
+    step.refs = refs;
+    step.slot_of = r.slot_of();
+    step.prev_hist = r.prev_hist();
+    step.hist = r.d_hist;
+    step.J = J;
+    for (int j = 0; j < J; j++) {
+        step.j = j;
         for (int ph = 0; ph < 4; ph++)
-            run_phase(m, PH_OVERLAP + ph, [&] {
-                return launch_serial_frame(dfp, bs, j, ss, m->vt, m->inst, m->d_next_id, eta, dot_err, ph, st);
-            });
-    return (int)(m->launches - before);
+            run_phase(r, PH_OVERLAP + ph, [&] { return launch_serial_step(dfp, bs, step, G, eta, dot_err, ph, st); });
+    }
+    return (int)(r.launches - before);
 }
 
-// The batch's kernel sequence captured once per (B, token dtypes) and
-// replayed; tables that move (growth) invalidate the cache.
-disc_status batch_graph(disc_map* m, int B, bool any_bf16, bool any_f32, BatchGraph** out)
+long long graph_key(int S, int G, int J, bool any_bf16, bool any_f32)
 {
-    const int key = B * 4 + (any_bf16 ? 2 : 0) + (any_f32 ? 1 : 0);
-    if (m->graph_vt_keys != m->vt.keys || m->graph_inst_parent != m->inst.parent) {
-        for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
-        m->graphs.clear();
-        m->graph_vt_keys = m->vt.keys;
-        m->graph_inst_parent = m->inst.parent;
-    }
-    auto it = m->graphs.find(key);
-    if (it != m->graphs.end()) {
+    return ((((long long)S << 20) | ((long long)G << 10) | J) << 2) | (any_bf16 ? 2 : 0) | (any_f32 ? 1 : 0);
+}
+
+// The batch's kernel sequence captured once per shape and replayed.
+disc_status batch_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32, BatchGraph** out)
+{
+    const long long key = graph_key(S, G, J, any_bf16, any_f32);
+    auto it = r.graphs.find(key);
+    if (it != r.graphs.end()) {
         *out = &it->second;
         return DISC_OK;
     }
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    const int64_t before = m->launches;
-    const int n = enqueue_batch_kernels(m, B, any_bf16, any_f32);
-    m->launches = before;  // counted when the graph is launched
-    cudaError_t e = cudaStreamEndCapture(m->stream, &graph);
+    CK(cudaStreamBeginCapture(r.stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = r.launches;
+    int64_t pl0[PH_COUNT];
+    for (int i = 0; i < PH_COUNT; i++) pl0[i] = r.phase_launches[i];
+    const int n = enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+    r.launches = before;  // counted when the graph is launched
+    for (int i = 0; i < PH_COUNT; i++) r.phase_launches[i] = pl0[i];
+    cudaError_t e = cudaStreamEndCapture(r.stream, &graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
@@ -438,116 +569,125 @@ disc_status batch_graph(disc_map* m, int B, bool any_bf16, bool any_f32, BatchGr
         cudaGetLastError();
         return DISC_ERR_CUDA;
     }
-    *out = &(m->graphs[key] = g);
+    *out = &(r.graphs[key] = g);
     return DISC_OK;
 }
 
-// Enqueue frames[0..B) (B <= Bmax, all valid) as one batch; counters of frame
-// j are copied to hist[j].  prev: counters of the frame before this batch in
-// the same call (an error there stops this batch), or NULL.
-disc_status enqueue_batch(disc_map* m, const disc_frame* frames, int B, FrameCounters* hist,
-                          const FrameCounters* prev)
+// Timing run of one batch: the sequence with its phase events is captured and
+// launched as one graph, so the device never waits on the host inside a
+// timed interval.  false: capture is not possible here (plain launches).
+bool launch_timed_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32)
 {
-    const int D = m->D, P = m->P;
-    uint64_t px = 0;
-    int64_t masks = 0;
-    bool any_bf16 = false, any_f32 = false;
-    for (int j = 0; j < B; j++) {
-        px += (uint64_t)frames[j].width * frames[j].height;
-        masks += frames[j].num_masks;
-        any_bf16 |= frames[j].token_dtype == DISC_TOKENS_BF16;
-        any_f32 |= frames[j].token_dtype == DISC_TOKENS_F32;
+    const size_t marks0 = r.marks.size(), ev0 = r.ev_used;
+    const int64_t l0 = r.launches;
+    int64_t pl0[PH_COUNT];
+    for (int i = 0; i < PH_COUNT; i++) pl0[i] = r.phase_launches[i];
+    auto undo = [&] {
+        r.marks.resize(marks0);
+        r.ev_used = ev0;
+        r.launches = l0;
+        for (int i = 0; i < PH_COUNT; i++) r.phase_launches[i] = pl0[i];
+        cudaGetLastError();
+    };
+    if (cudaStreamBeginCapture(r.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        undo();
+        return false;
     }
-    disc_status s = ensure_voxel_room(m, px);
-    if (s != DISC_OK) return s;
-    s = ensure_instance_room(m, masks);
-    if (s != DISC_OK) return s;
+    enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamEndCapture(r.stream, &graph) != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        undo();
+        return false;
+    }
+    cudaGraphDestroy(graph);
+    const bool ok = cudaGraphLaunch(exec, r.stream) == cudaSuccess;
+    cudaGraphExecDestroy(exec);  // freed once the launch completes
+    if (!ok) {
+        undo();
+        return false;
+    }
+    return true;
+}
 
-    std::vector<FrameParams> fps(B);
-    for (int j = 0; j < B; j++) {
-        const disc_frame* f = frames + j;
-        FrameParams& fp = fps[j];
-        fp.H = f->height;
-        fp.W = f->width;
-        fp.M = f->num_masks;
-        fp.P = P;
-        fp.D = D;
-        fp.Ph = m->cfg.patch_h;
-        fp.Pw = m->cfg.patch_w;
-        fp.Kpad = m->Kpad;
-        fp.Npad = std::max(16, (fp.M + 15) / 16 * 16);
-        fp.fx = f->fx;
-        fp.fy = f->fy;
-        fp.cx = f->cx;
-        fp.cy = f->cy;
-        for (int r = 0; r < 3; r++) {
-            for (int c = 0; c < 3; c++) fp.R[3 * r + c] = (float)f->T_world_cam[4 * r + c];
-            fp.t[r] = (float)f->T_world_cam[4 * r + 3];
-        }
-        fp.voxel = m->cfg.voxel_size;
-        // reciprocals rounded once to fp32 (host fp32 division is IEEE)
-        fp.inv_fx = 1.0f / f->fx;
-        fp.inv_fy = 1.0f / f->fy;
-        fp.inv_voxel = 1.0f / m->cfg.voxel_size;
-        fp.z_min = m->cfg.z_min;
-        fp.z_max = m->cfg.z_max;
-        fp.eps = m->cfg.eps;
-        fp.tau = m->cfg.tau_cos;
-        fp.lambda_size = m->cfg.lambda_size;
-        fp.ov_num = m->cfg.ov_num;
-        fp.ov_den = m->cfg.ov_den;
-        fp.min_px = std::max(1, m->cfg.min_mask_pixels);
-        fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
-        const size_t npx = (size_t)fp.H * fp.W;
-        const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
-        if (f->inputs_on_device) {
-            fp.depth = f->depth;
-            fp.labels = f->labels;
-            fp.tokens = f->tokens;
-            fp.gembed = f->global_embed;
-        } else {
-            float* dd = m->d_depth + (size_t)j * m->px_cap;
-            uint16_t* dl = m->d_labels + (size_t)j * m->px_cap;
-            unsigned char* dt = m->d_tokens + (size_t)j * P * D * 4;
-            CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, m->stream));
-            CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, m->stream));
-            CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, m->stream));
-            fp.depth = dd;
-            fp.labels = dl;
-            fp.tokens = dt;
-            fp.gembed = nullptr;
-            if (f->global_embed) {
-                float* dg = m->d_gembed + (size_t)j * D;
-                CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, m->stream));
-                fp.gembed = dg;
-            }
-        }
-    }
-    // pageable source: the call returns once the parameters are staged
-    CK(cudaMemcpyAsync(m->d_fps, fps.data(), sizeof(FrameParams) * B, cudaMemcpyHostToDevice, m->stream));
-    // status of the frame before this batch (0 when it is the first of the call)
-    if (prev) CK(cudaMemcpyAsync(m->d_prev_err, &prev->err, sizeof(int), cudaMemcpyDeviceToDevice, m->stream));
-    else CK(cudaMemsetAsync(m->d_prev_err, 0, sizeof(int), m->stream));
+disc_status check_frame(const disc_map* m, const Runner& r, const disc_frame* f)
+{
+    if (!f || !f->depth || !f->labels || !f->tokens) return DISC_ERR_INVALID_ARG;
+    if (f->width <= 0 || f->height <= 0 || f->width > m->cfg.max_width || f->height > m->cfg.max_height)
+        return DISC_ERR_INVALID_ARG;
+    if (f->width > r.Wmax || f->height > r.Hmax || (int64_t)f->width * f->height > (int64_t)r.px_cap)
+        return DISC_ERR_INVALID_ARG;
+    if (f->num_masks < 0 || f->num_masks > m->cfg.max_masks || f->num_masks > r.Mmax) return DISC_ERR_INVALID_ARG;
+    if (f->token_dtype != DISC_TOKENS_F32 && f->token_dtype != DISC_TOKENS_BF16) return DISC_ERR_INVALID_ARG;
+    if (!(f->fx != 0.0f) || !(f->fy != 0.0f)) return DISC_ERR_INVALID_ARG;
+    return DISC_OK;
+}
 
-    BatchGraph* g = nullptr;
-    if (!m->timing && !m->graphs_off && batch_graph(m, B, any_bf16, any_f32, &g) != DISC_OK) {
-        m->graphs_off = true;  // this stream or driver cannot capture the sequence
-        g = nullptr;
+// Frame parameters of frame f of map m in slot `slot` (map position g); host
+// inputs are staged into the slot's buffers.
+disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int slot, int g, FrameParams* out)
+{
+    const int P = r.P, D = r.D;
+    FrameParams fp{};
+    fp.H = f->height;
+    fp.W = f->width;
+    fp.M = f->num_masks;
+    fp.P = P;
+    fp.D = D;
+    fp.Ph = r.Ph;
+    fp.Pw = r.Pw;
+    fp.Kpad = r.Kpad;
+    fp.Npad = std::max(16, (fp.M + 15) / 16 * 16);
+    fp.fx = f->fx;
+    fp.fy = f->fy;
+    fp.cx = f->cx;
+    fp.cy = f->cy;
+    for (int i = 0; i < 3; i++) {
+        for (int c = 0; c < 3; c++) fp.R[3 * i + c] = (float)f->T_world_cam[4 * i + c];
+        fp.t[i] = (float)f->T_world_cam[4 * i + 3];
     }
-    if (g) {
-        CK(cudaGraphLaunch(g->exec, m->stream));
-        m->launches += g->kernels;
-    } else if (!(m->timing && !m->graphs_off && launch_timed_graph(m, B, any_bf16, any_f32))) {
-        enqueue_batch_kernels(m, B, any_bf16, any_f32);
+    fp.voxel = m->cfg.voxel_size;
+    // reciprocals rounded once to fp32 (host fp32 division is IEEE)
+    fp.inv_fx = 1.0f / f->fx;
+    fp.inv_fy = 1.0f / f->fy;
+    fp.inv_voxel = 1.0f / m->cfg.voxel_size;
+    fp.z_min = m->cfg.z_min;
+    fp.z_max = m->cfg.z_max;
+    fp.eps = m->cfg.eps;
+    fp.tau = m->cfg.tau_cos;
+    fp.lambda_size = m->cfg.lambda_size;
+    fp.ov_num = m->cfg.ov_num;
+    fp.ov_den = m->cfg.ov_den;
+    fp.min_px = std::max(1, m->cfg.min_mask_pixels);
+    fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
+    fp.map = g;
+    const size_t npx = (size_t)fp.H * fp.W;
+    const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
+    if (f->inputs_on_device) {
+        fp.depth = f->depth;
+        fp.labels = f->labels;
+        fp.tokens = f->tokens;
+        fp.gembed = f->global_embed;
+    } else {
+        float* dd = r.d_depth + (size_t)slot * r.px_cap;
+        uint16_t* dl = r.d_labels + (size_t)slot * r.px_cap;
+        unsigned char* dt = r.d_tokens + (size_t)slot * P * D * 4;
+        CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, r.stream));
+        CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, r.stream));
+        CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, r.stream));
+        fp.depth = dd;
+        fp.labels = dl;
+        fp.tokens = dt;
+        fp.gembed = nullptr;
+        if (f->global_embed) {
+            float* dg = r.d_gembed + (size_t)slot * D;
+            CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, r.stream));
+            fp.gembed = dg;
+        }
     }
-    // the batch's counters, in slot order, to the call's history
-    CK(cudaMemcpyAsync(hist, m->bs.base.ctr, sizeof(FrameCounters) * B, cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaGetLastError());
-    m->used_upper += px;
-    m->next_id_upper += masks;
-    m->last_slot = B - 1;
-    m->last_M = frames[B - 1].num_masks;
-    m->have_frame = true;
+    *out = fp;
     return DISC_OK;
 }
 
@@ -567,59 +707,182 @@ void to_stats(const FrameCounters& c, disc_frame_stats* s)
     s->status = c.err;
 }
 
-disc_status ensure_hist(disc_map* m, int n)
+// The frames one call integrates into one map.
+struct Work {
+    disc_map* m = nullptr;
+    const disc_frame* frames = nullptr;
+    int n = 0;                        // frames asked for
+    int valid = 0;                    // leading frames that pass the host checks
+    disc_frame_stats* stats = nullptr;
+    int done = 0;                     // frames integrated
+    disc_status status = DISC_OK;     // first failure of this map
+    std::vector<int> hist_idx;        // counters of each enqueued frame in the call's history
+};
+
+// Integrate every map's frames: batch b holds frames [b*J, (b+1)*J) of each
+// map; the maps of a batch run side by side, each map's frames in order.  A
+// frame that fails stops the later frames of its map (on the device), not
+// those of the other maps.  Returns the first status that is not DISC_OK.
+disc_status run_call(Runner& r, std::vector<Work>& w)
 {
-    if (n <= m->hist_cap) return DISC_OK;
-    if (m->d_hist) m->mem.release(m->d_hist, sizeof(FrameCounters) * m->hist_cap);
-    m->d_hist = m->mem.get<FrameCounters>(n);
-    if (m->mem.failed) {
-        m->mem.failed = false;
-        m->hist_cap = 0;
-        m->d_hist = nullptr;
-        return DISC_ERR_OOM;
+    int total = 0, nbatch = 0;
+    for (Work& wk : w) {
+        wk.valid = 0;
+        while (wk.valid < wk.n && check_frame(wk.m, r, wk.frames + wk.valid) == DISC_OK) wk.valid++;
+        total += wk.valid;
+        nbatch = std::max(nbatch, (wk.valid + r.Jmax - 1) / r.Jmax);
     }
-    m->hist_cap = n;
+    disc_status s = ensure_hist(r, std::max(total, 1));
+    if (s != DISC_OK) return s;
+    std::vector<unsigned char> blk(r.param_bytes);
+    int hoff = 0;
+    for (int b = 0; b < nbatch && s == DISC_OK; b++) {
+        const int lo = b * r.Jmax;
+        std::vector<int> gl;  // works with frames in this batch
+        int J = 0, S = 0;
+        for (int i = 0; i < (int)w.size(); i++) {
+            const int cnt = std::min(r.Jmax, w[i].valid - lo);
+            if (cnt <= 0) continue;
+            gl.push_back(i);
+            J = std::max(J, cnt);
+            S += cnt;
+        }
+        const int G = (int)gl.size();
+        if (G == 0) break;
+        bool any_bf16 = false, any_f32 = false;
+        for (int gi = 0; gi < G && s == DISC_OK; gi++) {
+            Work& wk = w[gl[gi]];
+            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            uint64_t px = 0;
+            int64_t masks = 0;
+            for (int j = 0; j < cnt; j++) {
+                const disc_frame& f = wk.frames[lo + j];
+                px += (uint64_t)f.width * f.height;
+                masks += f.num_masks;
+                any_bf16 |= f.token_dtype == DISC_TOKENS_BF16;
+                any_f32 |= f.token_dtype == DISC_TOKENS_F32;
+            }
+            s = ensure_voxel_room(wk.m, px, r.stream);
+            if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, r.stream);
+        }
+        if (s != DISC_OK) break;
+        std::fill(blk.begin(), blk.end(), 0);
+        FrameParams* hfp = (FrameParams*)blk.data();
+        MapRefs* hrefs = (MapRefs*)(blk.data() + r.off_refs);
+        int* hslot = (int*)(blk.data() + r.off_slot);
+        int* hprev = (int*)(blk.data() + r.off_prev);
+        int slot = 0;
+        for (int gi = 0; gi < G && s == DISC_OK; gi++) {
+            Work& wk = w[gl[gi]];
+            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            hrefs[gi] = map_refs(wk.m);
+            hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
+            for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
+            for (int j = 0; j < cnt && s == DISC_OK; j++) {
+                s = frame_params(r, wk.m, wk.frames + lo + j, slot, gi, hfp + slot);
+                hslot[gi * J + j] = slot;
+                wk.hist_idx.push_back(hoff + slot);
+                slot++;
+            }
+        }
+        if (s != DISC_OK) break;
+        // pageable source: the call returns once the block is staged
+        s = cuda_status(cudaMemcpyAsync(r.d_param, blk.data(), r.param_bytes, cudaMemcpyHostToDevice, r.stream));
+        if (s != DISC_OK) break;
+        BatchGraph* g = nullptr;
+        if (!r.timing && !r.graphs_off && batch_graph(r, S, G, J, any_bf16, any_f32, &g) != DISC_OK) {
+            r.graphs_off = true;  // this stream or driver cannot capture the sequence
+            g = nullptr;
+        }
+        if (g) {
+            s = cuda_status(cudaGraphLaunch(g->exec, r.stream));
+            r.launches += g->kernels;
+        } else if (!(r.timing && !r.graphs_off && launch_timed_graph(r, S, G, J, any_bf16, any_f32))) {
+            enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+        }
+        // the batch's counters, in slot order, to the call's history
+        if (s == DISC_OK)
+            s = cuda_status(cudaMemcpyAsync(r.d_hist + hoff, r.bs.base.ctr, sizeof(FrameCounters) * S,
+                                            cudaMemcpyDeviceToDevice, r.stream));
+        if (s == DISC_OK) s = cuda_status(cudaGetLastError());
+        for (int gi = 0; gi < G; gi++) {
+            Work& wk = w[gl[gi]];
+            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            for (int j = 0; j < cnt; j++) {
+                const disc_frame& f = wk.frames[lo + j];
+                wk.m->used_upper += (uint64_t)f.width * f.height;
+                wk.m->next_id_upper += f.num_masks;
+            }
+        }
+        r.last_slot = S - 1;
+        const Work& wl = w[gl[G - 1]];
+        r.last_M = wl.frames[lo + std::min(r.Jmax, wl.valid - lo) - 1].num_masks;
+        r.have_frame = true;
+        hoff += S;
+    }
+    std::vector<FrameCounters> c(std::max(hoff, 1));
+    if (hoff > 0) {
+        disc_status s2 = cuda_status(
+            cudaMemcpyAsync(c.data(), r.d_hist, sizeof(FrameCounters) * hoff, cudaMemcpyDeviceToHost, r.stream));
+        if (s == DISC_OK) s = s2;
+    }
+    disc_status s3 = cuda_status(cudaStreamSynchronize(r.stream));
+    if (s == DISC_OK) s = s3;
+    collect_timing(r);
+    disc_status first = s;
+    for (Work& wk : w) {
+        int exact_next_id = -1;  // frames without masks skip the kernel that records it
+        wk.done = 0;
+        wk.status = DISC_OK;
+        for (size_t i = 0; i < wk.hist_idx.size() && hoff > 0; i++) {
+            const FrameCounters& fc = c[wk.hist_idx[i]];
+            if (wk.stats) to_stats(fc, wk.stats + i);
+            if (wk.status != DISC_OK) continue;
+            if (fc.err != 0) {
+                wk.status = (disc_status)fc.err;
+                continue;
+            }
+            exact_next_id = std::max(exact_next_id, fc.next_id);
+            wk.done++;
+        }
+        if (exact_next_id > 0) wk.m->next_id_upper = std::max<int64_t>(exact_next_id, 0);
+        if (wk.status == DISC_OK && wk.valid < wk.n && wk.done == wk.valid) wk.status = DISC_ERR_INVALID_ARG;
+        if (wk.status == DISC_OK && s != DISC_OK && wk.done < wk.valid) wk.status = s;
+        if (first == DISC_OK) first = wk.status;
+    }
+    return first;
+}
+
+// the map's own runner, created on first use
+disc_status map_runner(disc_map* m)
+{
+    if (m->run) return DISC_OK;
+    Runner* r = new Runner();
+    disc_status s = runner_init(*r, m->cfg.device, m->stream, m->D, m->cfg.patch_h, m->cfg.patch_w,
+                                m->cfg.max_height, m->cfg.max_width, m->cfg.max_masks, 1, m->cfg.batch_frames);
+    if (s != DISC_OK) {
+        runner_release(*r);
+        delete r;
+        return s;
+    }
+    r->timing = m->timing_wanted;
+    m->run = r;
     return DISC_OK;
 }
 
-// Integrate frames[0..n): batches of Bmax; stops at the first invalid frame
-// (host check) or the first frame that fails on the device.
 disc_status integrate(disc_map* m, const disc_frame* frames, int n, disc_frame_stats* stats, int* n_done)
 {
     if (n_done) *n_done = 0;
-    disc_status s = ensure_hist(m, std::max(n, 1));
+    disc_status s = map_runner(m);
     if (s != DISC_OK) return s;
-    int valid = 0;
-    while (valid < n && check_frame(m, frames + valid) == DISC_OK) valid++;
-    int enq = 0;
-    for (int lo = 0; lo < valid; lo += m->Bmax) {
-        const int B = std::min(m->Bmax, valid - lo);
-        s = enqueue_batch(m, frames + lo, B, m->d_hist + lo, lo > 0 ? m->d_hist + lo - 1 : nullptr);
-        if (s != DISC_OK) break;
-        enq += B;
-    }
-    std::vector<FrameCounters> c(std::max(enq, 1));
-    if (enq > 0) CK(cudaMemcpyAsync(c.data(), m->d_hist, sizeof(FrameCounters) * enq, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    collect_timing(m);
-    int done = 0;
-    disc_status fs = DISC_OK;
-    int exact_next_id = -1;  // frames without masks skip the kernel that records it
-    for (int i = 0; i < enq; i++) {
-        if (stats) to_stats(c[i], stats + i);
-        if (c[i].err != 0) {
-            fs = (disc_status)c[i].err;
-            break;
-        }
-        exact_next_id = std::max(exact_next_id, c[i].next_id);
-        done++;
-    }
-    if (exact_next_id > 0) m->next_id_upper = std::max<int64_t>(exact_next_id, 0);
-    if (n_done) *n_done = done;
-    if (fs != DISC_OK) return fs;
-    if (s != DISC_OK) return s;
-    if (valid < n) return DISC_ERR_INVALID_ARG;
-    return DISC_OK;
+    std::vector<Work> w(1);
+    w[0].m = m;
+    w[0].frames = frames;
+    w[0].n = n;
+    w[0].stats = stats;
+    s = run_call(*m->run, w);
+    if (n_done) *n_done = w[0].done;
+    return s;
 }
 
 }  // namespace
@@ -665,16 +928,15 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
         return DISC_ERR_CUDA;
     }
     CK(cudaSetDevice(cfg->device));
+    if (set_kernel_attrs() != DISC_OK) return DISC_ERR_CUDA;
     disc_map* m = new disc_map();
     m->cfg = *cfg;
     m->cfg.voxel_capacity = (int64_t)next_pow2((uint64_t)cfg->voxel_capacity);
     if (m->cfg.batch_frames == 0) m->cfg.batch_frames = 32;
-    m->Bmax = m->cfg.batch_frames;
     m->D = cfg->embed_dim;
     m->P = cfg->patch_h * cfg->patch_w;
     m->Kpad = (m->P + GEMM_KC - 1) / GEMM_KC * GEMM_KC;
     m->MM = std::max(1, cfg->max_masks);
-    m->Npad_max = std::max(16, (m->MM + 15) / 16 * 16);
     if (cfg->cuda_stream) {
         m->stream = (cudaStream_t)cfg->cuda_stream;
     } else {
@@ -685,66 +947,12 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
         }
         m->own_stream = true;
     }
-    static bool attrs_set = false;
-    if (!attrs_set) {
-        cudaError_t e = set_feature_kernel_attrs(200 * 1024);
-        if (e == cudaSuccess) e = set_gemm_kernel_attrs();
-        if (e == cudaSuccess) e = set_serial_kernel_attrs();
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            if (m->own_stream) cudaStreamDestroy(m->stream);
-            delete m;
-            return DISC_ERR_CUDA;
-        }
-        attrs_set = true;
-    }
-    const int D = m->D, P = m->P, MM = m->MM, B = m->Bmax;
     const uint64_t npx = (uint64_t)cfg->max_width * cfg->max_height;
     const uint64_t scap = next_pow2(npx + npx / 2);  // per-frame hashes: load <= 2/3
-    m->px_cap = npx;
     DevAlloc& a = m->mem;
     m->vt.used = a.get<unsigned long long>(1);
     m->d_next_id = a.get<int>(1);
     m->d_flag = a.get<int>(1);
-    m->d_prev_err = a.get<int>(1);
-    m->d_fps = a.get<FrameParams>(B);
-    BatchScratch& bs = m->bs;
-    bs.sD = D;
-    bs.sP = P;
-    bs.sMM = MM;
-    bs.sMMP = (long long)MM * P;
-    bs.sW = (long long)m->Npad_max * m->Kpad;
-    bs.sMMD = (long long)MM * D;
-    bs.sS = 5LL * MM;
-    bs.scap = (long long)scap;
-    Scratch& sc = bs.base;
-    sc.sumF = a.get<long long>((size_t)B * D);
-    sc.fbar = a.get<float>((size_t)B * D);
-    sc.gvec = a.get<float>((size_t)B * D);
-    sc.gg = a.get<long long>(B);
-    sc.nsum = a.get<long long>(B);
-    sc.dotg = a.get<long long>((size_t)B * P);
-    sc.ffp = a.get<long long>((size_t)B * P);
-    sc.nrm = a.get<float>((size_t)B * P);
-    sc.Dp = a.get<float>((size_t)B * P);
-    sc.cosg = a.get<float>((size_t)B * P);
-    sc.fnorm = a.get<float>((size_t)B * P);
-    sc.cov = a.get<int32_t>((size_t)B * MM * P);
-    sc.npix = a.get<int32_t>((size_t)B * MM);
-    sc.W = a.get<float>((size_t)B * bs.sW);
-    sc.S = a.get<float>((size_t)B * 5 * MM);
-    sc.Bm = a.get<float>((size_t)B * MM);
-    sc.Ecan = a.get<float>((size_t)B * MM * D);
-    sc.Efast = a.get<float>((size_t)B * MM * D);
-    sc.ang = a.get<long long>((size_t)B * MM);
-    sc.nvox = a.get<int32_t>((size_t)B * MM);
-    sc.segrep = a.get<int32_t>((size_t)B * MM);
-    sc.sslot = a.get<SegSlot>((size_t)B * scap);
-    sc.sent = a.get<unsigned long long>((size_t)B * scap);
-    sc.slist = a.get<int32_t>((size_t)B * scap);
-    sc.elab = a.get<int32_t>((size_t)B * scap);
-    sc.smask = scap - 1;
-    sc.ctr = a.get<FrameCounters>(B);
     SerialScratch& ss = m->ss;
     ss.okeys = a.get<unsigned long long>(scap);
     ss.ocnt = a.get<int32_t>(scap);
@@ -762,16 +970,11 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     ss.copy_dst = a.get<int32_t>(ss.copy_cap);
     ss.copy_src = a.get<int32_t>(ss.copy_cap);
     ss.copy_n = a.get<int32_t>(1);
-    ss.prev_err = nullptr;
-    m->d_depth = a.get<float>((size_t)B * npx);
-    m->d_labels = a.get<uint16_t>((size_t)B * npx);
-    m->d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
-    m->d_gembed = a.get<float>((size_t)B * D);
     disc_status st = DISC_OK;
     if (a.failed) st = DISC_ERR_OOM;
     if (st == DISC_OK) {
         VoxelTable vt{};
-        st = alloc_voxel_table(m, (uint64_t)m->cfg.voxel_capacity, &vt);
+        st = alloc_voxel_table(m, (uint64_t)m->cfg.voxel_capacity, &vt, m->stream);
         if (st == DISC_OK) m->vt = vt;
     }
     if (st == DISC_OK) st = alloc_instances(m, cfg->instance_capacity, &m->inst);
@@ -779,18 +982,12 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
         cudaStream_t s = m->stream;
         cudaMemsetAsync(m->vt.used, 0, sizeof(unsigned long long), s);
         cudaMemsetAsync(m->d_next_id, 0, sizeof(int), s);
-        cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s);
-        cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s);
-        cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s);
-        cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s);
         cudaMemsetAsync(ss.okeys, 0xFF, sizeof(unsigned long long) * scap, s);
         cudaMemsetAsync(ss.ocnt, 0, sizeof(int32_t) * scap, s);
         cudaMemsetAsync(ss.nkeys, 0xFF, sizeof(unsigned long long) * scap, s);
         cudaMemsetAsync(ss.nown, 0x7F, sizeof(int32_t) * scap, s);  // large positive sentinel
         cudaMemsetAsync(ss.edge_n, 0, sizeof(int32_t), s);
         cudaMemsetAsync(ss.copy_n, 0, sizeof(int32_t), s);
-        cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s);
-        cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s);
         st = cuda_status(cudaStreamSynchronize(s));
     }
     if (st != DISC_OK) {
@@ -809,8 +1006,10 @@ void disc_map_destroy(disc_map* m)
     if (!m) return;
     cudaSetDevice(m->cfg.device);
     cudaStreamSynchronize(m->stream);
-    for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
-    for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (m->run) {
+        runner_release(*m->run);
+        delete m->run;
+    }
     m->mem.free_all();
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -820,8 +1019,6 @@ disc_status disc_integrate_frame(disc_map* m, const disc_frame* f, disc_frame_st
 {
     if (!m || !f) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
-    disc_status s = check_frame(m, f);
-    if (s != DISC_OK) return s;
     return integrate(m, f, 1, stats, nullptr);
 }
 
@@ -840,11 +1037,15 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
     if (!m || !r) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
-    const int M = m->have_frame ? m->last_M : 0, P = m->P, D = m->D;
-    const Scratch sc = m->bs.frame(m->last_slot);
+    const Runner* run = m->run;
+    const bool have = run && run->have_frame;
+    const int M = have ? run->last_M : 0, P = m->P, D = m->D;
+    r->num_masks = M;
+    r->n_seg = 0;
+    if (!have) return DISC_OK;
+    const Scratch sc = run->bs.frame(run->last_slot);
     FrameCounters c{};
     CK(cudaMemcpy(&c, sc.ctr, sizeof(c), cudaMemcpyDeviceToHost));
-    r->num_masks = M;
     if (r->fbar) CK(cudaMemcpy(r->fbar, sc.fbar, sizeof(float) * D, cudaMemcpyDeviceToHost));
     if (r->Dp) CK(cudaMemcpy(r->Dp, sc.Dp, sizeof(float) * P, cudaMemcpyDeviceToHost));
     if (r->cosg) CK(cudaMemcpy(r->cosg, sc.cosg, sizeof(float) * P, cudaMemcpyDeviceToHost));
@@ -875,13 +1076,141 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
     return DISC_OK;
 }
 
+// ---- groups of maps --------------------------------------------------------------------
+void disc_group_config_default(disc_group_config* c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->max_maps = 16;
+    c->frames_per_map = 4;
+    c->embed_dim = 768;
+    c->patch_h = 24;
+    c->patch_w = 24;
+    c->max_width = 640;
+    c->max_height = 480;
+    c->max_masks = 40;
+    c->cuda_stream = nullptr;
+    c->device = 0;
+}
+
+disc_status disc_group_create(const disc_group_config* cfg, disc_group** out)
+{
+    if (!cfg || !out) return DISC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const disc_group_config& c = *cfg;
+    if (c.max_maps <= 0 || c.max_maps > 1024 || c.frames_per_map <= 0 || c.frames_per_map > 256 ||
+        (int64_t)c.max_maps * c.frames_per_map > 4096)
+        return DISC_ERR_INVALID_ARG;
+    if (c.embed_dim <= 0 || c.embed_dim > 4096 || c.patch_h <= 0 || c.patch_w <= 0 ||
+        (int64_t)c.patch_h * c.patch_w > 16384)
+        return DISC_ERR_INVALID_ARG;
+    if (c.max_width <= 0 || c.max_height <= 0 || (int64_t)c.max_width * c.max_height > (1 << 24))
+        return DISC_ERR_INVALID_ARG;
+    if (c.max_masks < 0 || c.max_masks > MAX_MASKS || coverage_smem_bytes(c.max_masks, c.patch_w) > 200 * 1024)
+        return DISC_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return DISC_ERR_CUDA;
+    }
+    CK(cudaSetDevice(c.device));
+    if (set_kernel_attrs() != DISC_OK) return DISC_ERR_CUDA;
+    disc_group* g = new disc_group();
+    g->cfg = c;
+    cudaStream_t st = (cudaStream_t)c.cuda_stream;
+    if (!st) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            return DISC_ERR_CUDA;
+        }
+        g->own_stream = true;
+    }
+    disc_status s = runner_init(g->run, c.device, st, c.embed_dim, c.patch_h, c.patch_w, c.max_height,
+                                c.max_width, c.max_masks, c.max_maps, c.frames_per_map);
+    if (s != DISC_OK) {
+        runner_release(g->run);
+        if (g->own_stream) cudaStreamDestroy(st);
+        delete g;
+        return s;
+    }
+    *out = g;
+    return DISC_OK;
+}
+
+disc_status disc_group_integrate(disc_group* g, disc_map* const* maps, int32_t n_maps,
+                                 const disc_frame* const* frames, const int32_t* counts,
+                                 disc_frame_stats* const* stats, int32_t* n_done)
+{
+    if (!g || n_maps < 0 || n_maps > g->cfg.max_maps || (n_maps > 0 && (!maps || !frames || !counts)))
+        return DISC_ERR_INVALID_ARG;
+    if (n_done)
+        for (int i = 0; i < n_maps; i++) n_done[i] = 0;
+    std::vector<Work> w(n_maps);
+    for (int i = 0; i < n_maps; i++) {
+        disc_map* m = maps[i];
+        if (!m || counts[i] < 0 || (counts[i] > 0 && !frames[i])) return DISC_ERR_INVALID_ARG;
+        if (m->cfg.device != g->cfg.device || m->D != g->cfg.embed_dim || m->cfg.patch_h != g->cfg.patch_h ||
+            m->cfg.patch_w != g->cfg.patch_w)
+            return DISC_ERR_INVALID_ARG;
+        for (int k = 0; k < i; k++)
+            if (maps[k] == m) return DISC_ERR_INVALID_ARG;  // one entry per map
+        w[i].m = m;
+        w[i].frames = frames[i];
+        w[i].n = counts[i];
+        w[i].stats = stats ? stats[i] : nullptr;
+    }
+    if (n_maps == 0) return DISC_OK;
+    CK(cudaSetDevice(g->cfg.device));
+    // the maps' own streams may still hold work of earlier calls
+    for (int i = 0; i < n_maps; i++) CK(cudaStreamSynchronize(maps[i]->stream));
+    disc_status s = run_call(g->run, w);
+    if (n_done)
+        for (int i = 0; i < n_maps; i++) n_done[i] = w[i].done;
+    return s;
+}
+
+void disc_group_destroy(disc_group* g)
+{
+    if (!g) return;
+    cudaSetDevice(g->cfg.device);
+    cudaStream_t st = g->run.stream;
+    runner_release(g->run);
+    if (g->own_stream) cudaStreamDestroy(st);
+    delete g;
+}
+
+int64_t disc_group_kernel_launches(disc_group* g) { return g ? g->run.launches : 0; }
+
+int64_t disc_group_device_bytes(disc_group* g) { return g ? g->run.mem.bytes : 0; }
+
+disc_status disc_group_set_phase_timing(disc_group* g, int32_t enable)
+{
+    if (!g) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(g->cfg.device));
+    CK(cudaStreamSynchronize(g->run.stream));
+    reset_timing(g->run, enable != 0);
+    return DISC_OK;
+}
+
+disc_status disc_group_phase_times(disc_group* g, double* ms, int64_t* launches, int64_t* calls, int32_t n)
+{
+    if (!g || n < 0) return DISC_ERR_INVALID_ARG;
+    for (int i = 0; i < n && i < PH_COUNT; i++) {
+        if (ms) ms[i] = g->run.phase_ms[i];
+        if (launches) launches[i] = g->run.phase_launches[i];
+        if (calls) calls[i] = g->run.phase_calls[i];
+    }
+    return DISC_OK;
+}
+
 disc_status disc_map_counts(disc_map* m, int64_t* nv, int32_t* nid)
 {
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
-    if (nv) *nv = (int64_t)read_used(m);
-    if (nid) *nid = read_next_id(m);
+    if (nv) *nv = (int64_t)read_used(m, m->stream);
+    if (nid) *nid = read_next_id(m, m->stream);
     return DISC_OK;
 }
 
@@ -893,7 +1222,7 @@ disc_status disc_map_export_voxels(disc_map* m, uint64_t* keys, int32_t* ids, in
     const uint64_t tc = m->vt.mask + 1;
     std::vector<unsigned long long> k(tc);
     std::vector<int32_t> l(tc);
-    const int nid = read_next_id(m);
+    const int nid = read_next_id(m, m->stream);
     std::vector<int32_t> parent(std::max(nid, 1));
     CK(cudaMemcpy(k.data(), m->vt.keys, sizeof(unsigned long long) * tc, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(l.data(), m->vt.labels, sizeof(int32_t) * tc, cudaMemcpyDeviceToHost));
@@ -916,7 +1245,7 @@ disc_status disc_map_export_instances(disc_map* m, int32_t* parent, int64_t* cou
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
-    const int n = read_next_id(m);
+    const int n = read_next_id(m, m->stream);
     if (n > cap) return DISC_ERR_INVALID_ARG;
     if (n == 0) return DISC_OK;
     if (parent) CK(cudaMemcpy(parent, m->inst.parent, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
@@ -933,7 +1262,7 @@ disc_status disc_query_topk(disc_map* m, const float* q, int32_t nq, int32_t k, 
     if (nq == 0) return DISC_OK;
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
-    const int nid = read_next_id(m);
+    const int nid = read_next_id(m, m->stream);
     const int D = m->D;
     if (nid == 0) {
         for (int64_t i = 0; i < (int64_t)nq * k; i++) {
@@ -1109,22 +1438,17 @@ uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz)
            ((uint64_t)(kz + KEY_BIAS) & mask);
 }
 
-int64_t disc_map_device_bytes(disc_map* m) { return m ? m->mem.bytes : 0; }
+int64_t disc_map_device_bytes(disc_map* m) { return m ? m->mem.bytes + (m->run ? m->run->mem.bytes : 0) : 0; }
 
-int64_t disc_map_kernel_launches(disc_map* m) { return m ? m->launches : 0; }
+int64_t disc_map_kernel_launches(disc_map* m) { return m && m->run ? m->run->launches : 0; }
 
 disc_status disc_map_set_phase_timing(disc_map* m, int32_t enable)
 {
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
     CK(cudaStreamSynchronize(m->stream));
-    collect_timing(m);
-    m->timing = enable != 0;
-    for (int i = 0; i < PH_COUNT; i++) {
-        m->phase_ms[i] = 0.0;
-        m->phase_launches[i] = 0;
-        m->phase_calls[i] = 0;
-    }
+    m->timing_wanted = enable != 0;
+    if (m->run) reset_timing(*m->run, enable != 0);
     return DISC_OK;
 }
 
@@ -1132,9 +1456,9 @@ disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int
 {
     if (!m || n < 0) return DISC_ERR_INVALID_ARG;
     for (int i = 0; i < n && i < PH_COUNT; i++) {
-        if (ms) ms[i] = m->phase_ms[i];
-        if (launches) launches[i] = m->phase_launches[i];
-        if (calls) calls[i] = m->phase_calls[i];
+        if (ms) ms[i] = m->run ? m->run->phase_ms[i] : 0.0;
+        if (launches) launches[i] = m->run ? m->run->phase_launches[i] : 0;
+        if (calls) calls[i] = m->run ? m->run->phase_calls[i] : 0;
     }
     return DISC_OK;
 }

@@ -220,7 +220,27 @@ struct SerialScratch {
     int32_t* copy_src;          // >= 0 instance id, < 0: segment -(m+1)
     int32_t* copy_n;            // [1]
     int32_t copy_cap;
-    const int* prev_err;        // status of the frame before slot 0 in this call (0 for the first)
+};
+
+// Everything the kernels need of one map's resident state.  A batch holds an
+// array of these in device memory (one per map of the batch), so captured
+// launch sequences stay valid when a map's tables grow.
+struct MapRefs {
+    VoxelTable vt;
+    Instances inst;
+    SerialScratch ss;
+    int* next_id;               // [1] next unused instance id
+};
+
+// One step of the serial part over the maps of a batch: block row g runs the
+// j-th frame of map g.
+struct SerialStep {
+    const MapRefs* refs;        // [G]
+    const int* slot_of;         // [G * J] frame slot of frame j of map g, -1: none
+    const int* prev_hist;       // [G] index in hist of the frame before this batch, -1: none
+    const FrameCounters* hist;  // counters of the call's earlier batches
+    int J;                      // frames per map in this batch
+    int j;                      // this step
 };
 
 // frame parameters passed by value
@@ -233,6 +253,7 @@ struct FrameParams {
     float inv_fx, inv_fy, inv_voxel;   // 1/fx, 1/fy, 1/voxel rounded once to fp32
     int32_t ov_num, ov_den, min_px;
     int32_t token_bf16;
+    int32_t map;           // position of the frame's map in the batch (MapRefs index)
     const float* depth;
     const uint16_t* labels;
     const void* tokens;

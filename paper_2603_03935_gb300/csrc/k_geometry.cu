@@ -35,10 +35,15 @@ __global__ void k_slot_clear(BatchScratch bs, int D, int MM)
     }
 }
 
-// counters and scalar sums of every slot (after k_slot_clear has read them)
-__global__ void k_slot_reset(BatchScratch bs, int B)
+// counters and scalar sums of every slot (after k_slot_clear has read them),
+// and the serial part's edge and copy counters of every map
+__global__ void k_slot_reset(BatchScratch bs, int B, const MapRefs* refs, int G)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < G) {
+        *refs[b].ss.edge_n = 0;
+        *refs[b].ss.copy_n = 0;
+    }
     if (b >= B) return;
     const Scratch sc = bs.frame(b);
     *sc.gg = 0;
@@ -267,11 +272,12 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
 // ---- per unique (segment, voxel): Eq. 3 term, |V_m|, label at batch start ------
 // Per-segment sums gather in shared memory first (one global atomic per
 // block and segment).
-__global__ void k_entries(const FrameParams* fps, BatchScratch bs, VoxelTable vt, int f0)
+__global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs* refs, int f0)
 {
     extern __shared__ unsigned char ent_smem[];
     const FrameParams& fp = fps[f0 + blockIdx.y];
     const Scratch sc = bs.frame(f0 + blockIdx.y);
+    const VoxelTable vt = refs[fp.map].vt;
     long long* s_ang = (long long*)ent_smem;         // [M]
     int* s_nv = (int*)(s_ang + max(fp.M, 1));         // [M]
     for (int m = threadIdx.x; m < fp.M; m += blockDim.x) {
@@ -358,10 +364,10 @@ __global__ void k_quality(const FrameParams* fps, BatchScratch bs)
 }
 
 // ---- host launchers ------------------------------------------------------------------
-int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st)
+int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, const MapRefs* refs, int G, cudaStream_t st)
 {
     k_slot_clear<<<dim3(64, B), 256, 0, st>>>(bs, D, MM);
-    k_slot_reset<<<(B + 127) / 128, 128, 0, st>>>(bs, B);
+    k_slot_reset<<<(std::max(B, G) + 127) / 128, 128, 0, st>>>(bs, B, refs, G);
     return 2;
 }
 
@@ -373,11 +379,11 @@ int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, i
     return 1;
 }
 
-int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int f0, int nb, int Mmax,
+int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
                    cudaStream_t st)
 {
     const size_t smem = 12 * (size_t)std::max(Mmax, 1) + 16;
-    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, vt, f0);
+    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, refs, f0);
     return 1;
 }
 

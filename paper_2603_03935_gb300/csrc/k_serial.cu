@@ -21,12 +21,18 @@ namespace disc {
 
 __device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(&c->err, 0, code); }
 
-// an error of the previous frame of the same call stops this one
-__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, int f, const int* prev_err)
+// an error of the previous frame of the same map in the same call stops this one
+__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, const SerialStep& st, int g, int slot)
 {
-    const Scratch sc = bs.frame(f);
+    const Scratch sc = bs.frame(slot);
     if (sc.ctr->err) return true;
-    const int pe = f > 0 ? bs.frame(f - 1).ctr->err : *prev_err;
+    int pe = 0;
+    if (st.j > 0) {
+        pe = bs.frame(st.slot_of[g * st.J + st.j - 1]).ctr->err;
+    } else {
+        const int h = st.prev_hist[g];
+        if (h >= 0) pe = st.hist[h].err;
+    }
     if (pe) {
         set_err(sc.ctr, pe);
         return true;
@@ -49,6 +55,7 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
     int* pcnt = (int*)(pkey + OV_SLOTS);                    // [OV_SLOTS]
     constexpr int OV_THREADS = SER_THREADS;
     const int ne = sc.ctr->n_entries;
+    if (blockIdx.x * OV_THREADS >= ne) return;  // no entries for this block (uniform)
     for (int i = threadIdx.x; i < OV_SLOTS; i += OV_THREADS) {
         pkey[i] = EMPTY_KEY;
         pcnt[i] = 0;
@@ -238,17 +245,18 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
 // that also hands out local indices to the roots that carry an edge, and
 // per-local-root arrays for the union-find and the fusion.  Every step runs
 // in parallel on shared memory except the new-id scan over the masks.
-constexpr int UNION_THREADS = SER_THREADS;
+constexpr int UNION_THREADS = 256;
 constexpr int PAIR_CAP = 8192;             // distinct (segment, instance) overlaps per frame
 constexpr int EDGE_ROOT_CAP = 2048;        // distinct instances with an accepted edge per frame
 constexpr int EDGE_CAP = 4096;             // accepted (segment, instance) edges per frame
-constexpr int UHASH = 2 * PAIR_CAP;        // hash slots (load <= 1/2)
+constexpr int UHASH = 2 * PAIR_CAP;        // hash slots at most (load <= 1/2); a frame uses
+                                           // the next power of two >= 2 * its pairs
 constexpr unsigned UH_EMPTY = 0xffffffffu;
 constexpr unsigned UH_UNUSED = 0xffffffffu;
 constexpr unsigned UH_LOCAL = 0x80000000u;
 constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8;
 
-__device__ __forceinline__ unsigned uhash(unsigned k) { return (unsigned)(mix64(k) & (UHASH - 1)); }
+__device__ __forceinline__ unsigned uhash(unsigned k, unsigned mask) { return (unsigned)(mix64(k) & mask); }
 
 __device__ __forceinline__ int uf_find(const int* uf, int x)
 {
@@ -259,10 +267,10 @@ __device__ __forceinline__ int uf_find(const int* uf, int x)
     }
 }
 
-__device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hval, unsigned k)
+__device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hval, unsigned mask, unsigned k)
 {
-    unsigned h = uhash(k);
-    while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+    unsigned h = uhash(k, mask);
+    while (hkey[h] != k) h = (h + 1) & mask;
     return (int)(hval[h] & ~UH_LOCAL);
 }
 
@@ -293,12 +301,15 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
         return;
     }
+    unsigned hsize = 64;
+    while (hsize < 2u * (unsigned)npairs) hsize <<= 1;
+    const unsigned hm = hsize - 1;
     // the edges, once, into shared memory (segment, root)
     for (int e = tid; e < nedge; e += UNION_THREADS) {
         em[e] = ss.edge_m[e];
         ek[e] = ss.edge_k[e];
     }
-    for (int i = tid; i < UHASH; i += UNION_THREADS) {
+    for (int i = tid; i < (int)hsize; i += UNION_THREADS) {
         hkey[i] = UH_EMPTY;
         hval[i] = UH_UNUSED;
     }
@@ -319,7 +330,7 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     // (1) active set: distinct roots of all overlap pairs
     for (int i = tid; i < npairs; i += UNION_THREADS) {
         const unsigned k = (unsigned)(ss.okeys[ss.olist[i]] & 0xffffffffu);
-        unsigned h = uhash(k);
+        unsigned h = uhash(k, hm);
         while (true) {
             const unsigned cur = hkey[h];
             if (cur == k) break;
@@ -328,7 +339,7 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
                 if (prev == UH_EMPTY) { atomicAdd(&s_nroots, 1); break; }
                 if (prev == k) break;
             }
-            h = (h + 1) & (UHASH - 1);
+            h = (h + 1) & hm;
         }
     }
     __syncthreads();
@@ -336,15 +347,15 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     //     claim a root's slot assigns the index
     for (int e = tid; e < nedge; e += UNION_THREADS) {
         const unsigned k = (unsigned)ek[e];
-        unsigned h = uhash(k);
-        while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+        unsigned h = uhash(k, hm);
+        while (hkey[h] != k) h = (h + 1) & hm;
         atomicCAS(&hval[h], UH_UNUSED, (unsigned)e);
     }
     __syncthreads();
     for (int e = tid; e < nedge; e += UNION_THREADS) {
         const unsigned k = (unsigned)ek[e];
-        unsigned h = uhash(k);
-        while (hkey[h] != k) h = (h + 1) & (UHASH - 1);
+        unsigned h = uhash(k, hm);
+        while (hkey[h] != k) h = (h + 1) & hm;
         if (hval[h] == (unsigned)e) {
             const int x = atomicAdd(&s_nloc, 1);
             if (x < EDGE_ROOT_CAP) {
@@ -366,10 +377,10 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     //     root onto the segment's anchor; a hook always links the root with
     //     the larger instance id under the smaller one, so each set's root is
     //     its smallest instance id
-    for (int e = tid; e < nedge; e += UNION_THREADS) atomicMin(&anchor[em[e]], local_of(hkey, hval, (unsigned)ek[e]));
+    for (int e = tid; e < nedge; e += UNION_THREADS) atomicMin(&anchor[em[e]], local_of(hkey, hval, hm, (unsigned)ek[e]));
     __syncthreads();
     for (int e = tid; e < nedge; e += UNION_THREADS) {
-        int x = local_of(hkey, hval, (unsigned)ek[e]);
+        int x = local_of(hkey, hval, hm, (unsigned)ek[e]);
         int y = anchor[em[e]];
         while (true) {
             x = uf_find(uf, x);
@@ -461,6 +472,7 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     __syncthreads();
     if (tid == 0) {
         *ss.copy_n = s_ncopy;
+        *ss.edge_n = 0;  // the next frame's gates start a new edge list
         ctr->active_instances = s_nroots;
         ctr->new_instances = s_new;
         ctr->merges = s_merges;
@@ -546,76 +558,100 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Seri
 }
 
 // ---- kernels ------------------------------------------------------------------------
-// frame_blocked decided once per block (another block may raise an error
-// while this one reads), so every thread of the block takes the same path
-__device__ bool block_blocked(const BatchScratch& bs, int f, const int* prev_err)
+// Block row g runs frame j of map g.  Whether the frame is blocked is decided
+// once per block (another block may raise an error while this one reads), so
+// every thread of the block takes the same path.  Returns the frame slot, or
+// -1 when map g has no frame j or the frame is blocked.
+__device__ int block_slot(const BatchScratch& bs, const SerialStep& st, bool* blocked)
 {
-    __shared__ int s_blocked;
-    if (threadIdx.x == 0) s_blocked = frame_blocked(bs, f, prev_err) ? 1 : 0;
+    __shared__ int s_slot, s_blocked;
+    const int g = blockIdx.y;
+    if (threadIdx.x == 0) {
+        const int slot = st.slot_of[g * st.J + st.j];
+        s_slot = slot;
+        s_blocked = slot >= 0 && frame_blocked(bs, st, g, slot) ? 1 : 0;
+    }
     __syncthreads();
-    const bool b = s_blocked != 0;
+    const int slot = s_slot;
+    *blocked = s_blocked != 0;
     __syncthreads();
-    return b;
+    return slot;
 }
 
 constexpr size_t OV_SMEM = (size_t)OV_SLOTS * 12;
 
-__global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, int f, SerialScratch ss, VoxelTable vt,
-                                                         Instances inst)
+__global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, SerialStep st)
 {
     extern __shared__ __align__(16) unsigned char ov_smem[];
-    if (block_blocked(bs, f, ss.prev_err)) return;
-    phase_overlap(bs.frame(f), ss, vt, inst, ov_smem);
+    bool blocked;
+    const int slot = block_slot(bs, st, &blocked);
+    if (slot < 0 || blocked) return;
+    const MapRefs& R = st.refs[blockIdx.y];
+    const SerialScratch ss = R.ss;
+    const VoxelTable vt = R.vt;
+    const Instances inst = R.inst;
+    phase_overlap(bs.frame(slot), ss, vt, inst, ov_smem);
 }
 
-__global__ void k_score(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, Instances inst,
-                        ScoreParams sp)
+__global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st, ScoreParams sp)
 {
-    if (block_blocked(bs, f, ss.prev_err)) return;
-    phase_score(fps[f], bs.frame(f), ss, inst, sp);
+    bool blocked;
+    const int slot = block_slot(bs, st, &blocked);
+    if (slot < 0 || blocked) return;
+    const MapRefs& R = st.refs[blockIdx.y];
+    const SerialScratch ss = R.ss;
+    const Instances inst = R.inst;
+    phase_score(fps[slot], bs.frame(slot), ss, inst, sp);
 }
 
-__global__ void __launch_bounds__(UNION_THREADS, 1)
-k_union(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, Instances inst, int* next_id)
+__global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
     extern __shared__ __align__(16) unsigned char union_smem[];
-    if (block_blocked(bs, f, ss.prev_err)) return;
-    phase_union(fps[f], bs.frame(f), ss, inst, next_id, union_smem);
+    bool blocked;
+    const int slot = block_slot(bs, st, &blocked);
+    if (slot < 0 || blocked) return;
+    const MapRefs& R = st.refs[blockIdx.y];
+    const SerialScratch ss = R.ss;
+    const Instances inst = R.inst;
+    phase_union(fps[slot], bs.frame(slot), ss, inst, R.next_id, union_smem);
 }
 
-__global__ void k_apply(const FrameParams* fps, BatchScratch bs, int f, SerialScratch ss, VoxelTable vt, Instances inst,
-                        const int* next_id)
+__global__ void k_apply(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
-    const bool ok = !block_blocked(bs, f, ss.prev_err);
-    phase_apply(fps[f], bs.frame(f), ss, vt, inst, next_id, ok);
-}
-
-// edge and copy counters of the next frame start at zero
-__global__ void k_serial_reset(SerialScratch ss)
-{
-    *ss.edge_n = 0;
-    *ss.copy_n = 0;
+    bool blocked;
+    const int slot = block_slot(bs, st, &blocked);
+    if (slot < 0) return;
+    const MapRefs& R = st.refs[blockIdx.y];
+    const SerialScratch ss = R.ss;
+    const VoxelTable vt = R.vt;
+    const Instances inst = R.inst;
+    phase_apply(fps[slot], bs.frame(slot), ss, vt, inst, R.next_id, !blocked);
 }
 
 // ---- host launcher ----------------------------------------------------------------
-int launch_serial_frame(const FrameParams* fps, const BatchScratch& bs, int f, const SerialScratch& ss,
-                        const VoxelTable& vt, const Instances& inst, int* next_id, float eta, float dot_err, int phase,
-                        cudaStream_t st)
+// Blocks per map: the whole GPU for a single map, fewer per map as the maps
+// of a batch multiply (they run side by side).
+static int per_map(int full, int G, int least)
+{
+    return std::max(least, (full + G - 1) / G);
+}
+
+int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, float eta,
+                       float dot_err, int phase, cudaStream_t st_)
 {
     switch (phase) {
         case 0:
-            k_overlap<<<152 * 2, SER_THREADS, OV_SMEM, st>>>(bs, f, ss, vt, inst);
+            k_overlap<<<dim3(per_map(152 * 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(bs, st);
             return 1;
         case 1:
-            k_score<<<152, 256, 0, st>>>(fps, bs, f, ss, inst, ScoreParams{eta, dot_err});
+            k_score<<<dim3(per_map(152, G, 4), G), 256, 0, st_>>>(fps, bs, st, ScoreParams{eta, dot_err});
             return 1;
         case 2:
-            k_union<<<1, UNION_THREADS, UNION_SMEM, st>>>(fps, bs, f, ss, inst, next_id);
+            k_union<<<dim3(1, G), UNION_THREADS, UNION_SMEM, st_>>>(fps, bs, st);
             return 1;
         default:
-            k_apply<<<152 * 2, 256, 0, st>>>(fps, bs, f, ss, vt, inst, next_id);
-            k_serial_reset<<<1, 1, 0, st>>>(ss);
-            return 2;
+            k_apply<<<dim3(per_map(152 * 2, G, 8), G), 256, 0, st_>>>(fps, bs, st);
+            return 1;
     }
 }
 

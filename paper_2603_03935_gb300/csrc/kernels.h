@@ -5,7 +5,8 @@
 //   batched (one launch covers every frame slot; nothing here writes the map):
 //     slot_clear, token_stats (Eq. 1), coverage, weights, pool_exact,
 //     pool_gemm (tcgen05), backproject, entries (+ Q)
-//   serial (per frame, in order; these read and write the map):
+//   serial (per frame of each map, in order; these read and write the maps,
+//   all maps of the batch side by side in one launch):
 //     overlap, score, union, apply
 #pragma once
 
@@ -33,7 +34,7 @@ enum Phase {
 };
 
 // batched
-int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st);
+int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, const MapRefs* refs, int G, cudaStream_t st);
 int launch_token_stats(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, bool any_bf16,
                        bool any_f32, cudaStream_t st);
 int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int Ph, int Pw, int Mmax, cudaStream_t st);
@@ -45,16 +46,16 @@ int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int 
 // back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
 // batch start) on frames [f0, f0 + nb); then Q of every segment
 int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
-int launch_entries(const FrameParams* fps, const BatchScratch& bs, const VoxelTable& vt, int f0, int nb, int Mmax,
+int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
                    cudaStream_t st);
 int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);
 // frames per back-projection/entries launch: their per-frame hashes stay in L2
 constexpr int GEOMETRY_CHUNK = 4;
 
-// serial part, frame slot f: phase 0 overlap, 1 score, 2 union, 3 apply
-int launch_serial_frame(const FrameParams* fps, const BatchScratch& bs, int f, const SerialScratch& ss,
-                        const VoxelTable& vt, const Instances& inst, int* next_id, float eta, float dot_err, int phase,
-                        cudaStream_t st);
+// serial part, step st.j over the G maps of a batch: phase 0 overlap,
+// 1 score, 2 union, 3 apply
+int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, float eta,
+                       float dot_err, int phase, cudaStream_t stream);
 
 size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);
