@@ -36,9 +36,19 @@ constexpr int MAX_MASKS = 256;
 constexpr int GEMM_MT = 128;    // token-dimension rows per GEMM tile
 constexpr int GEMM_KC = 32;     // patches per GEMM pipeline chunk
 
+// llrint(x * 2^S), S <= 62.  The product is exact (a power-of-two scale).
+// Kept off the fp64 pipe, which converts float -> int64 at a small fraction
+// of the fp32 rate on this part: below 2^31 in magnitude a 32-bit
+// conversion rounds it (to nearest, ties to even, as llrint); from 2^31 on
+// the float is an integer and its significand and exponent give it exactly.
 __device__ __forceinline__ long long fix32f(float x, int S)
 {
-    return __float2ll_rn(__fmul_rn(x, __int_as_float((127 + S) << 23)));
+    const float y = __fmul_rn(x, __int_as_float((127 + S) << 23));
+    if (fabsf(y) < 2147483648.0f) return (long long)__float2int_rn(y);
+    const unsigned b = __float_as_uint(y);
+    const int e = min((int)((b >> 23) & 0xffu) - 150, 39);  // >= 8 here; |y| < 2^63 for finite inputs in range
+    const long long v = (long long)((b & 0x7fffffu) | 0x800000u) << e;
+    return (b >> 31) ? -v : v;
 }
 __device__ __forceinline__ double unfix(long long n, int S)
 {
