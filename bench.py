@@ -134,12 +134,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "period_ms": self.period}
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary
+    (profiles/<kernel>_room_640x480.md), or None when there is none or the
+    kernel's source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_room_640x480.md")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", "#", " ")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        src = os.path.join(ROOT, kv["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != kv["source_sha256"]:
+            return None
+        return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
     """Bytes a phase must move for all frames of the timed batch together
     (see the design doc); divided by the phase's launches it gives the bytes per
     launch.  sts: per-frame stats, Ms: masks per frame."""
     per_frame = {
-        "backproject": lambda s, M: 6 * H * W + 36 * s["unique_seg_voxels"],
+        "backproject": lambda s, M: 6 * H * W + 44 * s["unique_seg_voxels"],
         "entries": lambda s, M: 52 * s["unique_seg_voxels"],
         "token_stats": lambda s, M: 4 * P * D,
         "pool_gemm": lambda s, M: 4 * P * D + 4 * M * Kpad + 4 * M * D,
@@ -359,7 +379,7 @@ def main():
     launch_ms = phases[dom]["ms"] / calls
     achieved = alg_total / (phases[dom]["ms"] / 1e3) / 1e9 if phases[dom]["ms"] > 0 and alg_total > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": measured_traffic(dom), "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
                 "launches_per_frame": calls / (TB * B)}
 
