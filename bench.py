@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--frames-per-step", type=int, default=32)
     ap.add_argument("--latency-frames", type=int, default=64)
     ap.add_argument("--timing-batches", type=int, default=4)
+    ap.add_argument("--batched-maps", type=int, default=64)
+    ap.add_argument("--batched-frames", type=int, default=4, help="frames of each map per batch")
+    ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -173,6 +176,90 @@ def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
     if phase not in per_frame:
         return 0.0
     return float(sum(per_frame[phase](s_, M) for s_, M in zip(sts, Ms)))
+
+
+BATCHED = "Batched: {G} independent room-scale maps of uneven size (320x240..640x480 frames, 20-120 objects, " \
+          "5-60 masks/frame, voxel 2.5 cm), bf16 tokens 24x24x768, {J} frames of every map per batch"
+
+
+def batched_scenes(G, seed0):
+    """G room scenes of uneven size: frame sizes, object counts and mask limits
+    cycle through fixed lists (seeded per map)."""
+    import synth
+    sizes = ((640, 480), (480, 360), (320, 240), (560, 420))
+    objs = (80, 20, 120, 50, 100)
+    masks = (40, 5, 60, 25, 12, 50)
+    return [synth.room_scene(seed=seed0 + g, width=sizes[g % 4][0], height=sizes[g % 4][1],
+                             n_objects=objs[g % 5], max_masks=masks[g % 6]) for g in range(G)]
+
+
+def run_batched(args, torch, dev, stream, rank):
+    """The batched form: every map's frames j..j+J of a step in one group call
+    (disc_group_integrate), device-resident bf16 inputs."""
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap, binding
+    from tests import common
+    G, J, T = args.batched_maps, args.batched_frames, args.batched_steps
+    scs = batched_scenes(G, 1000 + 97 * rank)
+    nf = (1 + T) * J
+    frs = [s.render(range(nf)) for s in scs]
+    dd = [torch.from_numpy(f.depth).to(dev) for f in frs]
+    ll = [torch.from_numpy(f.labels.view(np.int16)).to(dev) for f in frs]
+    tt = [torch.from_numpy(f.tokens).to(dev).to(torch.bfloat16).contiguous() for f in frs]
+    maps = [DiscMap(**common.disc_cfg(s, voxel_capacity=1 << 21, instance_capacity=1 << 12)) for s in scs]
+    grp = DiscGroup(max_maps=G, frames_per_map=J, embed_dim=scs[0].dim, patch_h=scs[0].patch_h,
+                    patch_w=scs[0].patch_w, max_width=max(s.width for s in scs),
+                    max_height=max(s.height for s in scs), max_masks=max(s.max_masks for s in scs),
+                    cuda_stream=stream.cuda_stream, device=dev.index)
+
+    def arrays(lo):
+        out = []
+        for g in range(G):
+            a = (binding.Frame * J)()
+            sc, fr = scs[g], frs[g]
+            for j in range(J):
+                i = lo + j
+                f = a[j]
+                f.width, f.height = sc.width, sc.height
+                f.fx, f.fy, f.cx, f.cy = sc.fx, sc.fy, sc.cx, sc.cy
+                for q, v in enumerate(fr.poses[i].reshape(16)):
+                    f.T_world_cam[q] = float(v)
+                f.depth, f.labels, f.tokens = dd[g][i].data_ptr(), ll[g][i].data_ptr(), tt[g][i].data_ptr()
+                f.token_dtype = 1
+                f.num_masks = int(fr.num_masks[i])
+                f.global_embed = None
+                f.inputs_on_device = 1
+            out.append(a)
+        return out
+
+    steps = [arrays(s * J) for s in range(1 + T)]
+    sts = [(binding.Stats * J)() for _ in range(G)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    assert grp.integrate_raw(maps, steps[0], [J] * G, sts) == 0
+    torch.cuda.synchronize()
+    times, upd = [], 0
+    for s in range(1, 1 + T):
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = grp.integrate_raw(maps, steps[s], [J] * G, sts)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        times.append(e0.elapsed_time(e1))
+        upd += sum(sts[g][j].unique_seg_voxels for g in range(G) for j in range(J))
+    total_ms = float(np.sum(times))
+    out = {"workload": BATCHED.format(G=G, J=J), "frames_per_s": T * G * J / (total_ms / 1e3),
+           "voxel_updates_per_s": upd / (total_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
+           "steps": T, "ms_per_batch": total_ms / T,
+           "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                                "mode": "a frame's result is ready when its batch ends"},
+           "gpu_launches_per_batch": grp.kernel_launches() // (1 + T),
+           "device_gb": (grp.device_bytes() + sum(m.device_bytes() for m in maps)) / 1e9}
+    grp.close()
+    for m in maps:
+        m.close()
+    return out
 
 
 def run_reference(args, rank):
@@ -383,6 +470,8 @@ def main():
                 "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
                 "launches_per_frame": calls / (TB * B)}
 
+    batched = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
+
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None
     if not args.no_e2e:
@@ -427,6 +516,7 @@ def main():
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"},
                "frame_ms_batched": total_ms / (K * B),
+               "batched": batched,
                "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
                "gpu_launches": int(launches),
                "roofline": roofline,

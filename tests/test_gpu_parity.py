@@ -256,3 +256,25 @@ def test_queries(torch_dev):
     pts = ((ks + 0.5) * sc.voxel_size).astype(np.float32)
     got = gmap.query_points(np.vstack([pts, [[100.0, 100.0, 100.0]]]))
     assert np.array_equal(got[:-1], vids[:200]) and got[-1] == -1
+
+
+def test_bf16_tokens_parity(torch_dev):
+    # bf16 tokens widen exactly to fp32: the oracle, given those fp32 values,
+    # must match bit for bit
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, device_frame
+    sc = synth.tiny_scene()
+    fr = sc.render(range(10))
+    cfg = common.disc_cfg(sc)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    for i in range(len(fr)):
+        t16 = torch.from_numpy(fr.tokens[i]).to(dev).to(torch.bfloat16).contiguous()
+        t32 = t16.float().cpu().numpy()
+        d = torch.from_numpy(fr.depth[i]).to(dev)
+        l = torch.from_numpy(fr.labels[i].view(np.int16)).to(dev)
+        st = gmap.integrate(device_frame(d, l, t16, fr.poses[i], intr, fr.num_masks[i]))
+        o = omap.integrate(fr.depth[i], fr.labels[i], t32, fr.poses[i], intr, fr.num_masks[i])
+        common.compare_frame(st, gmap.last_frame(), o, ctx=f"bf16 frame {i}")
+    common.compare_maps(gmap, omap, ctx="bf16 tokens")
