@@ -199,6 +199,72 @@ int64_t disc_group_kernel_launches(disc_group* group);
 int64_t disc_group_device_bytes(disc_group* group);
 void disc_group_destroy(disc_group* group); /* NULL-safe */
 
+/* ---- Serving: a request loop over many resident maps ----------------------
+ * Clients (any host threads) submit integrate and query requests for maps the
+ * server holds resident on the device.  A worker thread batches continuously:
+ * each batch takes, for up to group.max_maps maps with work (oldest request
+ * first), the leading frames of each map's queue (up to
+ * group.frames_per_map, stopping at the map's first query) and runs them as
+ * one group call; requests arriving meanwhile join the next batch.  A query
+ * runs after the frames submitted before it on the same map and before those
+ * after it, so every result equals the one of the same requests served alone.
+ * Maps are admitted while the device memory of the group scratch and all open
+ * maps stays within hbm_budget_bytes (the paper has no counterpart of this
+ * layer). */
+typedef struct disc_server disc_server; /* opaque */
+
+typedef struct {
+    disc_group_config group;  /* batch shape and limits of every map */
+    int64_t hbm_budget_bytes; /* admission limit for the group scratch plus the open maps */
+    int32_t max_queue;        /* requests queued or running at most; more: DISC_ERR_BUDGET */
+} disc_server_config;
+
+typedef struct {
+    int64_t frames, queries, batches; /* completed since creation or the last reset */
+    int64_t pending;                  /* requests queued or running */
+    int64_t resident_bytes;           /* group scratch + open maps at admission */
+    double busy_ms;                   /* host time inside batches */
+    double wall_ms;                   /* since creation or the last reset */
+    double p50_ms, p99_ms;            /* frame latency, submission to completion */
+} disc_server_report;
+
+/* Creates the server and its worker thread.  DISC_ERR_BUDGET when the group
+ * scratch alone passes the budget. */
+disc_status disc_server_create(const disc_server_config* cfg, disc_server** out_server);
+
+/* Opens a map (cfg's embed_dim, patch grid and device equal to the group's;
+ * frame size and masks within the group's).  DISC_ERR_BUDGET when admitting
+ * it would pass the budget. */
+disc_status disc_server_open_map(disc_server* server, const disc_map_config* cfg, int32_t* map_id);
+
+/* Waits for the map's requests, then frees it. */
+disc_status disc_server_close_map(disc_server* server, int32_t map_id);
+
+/* The map behind map_id, for export and checkpoints between requests (NULL
+ * when not open).  Do not use it while the map has requests pending. */
+disc_map* disc_server_map(disc_server* server, int32_t map_id);
+
+/* Queues one frame of map_id.  Its inputs (host or device, inputs_on_device)
+ * are copied before the call returns.  *ticket identifies the request. */
+disc_status disc_server_submit_frame(disc_server* server, int32_t map_id, const disc_frame* frame,
+                                     int64_t* ticket);
+
+/* Queues a top-k query: queries [nq][D] host memory, copied before return. */
+disc_status disc_server_submit_query(disc_server* server, int32_t map_id, const float* queries, int32_t nq,
+                                     int32_t k, int64_t* ticket);
+
+/* Waits for a request and returns its status.  A frame fills stats
+ * (nullable); a query fills ids and scores [nq][k] (nullable).  latency_ms
+ * (nullable): submission to completion.  A ticket can be waited for once. */
+disc_status disc_server_wait(disc_server* server, int64_t ticket, disc_frame_stats* stats, int32_t* ids,
+                             float* scores, double* latency_ms);
+
+disc_status disc_server_stats(disc_server* server, disc_server_report* out);
+disc_status disc_server_reset_stats(disc_server* server);
+
+/* Drains every queued request, then frees the maps, the group and the worker. */
+void disc_server_destroy(disc_server* server); /* NULL-safe */
+
 /* Copies the intermediates of the most recent frame that the map integrated
  * through disc_integrate_frame(s) (see disc_frame_report). */
 disc_status disc_map_last_frame(disc_map* map, disc_frame_report* report);

@@ -5,8 +5,8 @@ ABI of include/disc.h.  This package is a thin ctypes binding with the same
 names; it only marshals arguments.  There is no CPU fallback: when the library
 is missing, loading fails loudly.
 """
-from .binding import (DiscError, DiscGroup, DiscMap, config_default, device_frame, host_frame, lib, pack_key,
+from .binding import (DiscError, DiscGroup, DiscMap, DiscServer, config_default, device_frame, host_frame, lib, pack_key,
                       status_str, token_stats_static)
 
-__all__ = ["DiscError", "DiscGroup", "DiscMap", "config_default", "device_frame", "host_frame", "lib",
+__all__ = ["DiscError", "DiscGroup", "DiscMap", "DiscServer", "config_default", "device_frame", "host_frame", "lib",
            "pack_key", "status_str", "token_stats_static"]

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdisc.so")
 SOURCES = ["k_features.cu", "k_gemm.cu", "k_geometry.cu", "k_serial.cu", "k_maint.cu", "disc_api.cu",
-           "disc_static.cu"]
+           "disc_static.cu", "disc_server.cu"]
 HEADERS = ["disc_common.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no fused multiply-add anywhere, so every fp32 expression is
@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     if force or _stale(LIB, objs):
-        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -54,6 +54,16 @@ class GroupConfig(ctypes.Structure):
                 ("cuda_stream", c_vp), ("device", c_i32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("group", GroupConfig), ("hbm_budget_bytes", c_i64), ("max_queue", c_i32)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [("frames", c_i64), ("queries", c_i64), ("batches", c_i64), ("pending", c_i64),
+                ("resident_bytes", c_i64), ("busy_ms", c_f64), ("wall_ms", c_f64), ("p50_ms", c_f64),
+                ("p99_ms", c_f64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
                 ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
@@ -117,10 +127,24 @@ def lib():
         L.disc_group_device_bytes.restype = c_i64
         L.disc_group_destroy.argtypes = [c_vp]
         L.disc_group_destroy.restype = None
+        L.disc_server_create.argtypes = [P(ServerConfig), P(c_vp)]
+        L.disc_server_open_map.argtypes = [c_vp, P(Config), P(c_i32)]
+        L.disc_server_close_map.argtypes = [c_vp, c_i32]
+        L.disc_server_map.argtypes = [c_vp, c_i32]
+        L.disc_server_map.restype = c_vp
+        L.disc_server_submit_frame.argtypes = [c_vp, c_i32, P(Frame), P(c_i64)]
+        L.disc_server_submit_query.argtypes = [c_vp, c_i32, c_vp, c_i32, c_i32, P(c_i64)]
+        L.disc_server_wait.argtypes = [c_vp, c_i64, P(Stats), c_vp, c_vp, P(c_f64)]
+        L.disc_server_stats.argtypes = [c_vp, P(ServerReport)]
+        L.disc_server_reset_stats.argtypes = [c_vp]
+        L.disc_server_destroy.argtypes = [c_vp]
+        L.disc_server_destroy.restype = None
         for f in ("disc_map_create", "disc_integrate_frame", "disc_integrate_frames", "disc_map_last_frame",
                   "disc_query_topk", "disc_query_points", "disc_map_counts", "disc_map_export_voxels",
                   "disc_map_export_instances", "disc_map_save", "disc_map_load", "disc_group_create",
-                  "disc_group_integrate", "disc_group_set_phase_timing", "disc_group_phase_times"):
+                  "disc_group_integrate", "disc_group_set_phase_timing", "disc_group_phase_times",
+                  "disc_server_create", "disc_server_open_map", "disc_server_close_map", "disc_server_submit_frame",
+                  "disc_server_submit_query", "disc_server_wait", "disc_server_stats", "disc_server_reset_stats"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -235,9 +259,9 @@ class DiscMap:
 
     def close(self):
         h = getattr(self, "_h", None)
-        if h:
+        if h and getattr(self, "_owned", True):
             lib().disc_map_destroy(h)
-            self._h = None
+        self._h = None
 
     __del__ = close
 
@@ -431,3 +455,97 @@ class DiscGroup:
                "disc_group_phase_times")
         return {lib().disc_phase_name(i).decode(): dict(ms=float(ms[i]), launches=int(la[i]), calls=int(ca[i]))
                 for i in range(n)}
+
+
+class DiscServer:
+    """Request loop over resident maps (disc_server_create ... disc_server_destroy)."""
+
+    def __init__(self, hbm_budget_bytes, max_queue=4096, **group):
+        c = ServerConfig()
+        lib().disc_group_config_default(ctypes.byref(c.group))
+        for k, v in group.items():
+            setattr(c.group, k, v)
+        c.hbm_budget_bytes = int(hbm_budget_bytes)
+        c.max_queue = int(max_queue)
+        h = c_vp()
+        _check(lib().disc_server_create(ctypes.byref(c), ctypes.byref(h)), "disc_server_create")
+        self._h = h
+        self.D = int(c.group.embed_dim)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().disc_server_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def open_map(self, **cfg) -> int:
+        c = Config(**config_default(**cfg))
+        mid = c_i32(-1)
+        rc = lib().disc_server_open_map(self._h, ctypes.byref(c), ctypes.byref(mid))
+        _check(rc, "disc_server_open_map")
+        return int(mid.value)
+
+    def try_open_map(self, **cfg):
+        """(status, map id or -1) without raising."""
+        c = Config(**config_default(**cfg))
+        mid = c_i32(-1)
+        rc = lib().disc_server_open_map(self._h, ctypes.byref(c), ctypes.byref(mid))
+        return rc, int(mid.value)
+
+    def close_map(self, map_id: int):
+        _check(lib().disc_server_close_map(self._h, map_id), "disc_server_close_map")
+
+    def map(self, map_id: int) -> DiscMap:
+        """A non-owning view of the map (export, queries) between requests."""
+        h = lib().disc_server_map(self._h, map_id)
+        if not h:
+            raise DiscError(-1, "disc_server_map")
+        m = DiscMap._from_handle(c_vp(h))
+        m._owned = False
+        return m
+
+    def submit_frame(self, map_id: int, frame) -> int:
+        fr, _keep = frame
+        t = c_i64(0)
+        _check(lib().disc_server_submit_frame(self._h, map_id, ctypes.byref(fr), ctypes.byref(t)),
+               "disc_server_submit_frame")
+        return int(t.value)
+
+    def submit_frame_raw(self, map_id: int, fr) -> int:
+        t = c_i64(0)
+        rc = lib().disc_server_submit_frame(self._h, map_id, ctypes.byref(fr), ctypes.byref(t))
+        return int(t.value) if rc == 0 else rc
+
+    def submit_query(self, map_id: int, queries, k: int) -> int:
+        q = np.ascontiguousarray(queries, np.float32).reshape(-1, self.D)
+        t = c_i64(0)
+        _check(lib().disc_server_submit_query(self._h, map_id, q.ctypes.data, q.shape[0], k, ctypes.byref(t)),
+               "disc_server_submit_query")
+        return int(t.value), q.shape[0], k
+
+    def wait_frame(self, ticket: int):
+        st = Stats()
+        lat = c_f64(0.0)
+        rc = lib().disc_server_wait(self._h, ticket, ctypes.byref(st), None, None, ctypes.byref(lat))
+        d = st.as_dict()
+        d["rc"] = rc
+        d["latency_ms"] = float(lat.value)
+        return d
+
+    def wait_query(self, tq):
+        ticket, nq, k = tq
+        ids = np.zeros((nq, k), np.int32)
+        sc = np.zeros((nq, k), np.float32)
+        lat = c_f64(0.0)
+        rc = lib().disc_server_wait(self._h, ticket, None, ids.ctypes.data, sc.ctypes.data, ctypes.byref(lat))
+        return rc, ids, sc, float(lat.value)
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(lib().disc_server_stats(self._h, ctypes.byref(r)), "disc_server_stats")
+        return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def reset_stats(self):
+        _check(lib().disc_server_reset_stats(self._h), "disc_server_reset_stats")
