@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-frames", type=int, default=4, help="frames of each map per batch")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--served-maps", type=int, default=32)
+    ap.add_argument("--served-rates", default="4000,8000,16000", help="offered frames/s, comma separated")
+    ap.add_argument("--served-seconds", type=float, default=1.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -262,6 +265,90 @@ def run_batched(args, torch, dev, stream, rank):
     return out
 
 
+SERVED = "Served: {G} resident room-scale maps of mixed size (320x240..640x480, 5-60 masks, bf16 tokens), " \
+         "Poisson arrivals, integrate:query 9:1 (top-5 of 4 vectors), each map cycling through its {F} frames, " \
+         "4 client threads, continuous batching of up to {J} frames per map per batch"
+
+
+def run_served(args, torch, dev, rank):
+    """The served form: requests from client threads at Poisson arrival times
+    into disc_server_*; p50/p99 frame latency (submission to completion) and
+    completed frames/s per offered rate."""
+    import threading
+    from paper_2603_03935_gb300 import DiscServer, binding
+    from tests import common
+    G, F, J = args.served_maps, 16, 4
+    scs = batched_scenes(G, 5000 + 97 * rank)
+    frs = [sc.render(range(F)) for sc in scs]
+    bf = []
+    for sc, fr in zip(scs, frs):
+        t16 = torch.from_numpy(fr.tokens).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+        bf.append([binding.host_frame(fr.depth[i], fr.labels[i], t16[i], fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy),
+                                      fr.num_masks[i]) for i in range(F)])
+    srv = DiscServer(64 << 30, max_queue=1 << 16, max_maps=G, frames_per_map=J, embed_dim=scs[0].dim,
+                     patch_h=scs[0].patch_h, patch_w=scs[0].patch_w, max_width=max(s.width for s in scs),
+                     max_height=max(s.height for s in scs), max_masks=max(s.max_masks for s in scs),
+                     device=dev.index)
+    ids = [srv.open_map(**common.disc_cfg(sc, voxel_capacity=1 << 21, instance_capacity=1 << 12)) for sc in scs]
+    queries = [fr.tokens[0][:4] for fr in frs]
+    # warm-up: every map takes its frames once
+    for g in range(G):
+        for i in range(F):
+            srv.wait_frame(srv.submit_frame(ids[g], bf[g][i]))
+    rng = np.random.default_rng(11 + rank)
+    out = []
+    for rate in [float(x) for x in args.served_rates.split(",") if x]:
+        n = int(rate / 0.9 * args.served_seconds)  # requests; 9 in 10 are frames
+        gaps = rng.exponential(1.0 / (rate / 0.9), n)
+        when = np.cumsum(gaps)
+        which = rng.integers(0, G, n)
+        is_q = rng.random(n) < 0.1
+        nxt = [0] * G
+        plan = []
+        for r in range(n):
+            g = int(which[r])
+            if is_q[r]:
+                plan.append((when[r], g, -1))
+            else:
+                plan.append((when[r], g, nxt[g] % F))
+                nxt[g] += 1
+        srv.reset_stats()
+        fail = []
+
+        def client(c):
+            tk = []
+            t0 = start
+            for r in range(c, n, 4):
+                at, g, i = plan[r]
+                d = t0 + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                if i < 0:
+                    tk.append((True, srv.submit_query(ids[g], queries[g], 5)))
+                else:
+                    tk.append((False, srv.submit_frame(ids[g], bf[g][i])))
+            for q, t in tk:
+                rc = srv.wait_query(t)[0] if q else srv.wait_frame(t)["rc"]
+                if rc != 0:
+                    fail.append(rc)
+
+        start = time.perf_counter()
+        th = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        wall = time.perf_counter() - start
+        rep = srv.stats()
+        assert not fail, fail[:5]
+        out.append({"offered_frames_per_s": rate, "frames_per_s": rep["frames"] / wall,
+                    "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "frames": rep["frames"],
+                    "queries": rep["queries"], "batches": rep["batches"],
+                    "frames_per_batch": rep["frames"] / max(rep["batches"], 1)})
+    srv.close()
+    return {"workload": SERVED.format(G=G, F=F, J=J), "rates": out}
+
+
 def run_reference(args, rank):
     """The oracle, as it stands, on the host cores: same workload and metric."""
     import oracle
@@ -471,6 +558,7 @@ def main():
                 "launches_per_frame": calls / (TB * B)}
 
     batched = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
+    served = run_served(args, torch, dev, rank) if args.served_maps > 0 else None
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None
@@ -517,6 +605,7 @@ def main():
                               "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"},
                "frame_ms_batched": total_ms / (K * B),
                "batched": batched,
+               "served": served,
                "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
                "gpu_launches": int(launches),
                "roofline": roofline,

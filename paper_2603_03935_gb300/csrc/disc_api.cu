@@ -94,6 +94,7 @@ struct Runner {
     float* d_gembed = nullptr;
     bool graphs_off = false;
     std::map<long long, BatchGraph> graphs;
+    std::map<long long, int> shapes_seen;  // batch shapes launched directly so far
     int64_t launches = 0;
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -131,6 +132,8 @@ struct disc_map {
     int64_t next_id_upper = 0;
     Runner* run = nullptr;  // created by the map's first own integration call
     bool timing_wanted = false;
+    unsigned char* qscratch = nullptr;  // query buffers, grown on demand and kept
+    size_t qcap = 0;
 };
 
 struct disc_group {
@@ -287,6 +290,7 @@ disc_status ensure_hist(Runner& r, int n)
     // captured sequences hold the old pointer
     for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
     r.graphs.clear();
+    r.shapes_seen.clear();
     const int cap = std::max(n, 2 * r.hist_cap);
     r.d_hist = r.mem.get<FrameCounters>(cap);
     if (r.mem.failed) {
@@ -419,6 +423,24 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     return DISC_OK;
 }
 
+// device scratch of at least `bytes` for query calls (no allocation once it
+// is large enough: a freed buffer would synchronise the device each call)
+unsigned char* query_scratch(disc_map* m, size_t bytes)
+{
+    if (bytes <= m->qcap) return m->qscratch;
+    if (m->qscratch) m->mem.release(m->qscratch, m->qcap);
+    const size_t cap = std::max(bytes, 2 * m->qcap);
+    m->qscratch = m->mem.get<unsigned char>(cap);
+    if (m->mem.failed) {
+        m->mem.failed = false;
+        m->qscratch = nullptr;
+        m->qcap = 0;
+        return nullptr;
+    }
+    m->qcap = cap;
+    return m->qscratch;
+}
+
 MapRefs map_refs(const disc_map* m)
 {
     MapRefs r;
@@ -538,14 +560,25 @@ long long graph_key(int S, int G, int J, bool any_bf16, bool any_f32)
     return ((((long long)S << 20) | ((long long)G << 10) | J) << 2) | (any_bf16 ? 2 : 0) | (any_f32 ? 1 : 0);
 }
 
-// The batch's kernel sequence captured once per shape and replayed.
+// The batch's kernel sequence captured once per shape and replayed.  A shape
+// seen for the first time runs as plain launches (*out = NULL): under a mixed
+// load (groups, serving) most shapes are one-off and instantiating a graph
+// costs more than launching the kernels.  At most kMaxGraphs are kept.
+constexpr int kMaxGraphs = 64;
+
 disc_status batch_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32, BatchGraph** out)
 {
     const long long key = graph_key(S, G, J, any_bf16, any_f32);
+    *out = nullptr;
     auto it = r.graphs.find(key);
     if (it != r.graphs.end()) {
         *out = &it->second;
         return DISC_OK;
+    }
+    if (r.shapes_seen[key]++ == 0) return DISC_OK;
+    if ((int)r.graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(r.graphs.begin()->second.exec);
+        r.graphs.erase(r.graphs.begin());
     }
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(r.stream, cudaStreamCaptureModeThreadLocal));
@@ -794,6 +827,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             r.graphs_off = true;  // this stream or driver cannot capture the sequence
             g = nullptr;
         }
+        // g == NULL: plain launches (first sighting of a shape, timing, no capture)
         if (g) {
             s = cuda_status(cudaGraphLaunch(g->exec, r.stream));
             r.launches += g->kernels;
@@ -1271,28 +1305,19 @@ disc_status disc_query_topk(disc_map* m, const float* q, int32_t nq, int32_t k, 
         }
         return DISC_OK;
     }
-    float *dq = nullptr, *dsc = nullptr, *dout = nullptr;
-    int* dids = nullptr;
-    disc_status s = DISC_OK;
-    if (cudaMalloc(&dq, sizeof(float) * (size_t)nq * D) != cudaSuccess ||
-        cudaMalloc(&dsc, sizeof(float) * (size_t)nq * nid) != cudaSuccess ||
-        cudaMalloc(&dout, sizeof(float) * (size_t)nq * k) != cudaSuccess ||
-        cudaMalloc(&dids, sizeof(int) * (size_t)nq * k) != cudaSuccess) {
-        cudaGetLastError();
-        s = DISC_ERR_OOM;
-    }
-    if (s == DISC_OK) {
-        cudaMemcpyAsync(dq, q, sizeof(float) * (size_t)nq * D, cudaMemcpyHostToDevice, m->stream);
-        launch_query_topk(dq, nq, D, m->inst, nid, dsc, k, dids, dout, m->stream);
-        cudaMemcpyAsync(ids, dids, sizeof(int) * (size_t)nq * k, cudaMemcpyDeviceToHost, m->stream);
-        cudaMemcpyAsync(scores, dout, sizeof(float) * (size_t)nq * k, cudaMemcpyDeviceToHost, m->stream);
-        s = cuda_status(cudaStreamSynchronize(m->stream));
-    }
-    cudaFree(dq);
-    cudaFree(dsc);
-    cudaFree(dout);
-    cudaFree(dids);
-    return s;
+    const size_t b_q = align256(sizeof(float) * (size_t)nq * D), b_s = align256(sizeof(float) * (size_t)nq * nid);
+    const size_t b_o = align256(sizeof(float) * (size_t)nq * k);
+    unsigned char* base = query_scratch(m, b_q + b_s + 2 * b_o);
+    if (!base) return DISC_ERR_OOM;
+    float* dq = (float*)base;
+    float* dsc = (float*)(base + b_q);
+    float* dout = (float*)(base + b_q + b_s);
+    int* dids = (int*)(base + b_q + b_s + b_o);
+    CK(cudaMemcpyAsync(dq, q, sizeof(float) * (size_t)nq * D, cudaMemcpyHostToDevice, m->stream));
+    launch_query_topk(dq, nq, D, m->inst, nid, dsc, k, dids, dout, m->stream);
+    CK(cudaMemcpyAsync(ids, dids, sizeof(int) * (size_t)nq * k, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaMemcpyAsync(scores, dout, sizeof(float) * (size_t)nq * k, cudaMemcpyDeviceToHost, m->stream));
+    return cuda_status(cudaStreamSynchronize(m->stream));
 }
 
 disc_status disc_query_points(disc_map* m, const float* xyz, int64_t n, int32_t* ids)
@@ -1300,22 +1325,15 @@ disc_status disc_query_points(disc_map* m, const float* xyz, int64_t n, int32_t*
     if (!m || n < 0 || (n > 0 && (!xyz || !ids))) return DISC_ERR_INVALID_ARG;
     if (n == 0) return DISC_OK;
     CK(cudaSetDevice(m->cfg.device));
-    float* dx = nullptr;
-    int* di = nullptr;
-    disc_status s = DISC_OK;
-    if (cudaMalloc(&dx, sizeof(float) * 3 * n) != cudaSuccess || cudaMalloc(&di, sizeof(int) * n) != cudaSuccess) {
-        cudaGetLastError();
-        s = DISC_ERR_OOM;
-    }
-    if (s == DISC_OK) {
-        cudaMemcpyAsync(dx, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream);
-        launch_query_points(dx, n, m->cfg.voxel_size, m->vt, m->inst, di, m->stream);
-        cudaMemcpyAsync(ids, di, sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream);
-        s = cuda_status(cudaStreamSynchronize(m->stream));
-    }
-    cudaFree(dx);
-    cudaFree(di);
-    return s;
+    const size_t b_x = align256(sizeof(float) * 3 * (size_t)n);
+    unsigned char* base = query_scratch(m, b_x + sizeof(int) * (size_t)n);
+    if (!base) return DISC_ERR_OOM;
+    float* dx = (float*)base;
+    int* di = (int*)(base + b_x);
+    CK(cudaMemcpyAsync(dx, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m->stream));
+    launch_query_points(dx, n, m->cfg.voxel_size, m->vt, m->inst, di, m->stream);
+    CK(cudaMemcpyAsync(ids, di, sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream));
+    return cuda_status(cudaStreamSynchronize(m->stream));
 }
 
 // checkpoint file: magic, config, counts, voxels (key, label), instance table

@@ -339,7 +339,13 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     const size_t tok = (size_t)g.patch_h * g.patch_w * g.embed_dim * (f->token_dtype == DISC_TOKENS_BF16 ? 2 : 4);
     const size_t od = 0, ol = od + ((4 * npx + 15) & ~(size_t)15), ot = ol + ((2 * npx + 15) & ~(size_t)15);
     const size_t og = ot + ((tok + 15) & ~(size_t)15), total = og + 4 * (size_t)g.embed_dim;
-    const cudaMemcpyKind kind = f->inputs_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    auto copy = [&](void* dst, const void* src, size_t n) {
+        if (!f->inputs_on_device) {
+            std::memcpy(dst, src, n);
+            return true;
+        }
+        return cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
     Request r;
     r.t_submit = Clock::now();
     {
@@ -352,10 +358,9 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     }
     r.host_bytes = total;
     // the caller's inputs, copied now (host or device pointers)
-    bool ok = cudaMemcpy(r.host + od, f->depth, 4 * npx, kind) == cudaSuccess &&
-              cudaMemcpy(r.host + ol, f->labels, 2 * npx, kind) == cudaSuccess &&
-              cudaMemcpy(r.host + ot, f->tokens, tok, kind) == cudaSuccess;
-    if (ok && f->global_embed) ok = cudaMemcpy(r.host + og, f->global_embed, 4 * (size_t)g.embed_dim, kind) == cudaSuccess;
+    bool ok = copy(r.host + od, f->depth, 4 * npx) && copy(r.host + ol, f->labels, 2 * npx) &&
+              copy(r.host + ot, f->tokens, tok);
+    if (ok && f->global_embed) ok = copy(r.host + og, f->global_embed, 4 * (size_t)g.embed_dim);
     if (!ok) {
         cudaGetLastError();
         std::lock_guard<std::mutex> lk(s->mu);
