@@ -169,7 +169,7 @@ bool config_ok(const disc_map_config& c)
     if (c.voxel_capacity <= 0 || !(c.max_load > 0.0f && c.max_load < 1.0f)) return false;
     if (c.instance_capacity <= 0) return false;
     if (c.batch_frames < 0 || c.batch_frames > 256) return false;
-    if (c.precision != DISC_FP32) return false;  // only the fp32 fast path is built
+    if (c.precision != DISC_FP32 && c.precision != DISC_BF16) return false;  // FP8 E4M3 is not built
     return true;
 }
 
@@ -330,6 +330,7 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
     in.count = m->mem.get<long long>(cap);
     in.Q = m->mem.get<float>(cap);
     in.E = m->mem.get<float>((size_t)cap * m->D);
+    in.Eb = m->cfg.precision == DISC_BF16 ? m->mem.get<uint16_t>((size_t)cap * m->D) : nullptr;
     in.n_obs = m->mem.get<int32_t>(cap);
     if (m->mem.failed) {
         m->mem.failed = false;
@@ -337,6 +338,7 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
         if (in.count) m->mem.release(in.count, sizeof(long long) * cap);
         if (in.Q) m->mem.release(in.Q, sizeof(float) * cap);
         if (in.E) m->mem.release(in.E, sizeof(float) * (size_t)cap * m->D);
+        if (in.Eb) m->mem.release(in.Eb, sizeof(uint16_t) * (size_t)cap * m->D);
         if (in.n_obs) m->mem.release(in.n_obs, sizeof(int32_t) * cap);
         return DISC_ERR_OOM;
     }
@@ -411,6 +413,8 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     CK(cudaMemcpyAsync(ni.count, m->inst.count, sizeof(long long) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ni.Q, m->inst.Q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ni.E, m->inst.E, sizeof(float) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+    if (ni.Eb)
+        CK(cudaMemcpyAsync(ni.Eb, m->inst.Eb, sizeof(uint16_t) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ni.n_obs, m->inst.n_obs, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     const int oc = m->inst.cap;
@@ -418,6 +422,7 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     m->mem.release(m->inst.count, sizeof(long long) * oc);
     m->mem.release(m->inst.Q, sizeof(float) * oc);
     m->mem.release(m->inst.E, sizeof(float) * (size_t)oc * m->D);
+    if (m->inst.Eb) m->mem.release(m->inst.Eb, sizeof(uint16_t) * (size_t)oc * m->D);
     m->mem.release(m->inst.n_obs, sizeof(int32_t) * oc);
     m->inst = ni;
     return DISC_OK;
@@ -514,8 +519,13 @@ void reset_timing(Runner& r, bool enable)
 // early in their blocks) and per-frame values and map state are read on the
 // device, so the sequence depends on (S, G, J, token dtypes) only and is
 // replayed as a CUDA graph.
-int enqueue_batch_kernels(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32)
+// combos: bit (2 * token_bf16 + precision_bf16) set for every kind of frame in the batch
+int enqueue_batch_kernels(Runner& r, int S, int G, int J, int combos)
 {
+    const bool any_bf16 = (combos & 12) != 0, any_f32 = (combos & 3) != 0;
+    bool any[2][2];
+    for (int t = 0; t < 2; t++)
+        for (int q = 0; q < 2; q++) any[t][q] = (combos >> (2 * t + q)) & 1;
     const int D = r.D, P = r.P, Mmax = r.Mmax;
     cudaStream_t st = r.stream;
     const BatchScratch& bs = r.bs;
@@ -527,7 +537,7 @@ int enqueue_batch_kernels(Runner& r, int S, int G, int J, bool any_bf16, bool an
     run_phase(r, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, S, r.Ph, r.Pw, Mmax, st); });
     run_phase(r, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
     run_phase(r, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(r, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(r, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, st); });
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
             const int nb = std::min(GEOMETRY_CHUNK, S - f0);
@@ -536,11 +546,6 @@ int enqueue_batch_kernels(Runner& r, int S, int G, int J, bool any_bf16, bool an
         }
         run_phase(r, PH_ENTRIES, [&] { return launch_quality(dfp, bs, S, st); });
     }
-    // error bound of the tensor-core pooled embedding relative to
-    // sum_p w_p ||f_p||: split residue 3 * 2^-22 plus fp32 accumulation of
-    // 3 K products; and of a warp-level fp32 cosine
-    const float eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * r.Kpad * std::ldexp(1.0, -24));
-    const float dot_err = (float)(3.0 * D * std::ldexp(1.0, -24));
     SerialStep step;
     step.refs = refs;
     step.slot_of = r.slot_of();
@@ -550,14 +555,14 @@ int enqueue_batch_kernels(Runner& r, int S, int G, int J, bool any_bf16, bool an
     for (int j = 0; j < J; j++) {
         step.j = j;
         for (int ph = 0; ph < 4; ph++)
-            run_phase(r, PH_OVERLAP + ph, [&] { return launch_serial_step(dfp, bs, step, G, eta, dot_err, ph, st); });
+            run_phase(r, PH_OVERLAP + ph, [&] { return launch_serial_step(dfp, bs, step, G, ph, st); });
     }
     return (int)(r.launches - before);
 }
 
-long long graph_key(int S, int G, int J, bool any_bf16, bool any_f32)
+long long graph_key(int S, int G, int J, int combos)
 {
-    return ((((long long)S << 20) | ((long long)G << 10) | J) << 2) | (any_bf16 ? 2 : 0) | (any_f32 ? 1 : 0);
+    return ((((long long)S << 20) | ((long long)G << 10) | J) << 4) | combos;
 }
 
 // The batch's kernel sequence captured once per shape and replayed.  A shape
@@ -566,9 +571,9 @@ long long graph_key(int S, int G, int J, bool any_bf16, bool any_f32)
 // costs more than launching the kernels.  At most kMaxGraphs are kept.
 constexpr int kMaxGraphs = 64;
 
-disc_status batch_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32, BatchGraph** out)
+disc_status batch_graph(Runner& r, int S, int G, int J, int combos, BatchGraph** out)
 {
-    const long long key = graph_key(S, G, J, any_bf16, any_f32);
+    const long long key = graph_key(S, G, J, combos);
     *out = nullptr;
     auto it = r.graphs.find(key);
     if (it != r.graphs.end()) {
@@ -585,7 +590,7 @@ disc_status batch_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_
     const int64_t before = r.launches;
     int64_t pl0[PH_COUNT];
     for (int i = 0; i < PH_COUNT; i++) pl0[i] = r.phase_launches[i];
-    const int n = enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+    const int n = enqueue_batch_kernels(r, S, G, J, combos);
     r.launches = before;  // counted when the graph is launched
     for (int i = 0; i < PH_COUNT; i++) r.phase_launches[i] = pl0[i];
     cudaError_t e = cudaStreamEndCapture(r.stream, &graph);
@@ -609,7 +614,7 @@ disc_status batch_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_
 // Timing run of one batch: the sequence with its phase events is captured and
 // launched as one graph, so the device never waits on the host inside a
 // timed interval.  false: capture is not possible here (plain launches).
-bool launch_timed_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_f32)
+bool launch_timed_graph(Runner& r, int S, int G, int J, int combos)
 {
     const size_t marks0 = r.marks.size(), ev0 = r.ev_used;
     const int64_t l0 = r.launches;
@@ -626,7 +631,7 @@ bool launch_timed_graph(Runner& r, int S, int G, int J, bool any_bf16, bool any_
         undo();
         return false;
     }
-    enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+    enqueue_batch_kernels(r, S, G, J, combos);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if (cudaStreamEndCapture(r.stream, &graph) != cudaSuccess || !graph ||
@@ -696,6 +701,22 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     fp.min_px = std::max(1, m->cfg.min_mask_pixels);
     fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
     fp.map = g;
+    // error bounds of the fast score, relative to sum_p w_p ||f_p|| (pooled
+    // embedding) and absolute on the cosine:
+    //   FP32: tf32 split residue 3 * 2^-22 plus fp32 accumulation of 3 K
+    //         products; fp32 warp cosine 3 D 2^-24
+    //   BF16: both operands rounded to bf16, 2 * 2^-9, plus fp32 accumulation
+    //         of K products; the bf16 scoring copy of E_k adds 2^-9 relative,
+    //         at most 2 * 2^-9 on the cosine
+    const double K = r.Kpad, u24 = std::ldexp(1.0, -24), u9 = std::ldexp(1.0, -9);
+    fp.precision = m->cfg.precision;
+    if (m->cfg.precision == DISC_BF16) {
+        fp.eta = (float)(2.0 * u9 + u9 * u9 + 3.0 * K * u24);
+        fp.dot_err = (float)(3.0 * u9 + 3.0 * D * u24);
+    } else {
+        fp.eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * K * u24);
+        fp.dot_err = (float)(3.0 * D * u24);
+    }
     const size_t npx = (size_t)fp.H * fp.W;
     const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
     if (f->inputs_on_device) {
@@ -782,7 +803,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         }
         const int G = (int)gl.size();
         if (G == 0) break;
-        bool any_bf16 = false, any_f32 = false;
+        int combos = 0;
         for (int gi = 0; gi < G && s == DISC_OK; gi++) {
             Work& wk = w[gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
@@ -792,8 +813,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 const disc_frame& f = wk.frames[lo + j];
                 px += (uint64_t)f.width * f.height;
                 masks += f.num_masks;
-                any_bf16 |= f.token_dtype == DISC_TOKENS_BF16;
-                any_f32 |= f.token_dtype == DISC_TOKENS_F32;
+                combos |= 1 << (2 * (f.token_dtype == DISC_TOKENS_BF16) + (wk.m->cfg.precision == DISC_BF16));
             }
             s = ensure_voxel_room(wk.m, px, r.stream);
             if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, r.stream);
@@ -823,7 +843,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         s = cuda_status(cudaMemcpyAsync(r.d_param, blk.data(), r.param_bytes, cudaMemcpyHostToDevice, r.stream));
         if (s != DISC_OK) break;
         BatchGraph* g = nullptr;
-        if (!r.timing && !r.graphs_off && batch_graph(r, S, G, J, any_bf16, any_f32, &g) != DISC_OK) {
+        if (!r.timing && !r.graphs_off && batch_graph(r, S, G, J, combos, &g) != DISC_OK) {
             r.graphs_off = true;  // this stream or driver cannot capture the sequence
             g = nullptr;
         }
@@ -831,8 +851,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (g) {
             s = cuda_status(cudaGraphLaunch(g->exec, r.stream));
             r.launches += g->kernels;
-        } else if (!(r.timing && !r.graphs_off && launch_timed_graph(r, S, G, J, any_bf16, any_f32))) {
-            enqueue_batch_kernels(r, S, G, J, any_bf16, any_f32);
+        } else if (!(r.timing && !r.graphs_off && launch_timed_graph(r, S, G, J, combos))) {
+            enqueue_batch_kernels(r, S, G, J, combos);
         }
         // the batch's counters, in slot order, to the call's history
         if (s == DISC_OK)
@@ -1391,6 +1411,7 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     std::vector<int32_t> parent(std::max(nid, 1)), obs(std::max(nid, 1));
     std::vector<int64_t> count(std::max(nid, 1));
     std::vector<float> Q(std::max(nid, 1)), E((size_t)std::max(nid, 1) * D);
+    std::vector<uint16_t> Eb(ok && c.precision == DISC_BF16 ? (size_t)std::max(nid, 1) * D : 0);
     if (ok && nv) ok = std::fread(keys.data(), 8, nv, fp) == (size_t)nv && std::fread(ids.data(), 4, nv, fp) == (size_t)nv;
     if (ok && nid)
         ok = std::fread(parent.data(), 4, nid, fp) == (size_t)nid && std::fread(count.data(), 8, nid, fp) == (size_t)nid &&
@@ -1430,6 +1451,15 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
         cudaMemcpyAsync(m->inst.count, count.data(), 8 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->inst.Q, Q.data(), 4 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->inst.E, E.data(), 4 * (size_t)nid * D, cudaMemcpyHostToDevice, m->stream);
+        if (m->inst.Eb) {
+            // bf16 scoring copy, rounded to nearest even as on the device
+            for (size_t i = 0; i < (size_t)nid * D; i++) {
+                uint32_t b;
+                std::memcpy(&b, &E[i], 4);
+                Eb[i] = (uint16_t)((b + 0x7fffu + ((b >> 16) & 1u)) >> 16);
+            }
+            cudaMemcpyAsync(m->inst.Eb, Eb.data(), 2 * (size_t)nid * D, cudaMemcpyHostToDevice, m->stream);
+        }
         cudaMemcpyAsync(m->inst.n_obs, obs.data(), 4 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->d_next_id, &nid, sizeof(int), cudaMemcpyHostToDevice, m->stream);
     }

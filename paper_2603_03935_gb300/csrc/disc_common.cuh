@@ -110,6 +110,7 @@ struct Instances {
     long long* count;            // voxels per root
     float* Q;
     float* E;                    // [cap][D] stored embedding
+    uint16_t* Eb;                // [cap][D] bf16 scoring copy of E (BF16 precision), else NULL
     int32_t* n_obs;
     int32_t cap;
 };
@@ -264,6 +265,9 @@ struct FrameParams {
     int32_t ov_num, ov_den, min_px;
     int32_t token_bf16;
     int32_t map;           // position of the frame's map in the batch (MapRefs index)
+    int32_t precision;     // disc_precision of the fast pooled embedding and scoring
+    float eta;             // bound of |E_fast - E| relative to sum_p w_p ||f_p||
+    float dot_err;         // bound of the fast cosine's own error
     const float* depth;
     const uint16_t* labels;
     const void* tokens;

@@ -7,9 +7,11 @@
 // of one tcgen05 MMA and the masks (<= 256) form its N dimension:
 //   A (128 x 32, K-major) = F^T tile  -- transposed while staged into shared memory
 //   B (N   x 32, K-major) = W tile    -- W rows are already K-contiguous
-// The fp32 operands are split as x = hi + lo with hi, lo TF32 and three
-// kind::tf32 MMAs (hi*hi + hi*lo + lo*hi) accumulate in fp32 in TMEM, which
-// keeps the fp32-level accuracy of the product (relative error ~1e-6).
+// FP32 precision: the fp32 operands are split as x = hi + lo with hi, lo TF32
+// and three kind::tf32 MMAs (hi*hi + hi*lo + lo*hi) accumulate in fp32 in
+// TMEM, which keeps the fp32-level accuracy of the product (relative error
+// ~1e-6).  BF16 precision: both operands rounded to bf16 (tokens given in
+// bf16 are exact), one kind::f16 MMA per 16-wide K step, fp32 accumulation.
 //
 // One CTA = one 128-row tile of D; one elected thread issues the MMAs; a
 // two-stage shared-memory ring is recycled through mbarriers that
@@ -62,6 +64,26 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Instruction descriptor of kind::f16 with bf16 A/B: D fp32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -103,8 +125,8 @@ __device__ __forceinline__ float ldtok<__nv_bfloat16>(const __nv_bfloat16* F, si
 
 }  // namespace
 
-constexpr uint32_t A_TILE_BYTES = GEMM_MT * GEMM_KC * 4;  // 16 KB
-constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 4-wide K group
+constexpr uint32_t A_TILE_BYTES = GEMM_MT * GEMM_KC * 4;  // 16 KB (tf32); bf16 tiles take half
+constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 16-byte K group (4 tf32 / 8 bf16)
 
 // two pipeline stages + barriers; the trailing guard keeps every address an
 // MMA descriptor of this kernel can form inside the allocation
@@ -116,7 +138,7 @@ __host__ size_t gemm_smem_bytes(int NT)
     return std::min(base + GEMM_SMEM_GUARD, std::max(base, SMEM_MAX));
 }
 
-template <typename T>
+template <typename T, bool BF>
 __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -126,12 +148,17 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     const T* F = (const T*)fp.tokens;
     const int D = fp.D, P = fp.P, M = fp.M;
     const int d0 = blockIdx.x * GEMM_MT;
-    // uniform for the block: other dtype, no masks, tile past D, failed frame
-    if (fp.token_bf16 != (sizeof(T) == 2) || M <= 0 || d0 >= D || sc.ctr->err) return;
+    // uniform for the block: other dtype or precision, no masks, tile past D,
+    // failed frame
+    if (fp.token_bf16 != (sizeof(T) == 2) || (fp.precision == DISC_BF16) != BF || M <= 0 || d0 >= D ||
+        sc.ctr->err)
+        return;
 
-    const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * 4;
+    // per stage: tf32 A hi | A lo | B hi | B lo, or bf16 A | B
+    const uint32_t A_BYTES = BF ? A_TILE_BYTES / 2 : A_TILE_BYTES;
+    const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * (BF ? 2 : 4);
     const uint32_t B_LBO = (uint32_t)NT * 16;
-    const uint32_t STAGE = 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
+    const uint32_t STAGE = BF ? A_BYTES + B_TILE_BYTES : 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
     uint64_t* mbar = (uint64_t*)(smem + 2 * STAGE);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 2);
     uint32_t ncols = 32;
@@ -152,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = idesc_tf32(GEMM_MT, NT);
+    const uint32_t idesc = BF ? idesc_bf16(GEMM_MT, NT) : idesc_tf32(GEMM_MT, NT);
     const int nchunks = (P + GEMM_KC - 1) / GEMM_KC;
     bool failed = false;
     int last_commit = -1;  // chunk of the most recent commit (same on all threads)
@@ -166,6 +193,36 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
             if (__syncthreads_or(!ok)) { failed = true; break; }
         }
         const int p0 = c * GEMM_KC;
+        if constexpr (BF) {
+            // A: F^T tile in bf16, thread tid owns row d0 + tid, 8 patches per 16 B
+            {
+                const int d = d0 + tid;
+#pragma unroll
+                for (int kq = 0; kq < GEMM_KC / 8; kq++) {
+                    float x[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        const int p = p0 + 8 * kq + j;
+                        x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
+                    }
+                    const uint4 v = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]),
+                                               pack_bf16(x[6], x[7]));
+                    *(uint4*)(st + kq * A_LBO + tid * 16) = v;
+                }
+            }
+            // B: W tile in bf16, NT rows x 32 patches
+            {
+                uint8_t* Bt = st + A_BYTES;
+                for (int g = tid; g < NT * (GEMM_KC / 8); g += 128) {
+                    const int n = g >> 2, kq = g & 3;
+                    const float4 x0 = *(const float4*)(sc.W + (size_t)n * fp.Kpad + p0 + 8 * kq);
+                    const float4 x1 = *(const float4*)(sc.W + (size_t)n * fp.Kpad + p0 + 8 * kq + 4);
+                    const uint4 v = make_uint4(pack_bf16(x0.x, x0.y), pack_bf16(x0.z, x0.w), pack_bf16(x1.x, x1.y),
+                                               pack_bf16(x1.z, x1.w));
+                    *(uint4*)(Bt + kq * B_LBO + n * 16) = v;
+                }
+            }
+        } else {
         // A: F^T tile. Thread tid owns row r = tid (token dimension d0 + tid).
         {
             const int d = d0 + tid;
@@ -206,21 +263,33 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
                 *(float4*)(Blo + off) = lo;
             }
         }
+        }
         // make the generic-proxy stores visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             fence_after();
-            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_TILE_BYTES;
-            const uint32_t b_hi = a_hi + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+            if constexpr (BF) {
+                // K step 16 = two 16-byte core-matrix columns of bf16
+                const uint32_t a0 = smem_u32(st), b0 = a0 + A_BYTES;
 #pragma unroll
-            for (int ks = 0; ks < GEMM_KC / 8; ks++) {
-                const uint32_t ao = ks * 2 * A_LBO, bo = ks * 2 * B_LBO;
-                const uint64_t dah = smem_desc(a_hi + ao, A_LBO, 128), dal = smem_desc(a_lo + ao, A_LBO, 128);
-                const uint64_t dbh = smem_desc(b_hi + bo, B_LBO, 128), dbl = smem_desc(b_lo + bo, B_LBO, 128);
-                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                mma_tf32(tmem, dah, dbl, idesc, 1u);
-                mma_tf32(tmem, dal, dbh, idesc, 1u);
+                for (int ks = 0; ks < GEMM_KC / 16; ks++) {
+                    const uint32_t ao = ks * 2 * A_LBO, bo = ks * 2 * B_LBO;
+                    mma_bf16(tmem, smem_desc(a0 + ao, A_LBO, 128), smem_desc(b0 + bo, B_LBO, 128), idesc,
+                             (c > 0 || ks > 0) ? 1u : 0u);
+                }
+            } else {
+                const uint32_t a_hi = smem_u32(st), a_lo = a_hi + A_TILE_BYTES;
+                const uint32_t b_hi = a_hi + 2 * A_TILE_BYTES, b_lo = b_hi + B_TILE_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < GEMM_KC / 8; ks++) {
+                    const uint32_t ao = ks * 2 * A_LBO, bo = ks * 2 * B_LBO;
+                    const uint64_t dah = smem_desc(a_hi + ao, A_LBO, 128), dal = smem_desc(a_lo + ao, A_LBO, 128);
+                    const uint64_t dbh = smem_desc(b_hi + bo, B_LBO, 128), dbl = smem_desc(b_lo + bo, B_LBO, 128);
+                    mma_tf32(tmem, dah, dbh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(tmem, dah, dbl, idesc, 1u);
+                    mma_tf32(tmem, dal, dbh, idesc, 1u);
+                }
             }
             mma_commit(smem_u32(&mbar[s]));
         }
@@ -264,25 +333,31 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, bool any_bf16,
-                     bool any_f32, cudaStream_t st)
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][2],
+                     cudaStream_t st)
 {
     if (Mmax <= 0) return 0;
     const int NT = std::max(16, (Mmax + 15) / 16 * 16);
     const size_t smem = gemm_smem_bytes(NT);
     dim3 g((D + GEMM_MT - 1) / GEMM_MT, B);
     int n = 0;
-    if (any_f32) { k_pool_gemm<float><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
-    if (any_bf16) { k_pool_gemm<__nv_bfloat16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][0]) { k_pool_gemm<float, false><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][0]) { k_pool_gemm<__nv_bfloat16, false><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][1]) { k_pool_gemm<float, true><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][1]) { k_pool_gemm<__nv_bfloat16, true><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
     return n;
 }
 
 cudaError_t set_gemm_kernel_attrs()
 {
     const int mx = (int)gemm_smem_bytes(MAX_MASKS);
-    cudaError_t e = cudaFuncSetAttribute(k_pool_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = cudaFuncSetAttribute(k_pool_gemm<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pool_gemm<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
 }
 

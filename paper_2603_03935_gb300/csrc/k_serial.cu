@@ -11,6 +11,8 @@
 //                          (one CTA)
 //   k_apply    Sec. III-B  embedding copies, insertion of the new voxels,
 //                          flattening of the parent table, cleanup
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <climits>
 
@@ -147,13 +149,22 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
 }
 
 // ---- gates per (segment, instance) pair: one warp per pair -----------------------
-struct ScoreParams {
-    float eta;      // error bound of the tensor-core pooled embedding, relative to sum_p w_p ||f_p||
-    float dot_err;  // error bound of an fp32 warp cosine
-};
+// The fast cosine takes the tensor-core pooled embedding and the instance's
+// scoring copy (fp32, or bf16 at BF16 precision); inside its error band the
+// pair is re-scored exactly.
+__device__ __forceinline__ unsigned bf16_pair(float lo, float hi)
+{
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
 
-__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
-                            const ScoreParams& sp)
+__device__ __forceinline__ float4 bf16x4_to_f32(uint2 v)
+{
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u), __uint_as_float(v.y << 16),
+                       __uint_as_float(v.y & 0xffff0000u));
+}
+
+__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst)
 {
     const int lane = threadIdx.x & 31;
     const int npairs = sc.ctr->n_pairs;
@@ -171,7 +182,36 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
         const float* a = sc.Efast + (size_t)m * D;
         const float* b = inst.E + (size_t)k * D;
         float dt = 0.0f, na = 0.0f, nb = 0.0f;
-        if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads, 8 in flight per lane
+        if (inst.Eb && (D & 3) == 0) {  // bf16 scoring copy: 8-byte rows of 4
+            const float4* a4 = (const float4*)a;
+            const uint2* b4 = (const uint2*)(inst.Eb + (size_t)k * D);
+            const int n4 = D >> 2;
+            for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+                float4 xs[4];
+                uint2 ys[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int d = d0 + j * 32 + lane;
+                    xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ys[j] = d < n4 ? b4[d] : make_uint2(0u, 0u);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float4 x = xs[j], y = bf16x4_to_f32(ys[j]);
+                    dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                    nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+                }
+            }
+        } else if (inst.Eb) {
+            const uint16_t* bb = inst.Eb + (size_t)k * D;
+            for (int d = lane; d < D; d += 32) {
+                const float x = a[d], y = __uint_as_float((unsigned)bb[d] << 16);
+                dt += x * y;
+                na += x * x;
+                nb += y * y;
+            }
+        } else if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads, 8 in flight per lane
             const float4* a4 = (const float4*)a;
             const float4* b4 = (const float4*)b;
             const int n4 = D >> 2;
@@ -204,7 +244,7 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
         nb = warp_sum(nb);
         bool edge;
         const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
-        const float band = (na > 0.0f) ? 2.2f * sp.eta * sc.Bm[m] / sqrtf(na) + sp.dot_err + 1e-6f : 2.0f;
+        const float band = (na > 0.0f) ? 2.2f * fp.eta * sc.Bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
         if (fabsf(cf - fp.tau) > band) {
             edge = cf >= fp.tau;
         } else {
@@ -497,6 +537,7 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Seri
             const int src = ss.copy_src[c];
             const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
             float* to = inst.E + (size_t)ss.copy_dst[c] * D;
+            uint16_t* tb = inst.Eb ? inst.Eb + (size_t)ss.copy_dst[c] * D : nullptr;  // bf16 scoring copy
             if ((D & 3) == 0) {
                 const float4* f4 = (const float4*)from;
                 float4* t4 = (float4*)to;
@@ -511,11 +552,17 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Seri
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
                         const int d = d0 + j * 32 + lane;
-                        if (d < n4) t4[d] = r[j];
+                        if (d < n4) {
+                            t4[d] = r[j];
+                            if (tb) ((uint2*)tb)[d] = make_uint2(bf16_pair(r[j].x, r[j].y), bf16_pair(r[j].z, r[j].w));
+                        }
                     }
                 }
             } else {
-                for (int d = lane; d < D; d += 32) to[d] = from[d];
+                for (int d = lane; d < D; d += 32) {
+                    to[d] = from[d];
+                    if (tb) tb[d] = __bfloat16_as_ushort(__float2bfloat16_rn(from[d]));
+                }
             }
         }
         // new voxels: the lowest segment index owns a voxel
@@ -593,7 +640,7 @@ __global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, Serial
     phase_overlap(bs.frame(slot), ss, vt, inst, ov_smem);
 }
 
-__global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st, ScoreParams sp)
+__global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
     bool blocked;
     const int slot = block_slot(bs, st, &blocked);
@@ -601,7 +648,7 @@ __global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st, 
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
     const Instances inst = R.inst;
-    phase_score(fps[slot], bs.frame(slot), ss, inst, sp);
+    phase_score(fps[slot], bs.frame(slot), ss, inst);
 }
 
 __global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* fps, BatchScratch bs, SerialStep st)
@@ -636,15 +683,15 @@ static int per_map(int full, int G, int least)
     return std::max(least, (full + G - 1) / G);
 }
 
-int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, float eta,
-                       float dot_err, int phase, cudaStream_t st_)
+int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int phase,
+                       cudaStream_t st_)
 {
     switch (phase) {
         case 0:
             k_overlap<<<dim3(per_map(152 * 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(bs, st);
             return 1;
         case 1:
-            k_score<<<dim3(per_map(152, G, 4), G), 256, 0, st_>>>(fps, bs, st, ScoreParams{eta, dot_err});
+            k_score<<<dim3(per_map(152, G, 4), G), 256, 0, st_>>>(fps, bs, st);
             return 1;
         case 2:
             k_union<<<dim3(1, G), UNION_THREADS, UNION_SMEM, st_>>>(fps, bs, st);

@@ -41,8 +41,9 @@ int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int P
 int launch_weights(const FrameParams* fps, const BatchScratch& bs, int B, int Mmax, cudaStream_t st);
 int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, int Mmax, bool any_bf16,
                       bool any_f32, cudaStream_t st);
-int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, bool any_bf16,
-                     bool any_f32, cudaStream_t st);
+// one launch per (token dtype, precision) present: any[tok_bf16][prec_bf16]
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][2],
+                     cudaStream_t st);
 // back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
 // batch start) on frames [f0, f0 + nb); then Q of every segment
 int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
@@ -54,8 +55,8 @@ constexpr int GEOMETRY_CHUNK = 4;
 
 // serial part, step st.j over the G maps of a batch: phase 0 overlap,
 // 1 score, 2 union, 3 apply
-int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, float eta,
-                       float dot_err, int phase, cudaStream_t stream);
+int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int phase,
+                       cudaStream_t stream);
 
 size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);

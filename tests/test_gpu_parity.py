@@ -278,3 +278,101 @@ def test_bf16_tokens_parity(torch_dev):
         o = omap.integrate(fr.depth[i], fr.labels[i], t32, fr.poses[i], intr, fr.num_masks[i])
         common.compare_frame(st, gmap.last_frame(), o, ctx=f"bf16 frame {i}")
     common.compare_maps(gmap, omap, ctx="bf16 tokens")
+
+
+# BF16 precision: the fast pooled embedding (bf16 operands, fp32 accumulation
+# on the tensor cores) and the bf16 scoring copies only decide which pairs get
+# an exact re-score, so labels, counts and stored embeddings stay identical
+# to the oracle; the fast embedding's error against the fp64 pooling twin
+# stays within the bound the re-score band is built from.
+BF16_ETA = 2 * 2.0 ** -9 + 2.0 ** -18
+
+
+def _bf16_fast_error(rep, tokens, scene):
+    Dp64, E64 = oracle.pool_f64(tokens, rep["cov"], rep["npix"])
+    worst = 0.0
+    for m in range(len(rep["npix"])):
+        if rep["npix"][m] < 1 or not np.any(rep["W"][m]):
+            continue  # masks below the size filter carry no weights
+        # sum_p w_p ||f_p||
+        w = rep["W"][m].astype(np.float64)
+        bsum = float(np.sum(w * np.linalg.norm(tokens.astype(np.float64), axis=1)))
+        K = (scene.patch_h * scene.patch_w + 31) // 32 * 32
+        bound = (BF16_ETA + 3 * K * 2.0 ** -24) * bsum
+        err = float(np.linalg.norm(rep["E_fast"][m].astype(np.float64) - E64[m]))
+        assert err <= bound, f"mask {m}: |E_fast - E_fp64| = {err} > {bound}"
+        worst = max(worst, err / max(float(np.linalg.norm(E64[m])), 1e-30))
+    return worst
+
+
+def test_bf16_precision_parity_and_fp64_error(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(20))
+    cfg = common.disc_cfg(sc, precision=1)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    worst = 0.0
+    for i in range(len(fr)):
+        st = gmap.integrate(_dframe(torch, dev, fr, i))
+        o = omap.integrate(*oracle.frame_args(fr, i))
+        rep = gmap.last_frame()
+        common.compare_frame(st, rep, o, ctx=f"bf16 precision frame {i}", efast_tol=2e-2)
+        worst = max(worst, _bf16_fast_error(rep, fr.tokens[i], sc))
+    common.compare_maps(gmap, omap, ctx="bf16 precision")
+    assert worst < 1e-2, worst
+
+
+def test_bf16_precision_borderline_rescored(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(3))
+    probe = oracle.OracleMap(**oracle.config_for_scene(sc))
+    probe.integrate(*oracle.frame_args(fr, 0))
+    E0 = probe.instances()["E"]
+    r1 = probe.integrate(*oracle.frame_args(fr, 1))
+    m = int(np.argmax(r1["nvox"]))
+    k = int(r1["rep"][m]) if r1["rep"][m] < len(E0) else 0
+    tau = oracle.cosine(r1["E"][m], E0[k])
+    for t in (tau, np.nextafter(np.float32(tau), np.float32(2))):
+        cfg = common.disc_cfg(sc, tau_cos=float(t), precision=1)
+        gmap = DiscMap(**cfg)
+        omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+        border = 0
+        for i in range(3):
+            st = gmap.integrate(_dframe(torch, dev, fr, i))
+            o = omap.integrate(*oracle.frame_args(fr, i))
+            common.compare_frame(st, gmap.last_frame(), o, ctx=f"bf16 tau={t} frame {i}", efast_tol=2e-2)
+            border += st["borderline_rescored"]
+        common.compare_maps(gmap, omap, ctx=f"bf16 tau={t}")
+        assert border >= 1
+
+
+def test_bf16_precision_checkpoint_and_mixed_group(torch_dev, tmp_path):
+    # a bf16-precision map next to fp32 maps in one group; its checkpoint
+    # reloads to the same scoring behaviour
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(12))
+    frames = [_dframe(torch, dev, fr, i) for i in range(12)]
+    a32, a16 = DiscMap(**common.disc_cfg(sc)), DiscMap(**common.disc_cfg(sc, precision=1))
+    grp = DiscGroup(max_maps=2, frames_per_map=4, embed_dim=sc.dim, patch_h=sc.patch_h, patch_w=sc.patch_w,
+                    max_width=sc.width, max_height=sc.height, max_masks=sc.max_masks)
+    _, done, rc = grp.integrate([a32, a16], [frames[:6], frames[:6]])
+    assert rc == 0 and done == [6, 6]
+    a16.save(tmp_path / "m16.disc")
+    b16 = DiscMap.load(tmp_path / "m16.disc")
+    _, done, rc = grp.integrate([a32, b16], [frames[6:], frames[6:]])
+    assert rc == 0
+    for m in (a16,):
+        _, d, rc1 = m.integrate_frames(frames[6:])
+        assert rc1 == 0
+    for x, y, ctx in ((a32, b16, "fp32 vs bf16"), (a16, b16, "bf16 alone vs reloaded in a group")):
+        kx, ix = x.voxels()
+        ky, iy = y.voxels()
+        assert np.array_equal(kx, ky) and np.array_equal(ix, iy), ctx
+        ex, ey = x.instances(), y.instances()
+        assert np.array_equal(ex["E"].view(np.uint32), ey["E"].view(np.uint32)), ctx
