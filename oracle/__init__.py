@@ -84,6 +84,9 @@ def lib():
         L.oracle_cosine.restype = f32
         L.oracle_cosine.argtypes = [vp, vp, i32]
         L.oracle_pool_f64.argtypes = [vp, i32, i32, vp, vp, i32, ctypes.c_double, vp, vp]
+        L.oracle_finalize.restype = ctypes.c_int
+        L.oracle_finalize.argtypes = [vp, ctypes.POINTER(FinalizeConfig), ctypes.POINTER(FinalizeReport)]
+        L.oracle_set_state.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, i32]
         _lib = L
     return _lib
 
@@ -107,6 +110,16 @@ def config_for_scene(scene, **kw) -> dict:
     return c
 
 
+class FinalizeConfig(ctypes.Structure):
+    _fields_ = [("min_voxels", ctypes.c_int32), ("contact_num", ctypes.c_int32), ("contact_den", ctypes.c_int32),
+                ("tau_cos", ctypes.c_float)]
+
+
+class FinalizeReport(ctypes.Structure):
+    _fields_ = [("contact_pairs", ctypes.c_int32), ("merged", ctypes.c_int32), ("removed", ctypes.c_int32),
+                ("removed_voxels", ctypes.c_int64)]
+
+
 class OracleMap:
     """One map integrated frame by frame on the CPU."""
 
@@ -124,6 +137,28 @@ class OracleMap:
         if h:
             lib().oracle_map_destroy(h)
             self._h = None
+
+    def finalize(self, min_voxels, contact_num=1, contact_den=5, tau_cos=None):
+        """End-of-trajectory orphan merge and noise filter; returns the report."""
+        c = FinalizeConfig(int(min_voxels), int(contact_num), int(contact_den),
+                           float(self.cfg["tau_cos"] if tau_cos is None else tau_cos))
+        r = FinalizeReport()
+        rc = lib().oracle_finalize(self._h, ctypes.byref(c), ctypes.byref(r))
+        if rc != 0:
+            raise ValueError(f"oracle_finalize: {rc}")
+        return {k: int(getattr(r, k)) for k, _ in FinalizeReport._fields_}
+
+    def set_state(self, keys, labels, parent, count, Q, E, n_obs):
+        """Replace the map's voxels and instances (exact test situations)."""
+        keys = np.ascontiguousarray(keys, np.uint64)
+        labels = np.ascontiguousarray(labels, np.int32)
+        parent = np.ascontiguousarray(parent, np.int32)
+        count = np.ascontiguousarray(count, np.int64)
+        Q = np.ascontiguousarray(Q, np.float32)
+        E = np.ascontiguousarray(E, np.float32).reshape(len(parent), self.D)
+        n_obs = np.ascontiguousarray(n_obs, np.int32)
+        lib().oracle_set_state(self._h, keys.ctypes.data, labels.ctypes.data, len(keys), parent.ctypes.data,
+                               count.ctypes.data, Q.ctypes.data, E.ctypes.data, n_obs.ctypes.data, len(parent))
 
     def integrate(self, depth, labels, tokens, pose, intr, num_masks, global_embed=None,
                   report: bool = True):

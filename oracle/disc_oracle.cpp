@@ -106,6 +106,7 @@ struct oracle_map {
     std::vector<float> Q;
     std::vector<std::vector<float>> E;
     std::vector<int32_t> n_obs;
+    bool final_ = false;  // finalised: no more frames
 };
 
 oracle_map* oracle_map_create(const oracle_config* cfg)
@@ -195,7 +196,7 @@ float oracle_cosine(const float* a, const float* b, int32_t D) { return cosine_e
 // ---- one frame ----------------------------------------------------------------
 int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_report* rep)
 {
-    if (!map || !fr) return ORACLE_ERR_INVALID_ARG;
+    if (!map || !fr || map->final_) return ORACLE_ERR_INVALID_ARG;
     const oracle_config& cfg = map->cfg;
     const int H = fr->height, Wd = fr->width, D = cfg.embed_dim;
     const int Ph = cfg.patch_h, Pw = cfg.patch_w, P = Ph * Pw;
@@ -528,7 +529,7 @@ void oracle_export_voxels(const oracle_map* map, uint64_t* keys, int32_t* ids)
     std::sort(v.begin(), v.end());
     for (size_t i = 0; i < v.size(); i++) {
         keys[i] = v[i].first;
-        ids[i] = map->parent[v[i].second];
+        ids[i] = v[i].second >= 0 ? map->parent[v[i].second] : -1;
     }
 }
 
@@ -545,6 +546,133 @@ void oracle_export_instances(const oracle_map* map, int32_t* parent, int64_t* co
         if (E) std::memcpy(E + i * D, map->E[i].data(), sizeof(float) * D);
         if (n_obs) n_obs[i] = map->n_obs[i];
     }
+}
+
+// ---- End of the trajectory: orphan merge and noise filter (Sec. III-B) --------
+namespace {
+
+int32_t find_root(std::vector<int32_t>& uf, int32_t x)
+{
+    while (uf[x] != x) x = uf[x];
+    return x;
+}
+
+// face neighbours of a voxel key (in range)
+int neighbours6(uint64_t key, uint64_t out[6])
+{
+    int32_t k[3];
+    unpack(key, k);
+    int n = 0;
+    for (int a = 0; a < 3; a++)
+        for (int s = -1; s <= 1; s += 2) {
+            int32_t q[3] = {k[0], k[1], k[2]};
+            q[a] += s;
+            if (q[a] < -KEY_BIAS || q[a] > KEY_BIAS - 1) continue;
+            out[n++] = ((uint64_t)(q[0] + KEY_BIAS) << (2 * KEY_BITS)) | ((uint64_t)(q[1] + KEY_BIAS) << KEY_BITS) |
+                       (uint64_t)(q[2] + KEY_BIAS);
+        }
+    return n;
+}
+
+}  // namespace
+
+int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_finalize_report* rep)
+{
+    if (!map || !cfg || cfg->contact_den <= 0 || cfg->contact_num < 0 || map->final_) return ORACLE_ERR_INVALID_ARG;
+    const int D = map->cfg.embed_dim;
+    const int32_t nid = (int32_t)map->parent.size();
+    oracle_finalize_report r{};
+    // (1) contacts between the instances (roots) of face-adjacent voxels
+    std::map<std::pair<int32_t, int32_t>, int64_t> contact;
+    for (const auto& kv : map->vox) {
+        if (kv.second < 0) continue;
+        const int32_t a = map->parent[kv.second];
+        uint64_t nb[6];
+        const int n = neighbours6(kv.first, nb);
+        std::set<int32_t> seen;
+        for (int i = 0; i < n; i++) {
+            auto it = map->vox.find(nb[i]);
+            if (it == map->vox.end() || it->second < 0) continue;
+            const int32_t b = map->parent[it->second];
+            if (b != a) seen.insert(b);
+        }
+        for (int32_t b : seen) contact[{std::min(a, b), std::max(a, b)}] += 1;
+    }
+    r.contact_pairs = (int32_t)contact.size();
+    // (2) gates on the state at the start; union by smallest id
+    std::vector<int32_t> uf(nid);
+    for (int32_t i = 0; i < nid; i++) uf[i] = i;
+    for (const auto& c : contact) {
+        const int32_t a = c.first.first, b = c.first.second;
+        const int64_t mn = std::min(map->count[a], map->count[b]);
+        if (c.second * (int64_t)cfg->contact_den < (int64_t)cfg->contact_num * mn) continue;
+        if (!(cosine_exact(map->E[a].data(), map->E[b].data(), D) >= cfg->tau_cos)) continue;
+        const int32_t ra = find_root(uf, a), rb = find_root(uf, b);
+        if (ra != rb) uf[std::max(ra, rb)] = std::min(ra, rb);
+    }
+    // (3) per component: summed counts, the highest-Q member's Q and embedding
+    std::vector<int32_t> comp(nid), winner(nid, -1);
+    for (int32_t i = 0; i < nid; i++) comp[i] = find_root(uf, i);
+    for (int32_t i = 0; i < nid; i++) {
+        if (map->parent[i] != i || map->count[i] <= 0) continue;  // live instances only
+        int32_t& w = winner[comp[i]];
+        if (w < 0 || map->Q[i] > map->Q[w]) w = i;  // ascending ids: ties keep the smaller
+    }
+    const std::vector<int64_t> count0 = map->count;
+    const std::vector<int32_t> obs0 = map->n_obs;
+    for (int32_t i = 0; i < nid; i++) {
+        if (map->parent[i] != i || count0[i] <= 0 || comp[i] == i) continue;
+        const int32_t c = comp[i];
+        map->count[c] += count0[i];
+        map->n_obs[c] += obs0[i];
+        map->count[i] = 0;
+        map->parent[i] = c;
+        r.merged++;
+    }
+    for (int32_t c = 0; c < nid; c++) {
+        const int32_t w = winner[c];
+        if (w >= 0 && w != c) {
+            map->Q[c] = map->Q[w];
+            map->E[c] = map->E[w];
+        }
+    }
+    for (int32_t i = 0; i < nid; i++) map->parent[i] = map->parent[map->parent[i]];  // flat again
+    // (4) drop instances below the voxel count
+    std::vector<char> drop(nid, 0);
+    for (int32_t i = 0; i < nid; i++) {
+        if (map->parent[i] == i && map->count[i] > 0 && map->count[i] < cfg->min_voxels) {
+            drop[i] = 1;
+            r.removed++;
+            map->count[i] = 0;
+            map->n_obs[i] = 0;
+            map->Q[i] = 0.0f;
+        }
+    }
+    for (auto& kv : map->vox) {
+        if (kv.second >= 0 && drop[map->parent[kv.second]]) {
+            kv.second = -1;
+            r.removed_voxels++;
+        }
+    }
+    map->final_ = true;
+    if (rep) *rep = r;
+    return ORACLE_OK;
+}
+
+void oracle_set_state(oracle_map* map, const uint64_t* keys, const int32_t* labels, int64_t n,
+                      const int32_t* parent, const int64_t* count, const float* Q, const float* E,
+                      const int32_t* n_obs, int32_t nid)
+{
+    const int D = map->cfg.embed_dim;
+    map->vox.clear();
+    for (int64_t i = 0; i < n; i++) map->vox[keys[i]] = labels[i];
+    map->parent.assign(parent, parent + nid);
+    map->count.assign(count, count + nid);
+    map->Q.assign(Q, Q + nid);
+    map->n_obs.assign(n_obs, n_obs + nid);
+    map->E.assign(nid, std::vector<float>(D));
+    for (int32_t i = 0; i < nid; i++) std::memcpy(map->E[i].data(), E + (size_t)i * D, sizeof(float) * D);
+    map->final_ = false;
 }
 
 // ---- FP64 twin of Eq. 1 and the pooling (error statements only) ---------------

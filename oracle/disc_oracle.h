@@ -85,6 +85,40 @@ int32_t oracle_num_ids(const oracle_map* map);
 void oracle_export_instances(const oracle_map* map, int32_t* parent, int64_t* count, float* Q,
                              float* E, int32_t* n_obs);
 
+/* End of the trajectory (Sec. III-B, last paragraph): merge the remaining
+ * orphaned candidates, then drop instances below a voxel count.  Reading:
+ *   contact(a, b) = number of voxels of a or b with a face neighbour (one of
+ *                   the 6 voxels sharing a face) in the other instance;
+ *   a and b merge when contact * contact_den >= contact_num * min(|a|, |b|)
+ *   and the exact cosine of their embeddings is >= tau_cos (counts and
+ *   embeddings as they stand when finalisation starts); merges are
+ *   transitive, the smallest id represents a component, whose Q and
+ *   embedding are those of its member with the highest Q (ties: smallest id)
+ *   and whose voxel and observation counts are the members' sums;
+ *   then every live instance with 0 < count < min_voxels is dropped: its
+ *   voxels carry no instance (id -1) and its count, observations and Q are 0.
+ * The map is final afterwards (integration returns ORACLE_ERR_INVALID_ARG). */
+typedef struct {
+    int32_t min_voxels;
+    int32_t contact_num, contact_den;
+    float tau_cos;
+} oracle_finalize_config;
+
+typedef struct {
+    int32_t contact_pairs;   /* instance pairs in contact */
+    int32_t merged;          /* instances merged into another */
+    int32_t removed;         /* instances dropped by the voxel count */
+    int64_t removed_voxels;  /* their voxels */
+} oracle_finalize_report;
+
+int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_finalize_report* rep);
+
+/* Replace the map's state (test construction of exact situations): voxels
+ * keys[n] with instance labels (>= 0), instance arrays over nid ids. */
+void oracle_set_state(oracle_map* map, const uint64_t* keys, const int32_t* labels, int64_t n,
+                      const int32_t* parent, const int64_t* count, const float* Q, const float* E,
+                      const int32_t* n_obs, int32_t nid);
+
 /* Stage functions (Eq. 1, mask coverage, pooling) for unit pins. */
 int oracle_token_stats(const float* F, int32_t P, int32_t D, const float* g, float eps,
                        float* fbar, float* n, float* Dp, float* cosg);
