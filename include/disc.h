@@ -314,6 +314,39 @@ disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int
                                     const float* global_embed, float eps, float* Dp, float* cosg,
                                     void* cuda_stream);
 
+/* End of the trajectory (Sec. III-B, last paragraph): merge the remaining
+ * orphaned candidates, then drop noisy instances below a voxel count.  The
+ * paper fixes no criteria; this call takes:
+ *   contact(a, b) = voxels of instance a or b with a face neighbour (one of
+ *                   the 6 voxels sharing a face) in the other instance;
+ *   a and b merge when contact * contact_den >= contact_num * min(|a|, |b|)
+ *   and the cosine of their stored embeddings (exact sums, as in the
+ *   association gate) >= tau_cos, on the state as it stands at the call;
+ *   merges are transitive; a component keeps its smallest id, the Q and
+ *   embedding of its member with the highest Q (ties: smallest id), and the
+ *   sums of its voxel and observation counts;
+ *   then live instances with 0 < voxel count < min_voxels are dropped: their
+ *   voxels report instance -1, their count, observations and Q become 0, and
+ *   queries skip them.
+ * The map is final afterwards: integration calls (and group calls naming it)
+ * return DISC_ERR_INVALID_ARG; exports, queries and checkpoints still work
+ * (a checkpoint of a final map reloads final).  Same result bit for bit as
+ * the plain CPU statement of these steps. */
+typedef struct {
+    int32_t min_voxels;
+    int32_t contact_num, contact_den;
+    float tau_cos;
+} disc_finalize_config;
+
+typedef struct {
+    int32_t contact_pairs;  /* instance pairs in contact */
+    int32_t merged;         /* instances merged into another */
+    int32_t removed;        /* instances dropped by the voxel count */
+    int64_t removed_voxels; /* their voxels */
+} disc_finalize_report;
+
+disc_status disc_map_finalize(disc_map* map, const disc_finalize_config* cfg, disc_finalize_report* report);
+
 /* Voxel key packing: three signed 18-bit voxel coordinates (x, y, z), each
  * biased by 2^17, in bits 36..53, 18..35 and 0..17. */
 uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz);

@@ -64,6 +64,14 @@ class ServerReport(ctypes.Structure):
                 ("p99_ms", c_f64)]
 
 
+class FinalizeConfig(ctypes.Structure):
+    _fields_ = [("min_voxels", c_i32), ("contact_num", c_i32), ("contact_den", c_i32), ("tau_cos", c_f32)]
+
+
+class FinalizeReport(ctypes.Structure):
+    _fields_ = [("contact_pairs", c_i32), ("merged", c_i32), ("removed", c_i32), ("removed_voxels", c_i64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
                 ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
@@ -127,6 +135,7 @@ def lib():
         L.disc_group_device_bytes.restype = c_i64
         L.disc_group_destroy.argtypes = [c_vp]
         L.disc_group_destroy.restype = None
+        L.disc_map_finalize.argtypes = [c_vp, P(FinalizeConfig), P(FinalizeReport)]
         L.disc_server_create.argtypes = [P(ServerConfig), P(c_vp)]
         L.disc_server_open_map.argtypes = [c_vp, P(Config), P(c_i32)]
         L.disc_server_close_map.argtypes = [c_vp, c_i32]
@@ -144,7 +153,8 @@ def lib():
                   "disc_map_export_instances", "disc_map_save", "disc_map_load", "disc_group_create",
                   "disc_group_integrate", "disc_group_set_phase_timing", "disc_group_phase_times",
                   "disc_server_create", "disc_server_open_map", "disc_server_close_map", "disc_server_submit_frame",
-                  "disc_server_submit_query", "disc_server_wait", "disc_server_stats", "disc_server_reset_stats"):
+                  "disc_server_submit_query", "disc_server_wait", "disc_server_stats", "disc_server_reset_stats",
+                  "disc_map_finalize"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -373,6 +383,18 @@ class DiscMap:
 
     def device_bytes(self) -> int:
         return int(lib().disc_map_device_bytes(self._h))
+
+    def finalize(self, min_voxels, contact_num=1, contact_den=5, tau_cos=None, check: bool = True):
+        """End-of-trajectory orphan merge and voxel-count filter; the report."""
+        c = FinalizeConfig(int(min_voxels), int(contact_num), int(contact_den),
+                           float(self.cfg["tau_cos"] if tau_cos is None else tau_cos))
+        r = FinalizeReport()
+        rc = lib().disc_map_finalize(self._h, ctypes.byref(c), ctypes.byref(r))
+        if check:
+            _check(rc, "disc_map_finalize")
+        out = {k: int(getattr(r, k)) for k, _ in FinalizeReport._fields_}
+        out["rc"] = rc
+        return out
 
     def save(self, path):
         _check(lib().disc_map_save(self._h, str(path).encode()), "disc_map_save")

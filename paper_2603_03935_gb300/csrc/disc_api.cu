@@ -134,6 +134,7 @@ struct disc_map {
     bool timing_wanted = false;
     unsigned char* qscratch = nullptr;  // query buffers, grown on demand and kept
     size_t qcap = 0;
+    bool finalized = false;  // after disc_map_finalize: no more frames
 };
 
 struct disc_group {
@@ -927,6 +928,7 @@ disc_status map_runner(disc_map* m)
 disc_status integrate(disc_map* m, const disc_frame* frames, int n, disc_frame_stats* stats, int* n_done)
 {
     if (n_done) *n_done = 0;
+    if (m->finalized) return DISC_ERR_INVALID_ARG;
     disc_status s = map_runner(m);
     if (s != DISC_OK) return s;
     std::vector<Work> w(1);
@@ -1209,6 +1211,7 @@ disc_status disc_group_integrate(disc_group* g, disc_map* const* maps, int32_t n
             return DISC_ERR_INVALID_ARG;
         for (int k = 0; k < i; k++)
             if (maps[k] == m) return DISC_ERR_INVALID_ARG;  // one entry per map
+        if (m->finalized) return DISC_ERR_INVALID_ARG;
         w[i].m = m;
         w[i].frames = frames[i];
         w[i].n = counts[i];
@@ -1358,6 +1361,7 @@ disc_status disc_query_points(disc_map* m, const float* xyz, int64_t n, int32_t*
 
 // checkpoint file: magic, config, counts, voxels (key, label), instance table
 static const char kMagic[8] = {'D', 'I', 'S', 'C', 'M', 'A', 'P', '1'};
+static const char kMagicFinal[8] = {'D', 'I', 'S', 'C', 'M', 'A', 'P', 'F'};  // a finalised map
 
 disc_status disc_map_save(disc_map* m, const char* path)
 {
@@ -1380,7 +1384,7 @@ disc_status disc_map_save(disc_map* m, const char* path)
     if (!fp) return DISC_ERR_INVALID_ARG;
     disc_map_config c = m->cfg;
     c.cuda_stream = nullptr;
-    bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(&c, sizeof(c), 1, fp) == 1 &&
+    bool ok = std::fwrite(m->finalized ? kMagicFinal : kMagic, 1, 8, fp) == 8 && std::fwrite(&c, sizeof(c), 1, fp) == 1 &&
               std::fwrite(&nv, sizeof(nv), 1, fp) == 1 && std::fwrite(&nid, sizeof(nid), 1, fp) == 1;
     if (ok && nv) ok = std::fwrite(keys.data(), 8, nv, fp) == (size_t)nv && std::fwrite(ids.data(), 4, nv, fp) == (size_t)nv;
     if (ok && nid)
@@ -1401,7 +1405,8 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     disc_map_config c;
     int64_t nv = 0;
     int32_t nid = 0;
-    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+    bool ok = std::fread(magic, 1, 8, fp) == 8 &&
+              (std::memcmp(magic, kMagic, 8) == 0 || std::memcmp(magic, kMagicFinal, 8) == 0) &&
               std::fread(&c, sizeof(c), 1, fp) == 1 && std::fread(&nv, sizeof(nv), 1, fp) == 1 &&
               std::fread(&nid, sizeof(nid), 1, fp) == 1 && nv >= 0 && nid >= 0 && c.embed_dim > 0 &&
               c.embed_dim <= 4096;
@@ -1475,8 +1480,74 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     }
     m->used_upper = (uint64_t)nv;
     m->next_id_upper = nid;
+    m->finalized = std::memcmp(magic, kMagicFinal, 8) == 0;
     *out = m;
     return DISC_OK;
+}
+
+disc_status disc_map_finalize(disc_map* m, const disc_finalize_config* cfg, disc_finalize_report* rep)
+{
+    if (!m || !cfg || cfg->contact_den <= 0 || cfg->contact_num < 0 || cfg->min_voxels < 0) return DISC_ERR_INVALID_ARG;
+    if (m->finalized) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    CK(cudaStreamSynchronize(m->stream));
+    const int nid = read_next_id(m, m->stream);
+    cudaStream_t st = m->stream;
+    uint64_t pcap = next_pow2(std::max<uint64_t>(4096, 16 * (uint64_t)nid));
+    int32_t ctr[FIN_NCTR] = {};
+    unsigned long long removed_voxels = 0;
+    for (int attempt = 0; attempt < 4; attempt++, pcap *= 4) {
+        DevAlloc a;
+        FinalizeScratch fs{};
+        fs.pkeys = a.get<unsigned long long>(pcap);
+        fs.pcnt = a.get<int32_t>(pcap);
+        fs.plist = a.get<int32_t>(pcap);
+        fs.pmask = pcap - 1;
+        fs.ea = a.get<int32_t>(pcap);
+        fs.eb = a.get<int32_t>(pcap);
+        fs.comp = a.get<int32_t>(std::max(nid, 1));
+        fs.win = a.get<unsigned long long>(std::max(nid, 1));
+        fs.drop = a.get<unsigned char>(std::max(nid, 1));
+        fs.ctr = a.get<int32_t>(FIN_NCTR);
+        fs.removed_voxels = a.get<unsigned long long>(1);
+        if (a.failed) {
+            a.free_all();
+            return DISC_ERR_OOM;
+        }
+        disc_status s = DISC_OK;
+        auto run = [&](int phase) {
+            if (s != DISC_OK) return;
+            launch_finalize(phase, m->vt, m->inst, nid, m->D, fs, cfg->min_voxels, cfg->contact_num,
+                            cfg->contact_den, cfg->tau_cos, st);
+            s = cuda_status(cudaMemcpyAsync(ctr, fs.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, st));
+            if (s == DISC_OK) s = cuda_status(cudaStreamSynchronize(st));
+            if (s == DISC_OK && ctr[FIN_ERR]) s = (disc_status)ctr[FIN_ERR];
+        };
+        s = cuda_status(cudaMemsetAsync(fs.pkeys, 0xFF, sizeof(unsigned long long) * pcap, st));
+        if (s == DISC_OK) s = cuda_status(cudaMemsetAsync(fs.pcnt, 0, sizeof(int32_t) * pcap, st));
+        if (s == DISC_OK) s = cuda_status(cudaMemsetAsync(fs.ctr, 0, sizeof(int32_t) * FIN_NCTR, st));
+        if (s == DISC_OK) s = cuda_status(cudaMemsetAsync(fs.removed_voxels, 0, sizeof(unsigned long long), st));
+        run(0);  // contacts: the map is untouched until phase 2
+        if (s == DISC_ERR_TABLE_FULL) {
+            a.free_all();
+            continue;  // more distinct contact pairs than slots: a larger pair table
+        }
+        run(1);
+        run(2);
+        if (s == DISC_OK)
+            s = cuda_status(cudaMemcpy(&removed_voxels, fs.removed_voxels, sizeof(removed_voxels), cudaMemcpyDeviceToHost));
+        a.free_all();
+        if (s != DISC_OK) return s;
+        m->finalized = true;
+        if (rep) {
+            rep->contact_pairs = ctr[FIN_PAIRS];
+            rep->merged = ctr[FIN_MERGED];
+            rep->removed = ctr[FIN_REMOVED];
+            rep->removed_voxels = (int64_t)removed_voxels;
+        }
+        return DISC_OK;
+    }
+    return DISC_ERR_TABLE_FULL;
 }
 
 uint64_t disc_pack_key(int32_t kx, int32_t ky, int32_t kz)

@@ -243,6 +243,22 @@ struct MapRefs {
     int* next_id;               // [1] next unused instance id
 };
 
+// End-of-trajectory finalisation scratch (k_final.cu)
+enum { FIN_PAIRS = 0, FIN_EDGES, FIN_MERGED, FIN_REMOVED, FIN_ERR, FIN_NCTR };
+struct FinalizeScratch {
+    unsigned long long* pkeys;  // (min id << 32 | max id) of instances in contact; EMPTY = ~0
+    int32_t* pcnt;              // contact voxels per pair
+    int32_t* plist;             // occupied pair slots
+    unsigned long long pmask;
+    int32_t* ea;                // accepted pairs
+    int32_t* eb;
+    int32_t* comp;              // [nid] union-find over ids
+    unsigned long long* win;    // [nid] winner key per component
+    unsigned char* drop;        // [nid] dropped by the voxel count
+    int32_t* ctr;               // [FIN_NCTR]
+    unsigned long long* removed_voxels;
+};
+
 // One step of the serial part over the maps of a batch: block row g runs the
 // j-th frame of map g.
 struct SerialStep {

@@ -35,7 +35,7 @@ __global__ void k_query_scores(const float* q, int nq, int D, Instances inst, in
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= nid || qi >= nq) return;
     float s = -INFINITY;
-    if (inst.parent[i] == i) {
+    if (inst.parent[i] == i && inst.n_obs[i] > 0) {  // live (a dropped instance has no observations)
         const float* a = q + (size_t)qi * D;
         const float* b = inst.E + (size_t)i * D;
         float dt = 0.0f, na = 0.0f, nb = 0.0f;
@@ -95,7 +95,11 @@ __global__ void k_query_points(const float* xyz, long long n, float voxel, Voxel
             unsigned long long h = mix64(key) & vt.mask;
             for (unsigned long long pr = 0; pr <= vt.mask; pr++) {
                 unsigned long long kk = vt.keys[h];
-                if (kk == key) { out = inst.parent[vt.labels[h]]; break; }
+                if (kk == key) {
+                    const int lab = vt.labels[h];
+                    out = lab >= 0 ? inst.parent[lab] : -1;  // -1: the voxel's instance was dropped
+                    break;
+                }
                 if (kk == EMPTY_KEY) break;
                 h = (h + 1) & vt.mask;
             }

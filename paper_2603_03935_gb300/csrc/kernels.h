@@ -64,6 +64,10 @@ cudaError_t set_feature_kernel_attrs(int max_dyn_smem);
 cudaError_t set_gemm_kernel_attrs();
 cudaError_t set_serial_kernel_attrs();
 
+// end-of-trajectory finalisation, phases 0..2 (k_final.cu)
+int launch_finalize(int phase, const VoxelTable& vt, const Instances& inst, int nid, int D, const FinalizeScratch& fs,
+                    int min_voxels, int num, int den, float tau, cudaStream_t st);
+
 // maintenance and queries
 void launch_rehash(const VoxelTable& from, const VoxelTable& to, int* err, cudaStream_t st);
 void launch_query_topk(const float* q, int nq, int D, const Instances& inst, int nid, float* scores, int k,
