@@ -12,6 +12,11 @@ are not available here):
   * ``room``:  10x8x3 m room, 80 random boxes/ellipsoids (0.2-1.5 m),
     a smooth closed path of 2000 frames at 1.2 m height, 640x480, fx = fy = 525,
     1 % multiplicative depth noise, 40 masks, tokens 24x24x768, voxel 2.5 cm.
+  * ``multistory``: 3 floors of 40x30 m (3 m each) split into 8 rooms per floor
+    by partition walls along a central corridor, 1000 random objects, a
+    serpentine path through every room of every floor (5000 frames at 1.2 m
+    above the floor), 640x480, <= 100 masks, tokens 24x24x768, voxel 5 cm,
+    valid depth up to 20 m.
 """
 from __future__ import annotations
 
@@ -50,7 +55,10 @@ class _Scene(ctypes.Structure):
                 ("depth_noise", ctypes.c_double),
                 ("patch_h", ctypes.c_int32), ("patch_w", ctypes.c_int32), ("dim", ctypes.c_int32),
                 ("token_noise", ctypes.c_double), ("max_masks", ctypes.c_int32),
-                ("max_id", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("max_id", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("grid_nx", ctypes.c_int32), ("grid_ny", ctypes.c_int32),
+                ("grid_x0", ctypes.c_double), ("grid_y0", ctypes.c_double), ("grid_cell", ctypes.c_double),
+                ("cell_start", ctypes.POINTER(ctypes.c_int32)), ("cell_items", ctypes.POINTER(ctypes.c_int32))]
 
 
 _lib = None
@@ -114,7 +122,7 @@ class Scene:
         ext = [self.room_hi[i] - self.room_lo[i] for i in range(3)]
         return int(np.ceil(ext[b0] / self.tile - 1e-9)) * int(np.ceil(ext[b1] / self.tile - 1e-9))
 
-    def _cscene(self):
+    def _cscene(self, grid: bool = True):
         prims = (_Prim * max(1, len(self.prims)))()
         for i, (kind, pid, c, h) in enumerate(self.prims):
             prims[i].kind = kind
@@ -139,10 +147,36 @@ class Scene:
         s.max_masks = self.max_masks
         s.max_id = self.max_id
         s.seed = self.seed
-        return s, prims
+        keep = [prims]
+        if grid and len(self.prims) > 200:
+            # a 2 m grid over the floor plan: each ray tests the primitives
+            # of the cells it crosses only
+            cs = 2.0
+            x0, y0 = self.room_lo[0], self.room_lo[1]
+            nx = max(1, int(np.ceil((self.room_hi[0] - x0) / cs)))
+            ny = max(1, int(np.ceil((self.room_hi[1] - y0) / cs)))
+            cells = [[] for _ in range(nx * ny)]
+            for i, (_k, _id, c, h) in enumerate(self.prims):
+                i0 = max(0, int(np.floor((c[0] - h[0] - x0) / cs)))
+                i1 = min(nx - 1, int(np.floor((c[0] + h[0] - x0) / cs)))
+                j0 = max(0, int(np.floor((c[1] - h[1] - y0) / cs)))
+                j1 = min(ny - 1, int(np.floor((c[1] + h[1] - y0) / cs)))
+                for j in range(j0, j1 + 1):
+                    for ii in range(i0, i1 + 1):
+                        cells[j * nx + ii].append(i)
+            start = np.zeros(nx * ny + 1, np.int32)
+            start[1:] = np.cumsum([len(c) for c in cells])
+            items = np.array([i for c in cells for i in c] or [0], np.int32)
+            s.grid_nx, s.grid_ny = nx, ny
+            s.grid_x0, s.grid_y0, s.grid_cell = x0, y0, cs
+            s.cell_start = start.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            s.cell_items = items.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            keep += [start, items]
+        return s, keep
 
-    def render(self, frames) -> "Frames":
-        """Render the given frame indices (any order, computed in parallel)."""
+    def render(self, frames, grid: bool = True) -> "Frames":
+        """Render the given frame indices (any order, computed in parallel);
+        grid=False tests every primitive for every ray (same frames)."""
         frames = np.asarray(list(frames), dtype=np.int64)
         n = len(frames)
         H, W, P, D, M = self.height, self.width, self.patch_h * self.patch_w, self.dim, self.max_masks
@@ -153,7 +187,7 @@ class Scene:
         num_masks = np.zeros((n,), np.int32)
         ids = np.zeros((n, H, W), np.int32)
         poses = np.ascontiguousarray(self.poses[frames].reshape(n, 16), dtype=np.float64)
-        s, keep = self._cscene()
+        s, keep = self._cscene(grid)
         rc = _load().synth_render(ctypes.byref(s), n, poses.ctypes.data, frames.ctypes.data,
                                   depth.ctypes.data, labels.ctypes.data, tokens.ctypes.data,
                                   mask_ids.ctypes.data, num_masks.ctypes.data, ids.ctypes.data)
@@ -228,6 +262,107 @@ def _room_path(s: np.ndarray):
     x = cx + 3.2 * np.cos(s) + 0.5 * np.cos(3 * s)
     y = cy + 2.4 * np.sin(s) + 0.4 * np.sin(2 * s)
     return x, y
+
+
+def _polyline(points, n):
+    """n samples at equal arc length along the polyline, with the direction
+    of travel at each."""
+    pts = np.asarray(points, np.float64)
+    seg = np.linalg.norm(np.diff(pts, axis=0), axis=1)
+    cum = np.concatenate([[0.0], np.cumsum(seg)])
+    s = np.linspace(0.0, cum[-1], n, endpoint=False)
+    out, dirs = [], []
+    for v in s:
+        k = min(int(np.searchsorted(cum, v, side="right")) - 1, len(seg) - 1)
+        f = (v - cum[k]) / seg[k]
+        out.append(pts[k] + f * (pts[k + 1] - pts[k]))
+        dirs.append((pts[k + 1] - pts[k]) / seg[k])
+    return np.array(out), np.array(dirs)
+
+
+def multistory_scene(seed: int = 3, num_frames: int = 5000, n_objects: int = 1000, width: int = 640,
+                     height: int = 480, patch: int = 24, dim: int = 768, max_masks: int = 100,
+                     voxel: float = 0.05) -> Scene:
+    """Three 40x30x3 m floors; partition walls at x = 10, 20, 30 leave a
+    corridor at 13 <= y <= 17, so each floor has 8 rooms of 10x13 m; the floor
+    slabs and walls are cut into panels with one id each; objects are kept
+    0.6 m from the camera path and clear of the walls."""
+    rng = np.random.default_rng(seed)
+    off = 0.0113  # every face off the 5 cm voxel grid
+    prims = []
+    oid = 1
+
+    def box(c, h, kind=0):
+        nonlocal oid
+        prims.append((kind, oid, tuple(float(x) + off for x in c), tuple(float(x) for x in h)))
+        oid += 1
+
+    # floor slabs between the storeys, 5 x 5 m panels
+    for z in (3.0, 6.0):
+        for x in range(0, 40, 5):
+            for y in range(0, 30, 5):
+                box((x + 2.5, y + 2.5, z), (2.5, 2.5, 0.05))
+    # partition walls, 0.1 m thick, in panels of about 3 m
+    walls = []
+    for f in range(3):
+        z0 = 3.0 * f
+        for x in (10.0, 20.0, 30.0):
+            for ya, yb in ((0.0, 13.0), (17.0, 30.0)):
+                for k in range(4):
+                    y0 = ya + (yb - ya) * k / 4.0
+                    y1 = ya + (yb - ya) * (k + 1) / 4.0
+                    c, h = (x, 0.5 * (y0 + y1), z0 + 1.475), (0.05, 0.5 * (y1 - y0), 1.425)
+                    box(c, h)
+                    walls.append((c, h))
+    # the path: for every 10 m column of rooms, into the lower room, back to
+    # the corridor, into the upper room, back; one floor after the other
+    legs = []
+    for f in range(3):
+        pts = []
+        for x0 in (0.0, 10.0, 20.0, 30.0):
+            pts += [(x0 + 2.5, 15.0), (x0 + 2.5, 2.5), (x0 + 7.5, 2.5), (x0 + 7.5, 15.0),
+                    (x0 + 7.5, 27.5), (x0 + 2.5, 27.5), (x0 + 2.5, 15.5), (x0 + 9.0, 15.5)]
+        legs.append(pts)
+    per = [num_frames // 3 + (1 if f < num_frames % 3 else 0) for f in range(3)]
+    path_xy = np.concatenate([_polyline(p, 4 * len(p) * 20)[0] for p in legs])
+    # objects resting on the floors, inside the rooms, away from path and walls
+    tries = 0
+    placed = 0
+    while placed < n_objects and tries < 200000:
+        tries += 1
+        f = placed % 3
+        size = rng.uniform(0.2, 1.2, 3)
+        half = size / 2.0
+        c = np.array([rng.uniform(0.3 + half[0], 39.7 - half[0]), rng.uniform(0.3 + half[1], 29.7 - half[1]),
+                      3.0 * f + 0.05 + half[2]])
+        if 12.6 - half[1] < c[1] < 17.4 + half[1]:
+            continue  # corridor
+        if any(abs(c[0] - wc[0]) < half[0] + wh[0] + 0.15 and abs(c[1] - wc[1]) < half[1] + wh[1] + 0.15
+               for wc, wh in walls[:24]):  # one floor's walls; the plan repeats on every floor
+            continue
+        if np.min(np.hypot(path_xy[:, 0] - c[0], path_xy[:, 1] - c[1])) < float(np.hypot(half[0], half[1])) + 0.6:
+            continue
+        box(c, half, kind=int(rng.uniform() < 0.35))
+        placed += 1
+    poses = []
+    for f in range(3):
+        xy, dirs = _polyline(legs[f], per[f])
+        for (x, y), (dx, dy) in zip(xy, dirs):
+            eye = (x, y, 3.0 * f + 1.2)
+            poses.append(look_at(eye, (x + 3.0 * dx, y + 3.0 * dy, 3.0 * f + 0.6)))
+    faces = []
+    tile = 1.0
+    ext = (40.0, 30.0, 9.0)
+    for fc in range(6):
+        a = fc // 2
+        b0, b1 = (1 if a == 0 else 0), (1 if a == 2 else 2)
+        faces.append(oid)
+        oid += int(np.ceil(ext[b0] / tile)) * int(np.ceil(ext[b1] / tile))
+    f = 525.0 * width / 640.0
+    lo = (-0.0071, -0.0093, -0.0051)
+    hi = (40.0 + lo[0], 30.0 + lo[1], 9.0 + lo[2])
+    return Scene("multistory", lo, hi, tuple(faces), prims, np.stack(poses), width, height, f, f, width / 2.0,
+                 height / 2.0, 0.01, patch, patch, dim, 0.1, max_masks, voxel, 0.1, 20.0, seed, tile)
 
 
 def room_scene(seed: int = 1, num_frames: int = 2000, n_objects: int = 80,

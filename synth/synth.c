@@ -39,6 +39,13 @@ typedef struct {
     int32_t max_masks;
     int32_t max_id;                  /* ids are in [0, max_id] */
     uint64_t seed;
+    /* optional 2D uniform grid over (x, y) for scenes with many primitives:
+     * cell (i, j) lists the primitives whose (x, y) extent overlaps it,
+     * cell_items[cell_start[c] .. cell_start[c + 1]) with c = j * grid_nx + i */
+    int32_t grid_nx, grid_ny;        /* 0: test every primitive */
+    double grid_x0, grid_y0, grid_cell;
+    const int32_t* cell_start;
+    const int32_t* cell_items;
 } synth_scene;
 
 /* ---- counter-based generator (splitmix64 finaliser as a hash) ---------- */
@@ -160,11 +167,40 @@ static void render_ids(const synth_scene* s, const double* T, uint64_t frame,
             int face;
             double tbest = room_exit(s, o, d, &face);
             int32_t id = face >= 0 ? face_tile_id(s, o, d, tbest, face) : 0;
-            for (int i = 0; i < s->n_prims; i++) {
-                double t;
-                const synth_prim* p = &s->prims[i];
-                int hit = p->kind == 0 ? hit_box(p, o, d, &t) : hit_ellipsoid(p, o, d, &t);
-                if (hit && t < tbest) { tbest = t; id = p->id; }
+            if (s->grid_nx > 0) {
+                /* walk the (x, y) cells the ray crosses, nearest first; stop
+                 * once the nearest hit so far lies within the current cell */
+                const double cs = s->grid_cell;
+                int ix = (int)floor((o[0] - s->grid_x0) / cs), iy = (int)floor((o[1] - s->grid_y0) / cs);
+                if (ix < 0) ix = 0;
+                if (ix >= s->grid_nx) ix = s->grid_nx - 1;
+                if (iy < 0) iy = 0;
+                if (iy >= s->grid_ny) iy = s->grid_ny - 1;
+                const int sx = d[0] > 0.0 ? 1 : -1, sy = d[1] > 0.0 ? 1 : -1;
+                double tmx = d[0] != 0.0 ? (s->grid_x0 + (ix + (d[0] > 0.0)) * cs - o[0]) / d[0] : INFINITY;
+                double tmy = d[1] != 0.0 ? (s->grid_y0 + (iy + (d[1] > 0.0)) * cs - o[1]) / d[1] : INFINITY;
+                const double tdx = d[0] != 0.0 ? cs / fabs(d[0]) : INFINITY;
+                const double tdy = d[1] != 0.0 ? cs / fabs(d[1]) : INFINITY;
+                while (1) {
+                    const int c = iy * s->grid_nx + ix;
+                    for (int k = s->cell_start[c]; k < s->cell_start[c + 1]; k++) {
+                        double t;
+                        const synth_prim* p = &s->prims[s->cell_items[k]];
+                        int hit = p->kind == 0 ? hit_box(p, o, d, &t) : hit_ellipsoid(p, o, d, &t);
+                        if (hit && (t < tbest || (t == tbest && p->id < id))) { tbest = t; id = p->id; }
+                    }
+                    const double texit = tmx < tmy ? tmx : tmy;
+                    if (tbest <= texit || !isfinite(texit)) break;
+                    if (tmx < tmy) { ix += sx; tmx += tdx; } else { iy += sy; tmy += tdy; }
+                    if (ix < 0 || ix >= s->grid_nx || iy < 0 || iy >= s->grid_ny) break;
+                }
+            } else {
+                for (int i = 0; i < s->n_prims; i++) {
+                    double t;
+                    const synth_prim* p = &s->prims[i];
+                    int hit = p->kind == 0 ? hit_box(p, o, d, &t) : hit_ellipsoid(p, o, d, &t);
+                    if (hit && t < tbest) { tbest = t; id = p->id; }
+                }
             }
             size_t idx = (size_t)v * W + u;
             if (!isfinite(tbest) || id == 0) {

@@ -376,3 +376,29 @@ def test_bf16_precision_checkpoint_and_mixed_group(torch_dev, tmp_path):
         assert np.array_equal(kx, ky) and np.array_equal(ix, iy), ctx
         ex, ey = x.instances(), y.instances()
         assert np.array_equal(ex["E"].view(np.uint32), ey["E"].view(np.uint32)), ctx
+
+
+def test_multistory_bf16_parity(torch_dev):
+    # the multi-story building: up to 100 masks, 5 cm voxels, depth to 20 m,
+    # bf16 tokens at BF16 precision, a voxel table of 2^27 slots; consecutive
+    # frames on each of the three floors
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, device_frame
+    sc = synth.multistory_scene()
+    idx = [0, 1, 2, 3, 1700, 1701, 1702, 3400, 3401, 3402]
+    fr = sc.render(idx)
+    assert int(fr.num_masks.max()) == 100
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 27, instance_capacity=1 << 14, precision=1)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    for j in range(len(idx)):
+        t16 = torch.from_numpy(fr.tokens[j]).to(dev).to(torch.bfloat16).contiguous()
+        t32 = t16.float().cpu().numpy()
+        d = torch.from_numpy(fr.depth[j]).to(dev)
+        l = torch.from_numpy(fr.labels[j].view(np.int16)).to(dev)
+        st = gmap.integrate(device_frame(d, l, t16, fr.poses[j], intr, fr.num_masks[j]))
+        o = omap.integrate(fr.depth[j], fr.labels[j], t32, fr.poses[j], intr, fr.num_masks[j])
+        common.compare_frame(st, gmap.last_frame(), o, ctx=f"multistory frame {idx[j]}", efast_tol=2e-2)
+    common.compare_maps(gmap, omap, ctx="multistory")
+    assert gmap.cfg["voxel_capacity"] >= 1 << 27
