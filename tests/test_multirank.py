@@ -1,0 +1,61 @@
+"""The benchmark's multi-rank path on the CPU: two gloo ranks (replicas, no
+data-path collective) meet only for the max-over-ranks timing; the job rate
+counts every rank's frames over the slowest rank's time; the oracle arm runs
+on rank 0 alone."""
+import contextlib
+import io
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.rank_env()
+    local_ms = 100.0 + 50.0 * rank
+    mx = bench.max_over_ranks(local_ms, w, torch.device("cpu"))
+    rate = bench.whole_job_rate(320, w, mx)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((r, w, lr, mx, rate, bench.replica_seed(r)))
+
+
+def test_two_gloo_ranks_max_time_and_job_rate():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[:3] for o in out] == [(0, 2, 0), (1, 2, 1)]
+    assert all(o[3] == 150.0 for o in out)                    # the slowest rank's time
+    assert all(abs(o[4] - 640 / 0.150) < 1e-9 for o in out)  # 2 x 320 frames over it
+    assert out[0][5] != out[1][5]                             # each replica its own scene
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    import bench
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
+    args = bench.parse()
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(args, rank=1)
+    assert buf.getvalue() == ""
