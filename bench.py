@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--frames-per-step", type=int, default=32)
     ap.add_argument("--latency-frames", type=int, default=64)
     ap.add_argument("--timing-batches", type=int, default=4)
+    ap.add_argument("--batch-frames", type=int, default=0,
+                    help="frames per internal batch of a call (0: the map's default)")
+    ap.add_argument("--serial-sms", type=int, default=0,
+                    help="SMs of the serial part of overlapped batches (0: default, < 0: no overlap)")
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-frames", type=int, default=4, help="frames of each map per batch")
     ap.add_argument("--batched-steps", type=int, default=3)
@@ -470,6 +474,9 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     cfg = room_cfg(scene)
+    if args.batch_frames > 0:
+        cfg["batch_frames"] = args.batch_frames
+    cfg["serial_sms"] = args.serial_sms
     cfg["cuda_stream"] = stream.cuda_stream
     cfg["device"] = local
     depth = torch.from_numpy(fr.depth).to(dev)

@@ -75,6 +75,10 @@ typedef struct {
     void* cuda_stream;       /* cudaStream_t, or NULL: the map creates one */
     int32_t device;          /* CUDA device ordinal */
     int32_t batch_frames;    /* frames whose stateless phases share one launch (1..256) */
+    int32_t serial_sms;      /* > 0: calls of several batches overlap the next batch's stateless steps
+                                with this batch's serial steps, which run on their own set of this many
+                                SMs (a green context; without one, a high-priority stream); <= 0: no
+                                overlap (the default: the overlap measured slower on GB300) */
 } disc_map_config;
 
 typedef struct {
@@ -170,6 +174,7 @@ typedef struct {
     int32_t max_masks;       /* largest num_masks of any frame (<= 256) */
     void* cuda_stream;       /* cudaStream_t, or NULL: the group creates one */
     int32_t device;
+    int32_t serial_sms;      /* as in disc_map_config */
 } disc_group_config;
 
 /* Defaults: 16 maps x 4 frames, 640x480, 24x24x768, 40 masks. */

@@ -29,7 +29,7 @@ class Config(ctypes.Structure):
                 ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
                 ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
                 ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
-                ("device", c_i32), ("batch_frames", c_i32)]
+                ("device", c_i32), ("batch_frames", c_i32), ("serial_sms", c_i32)]
 
 
 class Frame(ctypes.Structure):
@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
 class GroupConfig(ctypes.Structure):
     _fields_ = [("max_maps", c_i32), ("frames_per_map", c_i32), ("embed_dim", c_i32), ("patch_h", c_i32),
                 ("patch_w", c_i32), ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
-                ("cuda_stream", c_vp), ("device", c_i32)]
+                ("cuda_stream", c_vp), ("device", c_i32), ("serial_sms", c_i32)]
 
 
 class ServerConfig(ctypes.Structure):

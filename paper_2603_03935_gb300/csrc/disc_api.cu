@@ -11,6 +11,8 @@
 #include <map>
 #include <vector>
 
+#include <cuda.h>
+
 #include "disc_common.cuh"
 #include "kernels.h"
 
@@ -76,16 +78,26 @@ struct BatchGraph {
 // batches that span many maps.
 struct Runner {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // the caller's stream (everything when not pipelined)
+    cudaStream_t stream2 = nullptr;  // stateless part of pipelined batches, lowest priority
+    cudaStream_t stream3 = nullptr;  // serial part of pipelined batches, highest priority
+    cudaEvent_t ev_join = nullptr;   // call start on the caller's stream, call end on stream3
+    CUgreenCtx green[2] = {};        // SM partitions of stream3 / stream2 (when the driver offers them)
+    int serial_sms = -1;             // SMs of the serial partition; < 0: no pipelining
     DevAlloc mem;
     int D = 0, P = 0, Ph = 0, Pw = 0, Kpad = 0, MM = 1, Npad_max = 16;
     int Hmax = 0, Wmax = 0, Mmax = 0;
     int Gmax = 1, Jmax = 1, S = 1;  // maps per batch, frames per map, slots = Gmax * Jmax
     size_t px_cap = 0;
-    BatchScratch bs{};
+    // Two sets of slot scratch and parameter blocks: batch b uses set b % 2,
+    // so the stateless part of batch b + 1 runs while the serial part of
+    // batch b still reads its own set.
+    BatchScratch bs[2] = {};
     // parameter block: FrameParams[S] | MapRefs[Gmax] | slot_of[Gmax * Jmax] | prev_hist[Gmax]
-    unsigned char* d_param = nullptr;
+    unsigned char* d_param[2] = {};
     size_t off_refs = 0, off_slot = 0, off_prev = 0, param_bytes = 0;
+    cudaEvent_t ev_state[2] = {}, ev_serial[2] = {};  // stateless / serial part of the set's last batch done
+    int cur = 0;                                        // set of the next batch
     FrameCounters* d_hist = nullptr;  // [hist_cap] per-frame counters of one call
     int hist_cap = 0;
     float* d_depth = nullptr;         // staging of host inputs, one slot per frame of a batch
@@ -107,13 +119,13 @@ struct Runner {
     double phase_ms[PH_COUNT] = {};
     int64_t phase_launches[PH_COUNT] = {};
     int64_t phase_calls[PH_COUNT] = {};
-    int last_slot = 0, last_M = 0;  // the most recent frame
+    int last_set = 0, last_slot = 0, last_M = 0;  // the most recent frame
     bool have_frame = false;
 
-    const FrameParams* fps() const { return (const FrameParams*)d_param; }
-    const MapRefs* refs() const { return (const MapRefs*)(d_param + off_refs); }
-    const int* slot_of() const { return (const int*)(d_param + off_slot); }
-    const int* prev_hist() const { return (const int*)(d_param + off_prev); }
+    const FrameParams* fps(int k) const { return (const FrameParams*)d_param[k]; }
+    const MapRefs* refs(int k) const { return (const MapRefs*)(d_param[k] + off_refs); }
+    const int* slot_of(int k) const { return (const int*)(d_param[k] + off_slot); }
+    const int* prev_hist(int k) const { return (const int*)(d_param[k] + off_prev); }
 };
 
 struct disc_map {
@@ -193,10 +205,84 @@ disc_status set_kernel_attrs()
 // ---- runner ----------------------------------------------------------------------
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Driver entry points of the green-context API, looked up through the
+// runtime (the library does not link the driver directly).
+struct GreenApi {
+    decltype(&::cuDeviceGet) deviceGet = nullptr;
+    decltype(&::cuDeviceGetDevResource) getResource = nullptr;
+    decltype(&::cuDevSmResourceSplitByCount) split = nullptr;
+    decltype(&::cuDevResourceGenerateDesc) desc = nullptr;
+    decltype(&::cuGreenCtxCreate) create = nullptr;
+    decltype(&::cuGreenCtxStreamCreate) stream = nullptr;
+    decltype(&::cuGreenCtxDestroy) destroy = nullptr;
+    decltype(&::cuStreamDestroy) streamDestroy = nullptr;
+    bool ok = false;
+};
+
+const GreenApi& green_api()
+{
+    static GreenApi g = [] {
+        GreenApi a;
+        auto get = [](const char* name, void** fn) {
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPoint(name, fn, cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess) {
+                cudaGetLastError();
+                *fn = nullptr;
+            }
+            return *fn != nullptr;
+        };
+        a.ok = get("cuDeviceGet", (void**)&a.deviceGet) && get("cuDeviceGetDevResource", (void**)&a.getResource) &&
+               get("cuDevSmResourceSplitByCount", (void**)&a.split) &&
+               get("cuDevResourceGenerateDesc", (void**)&a.desc) && get("cuGreenCtxCreate", (void**)&a.create) &&
+               get("cuGreenCtxStreamCreate", (void**)&a.stream) && get("cuGreenCtxDestroy", (void**)&a.destroy) &&
+               get("cuStreamDestroy", (void**)&a.streamDestroy);
+        return a;
+    }();
+    return g;
+}
+
+// Green contexts over disjoint SM sets: r.serial_sms SMs for stream3, the rest
+// for stream2.  false when the driver does not offer them (nothing is kept).
+bool make_green_streams(Runner& r)
+{
+    const GreenApi& g = green_api();
+    if (!g.ok) return false;
+    CUdevice dev;
+    CUdevResource all, part[1], rest;
+    unsigned n = 1;
+    CUdevResourceDesc d0, d1;
+    if (g.deviceGet(&dev, r.device) != CUDA_SUCCESS ||
+        g.getResource(dev, &all, CU_DEV_RESOURCE_TYPE_SM) != CUDA_SUCCESS ||
+        all.sm.smCount < (unsigned)r.serial_sms + 16u ||
+        g.split(part, &n, &all, &rest, 0, (unsigned)r.serial_sms) != CUDA_SUCCESS || n != 1 ||
+        g.desc(&d0, &part[0], 1) != CUDA_SUCCESS || g.desc(&d1, &rest, 1) != CUDA_SUCCESS)
+        return false;
+    if (g.create(&r.green[0], d0, dev, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS) return false;
+    if (g.create(&r.green[1], d1, dev, CU_GREEN_CTX_DEFAULT_STREAM) != CUDA_SUCCESS) {
+        g.destroy(r.green[0]);
+        r.green[0] = nullptr;
+        return false;
+    }
+    CUstream s3 = nullptr, s2 = nullptr;
+    if (g.stream(&s3, r.green[0], CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS ||
+        g.stream(&s2, r.green[1], CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) {
+        if (s3) g.streamDestroy(s3);
+        g.destroy(r.green[0]);
+        g.destroy(r.green[1]);
+        r.green[0] = r.green[1] = nullptr;
+        return false;
+    }
+    r.stream3 = (cudaStream_t)s3;
+    r.stream2 = (cudaStream_t)s2;
+    return true;
+}
+
 disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int Ph, int Pw, int Hmax, int Wmax,
-                        int Mmax, int Gmax, int Jmax)
+                        int Mmax, int Gmax, int Jmax, int serial_sms)
 {
     r.device = device;
+    r.serial_sms = serial_sms == 0 ? -1 : serial_sms;  // overlap only on request: measured slower here
     r.stream = stream;
     r.D = D;
     r.Ph = Ph;
@@ -220,63 +306,103 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     r.off_slot = r.off_refs + align256(sizeof(MapRefs) * Gmax);
     r.off_prev = r.off_slot + align256(sizeof(int) * Gmax * Jmax);
     r.param_bytes = r.off_prev + align256(sizeof(int) * Gmax);
-    r.d_param = a.get<unsigned char>(r.param_bytes);
-    BatchScratch& bs = r.bs;
-    bs.sD = D;
-    bs.sP = P;
-    bs.sMM = MM;
-    bs.sMMP = (long long)MM * P;
-    bs.sW = (long long)r.Npad_max * r.Kpad;
-    bs.sMMD = (long long)MM * D;
-    bs.sS = 5LL * MM;
-    bs.scap = (long long)scap;
-    Scratch& sc = bs.base;
-    sc.sumF = a.get<long long>((size_t)B * D);
-    sc.fbar = a.get<float>((size_t)B * D);
-    sc.gvec = a.get<float>((size_t)B * D);
-    sc.gg = a.get<long long>(B);
-    sc.nsum = a.get<long long>(B);
-    sc.dotg = a.get<long long>((size_t)B * P);
-    sc.ffp = a.get<long long>((size_t)B * P);
-    sc.nrm = a.get<float>((size_t)B * P);
-    sc.Dp = a.get<float>((size_t)B * P);
-    sc.cosg = a.get<float>((size_t)B * P);
-    sc.fnorm = a.get<float>((size_t)B * P);
-    sc.cov = a.get<int32_t>((size_t)B * MM * P);
-    sc.npix = a.get<int32_t>((size_t)B * MM);
-    sc.W = a.get<float>((size_t)B * bs.sW);
-    sc.S = a.get<float>((size_t)B * 5 * MM);
-    sc.Bm = a.get<float>((size_t)B * MM);
-    sc.Ecan = a.get<float>((size_t)B * MM * D);
-    sc.Efast = a.get<float>((size_t)B * MM * D);
-    sc.ang = a.get<long long>((size_t)B * MM);
-    sc.nvox = a.get<int32_t>((size_t)B * MM);
-    sc.segrep = a.get<int32_t>((size_t)B * MM);
-    sc.sslot = a.get<SegSlot>((size_t)B * scap);
-    sc.sent = a.get<unsigned long long>((size_t)B * scap);
-    sc.slist = a.get<int32_t>((size_t)B * scap);
-    sc.elab = a.get<int32_t>((size_t)B * scap);
-    sc.smask = scap - 1;
-    sc.ctr = a.get<FrameCounters>(B);
+    for (int k = 0; k < 2; k++) {
+        r.d_param[k] = a.get<unsigned char>(r.param_bytes);
+        BatchScratch& bs = r.bs[k];
+        bs.sD = D;
+        bs.sP = P;
+        bs.sMM = MM;
+        bs.sMMP = (long long)MM * P;
+        bs.sW = (long long)r.Npad_max * r.Kpad;
+        bs.sMMD = (long long)MM * D;
+        bs.sS = 5LL * MM;
+        bs.scap = (long long)scap;
+        Scratch& sc = bs.base;
+        sc.sumF = a.get<long long>((size_t)B * D);
+        sc.fbar = a.get<float>((size_t)B * D);
+        sc.gvec = a.get<float>((size_t)B * D);
+        sc.gg = a.get<long long>(B);
+        sc.nsum = a.get<long long>(B);
+        sc.dotg = a.get<long long>((size_t)B * P);
+        sc.ffp = a.get<long long>((size_t)B * P);
+        sc.nrm = a.get<float>((size_t)B * P);
+        sc.Dp = a.get<float>((size_t)B * P);
+        sc.cosg = a.get<float>((size_t)B * P);
+        sc.fnorm = a.get<float>((size_t)B * P);
+        sc.cov = a.get<int32_t>((size_t)B * MM * P);
+        sc.npix = a.get<int32_t>((size_t)B * MM);
+        sc.W = a.get<float>((size_t)B * bs.sW);
+        sc.S = a.get<float>((size_t)B * 5 * MM);
+        sc.Bm = a.get<float>((size_t)B * MM);
+        sc.Ecan = a.get<float>((size_t)B * MM * D);
+        sc.Efast = a.get<float>((size_t)B * MM * D);
+        sc.ang = a.get<long long>((size_t)B * MM);
+        sc.nvox = a.get<int32_t>((size_t)B * MM);
+        sc.segrep = a.get<int32_t>((size_t)B * MM);
+        sc.sslot = a.get<SegSlot>((size_t)B * scap);
+        sc.sent = a.get<unsigned long long>((size_t)B * scap);
+        sc.slist = a.get<int32_t>((size_t)B * scap);
+        sc.elab = a.get<int32_t>((size_t)B * scap);
+        sc.smask = scap - 1;
+        sc.ctr = a.get<FrameCounters>(B);
+    }
     r.d_depth = a.get<float>((size_t)B * npx);
     r.d_labels = a.get<uint16_t>((size_t)B * npx);
     r.d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
     r.d_gembed = a.get<float>((size_t)B * D);
     if (a.failed) return DISC_ERR_OOM;
+    // Pipelined batches put the serial part (a latency-bound chain of small
+    // launches) on its own partition of serial_sms SMs and the stateless part
+    // of the next batch on the rest, so the chain never waits for SMs that
+    // long stateless blocks hold.  Without green contexts: two streams of
+    // highest / lowest priority.
+    if (r.serial_sms < 0 || !make_green_streams(r)) {
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CK(cudaStreamCreateWithPriority(&r.stream2, cudaStreamNonBlocking, prio_lo));
+        CK(cudaStreamCreateWithPriority(&r.stream3, cudaStreamNonBlocking, prio_hi));
+    }
+    CK(cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming));
+    for (int k = 0; k < 2; k++) {
+        CK(cudaEventCreateWithFlags(&r.ev_state[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.ev_serial[k], cudaEventDisableTiming));
+    }
     cudaStream_t s = r.stream;
-    CK(cudaMemsetAsync(r.d_param, 0, r.param_bytes, s));
-    CK(cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s));
-    CK(cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s));
-    CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
-    CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
-    CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
-    CK(cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s));
+    for (int k = 0; k < 2; k++) {
+        const BatchScratch& bs = r.bs[k];
+        const Scratch& sc = bs.base;
+        CK(cudaMemsetAsync(r.d_param[k], 0, r.param_bytes, s));
+        CK(cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s));
+        CK(cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s));
+        CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
+        CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
+        CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
+        CK(cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s));
+    }
     return cuda_status(cudaStreamSynchronize(s));
 }
 
 void runner_release(Runner& r)
 {
     cudaStreamSynchronize(r.stream);
+    for (cudaStream_t* sp : {&r.stream2, &r.stream3}) {
+        if (*sp) {
+            cudaStreamSynchronize(*sp);
+            cudaStreamDestroy(*sp);
+            *sp = nullptr;
+        }
+    }
+    if (r.ev_join) cudaEventDestroy(r.ev_join);
+    r.ev_join = nullptr;
+    for (int i = 0; i < 2; i++) {
+        if (r.green[i]) green_api().destroy(r.green[i]);
+        r.green[i] = nullptr;
+    }
+    for (int k = 0; k < 2; k++) {
+        if (r.ev_state[k]) cudaEventDestroy(r.ev_state[k]);
+        if (r.ev_serial[k]) cudaEventDestroy(r.ev_serial[k]);
+        r.ev_state[k] = r.ev_serial[k] = nullptr;
+    }
     for (cudaEvent_t e : r.ev_pool) cudaEventDestroy(e);
     r.ev_pool.clear();
     for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -317,6 +443,9 @@ disc_status alloc_voxel_table(disc_map* m, uint64_t cap, VoxelTable* out, cudaSt
         return DISC_ERR_OOM;
     }
     CK(cudaMemsetAsync(t.keys, 0xFF, sizeof(unsigned long long) * cap, st));
+    // an empty slot's label reads -1: a lookup racing an insert sees a key
+    // with no label yet as absent
+    CK(cudaMemsetAsync(t.labels, 0xFF, sizeof(int32_t) * cap, st));
     t.mask = cap - 1;
     t.used = m->vt.used;
     *out = t;
@@ -474,15 +603,15 @@ cudaEvent_t take_event(Runner& r)
 // Enqueue one phase; with timing on, bracket it with events on the runner's
 // stream (event-record nodes when the stream is being captured).
 template <class F>
-void run_phase(Runner& r, int ph, F&& launch)
+void run_phase(Runner& r, int ph, cudaStream_t st, F&& launch)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (r.timing && (a = take_event(r))) cudaEventRecordWithFlags(a, r.stream, cudaEventRecordExternal);
+    if (r.timing && (a = take_event(r))) cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
     const int n = launch();
     r.launches += n;
     r.phase_launches[ph] += n;
     if (a && (b = take_event(r))) {
-        cudaEventRecordWithFlags(b, r.stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
         if (n > 0) r.marks.push_back({ph, a, b});
     }
 }
@@ -515,66 +644,81 @@ void reset_timing(Runner& r, bool enable)
 }
 
 // ---- one batch -------------------------------------------------------------------
-// Every kernel of one batch of S frame slots over G maps (J frames per map at
-// most), in order.  Grids follow the runner's maxima (smaller frames return
-// early in their blocks) and per-frame values and map state are read on the
-// device, so the sequence depends on (S, G, J, token dtypes) only and is
-// replayed as a CUDA graph.
+// A batch of S frame slots over G maps (J frames per map at most) runs in two
+// parts.  Grids follow the runner's maxima (smaller frames return early in
+// their blocks) and per-frame values and map state are read on the device,
+// so each part depends on its shape only and is replayed as a CUDA graph.
+//   stateless: every kernel over all slots (reads no map state that frames
+//              change except the voxel lookup of k_entries, see below)
+//   serial:    overlap, score, union, apply for frame j of every map, j = 0..J-1
+// k_entries may run while the serial part of the previous batch inserts
+// voxels: a voxel's label never changes once written, an empty slot's label
+// reads -1, so the lookup returns either the final label or "absent", and an
+// absent voxel is looked up again by k_overlap after the earlier frames.
+
 // combos: bit (2 * token_bf16 + precision_bf16) set for every kind of frame in the batch
-int enqueue_batch_kernels(Runner& r, int S, int G, int J, int combos)
+int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
 {
     const bool any_bf16 = (combos & 12) != 0, any_f32 = (combos & 3) != 0;
     bool any[2][2];
     for (int t = 0; t < 2; t++)
         for (int q = 0; q < 2; q++) any[t][q] = (combos >> (2 * t + q)) & 1;
     const int D = r.D, P = r.P, Mmax = r.Mmax;
-    cudaStream_t st = r.stream;
-    const BatchScratch& bs = r.bs;
-    const FrameParams* dfp = r.fps();
-    const MapRefs* refs = r.refs();
+    const BatchScratch& bs = r.bs[k];
+    const FrameParams* dfp = r.fps(k);
+    const MapRefs* refs = r.refs(k);
     const int64_t before = r.launches;
-    run_phase(r, PH_CLEAR, [&] { return launch_slot_clear(bs, S, D, r.MM, refs, G, st); });
-    run_phase(r, PH_TOKENS, [&] { return launch_token_stats(dfp, bs, S, P, D, any_bf16, any_f32, st); });
-    run_phase(r, PH_COVERAGE, [&] { return launch_coverage(dfp, bs, S, r.Ph, r.Pw, Mmax, st); });
-    run_phase(r, PH_WEIGHTS, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
-    run_phase(r, PH_POOL_EXACT, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(r, PH_POOL_GEMM, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, st); });
+    run_phase(r, PH_CLEAR, st, [&] { return launch_slot_clear(bs, S, D, r.MM, st); });
+    run_phase(r, PH_TOKENS, st, [&] { return launch_token_stats(dfp, bs, S, P, D, any_bf16, any_f32, st); });
+    run_phase(r, PH_COVERAGE, st, [&] { return launch_coverage(dfp, bs, S, r.Ph, r.Pw, Mmax, st); });
+    run_phase(r, PH_WEIGHTS, st, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
+    run_phase(r, PH_POOL_EXACT, st, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
+    run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, st); });
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
             const int nb = std::min(GEOMETRY_CHUNK, S - f0);
-            run_phase(r, PH_BACKPROJECT, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
-            run_phase(r, PH_ENTRIES, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
+            run_phase(r, PH_BACKPROJECT, st, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
+            run_phase(r, PH_ENTRIES, st, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
         }
-        run_phase(r, PH_ENTRIES, [&] { return launch_quality(dfp, bs, S, st); });
-    }
-    SerialStep step;
-    step.refs = refs;
-    step.slot_of = r.slot_of();
-    step.prev_hist = r.prev_hist();
-    step.hist = r.d_hist;
-    step.J = J;
-    for (int j = 0; j < J; j++) {
-        step.j = j;
-        for (int ph = 0; ph < 4; ph++)
-            run_phase(r, PH_OVERLAP + ph, [&] { return launch_serial_step(dfp, bs, step, G, ph, st); });
+        run_phase(r, PH_ENTRIES, st, [&] { return launch_quality(dfp, bs, S, st); });
     }
     return (int)(r.launches - before);
 }
 
-long long graph_key(int S, int G, int J, int combos)
+int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 {
-    return ((((long long)S << 20) | ((long long)G << 10) | J) << 4) | combos;
+    const BatchScratch& bs = r.bs[k];
+    const FrameParams* dfp = r.fps(k);
+    const int64_t before = r.launches;
+    SerialStep step;
+    step.refs = r.refs(k);
+    step.slot_of = r.slot_of(k);
+    step.prev_hist = r.prev_hist(k);
+    step.hist = r.d_hist;
+    step.J = J;
+    run_phase(r, PH_OVERLAP, st, [&] { return launch_serial_begin(step.refs, G, st); });
+    for (int j = 0; j < J; j++) {
+        step.j = j;
+        for (int ph = 0; ph < 4; ph++)
+            run_phase(r, PH_OVERLAP + ph, st, [&] { return launch_serial_step(dfp, bs, step, G, ph, st); });
+    }
+    return (int)(r.launches - before);
 }
 
-// The batch's kernel sequence captured once per shape and replayed.  A shape
+long long graph_key(int part, int k, int S, int G, int J, int combos)
+{
+    return (((((((long long)S << 11) | G) << 9) | J) << 4 | combos) << 2) | (part << 1) | k;
+}
+
+// A part's kernel sequence captured once per shape and replayed.  A shape
 // seen for the first time runs as plain launches (*out = NULL): under a mixed
 // load (groups, serving) most shapes are one-off and instantiating a graph
 // costs more than launching the kernels.  At most kMaxGraphs are kept.
-constexpr int kMaxGraphs = 64;
+constexpr int kMaxGraphs = 96;
 
-disc_status batch_graph(Runner& r, int S, int G, int J, int combos, BatchGraph** out)
+template <class F>
+disc_status part_graph(Runner& r, long long key, cudaStream_t st, F&& enqueue, BatchGraph** out)
 {
-    const long long key = graph_key(S, G, J, combos);
     *out = nullptr;
     auto it = r.graphs.find(key);
     if (it != r.graphs.end()) {
@@ -587,14 +731,14 @@ disc_status batch_graph(Runner& r, int S, int G, int J, int combos, BatchGraph**
         r.graphs.erase(r.graphs.begin());
     }
     cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(r.stream, cudaStreamCaptureModeThreadLocal));
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int64_t before = r.launches;
     int64_t pl0[PH_COUNT];
     for (int i = 0; i < PH_COUNT; i++) pl0[i] = r.phase_launches[i];
-    const int n = enqueue_batch_kernels(r, S, G, J, combos);
+    const int n = enqueue();
     r.launches = before;  // counted when the graph is launched
     for (int i = 0; i < PH_COUNT; i++) r.phase_launches[i] = pl0[i];
-    cudaError_t e = cudaStreamEndCapture(r.stream, &graph);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
@@ -612,10 +756,27 @@ disc_status batch_graph(Runner& r, int S, int G, int J, int combos, BatchGraph**
     return DISC_OK;
 }
 
-// Timing run of one batch: the sequence with its phase events is captured and
-// launched as one graph, so the device never waits on the host inside a
-// timed interval.  false: capture is not possible here (plain launches).
-bool launch_timed_graph(Runner& r, int S, int G, int J, int combos)
+// Run one part: its graph when there is one, else plain launches.
+template <class F>
+disc_status run_part(Runner& r, long long key, cudaStream_t st, F&& enqueue)
+{
+    BatchGraph* g = nullptr;
+    if (!r.graphs_off && part_graph(r, key, st, enqueue, &g) != DISC_OK) {
+        r.graphs_off = true;  // this stream or driver cannot capture the sequence
+        g = nullptr;
+    }
+    if (g) {
+        r.launches += g->kernels;
+        return cuda_status(cudaGraphLaunch(g->exec, st));
+    }
+    enqueue();
+    return DISC_OK;
+}
+
+// Timing run of one batch: both parts with their phase events, captured and
+// launched as one graph on the runner's stream, so the device never waits on
+// the host inside a timed interval.  false: capture is not possible here.
+bool launch_timed_graph(Runner& r, int k, int S, int G, int J, int combos)
 {
     const size_t marks0 = r.marks.size(), ev0 = r.ev_used;
     const int64_t l0 = r.launches;
@@ -632,7 +793,8 @@ bool launch_timed_graph(Runner& r, int S, int G, int J, int combos)
         undo();
         return false;
     }
-    enqueue_batch_kernels(r, S, G, J, combos);
+    enqueue_stateless(r, k, S, combos, r.stream);
+    enqueue_serial(r, k, G, J, r.stream);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if (cudaStreamEndCapture(r.stream, &graph) != cudaSuccess || !graph ||
@@ -666,7 +828,8 @@ disc_status check_frame(const disc_map* m, const Runner& r, const disc_frame* f)
 
 // Frame parameters of frame f of map m in slot `slot` (map position g); host
 // inputs are staged into the slot's buffers.
-disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int slot, int g, FrameParams* out)
+disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int slot, int g, FrameParams* out,
+                         cudaStream_t st)
 {
     const int P = r.P, D = r.D;
     FrameParams fp{};
@@ -729,16 +892,16 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
         float* dd = r.d_depth + (size_t)slot * r.px_cap;
         uint16_t* dl = r.d_labels + (size_t)slot * r.px_cap;
         unsigned char* dt = r.d_tokens + (size_t)slot * P * D * 4;
-        CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, r.stream));
-        CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, r.stream));
-        CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, r.stream));
+        CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, st));
         fp.depth = dd;
         fp.labels = dl;
         fp.tokens = dt;
         fp.gembed = nullptr;
         if (f->global_embed) {
             float* dg = r.d_gembed + (size_t)slot * D;
-            CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, r.stream));
+            CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, st));
             fp.gembed = dg;
         }
     }
@@ -789,6 +952,18 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     }
     disc_status s = ensure_hist(r, std::max(total, 1));
     if (s != DISC_OK) return s;
+    // pipelined (calls of several batches): the runner's two streams start
+    // after the caller's earlier work and the caller's stream waits for their
+    // end; a single batch runs on the caller's stream
+    const bool pipe = !r.timing && nbatch > 1 && r.serial_sms > 0;
+    cudaStream_t sr = pipe ? r.stream3 : r.stream;  // serial part
+    cudaStream_t ss = pipe ? r.stream2 : r.stream;  // stateless part
+    if (pipe) {
+        s = cuda_status(cudaEventRecord(r.ev_join, r.stream));
+        if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream2, r.ev_join, 0));
+        if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream3, r.ev_join, 0));
+        if (s != DISC_OK) return s;
+    }
     std::vector<unsigned char> blk(r.param_bytes);
     int hoff = 0;
     for (int b = 0; b < nbatch && s == DISC_OK; b++) {
@@ -816,9 +991,16 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 masks += f.num_masks;
                 combos |= 1 << (2 * (f.token_dtype == DISC_TOKENS_BF16) + (wk.m->cfg.precision == DISC_BF16));
             }
-            s = ensure_voxel_room(wk.m, px, r.stream);
-            if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, r.stream);
+            s = ensure_voxel_room(wk.m, px, sr);
+            if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, sr);
         }
+        if (s != DISC_OK) break;
+        // set k: its previous batch's serial part must be done before the
+        // stateless part of this batch overwrites the set (pipelined batches:
+        // stateless on stream2, serial on the runner's stream)
+        const int k = r.cur;
+        r.cur ^= 1;
+        if (pipe) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_serial[k], 0));
         if (s != DISC_OK) break;
         std::fill(blk.begin(), blk.end(), 0);
         FrameParams* hfp = (FrameParams*)blk.data();
@@ -833,7 +1015,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && s == DISC_OK; j++) {
-                s = frame_params(r, wk.m, wk.frames + lo + j, slot, gi, hfp + slot);
+                s = frame_params(r, wk.m, wk.frames + lo + j, slot, gi, hfp + slot, ss);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
@@ -841,24 +1023,25 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         }
         if (s != DISC_OK) break;
         // pageable source: the call returns once the block is staged
-        s = cuda_status(cudaMemcpyAsync(r.d_param, blk.data(), r.param_bytes, cudaMemcpyHostToDevice, r.stream));
+        s = cuda_status(cudaMemcpyAsync(r.d_param[k], blk.data(), r.param_bytes, cudaMemcpyHostToDevice, ss));
         if (s != DISC_OK) break;
-        BatchGraph* g = nullptr;
-        if (!r.timing && !r.graphs_off && batch_graph(r, S, G, J, combos, &g) != DISC_OK) {
-            r.graphs_off = true;  // this stream or driver cannot capture the sequence
-            g = nullptr;
-        }
-        // g == NULL: plain launches (first sighting of a shape, timing, no capture)
-        if (g) {
-            s = cuda_status(cudaGraphLaunch(g->exec, r.stream));
-            r.launches += g->kernels;
-        } else if (!(r.timing && !r.graphs_off && launch_timed_graph(r, S, G, J, combos))) {
-            enqueue_batch_kernels(r, S, G, J, combos);
+        if (r.timing && !r.graphs_off && launch_timed_graph(r, k, S, G, J, combos)) {
+            // both parts with their phase events, one graph on the runner's stream
+        } else {
+            s = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
+                         [&] { return enqueue_stateless(r, k, S, combos, ss); });
+            if (s == DISC_OK && pipe) {
+                s = cuda_status(cudaEventRecord(r.ev_state[k], ss));
+                if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(sr, r.ev_state[k], 0));
+            }
+            if (s == DISC_OK)
+                s = run_part(r, graph_key(1, k, 0, G, J, 0), sr, [&] { return enqueue_serial(r, k, G, J, sr); });
         }
         // the batch's counters, in slot order, to the call's history
         if (s == DISC_OK)
-            s = cuda_status(cudaMemcpyAsync(r.d_hist + hoff, r.bs.base.ctr, sizeof(FrameCounters) * S,
-                                            cudaMemcpyDeviceToDevice, r.stream));
+            s = cuda_status(cudaMemcpyAsync(r.d_hist + hoff, r.bs[k].base.ctr, sizeof(FrameCounters) * S,
+                                            cudaMemcpyDeviceToDevice, sr));
+        if (s == DISC_OK && pipe) s = cuda_status(cudaEventRecord(r.ev_serial[k], sr));
         if (s == DISC_OK) s = cuda_status(cudaGetLastError());
         for (int gi = 0; gi < G; gi++) {
             Work& wk = w[gl[gi]];
@@ -869,11 +1052,17 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 wk.m->next_id_upper += f.num_masks;
             }
         }
+        r.last_set = k;
         r.last_slot = S - 1;
         const Work& wl = w[gl[G - 1]];
         r.last_M = wl.frames[lo + std::min(r.Jmax, wl.valid - lo) - 1].num_masks;
         r.have_frame = true;
         hoff += S;
+    }
+    if (pipe) {
+        // the caller's stream continues after the call's work
+        cudaEventRecord(r.ev_join, r.stream3);
+        cudaStreamWaitEvent(r.stream, r.ev_join, 0);
     }
     std::vector<FrameCounters> c(std::max(hoff, 1));
     if (hoff > 0) {
@@ -882,6 +1071,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (s == DISC_OK) s = s2;
     }
     disc_status s3 = cuda_status(cudaStreamSynchronize(r.stream));
+    if (s == DISC_OK) s = s3;
+    s3 = cuda_status(cudaStreamSynchronize(r.stream2));
     if (s == DISC_OK) s = s3;
     collect_timing(r);
     disc_status first = s;
@@ -914,7 +1105,8 @@ disc_status map_runner(disc_map* m)
     if (m->run) return DISC_OK;
     Runner* r = new Runner();
     disc_status s = runner_init(*r, m->cfg.device, m->stream, m->D, m->cfg.patch_h, m->cfg.patch_w,
-                                m->cfg.max_height, m->cfg.max_width, m->cfg.max_masks, 1, m->cfg.batch_frames);
+                                m->cfg.max_height, m->cfg.max_width, m->cfg.max_masks, 1, m->cfg.batch_frames,
+                                m->cfg.serial_sms);
     if (s != DISC_OK) {
         runner_release(*r);
         delete r;
@@ -1099,7 +1291,7 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
     r->num_masks = M;
     r->n_seg = 0;
     if (!have) return DISC_OK;
-    const Scratch sc = run->bs.frame(run->last_slot);
+    const Scratch sc = run->bs[run->last_set].frame(run->last_slot);
     FrameCounters c{};
     CK(cudaMemcpy(&c, sc.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     if (r->fbar) CK(cudaMemcpy(r->fbar, sc.fbar, sizeof(float) * D, cudaMemcpyDeviceToHost));
@@ -1183,7 +1375,7 @@ disc_status disc_group_create(const disc_group_config* cfg, disc_group** out)
         g->own_stream = true;
     }
     disc_status s = runner_init(g->run, c.device, st, c.embed_dim, c.patch_h, c.patch_w, c.max_height,
-                                c.max_width, c.max_masks, c.max_maps, c.frames_per_map);
+                                c.max_width, c.max_masks, c.max_maps, c.frames_per_map, c.serial_sms);
     if (s != DISC_OK) {
         runner_release(g->run);
         if (g->own_stream) cudaStreamDestroy(st);

@@ -35,15 +35,10 @@ __global__ void k_slot_clear(BatchScratch bs, int D, int MM)
     }
 }
 
-// counters and scalar sums of every slot (after k_slot_clear has read them),
-// and the serial part's edge and copy counters of every map
-__global__ void k_slot_reset(BatchScratch bs, int B, const MapRefs* refs, int G)
+// counters and scalar sums of every slot (after k_slot_clear has read them)
+__global__ void k_slot_reset(BatchScratch bs, int B)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < G) {
-        *refs[b].ss.edge_n = 0;
-        *refs[b].ss.copy_n = 0;
-    }
     if (b >= B) return;
     const Scratch sc = bs.frame(b);
     *sc.gg = 0;
@@ -364,10 +359,10 @@ __global__ void k_quality(const FrameParams* fps, BatchScratch bs)
 }
 
 // ---- host launchers ------------------------------------------------------------------
-int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, const MapRefs* refs, int G, cudaStream_t st)
+int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st)
 {
     k_slot_clear<<<dim3(64, B), 256, 0, st>>>(bs, D, MM);
-    k_slot_reset<<<(std::max(B, G) + 127) / 128, 128, 0, st>>>(bs, B, refs, G);
+    k_slot_reset<<<(B + 127) / 128, 128, 0, st>>>(bs, B);
     return 2;
 }
 

@@ -675,7 +675,22 @@ __global__ void k_apply(const FrameParams* fps, BatchScratch bs, SerialStep st)
     phase_apply(fps[slot], bs.frame(slot), ss, vt, inst, R.next_id, !blocked);
 }
 
+__global__ void k_serial_begin(const MapRefs* refs, int G)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) {
+        *refs[g].ss.edge_n = 0;
+        *refs[g].ss.copy_n = 0;
+    }
+}
+
 // ---- host launcher ----------------------------------------------------------------
+int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st)
+{
+    k_serial_begin<<<(G + 127) / 128, 128, 0, st>>>(refs, G);
+    return 1;
+}
+
 // Blocks per map: the whole GPU for a single map, fewer per map as the maps
 // of a batch multiply (they run side by side).
 static int per_map(int full, int G, int least)

@@ -34,7 +34,7 @@ enum Phase {
 };
 
 // batched
-int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, const MapRefs* refs, int G, cudaStream_t st);
+int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st);
 int launch_token_stats(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, bool any_bf16,
                        bool any_f32, cudaStream_t st);
 int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int Ph, int Pw, int Mmax, cudaStream_t st);
@@ -53,6 +53,8 @@ int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaSt
 // frames per back-projection/entries launch: their per-frame hashes stay in L2
 constexpr int GEOMETRY_CHUNK = 4;
 
+// start of a batch's serial part: every map's edge and copy counters to zero
+int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st);
 // serial part, step st.j over the G maps of a batch: phase 0 overlap,
 // 1 score, 2 union, 3 apply
 int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int phase,

@@ -402,3 +402,30 @@ def test_multistory_bf16_parity(torch_dev):
         common.compare_frame(st, gmap.last_frame(), o, ctx=f"multistory frame {idx[j]}", efast_tol=2e-2)
     common.compare_maps(gmap, omap, ctx="multistory")
     assert gmap.cfg["voxel_capacity"] >= 1 << 27
+
+
+def test_overlapped_batches_equal_sequential(torch_dev):
+    # serial_sms > 0: the stateless steps of the next batch overlap the serial
+    # steps of this one (two streams, SM partitions); results must not change
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.room_scene()
+    fr = sc.render(range(40))
+    frames = [_dframe(torch, dev, fr, i) for i in range(40)]
+    kw = dict(voxel_capacity=1 << 22, instance_capacity=1 << 12, batch_frames=8)
+    a = DiscMap(**common.disc_cfg(sc, **kw))
+    b = DiscMap(**common.disc_cfg(sc, serial_sms=48, **kw))
+    for lo in (0, 24):
+        sa, da, ra = a.integrate_frames(frames[lo:lo + 16] if lo == 0 else frames[lo:])
+        sb, db, rb = b.integrate_frames(frames[lo:lo + 16] if lo == 0 else frames[lo:])
+        assert ra == rb == 0 and da == db
+        for x, y in zip(sa, sb):
+            for k in ("unique_seg_voxels", "new_voxels", "new_instances", "merges", "overlap_pairs"):
+                assert x[k] == y[k]
+    ka, ia = a.voxels()
+    kb, ib = b.voxels()
+    assert np.array_equal(ka, kb) and np.array_equal(ia, ib)
+    ea, eb = a.instances(), b.instances()
+    for k in ("parent", "count", "n_obs"):
+        assert np.array_equal(ea[k], eb[k])
+    assert np.array_equal(ea["E"].view(np.uint32), eb["E"].view(np.uint32))
