@@ -32,7 +32,8 @@ class Config(ctypes.Structure):
                 ("eps", ctypes.c_float), ("tau_cos", ctypes.c_float), ("lambda_size", ctypes.c_float),
                 ("ov_num", ctypes.c_int32), ("ov_den", ctypes.c_int32),
                 ("embed_dim", ctypes.c_int32), ("patch_h", ctypes.c_int32), ("patch_w", ctypes.c_int32),
-                ("min_mask_pixels", ctypes.c_int32)]
+                ("min_mask_pixels", ctypes.c_int32), ("dbscan_eps", ctypes.c_float),
+                ("dbscan_min_pts", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -52,7 +53,8 @@ class Report(ctypes.Structure):
                 ("valid_pixels", ctypes.c_int32), ("dropped_pixels", ctypes.c_int32),
                 ("new_voxels", ctypes.c_int32), ("active_instances", ctypes.c_int32),
                 ("new_instances", ctypes.c_int32), ("merges", ctypes.c_int32),
-                ("live_segments", ctypes.c_int32), ("overlap_pairs", ctypes.c_int32)]
+                ("live_segments", ctypes.c_int32), ("overlap_pairs", ctypes.c_int32),
+                ("denoised_pixels", ctypes.c_int32)]
 
 
 _lib = None
@@ -84,6 +86,7 @@ def lib():
         L.oracle_cosine.restype = f32
         L.oracle_cosine.argtypes = [vp, vp, i32]
         L.oracle_pool_f64.argtypes = [vp, i32, i32, vp, vp, i32, ctypes.c_double, vp, vp]
+        L.oracle_dbscan_noise.argtypes = [vp, vp, i64, f32, i32, vp]
         L.oracle_finalize.restype = ctypes.c_int
         L.oracle_finalize.argtypes = [vp, ctypes.POINTER(FinalizeConfig), ctypes.POINTER(FinalizeReport)]
         L.oracle_set_state.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, i32]
@@ -97,7 +100,8 @@ def _p(a):
 
 def default_config(D: int, Ph: int, Pw: int, voxel: float, **kw) -> dict:
     c = dict(voxel_size=voxel, z_min=0.1, z_max=10.0, eps=1e-6, tau_cos=0.75, lambda_size=3.3,
-             ov_num=1, ov_den=5, embed_dim=D, patch_h=Ph, patch_w=Pw, min_mask_pixels=1)
+             ov_num=1, ov_den=5, embed_dim=D, patch_h=Ph, patch_w=Pw, min_mask_pixels=1,
+             dbscan_eps=0.0, dbscan_min_pts=1)
     c.update(kw)
     return c
 
@@ -201,7 +205,7 @@ class OracleMap:
             out["seg_keys"] = out["seg_keys"][:n]
             out["seg_m"] = out["seg_m"][:n]
             for k in ("valid_pixels", "dropped_pixels", "new_voxels", "active_instances", "new_instances",
-                      "merges", "live_segments", "overlap_pairs"):
+                      "merges", "live_segments", "overlap_pairs", "denoised_pixels"):
                 out[k] = int(getattr(rep, k))
             out["n_seg"] = n
         return out
@@ -285,3 +289,14 @@ def frame_args(frames, i):
     sc = frames.scene
     return (frames.depth[i], frames.labels[i], frames.tokens[i], frames.poses[i],
             (sc.fx, sc.fy, sc.cx, sc.cy), int(frames.num_masks[i]))
+
+
+def dbscan_noise(points, seg, eps, min_pts):
+    """Noise flags of the per-segment DBSCAN filter (Sec. III-A)."""
+    pts = np.ascontiguousarray(points, np.float32).reshape(-1, 3)
+    sg = np.ascontiguousarray(seg, np.int32)
+    out = np.zeros(len(pts), np.uint8)
+    if len(pts):
+        lib().oracle_dbscan_noise(pts.ctypes.data, sg.ctypes.data, len(pts), float(eps), int(min_pts),
+                                  out.ctypes.data)
+    return out.astype(bool)

@@ -13,8 +13,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <array>
 #include <functional>
 #include <map>
+#include <tuple>
 #include <set>
 #include <unordered_map>
 #include <vector>
@@ -193,6 +195,52 @@ void oracle_unpack_key(uint64_t key, int32_t* kx, int32_t* ky, int32_t* kz)
 
 float oracle_cosine(const float* a, const float* b, int32_t D) { return cosine_exact(a, b, D); }
 
+// ---- Sec. III-A: DBSCAN noise per segment ----------------------------------------
+// Neighbours are looked for in the 27 grid cells around a point; the cells are
+// 1.001 eps wide, so every point within eps lies in one of them (the grid only
+// narrows the search, the decision is the exact squared-distance test).
+void oracle_dbscan_noise(const float* pts, const int32_t* seg, int64_t n, float eps, int32_t min_pts,
+                         uint8_t* noise)
+{
+    const float eps2 = eps * eps;
+    const float inv_c = 1.0f / (eps * 1.001f);
+    std::map<std::tuple<int32_t, int32_t, int32_t, int32_t>, std::vector<int64_t>> cells;
+    std::vector<std::array<int32_t, 3>> cell_of(n);
+    for (int64_t i = 0; i < n; i++) {
+        for (int a = 0; a < 3; a++) cell_of[i][a] = (int32_t)std::floor(pts[3 * i + a] * inv_c);
+        cells[{seg[i], cell_of[i][0], cell_of[i][1], cell_of[i][2]}].push_back(i);
+    }
+    auto within = [&](int64_t i, int64_t j) {
+        const float dx = pts[3 * i] - pts[3 * j], dy = pts[3 * i + 1] - pts[3 * j + 1], dz = pts[3 * i + 2] - pts[3 * j + 2];
+        return (dx * dx + dy * dy) + dz * dz <= eps2;
+    };
+    auto for_neighbours = [&](int64_t i, const std::function<bool(int64_t)>& f) {
+        for (int dx = -1; dx <= 1; dx++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dz = -1; dz <= 1; dz++) {
+                    auto it = cells.find({seg[i], cell_of[i][0] + dx, cell_of[i][1] + dy, cell_of[i][2] + dz});
+                    if (it == cells.end()) continue;
+                    for (int64_t j : it->second)
+                        if (within(i, j) && !f(j)) return;
+                }
+    };
+    std::vector<char> core(n, 0);
+    for (int64_t i = 0; i < n; i++) {
+        int64_t cnt = 0;
+        for_neighbours(i, [&](int64_t) { return ++cnt < min_pts; });
+        core[i] = cnt >= min_pts;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        bool keep = core[i];
+        if (!keep)
+            for_neighbours(i, [&](int64_t j) {
+                keep = core[j] != 0;
+                return !keep;
+            });
+        noise[i] = keep ? 0 : 1;
+    }
+}
+
 // ---- one frame ----------------------------------------------------------------
 int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_report* rep)
 {
@@ -259,11 +307,45 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         S_size[m] = std::min((cfg.lambda_size * (float)npix[m]) / (float)(H * Wd), 1.0f);
     }
 
+    // (a5') Sec. III-A: each segment's points (pixels of an active mask with
+    // valid depth and an in-range voxel) filtered by DBSCAN; noise pixels
+    // count as invalid depth from here on.
+    std::vector<uint8_t> noise((size_t)H * Wd, 0);
+    int denoised = 0;
+    if (cfg.dbscan_eps > 0.0f) {
+        std::vector<float> pts;
+        std::vector<int32_t> sg;
+        std::vector<size_t> at;
+        for (int v = 0; v < H; v++)
+            for (int u = 0; u < Wd; u++) {
+                const size_t i = (size_t)v * Wd + u;
+                const int lab = fr->labels[i];
+                if (lab < 1 || lab > M || !mask_ok[lab - 1]) continue;
+                const float z = fr->depth[i];
+                if (!(z >= cfg.z_min && z <= cfg.z_max)) continue;
+                float p0[3];
+                world_point(T, fr->fx, fr->fy, fr->cx, fr->cy, u, v, z, p0);
+                uint64_t key;
+                if (!key_of(p0[0], p0[1], p0[2], s, &key)) continue;
+                pts.insert(pts.end(), p0, p0 + 3);
+                sg.push_back(lab);
+                at.push_back(i);
+            }
+        std::vector<uint8_t> nz(at.size());
+        if (!at.empty()) oracle_dbscan_noise(pts.data(), sg.data(), (int64_t)at.size(), cfg.dbscan_eps,
+                                             cfg.dbscan_min_pts, nz.data());
+        for (size_t k = 0; k < at.size(); k++)
+            if (nz[k]) {
+                noise[at[k]] = 1;
+                denoised++;
+            }
+    }
+
     // (a5) back-projection, keys and pixel normals.
     auto valid_px = [&](int u, int v, int lab) -> bool {
         if (u < 0 || v < 0 || u >= Wd || v >= H) return false;
         size_t i = (size_t)v * Wd + u;
-        if (fr->labels[i] != lab) return false;
+        if (fr->labels[i] != lab || noise[i]) return false;
         float z = fr->depth[i];
         return z >= cfg.z_min && z <= cfg.z_max;
     };
@@ -517,6 +599,7 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         rep->merges = merges;
         rep->live_segments = live;
         rep->overlap_pairs = pairs;
+        rep->denoised_pixels = denoised;
     }
     return ORACLE_OK;
 }

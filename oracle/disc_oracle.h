@@ -34,6 +34,8 @@ typedef struct {
     int32_t embed_dim;     /* D */
     int32_t patch_h, patch_w;
     int32_t min_mask_pixels;
+    float dbscan_eps;        /* > 0: per-segment DBSCAN denoise before voxelisation (radius, metres) */
+    int32_t dbscan_min_pts;  /* core point: at least this many points of its segment within eps */
 } oracle_config;
 
 typedef struct {
@@ -66,6 +68,7 @@ typedef struct {
     int64_t n_seg;      /* out: number of unique (segment, voxel) pairs */
     int32_t valid_pixels, dropped_pixels, new_voxels, active_instances;
     int32_t new_instances, merges, live_segments, overlap_pairs;
+    int32_t denoised_pixels;   /* pixels DBSCAN marked as noise */
 } oracle_report;
 
 enum { ORACLE_OK = 0, ORACLE_ERR_INVALID_ARG = -1, ORACLE_ERR_RANGE = -7 };
@@ -118,6 +121,16 @@ int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_f
 void oracle_set_state(oracle_map* map, const uint64_t* keys, const int32_t* labels, int64_t n,
                       const int32_t* parent, const int64_t* count, const float* Q, const float* E,
                       const int32_t* n_obs, int32_t nid);
+
+/* DBSCAN noise of Sec. III-A (the step between back-projection and
+ * voxelisation), per segment.  Reading: a point is core when at least
+ * min_pts points of its segment (itself included) lie within eps; a point is
+ * kept when it is core or within eps of a core point of its segment; the
+ * others are noise (noise[i] = 1).  Distances are compared squared in fp32:
+ * ((dx*dx + dy*dy) + dz*dz) <= eps*eps, with dx = x_i - x_j, no FMA.
+ * Requires eps > 0; pts [n][3], seg [n]. */
+void oracle_dbscan_noise(const float* pts, const int32_t* seg, int64_t n, float eps, int32_t min_pts,
+                         uint8_t* noise);
 
 /* Stage functions (Eq. 1, mask coverage, pooling) for unit pins. */
 int oracle_token_stats(const float* F, int32_t P, int32_t D, const float* g, float eps,
