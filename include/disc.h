@@ -75,6 +75,11 @@ typedef struct {
     void* cuda_stream;       /* cudaStream_t, or NULL: the map creates one */
     int32_t device;          /* CUDA device ordinal */
     int32_t batch_frames;    /* frames whose stateless phases share one launch (1..256) */
+    float dbscan_eps;        /* > 0: per-segment DBSCAN noise filter before voxelisation (Sec. III-A):
+                                a point is core with >= dbscan_min_pts points of its segment within
+                                this radius (metres, >= voxel_size), kept when core or within the
+                                radius of a core point; noise pixels count as invalid depth */
+    int32_t dbscan_min_pts;  /* >= 1 when dbscan_eps > 0 */
     int32_t serial_sms;      /* > 0: calls of several batches overlap the next batch's stateless steps
                                 with this batch's serial steps, which run on their own set of this many
                                 SMs (a green context; without one, a high-priority stream); <= 0: no
@@ -107,6 +112,7 @@ typedef struct {
     int32_t borderline_rescored;/* fast cosines re-scored exactly near tau_cos */
     int32_t max_probe;          /* longest hash probe of the frame */
     int32_t status;             /* disc_status of the frame */
+    int32_t denoised_pixels;    /* pixels the DBSCAN filter removed */
 } disc_frame_stats;
 
 /* Intermediates of the most recent frame, copied to caller host buffers (any

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdisc.so")
 SOURCES = ["k_features.cu", "k_gemm.cu", "k_geometry.cu", "k_serial.cu", "k_maint.cu", "disc_api.cu",
-           "disc_static.cu", "disc_server.cu", "k_final.cu"]
+           "disc_static.cu", "disc_server.cu", "k_final.cu", "k_dbscan.cu"]
 HEADERS = ["disc_common.cuh", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no fused multiply-add anywhere, so every fp32 expression is

@@ -29,7 +29,8 @@ class Config(ctypes.Structure):
                 ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
                 ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
                 ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
-                ("device", c_i32), ("batch_frames", c_i32), ("serial_sms", c_i32)]
+                ("device", c_i32), ("batch_frames", c_i32), ("dbscan_eps", c_f32), ("dbscan_min_pts", c_i32),
+                ("serial_sms", c_i32)]
 
 
 class Frame(ctypes.Structure):
@@ -42,7 +43,8 @@ class Frame(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, c_i32) for k in ("valid_pixels", "dropped_pixels", "unique_seg_voxels", "new_voxels",
                                      "active_instances", "overlap_pairs", "new_instances", "merges",
-                                     "live_segments", "borderline_rescored", "max_probe", "status")]
+                                     "live_segments", "borderline_rescored", "max_probe", "status",
+                                     "denoised_pixels")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -372,7 +374,7 @@ class DiscMap:
         _check(lib().disc_map_set_phase_timing(self._h, 1 if enable else 0), "disc_map_set_phase_timing")
 
     def phase_times(self) -> dict:
-        n = 12
+        n = 13
         ms = np.zeros(n, np.float64)
         la = np.zeros(n, np.int64)
         ca = np.zeros(n, np.int64)
@@ -469,7 +471,7 @@ class DiscGroup:
         _check(lib().disc_group_set_phase_timing(self._h, 1 if enable else 0), "disc_group_set_phase_timing")
 
     def phase_times(self) -> dict:
-        n = 12
+        n = 13
         ms = np.zeros(n, np.float64)
         la = np.zeros(n, np.int64)
         ca = np.zeros(n, np.int64)

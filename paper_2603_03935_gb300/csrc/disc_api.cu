@@ -183,6 +183,9 @@ bool config_ok(const disc_map_config& c)
     if (c.instance_capacity <= 0) return false;
     if (c.batch_frames < 0 || c.batch_frames > 256) return false;
     if (c.precision != DISC_FP32 && c.precision != DISC_BF16) return false;  // FP8 E4M3 is not built
+    // DBSCAN cells at least a voxel wide keep cell coordinates in key range
+    if (!(c.dbscan_eps >= 0.0f) || (c.dbscan_eps > 0.0f && (c.dbscan_eps < c.voxel_size || c.dbscan_min_pts < 1)))
+        return false;
     return true;
 }
 
@@ -430,6 +433,42 @@ disc_status ensure_hist(Runner& r, int n)
     return DISC_OK;
 }
 
+// The DBSCAN scratch of both slot sets, allocated when a frame first asks
+// for the filter (captured graphs hold the old slot pointers).
+disc_status ensure_dbscan(Runner& r)
+{
+    if (r.bs[0].base.dkey) return DISC_OK;
+    const size_t B = r.S, scap = (size_t)r.bs[0].scap, px = r.px_cap;
+    DevAlloc& a = r.mem;
+    for (int k = 0; k < 2; k++) {
+        Scratch& sc = r.bs[k].base;
+        sc.dkey = a.get<unsigned long long>(B * scap);
+        sc.dcnt = a.get<int32_t>(B * scap);
+        sc.dpos = a.get<int32_t>(B * scap);
+        sc.dlist = a.get<int32_t>(B * scap);
+        sc.dstart = a.get<int32_t>(B * scap);
+        sc.dfill = a.get<int32_t>(B * scap);
+        sc.dpt = a.get<float4>(B * px);
+        sc.dcell = a.get<int32_t>(B * px);
+        sc.dorder = a.get<int32_t>(B * px);
+        sc.dflag = a.get<unsigned char>(B * px);
+        r.bs[k].spx = (long long)px;
+    }
+    if (a.failed) {
+        a.failed = false;
+        for (int k = 0; k < 2; k++) r.bs[k].base.dkey = nullptr;
+        return DISC_ERR_OOM;
+    }
+    for (int k = 0; k < 2; k++) {
+        CK(cudaMemsetAsync(r.bs[k].base.dkey, 0, sizeof(unsigned long long) * B * scap, r.stream));
+        CK(cudaMemsetAsync(r.bs[k].base.dcnt, 0, sizeof(int32_t) * B * scap, r.stream));
+    }  // the slots' n_cells are 0 until a frame with the filter ran in them
+    for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
+    r.graphs.clear();
+    r.shapes_seen.clear();
+    return cuda_status(cudaStreamSynchronize(r.stream));
+}
+
 // ---- map tables --------------------------------------------------------------------
 disc_status alloc_voxel_table(disc_map* m, uint64_t cap, VoxelTable* out, cudaStream_t st)
 {
@@ -656,10 +695,11 @@ void reset_timing(Runner& r, bool enable)
 // reads -1, so the lookup returns either the final label or "absent", and an
 // absent voxel is looked up again by k_overlap after the earlier frames.
 
-// combos: bit (2 * token_bf16 + precision_bf16) set for every kind of frame in the batch
+// combos: bit (2 * token_bf16 + precision_bf16) set for every kind of frame in
+// the batch; bit 4: some frame runs the DBSCAN filter
 int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
 {
-    const bool any_bf16 = (combos & 12) != 0, any_f32 = (combos & 3) != 0;
+    const bool any_bf16 = (combos & 12) != 0, any_f32 = (combos & 3) != 0;  // bits 0-3
     bool any[2][2];
     for (int t = 0; t < 2; t++)
         for (int q = 0; q < 2; q++) any[t][q] = (combos >> (2 * t + q)) & 1;
@@ -677,6 +717,8 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
             const int nb = std::min(GEOMETRY_CHUNK, S - f0);
+            if (combos & 16)
+                run_phase(r, PH_DBSCAN, st, [&] { return launch_dbscan(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_BACKPROJECT, st, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_ENTRIES, st, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
         }
@@ -707,7 +749,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 
 long long graph_key(int part, int k, int S, int G, int J, int combos)
 {
-    return (((((((long long)S << 11) | G) << 9) | J) << 4 | combos) << 2) | (part << 1) | k;
+    return (((((((long long)S << 11) | G) << 9) | J) << 5 | combos) << 2) | (part << 1) | k;
 }
 
 // A part's kernel sequence captured once per shape and replayed.  A shape
@@ -874,6 +916,9 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     //         at most 2 * 2^-9 on the cosine
     const double K = r.Kpad, u24 = std::ldexp(1.0, -24), u9 = std::ldexp(1.0, -9);
     fp.precision = m->cfg.precision;
+    fp.db_min_pts = m->cfg.dbscan_eps > 0.0f ? m->cfg.dbscan_min_pts : 0;
+    fp.db_eps2 = m->cfg.dbscan_eps * m->cfg.dbscan_eps;
+    fp.db_inv_cell = m->cfg.dbscan_eps > 0.0f ? 1.0f / (m->cfg.dbscan_eps * 1.001f) : 0.0f;
     if (m->cfg.precision == DISC_BF16) {
         fp.eta = (float)(2.0 * u9 + u9 * u9 + 3.0 * K * u24);
         fp.dot_err = (float)(3.0 * u9 + 3.0 * D * u24);
@@ -923,6 +968,7 @@ void to_stats(const FrameCounters& c, disc_frame_stats* s)
     s->borderline_rescored = c.borderline;
     s->max_probe = c.max_probe;
     s->status = c.err;
+    s->denoised_pixels = c.denoised;
 }
 
 // The frames one call integrates into one map.
@@ -951,6 +997,9 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         nbatch = std::max(nbatch, (wk.valid + r.Jmax - 1) / r.Jmax);
     }
     disc_status s = ensure_hist(r, std::max(total, 1));
+    if (s != DISC_OK) return s;
+    for (const Work& wk : w)
+        if (wk.valid > 0 && wk.m->cfg.dbscan_eps > 0.0f) s = ensure_dbscan(r);
     if (s != DISC_OK) return s;
     // pipelined (calls of several batches): the runner's two streams start
     // after the caller's earlier work and the caller's stream waits for their
@@ -990,6 +1039,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 px += (uint64_t)f.width * f.height;
                 masks += f.num_masks;
                 combos |= 1 << (2 * (f.token_dtype == DISC_TOKENS_BF16) + (wk.m->cfg.precision == DISC_BF16));
+                if (wk.m->cfg.dbscan_eps > 0.0f) combos |= 16;
             }
             s = ensure_voxel_room(wk.m, px, sr);
             if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, sr);
@@ -1777,8 +1827,8 @@ disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int
 const char* disc_phase_name(int32_t i)
 {
     static const char* names[PH_COUNT] = {"clear",     "token_stats", "coverage", "weights", "pool_exact",
-                                          "pool_gemm", "backproject", "entries",  "overlap", "score",
-                                          "union",     "apply"};
+                                          "pool_gemm", "dbscan",      "backproject", "entries", "overlap",
+                                          "score",     "union",       "apply"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : "";
 }
 

@@ -132,7 +132,9 @@ struct FrameCounters {
     int32_t next_id;             // instance ids handed out so far
     int32_t num_masks;           // of the frame
     int32_t n_edges;
-    int32_t pad;
+    int32_t n_cells;             // DBSCAN grid cells of the frame
+    int32_t denoised;            // pixels DBSCAN marked as noise
+    int32_t pad[3];
 };
 
 // One slot of the per-frame (segment, voxel) hash: one 32-byte sector.
@@ -173,13 +175,24 @@ struct Scratch {
     int32_t* elab;              // [scap] per entry: label at batch start, -1 absent
     unsigned long long smask;
     FrameCounters* ctr;
+    // DBSCAN (Sec. III-A), allocated once a frame asks for it
+    unsigned long long* dkey;   // [scap] (mask << 54 | cell); EMPTY = 0
+    int32_t* dcnt;              // [scap] points per cell
+    int32_t* dpos;              // [scap] cell -> position in the cell list
+    int32_t* dlist;             // [scap] cell list (hash slots, claim order)
+    int32_t* dstart;            // [scap] first point of list position i in dorder
+    int32_t* dfill;             // [scap] scatter cursor per list position
+    float4* dpt;                // [px] world point and mask of each point
+    int32_t* dcell;             // [px] hash slot of the pixel's cell, -1: not a point
+    int32_t* dorder;            // [px] points in cell order
+    unsigned char* dflag;       // [px] bit 0 core, bit 1 noise
 };
 
 // The frame slots of one batch: base pointers plus the per-frame stride of
 // every array (in elements).
 struct BatchScratch {
     Scratch base;
-    long long sD, sP, sMM, sMMP, sW, sMMD, sS, scap;
+    long long sD, sP, sMM, sMMP, sW, sMMD, sS, scap, spx;
     __host__ __device__ Scratch frame(int f) const
     {
         Scratch s = base;
@@ -209,6 +222,18 @@ struct BatchScratch {
         s.sent += f * scap;
         s.elab += f * scap;
         s.ctr += f;
+        if (s.dkey) {
+            s.dkey += f * scap;
+            s.dcnt += f * scap;
+            s.dpos += f * scap;
+            s.dlist += f * scap;
+            s.dstart += f * scap;
+            s.dfill += f * scap;
+            s.dpt += f * spx;
+            s.dcell += f * spx;
+            s.dorder += f * spx;
+            s.dflag += f * spx;
+        }
         return s;
     }
 };
@@ -282,6 +307,9 @@ struct FrameParams {
     int32_t token_bf16;
     int32_t map;           // position of the frame's map in the batch (MapRefs index)
     int32_t precision;     // disc_precision of the fast pooled embedding and scoring
+    int32_t db_min_pts;    // DBSCAN core threshold; 0: no DBSCAN for this frame
+    float db_eps2;         // eps * eps
+    float db_inv_cell;     // 1 / (1.001 eps): grid cells a little wider than eps
     float eta;             // bound of |E_fast - E| relative to sum_p w_p ||f_p||
     float dot_err;         // bound of the fast cosine's own error
     const float* depth;
@@ -289,5 +317,18 @@ struct FrameParams {
     const void* tokens;
     const float* gembed;   // nullable
 };
+
+// ---- Sec. III-A: world point of pixel (u, v) at depth z -------------------------
+__device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v, float z, float p[3])
+{
+    float xc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fp.cx), z), fp.inv_fx);
+    float yc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), fp.cy), z), fp.inv_fy);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+        p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(fp.R[3 * r], xc), __fmul_rn(fp.R[3 * r + 1], yc)),
+                                   __fmul_rn(fp.R[3 * r + 2], z)),
+                         fp.t[r]);
+}
+
 
 }  // namespace disc

@@ -22,9 +22,14 @@ __global__ void k_slot_clear(BatchScratch bs, int D, int MM)
 {
     const Scratch sc = bs.frame(blockIdx.y);
     const int ne = sc.ctr->n_entries;
-    const int n = max(ne, max(D, MM));
+    const int nc = sc.dkey ? sc.ctr->n_cells : 0;
+    const int n = max(max(ne, nc), max(D, MM));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (i < ne) sc.sslot[sc.slist[i]] = SegSlot{0ull, {0, 0, 0}};
+        if (i < nc) {
+            sc.dkey[sc.dlist[i]] = 0ull;
+            sc.dcnt[sc.dlist[i]] = 0;
+        }
         if (i < D) sc.sumF[i] = 0;
         if (i < MM) {
             sc.npix[i] = 0;
@@ -46,19 +51,6 @@ __global__ void k_slot_reset(BatchScratch bs, int B)
     FrameCounters z = {};
     *sc.ctr = z;
 }
-
-// ---- Sec. III-A: world point of pixel (u, v) at depth z -------------------------
-__device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v, float z, float p[3])
-{
-    float xc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fp.cx), z), fp.inv_fx);
-    float yc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), fp.cy), z), fp.inv_fy);
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-        p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(fp.R[3 * r], xc), __fmul_rn(fp.R[3 * r + 1], yc)),
-                                   __fmul_rn(fp.R[3 * r + 2], z)),
-                         fp.t[r]);
-}
-
 
 // ---- back-projection + per-segment voxel dedupe (one thread per pixel) ----------
 // A block covers a 32 x 16 pixel tile.  The tile and a one-pixel halo are
@@ -99,7 +91,9 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
             const size_t idx = (size_t)hv * fp.W + hu;
             const int lab = fp.labels[idx];
             const float z = fp.depth[idx];
-            if (lab >= 1 && lab <= fp.M && z >= fp.z_min && z <= fp.z_max) {
+            // a DBSCAN noise pixel counts as invalid depth
+            if (lab >= 1 && lab <= fp.M && z >= fp.z_min && z <= fp.z_max &&
+                !(fp.db_min_pts > 0 && (sc.dflag[idx] & 2))) {
                 t.lab = lab;
                 world_point(fp, hu, hv, z, t.p);
             }

@@ -24,6 +24,7 @@ enum Phase {
     PH_WEIGHTS,       // pooling weights, S_size / S_sem / S_dist
     PH_POOL_EXACT,    // exact D-weighted pooled embedding
     PH_POOL_GEMM,     // tcgen05 pooled embedding (fast score)
+    PH_DBSCAN,        // Sec. III-A noise filter of the segment points (chunks of frames)
     PH_BACKPROJECT,   // depth -> voxel keys, normals, per-segment sets (chunks of frames)
     PH_ENTRIES,       // S_angle terms, |V_m|, labels at batch start (chunks), then Q
     PH_OVERLAP,       // per frame: overlap histogram against the current map
@@ -47,6 +48,8 @@ int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int 
 // back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
 // batch start) on frames [f0, f0 + nb); then Q of every segment
 int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
+// DBSCAN noise flags of frames [f0, f0 + nb) (frames without DBSCAN return at once)
+int launch_dbscan(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
 int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
                    cudaStream_t st);
 int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);

@@ -28,7 +28,10 @@ def disc_cfg(scene, **kw):
 def to_oracle_cfg(dcfg):
     keys = ("voxel_size", "z_min", "z_max", "eps", "tau_cos", "lambda_size", "ov_num", "ov_den",
             "embed_dim", "patch_h", "patch_w", "min_mask_pixels")
-    return {k: dcfg[k] for k in keys}
+    out = {k: dcfg[k] for k in keys}
+    out["dbscan_eps"] = dcfg.get("dbscan_eps", 0.0)
+    out["dbscan_min_pts"] = dcfg.get("dbscan_min_pts", 1)
+    return out
 
 
 EXACT_FIELDS = ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "S", "nvox", "rep")
@@ -36,7 +39,7 @@ COUNT_FIELDS = (("valid_pixels", "valid_pixels"), ("dropped_pixels", "dropped_pi
                 ("new_voxels", "new_voxels"), ("active_instances", "active_instances"),
                 ("new_instances", "new_instances"), ("merges", "merges"),
                 ("live_segments", "live_segments"), ("overlap_pairs", "overlap_pairs"),
-                ("unique_seg_voxels", "n_seg"))
+                ("unique_seg_voxels", "n_seg"), ("denoised_pixels", "denoised_pixels"))
 
 
 def rel_err_rows(a, b):

@@ -429,3 +429,54 @@ def test_overlapped_batches_equal_sequential(torch_dev):
     for k in ("parent", "count", "n_obs"):
         assert np.array_equal(ea[k], eb[k])
     assert np.array_equal(ea["E"].view(np.uint32), eb["E"].view(np.uint32))
+
+
+@pytest.mark.parametrize("eps,min_pts", [(0.05, 6), (0.08, 12)])
+def test_dbscan_tiny_trajectory_parity(torch_dev, eps, min_pts):
+    # Sec. III-A noise filter: Tiny frames have 3-5 cm between pixels, so
+    # segment edges and thin objects produce noise points
+    sc = synth.tiny_scene()
+    gmap, omap, stats = run_parity(torch_dev, sc, range(20), dbscan_eps=eps, dbscan_min_pts=min_pts)
+    assert sum(s["denoised_pixels"] for s in stats) > 0
+
+
+def test_dbscan_room_frames_batched_parity(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.room_scene()
+    fr = sc.render(range(40))
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 22, instance_capacity=1 << 12, dbscan_eps=0.05,
+                          dbscan_min_pts=10)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    for lo, hi in ((0, 32), (32, 40)):  # a full batch, then a partial one reusing the slots
+        frames = [_dframe(torch, dev, fr, i) for i in range(lo, hi)]
+        stats, done, rc = gmap.integrate_frames(frames)
+        assert rc == 0 and done == hi - lo
+        for j, st in enumerate(stats):
+            o = omap.integrate(*oracle.frame_args(fr, lo + j), report=True)
+            for gk, ok in common.COUNT_FIELDS:
+                assert st[gk] == o[ok], f"frame {lo + j} {gk}: {st[gk]} vs {o[ok]}"
+    common.compare_maps(gmap, omap, ctx="room dbscan")
+
+
+def test_dbscan_wall_outliers(torch_dev):
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    H, W, f = 48, 64, 50.0
+    depth = scenes.plane_depth(H, W, f, f, W / 2, H / 2, 2.0)
+    labels = np.ones((H, W), np.uint16)
+    outliers = [(10, 10), (20, 40), (30, 25), (40, 50)]
+    for (v, u) in outliers:
+        depth[v, u] = 1.5
+    tok = np.random.default_rng(5).standard_normal((48, 16)).astype(np.float32)
+    intr = (f, f, W / 2, H / 2)
+    cfg = dict(voxel_size=0.05, embed_dim=16, patch_h=6, patch_w=8, max_width=W, max_height=H, max_masks=2,
+               min_mask_pixels=3, voxel_capacity=1 << 14, instance_capacity=16, dbscan_eps=0.05, dbscan_min_pts=4)
+    gmap = DiscMap(**cfg)
+    ocfg = oracle.default_config(16, 6, 8, 0.05, min_mask_pixels=3, dbscan_eps=0.05, dbscan_min_pts=4)
+    omap = oracle.OracleMap(**ocfg)
+    st = gmap.integrate(host_frame(depth, labels, tok, np.eye(4), intr, 1))
+    o = omap.integrate(depth, labels, tok, np.eye(4), intr, 1)
+    assert st["denoised_pixels"] == o["denoised_pixels"] == len(outliers)
+    common.compare_frame(st, gmap.last_frame(), o, ctx="wall outliers")
+    common.compare_maps(gmap, omap, ctx="wall outliers")
