@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--served-maps", type=int, default=32)
     ap.add_argument("--served-rates", default="4000,8000,16000", help="offered frames/s, comma separated")
     ap.add_argument("--served-seconds", type=float, default=1.0)
+    ap.add_argument("--dbscan-steps", type=int, default=20,
+                    help="steps of the same workload with the DBSCAN filter on (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -542,6 +544,31 @@ def main():
     clk = clocks.stop()
     frames_all = K * B * world
 
+    # the same workload with the Sec. III-A DBSCAN filter on (eps 5 cm, 10 points)
+    dbscan = None
+    if args.dbscan_steps > 0:
+        dcfg = dict(cfg, dbscan_eps=0.05, dbscan_min_pts=10)
+        dmap = DiscMap(**dcfg)
+        for s_ in range(Wm):
+            assert dmap.integrate_frames_raw(steps[s_], B, stats) == 0
+        torch.cuda.synchronize()
+        dt_ms, den, nf = 0.0, 0, 0
+        for s_ in range(Wm, Wm + min(args.dbscan_steps, K)):
+            flush.fill_(float(s_))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = dmap.integrate_frames_raw(steps[s_], B, stats)
+            e1.record(stream)
+            e1.synchronize()
+            assert rc == 0, rc
+            dt_ms += e0.elapsed_time(e1)
+            den += sum(stats[j].denoised_pixels for j in range(B))
+            nf += B
+        dmap.close()
+        dbscan = {"frames_per_s": nf / (dt_ms / 1e3), "eps_m": 0.05, "min_pts": 10, "frames": nf,
+                  "denoised_pixels_per_frame": den / nf}
+
     # per-phase device time on the following batches (event-record nodes
     # around each phase, inside the batch's graph)
     lo = n_main
@@ -632,6 +659,7 @@ def main():
                               "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"},
                "frame_ms_batched": total_ms / (K * B),
                "batched": batched,
+               "dbscan": dbscan,
                "served": served,
                "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
                "gpu_launches": int(launches),
