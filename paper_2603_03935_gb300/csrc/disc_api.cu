@@ -452,6 +452,8 @@ disc_status ensure_dbscan(Runner& r)
         sc.dcell = a.get<int32_t>(B * px);
         sc.dorder = a.get<int32_t>(B * px);
         sc.dflag = a.get<unsigned char>(B * px);
+        sc.dsp = a.get<float4>(B * px);
+        sc.dund = a.get<int32_t>(B * px);
         r.bs[k].spx = (long long)px;
     }
     if (a.failed) {

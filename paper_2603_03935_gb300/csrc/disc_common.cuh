@@ -134,7 +134,8 @@ struct FrameCounters {
     int32_t n_edges;
     int32_t n_cells;             // DBSCAN grid cells of the frame
     int32_t denoised;            // pixels DBSCAN marked as noise
-    int32_t pad[3];
+    int32_t db_left[2];          // DBSCAN points left to the warp-wide core / noise search
+    int32_t db_cursor;           // DBSCAN cell ranges handed out
 };
 
 // One slot of the per-frame (segment, voxel) hash: one 32-byte sector.
@@ -186,6 +187,8 @@ struct Scratch {
     int32_t* dcell;             // [px] hash slot of the pixel's cell, -1: not a point
     int32_t* dorder;            // [px] points in cell order
     unsigned char* dflag;       // [px] bit 0 core, bit 1 noise
+    float4* dsp;                // [px] the points in cell order (copies of dpt)
+    int32_t* dund;              // [px] points the pixel window left undecided
 };
 
 // The frame slots of one batch: base pointers plus the per-frame stride of
@@ -233,6 +236,8 @@ struct BatchScratch {
             s.dcell += f * spx;
             s.dorder += f * spx;
             s.dflag += f * spx;
+            s.dsp += f * spx;
+            s.dund += f * spx;
         }
         return s;
     }

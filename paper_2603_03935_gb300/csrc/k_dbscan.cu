@@ -6,13 +6,25 @@
 // are noise and count as invalid depth for the back-projection.
 //
 // Per frame (chunks of frames like the back-projection):
-//   k_db_points   world point of every point pixel; its (mask, cell) in a
-//                 hash of cells 1.001 eps wide, so every point within eps of
-//                 a point lies in the 27 cells around it
-//   k_db_offsets  first position of every cell in the cell-ordered list
-//   k_db_scatter  the points in cell order
-//   k_db_core     core flags (counting stops at min_pts)
-//   k_db_noise    noise flags of the points with no core point within eps
+//   k_db_points      world point of every point pixel; its (mask, cell) in a
+//                    hash of cells 1.001 eps wide, so every point within eps
+//                    of a point lies in the 27 cells around it
+//   k_db_ranges      a range of the cell-ordered point list for every cell
+//   k_db_scatter     the points in cell order
+//   k_db_core        core flags from the 5x5 pixels around each point: those
+//                    are distinct points of the frame, so min_pts of them
+//                    within eps already make the point core
+//   k_db_core_full   the points the window left undecided, one warp each,
+//                    over the 27 cells (counting stops at min_pts)
+//   k_db_noise       a non-core point with a core point among its 5x5
+//                    pixels within eps is kept
+//   k_db_noise_full  the rest, one warp each: noise when no core point of
+//                    the 27 cells lies within eps
+// Counting and "any core" do not depend on the order of the points, so the
+// order in which cells claim their ranges and points their places does not
+// reach the result.
+#include <algorithm>
+
 #include "disc_common.cuh"
 #include "kernels.h"
 
@@ -54,29 +66,86 @@ __device__ __forceinline__ bool within(float4 a, float4 b, float eps2)
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) <= eps2;
 }
 
-// Visit the points of the 27 cells around point p (same mask) that lie
-// within eps; f returns false to stop.
+// Warp-wide walk over the points of the 27 cells around point p (same mask),
+// 32 points at a time: f(hit, k) gets each lane's "within eps" and the
+// point's position k in the cell-ordered list, and returns true (uniform over
+// the warp) to stop.  Lane t < 27 looks up cell t at once (the point's own
+// cell on lane 0); the walk then runs over the cells' ranges laid end to end.
+// Every lane holds the same p, so the walk is uniform.
 template <class F>
-__device__ __forceinline__ void for_neighbours(const FrameParams& fp, const Scratch& sc, float4 p, F&& f)
+__device__ __forceinline__ void warp_neighbours(const FrameParams& fp, const Scratch& sc, float4 p, F&& f)
 {
     int c[3];
     cell_of(fp, p, c);
     const int lab = __float_as_int(p.w);
-    for (int dx = -1; dx <= 1; dx++)
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dz = -1; dz <= 1; dz++) {
-                const int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
-                if (q[0] < -KEY_BIAS || q[0] > KEY_BIAS - 1 || q[1] < -KEY_BIAS || q[1] > KEY_BIAS - 1 ||
-                    q[2] < -KEY_BIAS || q[2] > KEY_BIAS - 1)
-                    continue;
-                const long long h = find_cell(sc, cell_key(lab, q[0], q[1], q[2]));
-                if (h < 0) continue;
-                const int s0 = sc.dstart[sc.dpos[h]], n = sc.dcnt[h];
-                for (int j = 0; j < n; j++) {
-                    const int o = sc.dorder[s0 + j];
-                    if (within(p, sc.dpt[o], fp.db_eps2) && !f(o)) return;
-                }
+    const int lane = threadIdx.x & 31;
+    int s0 = 0, n = 0;
+    if (lane < 27) {
+        const int o27 = lane == 0 ? 13 : (lane <= 13 ? lane - 1 : lane);  // 13 = offset (0, 0, 0)
+        const int q[3] = {c[0] + o27 / 9 - 1, c[1] + (o27 / 3) % 3 - 1, c[2] + o27 % 3 - 1};
+        if (q[0] >= -KEY_BIAS && q[0] <= KEY_BIAS - 1 && q[1] >= -KEY_BIAS && q[1] <= KEY_BIAS - 1 &&
+            q[2] >= -KEY_BIAS && q[2] <= KEY_BIAS - 1) {
+            const long long h = find_cell(sc, cell_key(lab, q[0], q[1], q[2]));
+            if (h >= 0) {
+                s0 = sc.dstart[sc.dpos[h]];
+                n = sc.dcnt[h];
             }
+        }
+    }
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int excl = incl - n;  // non-decreasing over the lanes; lanes 27..31 hold the total
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int j0 = 0; j0 < total; j0 += 32) {
+        const int j = j0 + lane;
+        int cc = 0;  // the last lane whose range starts at or before j: the cell holding j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, cc + step);
+            if (e <= j) cc += step;
+        }
+        const int k = __shfl_sync(0xffffffffu, s0, cc) + j - __shfl_sync(0xffffffffu, excl, cc);
+        const bool hit = j < total && within(p, sc.dsp[k], fp.db_eps2);
+        if (f(hit, k)) return;
+    }
+}
+
+// Appends v to list (counter cnt) for the lanes with take; all 32 lanes call.
+__device__ __forceinline__ void warp_append(int* list, int* cnt, bool take, int v)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    int base = 0;
+    if (lane == lead) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (take) list[base + __popc(m & ((1u << lane) - 1))] = v;
+}
+
+// Visit the points among the 5x5 pixels around pixel (u, v), itself
+// included, of the same mask and within eps; f returns false to stop.
+// Returns false when f stopped the walk.
+template <class F>
+__device__ __forceinline__ bool for_window(const FrameParams& fp, const Scratch& sc, int u, int v, float4 p, F&& f)
+{
+    const int lab = __float_as_int(p.w);
+    for (int dv = -2; dv <= 2; dv++) {
+        const int vv = v + dv;
+        if (vv < 0 || vv >= fp.H) continue;
+        for (int du = -2; du <= 2; du++) {
+            const int uu = u + du;
+            if (uu < 0 || uu >= fp.W) continue;
+            const int o = vv * fp.W + uu;
+            if (sc.dcell[o] < 0) continue;
+            const float4 q = sc.dpt[o];
+            if (__float_as_int(q.w) == lab && within(p, q, fp.db_eps2) && !f(o)) return false;
+        }
+    }
+    return true;
 }
 
 }  // namespace
@@ -145,19 +214,16 @@ __global__ void k_db_points(const FrameParams* fps, BatchScratch bs, int f0)
     if (idx < npx) sc.dcell[idx] = pt ? (int)h : -1;
 }
 
-// one block per frame: exclusive scan of the cell sizes in list order
-__global__ void k_db_offsets(const FrameParams* fps, BatchScratch bs, int f0)
+// a range of the cell-ordered list per cell: each warp claims the sum of
+// its cells' sizes at once and splits it by a scan
+__global__ void k_db_ranges(const FrameParams* fps, BatchScratch bs, int f0)
 {
-    const FrameParams& fp = fps[f0 + blockIdx.x];
-    const Scratch sc = bs.frame(f0 + blockIdx.x);
+    const FrameParams& fp = fps[f0 + blockIdx.y];
+    const Scratch sc = bs.frame(f0 + blockIdx.y);
     if (fp.db_min_pts <= 0 || fp.M <= 0 || sc.ctr->err) return;
-    __shared__ int wsum[32];
-    __shared__ int carry;
     const int n = sc.ctr->n_cells;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {  // uniform per block
         const int i = i0 + threadIdx.x;
         const int x = i < n ? sc.dcnt[sc.dlist[i]] : 0;
         int incl = x;
@@ -166,27 +232,13 @@ __global__ void k_db_offsets(const FrameParams* fps, BatchScratch bs, int f0)
             const int y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = blockDim.x >> 5;
-            int w = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, d);
-                if (lane >= d) w += y;
-            }
-            if (lane < nw) wsum[lane] = w;  // inclusive warp totals
-        }
-        __syncthreads();
-        const int before = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - x;
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&sc.ctr->db_cursor, incl);
+        base = __shfl_sync(0xffffffffu, base, 31);
         if (i < n) {
-            sc.dstart[i] = before;
+            sc.dstart[i] = base + incl - x;
             sc.dfill[i] = 0;
         }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = before + x;
-        __syncthreads();
     }
 }
 
@@ -206,7 +258,9 @@ __global__ void k_db_scatter(const FrameParams* fps, BatchScratch bs, int f0)
     const int lead = __ffs(grp) - 1;
     if (lane == lead) base = atomicAdd(&sc.dfill[lp], __popc(grp));
     base = __shfl_sync(grp, base, lead);
-    sc.dorder[sc.dstart[lp] + base + __popc(grp & ((1u << lane) - 1))] = idx;
+    const int k = sc.dstart[lp] + base + __popc(grp & ((1u << lane) - 1));
+    sc.dorder[k] = idx;
+    sc.dsp[k] = sc.dpt[idx];
 }
 
 __global__ void k_db_core(const FrameParams* fps, BatchScratch bs, int f0)
@@ -216,12 +270,36 @@ __global__ void k_db_core(const FrameParams* fps, BatchScratch bs, int f0)
     if (fp.db_min_pts <= 0 || fp.M <= 0 || sc.ctr->err) return;
     const int npx = fp.W * fp.H;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= npx || sc.dcell[idx] < 0) return;
-    const float4 p = sc.dpt[idx];
-    int cnt = 0;
-    const int need = fp.db_min_pts;
-    for_neighbours(fp, sc, p, [&](int) { return ++cnt < need; });
-    if (cnt >= need) sc.dflag[idx] = 1;
+    bool left = false;
+    if (idx < npx && sc.dcell[idx] >= 0) {
+        int cnt = 0;
+        const int need = fp.db_min_pts;
+        for_window(fp, sc, idx % fp.W, idx / fp.W, sc.dpt[idx], [&](int) { return ++cnt < need; });
+        if (cnt >= need)
+            sc.dflag[idx] = 1;
+        else
+            left = true;
+    }
+    warp_append(sc.dund, &sc.ctr->db_left[0], left, idx);
+}
+
+// one warp per point the window left undecided
+__global__ void k_db_core_full(const FrameParams* fps, BatchScratch bs, int f0)
+{
+    const FrameParams& fp = fps[f0 + blockIdx.y];
+    const Scratch sc = bs.frame(f0 + blockIdx.y);
+    if (fp.db_min_pts <= 0 || fp.M <= 0 || sc.ctr->err) return;
+    const int n = sc.ctr->db_left[0], need = fp.db_min_pts;
+    const int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {  // uniform per warp
+        const int idx = sc.dund[i];
+        int cnt = 0;
+        warp_neighbours(fp, sc, sc.dpt[idx], [&](bool hit, int) {
+            cnt += __popc(__ballot_sync(0xffffffffu, hit));
+            return cnt >= need;
+        });
+        if ((threadIdx.x & 31) == 0 && cnt >= need) sc.dflag[idx] = 1;
+    }
 }
 
 __global__ void k_db_noise(const FrameParams* fps, BatchScratch bs, int f0)
@@ -231,32 +309,53 @@ __global__ void k_db_noise(const FrameParams* fps, BatchScratch bs, int f0)
     if (fp.db_min_pts <= 0 || fp.M <= 0 || sc.ctr->err) return;
     const int npx = fp.W * fp.H;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    bool noise = false;
+    bool left = false;
     if (idx < npx && sc.dcell[idx] >= 0 && !(sc.dflag[idx] & 1)) {
         bool near_core = false;
-        for_neighbours(fp, sc, sc.dpt[idx], [&](int o) {
+        for_window(fp, sc, idx % fp.W, idx / fp.W, sc.dpt[idx], [&](int o) {
             near_core = (sc.dflag[o] & 1) != 0;
             return !near_core;
         });
-        if (!near_core) {
+        left = !near_core;
+    }
+    warp_append(sc.dund, &sc.ctr->db_left[1], left, idx);
+}
+
+// one warp per non-core point with no core point in its window
+__global__ void k_db_noise_full(const FrameParams* fps, BatchScratch bs, int f0)
+{
+    const FrameParams& fp = fps[f0 + blockIdx.y];
+    const Scratch sc = bs.frame(f0 + blockIdx.y);
+    if (fp.db_min_pts <= 0 || fp.M <= 0 || sc.ctr->err) return;
+    const int n = sc.ctr->db_left[1];
+    const int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {  // uniform per warp
+        const int idx = sc.dund[i];
+        bool kept = false;
+        warp_neighbours(fp, sc, sc.dpt[idx], [&](bool hit, int k) {
+            kept = __any_sync(0xffffffffu, hit && (sc.dflag[sc.dorder[k]] & 1));
+            return kept;
+        });
+        if ((threadIdx.x & 31) == 0 && !kept) {
             sc.dflag[idx] = 2;
-            noise = true;
+            atomicAdd(&sc.ctr->denoised, 1);
         }
     }
-    const int nn = __popc(__ballot_sync(0xffffffffu, noise));
-    if ((threadIdx.x & 31) == 0 && nn) atomicAdd(&sc.ctr->denoised, nn);
 }
 
 int launch_dbscan(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st)
 {
     const int npx = H * W;
-    dim3 g((npx + 255) / 256, nb);
+    // the warp-wide searches: up to 64 resident warps on each of 152 SMs
+    const dim3 g((npx + 255) / 256, nb), gl(std::max(8, 1216 / std::max(nb, 1)), nb);
     k_db_points<<<g, 256, 0, st>>>(fps, bs, f0);
-    k_db_offsets<<<nb, 1024, 0, st>>>(fps, bs, f0);
+    k_db_ranges<<<dim3(16, nb), 256, 0, st>>>(fps, bs, f0);
     k_db_scatter<<<g, 256, 0, st>>>(fps, bs, f0);
     k_db_core<<<g, 256, 0, st>>>(fps, bs, f0);
+    k_db_core_full<<<gl, 256, 0, st>>>(fps, bs, f0);
     k_db_noise<<<g, 256, 0, st>>>(fps, bs, f0);
-    return 5;
+    k_db_noise_full<<<gl, 256, 0, st>>>(fps, bs, f0);
+    return 7;
 }
 
 }  // namespace disc
