@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--served-maps", type=int, default=32)
     ap.add_argument("--served-rates", default="4000,8000,16000", help="offered frames/s, comma separated")
     ap.add_argument("--served-seconds", type=float, default=1.0)
+    ap.add_argument("--served-precision", type=int, default=2, help="0 fp32, 1 bf16, 2 fp8 e4m3")
     ap.add_argument("--dbscan-steps", type=int, default=20,
                     help="steps of the same workload with the DBSCAN filter on (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -299,7 +300,8 @@ def run_batched(args, torch, dev, stream, rank):
     return out
 
 
-SERVED = "Served: {G} resident room-scale maps of mixed size (320x240..640x480, 5-60 masks, bf16 tokens), " \
+SERVED = "Served: {G} resident room-scale maps of mixed size (320x240..640x480, 5-60 masks, bf16 tokens, " \
+         "{prec} pooling and scoring), " \
          "Poisson arrivals, integrate:query 9:1 (top-5 of 4 vectors), each map cycling through its {F} frames, " \
          "4 client threads, continuous batching of up to {J} frames per map per batch"
 
@@ -323,7 +325,9 @@ def run_served(args, torch, dev, rank):
                      patch_h=scs[0].patch_h, patch_w=scs[0].patch_w, max_width=max(s.width for s in scs),
                      max_height=max(s.height for s in scs), max_masks=max(s.max_masks for s in scs),
                      device=dev.index)
-    ids = [srv.open_map(**common.disc_cfg(sc, voxel_capacity=1 << 21, instance_capacity=1 << 12)) for sc in scs]
+    # the served maps score in FP8 (E4M3 embeddings with per-vector scales)
+    ids = [srv.open_map(**common.disc_cfg(sc, voxel_capacity=1 << 21, instance_capacity=1 << 12,
+                                          precision=args.served_precision)) for sc in scs]
     queries = [fr.tokens[0][:4] for fr in frs]
     # warm-up: every map takes its frames once
     for g in range(G):
@@ -380,7 +384,8 @@ def run_served(args, torch, dev, rank):
                     "queries": rep["queries"], "batches": rep["batches"],
                     "frames_per_batch": rep["frames"] / max(rep["batches"], 1)})
     srv.close()
-    return {"workload": SERVED.format(G=G, F=F, J=J), "rates": out}
+    prec = ("fp32", "bf16", "fp8 e4m3")[args.served_precision]
+    return {"workload": SERVED.format(G=G, F=F, J=J, prec=prec), "rates": out}
 
 
 def run_reference(args, rank):

@@ -71,7 +71,14 @@ typedef struct {
     int64_t voxel_capacity;  /* initial hash slots (rounded up to a power of two) */
     float max_load;          /* the table doubles before its load would pass this */
     int32_t instance_capacity; /* initial instance slots (grows on demand) */
-    int32_t precision;       /* disc_precision of the fast pooling/scoring path */
+    int32_t precision;       /* disc_precision of the fast pooling/scoring path (Sec. III-B gate):
+                                FP32 = TF32x3 tensor-core pooling, fp32 scoring copies;
+                                BF16 = bf16 operands and scoring copies, fp32 accumulation;
+                                FP8_E4M3 = E4M3 operands with power-of-two per-vector scales
+                                (per token, per weight row, per stored embedding), fp32
+                                accumulation.  Every precision re-scores the pairs whose fast
+                                cosine lies within its error bound of tau_cos exactly, so
+                                labels, counts and stored embeddings are the same for all */
     void* cuda_stream;       /* cudaStream_t, or NULL: the map creates one */
     int32_t device;          /* CUDA device ordinal */
     int32_t batch_frames;    /* frames whose stateless phases share one launch (1..256) */
@@ -134,6 +141,7 @@ typedef struct {
     int64_t seg_cap;
     int64_t n_seg;      /* out: number of pairs */
     int32_t num_masks;  /* out */
+    float* E_bound;     /* [M] the bound of ||E_fast - E|| the association gate's re-score band uses */
 } disc_frame_report;
 
 /* Fills a config with the defaults used throughout (eps 1e-6, tau_cos 0.75,

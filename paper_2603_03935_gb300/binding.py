@@ -78,7 +78,7 @@ class Report(ctypes.Structure):
     _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
                 ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
                 ("seg_keys", c_vp), ("seg_m", c_vp), ("seg_cap", c_i64), ("n_seg", c_i64),
-                ("num_masks", c_i32)]
+                ("num_masks", c_i32), ("E_bound", c_vp)]
 
 
 _lib = None
@@ -313,15 +313,17 @@ class DiscMap:
                    W=np.zeros((max(M_cap, 1), P), np.float32), E=np.zeros((max(M_cap, 1), D), np.float32),
                    E_fast=np.zeros((max(M_cap, 1), D), np.float32), S=np.zeros((max(M_cap, 1), 5), np.float32),
                    nvox=np.zeros(max(M_cap, 1), np.int32), rep=np.zeros(max(M_cap, 1), np.int32),
-                   seg_keys=np.zeros(npx, np.uint64), seg_m=np.zeros(npx, np.int32))
+                   seg_keys=np.zeros(npx, np.uint64), seg_m=np.zeros(npx, np.int32),
+                   E_bound=np.zeros(max(M_cap, 1), np.float32))
         r = Report()
-        for k in ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "seg_keys", "seg_m"):
+        for k in ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "seg_keys", "seg_m",
+                  "E_bound"):
             setattr(r, k, out[k].ctypes.data)
         r.seg_cap = npx
         _check(lib().disc_map_last_frame(self._h, ctypes.byref(r)), "disc_map_last_frame")
         M = int(r.num_masks)
         n = int(r.n_seg)
-        for k in ("cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep"):
+        for k in ("cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "E_bound"):
             out[k] = out[k][:M]
         order = np.lexsort((out["seg_keys"][:n], out["seg_m"][:n]))
         out["seg_keys"] = out["seg_keys"][:n][order]

@@ -182,7 +182,7 @@ bool config_ok(const disc_map_config& c)
     if (c.voxel_capacity <= 0 || !(c.max_load > 0.0f && c.max_load < 1.0f)) return false;
     if (c.instance_capacity <= 0) return false;
     if (c.batch_frames < 0 || c.batch_frames > 256) return false;
-    if (c.precision != DISC_FP32 && c.precision != DISC_BF16) return false;  // FP8 E4M3 is not built
+    if (c.precision != DISC_FP32 && c.precision != DISC_BF16 && c.precision != DISC_FP8_E4M3) return false;
     // DBSCAN cells at least a voxel wide keep cell coordinates in key range
     if (!(c.dbscan_eps >= 0.0f) || (c.dbscan_eps > 0.0f && (c.dbscan_eps < c.voxel_size || c.dbscan_min_pts < 1)))
         return false;
@@ -332,6 +332,11 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         sc.Dp = a.get<float>((size_t)B * P);
         sc.cosg = a.get<float>((size_t)B * P);
         sc.fnorm = a.get<float>((size_t)B * P);
+        sc.qexp = a.get<int32_t>((size_t)B * P);
+        sc.qerr = a.get<float>((size_t)B * P);
+        sc.qnrm = a.get<float>((size_t)B * P);
+        sc.qexpm = a.get<int32_t>((size_t)B * MM);
+        sc.W8 = a.get<uint8_t>((size_t)B * bs.sW);
         sc.cov = a.get<int32_t>((size_t)B * MM * P);
         sc.npix = a.get<int32_t>((size_t)B * MM);
         sc.W = a.get<float>((size_t)B * bs.sW);
@@ -377,6 +382,8 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         CK(cudaMemsetAsync(r.d_param[k], 0, r.param_bytes, s));
         CK(cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s));
         CK(cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s));
+        CK(cudaMemsetAsync(sc.W8, 0, (size_t)B * bs.sW, s));
+        CK(cudaMemsetAsync(sc.qexpm, 0, sizeof(int32_t) * (size_t)B * MM, s));
         CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
         CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
         CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
@@ -502,6 +509,8 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
     in.Q = m->mem.get<float>(cap);
     in.E = m->mem.get<float>((size_t)cap * m->D);
     in.Eb = m->cfg.precision == DISC_BF16 ? m->mem.get<uint16_t>((size_t)cap * m->D) : nullptr;
+    in.E8 = m->cfg.precision == DISC_FP8_E4M3 ? m->mem.get<uint8_t>((size_t)cap * m->D) : nullptr;
+    in.Er = m->cfg.precision == DISC_FP8_E4M3 ? m->mem.get<float>(cap) : nullptr;
     in.n_obs = m->mem.get<int32_t>(cap);
     if (m->mem.failed) {
         m->mem.failed = false;
@@ -510,6 +519,8 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
         if (in.Q) m->mem.release(in.Q, sizeof(float) * cap);
         if (in.E) m->mem.release(in.E, sizeof(float) * (size_t)cap * m->D);
         if (in.Eb) m->mem.release(in.Eb, sizeof(uint16_t) * (size_t)cap * m->D);
+        if (in.E8) m->mem.release(in.E8, (size_t)cap * m->D);
+        if (in.Er) m->mem.release(in.Er, sizeof(float) * cap);
         if (in.n_obs) m->mem.release(in.n_obs, sizeof(int32_t) * cap);
         return DISC_ERR_OOM;
     }
@@ -586,6 +597,10 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     CK(cudaMemcpyAsync(ni.E, m->inst.E, sizeof(float) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
     if (ni.Eb)
         CK(cudaMemcpyAsync(ni.Eb, m->inst.Eb, sizeof(uint16_t) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+    if (ni.E8) {
+        CK(cudaMemcpyAsync(ni.E8, m->inst.E8, (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ni.Er, m->inst.Er, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    }
     CK(cudaMemcpyAsync(ni.n_obs, m->inst.n_obs, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     const int oc = m->inst.cap;
@@ -594,6 +609,8 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     m->mem.release(m->inst.Q, sizeof(float) * oc);
     m->mem.release(m->inst.E, sizeof(float) * (size_t)oc * m->D);
     if (m->inst.Eb) m->mem.release(m->inst.Eb, sizeof(uint16_t) * (size_t)oc * m->D);
+    if (m->inst.E8) m->mem.release(m->inst.E8, (size_t)oc * m->D);
+    if (m->inst.Er) m->mem.release(m->inst.Er, sizeof(float) * oc);
     m->mem.release(m->inst.n_obs, sizeof(int32_t) * oc);
     m->inst = ni;
     return DISC_OK;
@@ -697,14 +714,16 @@ void reset_timing(Runner& r, bool enable)
 // reads -1, so the lookup returns either the final label or "absent", and an
 // absent voxel is looked up again by k_overlap after the earlier frames.
 
-// combos: bit (2 * token_bf16 + precision_bf16) set for every kind of frame in
-// the batch; bit 4: some frame runs the DBSCAN filter
+// combos: bit (3 * token_bf16 + precision) set for every kind of frame in
+// the batch; bit COMBO_DBSCAN: some frame runs the DBSCAN filter
+constexpr int COMBO_DBSCAN = 1 << 6;
+
 int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
 {
-    const bool any_bf16 = (combos & 12) != 0, any_f32 = (combos & 3) != 0;  // bits 0-3
-    bool any[2][2];
+    const bool any_bf16 = (combos & 070) != 0, any_f32 = (combos & 07) != 0;  // bits 0-5
+    bool any[2][3];
     for (int t = 0; t < 2; t++)
-        for (int q = 0; q < 2; q++) any[t][q] = (combos >> (2 * t + q)) & 1;
+        for (int q = 0; q < 3; q++) any[t][q] = (combos >> (3 * t + q)) & 1;
     const int D = r.D, P = r.P, Mmax = r.Mmax;
     const BatchScratch& bs = r.bs[k];
     const FrameParams* dfp = r.fps(k);
@@ -719,7 +738,7 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
             const int nb = std::min(GEOMETRY_CHUNK, S - f0);
-            if (combos & 16)
+            if (combos & COMBO_DBSCAN)
                 run_phase(r, PH_DBSCAN, st, [&] { return launch_dbscan(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_BACKPROJECT, st, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_ENTRIES, st, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
@@ -751,7 +770,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 
 long long graph_key(int part, int k, int S, int G, int J, int combos)
 {
-    return (((((((long long)S << 11) | G) << 9) | J) << 5 | combos) << 2) | (part << 1) | k;
+    return (((((((long long)S << 11) | G) << 9) | J) << 7 | combos) << 2) | (part << 1) | k;
 }
 
 // A part's kernel sequence captured once per shape and replayed.  A shape
@@ -872,6 +891,32 @@ disc_status check_frame(const disc_map* m, const Runner& r, const disc_frame* f)
 
 // Frame parameters of frame f of map m in slot `slot` (map position g); host
 // inputs are staged into the slot's buffers.
+
+// Error bounds of the fast score: eta scales the per-mask Bm into the bound
+// of |E_fast - E|, dot_err bounds the fast cosine's own error.
+//   FP32: Bm = sum_p w_p ||f_p||; tf32 split residue 3 * 2^-22 plus fp32
+//         accumulation of 3 K products; fp32 warp cosine 3 D 2^-24
+//   BF16: both operands rounded to bf16, 2 * 2^-9, plus fp32 accumulation
+//         of K products; the bf16 scoring copy of E_k adds 2^-9 relative,
+//         at most 2 * 2^-9 on the cosine
+//   FP8:  the weights kernel stores the whole bound of |E_fast - E| in Bm
+//         (eta 1); each E4M3 scoring copy carries its own relative error
+//         bound, added per instance in the gate
+void fast_error_terms(int precision, int Kpad, int D, float* eta, float* dot_err)
+{
+    const double K = Kpad, u24 = std::ldexp(1.0, -24), u9 = std::ldexp(1.0, -9);
+    if (precision == DISC_BF16) {
+        *eta = (float)(2.0 * u9 + u9 * u9 + 3.0 * K * u24);
+        *dot_err = (float)(3.0 * u9 + 3.0 * D * u24);
+    } else if (precision == DISC_FP8_E4M3) {
+        *eta = 1.0f;
+        *dot_err = (float)(3.0 * D * u24);
+    } else {
+        *eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * K * u24);
+        *dot_err = (float)(3.0 * D * u24);
+    }
+}
+
 disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int slot, int g, FrameParams* out,
                          cudaStream_t st)
 {
@@ -909,25 +954,11 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     fp.min_px = std::max(1, m->cfg.min_mask_pixels);
     fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
     fp.map = g;
-    // error bounds of the fast score, relative to sum_p w_p ||f_p|| (pooled
-    // embedding) and absolute on the cosine:
-    //   FP32: tf32 split residue 3 * 2^-22 plus fp32 accumulation of 3 K
-    //         products; fp32 warp cosine 3 D 2^-24
-    //   BF16: both operands rounded to bf16, 2 * 2^-9, plus fp32 accumulation
-    //         of K products; the bf16 scoring copy of E_k adds 2^-9 relative,
-    //         at most 2 * 2^-9 on the cosine
-    const double K = r.Kpad, u24 = std::ldexp(1.0, -24), u9 = std::ldexp(1.0, -9);
     fp.precision = m->cfg.precision;
     fp.db_min_pts = m->cfg.dbscan_eps > 0.0f ? m->cfg.dbscan_min_pts : 0;
     fp.db_eps2 = m->cfg.dbscan_eps * m->cfg.dbscan_eps;
     fp.db_inv_cell = m->cfg.dbscan_eps > 0.0f ? 1.0f / (m->cfg.dbscan_eps * 1.001f) : 0.0f;
-    if (m->cfg.precision == DISC_BF16) {
-        fp.eta = (float)(2.0 * u9 + u9 * u9 + 3.0 * K * u24);
-        fp.dot_err = (float)(3.0 * u9 + 3.0 * D * u24);
-    } else {
-        fp.eta = (float)(3.0 * std::ldexp(1.0, -22) + 3.0 * K * u24);
-        fp.dot_err = (float)(3.0 * D * u24);
-    }
+    fast_error_terms(m->cfg.precision, r.Kpad, D, &fp.eta, &fp.dot_err);
     const size_t npx = (size_t)fp.H * fp.W;
     const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
     if (f->inputs_on_device) {
@@ -1040,8 +1071,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 const disc_frame& f = wk.frames[lo + j];
                 px += (uint64_t)f.width * f.height;
                 masks += f.num_masks;
-                combos |= 1 << (2 * (f.token_dtype == DISC_TOKENS_BF16) + (wk.m->cfg.precision == DISC_BF16));
-                if (wk.m->cfg.dbscan_eps > 0.0f) combos |= 16;
+                combos |= 1 << (3 * (f.token_dtype == DISC_TOKENS_BF16) + wk.m->cfg.precision);
+                if (wk.m->cfg.dbscan_eps > 0.0f) combos |= COMBO_DBSCAN;
             }
             s = ensure_voxel_room(wk.m, px, sr);
             if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, sr);
@@ -1360,6 +1391,12 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
         if (r->S) CK(cudaMemcpy(r->S, sc.S, sizeof(float) * 5 * M, cudaMemcpyDeviceToHost));
         if (r->nvox) CK(cudaMemcpy(r->nvox, sc.nvox, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
         if (r->rep) CK(cudaMemcpy(r->rep, sc.segrep, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
+        if (r->E_bound) {
+            float eta = 0.0f, dot_err = 0.0f;
+            fast_error_terms(m->cfg.precision, m->Kpad, D, &eta, &dot_err);
+            CK(cudaMemcpy(r->E_bound, sc.Bm, sizeof(float) * M, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < M; i++) r->E_bound[i] *= eta;
+        }
     }
     r->n_seg = c.n_entries;
     if (r->seg_keys && r->seg_m && c.n_entries > 0) {
@@ -1709,6 +1746,7 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
             }
             cudaMemcpyAsync(m->inst.Eb, Eb.data(), 2 * (size_t)nid * D, cudaMemcpyHostToDevice, m->stream);
         }
+        if (m->inst.E8) launch_e4m3_copies(m->inst, nid, D, m->stream);  // scoring copies from E
         cudaMemcpyAsync(m->inst.n_obs, obs.data(), 4 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->d_next_id, &nid, sizeof(int), cudaMemcpyHostToDevice, m->stream);
     }

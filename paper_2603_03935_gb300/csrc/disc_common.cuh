@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "../../include/disc.h"
@@ -111,6 +112,8 @@ struct Instances {
     float* Q;
     float* E;                    // [cap][D] stored embedding
     uint16_t* Eb;                // [cap][D] bf16 scoring copy of E (BF16 precision), else NULL
+    uint8_t* E8;                 // [cap][D] E4M3 scoring copy of E / 2^e (FP8 precision), else NULL
+    float* Er;                   // [cap] bound of ||2^e E8 - E|| / ||E|| for the E4M3 copy
     int32_t* n_obs;
     int32_t cap;
 };
@@ -158,6 +161,12 @@ struct Scratch {
     float* Dp;          // [P]
     float* cosg;        // [P]
     float* fnorm;       // [P]
+    // E4M3 operands (FP8 precision): token p is quantised as f_p / 2^qexp[p]
+    int32_t* qexp;      // [P]
+    float* qerr;        // [P] bound of ||2^qexp q_p - f_p||
+    float* qnrm;        // [P] bound of ||q_p|| (quantised units)
+    int32_t* qexpm;     // [MM] mask m's weight row is quantised as 2^qexp[p] w / 2^qexpm[m]
+    uint8_t* W8;        // [Npad_max][Kpad] E4M3 weight rows, zero padded
     // coverage / weights / pooling
     int32_t* cov;       // [MM][P]
     int32_t* npix;      // [MM]
@@ -210,6 +219,11 @@ struct BatchScratch {
         s.Dp += f * sP;
         s.cosg += f * sP;
         s.fnorm += f * sP;
+        s.qexp += f * sP;
+        s.qerr += f * sP;
+        s.qnrm += f * sP;
+        s.qexpm += f * sMM;
+        s.W8 += f * sW;
         s.cov += f * sMMP;
         s.npix += f * sMM;
         s.W += f * sW;
@@ -335,5 +349,55 @@ __device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v,
                          fp.t[r]);
 }
 
+// ---- E4M3 (OCP FP8: 4 exponent bits, 3 mantissa bits, largest finite 448) ----
+// Power-of-two scales keep the scaling itself exact: a vector with largest
+// magnitude mx is stored as x / 2^e with e the least integer such that
+// mx <= 448 * 2^e, so the conversion rounds once (to nearest even, finite).
+__device__ __forceinline__ int e4m3_exp(float mx)
+{
+    if (!(mx > 0.0f) || !(mx <= 3.0e38f)) return 0;
+    int e = ilogbf(mx) - 8;  // 448 = 1.75 * 2^8
+    for (int i = 0; i < 4 && mx > ldexpf(448.0f, e); i++) e++;
+    for (int i = 0; i < 4 && mx <= ldexpf(448.0f, e - 1); i++) e--;
+    return e;
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float x)
+{
+    return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+__device__ __forceinline__ float from_e4m3(uint8_t q)
+{
+    __nv_fp8_e4m3 v;
+    v.__x = (__nv_fp8_storage_t)q;
+    return (float)v;
+}
+
+// One warp writes the E4M3 scoring copy q = rn(x / 2^e) of an embedding row
+// and a bound of its relative error ||2^e q - x|| / ||x||, taken from the
+// actual residue (fp32 sums widened by 1 + 2^-9).  All 32 lanes call.
+__device__ __forceinline__ void e4m3_copy_row(const float* x, int D, uint8_t* q8, float* er)
+{
+    const int lane = threadIdx.x & 31;
+    float mx = 0.0f;
+    for (int d = lane; d < D; d += 32) mx = fmaxf(mx, fabsf(x[d]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = e4m3_exp(mx);
+    float se = 0.0f, sn = 0.0f;
+    for (int d = lane; d < D; d += 32) {
+        const float v = x[d];
+        const uint8_t q = to_e4m3(ldexpf(v, -e));
+        q8[d] = q;
+        const float r = __fsub_rn(ldexpf(from_e4m3(q), e), v);
+        se = __fadd_rn(se, __fmul_rn(r, r));
+        sn = __fadd_rn(sn, __fmul_rn(v, v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        se = __fadd_rn(se, __shfl_xor_sync(0xffffffffu, se, o));
+        sn = __fadd_rn(sn, __shfl_xor_sync(0xffffffffu, sn, o));
+    }
+    if (lane == 0) *er = sn > 0.0f ? __fmul_rn(__fdiv_rn(sqrtf(se), sqrtf(sn)), 1.0f + 0x1p-9f) : 0.0f;
+}
 
 }  // namespace disc

@@ -79,16 +79,40 @@ __global__ void k_tok_rows(const FrameParams* fps, BatchScratch bs)
     const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (p >= fp.P || sc.ctr->err) return;
     long long ss = 0, dg = 0, ff = 0;
+    float mx = 0.0f;
     for (int d = lane; d < fp.D; d += 32) {
         float f = tok<T>(F, (size_t)p * fp.D + d);
         float r = __fsub_rn(f, sc.fbar[d]);
         ss += fix32f(__fmul_rn(r, r), S_SQ);
         dg += fix32f(__fmul_rn(f, sc.gvec[d]), S_SQ);
         ff += fix32f(__fmul_rn(f, f), S_SQ);
+        mx = fmaxf(mx, fabsf(f));
     }
     ss = warp_sum(ss);
     dg = warp_sum(dg);
     ff = warp_sum(ff);
+    if (fp.precision == DISC_FP8_E4M3) {
+        // the token's E4M3 operand q_p = rn(f_p / 2^e) and, from its actual
+        // residue, bounds of ||2^e q_p - f_p|| and ||q_p||; fp32 sums of at
+        // most D/32 + 5 levels stay within (1 + 2^-10) of the exact values
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int e = e4m3_exp(mx);
+        float se = 0.0f, sn = 0.0f;
+        for (int d = lane; d < fp.D; d += 32) {
+            const float f = tok<T>(F, (size_t)p * fp.D + d);
+            const float q = from_e4m3(to_e4m3(ldexpf(f, -e)));
+            const float r = __fsub_rn(ldexpf(q, e), f);
+            se = __fadd_rn(se, __fmul_rn(r, r));
+            sn = __fadd_rn(sn, __fmul_rn(q, q));
+        }
+        se = warp_sum(se);
+        sn = warp_sum(sn);
+        if (lane == 0) {
+            sc.qexp[p] = e;
+            sc.qerr[p] = __fmul_rn(sqrtf(se), 1.0f + 0x1p-10f);
+            sc.qnrm[p] = __fmul_rn(sqrtf(sn), 1.0f + 0x1p-10f);
+        }
+    }
     if (lane == 0) {
         float n = __double2float_rn(__dsqrt_rn(unfix(ss, S_SQ)));
         sc.nrm[p] = n;
@@ -163,6 +187,54 @@ __device__ __forceinline__ T block_sum(T v, T* red)
     return s;
 }
 
+__device__ __forceinline__ float block_max(float v, float* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    float s = 0.0f;
+    for (int i = 0; i < nw; i++) s = fmaxf(s, red[i]);
+    __syncthreads();
+    return s;
+}
+
+// FP8 precision: the weight row of mask m as E4M3 operands and the bound of
+// the pooled embedding the tensor cores form from them.  Token p enters the
+// GEMM as q_p = rn(f_p / 2^a_p), so its weight is scaled to w'_p = 2^a_p w_p
+// (exact) and the row stored as r_p = rn(w'_p / 2^b); the GEMM returns
+// 2^b sum_p r_p q_p.  Against e = sum_p w_p f_p its error is at most
+//   sum_p |2^b r_p - w'_p| ||q_p||       (weight rounding)
+// + sum_p w_p ||2^a_p q_p - f_p||         (token rounding)
+// + g 2^b sum_p r_p ||q_p||               (accumulation)
+// with g = (Kpad/32 + 2) 2^-12: an allowance of 12 bits per addition of a
+// 32-deep MMA step into the accumulator, well below fp32's own rounding.
+// The sum is taken in fp32 and widened by (1 + 2^-10).  Returns the bound.
+__device__ float fp8_weights(const FrameParams& fp, const Scratch& sc, int m, const float* w, uint8_t* w8,
+                             float* red)
+{
+    float mx = 0.0f;
+    for (int p = threadIdx.x; p < fp.P; p += blockDim.x) mx = fmaxf(mx, ldexpf(w[p], sc.qexp[p]));
+    mx = block_max(mx, red);
+    const int b = e4m3_exp(mx);
+    float g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
+    for (int p = threadIdx.x; p < fp.P; p += blockDim.x) {
+        const float ws = ldexpf(w[p], sc.qexp[p]);
+        const uint8_t q = to_e4m3(ldexpf(ws, -b));
+        w8[p] = q;
+        const float r = from_e4m3(q);
+        g1 = __fadd_rn(g1, __fmul_rn(fabsf(__fsub_rn(ldexpf(r, b), ws)), sc.qnrm[p]));
+        g2 = __fadd_rn(g2, __fmul_rn(w[p], sc.qerr[p]));
+        g3 = __fadd_rn(g3, __fmul_rn(r, sc.qnrm[p]));
+    }
+    g1 = block_sum(g1, red);
+    g2 = block_sum(g2, red);
+    g3 = block_sum(g3, red);
+    if (threadIdx.x == 0) sc.qexpm[m] = b;
+    const float gam = ldexpf((float)(fp.Kpad / 32 + 2), -12);
+    return __fmul_rn(__fadd_rn(__fadd_rn(g1, g2), __fmul_rn(gam, ldexpf(g3, b))), 1.0f + 0x1p-10f);
+}
+
 // ---- pooling weights and the image-based quality terms (one block per mask) ---
 // a_p = c_p * D_p;  w_p = a_p / sum a  (sum a == 0: w_p = c_p / |M|);
 // S_size = min(lambda |M| / (H W), 1);  S_dist = 0.5 + 0.5 * sum a / |M|;
@@ -179,8 +251,13 @@ __global__ void k_weights(const FrameParams* fps, BatchScratch bs)
     float* w = sc.W + (size_t)m * fp.Kpad;
     float* S = sc.S + 5 * m;
     const int32_t* c = sc.cov + (size_t)m * fp.P;
+    const bool fp8 = fp.precision == DISC_FP8_E4M3;
+    uint8_t* w8 = sc.W8 + (size_t)m * fp.Kpad;
     if (npix < fp.min_px) {
-        for (int p = threadIdx.x; p < fp.P; p += blockDim.x) w[p] = 0.0f;
+        for (int p = threadIdx.x; p < fp.P; p += blockDim.x) {
+            w[p] = 0.0f;
+            if (fp8) w8[p] = 0;
+        }
         if (threadIdx.x < 5) S[threadIdx.x] = 0.0f;
         if (threadIdx.x == 0) sc.Bm[m] = 0.0f;
         return;
@@ -203,6 +280,7 @@ __global__ void k_weights(const FrameParams* fps, BatchScratch bs)
         bsum += wp * sc.fnorm[p];
     }
     bsum = block_sum(bsum, red_f);
+    if (fp8) bsum = fp8_weights(fp, sc, m, w, w8, red_f);
     if (threadIdx.x == 0) {
         sc.Bm[m] = bsum;
         S[0] = fminf(__fdiv_rn(__fmul_rn(fp.lambda_size, (float)npix), (float)(fp.H * fp.W)), 1.0f);

@@ -201,8 +201,12 @@ __global__ void k_fin_fuse(Instances inst, int nid, int D, FinalizeScratch fs)
         for (int d = lane; d < D; d += 32) {
             inst.E[(size_t)c * D + d] = inst.E[(size_t)w * D + d];
             if (inst.Eb) inst.Eb[(size_t)c * D + d] = inst.Eb[(size_t)w * D + d];
+            if (inst.E8) inst.E8[(size_t)c * D + d] = inst.E8[(size_t)w * D + d];
         }
-        if (lane == 0) inst.Q[c] = inst.Q[w];
+        if (lane == 0) {
+            inst.Q[c] = inst.Q[w];
+            if (inst.Er) inst.Er[c] = inst.Er[w];
+        }
     }
 }
 

@@ -12,6 +12,10 @@
 // TMEM, which keeps the fp32-level accuracy of the product (relative error
 // ~1e-6).  BF16 precision: both operands rounded to bf16 (tokens given in
 // bf16 are exact), one kind::f16 MMA per 16-wide K step, fp32 accumulation.
+// FP8 precision: E4M3 operands with power-of-two scales, token p as
+// rn(f_p / 2^a_p) and the weight rows prepared by the weights kernel, one
+// kind::f8f6f4 MMA per 32-wide K step; the epilogue multiplies column m by
+// its row scale 2^b_m.
 //
 // One CTA = one 128-row tile of D; one elected thread issues the MMAs; a
 // two-stage shared-memory ring is recycled through mbarriers that
@@ -78,6 +82,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Instruction descriptor of kind::f8f6f4 with E4M3 A/B: D fp32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N)
+{
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ uint32_t pack_e4m3(float a, float b, float c, float d)
+{
+    return (uint32_t)to_e4m3(a) | ((uint32_t)to_e4m3(b) << 8) | ((uint32_t)to_e4m3(c) << 16) |
+           ((uint32_t)to_e4m3(d) << 24);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
@@ -125,8 +149,8 @@ __device__ __forceinline__ float ldtok<__nv_bfloat16>(const __nv_bfloat16* F, si
 
 }  // namespace
 
-constexpr uint32_t A_TILE_BYTES = GEMM_MT * GEMM_KC * 4;  // 16 KB (tf32); bf16 tiles take half
-constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 16-byte K group (4 tf32 / 8 bf16)
+constexpr uint32_t A_TILE_BYTES = GEMM_MT * GEMM_KC * 4;  // 16 KB (tf32); bf16 tiles take half, e4m3 a quarter
+constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 16-byte K group (4 tf32 / 8 bf16 / 16 e4m3)
 
 // two pipeline stages + barriers; the trailing guard keeps every address an
 // MMA descriptor of this kernel can form inside the allocation
@@ -138,7 +162,8 @@ __host__ size_t gemm_smem_bytes(int NT)
     return std::min(base + GEMM_SMEM_GUARD, std::max(base, SMEM_MAX));
 }
 
-template <typename T, bool BF>
+// PR: the disc_precision of the frames this instance serves
+template <typename T, int PR>
 __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -150,15 +175,15 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     const int d0 = blockIdx.x * GEMM_MT;
     // uniform for the block: other dtype or precision, no masks, tile past D,
     // failed frame
-    if (fp.token_bf16 != (sizeof(T) == 2) || (fp.precision == DISC_BF16) != BF || M <= 0 || d0 >= D ||
-        sc.ctr->err)
-        return;
+    if (fp.token_bf16 != (sizeof(T) == 2) || fp.precision != PR || M <= 0 || d0 >= D || sc.ctr->err) return;
 
-    // per stage: tf32 A hi | A lo | B hi | B lo, or bf16 A | B
-    const uint32_t A_BYTES = BF ? A_TILE_BYTES / 2 : A_TILE_BYTES;
-    const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * (BF ? 2 : 4);
+    // per stage: tf32 A hi | A lo | B hi | B lo, or bf16 / e4m3 A | B
+    constexpr bool BF = PR == DISC_BF16, F8 = PR == DISC_FP8_E4M3;
+    constexpr uint32_t EB = F8 ? 1 : (BF ? 2 : 4);  // operand bytes
+    const uint32_t A_BYTES = A_TILE_BYTES / 4 * EB;
+    const uint32_t B_TILE_BYTES = (uint32_t)NT * GEMM_KC * EB;
     const uint32_t B_LBO = (uint32_t)NT * 16;
-    const uint32_t STAGE = BF ? A_BYTES + B_TILE_BYTES : 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
+    const uint32_t STAGE = (BF || F8) ? A_BYTES + B_TILE_BYTES : 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
     uint64_t* mbar = (uint64_t*)(smem + 2 * STAGE);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 2);
     uint32_t ncols = 32;
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = BF ? idesc_bf16(GEMM_MT, NT) : idesc_tf32(GEMM_MT, NT);
+    const uint32_t idesc = F8 ? idesc_e4m3(GEMM_MT, NT) : (BF ? idesc_bf16(GEMM_MT, NT) : idesc_tf32(GEMM_MT, NT));
     const int nchunks = (P + GEMM_KC - 1) / GEMM_KC;
     bool failed = false;
     int last_commit = -1;  // chunk of the most recent commit (same on all threads)
@@ -193,7 +218,33 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
             if (__syncthreads_or(!ok)) { failed = true; break; }
         }
         const int p0 = c * GEMM_KC;
-        if constexpr (BF) {
+        if constexpr (F8) {
+            // A: F^T tile in e4m3, thread tid owns row d0 + tid, 16 patches per 16 B
+            {
+                const int d = d0 + tid;
+#pragma unroll
+                for (int kq = 0; kq < GEMM_KC / 16; kq++) {
+                    float x[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int p = p0 + 16 * kq + j;
+                        x[j] = (d < D && p < P) ? ldexpf(ldtok<T>(F, (size_t)p * D + d), -sc.qexp[p]) : 0.0f;
+                    }
+                    const uint4 v = make_uint4(pack_e4m3(x[0], x[1], x[2], x[3]), pack_e4m3(x[4], x[5], x[6], x[7]),
+                                               pack_e4m3(x[8], x[9], x[10], x[11]),
+                                               pack_e4m3(x[12], x[13], x[14], x[15]));
+                    *(uint4*)(st + kq * A_LBO + tid * 16) = v;
+                }
+            }
+            // B: the e4m3 weight rows, NT rows x 32 patches
+            {
+                uint8_t* Bt = st + A_BYTES;
+                for (int g = tid; g < NT * (GEMM_KC / 16); g += 128) {
+                    const int n = g >> 1, kq = g & 1;
+                    *(uint4*)(Bt + kq * B_LBO + n * 16) = *(const uint4*)(sc.W8 + (size_t)n * fp.Kpad + p0 + 16 * kq);
+                }
+            }
+        } else if constexpr (BF) {
             // A: F^T tile in bf16, thread tid owns row d0 + tid, 8 patches per 16 B
             {
                 const int d = d0 + tid;
@@ -269,7 +320,11 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         __syncthreads();
         if (tid == 0) {
             fence_after();
-            if constexpr (BF) {
+            if constexpr (F8) {
+                // one K step of 32 = two 16-byte core-matrix columns of e4m3
+                const uint32_t a0 = smem_u32(st), b0 = a0 + A_BYTES;
+                mma_e4m3(tmem, smem_desc(a0, A_LBO, 128), smem_desc(b0, B_LBO, 128), idesc, c > 0 ? 1u : 0u);
+            } else if constexpr (BF) {
                 // K step 16 = two 16-byte core-matrix columns of bf16
                 const uint32_t a0 = smem_u32(st), b0 = a0 + A_BYTES;
 #pragma unroll
@@ -318,7 +373,11 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 const int m = c0 + j;
-                if (m < M && d < D) sc.Efast[(size_t)m * D + d] = __uint_as_float(r[j]);
+                if (m < M && d < D) {
+                    float v = __uint_as_float(r[j]);
+                    if constexpr (F8) v = ldexpf(v, sc.qexpm[m]);
+                    sc.Efast[(size_t)m * D + d] = v;
+                }
             }
         }
     } else if (failed) {
@@ -333,7 +392,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][2],
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][3],
                      cudaStream_t st)
 {
     if (Mmax <= 0) return 0;
@@ -341,23 +400,30 @@ int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int 
     const size_t smem = gemm_smem_bytes(NT);
     dim3 g((D + GEMM_MT - 1) / GEMM_MT, B);
     int n = 0;
-    if (any[0][0]) { k_pool_gemm<float, false><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
-    if (any[1][0]) { k_pool_gemm<__nv_bfloat16, false><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
-    if (any[0][1]) { k_pool_gemm<float, true><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
-    if (any[1][1]) { k_pool_gemm<__nv_bfloat16, true><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][0]) { k_pool_gemm<float, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][0]) { k_pool_gemm<__nv_bfloat16, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][1]) { k_pool_gemm<float, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][1]) { k_pool_gemm<__nv_bfloat16, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][2]) { k_pool_gemm<float, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][2]) { k_pool_gemm<__nv_bfloat16, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
     return n;
+}
+
+template <typename T, int PR>
+static cudaError_t gemm_attr(int mx)
+{
+    return cudaFuncSetAttribute(k_pool_gemm<T, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 cudaError_t set_gemm_kernel_attrs()
 {
     const int mx = (int)gemm_smem_bytes(MAX_MASKS);
-    cudaError_t e = cudaFuncSetAttribute(k_pool_gemm<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pool_gemm<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pool_gemm<__nv_bfloat16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaError_t e = gemm_attr<float, DISC_FP32>(mx);
+    if (e == cudaSuccess) e = gemm_attr<__nv_bfloat16, DISC_FP32>(mx);
+    if (e == cudaSuccess) e = gemm_attr<float, DISC_BF16>(mx);
+    if (e == cudaSuccess) e = gemm_attr<__nv_bfloat16, DISC_BF16>(mx);
+    if (e == cudaSuccess) e = gemm_attr<float, DISC_FP8_E4M3>(mx);
+    if (e == cudaSuccess) e = gemm_attr<__nv_bfloat16, DISC_FP8_E4M3>(mx);
     return e;
 }
 

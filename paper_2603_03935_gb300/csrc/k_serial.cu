@@ -150,7 +150,8 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
 
 // ---- gates per (segment, instance) pair: one warp per pair -----------------------
 // The fast cosine takes the tensor-core pooled embedding and the instance's
-// scoring copy (fp32, or bf16 at BF16 precision); inside its error band the
+// scoring copy (fp32, bf16 at BF16 precision, E4M3 at FP8 precision: the
+// copy's power-of-two scale cancels in the cosine); inside its error band the
 // pair is re-scored exactly.
 __device__ __forceinline__ unsigned bf16_pair(float lo, float hi)
 {
@@ -203,6 +204,14 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
                     nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
                 }
             }
+        } else if (inst.E8) {
+            const uint8_t* b8 = inst.E8 + (size_t)k * D;
+            for (int d = lane; d < D; d += 32) {
+                const float x = a[d], y = from_e4m3(b8[d]);
+                dt += x * y;
+                na += x * x;
+                nb += y * y;
+            }
         } else if (inst.Eb) {
             const uint16_t* bb = inst.Eb + (size_t)k * D;
             for (int d = lane; d < D; d += 32) {
@@ -244,7 +253,10 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
         nb = warp_sum(nb);
         bool edge;
         const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
-        const float band = (na > 0.0f) ? 2.2f * fp.eta * sc.Bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
+        // |cos(a, b') - cos(e, b)| <= 2 |a - e| / |a| + 2 |b' - b| / |b|, plus
+        // the fp32 arithmetic of cf; 10 % slack on the bounds
+        float band = (na > 0.0f) ? 2.2f * fp.eta * sc.Bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
+        if (inst.Er) band += 2.2f * inst.Er[k];
         if (fabsf(cf - fp.tau) > band) {
             edge = cf >= fp.tau;
         } else {
@@ -538,6 +550,7 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Seri
             const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
             float* to = inst.E + (size_t)ss.copy_dst[c] * D;
             uint16_t* tb = inst.Eb ? inst.Eb + (size_t)ss.copy_dst[c] * D : nullptr;  // bf16 scoring copy
+            if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)ss.copy_dst[c] * D, inst.Er + ss.copy_dst[c]);
             if ((D & 3) == 0) {
                 const float4* f4 = (const float4*)from;
                 float4* t4 = (float4*)to;
@@ -685,6 +698,21 @@ __global__ void k_serial_begin(const MapRefs* refs, int G)
 }
 
 // ---- host launcher ----------------------------------------------------------------
+// E4M3 scoring copies of instances [0, n) from their stored embeddings (one
+// warp per instance), as the apply phase writes them
+__global__ void k_e4m3_copies(Instances inst, int n, int D)
+{
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += (gridDim.x * blockDim.x) >> 5)
+        e4m3_copy_row(inst.E + (size_t)k * D, D, inst.E8 + (size_t)k * D, inst.Er + k);
+}
+
+int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st)
+{
+    if (n <= 0 || !inst.E8) return 0;
+    k_e4m3_copies<<<std::min((n + 7) / 8, 1216), 256, 0, st>>>(inst, n, D);
+    return 1;
+}
+
 int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st)
 {
     k_serial_begin<<<(G + 127) / 128, 128, 0, st>>>(refs, G);

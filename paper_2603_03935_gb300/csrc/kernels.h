@@ -43,7 +43,7 @@ int launch_weights(const FrameParams* fps, const BatchScratch& bs, int B, int Mm
 int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, int Mmax, bool any_bf16,
                       bool any_f32, cudaStream_t st);
 // one launch per (token dtype, precision) present: any[tok_bf16][prec_bf16]
-int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][2],
+int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][3],
                      cudaStream_t st);
 // back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
 // batch start) on frames [f0, f0 + nb); then Q of every segment
@@ -57,6 +57,7 @@ int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaSt
 constexpr int GEOMETRY_CHUNK = 4;
 
 // start of a batch's serial part: every map's edge and copy counters to zero
+int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st);
 int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st);
 // serial part, step st.j over the G maps of a batch: phase 0 overlap,
 // 1 score, 2 union, 3 apply

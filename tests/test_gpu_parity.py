@@ -378,6 +378,122 @@ def test_bf16_precision_checkpoint_and_mixed_group(torch_dev, tmp_path):
         assert np.array_equal(ex["E"].view(np.uint32), ey["E"].view(np.uint32)), ctx
 
 
+# FP8 precision: E4M3 operands with power-of-two per-vector scales (per
+# token, per weight row, per stored embedding) and fp32 accumulation.  The
+# weights kernel bounds |E_fast - e| per mask from the actual rounding
+# residues; the test checks that bound against e = sum_p w_p f_p taken in
+# fp64, checks a looser a-priori bound that follows from the format alone
+# (3 mantissa bits: relative rounding 2^-4, subnormal step 2^-9 of the
+# scale), and states the error against the fp64 pooling twin.
+def _fp8_apriori(n_patches, D, K):
+    sub = 2.0 ** -10 * n_patches * np.sqrt(D) / 112.0  # weight rows' subnormal rounding
+    tok = 2.0 ** -4 + np.sqrt(D) * 2.0 ** -10 / 224.0  # token rounding, relative to ||f_p||
+    acc = (K / 32 + 2) * 2.0 ** -12
+    return ((1 + tok) * (2.0 ** -4 + sub) + tok + 2 * acc) * 1.01
+
+
+def _fp8_fast_error(rep, tokens, scene):
+    F = tokens.astype(np.float64)
+    _, E64 = oracle.pool_f64(tokens, rep["cov"], rep["npix"])
+    K = (scene.patch_h * scene.patch_w + 31) // 32 * 32
+    worst, tight = 0.0, []
+    for m in range(len(rep["npix"])):
+        if rep["npix"][m] < 1 or not np.any(rep["W"][m]):
+            continue
+        w = rep["W"][m].astype(np.float64)
+        e = w @ F  # sum_p w_p f_p with the frame's fp32 weights, in fp64
+        err = float(np.linalg.norm(rep["E_fast"][m].astype(np.float64) - e))
+        bound = float(rep["E_bound"][m])
+        assert err <= bound, f"mask {m}: |E_fast - e| = {err} > device bound {bound}"
+        bsum = float(np.sum(w * np.linalg.norm(F, axis=1)))
+        apri = _fp8_apriori(int(np.count_nonzero(w)), F.shape[1], K) * bsum
+        assert bound <= apri, f"mask {m}: device bound {bound} above the a-priori bound {apri}"
+        tight.append(bound / apri)
+        worst = max(worst, float(np.linalg.norm(rep["E_fast"][m] - E64[m])) / max(float(np.linalg.norm(E64[m])), 1e-30))
+    return worst, tight
+
+
+def test_fp8_precision_parity_and_fp64_error(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(20))
+    cfg = common.disc_cfg(sc, precision=2)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    worst, tight, border = 0.0, [], 0
+    for i in range(len(fr)):
+        st = gmap.integrate(_dframe(torch, dev, fr, i))
+        o = omap.integrate(*oracle.frame_args(fr, i))
+        rep = gmap.last_frame()
+        common.compare_frame(st, rep, o, ctx=f"fp8 precision frame {i}", efast_tol=0.15)
+        w, t = _fp8_fast_error(rep, fr.tokens[i], sc)
+        worst, tight, border = max(worst, w), tight + t, border + st["borderline_rescored"]
+    common.compare_maps(gmap, omap, ctx="fp8 precision")
+    inst = gmap.instances()
+    ea = omap.instances()["E"]
+    assert np.array_equal(inst["E"].view(np.uint32), ea.view(np.uint32))
+    # E4M3 keeps 3 mantissa bits: a few percent against fp64, and the
+    # device's residue-based bound well inside the format's worst case
+    assert 1e-3 < worst < 0.1, worst
+    assert max(tight) < 0.8, max(tight)
+
+
+def test_fp8_precision_borderline_rescored(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(3))
+    probe = oracle.OracleMap(**oracle.config_for_scene(sc))
+    probe.integrate(*oracle.frame_args(fr, 0))
+    E0 = probe.instances()["E"]
+    r1 = probe.integrate(*oracle.frame_args(fr, 1))
+    m = int(np.argmax(r1["nvox"]))
+    k = int(r1["rep"][m]) if r1["rep"][m] < len(E0) else 0
+    tau = oracle.cosine(r1["E"][m], E0[k])
+    for t in (tau, np.nextafter(np.float32(tau), np.float32(2)), np.nextafter(np.float32(tau), np.float32(0))):
+        cfg = common.disc_cfg(sc, tau_cos=float(t), precision=2)
+        gmap = DiscMap(**cfg)
+        omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+        border = 0
+        for i in range(3):
+            st = gmap.integrate(_dframe(torch, dev, fr, i))
+            o = omap.integrate(*oracle.frame_args(fr, i))
+            common.compare_frame(st, gmap.last_frame(), o, ctx=f"fp8 tau={t} frame {i}", efast_tol=0.15)
+            border += st["borderline_rescored"]
+        common.compare_maps(gmap, omap, ctx=f"fp8 tau={t}")
+        assert border >= 1
+
+
+def test_fp8_precision_checkpoint_and_mixed_group(torch_dev, tmp_path):
+    # fp32, bf16 and fp8 maps side by side in one group give one and the same
+    # map; an fp8 checkpoint reloads with rebuilt E4M3 scoring copies
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(12))
+    frames = [_dframe(torch, dev, fr, i) for i in range(12)]
+    maps = [DiscMap(**common.disc_cfg(sc, precision=p)) for p in (0, 1, 2)]
+    grp = DiscGroup(max_maps=3, frames_per_map=4, embed_dim=sc.dim, patch_h=sc.patch_h, patch_w=sc.patch_w,
+                    max_width=sc.width, max_height=sc.height, max_masks=sc.max_masks)
+    _, done, rc = grp.integrate(maps, [frames[:6]] * 3)
+    assert rc == 0 and done == [6, 6, 6]
+    maps[2].save(tmp_path / "m8.disc")
+    b8 = DiscMap.load(tmp_path / "m8.disc")
+    _, done, rc = grp.integrate(maps[:2] + [b8], [frames[6:]] * 3)
+    assert rc == 0
+    _, _, rc1 = maps[2].integrate_frames(frames[6:])
+    assert rc1 == 0
+    for y, ctx in ((maps[1], "bf16"), (b8, "fp8 reloaded in a group"), (maps[2], "fp8 alone")):
+        kx, ix = maps[0].voxels()
+        ky, iy = y.voxels()
+        assert np.array_equal(kx, ky) and np.array_equal(ix, iy), ctx
+        ex, ey = maps[0].instances(), y.instances()
+        for k in ("parent", "count", "n_obs"):
+            assert np.array_equal(ex[k], ey[k]), (ctx, k)
+        assert np.array_equal(ex["E"].view(np.uint32), ey["E"].view(np.uint32)), ctx
+
+
 def test_multistory_bf16_parity(torch_dev):
     # the multi-story building: up to 100 masks, 5 cm voxels, depth to 20 m,
     # bf16 tokens at BF16 precision, a voxel table of 2^27 slots; consecutive
