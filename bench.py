@@ -643,11 +643,31 @@ def main():
             e1.synchronize()
             assert rc == 0, rc
             et.append(e0.elapsed_time(e1))
+        # the same K steps as one call (a trajectory handed over at once): the
+        # copies of batch b + 1 overlap the kernels of batch b
         m2.close()
+        m3 = DiscMap(**cfg)
+        for s in range(Wm):
+            assert m3.integrate_frames_raw(hsteps[s], B, stats) == 0
+        allf = frame_array(Wm * B, (Wm + K) * B, on_device=False, host=(hd, hl, ht))
+        allst = (binding.Stats * (K * B))()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = m3.integrate_frames_raw(allf, K * B, allst)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        traj_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        m3.close()
         e2e_ms = max_over_ranks(float(np.sum(et)), world, dev)
         e2e = {"value": whole_job_rate(K * B, world, e2e_ms), "unit": "frames/s",
                "h2d_bytes_per_step": B * (H * W_ * 6 + P * D * 4),
-               "d2h_bytes_per_step": B * 64}
+               "d2h_bytes_per_step": B * 64,
+               "calls": "one disc_integrate_frames call per step (32 frames), host buffers, synchronous",
+               "one_call_trajectory": {"value": whole_job_rate(K * B, world, traj_ms), "unit": "frames/s",
+                                       "frames": K * B}}
 
     if rank == 0:
         cpu = cpu_baseline(scene, fr, args.cpu_seconds) if world == 1 else None

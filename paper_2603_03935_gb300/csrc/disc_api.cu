@@ -100,7 +100,13 @@ struct Runner {
     int cur = 0;                                        // set of the next batch
     FrameCounters* d_hist = nullptr;  // [hist_cap] per-frame counters of one call
     int hist_cap = 0;
-    float* d_depth = nullptr;         // staging of host inputs, one slot per frame of a batch
+    cudaStream_t stream_in = nullptr; // host-to-device copies of host inputs
+    unsigned long long* d_room = nullptr;  // [2 Gmax] per map of a batch: voxel count, pairs of its frames
+    unsigned long long* h_room = nullptr;  // pinned copy of d_room
+    cudaEvent_t ev_room = nullptr;
+    cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {};  // staging set k filled / read by its last batch
+    float* d_depth = nullptr;         // staging of host inputs: two sets (one per scratch set) of one
+                                      // slot per frame of a batch
     uint16_t* d_labels = nullptr;
     unsigned char* d_tokens = nullptr;
     float* d_gembed = nullptr;
@@ -354,10 +360,11 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         sc.smask = scap - 1;
         sc.ctr = a.get<FrameCounters>(B);
     }
-    r.d_depth = a.get<float>((size_t)B * npx);
-    r.d_labels = a.get<uint16_t>((size_t)B * npx);
-    r.d_tokens = a.get<unsigned char>((size_t)B * P * D * 4);
-    r.d_gembed = a.get<float>((size_t)B * D);
+    r.d_depth = a.get<float>((size_t)2 * B * npx);
+    r.d_labels = a.get<uint16_t>((size_t)2 * B * npx);
+    r.d_tokens = a.get<unsigned char>((size_t)2 * B * P * D * 4);
+    r.d_gembed = a.get<float>((size_t)2 * B * D);
+    r.d_room = a.get<unsigned long long>((size_t)2 * Gmax);
     if (a.failed) return DISC_ERR_OOM;
     // Pipelined batches put the serial part (a latency-bound chain of small
     // launches) on its own partition of serial_sms SMs and the stateless part
@@ -371,7 +378,12 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         CK(cudaStreamCreateWithPriority(&r.stream3, cudaStreamNonBlocking, prio_hi));
     }
     CK(cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&r.stream_in, cudaStreamNonBlocking));
+    CK(cudaHostAlloc(&r.h_room, sizeof(unsigned long long) * 2 * Gmax, cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&r.ev_room, cudaEventDisableTiming));
     for (int k = 0; k < 2; k++) {
+        CK(cudaEventCreateWithFlags(&r.ev_in_ready[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.ev_in_free[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_state[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_serial[k], cudaEventDisableTiming));
     }
@@ -395,7 +407,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
 void runner_release(Runner& r)
 {
     cudaStreamSynchronize(r.stream);
-    for (cudaStream_t* sp : {&r.stream2, &r.stream3}) {
+    for (cudaStream_t* sp : {&r.stream2, &r.stream3, &r.stream_in}) {
         if (*sp) {
             cudaStreamSynchronize(*sp);
             cudaStreamDestroy(*sp);
@@ -404,6 +416,10 @@ void runner_release(Runner& r)
     }
     if (r.ev_join) cudaEventDestroy(r.ev_join);
     r.ev_join = nullptr;
+    if (r.ev_room) cudaEventDestroy(r.ev_room);
+    r.ev_room = nullptr;
+    if (r.h_room) cudaFreeHost(r.h_room);
+    r.h_room = nullptr;
     for (int i = 0; i < 2; i++) {
         if (r.green[i]) green_api().destroy(r.green[i]);
         r.green[i] = nullptr;
@@ -411,7 +427,9 @@ void runner_release(Runner& r)
     for (int k = 0; k < 2; k++) {
         if (r.ev_state[k]) cudaEventDestroy(r.ev_state[k]);
         if (r.ev_serial[k]) cudaEventDestroy(r.ev_serial[k]);
-        r.ev_state[k] = r.ev_serial[k] = nullptr;
+        if (r.ev_in_ready[k]) cudaEventDestroy(r.ev_in_ready[k]);
+        if (r.ev_in_free[k]) cudaEventDestroy(r.ev_in_free[k]);
+        r.ev_state[k] = r.ev_serial[k] = r.ev_in_ready[k] = r.ev_in_free[k] = nullptr;
     }
     for (cudaEvent_t e : r.ev_pool) cudaEventDestroy(e);
     r.ev_pool.clear();
@@ -544,17 +562,13 @@ uint64_t read_used(disc_map* m, cudaStream_t st)
     return v;
 }
 
-// Grow the voxel table so that `incoming` more voxels keep the load below
-// max_load.  Uses a host bound first; synchronises `st` (the stream the map's
-// kernels run on) only when the bound is hit.
-disc_status ensure_voxel_room(disc_map* m, uint64_t incoming, cudaStream_t st)
+// Grow the voxel table (doubling) until `need` voxels keep the load at or
+// below max_load.  st is the stream the map's kernels run on; synchronises it
+// when the table grows.
+disc_status grow_voxel_table(disc_map* m, uint64_t need, cudaStream_t st)
 {
-    const double lim = (double)m->cfg.max_load * (double)(m->vt.mask + 1);
-    if ((double)(m->used_upper + incoming) <= lim) return DISC_OK;
-    CK(cudaStreamSynchronize(st));
-    m->used_upper = read_used(m, st);
     uint64_t cap = m->vt.mask + 1;
-    while ((double)(m->used_upper + incoming) > (double)m->cfg.max_load * (double)cap) cap <<= 1;
+    while ((double)need > (double)m->cfg.max_load * (double)cap) cap <<= 1;
     if (cap == m->vt.mask + 1) return DISC_OK;
     VoxelTable nt{};
     disc_status s = alloc_voxel_table(m, cap, &nt, st);
@@ -574,6 +588,18 @@ disc_status ensure_voxel_room(disc_map* m, uint64_t incoming, cudaStream_t st)
     m->mem.release(m->vt.labels, sizeof(int32_t) * old);
     m->vt = nt;
     return DISC_OK;
+}
+
+// Grow the voxel table so that `incoming` more voxels keep the load below
+// max_load, from a host bound (H * W per frame); synchronises `st` only when
+// the bound is hit.
+disc_status ensure_voxel_room(disc_map* m, uint64_t incoming, cudaStream_t st)
+{
+    const double lim = (double)m->cfg.max_load * (double)(m->vt.mask + 1);
+    if ((double)(m->used_upper + incoming) <= lim) return DISC_OK;
+    CK(cudaStreamSynchronize(st));
+    m->used_upper = read_used(m, st);
+    return grow_voxel_table(m, m->used_upper + incoming, st);
 }
 
 disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
@@ -917,8 +943,35 @@ void fast_error_terms(int precision, int Kpad, int D, float* eta, float* dot_err
     }
 }
 
-disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int slot, int g, FrameParams* out,
-                         cudaStream_t st)
+// Host-to-device copies of one batch's inputs, one list per input kind.
+// Copies whose sources and destinations both continue the previous copy of
+// the same kind (frames laid out back to back, as a trajectory in one host
+// array) merge into one larger copy.
+struct CopyList {
+    struct Item { char* dst; const char* src; size_t bytes; };
+    std::vector<Item> kind[4];
+    void add(int k, void* dst, const void* src, size_t bytes)
+    {
+        std::vector<Item>& v = kind[k];
+        if (!v.empty() && v.back().dst + v.back().bytes == (char*)dst && v.back().src + v.back().bytes == (const char*)src)
+            v.back().bytes += bytes;
+        else
+            v.push_back({(char*)dst, (const char*)src, bytes});
+    }
+    bool empty() const { return kind[0].empty() && kind[1].empty() && kind[2].empty() && kind[3].empty(); }
+    disc_status issue(cudaStream_t st)
+    {
+        for (auto& v : kind) {
+            for (const Item& it : v) CK(cudaMemcpyAsync(it.dst, it.src, it.bytes, cudaMemcpyHostToDevice, st));
+            v.clear();
+        }
+        return DISC_OK;
+    }
+};
+
+// Host inputs are staged in staging set `set` (copies collected in cl).
+disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int set, int slot, int g,
+                         FrameParams* out, CopyList* cl)
 {
     const int P = r.P, D = r.D;
     FrameParams fp{};
@@ -967,19 +1020,20 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
         fp.tokens = f->tokens;
         fp.gembed = f->global_embed;
     } else {
-        float* dd = r.d_depth + (size_t)slot * r.px_cap;
-        uint16_t* dl = r.d_labels + (size_t)slot * r.px_cap;
-        unsigned char* dt = r.d_tokens + (size_t)slot * P * D * 4;
-        CK(cudaMemcpyAsync(dd, f->depth, sizeof(float) * npx, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(dl, f->labels, sizeof(uint16_t) * npx, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(dt, f->tokens, tok_bytes, cudaMemcpyHostToDevice, st));
+        const size_t at = (size_t)set * r.S + slot;
+        float* dd = r.d_depth + at * r.px_cap;
+        uint16_t* dl = r.d_labels + at * r.px_cap;
+        unsigned char* dt = r.d_tokens + at * P * D * 4;
+        cl->add(0, dd, f->depth, sizeof(float) * npx);
+        cl->add(1, dl, f->labels, sizeof(uint16_t) * npx);
+        cl->add(2, dt, f->tokens, tok_bytes);
         fp.depth = dd;
         fp.labels = dl;
         fp.tokens = dt;
         fp.gembed = nullptr;
         if (f->global_embed) {
-            float* dg = r.d_gembed + (size_t)slot * D;
-            CK(cudaMemcpyAsync(dg, f->global_embed, sizeof(float) * D, cudaMemcpyHostToDevice, st));
+            float* dg = r.d_gembed + at * D;
+            cl->add(3, dg, f->global_embed, sizeof(float) * D);
             fp.gembed = dg;
         }
     }
@@ -1016,6 +1070,35 @@ struct Work {
     std::vector<int> hist_idx;        // counters of each enqueued frame in the call's history
 };
 
+// Between a batch's stateless and serial parts (on the serial stream, after
+// the stateless part): each map's exact voxel count and the unique (segment,
+// voxel) pairs of its frames, which bound the voxels the batch inserts, come
+// back to the host; a table that could pass max_load grows (rehash) before
+// the serial part, and the map's table pointers in the batch's parameter
+// block are refreshed.  Only this small read is waited for, so the input
+// copies of the next batch run while the serial part computes.
+disc_status room_check(Runner& r, int k, int G, int J, std::vector<Work>& w, const std::vector<int>& gl,
+                       MapRefs* hrefs, cudaStream_t sr)
+{
+    launch_room(r.refs(k), G, r.slot_of(k), J, r.bs[k], r.d_room, sr);
+    r.launches++;
+    CK(cudaMemcpyAsync(r.h_room, r.d_room, sizeof(unsigned long long) * 2 * G, cudaMemcpyDeviceToHost, sr));
+    CK(cudaEventRecord(r.ev_room, sr));
+    CK(cudaEventSynchronize(r.ev_room));
+    for (int gi = 0; gi < G; gi++) {
+        disc_map* m = w[gl[gi]].m;
+        const uint64_t need = r.h_room[2 * gi] + r.h_room[2 * gi + 1];
+        m->used_upper = need;  // the count after this batch is at most this
+        if ((double)need <= (double)m->cfg.max_load * (double)(m->vt.mask + 1)) continue;
+        disc_status s = grow_voxel_table(m, need, sr);
+        if (s != DISC_OK) return s;
+        hrefs[gi] = map_refs(m);
+        CK(cudaMemcpyAsync(r.d_param[k] + r.off_refs + sizeof(MapRefs) * gi, &hrefs[gi], sizeof(MapRefs),
+                           cudaMemcpyHostToDevice, sr));
+    }
+    return DISC_OK;
+}
+
 // Integrate every map's frames: batch b holds frames [b*J, (b+1)*J) of each
 // map; the maps of a batch run side by side, each map's frames in order.  A
 // frame that fails stops the later frames of its map (on the device), not
@@ -1040,13 +1123,17 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     const bool pipe = !r.timing && nbatch > 1 && r.serial_sms > 0;
     cudaStream_t sr = pipe ? r.stream3 : r.stream;  // serial part
     cudaStream_t ss = pipe ? r.stream2 : r.stream;  // stateless part
+    // the input copies (and, pipelined, both parts) start after the caller's
+    // earlier work on its stream
+    s = cuda_status(cudaEventRecord(r.ev_join, r.stream));
+    if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream_in, r.ev_join, 0));
     if (pipe) {
-        s = cuda_status(cudaEventRecord(r.ev_join, r.stream));
         if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream2, r.ev_join, 0));
         if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream3, r.ev_join, 0));
-        if (s != DISC_OK) return s;
     }
+    if (s != DISC_OK) return s;
     std::vector<unsigned char> blk(r.param_bytes);
+    const bool one_graph = r.timing && !r.graphs_off;
     int hoff = 0;
     for (int b = 0; b < nbatch && s == DISC_OK; b++) {
         const int lo = b * r.Jmax;
@@ -1074,7 +1161,9 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 combos |= 1 << (3 * (f.token_dtype == DISC_TOKENS_BF16) + wk.m->cfg.precision);
                 if (wk.m->cfg.dbscan_eps > 0.0f) combos |= COMBO_DBSCAN;
             }
-            s = ensure_voxel_room(wk.m, px, sr);
+            // one graph of both parts (phase timing): room from the host bound;
+            // otherwise from the device between the parts (room_check)
+            if (one_graph) s = ensure_voxel_room(wk.m, px, sr);
             if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, sr);
         }
         if (s != DISC_OK) break;
@@ -1091,6 +1180,11 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         int* hslot = (int*)(blk.data() + r.off_slot);
         int* hprev = (int*)(blk.data() + r.off_prev);
         int slot = 0;
+        CopyList cl;
+        // host inputs of this batch go to staging set k once the set's last
+        // batch has read its inputs (its stateless part), on the input
+        // stream, so they overlap the previous batch's kernels
+        s = cuda_status(cudaStreamWaitEvent(r.stream_in, r.ev_in_free[k], 0));
         for (int gi = 0; gi < G && s == DISC_OK; gi++) {
             Work& wk = w[gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
@@ -1098,11 +1192,17 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && s == DISC_OK; j++) {
-                s = frame_params(r, wk.m, wk.frames + lo + j, slot, gi, hfp + slot, ss);
+                s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, &cl);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
             }
+        }
+        const bool copied = !cl.empty();
+        if (s == DISC_OK && copied) {
+            s = cl.issue(r.stream_in);
+            if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_ready[k], r.stream_in));
+            if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_ready[k], 0));
         }
         if (s != DISC_OK) break;
         // pageable source: the call returns once the block is staged
@@ -1110,13 +1210,16 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (s != DISC_OK) break;
         if (r.timing && !r.graphs_off && launch_timed_graph(r, k, S, G, J, combos)) {
             // both parts with their phase events, one graph on the runner's stream
+            if (copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], r.stream));
         } else {
             s = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
                          [&] { return enqueue_stateless(r, k, S, combos, ss); });
+            if (s == DISC_OK && copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], ss));
             if (s == DISC_OK && pipe) {
                 s = cuda_status(cudaEventRecord(r.ev_state[k], ss));
                 if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(sr, r.ev_state[k], 0));
             }
+            if (s == DISC_OK && !one_graph) s = room_check(r, k, G, J, w, gl, hrefs, sr);
             if (s == DISC_OK)
                 s = run_part(r, graph_key(1, k, 0, G, J, 0), sr, [&] { return enqueue_serial(r, k, G, J, sr); });
         }
@@ -1131,7 +1234,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             const int cnt = std::min(r.Jmax, wk.valid - lo);
             for (int j = 0; j < cnt; j++) {
                 const disc_frame& f = wk.frames[lo + j];
-                wk.m->used_upper += (uint64_t)f.width * f.height;
+                if (one_graph) wk.m->used_upper += (uint64_t)f.width * f.height;
                 wk.m->next_id_upper += f.num_masks;
             }
         }
@@ -1156,6 +1259,9 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     disc_status s3 = cuda_status(cudaStreamSynchronize(r.stream));
     if (s == DISC_OK) s = s3;
     s3 = cuda_status(cudaStreamSynchronize(r.stream2));
+    if (s == DISC_OK) s = s3;
+    // no copy from the caller's host buffers outlives the call
+    s3 = cuda_status(cudaStreamSynchronize(r.stream_in));
     if (s == DISC_OK) s = s3;
     collect_timing(r);
     disc_status first = s;

@@ -713,6 +713,30 @@ int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st)
     return 1;
 }
 
+// Room check between a batch's two parts: per map of the batch, its voxel
+// count (after every earlier batch) and the unique (segment, voxel) pairs of
+// its frames in this batch, an upper bound of the voxels the batch inserts.
+__global__ void k_room(const MapRefs* refs, int G, const int* slot_of, int J, BatchScratch bs,
+                       unsigned long long* out)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        unsigned long long inc = 0;
+        for (int j = 0; j < J; j++) {
+            const int slot = slot_of[g * J + j];
+            if (slot >= 0) inc += (unsigned long long)max(bs.frame(slot).ctr->n_entries, 0);
+        }
+        out[2 * g] = *refs[g].vt.used;
+        out[2 * g + 1] = inc;
+    }
+}
+
+int launch_room(const MapRefs* refs, int G, const int* slot_of, int J, const BatchScratch& bs, unsigned long long* out,
+                cudaStream_t st)
+{
+    k_room<<<(G + 127) / 128, 128, 0, st>>>(refs, G, slot_of, J, bs, out);
+    return 1;
+}
+
 int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st)
 {
     k_serial_begin<<<(G + 127) / 128, 128, 0, st>>>(refs, G);

@@ -58,6 +58,8 @@ constexpr int GEOMETRY_CHUNK = 4;
 
 // start of a batch's serial part: every map's edge and copy counters to zero
 int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st);
+int launch_room(const MapRefs* refs, int G, const int* slot_of, int J, const BatchScratch& bs, unsigned long long* out,
+                cudaStream_t st);
 int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st);
 // serial part, step st.j over the G maps of a batch: phase 0 overlap,
 // 1 score, 2 union, 3 apply
