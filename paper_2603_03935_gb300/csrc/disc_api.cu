@@ -326,6 +326,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         bs.sMMD = (long long)MM * D;
         bs.sS = 5LL * MM;
         bs.scap = (long long)scap;
+        bs.sK = r.Kpad;
         Scratch& sc = bs.base;
         sc.sumF = a.get<long long>((size_t)B * D);
         sc.fbar = a.get<float>((size_t)B * D);
@@ -339,6 +340,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         sc.cosg = a.get<float>((size_t)B * P);
         sc.fnorm = a.get<float>((size_t)B * P);
         sc.qexp = a.get<int32_t>((size_t)B * P);
+        sc.qmul = a.get<float>((size_t)B * r.Kpad);
         sc.qerr = a.get<float>((size_t)B * P);
         sc.qnrm = a.get<float>((size_t)B * P);
         sc.qexpm = a.get<int32_t>((size_t)B * MM);
@@ -395,6 +397,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         CK(cudaMemsetAsync(sc.ctr, 0, sizeof(FrameCounters) * B, s));
         CK(cudaMemsetAsync(sc.W, 0, sizeof(float) * (size_t)B * bs.sW, s));
         CK(cudaMemsetAsync(sc.W8, 0, (size_t)B * bs.sW, s));
+        CK(cudaMemsetAsync(sc.qmul, 0, sizeof(float) * (size_t)B * r.Kpad, s));
         CK(cudaMemsetAsync(sc.qexpm, 0, sizeof(int32_t) * (size_t)B * MM, s));
         CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
         CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));

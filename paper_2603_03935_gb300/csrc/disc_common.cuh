@@ -163,6 +163,7 @@ struct Scratch {
     float* fnorm;       // [P]
     // E4M3 operands (FP8 precision): token p is quantised as f_p / 2^qexp[p]
     int32_t* qexp;      // [P]
+    float* qmul;        // [Kpad] 2^-qexp[p] (0 past P): the GEMM's token scaling
     float* qerr;        // [P] bound of ||2^qexp q_p - f_p||
     float* qnrm;        // [P] bound of ||q_p|| (quantised units)
     int32_t* qexpm;     // [MM] mask m's weight row is quantised as 2^qexp[p] w / 2^qexpm[m]
@@ -204,7 +205,7 @@ struct Scratch {
 // every array (in elements).
 struct BatchScratch {
     Scratch base;
-    long long sD, sP, sMM, sMMP, sW, sMMD, sS, scap, spx;
+    long long sD, sP, sMM, sMMP, sW, sMMD, sS, scap, spx, sK;
     __host__ __device__ Scratch frame(int f) const
     {
         Scratch s = base;
@@ -220,6 +221,7 @@ struct BatchScratch {
         s.cosg += f * sP;
         s.fnorm += f * sP;
         s.qexp += f * sP;
+        s.qmul += f * sK;
         s.qerr += f * sP;
         s.qnrm += f * sP;
         s.qexpm += f * sMM;
@@ -362,6 +364,14 @@ __device__ __forceinline__ int e4m3_exp(float mx)
     return e;
 }
 
+// x * 2^e, correctly rounded (exact unless the result is subnormal): one
+// multiply by the power of two when that is a normal float, else ldexpf
+__device__ __forceinline__ float scale_pow2(float x, int e)
+{
+    if (e >= -126 && e <= 127) return __fmul_rn(x, __int_as_float((127 + e) << 23));
+    return ldexpf(x, e);
+}
+
 __device__ __forceinline__ uint8_t to_e4m3(float x)
 {
     return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
@@ -387,9 +397,9 @@ __device__ __forceinline__ void e4m3_copy_row(const float* x, int D, uint8_t* q8
     float se = 0.0f, sn = 0.0f;
     for (int d = lane; d < D; d += 32) {
         const float v = x[d];
-        const uint8_t q = to_e4m3(ldexpf(v, -e));
+        const uint8_t q = to_e4m3(scale_pow2(v, -e));
         q8[d] = q;
-        const float r = __fsub_rn(ldexpf(from_e4m3(q), e), v);
+        const float r = __fsub_rn(scale_pow2(from_e4m3(q), e), v);
         se = __fadd_rn(se, __fmul_rn(r, r));
         sn = __fadd_rn(sn, __fmul_rn(v, v));
     }

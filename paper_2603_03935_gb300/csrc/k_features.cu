@@ -96,12 +96,14 @@ __global__ void k_tok_rows(const FrameParams* fps, BatchScratch bs)
         // residue, bounds of ||2^e q_p - f_p|| and ||q_p||; fp32 sums of at
         // most D/32 + 5 levels stay within (1 + 2^-10) of the exact values
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const int e = e4m3_exp(mx);
+        // (any e with max |f| <= 448 * 2^e serves; from -127 on, 2^-e is a
+        // normal float, so the GEMM scales by one exact multiply)
+        const int e = max(e4m3_exp(mx), -127);
         float se = 0.0f, sn = 0.0f;
         for (int d = lane; d < fp.D; d += 32) {
             const float f = tok<T>(F, (size_t)p * fp.D + d);
-            const float q = from_e4m3(to_e4m3(ldexpf(f, -e)));
-            const float r = __fsub_rn(ldexpf(q, e), f);
+            const float q = from_e4m3(to_e4m3(scale_pow2(f, -e)));
+            const float r = __fsub_rn(scale_pow2(q, e), f);
             se = __fadd_rn(se, __fmul_rn(r, r));
             sn = __fadd_rn(sn, __fmul_rn(q, q));
         }
@@ -109,6 +111,7 @@ __global__ void k_tok_rows(const FrameParams* fps, BatchScratch bs)
         sn = warp_sum(sn);
         if (lane == 0) {
             sc.qexp[p] = e;
+            sc.qmul[p] = __int_as_float((127 - e) << 23);
             sc.qerr[p] = __fmul_rn(sqrtf(se), 1.0f + 0x1p-10f);
             sc.qnrm[p] = __fmul_rn(sqrtf(sn), 1.0f + 0x1p-10f);
         }
@@ -214,16 +217,16 @@ __device__ float fp8_weights(const FrameParams& fp, const Scratch& sc, int m, co
                              float* red)
 {
     float mx = 0.0f;
-    for (int p = threadIdx.x; p < fp.P; p += blockDim.x) mx = fmaxf(mx, ldexpf(w[p], sc.qexp[p]));
+    for (int p = threadIdx.x; p < fp.P; p += blockDim.x) mx = fmaxf(mx, scale_pow2(w[p], sc.qexp[p]));
     mx = block_max(mx, red);
     const int b = e4m3_exp(mx);
     float g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
     for (int p = threadIdx.x; p < fp.P; p += blockDim.x) {
-        const float ws = ldexpf(w[p], sc.qexp[p]);
-        const uint8_t q = to_e4m3(ldexpf(ws, -b));
+        const float ws = scale_pow2(w[p], sc.qexp[p]);
+        const uint8_t q = to_e4m3(scale_pow2(ws, -b));
         w8[p] = q;
         const float r = from_e4m3(q);
-        g1 = __fadd_rn(g1, __fmul_rn(fabsf(__fsub_rn(ldexpf(r, b), ws)), sc.qnrm[p]));
+        g1 = __fadd_rn(g1, __fmul_rn(fabsf(__fsub_rn(scale_pow2(r, b), ws)), sc.qnrm[p]));
         g2 = __fadd_rn(g2, __fmul_rn(w[p], sc.qerr[p]));
         g3 = __fadd_rn(g3, __fmul_rn(r, sc.qnrm[p]));
     }
@@ -232,7 +235,7 @@ __device__ float fp8_weights(const FrameParams& fp, const Scratch& sc, int m, co
     g3 = block_sum(g3, red);
     if (threadIdx.x == 0) sc.qexpm[m] = b;
     const float gam = ldexpf((float)(fp.Kpad / 32 + 2), -12);
-    return __fmul_rn(__fadd_rn(__fadd_rn(g1, g2), __fmul_rn(gam, ldexpf(g3, b))), 1.0f + 0x1p-10f);
+    return __fmul_rn(__fadd_rn(__fadd_rn(g1, g2), __fmul_rn(gam, scale_pow2(g3, b))), 1.0f + 0x1p-10f);
 }
 
 // ---- pooling weights and the image-based quality terms (one block per mask) ---

@@ -219,20 +219,31 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         }
         const int p0 = c * GEMM_KC;
         if constexpr (F8) {
-            // A: F^T tile in e4m3, thread tid owns row d0 + tid, 16 patches per 16 B
+            // A: F^T tile in e4m3, thread tid owns row d0 + tid, 16 patches per
+            // 16 B; all loads first, then one exact multiply by 2^-a_p each
             {
                 const int d = d0 + tid;
+                float x[GEMM_KC];
+#pragma unroll
+                for (int j = 0; j < GEMM_KC; j++) {
+                    const int p = p0 + j;
+                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
+                }
+                const float4* qm = (const float4*)(sc.qmul + p0);  // zero past P
+#pragma unroll
+                for (int q4 = 0; q4 < GEMM_KC / 4; q4++) {
+                    const float4 mu = qm[q4];
+                    x[4 * q4] = __fmul_rn(x[4 * q4], mu.x);
+                    x[4 * q4 + 1] = __fmul_rn(x[4 * q4 + 1], mu.y);
+                    x[4 * q4 + 2] = __fmul_rn(x[4 * q4 + 2], mu.z);
+                    x[4 * q4 + 3] = __fmul_rn(x[4 * q4 + 3], mu.w);
+                }
 #pragma unroll
                 for (int kq = 0; kq < GEMM_KC / 16; kq++) {
-                    float x[16];
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int p = p0 + 16 * kq + j;
-                        x[j] = (d < D && p < P) ? ldexpf(ldtok<T>(F, (size_t)p * D + d), -sc.qexp[p]) : 0.0f;
-                    }
-                    const uint4 v = make_uint4(pack_e4m3(x[0], x[1], x[2], x[3]), pack_e4m3(x[4], x[5], x[6], x[7]),
-                                               pack_e4m3(x[8], x[9], x[10], x[11]),
-                                               pack_e4m3(x[12], x[13], x[14], x[15]));
+                    const float* y = x + 16 * kq;
+                    const uint4 v = make_uint4(pack_e4m3(y[0], y[1], y[2], y[3]), pack_e4m3(y[4], y[5], y[6], y[7]),
+                                               pack_e4m3(y[8], y[9], y[10], y[11]),
+                                               pack_e4m3(y[12], y[13], y[14], y[15]));
                     *(uint4*)(st + kq * A_LBO + tid * 16) = v;
                 }
             }
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
                 const int m = c0 + j;
                 if (m < M && d < D) {
                     float v = __uint_as_float(r[j]);
-                    if constexpr (F8) v = ldexpf(v, sc.qexpm[m]);
+                    if constexpr (F8) v = scale_pow2(v, sc.qexpm[m]);
                     sc.Efast[(size_t)m * D + d] = v;
                 }
             }

@@ -204,6 +204,29 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
                     nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
                 }
             }
+        } else if (inst.E8 && (D & 3) == 0) {  // E4M3 scoring copy: 4-byte words of 4
+            const float4* a4 = (const float4*)a;
+            const uint32_t* b4 = (const uint32_t*)(inst.E8 + (size_t)k * D);
+            const int n4 = D >> 2;
+            for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+                float4 xs[4];
+                uint32_t ys[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int d = d0 + j * 32 + lane;
+                    xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ys[j] = d < n4 ? b4[d] : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float4 x = xs[j];
+                    const float y0 = from_e4m3(ys[j] & 0xffu), y1 = from_e4m3((ys[j] >> 8) & 0xffu);
+                    const float y2 = from_e4m3((ys[j] >> 16) & 0xffu), y3 = from_e4m3(ys[j] >> 24);
+                    dt += x.x * y0 + x.y * y1 + x.z * y2 + x.w * y3;
+                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                    nb += y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3;
+                }
+            }
         } else if (inst.E8) {
             const uint8_t* b8 = inst.E8 + (size_t)k * D;
             for (int d = lane; d < D; d += 32) {
@@ -263,11 +286,37 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
             // exact re-score with the exact pooled embedding
             const float* ae = sc.Ecan + (size_t)m * D;
             long long xd = 0, xa = 0, xb = 0;
-            for (int d = lane; d < D; d += 32) {
-                const float x = ae[d], y = b[d];
-                xd += fix32f(__fmul_rn(x, y), S_SQ);
-                xa += fix32f(__fmul_rn(x, x), S_SQ);
-                xb += fix32f(__fmul_rn(y, y), S_SQ);
+            if ((D & 3) == 0) {  // all of a lane's loads in flight before the exact sums
+                const float4* a4 = (const float4*)ae;
+                const float4* b4 = (const float4*)b;
+                const int n4 = D >> 2;
+                for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+                    float4 xs[4], ys[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int d = d0 + j * 32 + lane;
+                        xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        ys[j] = d < n4 ? b4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const float xv[4] = {xs[j].x, xs[j].y, xs[j].z, xs[j].w};
+                        const float yv[4] = {ys[j].x, ys[j].y, ys[j].z, ys[j].w};
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            xd += fix32f(__fmul_rn(xv[c], yv[c]), S_SQ);
+                            xa += fix32f(__fmul_rn(xv[c], xv[c]), S_SQ);
+                            xb += fix32f(__fmul_rn(yv[c], yv[c]), S_SQ);
+                        }
+                    }
+                }
+            } else {
+                for (int d = lane; d < D; d += 32) {
+                    const float x = ae[d], y = b[d];
+                    xd += fix32f(__fmul_rn(x, y), S_SQ);
+                    xa += fix32f(__fmul_rn(x, x), S_SQ);
+                    xb += fix32f(__fmul_rn(y, y), S_SQ);
+                }
             }
             xd = warp_sum(xd);
             xa = warp_sum(xa);

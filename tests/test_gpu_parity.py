@@ -349,6 +349,7 @@ def test_bf16_precision_parity_and_fp64_error(torch_dev):
         common.compare_frame(st, rep, o, ctx=f"bf16 precision frame {i}", efast_tol=2e-2)
         worst = max(worst, _bf16_fast_error(rep, fr.tokens[i], sc))
     common.compare_maps(gmap, omap, ctx="bf16 precision")
+    print(f"bf16 tiny: worst |E_fast - E64| / |E64| = {worst:.5f}")
     assert worst < 1e-2, worst
 
 
@@ -463,8 +464,36 @@ def test_fp8_precision_parity_and_fp64_error(torch_dev):
     assert np.array_equal(inst["E"].view(np.uint32), ea.view(np.uint32))
     # E4M3 keeps 3 mantissa bits: a few percent against fp64, and the
     # device's residue-based bound well inside the format's worst case
+    print(f"fp8 tiny: worst |E_fast - E64| / |E64| = {worst:.4f}, device bound / a-priori bound <= "
+          f"{max(tight):.3f} (median {float(np.median(tight)):.3f}), re-scored pairs {border}")
     assert 1e-3 < worst < 0.1, worst
     assert max(tight) < 0.8, max(tight)
+
+
+def test_fp8_precision_room_scale(torch_dev):
+    # full 640x480 frames, 24x24x768 tokens, 40 masks: labels and stored
+    # embeddings identical to the oracle; the E4M3 fast embedding within the
+    # device bound of every mask, and that bound within the format's worst case
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.room_scene(num_frames=2000)
+    idx = [0, 1, 2, 3, 250, 251]
+    fr = sc.render(idx)
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 22, instance_capacity=1024, precision=2)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    worst, tight, border = 0.0, [], 0
+    for i in range(len(idx)):
+        st = gmap.integrate(_dframe(torch, dev, fr, i))
+        o = omap.integrate(*oracle.frame_args(fr, i))
+        rep = gmap.last_frame()
+        common.compare_frame(st, rep, o, ctx=f"fp8 room frame {idx[i]}", efast_tol=0.15)
+        w, t = _fp8_fast_error(rep, fr.tokens[i], sc)
+        worst, tight, border = max(worst, w), tight + t, border + st["borderline_rescored"]
+    common.compare_maps(gmap, omap, ctx="fp8 room")
+    print(f"fp8 room: worst |E_fast - E64| / |E64| = {worst:.4f}, device bound / a-priori bound <= "
+          f"{max(tight):.3f} (median {float(np.median(tight)):.3f}), re-scored pairs {border}")
+    assert worst < 0.1
 
 
 def test_fp8_precision_borderline_rescored(torch_dev):
