@@ -91,6 +91,9 @@ typedef struct {
                                 with this batch's serial steps, which run on their own set of this many
                                 SMs (a green context; without one, a high-priority stream); <= 0: no
                                 overlap (the default: the overlap measured slower on GB300) */
+    int32_t overlap_dilation;/* 1: a segment voxel also overlaps the instances labelling any of its 26
+                                neighbours (the "immediate neighborhood" of Sec. III-B), once per
+                                instance; 0 (default): the voxel itself only */
 } disc_map_config;
 
 typedef struct {

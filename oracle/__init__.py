@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
                 ("ov_num", ctypes.c_int32), ("ov_den", ctypes.c_int32),
                 ("embed_dim", ctypes.c_int32), ("patch_h", ctypes.c_int32), ("patch_w", ctypes.c_int32),
                 ("min_mask_pixels", ctypes.c_int32), ("dbscan_eps", ctypes.c_float),
-                ("dbscan_min_pts", ctypes.c_int32)]
+                ("dbscan_min_pts", ctypes.c_int32), ("overlap_dilation", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -101,7 +101,7 @@ def _p(a):
 def default_config(D: int, Ph: int, Pw: int, voxel: float, **kw) -> dict:
     c = dict(voxel_size=voxel, z_min=0.1, z_max=10.0, eps=1e-6, tau_cos=0.75, lambda_size=3.3,
              ov_num=1, ov_den=5, embed_dim=D, patch_h=Ph, patch_w=Pw, min_mask_pixels=1,
-             dbscan_eps=0.0, dbscan_min_pts=1)
+             dbscan_eps=0.0, dbscan_min_pts=1, overlap_dilation=0)
     c.update(kw)
     return c
 

@@ -441,15 +441,33 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         Qm[m] = ((S_size[m] * S_ang[m]) * S_sem[m]) * S_dist[m];
     }
 
-    // (a7) overlap with the map as it stood before this frame.
+    // (a7) overlap with the map as it stood before this frame.  With
+    // overlap_dilation (the "immediate neighborhood" of Sec. III-B) a segment
+    // voxel overlaps every instance that labels it or one of its 26
+    // neighbours, once per instance.
     std::vector<std::map<int32_t, int64_t>> ov(M);  // per segment: root -> voxels
     std::set<int32_t> active;
     for (auto& kv : segvox) {
-        auto it = map->vox.find(kv.first.second);
-        if (it == map->vox.end()) continue;
-        int32_t root = map->parent[it->second];
-        ov[kv.first.first - 1][root] += 1;
-        active.insert(root);
+        std::set<int32_t> roots;
+        int32_t k[3];
+        unpack(kv.first.second, k);
+        const int reach = cfg.overlap_dilation ? 1 : 0;
+        for (int dx = -reach; dx <= reach; dx++)
+            for (int dy = -reach; dy <= reach; dy++)
+                for (int dz = -reach; dz <= reach; dz++) {
+                    const int32_t q[3] = {k[0] + dx, k[1] + dy, k[2] + dz};
+                    bool in = true;
+                    for (int a = 0; a < 3; a++) in = in && q[a] >= -KEY_BIAS && q[a] <= KEY_BIAS - 1;
+                    if (!in) continue;
+                    const uint64_t nk = ((uint64_t)(q[0] + KEY_BIAS) << (2 * KEY_BITS)) |
+                                        ((uint64_t)(q[1] + KEY_BIAS) << KEY_BITS) | (uint64_t)(q[2] + KEY_BIAS);
+                    auto it = map->vox.find(nk);
+                    if (it != map->vox.end()) roots.insert(map->parent[it->second]);
+                }
+        for (int32_t root : roots) {
+            ov[kv.first.first - 1][root] += 1;
+            active.insert(root);
+        }
     }
     int pairs = 0;
     for (int m = 0; m < M; m++) pairs += (int)ov[m].size();

@@ -36,6 +36,7 @@ typedef struct {
     int32_t min_mask_pixels;
     float dbscan_eps;        /* > 0: per-segment DBSCAN denoise before voxelisation (radius, metres) */
     int32_t dbscan_min_pts;  /* core point: at least this many points of its segment within eps */
+    int32_t overlap_dilation;/* 1: a segment voxel also overlaps the instances of its 26 neighbours */
 } oracle_config;
 
 typedef struct {

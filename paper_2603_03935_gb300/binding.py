@@ -30,7 +30,7 @@ class Config(ctypes.Structure):
                 ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
                 ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
                 ("device", c_i32), ("batch_frames", c_i32), ("dbscan_eps", c_f32), ("dbscan_min_pts", c_i32),
-                ("serial_sms", c_i32)]
+                ("serial_sms", c_i32), ("overlap_dilation", c_i32)]
 
 
 class Frame(ctypes.Structure):

@@ -189,6 +189,7 @@ bool config_ok(const disc_map_config& c)
     if (c.instance_capacity <= 0) return false;
     if (c.batch_frames < 0 || c.batch_frames > 256) return false;
     if (c.precision != DISC_FP32 && c.precision != DISC_BF16 && c.precision != DISC_FP8_E4M3) return false;
+    if (c.overlap_dilation != 0 && c.overlap_dilation != 1) return false;
     // DBSCAN cells at least a voxel wide keep cell coordinates in key range
     if (!(c.dbscan_eps >= 0.0f) || (c.dbscan_eps > 0.0f && (c.dbscan_eps < c.voxel_size || c.dbscan_min_pts < 1)))
         return false;
@@ -1011,6 +1012,7 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
     fp.map = g;
     fp.precision = m->cfg.precision;
+    fp.dilate = m->cfg.overlap_dilation;
     fp.db_min_pts = m->cfg.dbscan_eps > 0.0f ? m->cfg.dbscan_min_pts : 0;
     fp.db_eps2 = m->cfg.dbscan_eps * m->cfg.dbscan_eps;
     fp.db_inv_cell = m->cfg.dbscan_eps > 0.0f ? 1.0f / (m->cfg.dbscan_eps * 1.001f) : 0.0f;

@@ -328,6 +328,7 @@ struct FrameParams {
     int32_t token_bf16;
     int32_t map;           // position of the frame's map in the batch (MapRefs index)
     int32_t precision;     // disc_precision of the fast pooled embedding and scoring
+    int32_t dilate;        // overlap_dilation: 26-neighbour overlap
     int32_t db_min_pts;    // DBSCAN core threshold; 0: no DBSCAN for this frame
     float db_eps2;         // eps * eps
     float db_inv_cell;     // 1 / (1.001 eps): grid cells a little wider than eps

@@ -50,8 +50,76 @@ __device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, const Seri
 constexpr int SER_THREADS = 1024;
 constexpr int OV_SLOTS = 2 * SER_THREADS;
 
+// label of a key in the voxel table, -1 if absent
+__device__ __forceinline__ int vt_label(const VoxelTable& vt, unsigned long long key)
+{
+    unsigned long long h = mix64(key) & vt.mask;
+    for (unsigned long long pr = 0; pr <= vt.mask; pr++) {
+        const unsigned long long kk = vt.keys[h];
+        if (kk == key) return vt.labels[h];
+        if (kk == EMPTY_KEY) return -1;
+        h = (h + 1) & vt.mask;
+    }
+    return -1;
+}
+
+// one more voxel of segment-instance pair okey in the frame's pair hash
+__device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned long long okey)
+{
+    unsigned long long t = mix64(okey) & ss.omask;
+    for (unsigned long long pr = 0;; pr++) {
+        const unsigned long long cur = ss.okeys[t];
+        if (cur == okey) break;
+        if (cur == EMPTY_KEY) {
+            const unsigned long long prev = atomicCAS(&ss.okeys[t], EMPTY_KEY, okey);
+            if (prev == EMPTY_KEY) {
+                ss.olist[atomicAdd(&sc.ctr->n_pairs, 1)] = (int)t;
+                break;
+            }
+            if (prev == okey) break;
+        }
+        t = (t + 1) & ss.omask;
+        if (pr > ss.omask) {
+            set_err(sc.ctr, DISC_ERR_TABLE_FULL);
+            return;
+        }
+    }
+    atomicAdd(&ss.ocnt[t], 1);
+}
+
+// Neighbourhood overlap (overlap_dilation): segment voxel `key` (label lab,
+// -1 if absent) overlaps each distinct instance labelling it or one of its 26
+// neighbours, once.  One entry may add up to 27 pairs, so they go straight to
+// the frame's pair hash.
+__device__ void dilated_pairs(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
+                              int m, unsigned long long key, int lab)
+{
+    int roots[27];
+    int nr = 0;
+    if (lab >= 0) roots[nr++] = inst.parent[lab];
+    int k[3];
+    unpack_key(key, k);
+    for (int t = 0; t < 27; t++) {
+        if (t == 13) continue;  // the voxel itself
+        const int q[3] = {k[0] + t / 9 - 1, k[1] + (t / 3) % 3 - 1, k[2] + t % 3 - 1};
+        if (q[0] < -KEY_BIAS || q[0] > KEY_BIAS - 1 || q[1] < -KEY_BIAS || q[1] > KEY_BIAS - 1 ||
+            q[2] < -KEY_BIAS || q[2] > KEY_BIAS - 1)
+            continue;
+        const unsigned long long nk = ((unsigned long long)(q[0] + KEY_BIAS) << (2 * KEY_BITS)) |
+                                      ((unsigned long long)(q[1] + KEY_BIAS) << KEY_BITS) |
+                                      (unsigned long long)(q[2] + KEY_BIAS);
+        const int nl = vt_label(vt, nk);
+        if (nl < 0) continue;
+        const int r = inst.parent[nl];
+        bool seen = false;
+        for (int j = 0; j < nr; j++) seen |= roots[j] == r;
+        if (!seen) roots[nr++] = r;
+    }
+    for (int j = 0; j < nr; j++) add_pair(sc, ss, ((unsigned long long)m << 32) | (unsigned)roots[j]);
+}
+
 __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
-                              unsigned char* smem)
+                              unsigned char* smem, bool dilate)
 {
     unsigned long long* pkey = (unsigned long long*)smem;   // [OV_SLOTS]
     int* pcnt = (int*)(pkey + OV_SLOTS);                    // [OV_SLOTS]
@@ -82,7 +150,8 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
                     h = (h + 1) & vt.mask;
                 }
             }
-            if (lab >= 0) {
+            if (dilate) dilated_pairs(sc, ss, vt, inst, m, key, lab);
+            if (lab >= 0 && !dilate) {
                 const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
                 unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
                 while (true) {
@@ -91,7 +160,7 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
                     t = (t + 1) & (OV_SLOTS - 1);
                 }
                 atomicAdd(&pcnt[t], 1);
-            } else {
+            } else if (lab < 0) {
                 unsigned long long t = mix64(key) & ss.nmask;
                 for (int pr = 0;; pr++) {
                     const unsigned long long cur = ss.nkeys[t];
@@ -689,7 +758,7 @@ __device__ int block_slot(const BatchScratch& bs, const SerialStep& st, bool* bl
 
 constexpr size_t OV_SMEM = (size_t)OV_SLOTS * 12;
 
-__global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, SerialStep st)
+__global__ void __launch_bounds__(SER_THREADS) k_overlap(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
     extern __shared__ __align__(16) unsigned char ov_smem[];
     bool blocked;
@@ -699,7 +768,7 @@ __global__ void __launch_bounds__(SER_THREADS) k_overlap(BatchScratch bs, Serial
     const SerialScratch ss = R.ss;
     const VoxelTable vt = R.vt;
     const Instances inst = R.inst;
-    phase_overlap(bs.frame(slot), ss, vt, inst, ov_smem);
+    phase_overlap(bs.frame(slot), ss, vt, inst, ov_smem, fps[slot].dilate != 0);
 }
 
 __global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st)
@@ -804,7 +873,7 @@ int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const Ser
 {
     switch (phase) {
         case 0:
-            k_overlap<<<dim3(per_map(152 * 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(bs, st);
+            k_overlap<<<dim3(per_map(152 * 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(fps, bs, st);
             return 1;
         case 1:
             k_score<<<dim3(per_map(152, G, 4), G), 256, 0, st_>>>(fps, bs, st);

@@ -31,6 +31,7 @@ def to_oracle_cfg(dcfg):
     out = {k: dcfg[k] for k in keys}
     out["dbscan_eps"] = dcfg.get("dbscan_eps", 0.0)
     out["dbscan_min_pts"] = dcfg.get("dbscan_min_pts", 1)
+    out["overlap_dilation"] = dcfg.get("overlap_dilation", 0)
     return out
 
 

@@ -105,6 +105,33 @@ def test_room_scale_frames_parity(torch_dev):
     run_parity(torch_dev, sc, [0, 1, 2, 3, 250, 251], voxel_capacity=1 << 22, instance_capacity=1024)
 
 
+def test_tiny_parity_with_neighbourhood_overlap(torch_dev):
+    # overlap_dilation: a segment voxel also overlaps the instances of its 26
+    # neighbours (Sec. III-B "immediate neighborhood")
+    _, _, stats = run_parity(torch_dev, synth.tiny_scene(), range(20), overlap_dilation=1)
+    assert sum(st["overlap_pairs"] for st in stats) > 0
+
+
+def test_room_batched_parity_with_neighbourhood_overlap(torch_dev):
+    # 32 full-size frames in one call: neighbours inserted by earlier frames
+    # of the batch must be seen by the later ones
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap
+    sc = synth.room_scene(num_frames=2000)
+    fr = sc.render(range(32))
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 24, instance_capacity=1 << 16, overlap_dilation=1)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    frames = [_dframe(torch, dev, fr, i) for i in range(32)]
+    stats, done, rc = gmap.integrate_frames(frames)
+    assert rc == 0 and done == 32
+    for j, st in enumerate(stats):
+        o = omap.integrate(*oracle.frame_args(fr, j), report=True)
+        for gk, ok in common.COUNT_FIELDS:
+            assert st[gk] == o[ok], f"frame {j} {gk}: {st[gk]} vs {o[ok]}"
+    common.compare_maps(gmap, omap, ctx="room batched, neighbourhood overlap")
+
+
 def test_room_trajectory_batched_parity(torch_dev):
     # the launch configuration the benchmark times: 32 consecutive full-size
     # frames per disc_integrate_frames call, device-resident inputs
