@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=0,
                     help="fast pooling/scoring precision of the plain path: 0 fp32 (the Room-scale "
                          "configuration), 1 bf16, 2 fp8 e4m3")
+    ap.add_argument("--dilation-steps", type=int, default=20,
+                    help="steps of the same workload with the 26-neighbour overlap (0: skip)")
     ap.add_argument("--dbscan-steps", type=int, default=20,
                     help="steps of the same workload with the DBSCAN filter on (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -553,30 +555,43 @@ def main():
     clk = clocks.stop()
     frames_all = K * B * world
 
-    # the same workload with the Sec. III-A DBSCAN filter on (eps 5 cm, 10 points)
-    dbscan = None
-    if args.dbscan_steps > 0:
-        dcfg = dict(cfg, dbscan_eps=0.05, dbscan_min_pts=10)
-        dmap = DiscMap(**dcfg)
+    def variant(extra, nsteps):
+        """The same steps on a fresh map with config changes; frames/s and the
+        per-frame counters summed."""
+        vmap = DiscMap(**dict(cfg, **extra))
         for s_ in range(Wm):
-            assert dmap.integrate_frames_raw(steps[s_], B, stats) == 0
+            assert vmap.integrate_frames_raw(steps[s_], B, stats) == 0
         torch.cuda.synchronize()
-        dt_ms, den, nf = 0.0, 0, 0
-        for s_ in range(Wm, Wm + min(args.dbscan_steps, K)):
+        dt_ms, nf, sums = 0.0, 0, {}
+        for s_ in range(Wm, Wm + min(nsteps, K)):
             flush.fill_(float(s_))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rc = dmap.integrate_frames_raw(steps[s_], B, stats)
+            rc = vmap.integrate_frames_raw(steps[s_], B, stats)
             e1.record(stream)
             e1.synchronize()
             assert rc == 0, rc
             dt_ms += e0.elapsed_time(e1)
-            den += sum(stats[j].denoised_pixels for j in range(B))
+            for j in range(B):
+                for k_, v_ in stats[j].as_dict().items():
+                    sums[k_] = sums.get(k_, 0) + v_
             nf += B
-        dmap.close()
-        dbscan = {"frames_per_s": nf / (dt_ms / 1e3), "eps_m": 0.05, "min_pts": 10, "frames": nf,
-                  "denoised_pixels_per_frame": den / nf}
+        vmap.close()
+        return nf / (dt_ms / 1e3), nf, {k_: v_ / nf for k_, v_ in sums.items()}
+
+    # the same workload with the Sec. III-A DBSCAN filter on (eps 5 cm, 10 points)
+    dbscan = None
+    if args.dbscan_steps > 0:
+        fps_, nf, per = variant(dict(dbscan_eps=0.05, dbscan_min_pts=10), args.dbscan_steps)
+        dbscan = {"frames_per_s": fps_, "eps_m": 0.05, "min_pts": 10, "frames": nf,
+                  "denoised_pixels_per_frame": per["denoised_pixels"]}
+    # and with the neighbourhood overlap (26-neighbour dilation, Sec. III-B)
+    dilation = None
+    if args.dilation_steps > 0:
+        fps_, nf, per = variant(dict(overlap_dilation=1), args.dilation_steps)
+        dilation = {"frames_per_s": fps_, "frames": nf, "overlap_pairs_per_frame": per["overlap_pairs"],
+                    "merges_per_frame": per["merges"], "new_instances_per_frame": per["new_instances"]}
 
     # per-phase device time on the following batches (event-record nodes
     # around each phase, inside the batch's graph)
@@ -694,6 +709,7 @@ def main():
                "frame_ms_batched": total_ms / (K * B),
                "batched": batched,
                "dbscan": dbscan,
+               "dilation": dilation,
                "served": served,
                "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
                "gpu_launches": int(launches),
