@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
                 ("ov_num", ctypes.c_int32), ("ov_den", ctypes.c_int32),
                 ("embed_dim", ctypes.c_int32), ("patch_h", ctypes.c_int32), ("patch_w", ctypes.c_int32),
                 ("min_mask_pixels", ctypes.c_int32), ("dbscan_eps", ctypes.c_float),
-                ("dbscan_min_pts", ctypes.c_int32), ("overlap_dilation", ctypes.c_int32)]
+                ("dbscan_min_pts", ctypes.c_int32), ("overlap_dilation", ctypes.c_int32),
+                ("assoc_dim", ctypes.c_int32), ("assoc_patch_h", ctypes.c_int32), ("assoc_patch_w", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -41,7 +42,8 @@ class Frame(ctypes.Structure):
                 ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("T_world_cam", ctypes.c_double * 16),
                 ("depth", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("tokens", ctypes.c_void_p),
-                ("num_masks", ctypes.c_int32), ("global_embed", ctypes.c_void_p)]
+                ("num_masks", ctypes.c_int32), ("global_embed", ctypes.c_void_p),
+                ("assoc_tokens", ctypes.c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -54,7 +56,7 @@ class Report(ctypes.Structure):
                 ("new_voxels", ctypes.c_int32), ("active_instances", ctypes.c_int32),
                 ("new_instances", ctypes.c_int32), ("merges", ctypes.c_int32),
                 ("live_segments", ctypes.c_int32), ("overlap_pairs", ctypes.c_int32),
-                ("denoised_pixels", ctypes.c_int32)]
+                ("denoised_pixels", ctypes.c_int32), ("A", ctypes.c_void_p)]
 
 
 _lib = None
@@ -90,6 +92,10 @@ def lib():
         L.oracle_finalize.restype = ctypes.c_int
         L.oracle_finalize.argtypes = [vp, ctypes.POINTER(FinalizeConfig), ctypes.POINTER(FinalizeReport)]
         L.oracle_set_state.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp, i32]
+        L.oracle_set_assoc.argtypes = [vp, vp, i32]
+        L.oracle_export_assoc.argtypes = [vp, vp]
+        L.oracle_query_heatmap.restype = ctypes.c_int
+        L.oracle_query_heatmap.argtypes = [vp, i32, i32, vp, f32, vp]
         _lib = L
     return _lib
 
@@ -101,7 +107,8 @@ def _p(a):
 def default_config(D: int, Ph: int, Pw: int, voxel: float, **kw) -> dict:
     c = dict(voxel_size=voxel, z_min=0.1, z_max=10.0, eps=1e-6, tau_cos=0.75, lambda_size=3.3,
              ov_num=1, ov_den=5, embed_dim=D, patch_h=Ph, patch_w=Pw, min_mask_pixels=1,
-             dbscan_eps=0.0, dbscan_min_pts=1, overlap_dilation=0)
+             dbscan_eps=0.0, dbscan_min_pts=1, overlap_dilation=0, assoc_dim=0, assoc_patch_h=0,
+             assoc_patch_w=0)
     c.update(kw)
     return c
 
@@ -135,6 +142,8 @@ class OracleMap:
             raise ValueError("bad oracle config")
         self.D = cfg["embed_dim"]
         self.P = cfg["patch_h"] * cfg["patch_w"]
+        self.Da = int(cfg.get("assoc_dim", 0))
+        self.Pa = int(cfg.get("assoc_patch_h", 0)) * int(cfg.get("assoc_patch_w", 0))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -152,7 +161,7 @@ class OracleMap:
             raise ValueError(f"oracle_finalize: {rc}")
         return {k: int(getattr(r, k)) for k, _ in FinalizeReport._fields_}
 
-    def set_state(self, keys, labels, parent, count, Q, E, n_obs):
+    def set_state(self, keys, labels, parent, count, Q, E, n_obs, A=None):
         """Replace the map's voxels and instances (exact test situations)."""
         keys = np.ascontiguousarray(keys, np.uint64)
         labels = np.ascontiguousarray(labels, np.int32)
@@ -163,10 +172,14 @@ class OracleMap:
         n_obs = np.ascontiguousarray(n_obs, np.int32)
         lib().oracle_set_state(self._h, keys.ctypes.data, labels.ctypes.data, len(keys), parent.ctypes.data,
                                count.ctypes.data, Q.ctypes.data, E.ctypes.data, n_obs.ctypes.data, len(parent))
+        if A is not None:
+            A = np.ascontiguousarray(A, np.float32).reshape(len(parent), self.Da)
+            lib().oracle_set_assoc(self._h, A.ctypes.data, len(parent))
 
     def integrate(self, depth, labels, tokens, pose, intr, num_masks, global_embed=None,
-                  report: bool = True):
-        """Integrate one frame; returns a dict of intermediates when report=True."""
+                  report: bool = True, assoc_tokens=None):
+        """Integrate one frame; returns a dict of intermediates when report=True.
+        assoc_tokens: the second token grid [Pa][Da] when the map has one."""
         H, W = depth.shape
         depth = np.ascontiguousarray(depth, np.float32)
         labels = np.ascontiguousarray(labels, np.uint16)
@@ -180,6 +193,10 @@ class OracleMap:
         f.depth, f.labels, f.tokens = depth.ctypes.data, labels.ctypes.data, tokens.ctypes.data
         f.num_masks = int(num_masks)
         f.global_embed = _p(g)
+        at = None
+        if self.Da > 0:
+            at = np.ascontiguousarray(assoc_tokens, np.float32).reshape(self.Pa, self.Da)
+            f.assoc_tokens = at.ctypes.data
         M, P, D = int(num_masks), self.P, self.D
         out = None
         rep = Report()
@@ -194,14 +211,18 @@ class OracleMap:
                        seg_m=np.zeros(cap, np.int32))
             for k in ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "S", "nvox", "rep", "seg_keys", "seg_m"):
                 setattr(rep, k, out[k].ctypes.data)
+            if self.Da > 0:
+                out["A"] = np.zeros((Mx, self.Da), np.float32)
+                rep.A = out["A"].ctypes.data
             rep.seg_cap = cap
         rc = lib().oracle_integrate_frame(self._h, ctypes.byref(f), ctypes.byref(rep) if report else None)
         if rc != 0:
             raise RuntimeError(f"oracle_integrate_frame failed: {rc}")
         if report:
             n = int(rep.n_seg)
-            for k in ("cov", "npix", "W", "E", "S", "nvox", "rep"):
-                out[k] = out[k][:M]
+            for k in ("cov", "npix", "W", "E", "S", "nvox", "rep", "A"):
+                if k in out:
+                    out[k] = out[k][:M]
             out["seg_keys"] = out["seg_keys"][:n]
             out["seg_m"] = out["seg_m"][:n]
             for k in ("valid_pixels", "dropped_pixels", "new_voxels", "active_instances", "new_instances",
@@ -228,7 +249,25 @@ class OracleMap:
         if n:
             lib().oracle_export_instances(self._h, parent.ctypes.data, count.ctypes.data, Q.ctypes.data,
                                           E.ctypes.data, obs.ctypes.data)
-        return dict(parent=parent, count=count, Q=Q, E=E, n_obs=obs)
+        out = dict(parent=parent, count=count, Q=Q, E=E, n_obs=obs)
+        if self.Da > 0:
+            A = np.zeros((n, self.Da), np.float32)
+            if n:
+                lib().oracle_export_assoc(self._h, A.ctypes.data)
+            out["A"] = A
+        return out
+
+
+def query_heatmap(F: np.ndarray, q: np.ndarray, eps: float = 1e-6) -> np.ndarray:
+    """Fig. 2 heatmap: D_p * cos(f_p, q) over a token grid [P][D]."""
+    F = np.ascontiguousarray(F, np.float32)
+    P, D = F.shape
+    q = np.ascontiguousarray(q, np.float32).reshape(D)
+    heat = np.zeros(P, np.float32)
+    rc = lib().oracle_query_heatmap(F.ctypes.data, P, D, q.ctypes.data, eps, heat.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_query_heatmap: {rc}")
+    return heat
 
 
 def token_stats(F: np.ndarray, g=None, eps: float = 1e-6):

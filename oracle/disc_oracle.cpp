@@ -107,6 +107,7 @@ struct oracle_map {
     std::vector<int64_t> count;                 // voxels per root
     std::vector<float> Q;
     std::vector<std::vector<float>> E;
+    std::vector<std::vector<float>> A;          // association features (second token grid)
     std::vector<int32_t> n_obs;
     bool final_ = false;  // finalised: no more frames
 };
@@ -114,6 +115,10 @@ struct oracle_map {
 oracle_map* oracle_map_create(const oracle_config* cfg)
 {
     if (!cfg || cfg->embed_dim <= 0 || cfg->patch_h <= 0 || cfg->patch_w <= 0 || !(cfg->voxel_size > 0.0f))
+        return nullptr;
+    if (cfg->assoc_dim < 0 || cfg->assoc_dim > 4096 ||
+        (cfg->assoc_dim > 0 && (cfg->assoc_patch_h <= 0 || cfg->assoc_patch_w <= 0 ||
+                                cfg->assoc_patch_h * cfg->assoc_patch_w > 16384)))
         return nullptr;
     oracle_map* m = new oracle_map();
     m->cfg = *cfg;
@@ -253,6 +258,12 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         D > 4096 || !fr->depth || !fr->labels || !fr->tokens)
         return ORACLE_ERR_INVALID_ARG;
     const float s = cfg.voxel_size;
+    const int Da = cfg.assoc_dim, Pa = cfg.assoc_patch_h * cfg.assoc_patch_w;
+    if (Da > 0) {
+        if (!fr->assoc_tokens) return ORACLE_ERR_INVALID_ARG;
+        for (int64_t i = 0; i < (int64_t)Pa * Da; i++)
+            if (!(std::fabs(fr->assoc_tokens[i]) <= TOKEN_LIMIT)) return ORACLE_ERR_RANGE;
+    }
 
     // Pose rounded once to fp32.
     Pose T;
@@ -305,6 +316,26 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         float sm = (float)(unfix(sem, S_SEM) / (double)npix[m]);
         S_sem[m] = std::min(std::max(sm, 0.0f), 1.0f);
         S_size[m] = std::min((cfg.lambda_size * (float)npix[m]) / (float)(H * Wd), 1.0f);
+    }
+
+    // (a3') with a second token grid: each mask's association feature, the
+    // pixel-level mean of that grid's tokens over the mask
+    std::vector<float> Am((size_t)M * std::max(Da, 1), 0.0f);
+    if (Da > 0) {
+        const int Pha = cfg.assoc_patch_h, Pwa = cfg.assoc_patch_w;
+        std::vector<int32_t> cova((size_t)std::max(M, 1) * Pa), npa(std::max(M, 1));
+        oracle_mask_coverage(fr->labels, H, Wd, Pha, Pwa, M, cova.data(), npa.data());
+        for (int m = 0; m < M; m++) {
+            if (!mask_ok[m]) continue;
+            for (int d = 0; d < Da; d++) {
+                int64_t acc = 0;
+                for (int p = 0; p < Pa; p++) {
+                    const float w = (float)cova[(size_t)m * Pa + p] / (float)npix[m];
+                    acc += fix(w * fr->assoc_tokens[(int64_t)p * Da + d], S_EMB);
+                }
+                Am[(size_t)m * Da + d] = (float)unfix(acc, S_EMB);
+            }
+        }
     }
 
     // (a5') Sec. III-A: each segment's points (pixels of an active mask with
@@ -482,7 +513,9 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
             int64_t denom = std::min<int64_t>(nvox[m], vk);
             bool geo = kv.second * (int64_t)cfg.ov_den >= (int64_t)cfg.ov_num * denom;
             if (!geo) continue;
-            float c = cosine_exact(&Em[(size_t)m * D], map->E[kv.first].data(), D);
+            // the association feature: the second grid's when there is one
+            float c = Da > 0 ? cosine_exact(&Am[(size_t)m * Da], map->A[kv.first].data(), Da)
+                             : cosine_exact(&Em[(size_t)m * D], map->E[kv.first].data(), D);
             if (c >= cfg.tau_cos) edges[m].push_back(kv.first);
         }
     }
@@ -511,22 +544,27 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
     std::map<int32_t, std::vector<int32_t>> comp;  // rep -> member roots (ascending)
     for (auto& kv : uf) comp[find(kv.first)].push_back(kv.first);
     // (a10) fusion candidates gathered before any state changes.
+    // The winning observation brings both its embedding and (with a second
+    // grid) its association feature.
     struct Cand {
         float q;
         const float* e;
+        const float* a;
     };
-    std::map<int32_t, std::vector<float>> fusedE;
+    std::map<int32_t, std::vector<float>> fusedE, fusedA;
     std::map<int32_t, float> fusedQ;
+    auto inst_a = [&](int32_t k) { return Da > 0 ? map->A[k].data() : nullptr; };
     for (auto& kv : comp) {
         int32_t r = kv.first;
-        Cand best{map->Q[kv.second[0]], map->E[kv.second[0]].data()};
+        Cand best{map->Q[kv.second[0]], map->E[kv.second[0]].data(), inst_a(kv.second[0])};
         for (size_t i = 1; i < kv.second.size(); i++) {
             int32_t k = kv.second[i];
-            if (map->Q[k] > best.q) best = {map->Q[k], map->E[k].data()};
+            if (map->Q[k] > best.q) best = {map->Q[k], map->E[k].data(), inst_a(k)};
         }
         for (int m = 0; m < M; m++)
-            if (segrep[m] == r && Qm[m] > best.q) best = {Qm[m], &Em[(size_t)m * D]};
+            if (segrep[m] == r && Qm[m] > best.q) best = {Qm[m], &Em[(size_t)m * D], &Am[(size_t)m * std::max(Da, 1)]};
         fusedE[r] = std::vector<float>(best.e, best.e + D);
+        if (Da > 0) fusedA[r] = std::vector<float>(best.a, best.a + Da);
         fusedQ[r] = best.q;
     }
     for (auto& kv : comp) {
@@ -544,6 +582,7 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         for (int m = 0; m < M; m++)
             if (segrep[m] == r) obs++;
         map->E[r] = fusedE[r];
+        if (Da > 0) map->A[r] = fusedA[r];
         map->Q[r] = fusedQ[r];
         map->n_obs[r] = obs;
     }
@@ -558,6 +597,7 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         map->count.push_back(0);
         map->Q.push_back(Qm[m]);
         map->E.emplace_back(&Em[(size_t)m * D], &Em[(size_t)m * D] + D);
+        if (Da > 0) map->A.emplace_back(&Am[(size_t)m * Da], &Am[(size_t)m * Da] + Da);
         map->n_obs.push_back(1);
         segrep[m] = id;
         new_inst++;
@@ -589,6 +629,7 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
         if (rep->npix && M) std::memcpy(rep->npix, npix.data(), sizeof(int32_t) * M);
         if (rep->W && M) std::memcpy(rep->W, Wt.data(), sizeof(float) * (size_t)M * P);
         if (rep->E && M) std::memcpy(rep->E, Em.data(), sizeof(float) * (size_t)M * D);
+        if (rep->A && M && Da > 0) std::memcpy(rep->A, Am.data(), sizeof(float) * (size_t)M * Da);
         if (rep->S)
             for (int m = 0; m < M; m++) {
                 rep->S[5 * m + 0] = S_size[m];
@@ -707,7 +748,10 @@ int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_f
         const int32_t a = c.first.first, b = c.first.second;
         const int64_t mn = std::min(map->count[a], map->count[b]);
         if (c.second * (int64_t)cfg->contact_den < (int64_t)cfg->contact_num * mn) continue;
-        if (!(cosine_exact(map->E[a].data(), map->E[b].data(), D) >= cfg->tau_cos)) continue;
+        const bool similar = map->cfg.assoc_dim > 0
+                                 ? cosine_exact(map->A[a].data(), map->A[b].data(), map->cfg.assoc_dim) >= cfg->tau_cos
+                                 : cosine_exact(map->E[a].data(), map->E[b].data(), D) >= cfg->tau_cos;
+        if (!similar) continue;
         const int32_t ra = find_root(uf, a), rb = find_root(uf, b);
         if (ra != rb) uf[std::max(ra, rb)] = std::min(ra, rb);
     }
@@ -735,6 +779,7 @@ int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_f
         if (w >= 0 && w != c) {
             map->Q[c] = map->Q[w];
             map->E[c] = map->E[w];
+            if (map->cfg.assoc_dim > 0) map->A[c] = map->A[w];
         }
     }
     for (int32_t i = 0; i < nid; i++) map->parent[i] = map->parent[map->parent[i]];  // flat again
@@ -773,7 +818,34 @@ void oracle_set_state(oracle_map* map, const uint64_t* keys, const int32_t* labe
     map->n_obs.assign(n_obs, n_obs + nid);
     map->E.assign(nid, std::vector<float>(D));
     for (int32_t i = 0; i < nid; i++) std::memcpy(map->E[i].data(), E + (size_t)i * D, sizeof(float) * D);
+    map->A.assign(map->cfg.assoc_dim > 0 ? nid : 0, std::vector<float>(std::max(map->cfg.assoc_dim, 0)));
     map->final_ = false;
+}
+
+void oracle_set_assoc(oracle_map* map, const float* A, int32_t nid)
+{
+    const int Da = map->cfg.assoc_dim;
+    if (Da <= 0) return;
+    map->A.assign(nid, std::vector<float>(Da));
+    for (int32_t i = 0; i < nid; i++) std::memcpy(map->A[i].data(), A + (size_t)i * Da, sizeof(float) * Da);
+}
+
+void oracle_export_assoc(const oracle_map* map, float* A)
+{
+    const int Da = map->cfg.assoc_dim;
+    for (size_t i = 0; i < map->A.size() && Da > 0; i++) std::memcpy(A + i * Da, map->A[i].data(), sizeof(float) * Da);
+}
+
+// Fig. 2: Eq. 1 on the grid with the query in the place of the global
+// embedding gives D_p and cos(f_p, q); the heatmap is their product.
+int oracle_query_heatmap(const float* F, int32_t P, int32_t D, const float* q, float eps, float* heat)
+{
+    if (!F || !q || !heat || P <= 0 || D <= 0) return ORACLE_ERR_INVALID_ARG;
+    std::vector<float> Dp(P), c(P);
+    const int st = oracle_token_stats(F, P, D, q, eps, nullptr, nullptr, Dp.data(), c.data());
+    if (st != ORACLE_OK) return st;
+    for (int p = 0; p < P; p++) heat[p] = Dp[p] * c[p];
+    return ORACLE_OK;
 }
 
 // ---- FP64 twin of Eq. 1 and the pooling (error statements only) ---------------

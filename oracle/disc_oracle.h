@@ -37,6 +37,11 @@ typedef struct {
     float dbscan_eps;        /* > 0: per-segment DBSCAN denoise before voxelisation (radius, metres) */
     int32_t dbscan_min_pts;  /* core point: at least this many points of its segment within eps */
     int32_t overlap_dilation;/* 1: a segment voxel also overlaps the instances of its 26 neighbours */
+    int32_t assoc_dim;       /* > 0: a second token grid [assoc_patch_h * assoc_patch_w][assoc_dim]
+                                drives association (Sec. III-A/B: DINOv2 tokens for tracking, CLIP
+                                tokens for the stored embedding); its pooled feature per mask is the
+                                pixel-level mean over the mask (w_p = c_p / |M|) */
+    int32_t assoc_patch_h, assoc_patch_w;
 } oracle_config;
 
 typedef struct {
@@ -48,6 +53,7 @@ typedef struct {
     const float* tokens;       /* [Ph*Pw][D] */
     int32_t num_masks;
     const float* global_embed; /* [D] or NULL (then the mean token) */
+    const float* assoc_tokens; /* [assoc_patch_h * assoc_patch_w][assoc_dim] when assoc_dim > 0 */
 } oracle_frame;
 
 /* Per-frame intermediates; every pointer is optional (NULL = not wanted).
@@ -70,6 +76,7 @@ typedef struct {
     int32_t valid_pixels, dropped_pixels, new_voxels, active_instances;
     int32_t new_instances, merges, live_segments, overlap_pairs;
     int32_t denoised_pixels;   /* pixels DBSCAN marked as noise */
+    float* A;           /* [M][assoc_dim] pooled association features (assoc_dim > 0) */
 } oracle_report;
 
 enum { ORACLE_OK = 0, ORACLE_ERR_INVALID_ARG = -1, ORACLE_ERR_RANGE = -7 };
@@ -89,12 +96,21 @@ int32_t oracle_num_ids(const oracle_map* map);
 void oracle_export_instances(const oracle_map* map, int32_t* parent, int64_t* count, float* Q,
                              float* E, int32_t* n_obs);
 
+/* Per id: the association feature [assoc_dim] (assoc_dim > 0). */
+void oracle_export_assoc(const oracle_map* map, float* A);
+
+/* Fig. 2: the distinctiveness-weighted cosine heatmap of a query vector q [D]
+ * over a token grid [P][D]: heat_p = D_p * cos(f_p, q), D_p of Eq. 1 and the
+ * exact cosine, their product rounded once to fp32. */
+int oracle_query_heatmap(const float* F, int32_t P, int32_t D, const float* q, float eps, float* heat);
+
 /* End of the trajectory (Sec. III-B, last paragraph): merge the remaining
  * orphaned candidates, then drop instances below a voxel count.  Reading:
  *   contact(a, b) = number of voxels of a or b with a face neighbour (one of
  *                   the 6 voxels sharing a face) in the other instance;
  *   a and b merge when contact * contact_den >= contact_num * min(|a|, |b|)
- *   and the exact cosine of their embeddings is >= tau_cos (counts and
+ *   and the exact cosine of their embeddings (the association features when
+ *   the map has a second token grid) is >= tau_cos (counts and
  *   embeddings as they stand when finalisation starts); merges are
  *   transitive, the smallest id represents a component, whose Q and
  *   embedding are those of its member with the highest Q (ties: smallest id)
@@ -122,6 +138,8 @@ int oracle_finalize(oracle_map* map, const oracle_finalize_config* cfg, oracle_f
 void oracle_set_state(oracle_map* map, const uint64_t* keys, const int32_t* labels, int64_t n,
                       const int32_t* parent, const int64_t* count, const float* Q, const float* E,
                       const int32_t* n_obs, int32_t nid);
+/* With a second token grid: the association features [nid][assoc_dim]. */
+void oracle_set_assoc(oracle_map* map, const float* A, int32_t nid);
 
 /* DBSCAN noise of Sec. III-A (the step between back-projection and
  * voxelisation), per segment.  Reading: a point is core when at least

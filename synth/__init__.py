@@ -73,6 +73,10 @@ def _load():
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]
+        _lib.synth_assoc_tokens.restype = ctypes.c_int
+        _lib.synth_assoc_tokens.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_void_p]
         _lib.synth_object_mean.restype = None
         _lib.synth_object_mean.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int32, ctypes.c_void_p]
     return _lib
@@ -219,6 +223,20 @@ class Frames:
 
     def __len__(self):
         return int(self.index.shape[0])
+
+    def assoc_tokens(self, patch_h: int, patch_w: int, dim: int) -> np.ndarray:
+        """A second token grid [n, patch_h * patch_w, dim] (the association
+        encoder's): per-object means and noise of their own, same recipe."""
+        out = np.zeros((len(self), patch_h * patch_w, dim), np.float32)
+        s, keep = self.scene._cscene(grid=False)
+        ids = np.ascontiguousarray(self.ids, np.int32)
+        idx = np.ascontiguousarray(self.index, np.int64)
+        rc = _load().synth_assoc_tokens(ctypes.byref(s), len(self), idx.ctypes.data, ids.ctypes.data,
+                                        patch_h, patch_w, dim, out.ctypes.data)
+        del keep
+        if rc != 0:
+            raise RuntimeError(f"synth_assoc_tokens failed: {rc}")
+        return out
 
 
 def look_at(eye, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:

@@ -75,7 +75,7 @@ static double normal4(uint64_t seed, uint64_t a, uint64_t b, uint64_t c)
     return (s - 2.0) * 1.7320508075688772; /* sqrt(12/4) */
 }
 
-enum { STREAM_MEAN = 1, STREAM_TOKEN = 2, STREAM_DEPTH = 3 };
+enum { STREAM_MEAN = 1, STREAM_TOKEN = 2, STREAM_DEPTH = 3, STREAM_AMEAN = 4, STREAM_ATOKEN = 5 };
 
 /* ---- ray casting --------------------------------------------------------- */
 static int hit_box(const synth_prim* p, const double o[3], const double d[3], double* t_out)
@@ -249,11 +249,12 @@ static int32_t make_masks(const synth_scene* s, const int32_t* ids, uint16_t* la
     return nm;
 }
 
-/* Patch tokens: the object at the patch-centre pixel picks the mean vector
- * (id 0 = background mean), plus independent noise per (frame, patch, dim). */
-static void make_tokens(const synth_scene* s, uint64_t frame, const int32_t* ids, float* tokens)
+/* Patch tokens of a Ph x Pw x Dd grid: the object at the patch-centre pixel
+ * picks the mean vector (id 0 = background mean) of stream sm, plus
+ * independent noise per (frame, patch, dim) of stream st. */
+static void grid_tokens(const synth_scene* s, int Ph, int Pw, int Dd, int sm, int st, uint64_t frame,
+                        const int32_t* ids, float* tokens)
 {
-    const int Ph = s->patch_h, Pw = s->patch_w, Dd = s->dim;
     for (int i = 0; i < Ph; i++) {
         for (int j = 0; j < Pw; j++) {
             int vc = ((2 * i + 1) * s->height) / (2 * Ph);
@@ -262,12 +263,17 @@ static void make_tokens(const synth_scene* s, uint64_t frame, const int32_t* ids
             size_t p = (size_t)i * Pw + j;
             float* out = tokens + p * Dd;
             for (int d = 0; d < Dd; d++) {
-                double mu = normal4(s->seed, STREAM_MEAN, (uint64_t)id, (uint64_t)d);
-                double nz = normal4(s->seed, STREAM_TOKEN, frame * 1000003ull + p, (uint64_t)d);
+                double mu = normal4(s->seed, sm, (uint64_t)id, (uint64_t)d);
+                double nz = normal4(s->seed, st, frame * 1000003ull + p, (uint64_t)d);
                 out[d] = (float)(mu + s->token_noise * nz);
             }
         }
     }
+}
+
+static void make_tokens(const synth_scene* s, uint64_t frame, const int32_t* ids, float* tokens)
+{
+    grid_tokens(s, s->patch_h, s->patch_w, s->dim, STREAM_MEAN, STREAM_TOKEN, frame, ids, tokens);
 }
 
 /*
@@ -301,6 +307,21 @@ int synth_render(const synth_scene* s, int32_t n, const double* poses, const int
         free(counts);
     }
     return err;
+}
+
+/* A second token grid (the association encoder's) of n rendered frames from
+ * their id images [n][H][W]: per-object means and noise from streams of
+ * their own.  out: [n][Ph*Pw][Dd]. */
+int synth_assoc_tokens(const synth_scene* s, int32_t n, const int64_t* frame_ids, const int32_t* id_image,
+                       int32_t Ph, int32_t Pw, int32_t Dd, float* out)
+{
+    if (!s || n < 0 || Ph <= 0 || Pw <= 0 || Dd <= 0) return -1;
+    const size_t npx = (size_t)s->width * s->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t f = 0; f < n; f++)
+        grid_tokens(s, Ph, Pw, Dd, STREAM_AMEAN, STREAM_ATOKEN, (uint64_t)frame_ids[f], id_image + npx * f,
+                    out + (size_t)Ph * Pw * Dd * f);
+    return 0;
 }
 
 /* Object mean vector (the noiseless token of an object), for query tests. */
