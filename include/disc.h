@@ -94,6 +94,15 @@ typedef struct {
     int32_t overlap_dilation;/* 1: a segment voxel also overlaps the instances labelling any of its 26
                                 neighbours (the "immediate neighborhood" of Sec. III-B), once per
                                 instance; 0 (default): the voxel itself only */
+    int32_t assoc_dim;       /* > 0: frames carry a second token grid [assoc_patch_h * assoc_patch_w]
+                                [assoc_dim] (the association encoder's, e.g. DINOv2, Sec. III-A)
+                                that drives association: each mask's association feature is the
+                                pixel-level mean of that grid's tokens over the mask, the cosine
+                                gate (and disc_map_finalize) compares those features, and each
+                                instance keeps one, replaced with its embedding when a better view
+                                wins the fusion; Eq. 1, the quality terms, the stored embedding
+                                and the queries stay on the first grid (CLIP).  0: one grid */
+    int32_t assoc_patch_h, assoc_patch_w; /* the second grid; product <= 16384; assoc_dim <= 4096 */
 } disc_map_config;
 
 typedef struct {
@@ -107,6 +116,8 @@ typedef struct {
     int32_t num_masks;       /* labels above num_masks count as background */
     const float* global_embed; /* [D] global image embedding, or NULL -> mean token */
     int32_t inputs_on_device;  /* 1: pointers are device memory; 0: host memory */
+    const void* assoc_tokens;  /* [assoc_patch_h*assoc_patch_w][assoc_dim] (token_dtype) when the
+                                  map has a second grid; else ignored */
 } disc_frame;
 
 typedef struct {
@@ -144,7 +155,10 @@ typedef struct {
     int64_t seg_cap;
     int64_t n_seg;      /* out: number of pairs */
     int32_t num_masks;  /* out */
-    float* E_bound;     /* [M] the bound of ||E_fast - E|| the association gate's re-score band uses */
+    float* E_bound;     /* [M] the bound of ||E_fast - E|| the association gate's re-score band uses
+                           (of ||A_fast - A|| with a second grid) */
+    float* A;           /* [M][assoc_dim] association features, exact path (second grid) */
+    float* A_fast;      /* [M][assoc_dim] association features, tensor-core path (second grid) */
 } disc_frame_report;
 
 /* Fills a config with the defaults used throughout (eps 1e-6, tau_cos 0.75,
@@ -192,6 +206,8 @@ typedef struct {
     void* cuda_stream;       /* cudaStream_t, or NULL: the group creates one */
     int32_t device;
     int32_t serial_sms;      /* as in disc_map_config */
+    int32_t assoc_dim, assoc_patch_h, assoc_patch_w; /* the second grid of maps that have one (0: none);
+                                                        such maps need a group with the same grid */
 } disc_group_config;
 
 /* Defaults: 16 maps x 4 frames, 640x480, 24x24x768, 40 masks. */
@@ -305,6 +321,10 @@ disc_status disc_query_points(disc_map* map, const float* xyz, int64_t n, int32_
  * arrays cover ids 0..num_ids-1 (parent[i] == i marks a live instance). */
 disc_status disc_map_counts(disc_map* map, int64_t* num_voxels, int32_t* num_ids);
 disc_status disc_map_export_voxels(disc_map* map, uint64_t* keys, int32_t* ids, int64_t cap);
+/* The association feature [assoc_dim] of every id 0..num_ids-1 (maps with a
+ * second grid), into a host buffer of cap rows. */
+disc_status disc_map_export_assoc(disc_map* map, float* A, int32_t cap);
+
 disc_status disc_map_export_instances(disc_map* map, int32_t* parent, int64_t* count, float* Q,
                                       float* E, int32_t* n_obs, int32_t cap);
 
@@ -335,6 +355,15 @@ disc_status disc_map_load(const char* path, const disc_map_config* cfg_override,
 disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
                                     const float* global_embed, float eps, float* Dp, float* cosg,
                                     void* cuda_stream);
+
+/* Fig. 2: the distinctiveness-weighted cosine heatmap of a query vector over a
+ * frame's token grid, heat_p = D_p * cos(f_p, q): D_p of Eq. 1 and the exact
+ * cosine, their product rounded once to fp32 (the heatmap the paper shows for
+ * a text query).  Arguments and the shared allocation-free working set as in
+ * disc_token_stats_static, with q [D] (device memory) in the place of the
+ * global embedding and heat [P] (device memory) written. */
+disc_status disc_query_heatmap(const void* tokens, int32_t token_dtype, int32_t P, int32_t D, const float* query,
+                               float eps, float* heat, void* cuda_stream);
 
 /* End of the trajectory (Sec. III-B, last paragraph): merge the remaining
  * orphaned candidates, then drop noisy instances below a voxel count.  The

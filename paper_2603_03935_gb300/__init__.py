@@ -6,7 +6,7 @@ names; it only marshals arguments.  There is no CPU fallback: when the library
 is missing, loading fails loudly.
 """
 from .binding import (DiscError, DiscGroup, DiscMap, DiscServer, config_default, device_frame, host_frame, lib, pack_key,
-                      status_str, token_stats_static)
+                      query_heatmap, status_str, token_stats_static)
 
 __all__ = ["DiscError", "DiscGroup", "DiscMap", "DiscServer", "config_default", "device_frame", "host_frame", "lib",
-           "pack_key", "status_str", "token_stats_static"]
+           "pack_key", "query_heatmap", "status_str", "token_stats_static"]

@@ -30,14 +30,15 @@ class Config(ctypes.Structure):
                 ("min_mask_pixels", c_i32), ("voxel_capacity", c_i64), ("max_load", c_f32),
                 ("instance_capacity", c_i32), ("precision", c_i32), ("cuda_stream", c_vp),
                 ("device", c_i32), ("batch_frames", c_i32), ("dbscan_eps", c_f32), ("dbscan_min_pts", c_i32),
-                ("serial_sms", c_i32), ("overlap_dilation", c_i32)]
+                ("serial_sms", c_i32), ("overlap_dilation", c_i32), ("assoc_dim", c_i32),
+                ("assoc_patch_h", c_i32), ("assoc_patch_w", c_i32)]
 
 
 class Frame(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32),
                 ("cy", c_f32), ("T_world_cam", c_f64 * 16), ("depth", c_vp), ("labels", c_vp),
                 ("tokens", c_vp), ("token_dtype", c_i32), ("num_masks", c_i32),
-                ("global_embed", c_vp), ("inputs_on_device", c_i32)]
+                ("global_embed", c_vp), ("inputs_on_device", c_i32), ("assoc_tokens", c_vp)]
 
 
 class Stats(ctypes.Structure):
@@ -53,7 +54,8 @@ class Stats(ctypes.Structure):
 class GroupConfig(ctypes.Structure):
     _fields_ = [("max_maps", c_i32), ("frames_per_map", c_i32), ("embed_dim", c_i32), ("patch_h", c_i32),
                 ("patch_w", c_i32), ("max_width", c_i32), ("max_height", c_i32), ("max_masks", c_i32),
-                ("cuda_stream", c_vp), ("device", c_i32), ("serial_sms", c_i32)]
+                ("cuda_stream", c_vp), ("device", c_i32), ("serial_sms", c_i32), ("assoc_dim", c_i32),
+                ("assoc_patch_h", c_i32), ("assoc_patch_w", c_i32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -78,7 +80,7 @@ class Report(ctypes.Structure):
     _fields_ = [("fbar", c_vp), ("Dp", c_vp), ("cosg", c_vp), ("cov", c_vp), ("npix", c_vp), ("W", c_vp),
                 ("E", c_vp), ("E_fast", c_vp), ("S", c_vp), ("nvox", c_vp), ("rep", c_vp),
                 ("seg_keys", c_vp), ("seg_m", c_vp), ("seg_cap", c_i64), ("n_seg", c_i64),
-                ("num_masks", c_i32), ("E_bound", c_vp)]
+                ("num_masks", c_i32), ("E_bound", c_vp), ("A", c_vp), ("A_fast", c_vp)]
 
 
 _lib = None
@@ -119,6 +121,10 @@ def lib():
         L.disc_phase_name.restype = ctypes.c_char_p
         L.disc_token_stats_static.argtypes = [c_vp, c_i32, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp, c_vp]
         L.disc_token_stats_static.restype = ctypes.c_int
+        L.disc_query_heatmap.argtypes = [c_vp, c_i32, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp]
+        L.disc_query_heatmap.restype = ctypes.c_int
+        L.disc_map_export_assoc.argtypes = [c_vp, c_vp, c_i32]
+        L.disc_map_export_assoc.restype = ctypes.c_int
         L.disc_map_device_bytes.argtypes = [c_vp]
         L.disc_map_device_bytes.restype = c_i64
         L.disc_map_destroy.argtypes = [c_vp]
@@ -190,8 +196,9 @@ def _fill_frame(fr: Frame, width, height, intr, pose):
         fr.T_world_cam[i] = float(v)
 
 
-def host_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None):
-    """A disc_frame over host numpy arrays (kept alive by the returned tuple)."""
+def host_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None, assoc_tokens=None):
+    """A disc_frame over host numpy arrays (kept alive by the returned tuple);
+    assoc_tokens: the second token grid, same dtype as tokens."""
     depth = np.ascontiguousarray(depth, np.float32)
     labels = np.ascontiguousarray(labels, np.uint16)
     if tokens.dtype == np.float32:
@@ -208,10 +215,14 @@ def host_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None):
     fr.num_masks = int(num_masks)
     fr.global_embed = None if g is None else g.ctypes.data
     fr.inputs_on_device = 0
-    return fr, (depth, labels, tokens, g)
+    at = None
+    if assoc_tokens is not None:
+        at = np.ascontiguousarray(assoc_tokens, tokens.dtype)
+        fr.assoc_tokens = at.ctypes.data
+    return fr, (depth, labels, tokens, g, at)
 
 
-def device_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None):
+def device_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None, assoc_tokens=None):
     """A disc_frame over device tensors (torch CUDA tensors or raw pointers).
 
     depth: float32 [H, W]; labels: int16/uint16 [H, W]; tokens: float32 or
@@ -225,7 +236,9 @@ def device_frame(depth, labels, tokens, pose, intr, num_masks, global_embed=None
     fr.num_masks = int(num_masks)
     fr.global_embed = None if global_embed is None else global_embed.data_ptr()
     fr.inputs_on_device = 1
-    return fr, (depth, labels, tokens, global_embed)
+    if assoc_tokens is not None:
+        fr.assoc_tokens = assoc_tokens.data_ptr()
+    return fr, (depth, labels, tokens, global_embed, assoc_tokens)
 
 
 def token_stats_static(tokens, global_embed=None, eps=1e-6, stream=None):
@@ -242,6 +255,20 @@ def token_stats_static(tokens, global_embed=None, eps=1e-6, stream=None):
                                        Dp.data_ptr(), cosg.data_ptr(), s.cuda_stream)
     _check(rc, "disc_token_stats_static")
     return Dp, cosg
+
+
+def query_heatmap(tokens, query, eps=1e-6, stream=None):
+    """Fig. 2 heatmap D_p * cos(f_p, q) of a query vector (CUDA tensor [D])
+    over a token grid (CUDA tensor [P, D], fp32 or bf16); no device allocation
+    in the library.  Returns a new CUDA tensor [P]."""
+    import torch
+    P, D = tokens.shape
+    heat = torch.empty(P, dtype=torch.float32, device=tokens.device)
+    s = torch.cuda.current_stream(tokens.device) if stream is None else stream
+    rc = lib().disc_query_heatmap(tokens.data_ptr(), 1 if tokens.dtype == torch.bfloat16 else 0, P, D,
+                                  query.data_ptr(), float(eps), heat.data_ptr(), s.cuda_stream)
+    _check(rc, "disc_query_heatmap")
+    return heat
 
 
 class DiscMap:
@@ -315,16 +342,22 @@ class DiscMap:
                    nvox=np.zeros(max(M_cap, 1), np.int32), rep=np.zeros(max(M_cap, 1), np.int32),
                    seg_keys=np.zeros(npx, np.uint64), seg_m=np.zeros(npx, np.int32),
                    E_bound=np.zeros(max(M_cap, 1), np.float32))
+        Da = int(self.cfg.get("assoc_dim", 0))
+        if Da > 0:
+            out["A"] = np.zeros((max(M_cap, 1), Da), np.float32)
+            out["A_fast"] = np.zeros((max(M_cap, 1), Da), np.float32)
         r = Report()
         for k in ("fbar", "Dp", "cosg", "cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "seg_keys", "seg_m",
-                  "E_bound"):
-            setattr(r, k, out[k].ctypes.data)
+                  "E_bound", "A", "A_fast"):
+            if k in out:
+                setattr(r, k, out[k].ctypes.data)
         r.seg_cap = npx
         _check(lib().disc_map_last_frame(self._h, ctypes.byref(r)), "disc_map_last_frame")
         M = int(r.num_masks)
         n = int(r.n_seg)
-        for k in ("cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "E_bound"):
-            out[k] = out[k][:M]
+        for k in ("cov", "npix", "W", "E", "E_fast", "S", "nvox", "rep", "E_bound", "A", "A_fast"):
+            if k in out:
+                out[k] = out[k][:M]
         order = np.lexsort((out["seg_keys"][:n], out["seg_m"][:n]))
         out["seg_keys"] = out["seg_keys"][:n][order]
         out["seg_m"] = out["seg_m"][:n][order]
@@ -353,7 +386,13 @@ class DiscMap:
         obs = np.zeros(max(n, 1), np.int32)
         _check(lib().disc_map_export_instances(self._h, parent.ctypes.data, count.ctypes.data, Q.ctypes.data,
                                                 E.ctypes.data, obs.ctypes.data, n), "export_instances")
-        return dict(parent=parent[:n], count=count[:n], Q=Q[:n], E=E[:n], n_obs=obs[:n])
+        out = dict(parent=parent[:n], count=count[:n], Q=Q[:n], E=E[:n], n_obs=obs[:n])
+        Da = int(self.cfg.get("assoc_dim", 0))
+        if Da > 0:
+            A = np.zeros((max(n, 1), Da), np.float32)
+            _check(lib().disc_map_export_assoc(self._h, A.ctypes.data, max(n, 1)), "export_assoc")
+            out["A"] = A[:n]
+        return out
 
     def query_topk(self, queries, k):
         q = np.ascontiguousarray(queries, np.float32).reshape(-1, self.D)

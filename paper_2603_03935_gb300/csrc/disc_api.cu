@@ -110,6 +110,14 @@ struct Runner {
     uint16_t* d_labels = nullptr;
     unsigned char* d_tokens = nullptr;
     float* d_gembed = nullptr;
+    // The second token grid (association features), when the runner serves
+    // maps that have one: a second view of the feature kernels, with its own
+    // FrameParams per slot in the parameter block and its own slot scratch
+    // (sharing the primary slots' counters).
+    int Da = 0, Pha = 0, Pwa = 0, Pa = 0, Kpad_a = 0;
+    BatchScratch bsa[2] = {};
+    size_t off_fpa = 0;
+    unsigned char* d_atok = nullptr;  // staging of host association tokens (two sets)
     bool graphs_off = false;
     std::map<long long, BatchGraph> graphs;
     std::map<long long, int> shapes_seen;  // batch shapes launched directly so far
@@ -131,6 +139,7 @@ struct Runner {
     const FrameParams* fps(int k) const { return (const FrameParams*)d_param[k]; }
     const MapRefs* refs(int k) const { return (const MapRefs*)(d_param[k] + off_refs); }
     const int* slot_of(int k) const { return (const int*)(d_param[k] + off_slot); }
+    const FrameParams* fpa(int k) const { return (const FrameParams*)(d_param[k] + off_fpa); }
     const int* prev_hist(int k) const { return (const int*)(d_param[k] + off_prev); }
 };
 
@@ -190,6 +199,11 @@ bool config_ok(const disc_map_config& c)
     if (c.batch_frames < 0 || c.batch_frames > 256) return false;
     if (c.precision != DISC_FP32 && c.precision != DISC_BF16 && c.precision != DISC_FP8_E4M3) return false;
     if (c.overlap_dilation != 0 && c.overlap_dilation != 1) return false;
+    if (c.assoc_dim < 0 || c.assoc_dim > 4096) return false;
+    if (c.assoc_dim > 0 && (c.assoc_patch_h <= 0 || c.assoc_patch_w <= 0 ||
+                            (int64_t)c.assoc_patch_h * c.assoc_patch_w > 16384 ||
+                            coverage_smem_bytes(c.max_masks, c.assoc_patch_w) > 200 * 1024))
+        return false;
     // DBSCAN cells at least a voxel wide keep cell coordinates in key range
     if (!(c.dbscan_eps >= 0.0f) || (c.dbscan_eps > 0.0f && (c.dbscan_eps < c.voxel_size || c.dbscan_min_pts < 1)))
         return false;
@@ -289,8 +303,13 @@ bool make_green_streams(Runner& r)
 }
 
 disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int Ph, int Pw, int Hmax, int Wmax,
-                        int Mmax, int Gmax, int Jmax, int serial_sms)
+                        int Mmax, int Gmax, int Jmax, int serial_sms, int Da, int Pha, int Pwa)
 {
+    r.Da = Da > 0 ? Da : 0;
+    r.Pha = r.Da ? Pha : 0;
+    r.Pwa = r.Da ? Pwa : 0;
+    r.Pa = r.Pha * r.Pwa;
+    r.Kpad_a = (r.Pa + GEMM_KC - 1) / GEMM_KC * GEMM_KC;
     r.device = device;
     r.serial_sms = serial_sms == 0 ? -1 : serial_sms;  // overlap only on request: measured slower here
     r.stream = stream;
@@ -315,7 +334,8 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     r.off_refs = align256(sizeof(FrameParams) * B);
     r.off_slot = r.off_refs + align256(sizeof(MapRefs) * Gmax);
     r.off_prev = r.off_slot + align256(sizeof(int) * Gmax * Jmax);
-    r.param_bytes = r.off_prev + align256(sizeof(int) * Gmax);
+    r.off_fpa = r.off_prev + align256(sizeof(int) * Gmax);
+    r.param_bytes = r.off_fpa + (r.Da ? align256(sizeof(FrameParams) * B) : 0);
     for (int k = 0; k < 2; k++) {
         r.d_param[k] = a.get<unsigned char>(r.param_bytes);
         BatchScratch& bs = r.bs[k];
@@ -368,6 +388,49 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     r.d_tokens = a.get<unsigned char>((size_t)2 * B * P * D * 4);
     r.d_gembed = a.get<float>((size_t)2 * B * D);
     r.d_room = a.get<unsigned long long>((size_t)2 * Gmax);
+    if (r.Da) {
+        // the second grid's view: the feature kernels' arrays at its sizes;
+        // the counters are the primary slots' own
+        const int Da_ = r.Da, Pa = r.Pa, Ka = r.Kpad_a;
+        r.d_atok = a.get<unsigned char>((size_t)2 * B * Pa * Da_ * 4);
+        for (int k = 0; k < 2; k++) {
+            BatchScratch& v = r.bsa[k];
+            v.sD = Da_;
+            v.sP = Pa;
+            v.sMM = MM;
+            v.sMMP = (long long)MM * Pa;
+            v.sW = (long long)r.Npad_max * Ka;
+            v.sMMD = (long long)MM * Da_;
+            v.sS = 5LL * MM;
+            v.sK = Ka;
+            Scratch& sc = v.base;
+            sc.sumF = a.get<long long>((size_t)B * Da_);
+            sc.fbar = a.get<float>((size_t)B * Da_);
+            sc.gvec = a.get<float>((size_t)B * Da_);
+            sc.gg = a.get<long long>(B);
+            sc.nsum = a.get<long long>(B);
+            sc.dotg = a.get<long long>((size_t)B * Pa);
+            sc.ffp = a.get<long long>((size_t)B * Pa);
+            sc.nrm = a.get<float>((size_t)B * Pa);
+            sc.Dp = a.get<float>((size_t)B * Pa);
+            sc.cosg = a.get<float>((size_t)B * Pa);
+            sc.fnorm = a.get<float>((size_t)B * Pa);
+            sc.qexp = a.get<int32_t>((size_t)B * Pa);
+            sc.qmul = a.get<float>((size_t)B * Ka);
+            sc.qerr = a.get<float>((size_t)B * Pa);
+            sc.qnrm = a.get<float>((size_t)B * Pa);
+            sc.qexpm = a.get<int32_t>((size_t)B * MM);
+            sc.W8 = a.get<uint8_t>((size_t)B * v.sW);
+            sc.cov = a.get<int32_t>((size_t)B * MM * Pa);
+            sc.npix = a.get<int32_t>((size_t)B * MM);
+            sc.W = a.get<float>((size_t)B * v.sW);
+            sc.S = a.get<float>((size_t)B * 5 * MM);
+            sc.Bm = a.get<float>((size_t)B * MM);
+            sc.Ecan = a.get<float>((size_t)B * MM * Da_);
+            sc.Efast = a.get<float>((size_t)B * MM * Da_);
+            sc.ctr = r.bs[k].base.ctr;
+        }
+    }
     if (a.failed) return DISC_ERR_OOM;
     // Pipelined batches put the serial part (a latency-bound chain of small
     // launches) on its own partition of serial_sms SMs and the stateless part
@@ -404,6 +467,15 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
         CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
         CK(cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s));
+        if (r.Da) {
+            const BatchScratch& v = r.bsa[k];
+            CK(cudaMemsetAsync(v.base.W, 0, sizeof(float) * (size_t)B * v.sW, s));
+            CK(cudaMemsetAsync(v.base.W8, 0, (size_t)B * v.sW, s));
+            CK(cudaMemsetAsync(v.base.qmul, 0, sizeof(float) * (size_t)B * r.Kpad_a, s));
+            CK(cudaMemsetAsync(v.base.qexpm, 0, sizeof(int32_t) * (size_t)B * MM, s));
+            CK(cudaMemsetAsync(v.base.Ecan, 0, sizeof(float) * (size_t)B * MM * r.Da, s));
+            CK(cudaMemsetAsync(v.base.Efast, 0, sizeof(float) * (size_t)B * MM * r.Da, s));
+        }
     }
     return cuda_status(cudaStreamSynchronize(s));
 }
@@ -530,8 +602,13 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
     in.count = m->mem.get<long long>(cap);
     in.Q = m->mem.get<float>(cap);
     in.E = m->mem.get<float>((size_t)cap * m->D);
-    in.Eb = m->cfg.precision == DISC_BF16 ? m->mem.get<uint16_t>((size_t)cap * m->D) : nullptr;
-    in.E8 = m->cfg.precision == DISC_FP8_E4M3 ? m->mem.get<uint8_t>((size_t)cap * m->D) : nullptr;
+    // the scoring copies are copies of the association features when the map
+    // has a second grid, else of E
+    const int Da = m->cfg.assoc_dim, Ds = Da > 0 ? Da : m->D;
+    in.Da = Da;
+    in.A = Da > 0 ? m->mem.get<float>((size_t)cap * Da) : nullptr;
+    in.Eb = m->cfg.precision == DISC_BF16 ? m->mem.get<uint16_t>((size_t)cap * Ds) : nullptr;
+    in.E8 = m->cfg.precision == DISC_FP8_E4M3 ? m->mem.get<uint8_t>((size_t)cap * Ds) : nullptr;
     in.Er = m->cfg.precision == DISC_FP8_E4M3 ? m->mem.get<float>(cap) : nullptr;
     in.n_obs = m->mem.get<int32_t>(cap);
     if (m->mem.failed) {
@@ -540,8 +617,9 @@ disc_status alloc_instances(disc_map* m, int cap, Instances* out)
         if (in.count) m->mem.release(in.count, sizeof(long long) * cap);
         if (in.Q) m->mem.release(in.Q, sizeof(float) * cap);
         if (in.E) m->mem.release(in.E, sizeof(float) * (size_t)cap * m->D);
-        if (in.Eb) m->mem.release(in.Eb, sizeof(uint16_t) * (size_t)cap * m->D);
-        if (in.E8) m->mem.release(in.E8, (size_t)cap * m->D);
+        if (in.A) m->mem.release(in.A, sizeof(float) * (size_t)cap * Da);
+        if (in.Eb) m->mem.release(in.Eb, sizeof(uint16_t) * (size_t)cap * Ds);
+        if (in.E8) m->mem.release(in.E8, (size_t)cap * Ds);
         if (in.Er) m->mem.release(in.Er, sizeof(float) * cap);
         if (in.n_obs) m->mem.release(in.n_obs, sizeof(int32_t) * cap);
         return DISC_ERR_OOM;
@@ -625,10 +703,12 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     CK(cudaMemcpyAsync(ni.count, m->inst.count, sizeof(long long) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ni.Q, m->inst.Q, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(ni.E, m->inst.E, sizeof(float) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+    const int Ds = scoring_dim(ni, m->D);
+    if (ni.A) CK(cudaMemcpyAsync(ni.A, m->inst.A, sizeof(float) * (size_t)n * ni.Da, cudaMemcpyDeviceToDevice, st));
     if (ni.Eb)
-        CK(cudaMemcpyAsync(ni.Eb, m->inst.Eb, sizeof(uint16_t) * (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ni.Eb, m->inst.Eb, sizeof(uint16_t) * (size_t)n * Ds, cudaMemcpyDeviceToDevice, st));
     if (ni.E8) {
-        CK(cudaMemcpyAsync(ni.E8, m->inst.E8, (size_t)n * m->D, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ni.E8, m->inst.E8, (size_t)n * Ds, cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(ni.Er, m->inst.Er, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     }
     CK(cudaMemcpyAsync(ni.n_obs, m->inst.n_obs, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
@@ -638,8 +718,9 @@ disc_status ensure_instance_room(disc_map* m, int64_t incoming, cudaStream_t st)
     m->mem.release(m->inst.count, sizeof(long long) * oc);
     m->mem.release(m->inst.Q, sizeof(float) * oc);
     m->mem.release(m->inst.E, sizeof(float) * (size_t)oc * m->D);
-    if (m->inst.Eb) m->mem.release(m->inst.Eb, sizeof(uint16_t) * (size_t)oc * m->D);
-    if (m->inst.E8) m->mem.release(m->inst.E8, (size_t)oc * m->D);
+    if (m->inst.A) m->mem.release(m->inst.A, sizeof(float) * (size_t)oc * m->inst.Da);
+    if (m->inst.Eb) m->mem.release(m->inst.Eb, sizeof(uint16_t) * (size_t)oc * Ds);
+    if (m->inst.E8) m->mem.release(m->inst.E8, (size_t)oc * Ds);
     if (m->inst.Er) m->mem.release(m->inst.Er, sizeof(float) * oc);
     m->mem.release(m->inst.n_obs, sizeof(int32_t) * oc);
     m->inst = ni;
@@ -745,8 +826,10 @@ void reset_timing(Runner& r, bool enable)
 // absent voxel is looked up again by k_overlap after the earlier frames.
 
 // combos: bit (3 * token_bf16 + precision) set for every kind of frame in
-// the batch; bit COMBO_DBSCAN: some frame runs the DBSCAN filter
+// the batch; bit COMBO_DBSCAN: some frame runs the DBSCAN filter; bit
+// COMBO_ASSOC: the feature kernels also run on the second grid's view
 constexpr int COMBO_DBSCAN = 1 << 6;
+constexpr int COMBO_ASSOC = 1 << 7;  // some frame's map has a second token grid
 
 int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
 {
@@ -765,6 +848,19 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
     run_phase(r, PH_WEIGHTS, st, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
     run_phase(r, PH_POOL_EXACT, st, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
     run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, st); });
+    if ((combos & COMBO_ASSOC) && r.Da) {
+        // the association features: the same kernels on the second grid's
+        // view (pixel-mean weights; frames of maps without it are inert)
+        const BatchScratch& va = r.bsa[k];
+        const FrameParams* dfa = r.fpa(k);
+        run_phase(r, PH_CLEAR, st, [&] { return launch_view_clear(va, S, r.Da, r.MM, st); });
+        run_phase(r, PH_TOKENS, st, [&] { return launch_token_stats(dfa, va, S, r.Pa, r.Da, any_bf16, any_f32, st); });
+        run_phase(r, PH_COVERAGE, st, [&] { return launch_coverage(dfa, va, S, r.Pha, r.Pwa, Mmax, st); });
+        run_phase(r, PH_WEIGHTS, st, [&] { return launch_weights(dfa, va, S, Mmax, st); });
+        run_phase(r, PH_POOL_EXACT, st,
+                  [&] { return launch_pool_exact(dfa, va, S, r.Pa, r.Da, Mmax, any_bf16, any_f32, st); });
+        run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfa, va, S, r.Da, Mmax, any, st); });
+    }
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
             const int nb = std::min(GEOMETRY_CHUNK, S - f0);
@@ -789,6 +885,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
     step.prev_hist = r.prev_hist(k);
     step.hist = r.d_hist;
     step.J = J;
+    step.view = r.bsa[k];  // zero when the runner has no second grid
     run_phase(r, PH_OVERLAP, st, [&] { return launch_serial_begin(step.refs, G, st); });
     for (int j = 0; j < J; j++) {
         step.j = j;
@@ -800,7 +897,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 
 long long graph_key(int part, int k, int S, int G, int J, int combos)
 {
-    return (((((((long long)S << 11) | G) << 9) | J) << 7 | combos) << 2) | (part << 1) | k;
+    return (((((((long long)S << 11) | G) << 9) | J) << 8 | combos) << 2) | (part << 1) | k;
 }
 
 // A part's kernel sequence captured once per shape and replayed.  A shape
@@ -916,6 +1013,9 @@ disc_status check_frame(const disc_map* m, const Runner& r, const disc_frame* f)
     if (f->num_masks < 0 || f->num_masks > m->cfg.max_masks || f->num_masks > r.Mmax) return DISC_ERR_INVALID_ARG;
     if (f->token_dtype != DISC_TOKENS_F32 && f->token_dtype != DISC_TOKENS_BF16) return DISC_ERR_INVALID_ARG;
     if (!(f->fx != 0.0f) || !(f->fy != 0.0f)) return DISC_ERR_INVALID_ARG;
+    if (m->cfg.assoc_dim > 0 && (!f->assoc_tokens || r.Da != m->cfg.assoc_dim || r.Pha != m->cfg.assoc_patch_h ||
+                                 r.Pwa != m->cfg.assoc_patch_w))
+        return DISC_ERR_INVALID_ARG;
     return DISC_OK;
 }
 
@@ -953,7 +1053,7 @@ void fast_error_terms(int precision, int Kpad, int D, float* eta, float* dot_err
 // array) merge into one larger copy.
 struct CopyList {
     struct Item { char* dst; const char* src; size_t bytes; };
-    std::vector<Item> kind[4];
+    std::vector<Item> kind[5];  // depth, labels, tokens, global embedding, association tokens
     void add(int k, void* dst, const void* src, size_t bytes)
     {
         std::vector<Item>& v = kind[k];
@@ -962,7 +1062,12 @@ struct CopyList {
         else
             v.push_back({(char*)dst, (const char*)src, bytes});
     }
-    bool empty() const { return kind[0].empty() && kind[1].empty() && kind[2].empty() && kind[3].empty(); }
+    bool empty() const
+    {
+        for (const auto& v : kind)
+            if (!v.empty()) return false;
+        return true;
+    }
     disc_status issue(cudaStream_t st)
     {
         for (auto& v : kind) {
@@ -974,8 +1079,10 @@ struct CopyList {
 };
 
 // Host inputs are staged in staging set `set` (copies collected in cl).
+// With a second grid, *outa receives the view of the frame on that grid (for
+// maps without one, an inert view: no tokens, no masks).
 disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int set, int slot, int g,
-                         FrameParams* out, CopyList* cl)
+                         FrameParams* out, FrameParams* outa, CopyList* cl)
 {
     const int P = r.P, D = r.D;
     FrameParams fp{};
@@ -1016,7 +1123,13 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     fp.db_min_pts = m->cfg.dbscan_eps > 0.0f ? m->cfg.dbscan_min_pts : 0;
     fp.db_eps2 = m->cfg.dbscan_eps * m->cfg.dbscan_eps;
     fp.db_inv_cell = m->cfg.dbscan_eps > 0.0f ? 1.0f / (m->cfg.dbscan_eps * 1.001f) : 0.0f;
-    fast_error_terms(m->cfg.precision, r.Kpad, D, &fp.eta, &fp.dot_err);
+    const bool assoc = m->cfg.assoc_dim > 0;
+    fp.assoc = assoc;
+    // the fast score's bounds are those of the features the gate compares
+    if (assoc)
+        fast_error_terms(m->cfg.precision, r.Kpad_a, r.Da, &fp.eta, &fp.dot_err);
+    else
+        fast_error_terms(m->cfg.precision, r.Kpad, D, &fp.eta, &fp.dot_err);
     const size_t npx = (size_t)fp.H * fp.W;
     const size_t tok_bytes = (size_t)P * D * (fp.token_bf16 ? 2 : 4);
     if (f->inputs_on_device) {
@@ -1043,6 +1156,30 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
         }
     }
     *out = fp;
+    if (r.Da) {
+        FrameParams va = fp;
+        va.uniform_w = 1;
+        va.gembed = nullptr;
+        va.D = va.P = va.M = 0;  // inert unless the map has a second grid
+        va.tokens = nullptr;
+        if (assoc) {
+            va.D = r.Da;
+            va.P = r.Pa;
+            va.Ph = r.Pha;
+            va.Pw = r.Pwa;
+            va.Kpad = r.Kpad_a;
+            va.M = fp.M;
+            const size_t abytes = (size_t)r.Pa * r.Da * (fp.token_bf16 ? 2 : 4);
+            if (f->inputs_on_device) {
+                va.tokens = f->assoc_tokens;
+            } else {
+                unsigned char* da = r.d_atok + ((size_t)set * r.S + slot) * r.Pa * r.Da * 4;
+                cl->add(4, da, f->assoc_tokens, abytes);
+                va.tokens = da;
+            }
+        }
+        *outa = va;
+    }
     return DISC_OK;
 }
 
@@ -1165,6 +1302,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 masks += f.num_masks;
                 combos |= 1 << (3 * (f.token_dtype == DISC_TOKENS_BF16) + wk.m->cfg.precision);
                 if (wk.m->cfg.dbscan_eps > 0.0f) combos |= COMBO_DBSCAN;
+                if (wk.m->cfg.assoc_dim > 0) combos |= COMBO_ASSOC;
             }
             // one graph of both parts (phase timing): room from the host bound;
             // otherwise from the device between the parts (room_check)
@@ -1184,6 +1322,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         MapRefs* hrefs = (MapRefs*)(blk.data() + r.off_refs);
         int* hslot = (int*)(blk.data() + r.off_slot);
         int* hprev = (int*)(blk.data() + r.off_prev);
+        FrameParams* hfpa = r.Da ? (FrameParams*)(blk.data() + r.off_fpa) : nullptr;
         int slot = 0;
         CopyList cl;
         // host inputs of this batch go to staging set k once the set's last
@@ -1197,7 +1336,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && s == DISC_OK; j++) {
-                s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, &cl);
+                s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, hfpa ? hfpa + slot : nullptr,
+                                 &cl);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
@@ -1300,7 +1440,7 @@ disc_status map_runner(disc_map* m)
     Runner* r = new Runner();
     disc_status s = runner_init(*r, m->cfg.device, m->stream, m->D, m->cfg.patch_h, m->cfg.patch_w,
                                 m->cfg.max_height, m->cfg.max_width, m->cfg.max_masks, 1, m->cfg.batch_frames,
-                                m->cfg.serial_sms);
+                                m->cfg.serial_sms, m->cfg.assoc_dim, m->cfg.assoc_patch_h, m->cfg.assoc_patch_w);
     if (s != DISC_OK) {
         runner_release(*r);
         delete r;
@@ -1502,12 +1642,21 @@ disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
         if (r->S) CK(cudaMemcpy(r->S, sc.S, sizeof(float) * 5 * M, cudaMemcpyDeviceToHost));
         if (r->nvox) CK(cudaMemcpy(r->nvox, sc.nvox, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
         if (r->rep) CK(cudaMemcpy(r->rep, sc.segrep, sizeof(int32_t) * M, cudaMemcpyDeviceToHost));
+        // with a second grid, the gate's features and their bound are the view's
+        const bool assoc = m->cfg.assoc_dim > 0 && run->Da > 0;
+        const Scratch va = assoc ? run->bsa[run->last_set].frame(run->last_slot) : Scratch{};
         if (r->E_bound) {
             float eta = 0.0f, dot_err = 0.0f;
-            fast_error_terms(m->cfg.precision, m->Kpad, D, &eta, &dot_err);
-            CK(cudaMemcpy(r->E_bound, sc.Bm, sizeof(float) * M, cudaMemcpyDeviceToHost));
+            if (assoc)
+                fast_error_terms(m->cfg.precision, run->Kpad_a, run->Da, &eta, &dot_err);
+            else
+                fast_error_terms(m->cfg.precision, m->Kpad, D, &eta, &dot_err);
+            CK(cudaMemcpy(r->E_bound, assoc ? va.Bm : sc.Bm, sizeof(float) * M, cudaMemcpyDeviceToHost));
             for (int i = 0; i < M; i++) r->E_bound[i] *= eta;
         }
+        if (assoc && r->A) CK(cudaMemcpy(r->A, va.Ecan, sizeof(float) * (size_t)M * run->Da, cudaMemcpyDeviceToHost));
+        if (assoc && r->A_fast)
+            CK(cudaMemcpy(r->A_fast, va.Efast, sizeof(float) * (size_t)M * run->Da, cudaMemcpyDeviceToHost));
     }
     r->n_seg = c.n_entries;
     if (r->seg_keys && r->seg_m && c.n_entries > 0) {
@@ -1556,6 +1705,11 @@ disc_status disc_group_create(const disc_group_config* cfg, disc_group** out)
         return DISC_ERR_INVALID_ARG;
     if (c.max_masks < 0 || c.max_masks > MAX_MASKS || coverage_smem_bytes(c.max_masks, c.patch_w) > 200 * 1024)
         return DISC_ERR_INVALID_ARG;
+    if (c.assoc_dim < 0 || c.assoc_dim > 4096 ||
+        (c.assoc_dim > 0 && (c.assoc_patch_h <= 0 || c.assoc_patch_w <= 0 ||
+                             (int64_t)c.assoc_patch_h * c.assoc_patch_w > 16384 ||
+                             coverage_smem_bytes(c.max_masks, c.assoc_patch_w) > 200 * 1024)))
+        return DISC_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
         cudaGetLastError();
@@ -1575,7 +1729,8 @@ disc_status disc_group_create(const disc_group_config* cfg, disc_group** out)
         g->own_stream = true;
     }
     disc_status s = runner_init(g->run, c.device, st, c.embed_dim, c.patch_h, c.patch_w, c.max_height,
-                                c.max_width, c.max_masks, c.max_maps, c.frames_per_map, c.serial_sms);
+                                c.max_width, c.max_masks, c.max_maps, c.frames_per_map, c.serial_sms, c.assoc_dim,
+                                c.assoc_patch_h, c.assoc_patch_w);
     if (s != DISC_OK) {
         runner_release(g->run);
         if (g->own_stream) cudaStreamDestroy(st);
@@ -1688,6 +1843,17 @@ disc_status disc_map_export_voxels(disc_map* m, uint64_t* keys, int32_t* ids, in
     return DISC_OK;
 }
 
+disc_status disc_map_export_assoc(disc_map* m, float* A, int32_t cap)
+{
+    if (!m || !A || m->cfg.assoc_dim <= 0) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    CK(cudaStreamSynchronize(m->stream));
+    const int n = read_next_id(m, m->stream);
+    if (n > cap) return DISC_ERR_INVALID_ARG;
+    if (n > 0) CK(cudaMemcpy(A, m->inst.A, sizeof(float) * (size_t)n * m->inst.Da, cudaMemcpyDeviceToHost));
+    return DISC_OK;
+}
+
 disc_status disc_map_export_instances(disc_map* m, int32_t* parent, int64_t* count, float* Q, float* E,
                                       int32_t* n_obs, int32_t cap)
 {
@@ -1772,6 +1938,10 @@ disc_status disc_map_save(disc_map* m, const char* path)
     std::vector<float> Q(std::max(nid, 1)), E((size_t)std::max(nid, 1) * D);
     s = disc_map_export_instances(m, parent.data(), count.data(), Q.data(), E.data(), obs.data(), nid);
     if (s != DISC_OK) return s;
+    const int Da = m->cfg.assoc_dim;
+    std::vector<float> A((size_t)std::max(nid, 1) * std::max(Da, 1));
+    if (Da > 0) s = disc_map_export_assoc(m, A.data(), nid);
+    if (s != DISC_OK) return s;
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return DISC_ERR_INVALID_ARG;
     disc_map_config c = m->cfg;
@@ -1783,6 +1953,7 @@ disc_status disc_map_save(disc_map* m, const char* path)
         ok = std::fwrite(parent.data(), 4, nid, fp) == (size_t)nid && std::fwrite(count.data(), 8, nid, fp) == (size_t)nid &&
              std::fwrite(Q.data(), 4, nid, fp) == (size_t)nid &&
              std::fwrite(E.data(), 4, (size_t)nid * D, fp) == (size_t)nid * D && std::fwrite(obs.data(), 4, nid, fp) == (size_t)nid;
+    if (ok && nid && Da > 0) ok = std::fwrite(A.data(), 4, (size_t)nid * Da, fp) == (size_t)nid * Da;
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? DISC_OK : DISC_ERR_INVALID_ARG;
 }
@@ -1808,12 +1979,16 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     std::vector<int32_t> parent(std::max(nid, 1)), obs(std::max(nid, 1));
     std::vector<int64_t> count(std::max(nid, 1));
     std::vector<float> Q(std::max(nid, 1)), E((size_t)std::max(nid, 1) * D);
-    std::vector<uint16_t> Eb(ok && c.precision == DISC_BF16 ? (size_t)std::max(nid, 1) * D : 0);
+    const int Da = ok && c.assoc_dim > 0 && c.assoc_dim <= 4096 ? c.assoc_dim : 0;
+    const int Ds = Da > 0 ? Da : D;  // length of the scoring master's rows
+    std::vector<uint16_t> Eb(ok && c.precision == DISC_BF16 ? (size_t)std::max(nid, 1) * Ds : 0);
+    std::vector<float> A((size_t)std::max(nid, 1) * std::max(Da, 1));
     if (ok && nv) ok = std::fread(keys.data(), 8, nv, fp) == (size_t)nv && std::fread(ids.data(), 4, nv, fp) == (size_t)nv;
     if (ok && nid)
         ok = std::fread(parent.data(), 4, nid, fp) == (size_t)nid && std::fread(count.data(), 8, nid, fp) == (size_t)nid &&
              std::fread(Q.data(), 4, nid, fp) == (size_t)nid &&
              std::fread(E.data(), 4, (size_t)nid * D, fp) == (size_t)nid * D && std::fread(obs.data(), 4, nid, fp) == (size_t)nid;
+    if (ok && nid && Da > 0) ok = std::fread(A.data(), 4, (size_t)nid * Da, fp) == (size_t)nid * Da;
     std::fclose(fp);
     if (!ok) return DISC_ERR_INVALID_ARG;
     if (over) {
@@ -1848,16 +2023,19 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
         cudaMemcpyAsync(m->inst.count, count.data(), 8 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->inst.Q, Q.data(), 4 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->inst.E, E.data(), 4 * (size_t)nid * D, cudaMemcpyHostToDevice, m->stream);
+        if (m->inst.A) cudaMemcpyAsync(m->inst.A, A.data(), 4 * (size_t)nid * Da, cudaMemcpyHostToDevice, m->stream);
         if (m->inst.Eb) {
-            // bf16 scoring copy, rounded to nearest even as on the device
-            for (size_t i = 0; i < (size_t)nid * D; i++) {
+            // bf16 scoring copy of the scoring master, rounded to nearest even
+            // as on the device
+            const std::vector<float>& Sm = Da > 0 ? A : E;
+            for (size_t i = 0; i < (size_t)nid * Ds; i++) {
                 uint32_t b;
-                std::memcpy(&b, &E[i], 4);
+                std::memcpy(&b, &Sm[i], 4);
                 Eb[i] = (uint16_t)((b + 0x7fffu + ((b >> 16) & 1u)) >> 16);
             }
-            cudaMemcpyAsync(m->inst.Eb, Eb.data(), 2 * (size_t)nid * D, cudaMemcpyHostToDevice, m->stream);
+            cudaMemcpyAsync(m->inst.Eb, Eb.data(), 2 * (size_t)nid * Ds, cudaMemcpyHostToDevice, m->stream);
         }
-        if (m->inst.E8) launch_e4m3_copies(m->inst, nid, D, m->stream);  // scoring copies from E
+        if (m->inst.E8) launch_e4m3_copies(m->inst, nid, D, m->stream);  // from the scoring master
         cudaMemcpyAsync(m->inst.n_obs, obs.data(), 4 * nid, cudaMemcpyHostToDevice, m->stream);
         cudaMemcpyAsync(m->d_next_id, &nid, sizeof(int), cudaMemcpyHostToDevice, m->stream);
     }

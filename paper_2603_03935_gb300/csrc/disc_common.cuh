@@ -114,6 +114,9 @@ struct Instances {
     uint16_t* Eb;                // [cap][D] bf16 scoring copy of E (BF16 precision), else NULL
     uint8_t* E8;                 // [cap][D] E4M3 scoring copy of E / 2^e (FP8 precision), else NULL
     float* Er;                   // [cap] bound of ||2^e E8 - E|| / ||E|| for the E4M3 copy
+    float* A;                    // [cap][Da] association features (second token grid), else NULL;
+                                 // with them, the scoring copies Eb/E8/Er are copies of A, not E
+    int32_t Da;
     int32_t* n_obs;
     int32_t cap;
 };
@@ -314,6 +317,7 @@ struct SerialStep {
     const FrameCounters* hist;  // counters of the call's earlier batches
     int J;                      // frames per map in this batch
     int j;                      // this step
+    BatchScratch view;          // the second grid's features per slot (zero when the runner has none)
 };
 
 // frame parameters passed by value
@@ -329,6 +333,8 @@ struct FrameParams {
     int32_t map;           // position of the frame's map in the batch (MapRefs index)
     int32_t precision;     // disc_precision of the fast pooled embedding and scoring
     int32_t dilate;        // overlap_dilation: 26-neighbour overlap
+    int32_t assoc;         // the map has a second grid: association on its features
+    int32_t uniform_w;     // this is the second grid's view: pixel-mean weights c_p / |M|
     int32_t db_min_pts;    // DBSCAN core threshold; 0: no DBSCAN for this frame
     float db_eps2;         // eps * eps
     float db_inv_cell;     // 1 / (1.001 eps): grid cells a little wider than eps
@@ -410,5 +416,13 @@ __device__ __forceinline__ void e4m3_copy_row(const float* x, int D, uint8_t* q8
     }
     if (lane == 0) *er = sn > 0.0f ? __fmul_rn(__fdiv_rn(sqrtf(se), sqrtf(sn)), 1.0f + 0x1p-9f) : 0.0f;
 }
+
+// The embedding the association gate scores against: the association
+// feature with a second grid, else the stored embedding; its length.
+__host__ __device__ __forceinline__ const float* scoring_master(const Instances& in, int D)
+{
+    return in.A ? in.A : in.E;
+}
+__host__ __device__ __forceinline__ int scoring_dim(const Instances& in, int D) { return in.A ? in.Da : D; }
 
 }  // namespace disc

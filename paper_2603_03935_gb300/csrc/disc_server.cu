@@ -267,6 +267,10 @@ disc_status disc_server_open_map(disc_server* s, const disc_map_config* cfg, int
         cfg->patch_w != g.patch_w || cfg->max_width > g.max_width || cfg->max_height > g.max_height ||
         cfg->max_masks > g.max_masks)
         return DISC_ERR_INVALID_ARG;
+    // a second token grid needs the group's
+    if (cfg->assoc_dim > 0 && (cfg->assoc_dim != g.assoc_dim || cfg->assoc_patch_h != g.assoc_patch_h ||
+                               cfg->assoc_patch_w != g.assoc_patch_w))
+        return DISC_ERR_INVALID_ARG;
     if (cudaSetDevice(g.device) != cudaSuccess) {
         cudaGetLastError();
         return DISC_ERR_CUDA;
@@ -338,7 +342,11 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     const size_t npx = (size_t)f->width * f->height;
     const size_t tok = (size_t)g.patch_h * g.patch_w * g.embed_dim * (f->token_dtype == DISC_TOKENS_BF16 ? 2 : 4);
     const size_t od = 0, ol = od + ((4 * npx + 15) & ~(size_t)15), ot = ol + ((2 * npx + 15) & ~(size_t)15);
-    const size_t og = ot + ((tok + 15) & ~(size_t)15), total = og + 4 * (size_t)g.embed_dim;
+    const size_t atok = f->assoc_tokens && g.assoc_dim > 0 ? (size_t)g.assoc_patch_h * g.assoc_patch_w * g.assoc_dim *
+                                                                 (f->token_dtype == DISC_TOKENS_BF16 ? 2 : 4)
+                                                           : 0;
+    const size_t og = ot + ((tok + 15) & ~(size_t)15), oa = og + ((4 * (size_t)g.embed_dim + 15) & ~(size_t)15);
+    const size_t total = oa + atok;
     auto copy = [&](void* dst, const void* src, size_t n) {
         if (!f->inputs_on_device) {
             std::memcpy(dst, src, n);
@@ -361,6 +369,7 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     bool ok = copy(r.host + od, f->depth, 4 * npx) && copy(r.host + ol, f->labels, 2 * npx) &&
               copy(r.host + ot, f->tokens, tok);
     if (ok && f->global_embed) ok = copy(r.host + og, f->global_embed, 4 * (size_t)g.embed_dim);
+    if (ok && atok) ok = copy(r.host + oa, f->assoc_tokens, atok);
     if (!ok) {
         cudaGetLastError();
         std::lock_guard<std::mutex> lk(s->mu);
@@ -372,6 +381,7 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     r.frame.labels = (const uint16_t*)(r.host + ol);
     r.frame.tokens = r.host + ot;
     r.frame.global_embed = f->global_embed ? (const float*)(r.host + og) : nullptr;
+    r.frame.assoc_tokens = atok ? r.host + oa : nullptr;
     r.frame.inputs_on_device = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -38,7 +38,8 @@ constexpr size_t OFF_DOTG = align256(OFF_GVEC + 4 * (size_t)STATIC_MAX_D); // lo
 constexpr size_t OFF_FFP = align256(OFF_DOTG + 8 * (size_t)STATIC_MAX_P);  // long long [P]
 constexpr size_t OFF_NRM = align256(OFF_FFP + 8 * (size_t)STATIC_MAX_P);   // float [P]
 constexpr size_t OFF_FNORM = align256(OFF_NRM + 4 * (size_t)STATIC_MAX_P); // float [P]
-constexpr size_t OFF_PARAMS = align256(OFF_FNORM + 4 * (size_t)STATIC_MAX_P); // FrameParams
+constexpr size_t OFF_COS = align256(OFF_FNORM + 4 * (size_t)STATIC_MAX_P);   // float [P] (heatmap)
+constexpr size_t OFF_PARAMS = align256(OFF_COS + 4 * (size_t)STATIC_MAX_P);  // FrameParams
 constexpr size_t STATIC_BYTES = align256(OFF_PARAMS + sizeof(FrameParams));
 
 constexpr int MAX_DEVICES = 64;
@@ -50,11 +51,20 @@ unsigned char* g_addr[MAX_DEVICES] = {};
 // The working set: ~450 KB, one copy per GPU that loads the library.
 static __device__ __align__(256) unsigned char g_token_scratch[STATIC_BYTES];
 
-extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
-                                               const float* global_embed, float eps, float* Dp, float* cosg,
-                                               void* cuda_stream)
+// heat_p = D_p * cos(f_p, q), one fp32 rounding
+__global__ void k_heat(float* heat, const float* cosq, int P)
 {
-    if (!tokens || !Dp || !cosg || P <= 0 || D <= 0) return DISC_ERR_INVALID_ARG;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) heat[p] = __fmul_rn(heat[p], cosq[p]);
+}
+
+// Eq. 1 and the token cosines on the static working set; cosg may point into
+// the working set itself (offset OFF_COS, given as nullptr here)
+static disc_status static_stats(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
+                                const float* global_embed, float eps, float* Dp, float* cosg, void* cuda_stream,
+                                unsigned char** base_out)
+{
+    if (!tokens || !Dp || P <= 0 || D <= 0) return DISC_ERR_INVALID_ARG;
     if (P > STATIC_MAX_P || D > STATIC_MAX_D) return DISC_ERR_INVALID_ARG;
     if (token_dtype != DISC_TOKENS_F32 && token_dtype != DISC_TOKENS_BF16) return DISC_ERR_INVALID_ARG;
     if (!(eps >= 0.0f)) return DISC_ERR_INVALID_ARG;
@@ -100,7 +110,8 @@ extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token
     sc.nrm = (float*)(base + OFF_NRM);
     sc.fnorm = (float*)(base + OFF_FNORM);
     sc.Dp = Dp;
-    sc.cosg = cosg;
+    sc.cosg = cosg ? cosg : (float*)(base + OFF_COS);
+    *base_out = base;
 
     // counters, ||g||^2, the residual-norm sum and the column sums start at
     // zero; the frame parameters travel to the array as well (pageable
@@ -121,4 +132,31 @@ extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token
         return DISC_ERR_CUDA;
     }
     return (disc_status)err;
+}
+
+extern "C" disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
+                                               const float* global_embed, float eps, float* Dp, float* cosg,
+                                               void* cuda_stream)
+{
+    if (!cosg) return DISC_ERR_INVALID_ARG;
+    unsigned char* base = nullptr;
+    return static_stats(tokens, token_dtype, P, D, global_embed, eps, Dp, cosg, cuda_stream, &base);
+}
+
+// Fig. 2: Eq. 1 with the query in the place of the global embedding gives D_p
+// (written straight into heat) and cos(f_p, q); the heatmap is their product.
+extern "C" disc_status disc_query_heatmap(const void* tokens, int32_t token_dtype, int32_t P, int32_t D,
+                                          const float* query, float eps, float* heat, void* cuda_stream)
+{
+    if (!query || !heat) return DISC_ERR_INVALID_ARG;
+    unsigned char* base = nullptr;
+    disc_status s = static_stats(tokens, token_dtype, P, D, query, eps, heat, nullptr, cuda_stream, &base);
+    if (s != DISC_OK) return s;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    k_heat<<<(P + 255) / 256, 256, 0, st>>>(heat, (const float*)(base + OFF_COS), P);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return DISC_ERR_CUDA;
+    }
+    return DISC_OK;
 }

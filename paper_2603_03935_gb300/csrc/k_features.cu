@@ -239,7 +239,8 @@ __device__ float fp8_weights(const FrameParams& fp, const Scratch& sc, int m, co
 }
 
 // ---- pooling weights and the image-based quality terms (one block per mask) ---
-// a_p = c_p * D_p;  w_p = a_p / sum a  (sum a == 0: w_p = c_p / |M|);
+// a_p = c_p * D_p;  w_p = a_p / sum a  (sum a == 0, or the second grid's view:
+// w_p = c_p / |M|);
 // S_size = min(lambda |M| / (H W), 1);  S_dist = 0.5 + 0.5 * sum a / |M|;
 // S_sem = clamp(sum c_p ReLU(cos(f_p, g)) / |M|, 0, 1).
 __global__ void k_weights(const FrameParams* fps, BatchScratch bs)
@@ -278,7 +279,7 @@ __global__ void k_weights(const FrameParams* fps, BatchScratch bs)
     float bsum = 0.0f;
     for (int p = threadIdx.x; p < fp.P; p += blockDim.x) {
         float cp = (float)c[p];
-        float wp = A > 0 ? __fdiv_rn(__fmul_rn(cp, sc.Dp[p]), Af) : __fdiv_rn(cp, (float)npix);
+        float wp = A > 0 && !fp.uniform_w ? __fdiv_rn(__fmul_rn(cp, sc.Dp[p]), Af) : __fdiv_rn(cp, (float)npix);
         w[p] = wp;
         bsum += wp * sc.fnorm[p];
     }

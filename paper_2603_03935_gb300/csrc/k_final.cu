@@ -116,10 +116,13 @@ __global__ void k_fin_gates(Instances inst, int D, FinalizeScratch fs, int num, 
         const int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
         const long long mn = min(inst.count[a], inst.count[b]);
         if ((long long)fs.pcnt[h] * den < (long long)num * mn) continue;
-        const float* ea = inst.E + (size_t)a * D;
-        const float* eb = inst.E + (size_t)b * D;
+        // the association features with a second grid, else the embeddings
+        const float* Sm = scoring_master(inst, D);
+        const int Ds = scoring_dim(inst, D);
+        const float* ea = Sm + (size_t)a * Ds;
+        const float* eb = Sm + (size_t)b * Ds;
         long long xd = 0, xa = 0, xb = 0;
-        for (int d = lane; d < D; d += 32) {
+        for (int d = lane; d < Ds; d += 32) {
             const float x = ea[d], y = eb[d];
             xd += fix32f(__fmul_rn(x, y), S_SQ);
             xa += fix32f(__fmul_rn(x, x), S_SQ);
@@ -198,10 +201,13 @@ __global__ void k_fin_fuse(Instances inst, int nid, int D, FinalizeScratch fs)
         if (key == 0ull || fs.comp[c] != c) continue;
         const int w = (int)(0xffffffffu - (unsigned)(key & 0xffffffffu));
         if (w == c) continue;
-        for (int d = lane; d < D; d += 32) {
-            inst.E[(size_t)c * D + d] = inst.E[(size_t)w * D + d];
-            if (inst.Eb) inst.Eb[(size_t)c * D + d] = inst.Eb[(size_t)w * D + d];
-            if (inst.E8) inst.E8[(size_t)c * D + d] = inst.E8[(size_t)w * D + d];
+        for (int d = lane; d < D; d += 32) inst.E[(size_t)c * D + d] = inst.E[(size_t)w * D + d];
+        // the scoring copies are rows of the scoring master's length
+        const int Ds = scoring_dim(inst, D);
+        for (int d = lane; d < Ds; d += 32) {
+            if (inst.A) inst.A[(size_t)c * Ds + d] = inst.A[(size_t)w * Ds + d];
+            if (inst.Eb) inst.Eb[(size_t)c * Ds + d] = inst.Eb[(size_t)w * Ds + d];
+            if (inst.E8) inst.E8[(size_t)c * Ds + d] = inst.E8[(size_t)w * Ds + d];
         }
         if (lane == 0) {
             inst.Q[c] = inst.Q[w];

@@ -234,11 +234,18 @@ __device__ __forceinline__ float4 bf16x4_to_f32(uint2 v)
                        __uint_as_float(v.y & 0xffff0000u));
 }
 
-__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst)
+// With a second grid (inst.A), the fast and exact features, their bounds and
+// the instance side all come from the association features (view scratch va).
+__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scratch& va, const SerialScratch& ss,
+                            const Instances& inst)
 {
     const int lane = threadIdx.x & 31;
     const int npairs = sc.ctr->n_pairs;
-    const int D = fp.D;
+    const int D = scoring_dim(inst, fp.D);
+    const float* Sm = scoring_master(inst, fp.D);
+    const float* fast = inst.A ? va.Efast : sc.Efast;
+    const float* exact = inst.A ? va.Ecan : sc.Ecan;
+    const float* bm = inst.A ? va.Bm : sc.Bm;
     int border = 0;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npairs; i += (gridDim.x * blockDim.x) >> 5) {
         const int slot = ss.olist[i];
@@ -249,8 +256,8 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
         // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
         const long long denom = min((long long)sc.nvox[m], inst.count[k]);
         if (ov * (long long)fp.ov_den < (long long)fp.ov_num * denom) continue;
-        const float* a = sc.Efast + (size_t)m * D;
-        const float* b = inst.E + (size_t)k * D;
+        const float* a = fast + (size_t)m * D;
+        const float* b = Sm + (size_t)k * D;
         float dt = 0.0f, na = 0.0f, nb = 0.0f;
         if (inst.Eb && (D & 3) == 0) {  // bf16 scoring copy: 8-byte rows of 4
             const float4* a4 = (const float4*)a;
@@ -347,13 +354,13 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Seri
         const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
         // |cos(a, b') - cos(e, b)| <= 2 |a - e| / |a| + 2 |b' - b| / |b|, plus
         // the fp32 arithmetic of cf; 10 % slack on the bounds
-        float band = (na > 0.0f) ? 2.2f * fp.eta * sc.Bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
+        float band = (na > 0.0f) ? 2.2f * fp.eta * bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
         if (inst.Er) band += 2.2f * inst.Er[k];
         if (fabsf(cf - fp.tau) > band) {
             edge = cf >= fp.tau;
         } else {
             // exact re-score with the exact pooled embedding
-            const float* ae = sc.Ecan + (size_t)m * D;
+            const float* ae = exact + (size_t)m * D;
             long long xd = 0, xa = 0, xb = 0;
             if ((D & 3) == 0) {  // all of a lane's loads in flight before the exact sums
                 const float4* a4 = (const float4*)ae;
@@ -651,8 +658,40 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     }
 }
 
+// One warp copies an embedding row (and writes its bf16 copy when tb is set).
+__device__ __forceinline__ void copy_row(const float* from, float* to, uint16_t* tb, int D, int lane)
+{
+    if ((D & 3) == 0) {
+        const float4* f4 = (const float4*)from;
+        float4* t4 = (float4*)to;
+        const int n4 = D >> 2;
+        for (int d0 = 0; d0 < n4; d0 += 32 * 8) {
+            float4 r[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int d = d0 + j * 32 + lane;
+                if (d < n4) r[j] = f4[d];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int d = d0 + j * 32 + lane;
+                if (d < n4) {
+                    t4[d] = r[j];
+                    if (tb) ((uint2*)tb)[d] = make_uint2(bf16_pair(r[j].x, r[j].y), bf16_pair(r[j].z, r[j].w));
+                }
+            }
+        }
+    } else {
+        for (int d = lane; d < D; d += 32) {
+            to[d] = from[d];
+            if (tb) tb[d] = __bfloat16_as_ushort(__float2bfloat16_rn(from[d]));
+        }
+    }
+}
+
 // ---- embeddings, new voxels, parent flattening, cleanup ---------------------------
-__device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt,
+__device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Scratch& va, const SerialScratch& ss,
+                            const VoxelTable& vt,
                             const Instances& inst, const int* next_id, bool ok)
 {
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -661,39 +700,22 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Seri
     const int D = fp.D;
     if (ok) {
         // winning embeddings (the sources are never written in this frame):
-        // one warp per vector, all loads in flight before the stores
+        // one warp per vector, all loads in flight before the stores; the
+        // scoring copies follow the scoring master (the association feature
+        // with a second grid)
         const int nc = *ss.copy_n;
         for (int c = gtid >> 5; c < nc; c += gsz >> 5) {
-            const int src = ss.copy_src[c];
+            const int src = ss.copy_src[c], dst = ss.copy_dst[c];
             const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
-            float* to = inst.E + (size_t)ss.copy_dst[c] * D;
-            uint16_t* tb = inst.Eb ? inst.Eb + (size_t)ss.copy_dst[c] * D : nullptr;  // bf16 scoring copy
-            if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)ss.copy_dst[c] * D, inst.Er + ss.copy_dst[c]);
-            if ((D & 3) == 0) {
-                const float4* f4 = (const float4*)from;
-                float4* t4 = (float4*)to;
-                const int n4 = D >> 2;
-                for (int d0 = 0; d0 < n4; d0 += 32 * 8) {
-                    float4 r[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int d = d0 + j * 32 + lane;
-                        if (d < n4) r[j] = f4[d];
-                    }
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int d = d0 + j * 32 + lane;
-                        if (d < n4) {
-                            t4[d] = r[j];
-                            if (tb) ((uint2*)tb)[d] = make_uint2(bf16_pair(r[j].x, r[j].y), bf16_pair(r[j].z, r[j].w));
-                        }
-                    }
-                }
+            if (inst.A) {
+                const int Da = inst.Da;
+                const float* fa = src >= 0 ? inst.A + (size_t)src * Da : va.Ecan + (size_t)(-src - 1) * Da;
+                copy_row(from, inst.E + (size_t)dst * D, nullptr, D, lane);
+                copy_row(fa, inst.A + (size_t)dst * Da, inst.Eb ? inst.Eb + (size_t)dst * Da : nullptr, Da, lane);
+                if (inst.E8) e4m3_copy_row(fa, Da, inst.E8 + (size_t)dst * Da, inst.Er + dst);
             } else {
-                for (int d = lane; d < D; d += 32) {
-                    to[d] = from[d];
-                    if (tb) tb[d] = __bfloat16_as_ushort(__float2bfloat16_rn(from[d]));
-                }
+                copy_row(from, inst.E + (size_t)dst * D, inst.Eb ? inst.Eb + (size_t)dst * D : nullptr, D, lane);
+                if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)dst * D, inst.Er + dst);
             }
         }
         // new voxels: the lowest segment index owns a voxel
@@ -779,7 +801,7 @@ __global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st)
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
     const Instances inst = R.inst;
-    phase_score(fps[slot], bs.frame(slot), ss, inst);
+    phase_score(fps[slot], bs.frame(slot), st.view.frame(slot), ss, inst);
 }
 
 __global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* fps, BatchScratch bs, SerialStep st)
@@ -803,7 +825,7 @@ __global__ void k_apply(const FrameParams* fps, BatchScratch bs, SerialStep st)
     const SerialScratch ss = R.ss;
     const VoxelTable vt = R.vt;
     const Instances inst = R.inst;
-    phase_apply(fps[slot], bs.frame(slot), ss, vt, inst, R.next_id, !blocked);
+    phase_apply(fps[slot], bs.frame(slot), st.view.frame(slot), ss, vt, inst, R.next_id, !blocked);
 }
 
 __global__ void k_serial_begin(const MapRefs* refs, int G)
@@ -816,12 +838,14 @@ __global__ void k_serial_begin(const MapRefs* refs, int G)
 }
 
 // ---- host launcher ----------------------------------------------------------------
-// E4M3 scoring copies of instances [0, n) from their stored embeddings (one
+// E4M3 scoring copies of instances [0, n) from their scoring master (one
 // warp per instance), as the apply phase writes them
 __global__ void k_e4m3_copies(Instances inst, int n, int D)
 {
+    const float* Sm = scoring_master(inst, D);
+    const int Ds = scoring_dim(inst, D);
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += (gridDim.x * blockDim.x) >> 5)
-        e4m3_copy_row(inst.E + (size_t)k * D, D, inst.E8 + (size_t)k * D, inst.Er + k);
+        e4m3_copy_row(Sm + (size_t)k * Ds, Ds, inst.E8 + (size_t)k * Ds, inst.Er + k);
 }
 
 int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st)

@@ -36,6 +36,7 @@ enum Phase {
 
 // batched
 int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st);
+int launch_view_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st);
 int launch_token_stats(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, bool any_bf16,
                        bool any_f32, cudaStream_t st);
 int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int Ph, int Pw, int Mmax, cudaStream_t st);

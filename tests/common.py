@@ -32,6 +32,8 @@ def to_oracle_cfg(dcfg):
     out["dbscan_eps"] = dcfg.get("dbscan_eps", 0.0)
     out["dbscan_min_pts"] = dcfg.get("dbscan_min_pts", 1)
     out["overlap_dilation"] = dcfg.get("overlap_dilation", 0)
+    for k in ("assoc_dim", "assoc_patch_h", "assoc_patch_w"):
+        out[k] = dcfg.get(k, 0)
     return out
 
 
