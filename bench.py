@@ -55,10 +55,13 @@ def parse():
     ap.add_argument("--served-maps", type=int, default=32)
     ap.add_argument("--served-rates", default="4000,8000,12000,16000", help="offered frames/s, comma separated")
     ap.add_argument("--served-seconds", type=float, default=1.0)
+    ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
     ap.add_argument("--served-precision", type=int, default=2, help="0 fp32, 1 bf16, 2 fp8 e4m3")
     ap.add_argument("--precision", type=int, default=0,
                     help="fast pooling/scoring precision of the plain path: 0 fp32 (the Room-scale "
                          "configuration), 1 bf16, 2 fp8 e4m3")
+    ap.add_argument("--assoc-steps", type=int, default=5,
+                    help="steps with a second (24x32x1024) token grid driving association (0: skip)")
     ap.add_argument("--dilation-steps", type=int, default=20,
                     help="steps of the same workload with the 26-neighbour overlap (0: skip)")
     ap.add_argument("--dbscan-steps", type=int, default=20,
@@ -277,6 +280,10 @@ def run_batched(args, torch, dev, stream, rank):
     steps = [arrays(s * J) for s in range(1 + T)]
     sts = [(binding.Stats * J)() for _ in range(G)]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    # the launch schedule the autotuner picks on the first step's frames
+    # (fresh maps of the same configurations; the timed maps stay untouched)
+    tune = grp.autotune(maps, steps[0], [J] * G, reps=2) if args.batched_tune else None
+    l0 = grp.kernel_launches()
     assert grp.integrate_raw(maps, steps[0], [J] * G, sts) == 0
     torch.cuda.synchronize()
     times, upd = [], 0
@@ -297,7 +304,8 @@ def run_batched(args, torch, dev, stream, rank):
            "steps": T, "ms_per_batch": total_ms / T,
            "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                                 "mode": "a frame's result is ready when its batch ends"},
-           "gpu_launches_per_batch": grp.kernel_launches() // (1 + T),
+           "gpu_launches_per_batch": (grp.kernel_launches() - l0) // (1 + T),
+           "schedule": tune,
            "device_gb": (grp.device_bytes() + sum(m.device_bytes() for m in maps)) / 1e9}
     grp.close()
     for m in maps:
@@ -555,12 +563,13 @@ def main():
     clk = clocks.stop()
     frames_all = K * B * world
 
-    def variant(extra, nsteps):
-        """The same steps on a fresh map with config changes; frames/s and the
-        per-frame counters summed."""
+    def variant(extra, nsteps, vsteps=None):
+        """The same steps (or vsteps) on a fresh map with config changes;
+        frames/s and the per-frame counters averaged."""
+        steps_ = steps if vsteps is None else vsteps
         vmap = DiscMap(**dict(cfg, **extra))
         for s_ in range(Wm):
-            assert vmap.integrate_frames_raw(steps[s_], B, stats) == 0
+            assert vmap.integrate_frames_raw(steps_[s_], B, stats) == 0
         torch.cuda.synchronize()
         dt_ms, nf, sums = 0.0, 0, {}
         for s_ in range(Wm, Wm + min(nsteps, K)):
@@ -568,7 +577,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            rc = vmap.integrate_frames_raw(steps[s_], B, stats)
+            rc = vmap.integrate_frames_raw(steps_[s_], B, stats)
             e1.record(stream)
             e1.synchronize()
             assert rc == 0, rc
@@ -586,6 +595,27 @@ def main():
         fps_, nf, per = variant(dict(dbscan_eps=0.05, dbscan_min_pts=10), args.dbscan_steps)
         dbscan = {"frames_per_s": fps_, "eps_m": 0.05, "min_pts": 10, "frames": nf,
                   "denoised_pixels_per_frame": per["denoised_pixels"]}
+    # and with a second token grid driving association (1024-dim ViT-L
+    # features on a 24 x 32 patch grid, fp32), generated for the frames used
+    assoc = None
+    if args.assoc_steps > 0:
+        import dataclasses
+        A_H, A_W, A_D = 24, 32, 1024
+        nsa = Wm + min(args.assoc_steps, K)
+        nfa = min(nsa * B, n_render)
+        sub = dataclasses.replace(fr, index=fr.index[:nfa], ids=fr.ids[:nfa])
+        atok = torch.from_numpy(sub.assoc_tokens(A_H, A_W, A_D)).to(dev)
+        asteps = []
+        for s_ in range(nsa):
+            arr = frame_array(s_ * B, (s_ + 1) * B)
+            for j in range(B):
+                arr[j].assoc_tokens = atok[(s_ * B + j) % nfa].data_ptr()
+            asteps.append(arr)
+        fps_, nf, per = variant(dict(assoc_dim=A_D, assoc_patch_h=A_H, assoc_patch_w=A_W), args.assoc_steps, asteps)
+        assoc = {"frames_per_s": fps_, "frames": nf, "grid": f"{A_H}x{A_W}x{A_D} fp32",
+                 "merges_per_frame": per["merges"], "new_instances_per_frame": per["new_instances"]}
+        del atok
+
     # and with the neighbourhood overlap (26-neighbour dilation, Sec. III-B)
     dilation = None
     if args.dilation_steps > 0:
@@ -710,6 +740,7 @@ def main():
                "batched": batched,
                "dbscan": dbscan,
                "dilation": dilation,
+               "assoc_grid": assoc,
                "served": served,
                "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
                "gpu_launches": int(launches),

@@ -356,6 +356,38 @@ disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int
                                     const float* global_embed, float eps, float* Dp, float* cosg,
                                     void* cuda_stream);
 
+/* ---- Launch schedule and autotuner -----------------------------------------
+ * How a map's (or a group's) batches are cut into launches: the frames per
+ * launch of the geometry kernels (back-projection, entries, DBSCAN), whose
+ * per-frame hashes should stay in L2, and the CTA counts of the serial
+ * kernels, which trade parallel probes against launch cost.  Neither changes
+ * any result. */
+typedef struct {
+    int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 4) */
+    int32_t serial_ctas;     /* serial kernels' CTAs in quarters of the default count, 1..32 (default 4) */
+} disc_schedule;
+
+typedef struct {
+    disc_schedule best;      /* the schedule kept */
+    double best_ms;          /* its time for the sample (minimum over the timed repetitions) */
+    double default_ms;       /* the default schedule's time */
+    int32_t candidates;      /* schedules timed */
+} disc_tune_report;
+
+disc_status disc_map_set_schedule(disc_map* map, const disc_schedule* schedule);
+disc_status disc_group_set_schedule(disc_group* group, const disc_schedule* schedule);
+
+/* Autotuner: times each candidate schedule (geometry_chunk in {2, 4, 8} x
+ * serial_ctas in {2, 4, 8}) on the sample frames, integrated into fresh maps
+ * with the given maps' configurations (created and destroyed here; the given
+ * maps are not changed), two untimed passes then `reps` timed ones, and keeps
+ * the fastest for the map or group.  report may be NULL. */
+disc_status disc_map_autotune(disc_map* map, const disc_frame* frames, int32_t n, int32_t reps,
+                              disc_tune_report* report);
+disc_status disc_group_autotune(disc_group* group, disc_map* const* maps, int32_t n_maps,
+                                const disc_frame* const* frames, const int32_t* counts, int32_t reps,
+                                disc_tune_report* report);
+
 /* Fig. 2: the distinctiveness-weighted cosine heatmap of a query vector over a
  * frame's token grid, heat_p = D_p * cos(f_p, q): D_p of Eq. 1 and the exact
  * cosine, their product rounded once to fp32 (the heatmap the paper shows for

@@ -58,6 +58,19 @@ class GroupConfig(ctypes.Structure):
                 ("assoc_patch_h", c_i32), ("assoc_patch_w", c_i32)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("best", Schedule), ("best_ms", c_f64), ("default_ms", c_f64), ("candidates", c_i32)]
+
+    def as_dict(self):
+        return {"geometry_chunk": int(self.best.geometry_chunk), "serial_ctas": int(self.best.serial_ctas),
+                "best_ms": float(self.best_ms), "default_ms": float(self.default_ms),
+                "candidates": int(self.candidates)}
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("group", GroupConfig), ("hbm_budget_bytes", c_i64), ("max_queue", c_i32)]
 
@@ -124,6 +137,12 @@ def lib():
         L.disc_query_heatmap.argtypes = [c_vp, c_i32, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp]
         L.disc_query_heatmap.restype = ctypes.c_int
         L.disc_map_export_assoc.argtypes = [c_vp, c_vp, c_i32]
+        L.disc_map_set_schedule.argtypes = [c_vp, P(Schedule)]
+        L.disc_group_set_schedule.argtypes = [c_vp, P(Schedule)]
+        L.disc_map_autotune.argtypes = [c_vp, c_vp, c_i32, c_i32, P(TuneReport)]
+        L.disc_group_autotune.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, c_i32, P(TuneReport)]
+        for f in ("disc_map_set_schedule", "disc_group_set_schedule", "disc_map_autotune", "disc_group_autotune"):
+            getattr(L, f).restype = ctypes.c_int
         L.disc_map_export_assoc.restype = ctypes.c_int
         L.disc_map_device_bytes.argtypes = [c_vp]
         L.disc_map_device_bytes.restype = c_i64
@@ -331,6 +350,23 @@ class DiscMap:
         """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
         return lib().disc_integrate_frames(self._h, arr, n, stats, None)
 
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
+        _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
+               "disc_map_set_schedule")
+
+    def autotune(self, frames, reps=3) -> dict:
+        """Time the candidate launch schedules on sample frames (list of
+        (Frame, keepalive), or a ctypes Frame array) and keep the fastest."""
+        if isinstance(frames, list):
+            arr = (Frame * len(frames))()
+            for i, (fr, _k) in enumerate(frames):
+                arr[i] = fr
+        else:
+            arr = frames
+        r = TuneReport()
+        _check(lib().disc_map_autotune(self._h, arr, len(arr), reps, ctypes.byref(r)), "disc_map_autotune")
+        return r.as_dict()
+
     def last_frame(self) -> dict:
         M_cap = int(self.cfg["max_masks"])
         P, D = self.P, self.D
@@ -482,6 +518,22 @@ class DiscGroup:
         hs = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in stats_arrays]) \
             if stats_arrays is not None else None
         return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
+
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
+        _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
+               "disc_group_set_schedule")
+
+    def autotune(self, maps, frame_arrays, counts, reps=3) -> dict:
+        """Time the candidate launch schedules on a sample (per map a ctypes
+        Frame array and a count; fresh maps of the same configurations take
+        the frames) and keep the fastest for this group."""
+        n = len(maps)
+        hm = (c_vp * n)(*[m._h.value for m in maps])
+        hf = (c_vp * n)(*[ctypes.cast(a, c_vp).value for a in frame_arrays])
+        hc = (c_i32 * n)(*counts)
+        r = TuneReport()
+        _check(lib().disc_group_autotune(self._h, hm, n, hf, hc, reps, ctypes.byref(r)), "disc_group_autotune")
+        return r.as_dict()
 
     def integrate(self, maps, frames_per_map, check: bool = True):
         """frames_per_map: per map a list of (Frame, keepalive).  Returns

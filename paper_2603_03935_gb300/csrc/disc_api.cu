@@ -118,6 +118,9 @@ struct Runner {
     BatchScratch bsa[2] = {};
     size_t off_fpa = 0;
     unsigned char* d_atok = nullptr;  // staging of host association tokens (two sets)
+    // launch schedule (disc_*_set_schedule, disc_*_autotune)
+    int geo_chunk = GEOMETRY_CHUNK;   // frames per back-projection / entries / DBSCAN launch
+    int cta_scale = 4;                // serial kernels' CTAs in quarters of the default count
     bool graphs_off = false;
     std::map<long long, BatchGraph> graphs;
     std::map<long long, int> shapes_seen;  // batch shapes launched directly so far
@@ -862,8 +865,8 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
         run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfa, va, S, r.Da, Mmax, any, st); });
     }
     if (Mmax > 0) {
-        for (int f0 = 0; f0 < S; f0 += GEOMETRY_CHUNK) {
-            const int nb = std::min(GEOMETRY_CHUNK, S - f0);
+        for (int f0 = 0; f0 < S; f0 += r.geo_chunk) {
+            const int nb = std::min(r.geo_chunk, S - f0);
             if (combos & COMBO_DBSCAN)
                 run_phase(r, PH_DBSCAN, st, [&] { return launch_dbscan(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_BACKPROJECT, st, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
@@ -886,6 +889,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
     step.hist = r.d_hist;
     step.J = J;
     step.view = r.bsa[k];  // zero when the runner has no second grid
+    step.cta_scale = r.cta_scale;
     run_phase(r, PH_OVERLAP, st, [&] { return launch_serial_begin(step.refs, G, st); });
     for (int j = 0; j < J; j++) {
         step.j = j;
@@ -1772,6 +1776,128 @@ disc_status disc_group_integrate(disc_group* g, disc_map* const* maps, int32_t n
     if (n_done)
         for (int i = 0; i < n_maps; i++) n_done[i] = w[i].done;
     return s;
+}
+
+// ---- launch schedule and autotuner -------------------------------------------
+
+namespace {
+
+disc_status set_schedule(Runner& r, const disc_schedule* sch)
+{
+    if (!sch || sch->geometry_chunk < 1 || sch->geometry_chunk > 32 || sch->serial_ctas < 1 || sch->serial_ctas > 32)
+        return DISC_ERR_INVALID_ARG;
+    if (r.geo_chunk == sch->geometry_chunk && r.cta_scale == sch->serial_ctas) return DISC_OK;
+    CK(cudaStreamSynchronize(r.stream));
+    r.geo_chunk = sch->geometry_chunk;
+    r.cta_scale = sch->serial_ctas;
+    for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);  // captured with the old schedule
+    r.graphs.clear();
+    r.shapes_seen.clear();
+    return DISC_OK;
+}
+
+// Times every candidate schedule on the sample: fresh maps with the given
+// configurations take the frames through run_call on runner r; two untimed
+// passes (the second captures the graphs), then reps timed ones.
+disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
+                     const std::vector<std::pair<const disc_frame*, int>>& frames, int reps, disc_tune_report* out)
+{
+    if (reps < 1 || reps > 100) return DISC_ERR_INVALID_ARG;
+    const disc_schedule keep{r.geo_chunk, r.cta_scale};
+    disc_tune_report rep{};
+    rep.best_ms = 1e300;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    disc_status s = DISC_OK;
+    for (int geo : {4, 2, 8}) {  // the default first
+        for (int q : {4, 2, 8}) {
+            const disc_schedule cand{geo, q};
+            s = set_schedule(r, &cand);
+            double best = 1e300;
+            for (int pass = 0; pass < reps + 2 && s == DISC_OK; pass++) {
+                std::vector<disc_map*> maps(cfgs.size(), nullptr);
+                std::vector<Work> w(cfgs.size());
+                for (size_t i = 0; i < cfgs.size() && s == DISC_OK; i++) {
+                    disc_map_config c = *cfgs[i];
+                    c.cuda_stream = r.stream;
+                    s = disc_map_create(&c, nullptr, &maps[i]);
+                    w[i].m = maps[i];
+                    w[i].frames = frames[i].first;
+                    w[i].n = frames[i].second;
+                }
+                if (s == DISC_OK) {
+                    s = cuda_status(cudaEventRecord(e0, r.stream));
+                    if (s == DISC_OK) s = run_call(r, w);
+                    if (s == DISC_OK) s = cuda_status(cudaEventRecord(e1, r.stream));
+                    if (s == DISC_OK) s = cuda_status(cudaEventSynchronize(e1));
+                    float ms = 0.0f;
+                    if (s == DISC_OK) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+                    if (s == DISC_OK && pass >= 2) best = std::min(best, (double)ms);
+                }
+                for (disc_map* m : maps) disc_map_destroy(m);
+            }
+            if (s != DISC_OK) break;
+            rep.candidates++;
+            if (geo == 4 && q == 4) rep.default_ms = best;
+            if (best < rep.best_ms) {
+                rep.best_ms = best;
+                rep.best = cand;
+            }
+        }
+        if (s != DISC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != DISC_OK) {
+        set_schedule(r, &keep);
+        return s;
+    }
+    s = set_schedule(r, &rep.best);
+    if (out) *out = rep;
+    return s;
+}
+
+}  // namespace
+
+disc_status disc_map_set_schedule(disc_map* m, const disc_schedule* sch)
+{
+    if (!m || !sch) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    disc_status s = map_runner(m);
+    return s != DISC_OK ? s : set_schedule(*m->run, sch);
+}
+
+disc_status disc_group_set_schedule(disc_group* g, const disc_schedule* sch)
+{
+    if (!g || !sch) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(g->cfg.device));
+    return set_schedule(g->run, sch);
+}
+
+disc_status disc_map_autotune(disc_map* m, const disc_frame* frames, int32_t n, int32_t reps, disc_tune_report* report)
+{
+    if (!m || !frames || n <= 0) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    disc_status s = map_runner(m);
+    if (s != DISC_OK) return s;
+    CK(cudaStreamSynchronize(m->stream));
+    return autotune(*m->run, {&m->cfg}, {{frames, n}}, reps, report);
+}
+
+disc_status disc_group_autotune(disc_group* g, disc_map* const* maps, int32_t n_maps, const disc_frame* const* frames,
+                                const int32_t* counts, int32_t reps, disc_tune_report* report)
+{
+    if (!g || !maps || !frames || !counts || n_maps <= 0 || n_maps > g->cfg.max_maps) return DISC_ERR_INVALID_ARG;
+    std::vector<const disc_map_config*> cfgs;
+    std::vector<std::pair<const disc_frame*, int>> fr;
+    for (int i = 0; i < n_maps; i++) {
+        if (!maps[i] || !frames[i] || counts[i] <= 0) return DISC_ERR_INVALID_ARG;
+        cfgs.push_back(&maps[i]->cfg);
+        fr.push_back({frames[i], counts[i]});
+    }
+    CK(cudaSetDevice(g->cfg.device));
+    return autotune(g->run, cfgs, fr, reps, report);
 }
 
 void disc_group_destroy(disc_group* g)

@@ -318,6 +318,7 @@ struct SerialStep {
     int J;                      // frames per map in this batch
     int j;                      // this step
     BatchScratch view;          // the second grid's features per slot (zero when the runner has none)
+    int cta_scale;              // serial kernels' CTAs, in quarters of the default count (4 = default)
 };
 
 // frame parameters passed by value

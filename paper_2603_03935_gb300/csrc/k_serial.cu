@@ -87,35 +87,66 @@ __device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned lo
     atomicAdd(&ss.ocnt[t], 1);
 }
 
+// one more voxel of pair okey in the block's shared pair hash; false when a
+// bounded probe finds no room (the caller then adds it to the frame's hash)
+__device__ __forceinline__ bool add_pair_shared(unsigned long long* pkey, int* pcnt, unsigned long long okey)
+{
+    unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
+    for (int pr = 0; pr < 32; pr++) {
+        const unsigned long long prev = atomicCAS(&pkey[t], EMPTY_KEY, okey);
+        if (prev == EMPTY_KEY || prev == okey) {
+            atomicAdd(&pcnt[t], 1);
+            return true;
+        }
+        t = (t + 1) & (OV_SLOTS - 1);
+    }
+    return false;
+}
+
 // Neighbourhood overlap (overlap_dilation): segment voxel `key` (label lab,
 // -1 if absent) overlaps each distinct instance labelling it or one of its 26
-// neighbours, once.  One entry may add up to 27 pairs, so they go straight to
+// neighbours, once.  The pairs are staged in the block's shared hash like the
+// plain path's; one entry may add up to 27, so a full shared hash spills to
 // the frame's pair hash.
 __device__ void dilated_pairs(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
-                              int m, unsigned long long key, int lab)
+                              int m, unsigned long long key, int lab, unsigned long long* pkey, int* pcnt)
 {
     int roots[27];
     int nr = 0;
     if (lab >= 0) roots[nr++] = inst.parent[lab];
     int k[3];
     unpack_key(key, k);
-    for (int t = 0; t < 27; t++) {
-        if (t == 13) continue;  // the voxel itself
-        const int q[3] = {k[0] + t / 9 - 1, k[1] + (t / 3) % 3 - 1, k[2] + t % 3 - 1};
-        if (q[0] < -KEY_BIAS || q[0] > KEY_BIAS - 1 || q[1] < -KEY_BIAS || q[1] > KEY_BIAS - 1 ||
-            q[2] < -KEY_BIAS || q[2] > KEY_BIAS - 1)
-            continue;
-        const unsigned long long nk = ((unsigned long long)(q[0] + KEY_BIAS) << (2 * KEY_BITS)) |
-                                      ((unsigned long long)(q[1] + KEY_BIAS) << KEY_BITS) |
-                                      (unsigned long long)(q[2] + KEY_BIAS);
-        const int nl = vt_label(vt, nk);
-        if (nl < 0) continue;
-        const int r = inst.parent[nl];
-        bool seen = false;
-        for (int j = 0; j < nr; j++) seen |= roots[j] == r;
-        if (!seen) roots[nr++] = r;
+    // nine neighbours at a time (one x offset): every first probe slot loaded
+    // at once; only a collision walks on
+    for (int dx = -1; dx <= 1; dx++) {
+        unsigned long long nk[9], cur[9];
+        unsigned long long h[9];
+        bool in[9];
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            const int q[3] = {k[0] + dx, k[1] + j / 3 - 1, k[2] + j % 3 - 1};
+            in[j] = !(dx == 0 && j == 4) && q[0] >= -KEY_BIAS && q[0] <= KEY_BIAS - 1 && q[1] >= -KEY_BIAS &&
+                    q[1] <= KEY_BIAS - 1 && q[2] >= -KEY_BIAS && q[2] <= KEY_BIAS - 1;
+            nk[j] = ((unsigned long long)(q[0] + KEY_BIAS) << (2 * KEY_BITS)) |
+                    ((unsigned long long)(q[1] + KEY_BIAS) << KEY_BITS) | (unsigned long long)(q[2] + KEY_BIAS);
+            h[j] = mix64(nk[j]) & vt.mask;
+            cur[j] = in[j] ? vt.keys[h[j]] : EMPTY_KEY;
+        }
+#pragma unroll
+        for (int j = 0; j < 9; j++) {
+            if (!in[j] || cur[j] == EMPTY_KEY) continue;
+            const int nl = cur[j] == nk[j] ? vt.labels[h[j]] : vt_label(vt, nk[j]);
+            if (nl < 0) continue;
+            const int r = inst.parent[nl];
+            bool seen = false;
+            for (int t = 0; t < nr; t++) seen |= roots[t] == r;
+            if (!seen) roots[nr++] = r;
+        }
     }
-    for (int j = 0; j < nr; j++) add_pair(sc, ss, ((unsigned long long)m << 32) | (unsigned)roots[j]);
+    for (int j = 0; j < nr; j++) {
+        const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)roots[j];
+        if (!add_pair_shared(pkey, pcnt, okey)) add_pair(sc, ss, okey);
+    }
 }
 
 __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
@@ -150,7 +181,7 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
                     h = (h + 1) & vt.mask;
                 }
             }
-            if (dilate) dilated_pairs(sc, ss, vt, inst, m, key, lab);
+            if (dilate) dilated_pairs(sc, ss, vt, inst, m, key, lab, pkey, pcnt);
             if (lab >= 0 && !dilate) {
                 const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
                 unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
@@ -895,18 +926,19 @@ static int per_map(int full, int G, int least)
 int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int phase,
                        cudaStream_t st_)
 {
+    const int q = st.cta_scale > 0 ? st.cta_scale : 4;  // quarters of the default CTA counts
     switch (phase) {
         case 0:
-            k_overlap<<<dim3(per_map(152 * 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(fps, bs, st);
+            k_overlap<<<dim3(per_map(76 * 2 * q / 2, G, 8), G), SER_THREADS, OV_SMEM, st_>>>(fps, bs, st);
             return 1;
         case 1:
-            k_score<<<dim3(per_map(152, G, 4), G), 256, 0, st_>>>(fps, bs, st);
+            k_score<<<dim3(per_map(38 * q, G, 4), G), 256, 0, st_>>>(fps, bs, st);
             return 1;
         case 2:
             k_union<<<dim3(1, G), UNION_THREADS, UNION_SMEM, st_>>>(fps, bs, st);
             return 1;
         default:
-            k_apply<<<dim3(per_map(152 * 2, G, 8), G), 256, 0, st_>>>(fps, bs, st);
+            k_apply<<<dim3(per_map(76 * q, G, 8), G), 256, 0, st_>>>(fps, bs, st);
             return 1;
     }
 }

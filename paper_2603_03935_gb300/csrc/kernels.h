@@ -54,7 +54,8 @@ int launch_dbscan(const FrameParams* fps, const BatchScratch& bs, int f0, int nb
 int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
                    cudaStream_t st);
 int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);
-// frames per back-projection/entries launch: their per-frame hashes stay in L2
+// default frames per back-projection/entries/DBSCAN launch (their per-frame
+// hashes stay in L2); the runner's tuning may pick another
 constexpr int GEOMETRY_CHUNK = 4;
 
 // start of a batch's serial part: every map's edge and copy counters to zero

@@ -163,3 +163,45 @@ def test_group_room_scale_maps(torch_dev):
             for gk, ok in common.COUNT_FIELDS:
                 assert stats[g][j][gk] == o[ok], f"room map {g} frame {j} {gk}"
         common.compare_maps(maps[g], om, ctx=f"room map {g}")
+
+
+def test_schedules_leave_results_unchanged_and_autotune_picks_one(torch_dev):
+    # the launch schedule (frames per geometry launch, serial CTA counts)
+    # changes no result; the autotuner times fresh maps and keeps the tuned
+    # map and group untouched
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap
+    sc = synth.tiny_scene()
+    fr = sc.render(range(16))
+    frames = [_dframe(torch, dev, fr, i) for i in range(16)]
+    omap = oracle.OracleMap(**common.to_oracle_cfg(common.disc_cfg(sc)))
+    for i in range(16):
+        omap.integrate(*oracle.frame_args(fr, i))
+    for geo, q in ((4, 4), (1, 1), (2, 8), (8, 2), (32, 32)):
+        m = DiscMap(**common.disc_cfg(sc, batch_frames=8))
+        m.set_schedule(geo, q)
+        _, done, rc = m.integrate_frames(frames)
+        assert rc == 0 and done == 16
+        common.compare_maps(m, omap, ctx=f"schedule {geo}/{q}")
+    m = DiscMap(**common.disc_cfg(sc, batch_frames=8))
+    rep = m.autotune(frames[:8], reps=1)
+    assert rep["candidates"] == 9 and rep["best_ms"] <= rep["default_ms"]
+    assert rep["geometry_chunk"] in (2, 4, 8) and rep["serial_ctas"] in (2, 4, 8)
+    assert m.counts()[0] == 0
+    _, done, rc = m.integrate_frames(frames)
+    assert rc == 0
+    common.compare_maps(m, omap, ctx="after autotune")
+    # a group tuned on two maps' sample, then used
+    a, b = DiscMap(**common.disc_cfg(sc)), DiscMap(**common.disc_cfg(sc))
+    grp = DiscGroup(max_maps=2, frames_per_map=4, embed_dim=sc.dim, patch_h=sc.patch_h, patch_w=sc.patch_w,
+                    max_width=sc.width, max_height=sc.height, max_masks=sc.max_masks)
+    from paper_2603_03935_gb300 import binding
+    arr = (binding.Frame * 4)()
+    for i in range(4):
+        arr[i] = frames[i][0]
+    grep = grp.autotune([a, b], [arr, arr], [4, 4], reps=1)
+    assert grep["candidates"] == 9 and a.counts()[0] == 0 and b.counts()[0] == 0
+    _, done, rc = grp.integrate([a, b], [frames, frames])
+    assert rc == 0 and done == [16, 16]
+    common.compare_maps(a, omap, ctx="tuned group, map a")
+    common.compare_maps(b, omap, ctx="tuned group, map b")
