@@ -360,27 +360,6 @@ int launch_slot_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t
     return 2;
 }
 
-// the sums the second grid's view accumulates per slot: column sums, pixel
-// counts, ||g||^2 and the residual-norm sum (its counters are the primary's)
-__global__ void k_view_clear(BatchScratch bs, int D, int MM)
-{
-    const Scratch sc = bs.frame(blockIdx.y);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(D, MM); i += gridDim.x * blockDim.x) {
-        if (i < D) sc.sumF[i] = 0;
-        if (i < MM) sc.npix[i] = 0;
-        if (i == 0) {
-            *sc.gg = 0;
-            *sc.nsum = 0;
-        }
-    }
-}
-
-int launch_view_clear(const BatchScratch& bs, int B, int D, int MM, cudaStream_t st)
-{
-    k_view_clear<<<dim3(4, B), 256, 0, st>>>(bs, D, MM);
-    return 1;
-}
-
 // launch on frames [f0, f0 + nb) of the batch
 int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st)
 {

@@ -87,29 +87,12 @@ __device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned lo
     atomicAdd(&ss.ocnt[t], 1);
 }
 
-// one more voxel of pair okey in the block's shared pair hash; false when a
-// bounded probe finds no room (the caller then adds it to the frame's hash)
-__device__ __forceinline__ bool add_pair_shared(unsigned long long* pkey, int* pcnt, unsigned long long okey)
-{
-    unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
-    for (int pr = 0; pr < 32; pr++) {
-        const unsigned long long prev = atomicCAS(&pkey[t], EMPTY_KEY, okey);
-        if (prev == EMPTY_KEY || prev == okey) {
-            atomicAdd(&pcnt[t], 1);
-            return true;
-        }
-        t = (t + 1) & (OV_SLOTS - 1);
-    }
-    return false;
-}
-
 // Neighbourhood overlap (overlap_dilation): segment voxel `key` (label lab,
 // -1 if absent) overlaps each distinct instance labelling it or one of its 26
-// neighbours, once.  The pairs are staged in the block's shared hash like the
-// plain path's; one entry may add up to 27, so a full shared hash spills to
+// neighbours, once.  One entry may add up to 27 pairs, so they go straight to
 // the frame's pair hash.
 __device__ void dilated_pairs(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
-                              int m, unsigned long long key, int lab, unsigned long long* pkey, int* pcnt)
+                              int m, unsigned long long key, int lab)
 {
     int roots[27];
     int nr = 0;
@@ -143,10 +126,7 @@ __device__ void dilated_pairs(const Scratch& sc, const SerialScratch& ss, const 
             if (!seen) roots[nr++] = r;
         }
     }
-    for (int j = 0; j < nr; j++) {
-        const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)roots[j];
-        if (!add_pair_shared(pkey, pcnt, okey)) add_pair(sc, ss, okey);
-    }
+    for (int j = 0; j < nr; j++) add_pair(sc, ss, ((unsigned long long)m << 32) | (unsigned)roots[j]);
 }
 
 __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const VoxelTable& vt, const Instances& inst,
@@ -181,7 +161,7 @@ __device__ void phase_overlap(const Scratch& sc, const SerialScratch& ss, const 
                     h = (h + 1) & vt.mask;
                 }
             }
-            if (dilate) dilated_pairs(sc, ss, vt, inst, m, key, lab, pkey, pcnt);
+            if (dilate) dilated_pairs(sc, ss, vt, inst, m, key, lab);
             if (lab >= 0 && !dilate) {
                 const unsigned long long okey = ((unsigned long long)m << 32) | (unsigned)inst.parent[lab];
                 unsigned t = (unsigned)(mix64(okey) & (OV_SLOTS - 1));
@@ -466,6 +446,17 @@ constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (
 
 __device__ __forceinline__ unsigned uhash(unsigned k, unsigned mask) { return (unsigned)(mix64(k) & mask); }
 
+// float <-> unsigned key with the same order (for atomicMax over floats)
+__device__ __forceinline__ unsigned f2key(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __device__ __forceinline__ int uf_find(const int* uf, int x)
 {
     while (true) {
@@ -603,27 +594,40 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     __syncthreads();
     for (int m = tid; m < M; m += UNION_THREADS) srep[m] = anchor[m] != INT_MAX ? gid[uf[anchor[m]]] : -1;
     __syncthreads();
-    // (4) new instances for live segments without an edge, in mask order
-    if (tid == 0) {
-        int id = s_next;
-        for (int m = 0; m < M; m++) {
-            if (snv[m] > 0 && srep[m] < 0) {
-                if (id >= inst.cap) { set_err(ctr, DISC_ERR_CAPACITY); break; }
-                srep[m] = id;
-                inst.parent[id] = id;
-                inst.count[id] = 0;
-                inst.Q[id] = sq[m];
-                inst.n_obs[id] = 1;
-                const int c = s_ncopy++;
-                ss.copy_dst[c] = id;
-                ss.copy_src[c] = -(m + 1);
-                id++;
-                s_new++;
-            }
+    // (4) new instances for live segments without an edge, in mask order:
+    //     the id of mask m is next_id plus the number of such masks before it
+    //     (a block-wide exclusive scan; M <= UNION_THREADS)
+    {
+        __shared__ int wtot[UNION_THREADS / 32];
+        const int lane = tid & 31, wid = tid >> 5;
+        const bool want = tid < M && snv[tid] > 0 && srep[tid] < 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, want);
+        if (lane == 0) wtot[wid] = __popc(bal);
+        __syncthreads();
+        int before = __popc(bal & ((1u << lane) - 1)), total = 0;
+        for (int w = 0; w < UNION_THREADS / 32; w++) {
+            before += w < wid ? wtot[w] : 0;
+            total += wtot[w];
         }
-        if (!ctr->err) {
-            *next_id = id;
-            s_next = id;
+        const int base = s_next;
+        if (base + total > inst.cap) {
+            if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
+        } else if (want) {
+            const int id = base + before, m = tid;
+            srep[m] = id;
+            inst.parent[id] = id;
+            inst.count[id] = 0;
+            inst.Q[id] = sq[m];
+            inst.n_obs[id] = 1;
+            ss.copy_dst[before] = id;
+            ss.copy_src[before] = -(m + 1);
+        }
+        __syncthreads();
+        if (tid == 0 && !ctr->err) {
+            *next_id = base + total;
+            s_next = base + total;
+            s_new = total;
+            s_ncopy = total;
         }
     }
     __syncthreads();
@@ -631,41 +635,59 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     for (int m = tid; m < M; m += UNION_THREADS) sc.segrep[m] = srep[m];
     // (5) fusion per component: the candidates in the order (members by
     //     ascending id, then segments by ascending mask) keep the first one
-    //     whose Q is the component's maximum (strict '>' while scanning)
+    //     whose Q is the component's maximum (strict '>' while scanning):
+    //     the component's maximum (an atomic max on order-preserving keys),
+    //     then the smallest member id with that Q, else the smallest mask;
+    //     the stored Q is the winner's own value.  The edge arrays are no
+    //     longer needed and hold part of the per-root scratch.
+    unsigned* qmax = (unsigned*)best_q;                              // [nloc] key of the max Q
+    int* obs = best_src;                                             // [nloc] observations
+    unsigned long long* src_inst = (unsigned long long*)em;          // [nloc] (id << 32 | local) at the max
+    int* src_seg = ek;                                               // [nloc] smallest mask at the max
     for (int r = tid; r < nloc; r += UNION_THREADS) {
-        best_src[r] = INT_MIN;
-        if (uf[r] != r) continue;
-        const int rep = gid[r];
-        float q = -INFINITY;
-        int obs = 0;
-        for (int x = 0; x < nloc; x++) {
-            if (uf[x] != r) continue;
-            obs += oloc[x];
-            q = fmaxf(q, qloc[x]);
-        }
-        for (int m = 0; m < M; m++)
-            if (srep[m] == rep) {
-                obs++;
-                q = fmaxf(q, sq[m]);
-            }
-        int src = INT_MAX;
-        for (int x = 0; x < nloc; x++)
-            if (uf[x] == r && qloc[x] == q) src = min(src, gid[x]);
-        if (src == INT_MAX)
-            for (int m = 0; m < M && src == INT_MAX; m++)
-                if (srep[m] == rep && sq[m] == q) src = -(m + 1);
-        best_src[r] = src;
-        best_q[r] = q;
-        inst.n_obs[rep] = obs;
+        qmax[r] = 0u;
+        obs[r] = 0;
+        src_inst[r] = ~0ull;
+        src_seg[r] = INT_MAX;
     }
+    // the local root of each segment that joined a component
+    for (int m = tid; m < M; m += UNION_THREADS) snv[m] = anchor[m] != INT_MAX ? uf[anchor[m]] : -1;
+    __syncthreads();
+    for (int x = tid; x < nloc; x += UNION_THREADS) {
+        atomicMax(&qmax[uf[x]], f2key(qloc[x]));
+        atomicAdd(&obs[uf[x]], oloc[x]);
+    }
+    for (int m = tid; m < M; m += UNION_THREADS)
+        if (snv[m] >= 0) {
+            atomicMax(&qmax[snv[m]], f2key(sq[m]));
+            atomicAdd(&obs[snv[m]], 1);
+        }
+    __syncthreads();
+    for (int x = tid; x < nloc; x += UNION_THREADS)
+        if (qloc[x] == key2f(qmax[uf[x]]))
+            atomicMin(&src_inst[uf[x]], ((unsigned long long)(unsigned)gid[x] << 32) | (unsigned)x);
+    for (int m = tid; m < M; m += UNION_THREADS)
+        if (snv[m] >= 0 && sq[m] == key2f(qmax[snv[m]])) atomicMin(&src_seg[snv[m]], m);
     __syncthreads();
     for (int r = tid; r < nloc; r += UNION_THREADS) {
-        const int src = best_src[r];
-        if (src == INT_MIN || src == gid[r]) continue;
+        if (uf[r] != r) continue;
+        const int rep = gid[r];
+        inst.n_obs[rep] = obs[r];
+        int src;
+        float q;
+        if (src_inst[r] != ~0ull) {
+            const int x = (int)(src_inst[r] & 0xffffffffu);
+            src = gid[x];
+            q = qloc[x];
+        } else {
+            src = -(src_seg[r] + 1);
+            q = sq[src_seg[r]];
+        }
+        if (src == rep) continue;
         const int c = atomicAdd(&s_ncopy, 1);
-        ss.copy_dst[c] = gid[r];
+        ss.copy_dst[c] = rep;
         ss.copy_src[c] = src;
-        inst.Q[gid[r]] = best_q[r];
+        inst.Q[rep] = q;
     }
     // (6) merge members into their representative
     for (int x = tid; x < nloc; x += UNION_THREADS) {
