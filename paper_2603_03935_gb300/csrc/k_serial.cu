@@ -23,25 +23,6 @@ namespace disc {
 
 __device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(&c->err, 0, code); }
 
-// an error of the previous frame of the same map in the same call stops this one
-__device__ __forceinline__ bool frame_blocked(const BatchScratch& bs, const SerialStep& st, int g, int slot)
-{
-    const Scratch sc = bs.frame(slot);
-    if (sc.ctr->err) return true;
-    int pe = 0;
-    if (st.j > 0) {
-        pe = bs.frame(st.slot_of[g * st.J + st.j - 1]).ctr->err;
-    } else {
-        const int h = st.prev_hist[g];
-        if (h >= 0) pe = st.hist[h].err;
-    }
-    if (pe) {
-        set_err(sc.ctr, pe);
-        return true;
-    }
-    return false;
-}
-
 // ---- overlap histogram -----------------------------------------------------------
 // Each block takes 256 entries at a time.  Their (segment, root) pairs are
 // counted in a shared-memory hash first; only the block's distinct pairs
@@ -815,14 +796,42 @@ __device__ void phase_apply(const FrameParams& fp, const Scratch& sc, const Scra
 // once per block (another block may raise an error while this one reads), so
 // every thread of the block takes the same path.  Returns the frame slot, or
 // -1 when map g has no frame j or the frame is blocked.
-__device__ int block_slot(const BatchScratch& bs, const SerialStep& st, bool* blocked)
+// The frame slot of this block's map (block row g) and whether the frame is
+// blocked: by its own error, or (full check, the frame's first serial kernel)
+// by an error of the map's previous frame, which is then copied into this
+// frame's counters so that its later kernels need only their own.  Warp 0
+// loads the slot indices side by side, then both status words: two round
+// trips before the block's barrier.
+__device__ int block_slot(const BatchScratch& bs, const SerialStep& st, bool* blocked, bool full)
 {
     __shared__ int s_slot, s_blocked;
     const int g = blockIdx.y;
-    if (threadIdx.x == 0) {
-        const int slot = st.slot_of[g * st.J + st.j];
-        s_slot = slot;
-        s_blocked = slot >= 0 && frame_blocked(bs, st, g, slot) ? 1 : 0;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const bool prev_in_batch = st.j > 0;
+        int v = -1;
+        if (lane == 0)
+            v = st.slot_of[g * st.J + st.j];
+        else if (lane == 1 && full)
+            v = prev_in_batch ? st.slot_of[g * st.J + st.j - 1] : st.prev_hist[g];
+        const int slot = __shfl_sync(0xffffffffu, v, 0);
+        const int pidx = __shfl_sync(0xffffffffu, v, 1);
+        int e = 0;
+        if (lane == 0 && slot >= 0)
+            e = bs.frame(slot).ctr->err;
+        else if (lane == 1 && full && pidx >= 0)
+            e = prev_in_batch ? bs.frame(pidx).ctr->err : st.hist[pidx].err;
+        const int own = __shfl_sync(0xffffffffu, e, 0);
+        const int prev = __shfl_sync(0xffffffffu, e, 1);
+        if (lane == 0) {
+            bool b = slot >= 0 && own != 0;
+            if (slot >= 0 && !b && full && prev) {
+                set_err(bs.frame(slot).ctr, prev);
+                b = true;
+            }
+            s_slot = slot;
+            s_blocked = b ? 1 : 0;
+        }
     }
     __syncthreads();
     const int slot = s_slot;
@@ -837,7 +846,7 @@ __global__ void __launch_bounds__(SER_THREADS) k_overlap(const FrameParams* fps,
 {
     extern __shared__ __align__(16) unsigned char ov_smem[];
     bool blocked;
-    const int slot = block_slot(bs, st, &blocked);
+    const int slot = block_slot(bs, st, &blocked, true);
     if (slot < 0 || blocked) return;
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
@@ -849,7 +858,7 @@ __global__ void __launch_bounds__(SER_THREADS) k_overlap(const FrameParams* fps,
 __global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
     bool blocked;
-    const int slot = block_slot(bs, st, &blocked);
+    const int slot = block_slot(bs, st, &blocked, false);
     if (slot < 0 || blocked) return;
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
@@ -861,7 +870,7 @@ __global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* f
 {
     extern __shared__ __align__(16) unsigned char union_smem[];
     bool blocked;
-    const int slot = block_slot(bs, st, &blocked);
+    const int slot = block_slot(bs, st, &blocked, false);
     if (slot < 0 || blocked) return;
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
@@ -872,7 +881,7 @@ __global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* f
 __global__ void k_apply(const FrameParams* fps, BatchScratch bs, SerialStep st)
 {
     bool blocked;
-    const int slot = block_slot(bs, st, &blocked);
+    const int slot = block_slot(bs, st, &blocked, false);
     if (slot < 0) return;
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
