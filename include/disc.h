@@ -356,6 +356,17 @@ disc_status disc_token_stats_static(const void* tokens, int32_t token_dtype, int
                                     const float* global_embed, float eps, float* Dp, float* cosg,
                                     void* cuda_stream);
 
+/* ---- Test hooks (failure paths, made without a GPU fault) -------------------
+ * disc_debug_fail_alloc_after: after n more device allocations of the library
+ * the next ones fail as out of memory, until called again with n < 0 (also
+ * read once from the environment variable DISC_FAULT_ALLOC_AFTER).  Calls that
+ * hit it return DISC_ERR_OOM and leave maps as they were.
+ * disc_debug_gemm_stall: while on, the pooling GEMM on `device` issues no
+ * MMA, so its bounded waits (about 1 s) run out and each frame it serves fails
+ * with DISC_ERR_TIMEOUT, the map unchanged and the context usable. */
+void disc_debug_fail_alloc_after(int64_t n);
+disc_status disc_debug_gemm_stall(int32_t device, int32_t on);
+
 /* ---- Launch schedule and autotuner -----------------------------------------
  * How a map's (or a group's) batches are cut into launches: the frames per
  * launch of the geometry kernels (back-projection, entries, DBSCAN), whose

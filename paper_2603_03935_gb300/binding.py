@@ -137,6 +137,10 @@ def lib():
         L.disc_query_heatmap.argtypes = [c_vp, c_i32, c_i32, c_i32, c_vp, c_f32, c_vp, c_vp]
         L.disc_query_heatmap.restype = ctypes.c_int
         L.disc_map_export_assoc.argtypes = [c_vp, c_vp, c_i32]
+        L.disc_debug_fail_alloc_after.argtypes = [c_i64]
+        L.disc_debug_fail_alloc_after.restype = None
+        L.disc_debug_gemm_stall.argtypes = [c_i32, c_i32]
+        L.disc_debug_gemm_stall.restype = ctypes.c_int
         L.disc_map_set_schedule.argtypes = [c_vp, P(Schedule)]
         L.disc_group_set_schedule.argtypes = [c_vp, P(Schedule)]
         L.disc_map_autotune.argtypes = [c_vp, c_vp, c_i32, c_i32, P(TuneReport)]
@@ -274,6 +278,18 @@ def token_stats_static(tokens, global_embed=None, eps=1e-6, stream=None):
                                        Dp.data_ptr(), cosg.data_ptr(), s.cuda_stream)
     _check(rc, "disc_token_stats_static")
     return Dp, cosg
+
+
+def debug_fail_alloc_after(n: int):
+    """Test hook: after n more device allocations the library's allocations
+    fail as out of memory (n < 0: off)."""
+    lib().disc_debug_fail_alloc_after(int(n))
+
+
+def debug_gemm_stall(on: bool, device: int = 0):
+    """Test hook: the pooling GEMM issues no MMA, so its bounded waits run out
+    (~1 s) and the frames it serves fail with DISC_ERR_TIMEOUT."""
+    _check(lib().disc_debug_gemm_stall(int(device), 1 if on else 0), "disc_debug_gemm_stall")
 
 
 def query_heatmap(tokens, query, eps=1e-6, stream=None):

@@ -4,6 +4,7 @@
 // k_gemm.cu, k_geometry.cu and k_serial.cu, enqueued on the stream of the
 // map (its own calls) or of the group (batches over many maps).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -22,6 +23,25 @@ namespace {
 
 constexpr int PAIR_CAP = 8192;   // distinct (segment, instance) overlaps per frame (k_serial.cu)
 
+// Host-side fault injection (tests): after this many more device
+// allocations, the next one fails as if the device were out of memory
+// (-1: off).  Set by disc_debug_fail_alloc_after or the environment variable
+// DISC_FAULT_ALLOC_AFTER.
+std::atomic<int64_t> g_fail_alloc_after{[] {
+    const char* e = std::getenv("DISC_FAULT_ALLOC_AFTER");
+    return e ? (int64_t)std::atoll(e) : (int64_t)-1;
+}()};
+
+bool injected_alloc_failure()
+{
+    int64_t n = g_fail_alloc_after.load();
+    while (n >= 0) {
+        if (n == 0) return true;  // stays at 0: every later allocation fails too, until reset
+        if (g_fail_alloc_after.compare_exchange_weak(n, n - 1)) return false;
+    }
+    return false;
+}
+
 struct DevAlloc {
     std::vector<void*> ptrs;
     int64_t bytes = 0;
@@ -31,6 +51,10 @@ struct DevAlloc {
     {
         void* p = nullptr;
         if (n == 0) n = 1;
+        if (injected_alloc_failure()) {
+            failed = true;
+            return nullptr;
+        }
         if (cudaMalloc(&p, sizeof(T) * n) != cudaSuccess) {
             cudaGetLastError();
             failed = true;
@@ -1329,6 +1353,13 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         FrameParams* hfpa = r.Da ? (FrameParams*)(blk.data() + r.off_fpa) : nullptr;
         int slot = 0;
         CopyList cl;
+        // a batch that fails before its counters reach the call's history
+        // leaves no history entries behind: its frames count as not done
+        std::vector<size_t> mark(G);
+        for (int gi = 0; gi < G; gi++) mark[gi] = w[gl[gi]].hist_idx.size();
+        auto undo = [&] {
+            for (int gi = 0; gi < G; gi++) w[gl[gi]].hist_idx.resize(mark[gi]);
+        };
         // host inputs of this batch go to staging set k once the set's last
         // batch has read its inputs (its stateless part), on the input
         // stream, so they overlap the previous batch's kernels
@@ -1353,10 +1384,16 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_ready[k], r.stream_in));
             if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_ready[k], 0));
         }
-        if (s != DISC_OK) break;
+        if (s != DISC_OK) {
+            undo();
+            break;
+        }
         // pageable source: the call returns once the block is staged
         s = cuda_status(cudaMemcpyAsync(r.d_param[k], blk.data(), r.param_bytes, cudaMemcpyHostToDevice, ss));
-        if (s != DISC_OK) break;
+        if (s != DISC_OK) {
+            undo();
+            break;
+        }
         if (r.timing && !r.graphs_off && launch_timed_graph(r, k, S, G, J, combos)) {
             // both parts with their phase events, one graph on the runner's stream
             if (copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], r.stream));
@@ -1378,6 +1415,10 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                                             cudaMemcpyDeviceToDevice, sr));
         if (s == DISC_OK && pipe) s = cuda_status(cudaEventRecord(r.ev_serial[k], sr));
         if (s == DISC_OK) s = cuda_status(cudaGetLastError());
+        if (s != DISC_OK) {
+            undo();
+            break;
+        }
         for (int gi = 0; gi < G; gi++) {
             Work& wk = w[gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
@@ -1776,6 +1817,16 @@ disc_status disc_group_integrate(disc_group* g, disc_map* const* maps, int32_t n
     if (n_done)
         for (int i = 0; i < n_maps; i++) n_done[i] = w[i].done;
     return s;
+}
+
+// ---- test hooks: failures made on the host, waits that run out ---------------
+
+void disc_debug_fail_alloc_after(int64_t n) { g_fail_alloc_after.store(n < 0 ? -1 : n); }
+
+disc_status disc_debug_gemm_stall(int32_t device, int32_t on)
+{
+    CK(cudaSetDevice(device));
+    return cuda_status(set_gemm_stall(on != 0));
 }
 
 // ---- launch schedule and autotuner -------------------------------------------

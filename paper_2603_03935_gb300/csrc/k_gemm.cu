@@ -162,6 +162,17 @@ __host__ size_t gemm_smem_bytes(int NT)
     return std::min(base + GEMM_SMEM_GUARD, std::max(base, SMEM_MAX));
 }
 
+// Test hook: when set, the kernel issues no MMA and no commit, so its bounded
+// waits run out and the frame fails with DISC_ERR_TIMEOUT (nothing is in
+// flight when the tensor memory is freed).
+__device__ int g_gemm_stall = 0;
+
+cudaError_t set_gemm_stall(bool on)
+{
+    const int v = on ? 1 : 0;
+    return cudaMemcpyToSymbol(g_gemm_stall, &v, sizeof(v));
+}
+
 // PR: the disc_precision of the frames this instance serves
 template <typename T, int PR>
 __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT)
@@ -208,6 +219,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     const int nchunks = (P + GEMM_KC - 1) / GEMM_KC;
     bool failed = false;
     int last_commit = -1;  // chunk of the most recent commit (same on all threads)
+    const bool stall = g_gemm_stall != 0;  // uniform: read once
 
     for (int c = 0; c < nchunks && !failed; c++) {
         const int s = c & 1;
@@ -329,7 +341,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         // make the generic-proxy stores visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !stall) {
             fence_after();
             if constexpr (F8) {
                 // one K step of 32 = two 16-byte core-matrix columns of e4m3
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
             }
             mma_commit(smem_u32(&mbar[s]));
         }
-        last_commit = c;
+        if (!stall) last_commit = c;
     }
     if (!failed && nchunks > 0) {
         const int c = nchunks - 1;

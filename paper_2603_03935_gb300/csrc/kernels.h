@@ -72,6 +72,7 @@ size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);
 cudaError_t set_feature_kernel_attrs(int max_dyn_smem);
 cudaError_t set_gemm_kernel_attrs();
+cudaError_t set_gemm_stall(bool on);
 cudaError_t set_serial_kernel_attrs();
 
 // end-of-trajectory finalisation, phases 0..2 (k_final.cu)
