@@ -205,7 +205,8 @@ def measured_traffic(kernel):
 
 def algorithmic_bytes(phase, sts, H, W, P, D, Ms, Kpad):
     """Bytes a phase must move for all frames of the timed batch together
-    (see the design doc); divided by the phase's launches it gives the bytes per
+    (inputs read once, hash entries and table rows touched once: the per-frame
+    models below); divided by the phase's launches it gives the bytes per
     launch.  sts: per-frame stats, Ms: masks per frame."""
     per_frame = {
         "backproject": lambda s, M: 6 * H * W + 44 * s["unique_seg_voxels"],
