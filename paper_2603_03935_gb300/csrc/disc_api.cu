@@ -129,6 +129,7 @@ struct Runner {
     unsigned long long* h_room = nullptr;  // pinned copy of d_room
     cudaEvent_t ev_room = nullptr;
     cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {};  // staging set k filled / read by its last batch
+    cudaEvent_t ev_in_half[2] = {};                        // the second half of set k filled
     float* d_depth = nullptr;         // staging of host inputs: two sets (one per scratch set) of one
                                       // slot per frame of a batch
     uint16_t* d_labels = nullptr;
@@ -476,6 +477,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     CK(cudaEventCreateWithFlags(&r.ev_room, cudaEventDisableTiming));
     for (int k = 0; k < 2; k++) {
         CK(cudaEventCreateWithFlags(&r.ev_in_ready[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&r.ev_in_half[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_in_free[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_state[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_serial[k], cudaEventDisableTiming));
@@ -532,7 +534,8 @@ void runner_release(Runner& r)
         if (r.ev_serial[k]) cudaEventDestroy(r.ev_serial[k]);
         if (r.ev_in_ready[k]) cudaEventDestroy(r.ev_in_ready[k]);
         if (r.ev_in_free[k]) cudaEventDestroy(r.ev_in_free[k]);
-        r.ev_state[k] = r.ev_serial[k] = r.ev_in_ready[k] = r.ev_in_free[k] = nullptr;
+        if (r.ev_in_half[k]) cudaEventDestroy(r.ev_in_half[k]);
+        r.ev_state[k] = r.ev_serial[k] = r.ev_in_ready[k] = r.ev_in_free[k] = r.ev_in_half[k] = nullptr;
     }
     for (cudaEvent_t e : r.ev_pool) cudaEventDestroy(e);
     r.ev_pool.clear();
@@ -858,15 +861,18 @@ void reset_timing(Runner& r, bool enable)
 constexpr int COMBO_DBSCAN = 1 << 6;
 constexpr int COMBO_ASSOC = 1 << 7;  // some frame's map has a second token grid
 
-int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
+// slots [base, base + S) of set k (base > 0: the second half of a batch whose
+// halves wait for their own input copies)
+int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st, int base = 0)
 {
     const bool any_bf16 = (combos & 070) != 0, any_f32 = (combos & 07) != 0;  // bits 0-5
     bool any[2][3];
     for (int t = 0; t < 2; t++)
         for (int q = 0; q < 3; q++) any[t][q] = (combos >> (3 * t + q)) & 1;
     const int D = r.D, P = r.P, Mmax = r.Mmax;
-    const BatchScratch& bs = r.bs[k];
-    const FrameParams* dfp = r.fps(k);
+    BatchScratch bs = r.bs[k];
+    bs.base = r.bs[k].frame(base);
+    const FrameParams* dfp = r.fps(k) + base;
     const MapRefs* refs = r.refs(k);
     const int64_t before = r.launches;
     run_phase(r, PH_CLEAR, st, [&] { return launch_slot_clear(bs, S, D, r.MM, st); });
@@ -878,8 +884,9 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st)
     if ((combos & COMBO_ASSOC) && r.Da) {
         // the association features: the same kernels on the second grid's
         // view (pixel-mean weights; frames of maps without it are inert)
-        const BatchScratch& va = r.bsa[k];
-        const FrameParams* dfa = r.fpa(k);
+        BatchScratch va = r.bsa[k];
+        va.base = r.bsa[k].frame(base);
+        const FrameParams* dfa = r.fpa(k) + base;
         run_phase(r, PH_CLEAR, st, [&] { return launch_view_clear(va, S, r.Da, r.MM, st); });
         run_phase(r, PH_TOKENS, st, [&] { return launch_token_stats(dfa, va, S, r.Pa, r.Da, any_bf16, any_f32, st); });
         run_phase(r, PH_COVERAGE, st, [&] { return launch_coverage(dfa, va, S, r.Pha, r.Pwa, Mmax, st); });
@@ -925,7 +932,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 
 long long graph_key(int part, int k, int S, int G, int J, int combos)
 {
-    return (((((((long long)S << 11) | G) << 9) | J) << 8 | combos) << 2) | (part << 1) | k;
+    return (((((((long long)S << 11) | G) << 9) | J) << 8 | combos) << 3) | (part << 1) | k;
 }
 
 // A part's kernel sequence captured once per shape and replayed.  A shape
@@ -1089,6 +1096,13 @@ struct CopyList {
             v.back().bytes += bytes;
         else
             v.push_back({(char*)dst, (const char*)src, bytes});
+    }
+    void append(CopyList& o)  // o's copies after this list's, merged where they continue
+    {
+        for (int k = 0; k < 5; k++) {
+            for (const Item& it : o.kind[k]) add(k, it.dst, it.src, it.bytes);
+            o.kind[k].clear();
+        }
     }
     bool empty() const
     {
@@ -1352,7 +1366,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         int* hprev = (int*)(blk.data() + r.off_prev);
         FrameParams* hfpa = r.Da ? (FrameParams*)(blk.data() + r.off_fpa) : nullptr;
         int slot = 0;
-        CopyList cl;
+        CopyList cl[2];  // host inputs of the batch's first and second half
         // a batch that fails before its counters reach the call's history
         // leaves no history entries behind: its frames count as not done
         std::vector<size_t> mark(G);
@@ -1372,17 +1386,27 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && s == DISC_OK; j++) {
                 s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, hfpa ? hfpa + slot : nullptr,
-                                 &cl);
+                                 &cl[2 * slot >= S ? 1 : 0]);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
             }
         }
-        const bool copied = !cl.empty();
+        // With host inputs (and not one timed graph), the batch's stateless
+        // part runs in two halves: the second half's copies run while the
+        // first half computes.
+        const bool copied = !cl[0].empty() || !cl[1].empty();
+        const bool halves = copied && !(r.timing && !r.graphs_off) && S >= 8;
+        const int Sh = halves ? S / 2 : S;
+        if (!halves) cl[0].append(cl[1]);
         if (s == DISC_OK && copied) {
-            s = cl.issue(r.stream_in);
+            s = cl[0].issue(r.stream_in);
             if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_ready[k], r.stream_in));
             if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_ready[k], 0));
+            if (s == DISC_OK && halves) {
+                s = cl[1].issue(r.stream_in);
+                if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_half[k], r.stream_in));
+            }
         }
         if (s != DISC_OK) {
             undo();
@@ -1398,8 +1422,17 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             // both parts with their phase events, one graph on the runner's stream
             if (copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], r.stream));
         } else {
-            s = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
-                         [&] { return enqueue_stateless(r, k, S, combos, ss); });
+            if (halves) {
+                s = run_part(r, graph_key(2, k, Sh, 0, 0, combos), ss,
+                             [&] { return enqueue_stateless(r, k, Sh, combos, ss); });
+                if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_half[k], 0));
+                if (s == DISC_OK)
+                    s = run_part(r, graph_key(3, k, S - Sh, 0, 0, combos), ss,
+                                 [&] { return enqueue_stateless(r, k, S - Sh, combos, ss, Sh); });
+            } else {
+                s = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
+                             [&] { return enqueue_stateless(r, k, S, combos, ss); });
+            }
             if (s == DISC_OK && copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], ss));
             if (s == DISC_OK && pipe) {
                 s = cuda_status(cudaEventRecord(r.ev_state[k], ss));

@@ -66,6 +66,32 @@ def test_tiny_parity_with_host_inputs(torch_dev):
     run_parity(torch_dev, synth.tiny_scene(), range(0, 20, 3), host=True)
 
 
+@pytest.mark.parametrize("batch", [9, 16])
+def test_host_inputs_in_batches_split_in_halves(torch_dev, batch):
+    # batches of 8 or more host frames run their stateless part in two halves,
+    # the second half's copies under the first half's kernels (9: uneven)
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    sc = synth.tiny_scene()
+    fr = sc.render(range(20))
+    hd = torch.from_numpy(fr.depth).pin_memory()
+    hl = torch.from_numpy(fr.labels.view(np.int16)).pin_memory()
+    ht = torch.from_numpy(fr.tokens).pin_memory()
+    d, l, t = hd.numpy(), hl.numpy().view(np.uint16), ht.numpy()
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    frames = [host_frame(d[i], l[i], t[i], fr.poses[i], intr, fr.num_masks[i]) for i in range(20)]
+    cfg = common.disc_cfg(sc, batch_frames=batch)
+    gmap = DiscMap(**cfg)
+    stats, done, rc = gmap.integrate_frames(frames)
+    assert rc == 0 and done == 20
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    for i in range(20):
+        o = omap.integrate(*oracle.frame_args(fr, i))
+        for gk, ok in common.COUNT_FIELDS:
+            assert stats[i][gk] == o[ok], (i, gk)
+    common.compare_maps(gmap, omap, ctx=f"host frames, batches of {batch} in halves")
+
+
 def test_host_inputs_in_one_call_of_many_batches(torch_dev):
     # a whole trajectory from pinned host memory in one call: frames lie back
     # to back, so each batch's copies merge into one per input kind and run
