@@ -277,11 +277,16 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
     const int ne = sc.ctr->n_entries;
     int maxp = 0;
     if (!sc.ctr->err) {
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
-            const unsigned long long hk = sc.sent[i];
+        // whole warps iterate together (lanes past the end idle), so a warp
+        // whose 32 entries share one mask adds its sums with one atomic each
+        const int lane = threadIdx.x & 31;
+        for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ne; i0 += gridDim.x * blockDim.x) {
+            const int i = i0 + lane;
+            const bool valid = i < ne;
+            const unsigned long long hk = valid ? sc.sent[i] : 0ull;
             const int m = (int)(hk >> 54);
             const unsigned long long key = hk & ((1ull << 54) - 1);
-            const SegSlot slot = sc.sslot[sc.slist[i]];
+            const SegSlot slot = valid ? sc.sslot[sc.slist[i]] : SegSlot{0ull, {0, 0, 0}};
             float N[3] = {__double2float_rn(unfix(slot.n[0], S_VEC)), __double2float_rn(unfix(slot.n[1], S_VEC)),
                           __double2float_rn(unfix(slot.n[2], S_VEC))};
             float l2 = __fadd_rn(__fadd_rn(__fmul_rn(N[0], N[0]), __fmul_rn(N[1], N[1])), __fmul_rn(N[2], N[2]));
@@ -304,8 +309,19 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
                     if (!(term > 0.0f)) term = 0.0f;
                 }
             }
-            atomicAdd((unsigned long long*)&s_ang[m - 1], (unsigned long long)fix32f(term, S_VEC));
-            atomicAdd(&s_nv[m - 1], 1);
+            const long long tf = fix32f(term, S_VEC);
+            const int m0 = __shfl_sync(0xffffffffu, m, 0);
+            if (__all_sync(0xffffffffu, valid && m == m0)) {
+                const long long sum = warp_sum(tf);
+                if (lane == 0) {
+                    atomicAdd((unsigned long long*)&s_ang[m0 - 1], (unsigned long long)sum);
+                    atomicAdd(&s_nv[m0 - 1], 32);
+                }
+            } else if (valid) {
+                atomicAdd((unsigned long long*)&s_ang[m - 1], (unsigned long long)tf);
+                atomicAdd(&s_nv[m - 1], 1);
+            }
+            if (!valid) continue;
             // label in the map at the start of the batch (-1: absent then)
             unsigned long long h = mix64(key) & vt.mask;
             int lab = -1, probes = 0;
