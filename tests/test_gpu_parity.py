@@ -238,6 +238,39 @@ def test_empty_and_degenerate_frames(torch_dev):
     common.compare_maps(gmap, omap, ctx="degenerate")
 
 
+def test_maximum_mask_count(torch_dev):
+    # 256 masks per frame (the largest a frame may carry): a wall cut into a
+    # 16 x 16 grid of regions, seen from three slightly shifted poses; every
+    # mask is live, so the new-id scan and the pooling GEMM run at full width
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    H, W, f = 96, 128, 120.0
+    Ph, Pw, D = 12, 16, 64
+    rng = np.random.default_rng(11)
+    means = rng.standard_normal((257, D)).astype(np.float32)
+    v, u = np.mgrid[0:H, 0:W]
+    lab = (1 + (v * 16 // H) * 16 + (u * 16 // W)).astype(np.uint16)  # 1..256
+    cfg = dict(voxel_size=0.02, z_min=0.1, z_max=10.0, eps=1e-6, tau_cos=0.75, lambda_size=3.3, ov_num=1,
+               ov_den=5, embed_dim=D, patch_h=Ph, patch_w=Pw, max_width=W, max_height=H, max_masks=256,
+               min_mask_pixels=12, voxel_capacity=1 << 16, max_load=0.5, instance_capacity=1024)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    intr = (f, f, W / 2, H / 2)
+    for i in range(3):
+        depth = scenes.plane_depth(H, W, f, f, W / 2, H / 2, 1.513 + 0.004 * i)
+        pose = scenes.identity_pose()
+        pose[0, 3] = 0.003 * i
+        pv, pu = np.mgrid[0:Ph, 0:Pw]
+        pid = lab[((2 * pv + 1) * H) // (2 * Ph), ((2 * pu + 1) * W) // (2 * Pw)].reshape(-1)
+        tok = (means[pid] + 0.1 * rng.standard_normal((Ph * Pw, D))).astype(np.float32)
+        st = gmap.integrate(host_frame(depth, lab, tok, pose, intr, 256))
+        o = omap.integrate(depth, lab, tok, pose, intr, 256)
+        common.compare_frame(st, gmap.last_frame(), o, ctx=f"256 masks frame {i}")
+        assert st["live_segments"] == 256
+    common.compare_maps(gmap, omap, ctx="256 masks")
+    assert len(gmap.instances()["parent"]) >= 256
+
+
 def test_token_range_error_leaves_the_map_unchanged(torch_dev):
     torch, dev = torch_dev
     from paper_2603_03935_gb300 import DiscMap, host_frame

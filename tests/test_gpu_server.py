@@ -157,3 +157,37 @@ def test_admission_by_device_memory_budget(torch_dev):
     rc, second = srv.try_open_map(**common.disc_cfg(scs[0]))
     assert rc == 0 and second >= 0
     srv.close()
+
+
+def test_second_grid_and_precisions_in_one_server(torch_dev):
+    # maps with and without a second token grid, at FP32, BF16 and FP8, served
+    # side by side (the server copies every input, second grid included, at
+    # submission); each equals the same frames integrated alone
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    GRID = dict(assoc_dim=96, assoc_patch_h=6, assoc_patch_w=8)
+    scs = _scenes()[:2]
+    frs = [s.render(range(10)) for s in scs]
+    ats = [fr.assoc_tokens(6, 8, 96) for fr in frs]
+    srv = _server(scs, frames_per_map=3, **GRID)
+    kinds = [(0, 2, True), (1, 0, False), (0, 1, False), (1, 2, True)]  # (scene, precision, second grid)
+    cfgs = [common.disc_cfg(scs[s], precision=p, **(GRID if a else {})) for s, p, a in kinds]
+    ids = [srv.open_map(**c) for c in cfgs]
+
+    def frame(g, i):
+        s, _, a = kinds[g]
+        fr, sc = frs[s], scs[s]
+        return host_frame(fr.depth[i], fr.labels[i], fr.tokens[i], fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy),
+                          fr.num_masks[i], assoc_tokens=ats[s][i] if a else None)
+
+    tickets = [(g, srv.submit_frame(ids[g], frame(g, i))) for i in range(10) for g in range(len(kinds))]
+    for g, t in tickets:
+        assert srv.wait_frame(t)["rc"] == 0, g
+    for g, c in enumerate(cfgs):
+        alone = DiscMap(**c)
+        for i in range(10):
+            alone.integrate(frame(g, i))
+        _same_map(srv.map(ids[g]), alone, f"map {g} {kinds[g]}")
+        if kinds[g][2]:
+            assert np.array_equal(srv.map(ids[g]).instances()["A"].view(np.uint32),
+                                  alone.instances()["A"].view(np.uint32))
+    srv.close()
