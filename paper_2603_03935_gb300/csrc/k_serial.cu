@@ -24,7 +24,7 @@ namespace disc {
 __device__ __forceinline__ void set_err(FrameCounters* c, int code) { atomicCAS(&c->err, 0, code); }
 
 // ---- overlap histogram -----------------------------------------------------------
-// Each block takes 256 entries at a time.  Their (segment, root) pairs are
+// Each block takes 1024 entries at a time.  Their (segment, root) pairs are
 // counted in a shared-memory hash first; only the block's distinct pairs
 // then update the frame's global histogram.  Voxels absent from the map go
 // to the new-voxel hash with the lowest segment that contains them.
