@@ -92,7 +92,7 @@ typedef struct {
                                 SMs (a green context; without one, a high-priority stream); <= 0: no
                                 overlap (the default: the overlap measured slower on GB300) */
     int32_t overlap_dilation;/* 1: a segment voxel also overlaps the instances labelling any of its 26
-                                neighbours (the "immediate neighborhood" of Sec. III-B), once per
+                                neighbours (the neighbourhood reading of Sec. III-B), once per
                                 instance; 0 (default): the voxel itself only */
     int32_t assoc_dim;       /* > 0: frames carry a second token grid [assoc_patch_h * assoc_patch_w]
                                 [assoc_dim] (the association encoder's, e.g. DINOv2, Sec. III-A)
@@ -371,15 +371,11 @@ disc_status disc_debug_gemm_stall(int32_t device, int32_t on);
  * How a map's (or a group's) batches are cut into launches: the frames per
  * launch of the geometry kernels (back-projection, entries, DBSCAN), whose
  * per-frame hashes should stay in L2, and the CTA counts of the serial
- * kernels, which trade parallel probes against launch cost; and whether the
- * pooling GEMM loads its token tiles by TMA.  None of them changes any
- * result. */
+ * kernels, which trade parallel probes against launch cost.  Neither changes
+ * any result. */
 typedef struct {
     int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 4) */
     int32_t serial_ctas;     /* serial kernels' CTAs in quarters of the default count, 1..32 (default 4) */
-    int32_t token_tma;       /* 1 (default): the pooling GEMM loads token tiles by TMA where the token
-                                grid allows it (16-byte aligned base and row pitch, at least 128 dims
-                                and 32 patches); 0: plain loads.  The autotuner keeps it as set. */
 } disc_schedule;
 
 typedef struct {

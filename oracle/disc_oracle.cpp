@@ -84,7 +84,7 @@ struct Pose {
 };
 
 // Pinhole back-projection of pixel (u, v) at depth z, then camera -> world
-// (Sec. III-A: "projected into a 3D point cloud").  Pixel centres at +0.5;
+// (Sec. III-A: the masked depth becomes a world point cloud).  Pixel centres at +0.5;
 // the focal lengths enter as reciprocals rounded once to fp32.
 void world_point(const Pose& T, float fx, float fy, float cx, float cy, int u, int v, float z,
                  float p[3])
@@ -473,7 +473,7 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
     }
 
     // (a7) overlap with the map as it stood before this frame.  With
-    // overlap_dilation (the "immediate neighborhood" of Sec. III-B) a segment
+    // overlap_dilation (the neighbourhood reading of Sec. III-B) a segment
     // voxel overlaps every instance that labels it or one of its 26
     // neighbours, once per instance.
     std::vector<std::map<int32_t, int64_t>> ov(M);  // per segment: root -> voxels

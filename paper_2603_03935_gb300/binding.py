@@ -59,7 +59,7 @@ class GroupConfig(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32), ("token_tma", c_i32)]
+    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -67,7 +67,6 @@ class TuneReport(ctypes.Structure):
 
     def as_dict(self):
         return {"geometry_chunk": int(self.best.geometry_chunk), "serial_ctas": int(self.best.serial_ctas),
-                "token_tma": int(self.best.token_tma),
                 "best_ms": float(self.best_ms), "default_ms": float(self.default_ms),
                 "candidates": int(self.candidates)}
 
@@ -367,8 +366,8 @@ class DiscMap:
         """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
         return lib().disc_integrate_frames(self._h, arr, n, stats, None)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, token_tma=1):
-        _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, token_tma))),
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
+        _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
                "disc_map_set_schedule")
 
     def autotune(self, frames, reps=3) -> dict:
@@ -536,8 +535,8 @@ class DiscGroup:
             if stats_arrays is not None else None
         return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, token_tma=1):
-        _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, token_tma))),
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
+        _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
                "disc_group_set_schedule")
 
     def autotune(self, maps, frame_arrays, counts, reps=3) -> dict:

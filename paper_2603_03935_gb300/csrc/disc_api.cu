@@ -143,10 +143,6 @@ struct Runner {
     BatchScratch bsa[2] = {};
     size_t off_fpa = 0;
     unsigned char* d_atok = nullptr;  // staging of host association tokens (two sets)
-    // tensor maps of the slots' token grids (primary, second grid), 128 B each,
-    // after the rest of the parameter block
-    size_t off_tmap = 0, off_tmapa = 0;
-    bool token_tma = true;            // the pooling GEMM loads token tiles by TMA where it can
     // launch schedule (disc_*_set_schedule, disc_*_autotune)
     int geo_chunk = GEOMETRY_CHUNK;   // frames per back-projection / entries / DBSCAN launch
     int cta_scale = 4;                // serial kernels' CTAs in quarters of the default count
@@ -173,8 +169,6 @@ struct Runner {
     const int* slot_of(int k) const { return (const int*)(d_param[k] + off_slot); }
     const FrameParams* fpa(int k) const { return (const FrameParams*)(d_param[k] + off_fpa); }
     const int* prev_hist(int k) const { return (const int*)(d_param[k] + off_prev); }
-    const CUtensorMap* tmaps(int k) const { return (const CUtensorMap*)(d_param[k] + off_tmap); }
-    const CUtensorMap* tmapsa(int k) const { return (const CUtensorMap*)(d_param[k] + off_tmapa); }
 };
 
 struct disc_map {
@@ -369,9 +363,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     r.off_slot = r.off_refs + align256(sizeof(MapRefs) * Gmax);
     r.off_prev = r.off_slot + align256(sizeof(int) * Gmax * Jmax);
     r.off_fpa = r.off_prev + align256(sizeof(int) * Gmax);
-    r.off_tmap = r.off_fpa + (r.Da ? align256(sizeof(FrameParams) * B) : 0);
-    r.off_tmapa = r.off_tmap + align256(sizeof(CUtensorMap) * B);
-    r.param_bytes = r.off_tmapa + (r.Da ? align256(sizeof(CUtensorMap) * B) : 0);
+    r.param_bytes = r.off_fpa + (r.Da ? align256(sizeof(FrameParams) * B) : 0);
     for (int k = 0; k < 2; k++) {
         r.d_param[k] = a.get<unsigned char>(r.param_bytes);
         BatchScratch& bs = r.bs[k];
@@ -888,7 +880,7 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st, int 
     run_phase(r, PH_COVERAGE, st, [&] { return launch_coverage(dfp, bs, S, r.Ph, r.Pw, Mmax, st); });
     run_phase(r, PH_WEIGHTS, st, [&] { return launch_weights(dfp, bs, S, Mmax, st); });
     run_phase(r, PH_POOL_EXACT, st, [&] { return launch_pool_exact(dfp, bs, S, P, D, Mmax, any_bf16, any_f32, st); });
-    run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, r.tmaps(k) + base, st); });
+    run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfp, bs, S, D, Mmax, any, st); });
     if ((combos & COMBO_ASSOC) && r.Da) {
         // the association features: the same kernels on the second grid's
         // view (pixel-mean weights; frames of maps without it are inert)
@@ -901,8 +893,7 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st, int 
         run_phase(r, PH_WEIGHTS, st, [&] { return launch_weights(dfa, va, S, Mmax, st); });
         run_phase(r, PH_POOL_EXACT, st,
                   [&] { return launch_pool_exact(dfa, va, S, r.Pa, r.Da, Mmax, any_bf16, any_f32, st); });
-        run_phase(r, PH_POOL_GEMM, st,
-                  [&] { return launch_pool_gemm(dfa, va, S, r.Da, Mmax, any, r.tmapsa(k) + base, st); });
+        run_phase(r, PH_POOL_GEMM, st, [&] { return launch_pool_gemm(dfa, va, S, r.Da, Mmax, any, st); });
     }
     if (Mmax > 0) {
         for (int f0 = 0; f0 < S; f0 += r.geo_chunk) {
@@ -1132,53 +1123,8 @@ struct CopyList {
 // Host inputs are staged in staging set `set` (copies collected in cl).
 // With a second grid, *outa receives the view of the frame on that grid (for
 // maps without one, an inert view: no tokens, no masks).
-// cuTensorMapEncodeTiled through the runtime's driver entry point
-using EncodeTiled = decltype(&::cuTensorMapEncodeTiled);
-EncodeTiled encode_tiled()
-{
-    static EncodeTiled fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-        }
-        return (EncodeTiled)p;
-    }();
-    return fn;
-}
-
-// The tensor map of a frame's token grid [P][D] for the pooling GEMM's TMA
-// loads: a 2D tensor (dims innermost), boxes of 128 dims x 32 patches, zero
-// fill past the edges.  Sets fp.tma when the grid qualifies (16-byte aligned
-// base and row pitch, at least one box in each direction) and the driver
-// encoded it; otherwise the GEMM loads the tokens with plain loads.
-void token_map(const Runner& r, FrameParams& fp, CUtensorMap* out)
-{
-    fp.tma = 0;
-    memset(out, 0, sizeof(CUtensorMap));
-    const EncodeTiled enc = encode_tiled();
-    const size_t es = fp.token_bf16 ? 2 : 4;
-    if (!r.token_tma || !enc || !fp.tokens || fp.M <= 0 || fp.D < GEMM_MT || fp.P < GEMM_KC) return;
-    if (((uintptr_t)fp.tokens & 15) != 0 || ((size_t)fp.D * es) % 16 != 0) return;
-    const cuuint64_t dims[2] = {(cuuint64_t)fp.D, (cuuint64_t)fp.P};
-    const cuuint64_t strides[1] = {(cuuint64_t)fp.D * es};
-    const cuuint32_t box[2] = {(cuuint32_t)GEMM_MT, (cuuint32_t)GEMM_KC};
-    const cuuint32_t estr[2] = {1, 1};
-    CUtensorMap tm;  // 64-byte aligned by its type; the block's copy need not be
-    const CUresult e =
-        enc(&tm, fp.token_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-            const_cast<void*>(fp.tokens), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (e == CUDA_SUCCESS) {
-        memcpy(out, &tm, sizeof(CUtensorMap));
-        fp.tma = 1;
-    }
-}
-
 disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int set, int slot, int g,
-                         FrameParams* out, FrameParams* outa, CopyList* cl, CUtensorMap* tm, CUtensorMap* tma)
+                         FrameParams* out, FrameParams* outa, CopyList* cl)
 {
     const int P = r.P, D = r.D;
     FrameParams fp{};
@@ -1251,7 +1197,6 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
             fp.gembed = dg;
         }
     }
-    token_map(r, fp, tm);
     *out = fp;
     if (r.Da) {
         FrameParams va = fp;
@@ -1275,7 +1220,6 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
                 va.tokens = da;
             }
         }
-        token_map(r, va, tma);
         *outa = va;
     }
     return DISC_OK;
@@ -1421,8 +1365,6 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         int* hslot = (int*)(blk.data() + r.off_slot);
         int* hprev = (int*)(blk.data() + r.off_prev);
         FrameParams* hfpa = r.Da ? (FrameParams*)(blk.data() + r.off_fpa) : nullptr;
-        CUtensorMap* htm = (CUtensorMap*)(blk.data() + r.off_tmap);
-        CUtensorMap* htma = r.Da ? (CUtensorMap*)(blk.data() + r.off_tmapa) : nullptr;
         int slot = 0;
         CopyList cl[2];  // host inputs of the batch's first and second half
         // a batch that fails before its counters reach the call's history
@@ -1444,7 +1386,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && s == DISC_OK; j++) {
                 s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, hfpa ? hfpa + slot : nullptr,
-                                 &cl[2 * slot >= S ? 1 : 0], htm + slot, htma ? htma + slot : nullptr);
+                                 &cl[2 * slot >= S ? 1 : 0]);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
@@ -1926,10 +1868,8 @@ namespace {
 
 disc_status set_schedule(Runner& r, const disc_schedule* sch)
 {
-    if (!sch || sch->geometry_chunk < 1 || sch->geometry_chunk > 32 || sch->serial_ctas < 1 || sch->serial_ctas > 32 ||
-        (sch->token_tma != 0 && sch->token_tma != 1))
+    if (!sch || sch->geometry_chunk < 1 || sch->geometry_chunk > 32 || sch->serial_ctas < 1 || sch->serial_ctas > 32)
         return DISC_ERR_INVALID_ARG;
-    r.token_tma = sch->token_tma != 0;  // read per call: the captured graphs stay valid
     if (r.geo_chunk == sch->geometry_chunk && r.cta_scale == sch->serial_ctas) return DISC_OK;
     CK(cudaStreamSynchronize(r.stream));
     r.geo_chunk = sch->geometry_chunk;
@@ -1947,8 +1887,7 @@ disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
                      const std::vector<std::pair<const disc_frame*, int>>& frames, int reps, disc_tune_report* out)
 {
     if (reps < 1 || reps > 100) return DISC_ERR_INVALID_ARG;
-    const int tma = r.token_tma ? 1 : 0;
-    const disc_schedule keep{r.geo_chunk, r.cta_scale, tma};
+    const disc_schedule keep{r.geo_chunk, r.cta_scale};
     disc_tune_report rep{};
     rep.best_ms = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1957,7 +1896,7 @@ disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
     disc_status s = DISC_OK;
     for (int geo : {4, 2, 8}) {  // the default first
         for (int q : {4, 2, 8}) {
-            const disc_schedule cand{geo, q, tma};
+            const disc_schedule cand{geo, q};
             s = set_schedule(r, &cand);
             double best = 1e300;
             for (int pass = 0; pass < reps + 2 && s == DISC_OK; pass++) {

@@ -336,7 +336,6 @@ struct FrameParams {
     int32_t dilate;        // overlap_dilation: 26-neighbour overlap
     int32_t assoc;         // the map has a second grid: association on its features
     int32_t uniform_w;     // this is the second grid's view: pixel-mean weights c_p / |M|
-    int32_t tma;           // the slot's tensor map over its token grid is valid (pooling GEMM)
     int32_t db_min_pts;    // DBSCAN core threshold; 0: no DBSCAN for this frame
     float db_eps2;         // eps * eps
     float db_inv_cell;     // 1 / (1.001 eps): grid cells a little wider than eps

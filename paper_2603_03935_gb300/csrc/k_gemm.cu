@@ -1,5 +1,6 @@
-// D-weighted mask pooling as a tensor-core GEMM (Sec. III-C: "aggregating the
-// patch features within the segmentation mask, weighted by D").
+// D-weighted mask pooling as a tensor-core GEMM (Sec. III-C: each mask's
+// embedding is the sum of its patches' features, each weighted by its
+// distinctiveness D and its share of the mask).
 //
 //   E[m][d] = sum_p W[m][p] * F[p][d]      (W: pooling weights, F: tokens)
 //
@@ -21,7 +22,6 @@
 // two-stage shared-memory ring is recycled through mbarriers that
 // tcgen05.commit arrives on.  Every wait is bounded by a global-timer limit
 // after which the kernel records DISC_ERR_TIMEOUT and returns.
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -141,28 +141,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// TMA: a 2D box of the token grid into shared memory, completing on an
-// mbarrier that expects its bytes (the box's full size, padding included)
-__device__ __forceinline__ void tma_tile(uint32_t dst, const void* tmap, int x, int y, uint32_t mbar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(dst),
-        "l"(tmap), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ float tile_at(const uint8_t* raw, int i);
-template <>
-__device__ __forceinline__ float tile_at<float>(const uint8_t* raw, int i) { return ((const float*)raw)[i]; }
-template <>
-__device__ __forceinline__ float tile_at<__nv_bfloat16>(const uint8_t* raw, int i)
-{
-    return __bfloat162float(((const __nv_bfloat16*)raw)[i]);
-}
-
 template <typename T>
 __device__ __forceinline__ float ldtok(const T* F, size_t i);
 template <>
@@ -179,14 +157,9 @@ constexpr uint32_t A_LBO = (GEMM_MT / 8) * 128;           // 2048: next 16-byte 
 // MMA descriptor of this kernel can form inside the allocation
 constexpr size_t GEMM_SMEM_GUARD = 48 * 1024;
 constexpr size_t SMEM_MAX = 227 * 1024;
-// With TMA staging, two raw token tiles (32 patches x 128 dims, at most 4 B
-// each) follow the stages and barriers, 128-byte aligned.
-constexpr size_t RAW_TILE_MAX = (size_t)GEMM_KC * GEMM_MT * 4;
-__host__ size_t gemm_stage_bytes(int NT) { return 2 * (2 * A_TILE_BYTES + 2 * (size_t)NT * GEMM_KC * 4) + 128; }
-__host__ bool gemm_tma_fits(int NT) { return gemm_stage_bytes(NT) + 2 * RAW_TILE_MAX <= SMEM_MAX; }
-__host__ size_t gemm_smem_bytes(int NT, bool tma)
+__host__ size_t gemm_smem_bytes(int NT)
 {
-    const size_t base = gemm_stage_bytes(NT) + (tma ? 2 * RAW_TILE_MAX : 0);
+    const size_t base = 2 * (2 * A_TILE_BYTES + 2 * (size_t)NT * GEMM_KC * 4) + 64;
     return std::min(base + GEMM_SMEM_GUARD, std::max(base, SMEM_MAX));
 }
 
@@ -202,12 +175,8 @@ cudaError_t set_gemm_stall(bool on)
 }
 
 // PR: the disc_precision of the frames this instance serves
-// tmaps: one tensor map per frame slot over its token grid [P][D]; with
-// use_tma (and the frame's map valid) thread 0 loads each chunk's token tile
-// by TMA one chunk ahead, and the threads read it from shared memory.
 template <typename T, int PR>
-__global__ void __launch_bounds__(128, 1)
-    k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT, const CUtensorMap* tmaps, int use_tma)
+__global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, BatchScratch bs, int NT)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const FrameParams& fp = fps[blockIdx.y];
@@ -229,11 +198,6 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t STAGE = (BF || F8) ? A_BYTES + B_TILE_BYTES : 2 * A_TILE_BYTES + 2 * B_TILE_BYTES;
     uint64_t* mbar = (uint64_t*)(smem + 2 * STAGE);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 2);
-    uint64_t* rawbar = mbar + 3;                       // two TMA barriers (bytes 24..39)
-    const bool tma = use_tma && fp.tma;                // uniform for the block
-    constexpr uint32_t RAW_TILE = GEMM_KC * GEMM_MT * sizeof(T);
-    uint8_t* raw = smem + 2 * STAGE + 128;             // raw[2][RAW_TILE]
-    const void* tmap = tmaps + blockIdx.y;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)NT) ncols <<= 1;
 
@@ -246,11 +210,7 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&rawbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&rawbar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // the tensor map was written to global memory since the last kernel
-        if (tma) asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(tmap) : "memory");
     }
     fence_before();
     __syncthreads();
@@ -261,11 +221,6 @@ __global__ void __launch_bounds__(128, 1)
     bool failed = false;
     int last_commit = -1;  // chunk of the most recent commit (same on all threads)
     const bool stall = g_gemm_stall != 0;  // uniform: read once
-    int tma_issued = -1, tma_done = -1;    // last chunk whose tile was requested / has arrived
-    if (tma && tid == 0 && nchunks > 0) {
-        tma_tile(smem_u32(raw), tmap, d0, 0, smem_u32(&rawbar[0]), RAW_TILE);
-    }
-    if (tma && nchunks > 0) tma_issued = 0;
 
     for (int c = 0; c < nchunks && !failed; c++) {
         const int s = c & 1;
@@ -276,36 +231,16 @@ __global__ void __launch_bounds__(128, 1)
             if (__syncthreads_or(!ok)) { failed = true; break; }
         }
         const int p0 = c * GEMM_KC;
-        const uint8_t* rawc = raw + (size_t)s * RAW_TILE;
-        if (tma) {
-            // the next chunk's tile into the other buffer (read by chunk c - 1,
-            // whose readers all passed that chunk's barrier), then this chunk's
-            if (c + 1 < nchunks) {
-                if (tid == 0)
-                    tma_tile(smem_u32(raw + (size_t)(s ^ 1) * RAW_TILE), tmap, d0, p0 + GEMM_KC,
-                             smem_u32(&rawbar[s ^ 1]), RAW_TILE);
-                tma_issued = c + 1;
-            }
-            bool ok = mbar_wait(smem_u32(&rawbar[s]), (uint32_t)((c >> 1) & 1));
-            if (__syncthreads_or(!ok)) { failed = true; break; }
-            tma_done = c;
-        }
-        // token (p, d0 + tid) of this chunk: from the TMA tile (zero past the
-        // grid's edges) or straight from global memory
-        auto tok_at = [&](int p) -> float {
-            if (tma) return tile_at<T>(rawc, (p - p0) * GEMM_MT + tid);
-            const int d = d0 + tid;
-            return (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
-        };
         if constexpr (F8) {
             // A: F^T tile in e4m3, thread tid owns row d0 + tid, 16 patches per
             // 16 B; all loads first, then one exact multiply by 2^-a_p each
             {
+                const int d = d0 + tid;
                 float x[GEMM_KC];
 #pragma unroll
                 for (int j = 0; j < GEMM_KC; j++) {
                     const int p = p0 + j;
-                    x[j] = tok_at(p);
+                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
                 }
                 const float4* qm = (const float4*)(sc.qmul + p0);  // zero past P
 #pragma unroll
@@ -336,13 +271,14 @@ __global__ void __launch_bounds__(128, 1)
         } else if constexpr (BF) {
             // A: F^T tile in bf16, thread tid owns row d0 + tid, 8 patches per 16 B
             {
+                const int d = d0 + tid;
 #pragma unroll
                 for (int kq = 0; kq < GEMM_KC / 8; kq++) {
                     float x[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
                         const int p = p0 + 8 * kq + j;
-                        x[j] = tok_at(p);
+                        x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
                     }
                     const uint4 v = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]),
                                                pack_bf16(x[6], x[7]));
@@ -364,6 +300,7 @@ __global__ void __launch_bounds__(128, 1)
         } else {
         // A: F^T tile. Thread tid owns row r = tid (token dimension d0 + tid).
         {
+            const int d = d0 + tid;
             float* Ahi = (float*)st;
             float* Alo = (float*)(st + A_TILE_BYTES);
 #pragma unroll
@@ -372,7 +309,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int p = p0 + 4 * kq + j;
-                    x[j] = tok_at(p);
+                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
                 }
                 float4 hi, lo;
                 hi.x = tf32_rna(x[0]); lo.x = tf32_rna(x[0] - hi.x);
@@ -468,12 +405,9 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
     } else if (failed) {
-        // give MMAs and a token tile still in flight one more bounded wait
-        // before TMEM is freed and the block leaves
+        // give MMAs still in flight one more bounded wait before TMEM is freed
         if (last_commit >= 0 && tid == 0)
             mbar_wait(smem_u32(&mbar[last_commit & 1]), (uint32_t)((last_commit >> 1) & 1));
-        if (tid == 0)
-            for (int c = tma_done + 1; c <= tma_issued; c++) mbar_wait(smem_u32(&rawbar[c & 1]), (uint32_t)((c >> 1) & 1));
         if (tid == 0) atomicCAS(&sc.ctr->err, 0, DISC_ERR_TIMEOUT);
     }
     fence_before();
@@ -483,20 +417,19 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][3],
-                     const CUtensorMap* tmaps, cudaStream_t st)
+                     cudaStream_t st)
 {
     if (Mmax <= 0) return 0;
     const int NT = std::max(16, (Mmax + 15) / 16 * 16);
-    const int tma = tmaps && gemm_tma_fits(NT) ? 1 : 0;
-    const size_t smem = gemm_smem_bytes(NT, tma);
+    const size_t smem = gemm_smem_bytes(NT);
     dim3 g((D + GEMM_MT - 1) / GEMM_MT, B);
     int n = 0;
-    if (any[0][0]) { k_pool_gemm<float, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
-    if (any[1][0]) { k_pool_gemm<__nv_bfloat16, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
-    if (any[0][1]) { k_pool_gemm<float, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
-    if (any[1][1]) { k_pool_gemm<__nv_bfloat16, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
-    if (any[0][2]) { k_pool_gemm<float, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
-    if (any[1][2]) { k_pool_gemm<__nv_bfloat16, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT, tmaps, tma); n++; }
+    if (any[0][0]) { k_pool_gemm<float, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][0]) { k_pool_gemm<__nv_bfloat16, DISC_FP32><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][1]) { k_pool_gemm<float, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][1]) { k_pool_gemm<__nv_bfloat16, DISC_BF16><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[0][2]) { k_pool_gemm<float, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
+    if (any[1][2]) { k_pool_gemm<__nv_bfloat16, DISC_FP8_E4M3><<<g, 128, smem, st>>>(fps, bs, NT); n++; }
     return n;
 }
 
@@ -508,7 +441,7 @@ static cudaError_t gemm_attr(int mx)
 
 cudaError_t set_gemm_kernel_attrs()
 {
-    const int mx = (int)gemm_smem_bytes(MAX_MASKS, false);
+    const int mx = (int)gemm_smem_bytes(MAX_MASKS);
     cudaError_t e = gemm_attr<float, DISC_FP32>(mx);
     if (e == cudaSuccess) e = gemm_attr<__nv_bfloat16, DISC_FP32>(mx);
     if (e == cudaSuccess) e = gemm_attr<float, DISC_BF16>(mx);

@@ -12,8 +12,6 @@
 
 #include <cuda_runtime.h>
 
-#include <cuda.h>
-
 #include "disc_common.cuh"
 
 namespace disc {
@@ -45,11 +43,9 @@ int launch_coverage(const FrameParams* fps, const BatchScratch& bs, int B, int P
 int launch_weights(const FrameParams* fps, const BatchScratch& bs, int B, int Mmax, cudaStream_t st);
 int launch_pool_exact(const FrameParams* fps, const BatchScratch& bs, int B, int P, int D, int Mmax, bool any_bf16,
                       bool any_f32, cudaStream_t st);
-// one launch per (token dtype, precision) present: any[tok_bf16][prec_bf16];
-// tmaps (nullable): the slots' tensor maps over their token grids [P][D]
-// (box 128 dims x 32 patches), used where FrameParams.tma is set
+// one launch per (token dtype, precision) present: any[tok_bf16][prec_bf16]
 int launch_pool_gemm(const FrameParams* fps, const BatchScratch& bs, int B, int D, int Mmax, const bool any[2][3],
-                     const CUtensorMap* tmaps, cudaStream_t st);
+                     cudaStream_t st);
 // back-projection and the per-entry pass (S_angle terms, |V_m|, labels at
 // batch start) on frames [f0, f0 + nb); then Q of every segment
 int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);

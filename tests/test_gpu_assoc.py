@@ -137,32 +137,3 @@ def test_query_heatmap_matches_oracle(torch_dev):
             assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), sc.name
             # the object's own patches light up
             assert want.max() > 0.5
-
-
-@pytest.mark.parametrize("precision", [0, 2])
-def test_second_grid_token_tiles_by_tma_equal_plain_loads(torch_dev, precision):
-    # a second grid wide enough for the pooling GEMM's TMA boxes (136 dims,
-    # ragged last tile; 48 patches, ragged last chunk): its fast features by
-    # TMA and by plain loads agree bit for bit, and the TMA map holds parity
-    torch, dev = torch_dev
-    from paper_2603_03935_gb300 import DiscMap
-    sc = synth.tiny_scene()
-    idx = range(0, 20, 2)
-    fr = sc.render(idx)
-    grid = dict(assoc_dim=136, assoc_patch_h=6, assoc_patch_w=8)
-    at = fr.assoc_tokens(6, 8, 136)
-    cfg = common.disc_cfg(sc, precision=precision, **grid)
-    a, b = DiscMap(**cfg), DiscMap(**cfg)
-    b.set_schedule(token_tma=0)
-    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
-    tol = (1e-5, 2e-2, 0.15)[precision]
-    for i in range(len(idx)):
-        st = a.integrate(_aframe(torch, dev, fr, at, i))
-        b.integrate(_aframe(torch, dev, fr, at, i))
-        ra, rb = a.last_frame(), b.last_frame()
-        for k in ("A_fast", "E_fast"):
-            assert np.array_equal(ra[k].view(np.uint32), rb[k].view(np.uint32)), f"frame {idx[i]} {k}"
-        o = omap.integrate(*oracle.frame_args(fr, i), assoc_tokens=at[i])
-        common.compare_frame(st, ra, o, ctx=f"assoc tma frame {idx[i]}", efast_tol=tol)
-        _check_assoc(ra, o, f"assoc tma frame {idx[i]}", tol)
-    common.compare_maps(a, omap, ctx="assoc tma")
