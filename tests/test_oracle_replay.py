@@ -1,0 +1,207 @@
+"""The oracle's stateful steps (a7-a10 of the integration step, Sec. III-B and
+III-C) replayed independently in float64 Python.
+
+Each frame's segment voxel sets, pooled embeddings and quality scores come
+from the oracle's own report (a1-a6, pinned in test_oracle_pins.py); from
+them and the map as the replay holds it, the replay recomputes:
+  - the overlap histogram against the map before the frame (Sec. III-B);
+  - the association edges: the overlap coefficient ov / min(|V_m|, |V_k|)
+    >= num / den as an exact integer test, and the cosine of the pooled
+    embedding with the stored one >= tau, here in float64;
+  - the components of segments and instances (union-find), each keeping its
+    smallest instance id; a segment without an edge opens a new id, in mask
+    order; merged ids point at the representative;
+  - new voxels labelled with the instance of their lowest-index segment, and
+    the voxel counts;
+  - the fusion of Sec. III-C: over the existing members by ascending id,
+    then the segments by ascending mask, the first highest Q wins (strict >);
+  - observations: a component's members' sum plus its segments.
+Every frame's representatives and counters, and the final map (voxels, their
+instances, parents, counts, Q, embeddings, observations), must equal the
+oracle's.  The float64 cosine takes every gate decision the oracle's exact
+fp32-rounded cosine takes on these scenes; a frame where the two disagree
+fails the test.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+class Replay:
+    def __init__(self, cfg):
+        self.num, self.den = int(cfg["ov_num"]), int(cfg["ov_den"])
+        self.tau = float(cfg["tau_cos"])
+        self.vox = {}          # voxel key -> instance id written when it was inserted
+        self.parent, self.count, self.Q, self.E, self.obs = [], [], [], [], []
+
+    def root(self, i):
+        while self.parent[i] != i:
+            i = self.parent[i]
+        return i
+
+    @staticmethod
+    def cos64(a, b):
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        na, nb = np.linalg.norm(a), np.linalg.norm(b)
+        return float(a @ b / (na * nb)) if na > 0 and nb > 0 else 0.0
+
+    def frame(self, r, M):
+        seg = {}
+        for m, k in zip(r["seg_m"].tolist(), r["seg_keys"].tolist()):
+            seg.setdefault(m, []).append(k)
+        live = sorted(m for m in seg if seg[m])
+        nv = {m: len(seg[m]) for m in live}
+        # overlap histogram against the map before the frame
+        ov = {}
+        for m in live:
+            for k in seg[m]:
+                if k in self.vox:
+                    i = self.root(self.vox[k])
+                    ov[(m, i)] = ov.get((m, i), 0) + 1
+        edges = [(m, i) for (m, i), n in sorted(ov.items())
+                 if n * self.den >= self.num * min(nv[m], self.count[i])
+                 and self.cos64(r["E"][m - 1], self.E[i]) >= self.tau]
+        # components over segments ('s', m) and instances ('i', id)
+        uf = {}
+
+        def find(x):
+            while uf.setdefault(x, x) != x:
+                x = uf[x]
+            return x
+
+        for m, i in edges:
+            a, b = find(("s", m)), find(("i", i))
+            if a != b:
+                uf[a] = b
+        comp = {}
+        for m, i in edges:
+            comp.setdefault(find(("i", i)), [set(), set()])
+        for x in list(uf):
+            c = find(x)
+            if c in comp:
+                comp[c][0 if x[0] == "i" else 1].add(x[1])
+        rep = {}
+        merges = 0
+        for insts, segs in comp.values():
+            members = sorted(insts)
+            g = members[0]
+            merges += len(members) - 1
+            for i in members:
+                for x in range(len(self.parent)):
+                    if self.parent[x] == i:
+                        self.parent[x] = g
+            cands = [(self.Q[i], self.E[i]) for i in members]
+            cands += [(float(r["S"][m - 1][4]), r["E"][m - 1].copy()) for m in sorted(segs)]
+            best = 0
+            for j in range(1, len(cands)):
+                if cands[j][0] > cands[best][0]:
+                    best = j
+            total = sum(self.count[i] for i in members)
+            obs = sum(self.obs[i] for i in members) + len(segs)
+            for i in members[1:]:
+                self.count[i] = 0
+            self.count[g] = total
+            self.Q[g], self.E[g] = cands[best]
+            self.obs[g] = obs
+            for m in segs:
+                rep[m] = g
+        new_ids = 0
+        for m in live:
+            if m not in rep:
+                g = len(self.parent)
+                self.parent.append(g)
+                self.count.append(0)
+                self.Q.append(float(r["S"][m - 1][4]))
+                self.E.append(r["E"][m - 1].copy())
+                self.obs.append(1)
+                rep[m] = g
+                new_ids += 1
+        # new voxels: the instance of their lowest-index segment
+        owner = {}
+        for m in live:
+            for k in seg[m]:
+                if k not in self.vox and (k not in owner or m < owner[k]):
+                    owner[k] = m
+        for k, m in owner.items():
+            self.vox[k] = rep[m]
+            self.count[rep[m]] += 1
+        reps = np.array([rep.get(m, -1) for m in range(1, M + 1)], np.int32)
+        return dict(rep=reps, nv=nv, live=len(live), new_instances=new_ids, merges=merges,
+                    overlap_pairs=len(ov), active=len({i for (_, i) in ov}), new_voxels=len(owner))
+
+
+def _split_masks(labels, num_masks, max_masks, frame):
+    """Over-segmentation: on odd frames the two largest masks are cut into a
+    left and a right part (the right part takes a fresh label), so fragments
+    open separate instances and later views merge them."""
+    out = labels.copy()
+    if frame % 2 == 0:
+        return out, num_masks
+    ids, cnt = np.unique(labels[labels > 0], return_counts=True)
+    n = num_masks
+    for m in ids[np.argsort(-cnt)][:2]:
+        if n >= max_masks:
+            break
+        vs, us = np.nonzero(labels == m)
+        cut = int(np.median(us))
+        n += 1
+        out[(labels == m) & (np.arange(labels.shape[1])[None, :] > cut)] = n
+    return out, n
+
+
+def _replay(sc, idx, split=False, **kw):
+    fr = sc.render(idx)
+    cfg = oracle.config_for_scene(sc, **kw)
+    om = oracle.OracleMap(**cfg)
+    rp = Replay(cfg)
+    for i in range(len(fr)):
+        depth, labels, tokens, pose, intr, M = oracle.frame_args(fr, i)
+        if split:
+            labels, M = _split_masks(labels, M, sc.max_masks, i)
+        r = om.integrate(depth, labels, tokens, pose, intr, M)
+        x = rp.frame(r, M)
+        ctx = f"{sc.name} frame {idx[i]}"
+        assert np.array_equal(r["rep"], x["rep"]), (ctx, r["rep"], x["rep"])
+        for m, n in x["nv"].items():
+            assert r["nvox"][m - 1] == n, ctx
+        assert r["live_segments"] == x["live"], ctx
+        assert r["overlap_pairs"] == x["overlap_pairs"], ctx
+        assert r["active_instances"] == x["active"], ctx
+        assert r["new_instances"] == x["new_instances"], ctx
+        assert r["merges"] == x["merges"], ctx
+        assert r["new_voxels"] == x["new_voxels"], ctx
+    keys, ids = om.voxels()
+    assert sorted(rp.vox) == keys.tolist()
+    assert [rp.root(rp.vox[k]) for k in keys.tolist()] == ids.tolist()
+    inst = om.instances()
+    n = len(rp.parent)
+    assert len(inst["parent"]) == n
+    assert [rp.root(i) for i in range(n)] == inst["parent"].tolist()
+    roots = [i for i in range(n) if rp.parent[i] == i]
+    assert [rp.count[i] for i in roots] == inst["count"][roots].tolist()
+    assert [rp.obs[i] for i in roots] == inst["n_obs"][roots].tolist()
+    for i in roots:
+        assert np.float32(rp.Q[i]) == inst["Q"][i]
+        assert np.array_equal(np.asarray(rp.E[i], np.float32).view(np.uint32), inst["E"][i].view(np.uint32))
+    return len(roots), sum(1 for i in range(n) if rp.parent[i] != i)
+
+
+def test_replay_tiny_trajectory():
+    live, merged = _replay(synth.tiny_scene(), list(range(20)))
+    assert live >= 4
+
+
+def test_replay_tiny_trajectory_with_split_masks():
+    # fragments of one object open separate instances and merge later
+    live, merged = _replay(synth.tiny_scene(), list(range(20)), split=True)
+    assert merged > 0
+
+
+@pytest.mark.parametrize("stride", [7])
+def test_replay_room_frames(stride):
+    sc = synth.room_scene()
+    live, merged = _replay(sc, list(range(0, 14 * stride, stride)))
+    assert live >= 10
