@@ -15,6 +15,8 @@ The restatement follows the readings of the paper:
   - voxel normal: the normalised sum of its pixels' normals; view ray: the
     unit vector from the camera centre to the voxel centre;
     S_angle = sum_v max(0, -r_v . n_v) / |V_m| (Eq. 3);
+  - pooled embedding e_m = sum_p w_p f_p with w_p = c_p D_p / sum c D (the
+    coverage mean when every D is zero);
   - S_size = min(lambda |M| / (H W), 1); S_dist = 0.5 + 0.5 * sum_p c_p D_p /
     |M| with D of Eq. 1; S_sem = clamp(sum_p c_p ReLU(cos(f_p, g)) / |M|, 0, 1)
     with g the mean token; Q = S_size S_angle S_sem S_dist (Eq. 2).
@@ -119,11 +121,16 @@ def quality_f64(depth, labels, tokens, pose, intr, M, cfg, Ph, Pw):
         s_angle = acc / len(vox)
         cm = cov[m - 1].astype(np.float64)
         Mm = float(npix[m - 1])
+        # a3: pixel-level D-weighted mean of the tokens (coverage mean when
+        # every D is zero)
+        a = cm * Dp
+        w = a / a.sum() if a.sum() > 0 else cm / cm.sum()
+        E = w @ Fd
         s_size = min(lam * Mm / (H * W), 1.0)
         s_dist = 0.5 + 0.5 * float(cm @ Dp) / Mm
         s_sem = min(max(float(cm @ np.maximum(cosg, 0.0)) / Mm, 0.0), 1.0)
-        out[m] = dict(keys=set(vox), S=np.array([s_size, s_angle, s_sem, s_dist,
-                                                 s_size * s_angle * s_sem * s_dist]))
+        out[m] = dict(keys=set(vox), E=E, S=np.array([s_size, s_angle, s_sem, s_dist,
+                                                      s_size * s_angle * s_sem * s_dist]))
     return out
 
 
@@ -132,6 +139,7 @@ def _compare(sc, idx, tol_angle):
     cfg = oracle.config_for_scene(sc)
     om = oracle.OracleMap(**cfg)
     worst = np.zeros(5)
+    worst_e = 0.0
     masks = 0
     for i in range(len(fr)):
         args = oracle.frame_args(fr, i)
@@ -147,6 +155,9 @@ def _compare(sc, idx, tol_angle):
             assert sym <= max(2, len(q[m]["keys"]) // 500), (idx[i], m, sym)
             e = np.abs(r["S"][m - 1].astype(np.float64) - q[m]["S"])
             worst = np.maximum(worst, e)
+            E64 = q[m]["E"]
+            rel = np.linalg.norm(r["E"][m - 1].astype(np.float64) - E64) / np.linalg.norm(E64)
+            worst_e = max(worst_e, rel)
             masks += 1
     assert masks > 0
     # S_size exact up to fp32 rounding; S_sem and S_dist follow Eq. 1 and the
@@ -154,7 +165,8 @@ def _compare(sc, idx, tol_angle):
     assert worst[0] < 1e-6, worst
     assert worst[2] < 1e-6 and worst[3] < 1e-6, worst
     assert worst[1] < tol_angle and worst[4] < tol_angle, worst
-    return worst, masks
+    assert worst_e < 1e-6, worst_e  # the pooled embedding, per vector
+    return worst, worst_e, masks
 
 
 def test_quality_terms_tiny_trajectory():
