@@ -130,8 +130,11 @@ void worker_loop(disc_server* s)
     cudaSetDevice(s->cfg.group.device);
     while (true) {
         std::vector<int> gl;                       // maps of the batch
+        std::vector<disc_map*> mp;                 // and their handles, read under the lock: the slot
+                                                   // vector may grow (open_map) while the batch runs
         std::vector<std::vector<Request>> frames;  // their frames
         std::vector<std::pair<int, Request>> queries;
+        std::vector<disc_map*> qmaps;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] { return s->stop || s->pending > 0; });
@@ -141,6 +144,7 @@ void worker_loop(disc_server* s)
                 MapSlot& ms = s->maps[i];
                 while (!ms.queue.empty() && ms.queue.front().is_query) {
                     queries.push_back({i, std::move(ms.queue.front())});
+                    qmaps.push_back(ms.m);
                     ms.queue.pop_front();
                     ms.busy++;
                 }
@@ -161,15 +165,17 @@ void worker_loop(disc_server* s)
                 }
                 ms.busy += (int64_t)fr.size();
                 gl.push_back(o.second);
+                mp.push_back(ms.m);
                 frames.push_back(std::move(fr));
             }
         }
         // queries (the maps' earlier frames are complete: batches are synchronous)
-        for (auto& qr : queries) {
+        for (size_t qi = 0; qi < queries.size(); qi++) {
+            auto& qr = queries[qi];
             const Request& r = qr.second;
             std::vector<int32_t> ids((size_t)r.nq * r.k);
             std::vector<float> sc((size_t)r.nq * r.k);
-            const disc_status st = disc_query_topk(s->maps[qr.first].m, r.q.data(), r.nq, r.k, ids.data(), sc.data());
+            const disc_status st = disc_query_topk(qmaps[qi], r.q.data(), r.nq, r.k, ids.data(), sc.data());
             std::lock_guard<std::mutex> lk(s->mu);
             finish(s, r, st, nullptr, &ids, &sc);
             s->maps[qr.first].busy--;
@@ -179,14 +185,12 @@ void worker_loop(disc_server* s)
         if (gl.empty()) continue;
         // the batch: one group call over all its maps
         const int n = (int)gl.size();
-        std::vector<disc_map*> mp(n);
         std::vector<std::vector<disc_frame>> fv(n);
         std::vector<const disc_frame*> fptr(n);
         std::vector<int32_t> cnt(n), done(n);
         std::vector<std::vector<disc_frame_stats>> st(n);
         std::vector<disc_frame_stats*> sptr(n);
         for (int i = 0; i < n; i++) {
-            mp[i] = s->maps[gl[i]].m;
             for (const Request& r : frames[i]) fv[i].push_back(r.frame);
             fptr[i] = fv[i].data();
             cnt[i] = (int32_t)fv[i].size();
