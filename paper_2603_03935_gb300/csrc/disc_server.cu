@@ -389,6 +389,11 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     r.frame.inputs_on_device = 0;
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        // the map may have been closed while the inputs were copied
+        if (!s->maps[map_id].open || s->maps[map_id].closing) {
+            give_block(s, r.host, total);
+            return DISC_ERR_INVALID_ARG;
+        }
         r.ticket = s->next_ticket++;
         *ticket = r.ticket;
         s->results[r.ticket];
