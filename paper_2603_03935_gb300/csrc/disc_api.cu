@@ -2181,17 +2181,31 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     bool ok = std::fread(magic, 1, 8, fp) == 8 &&
               (std::memcmp(magic, kMagic, 8) == 0 || std::memcmp(magic, kMagicFinal, 8) == 0) &&
               std::fread(&c, sizeof(c), 1, fp) == 1 && std::fread(&nv, sizeof(nv), 1, fp) == 1 &&
-              std::fread(&nid, sizeof(nid), 1, fp) == 1 && nv >= 0 && nid >= 0 && c.embed_dim > 0 &&
-              c.embed_dim <= 4096;
-    const int D = ok ? c.embed_dim : 1;
+              std::fread(&nid, sizeof(nid), 1, fp) == 1 && nv >= 0 && nv <= (int64_t(1) << 40) && nid >= 0 &&
+              config_ok(c);
+    // the header's sizes must account for the whole file before anything is
+    // allocated from them
+    if (ok) {
+        const long here = std::ftell(fp);
+        const uint64_t per_id = 4 + 8 + 4 + 4 * (uint64_t)c.embed_dim + 4 + 4 * (uint64_t)c.assoc_dim;
+        const uint64_t want = (uint64_t)here + 12 * (uint64_t)nv + per_id * (uint64_t)nid;
+        ok = here > 0 && std::fseek(fp, 0, SEEK_END) == 0 && (uint64_t)std::ftell(fp) == want &&
+             std::fseek(fp, here, SEEK_SET) == 0;
+    }
+    if (!ok) {
+        std::fclose(fp);
+        return DISC_ERR_INVALID_ARG;
+    }
+    try {
+    const int D = c.embed_dim;
     std::vector<uint64_t> keys(std::max<int64_t>(nv, 1));
     std::vector<int32_t> ids(std::max<int64_t>(nv, 1));
     std::vector<int32_t> parent(std::max(nid, 1)), obs(std::max(nid, 1));
     std::vector<int64_t> count(std::max(nid, 1));
     std::vector<float> Q(std::max(nid, 1)), E((size_t)std::max(nid, 1) * D);
-    const int Da = ok && c.assoc_dim > 0 && c.assoc_dim <= 4096 ? c.assoc_dim : 0;
+    const int Da = c.assoc_dim;
     const int Ds = Da > 0 ? Da : D;  // length of the scoring master's rows
-    std::vector<uint16_t> Eb(ok && c.precision == DISC_BF16 ? (size_t)std::max(nid, 1) * Ds : 0);
+    std::vector<uint16_t> Eb(c.precision == DISC_BF16 ? (size_t)std::max(nid, 1) * Ds : 0);
     std::vector<float> A((size_t)std::max(nid, 1) * std::max(Da, 1));
     if (ok && nv) ok = std::fread(keys.data(), 8, nv, fp) == (size_t)nv && std::fread(ids.data(), 4, nv, fp) == (size_t)nv;
     if (ok && nid)
@@ -2200,6 +2214,7 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
              std::fread(E.data(), 4, (size_t)nid * D, fp) == (size_t)nid * D && std::fread(obs.data(), 4, nid, fp) == (size_t)nid;
     if (ok && nid && Da > 0) ok = std::fread(A.data(), 4, (size_t)nid * Da, fp) == (size_t)nid * Da;
     std::fclose(fp);
+    fp = nullptr;
     if (!ok) return DISC_ERR_INVALID_ARG;
     if (over) {
         c.cuda_stream = over->cuda_stream;
@@ -2264,6 +2279,10 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     m->finalized = std::memcmp(magic, kMagicFinal, 8) == 0;
     *out = m;
     return DISC_OK;
+    } catch (const std::bad_alloc&) {
+        if (fp) std::fclose(fp);
+        return DISC_ERR_OOM;
+    }
 }
 
 disc_status disc_map_finalize(disc_map* m, const disc_finalize_config* cfg, disc_finalize_report* rep)

@@ -67,3 +67,39 @@ def test_create_without_device_fails_cleanly(libdisc):
     import paper_2603_03935_gb300 as pkg
     with pytest.raises(pkg.DiscError):
         pkg.DiscMap()
+
+
+def test_corrupt_checkpoints_are_refused_before_any_allocation(libdisc, tmp_path):
+    # disc_map_load checks the header's config and that its sizes account for
+    # the whole file before it allocates or touches a device
+    import struct
+    import paper_2603_03935_gb300 as pkg
+    from paper_2603_03935_gb300 import binding as b
+    L = b.lib()
+    c = b.Config(**b.config_default(embed_dim=8, patch_h=2, patch_w=2, max_width=8, max_height=8,
+                                    max_masks=4, voxel_capacity=1 << 10, instance_capacity=16))
+    head = b"DISCMAP1" + bytes(c)
+
+    def load(blob):
+        p = tmp_path / "ck.bin"
+        p.write_bytes(blob)
+        h = ctypes.c_void_p()
+        return L.disc_map_load(str(p).encode(), None, ctypes.byref(h)), h.value
+
+    nv, nid = 3, 2
+    body = bytes(12 * nv + nid * (4 + 8 + 4 + 4 * 8 + 4))
+    good = head + struct.pack("<qi", nv, nid) + body
+    assert load(b"NOTAMAP1" + good[8:]) == (-1, None)              # magic
+    assert load(good[:-1]) == (-1, None)                           # one byte short
+    assert load(good + b"\0") == (-1, None)                        # one byte long
+    assert load(head + struct.pack("<qi", 1 << 41, nid) + body) == (-1, None)   # absurd voxel count
+    assert load(head + struct.pack("<qi", nv, -1) + body) == (-1, None)
+    bad = b.Config.from_buffer_copy(bytes(c))
+    bad.max_load = 0.0                                             # would never stop doubling the table
+    assert load(b"DISCMAP1" + bytes(bad) + struct.pack("<qi", nv, nid) + body) == (-1, None)
+    assert load(b"DISCMAP1" + bytes(c)[:10]) == (-1, None)         # truncated header
+    import torch
+    if not torch.cuda.is_available():
+        # the well-formed file passes every check and fails only at the device
+        rc, h = load(good)
+        assert rc != -1 and h is None
