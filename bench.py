@@ -23,6 +23,7 @@ import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -68,6 +69,8 @@ def parse():
                     help="steps of the same workload with the DBSCAN filter on (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--watchdog-s", type=float, default=600.0,
+                    help="a run still going after this long prints the sections it finished and ends")
     return ap.parse_args()
 
 
@@ -454,6 +457,40 @@ def cpu_baseline(scene, fr, budget_s):
             "sample": f"first {n} frames of the Room trajectory, fresh map ({upd / dt:.3g} voxel-updates/s)"}
 
 
+class Watchdog:
+    """Prints the line assembled so far and ends the process when the run
+    outlives its budget, so that a later section that stalls (the many-map
+    batched or served forms, say) cannot take the finished measurements with
+    it.  Unfinished sections carry an "error" entry; without the main
+    measurement nothing is printed and the exit status is 1."""
+
+    def __init__(self, budget_s, assemble):
+        self.assemble = assemble
+        self.lock = threading.Lock()
+        self.printed = False
+        self.done = threading.Event()
+        threading.Thread(target=self._run, args=(budget_s,), daemon=True).start()
+
+    def _run(self, budget_s):
+        if self.done.wait(budget_s):
+            return
+        with self.lock:
+            if self.printed:
+                return
+            line = self.assemble(unfinished="did not finish within the run's %.0f s budget" % budget_s)
+            if line is not None:
+                print(json.dumps(line), flush=True)
+                self.printed = True
+        os._exit(0 if self.printed else 1)
+
+    def emit(self, line):
+        with self.lock:
+            if not self.printed:
+                print(json.dumps(line), flush=True)
+                self.printed = True
+        self.done.set()
+
+
 def main():
     args = parse()
     rank, world, local = rank_env()
@@ -479,6 +516,36 @@ def main():
             dist.barrier()
 
     B, K, Wm = args.frames_per_step, args.steps, args.warmup
+    # the line's sections as they finish (the watchdog prints what is here)
+    state = {}
+    SECTIONS = ("dbscan", "assoc_grid", "dilation", "latency_ms", "phases_ms_per_frame", "roofline",
+                "cpu_baseline", "e2e", "batched", "served")
+
+    def assemble(unfinished=None):
+        core = state.get("core")
+        if core is None:
+            return None
+        total_ms = core["total_ms"]
+        out = {"metric": METRIC, "value": whole_job_rate(K * B, world, total_ms), "unit": "frames/s",
+               "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": total_ms / K,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded room trajectory; stands in for the paper's HM3D/Replica trajectories)",
+               "config": {"workload": WORKLOAD if args.precision == 0 else
+                          WORKLOAD.replace(", FP32", ", %s fast pooling and scoring (fp32 tokens)" %
+                                           ("BF16", "FP8 E4M3")[args.precision - 1]),
+                          "frames_per_step": B, "frames_timed": K * B,
+                          "trajectory_frames": core["n_render"],
+                          "l2": "flushed between timed steps (258 MB write)", "replicas": world},
+               "voxel_updates_per_s": core["updates"] * world / (total_ms / 1e3),
+               "new_voxels_per_s": core["new_vox"] * world / (total_ms / 1e3),
+               "frame_ms_batched": total_ms / (K * B),
+               "gpu_launches": int(core["launches"]),
+               "clocks": core["clk"]}
+        for k in SECTIONS:
+            out[k] = state[k] if k in state else ({"error": unfinished} if unfinished else None)
+        return out
+
+    dog = Watchdog(args.watchdog_s, assemble) if rank == 0 and args.watchdog_s > 0 else None
     # replicas only: every rank integrates its own map of its own scene; the
     # camera path is closed, so frames past its end continue on the next lap
     scene = synth.room_scene(seed=replica_seed(rank))
@@ -563,6 +630,8 @@ def main():
     total_ms = max_over_ranks(float(np.sum(times)), world, dev)
     clk = clocks.stop()
     frames_all = K * B * world
+    state["core"] = {"total_ms": total_ms, "updates": updates, "new_vox": new_vox, "launches": launches,
+                     "clk": clk, "n_render": n_render}
 
     def variant(extra, nsteps, vsteps=None):
         """The same steps (or vsteps) on a fresh map with config changes;
@@ -596,6 +665,7 @@ def main():
         fps_, nf, per = variant(dict(dbscan_eps=0.05, dbscan_min_pts=10), args.dbscan_steps)
         dbscan = {"frames_per_s": fps_, "eps_m": 0.05, "min_pts": 10, "frames": nf,
                   "denoised_pixels_per_frame": per["denoised_pixels"]}
+    state["dbscan"] = dbscan
     # and with a second token grid driving association (1024-dim ViT-L
     # features on a 24 x 32 patch grid, fp32), generated for the frames used
     assoc = None
@@ -616,6 +686,7 @@ def main():
         assoc = {"frames_per_s": fps_, "frames": nf, "grid": f"{A_H}x{A_W}x{A_D} fp32",
                  "merges_per_frame": per["merges"], "new_instances_per_frame": per["new_instances"]}
         del atok
+    state["assoc_grid"] = assoc
 
     # and with the neighbourhood overlap (26-neighbour dilation, Sec. III-B)
     dilation = None
@@ -623,6 +694,7 @@ def main():
         fps_, nf, per = variant(dict(overlap_dilation=1), args.dilation_steps)
         dilation = {"frames_per_s": fps_, "frames": nf, "overlap_pairs_per_frame": per["overlap_pairs"],
                     "merges_per_frame": per["merges"], "new_instances_per_frame": per["new_instances"]}
+    state["dilation"] = dilation
 
     # per-phase device time on the following batches (event-record nodes
     # around each phase, inside the batch's graph)
@@ -650,6 +722,8 @@ def main():
         assert rc == 0, rc
         lat.append(e0.elapsed_time(e1))
     gmap.close()
+    state["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"}
 
     # dominant single-kernel phase with a byte model, and its roofline (the
     # one-CTA union moves a few KB per frame and has none)
@@ -667,6 +741,11 @@ def main():
                 "frac": achieved / peak, "traffic": measured_traffic(dom), "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
                 "launches_per_frame": calls / (TB * B)}
+    state["phases_ms_per_frame"] = {k: round(v, 5) for k, v in per_frame.items()}
+    state["roofline"] = roofline
+    # the oracle on the host cores (GPU idle meanwhile), before the sections
+    # that follow
+    state["cpu_baseline"] = cpu_baseline(scene, fr, args.cpu_seconds) if rank == 0 and world == 1 else None
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
     e2e = None
@@ -715,41 +794,19 @@ def main():
                "calls": "one disc_integrate_frames call per step (32 frames), host buffers, synchronous",
                "one_call_trajectory": {"value": whole_job_rate(K * B, world, traj_ms), "unit": "frames/s",
                                        "frames": K * B}}
+    state["e2e"] = e2e
 
     # the batched and served forms last: their many maps and threads come
     # after every single-map measurement
-    batched = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
-    served = run_served(args, torch, dev, rank) if args.served_maps > 0 else None
+    state["batched"] = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
+    state["served"] = run_served(args, torch, dev, rank) if args.served_maps > 0 else None
 
     if rank == 0:
-        cpu = cpu_baseline(scene, fr, args.cpu_seconds) if world == 1 else None
-        out = {"metric": METRIC, "value": whole_job_rate(K * B, world, total_ms), "unit": "frames/s",
-               "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": total_ms / K,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic (seeded room trajectory; stands in for the paper's HM3D/Replica trajectories)",
-               "config": {"workload": WORKLOAD if args.precision == 0 else
-                          WORKLOAD.replace(", FP32", ", %s fast pooling and scoring (fp32 tokens)" %
-                                           ("BF16", "FP8 E4M3")[args.precision - 1]),
-                          "frames_per_step": B, "frames_timed": K * B,
-                          "trajectory_frames": n_render,
-                          "l2": "flushed between timed steps (258 MB write)", "replicas": world},
-               "voxel_updates_per_s": updates * world / (total_ms / 1e3),
-               "new_voxels_per_s": new_vox * world / (total_ms / 1e3),
-               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                              "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"},
-               "frame_ms_batched": total_ms / (K * B),
-               "batched": batched,
-               "dbscan": dbscan,
-               "dilation": dilation,
-               "assoc_grid": assoc,
-               "served": served,
-               "phases_ms_per_frame": {k: round(v, 5) for k, v in per_frame.items()},
-               "gpu_launches": int(launches),
-               "roofline": roofline,
-               "cpu_baseline": cpu,
-               "e2e": e2e,
-               "clocks": clk}
-        print(json.dumps(out))
+        line = assemble()
+        if dog is not None:
+            dog.emit(line)
+        else:
+            print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
