@@ -420,10 +420,7 @@ __device__ __forceinline__ void e4m3_copy_row(const float* x, int D, uint8_t* q8
 
 // The embedding the association gate scores against: the association
 // feature with a second grid, else the stored embedding; its length.
-__host__ __device__ __forceinline__ const float* scoring_master(const Instances& in, int D)
-{
-    return in.A ? in.A : in.E;
-}
+__host__ __device__ __forceinline__ const float* scoring_master(const Instances& in) { return in.A ? in.A : in.E; }
 __host__ __device__ __forceinline__ int scoring_dim(const Instances& in, int D) { return in.A ? in.Da : D; }
 
 }  // namespace disc

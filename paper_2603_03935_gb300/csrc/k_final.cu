@@ -117,7 +117,7 @@ __global__ void k_fin_gates(Instances inst, int D, FinalizeScratch fs, int num, 
         const long long mn = min(inst.count[a], inst.count[b]);
         if ((long long)fs.pcnt[h] * den < (long long)num * mn) continue;
         // the association features with a second grid, else the embeddings
-        const float* Sm = scoring_master(inst, D);
+        const float* Sm = scoring_master(inst);
         const int Ds = scoring_dim(inst, D);
         const float* ea = Sm + (size_t)a * Ds;
         const float* eb = Sm + (size_t)b * Ds;

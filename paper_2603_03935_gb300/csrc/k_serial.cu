@@ -234,7 +234,7 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scra
     const int lane = threadIdx.x & 31;
     const int npairs = sc.ctr->n_pairs;
     const int D = scoring_dim(inst, fp.D);
-    const float* Sm = scoring_master(inst, fp.D);
+    const float* Sm = scoring_master(inst);
     const float* fast = inst.A ? va.Efast : sc.Efast;
     const float* exact = inst.A ? va.Ecan : sc.Ecan;
     const float* bm = inst.A ? va.Bm : sc.Bm;
@@ -904,7 +904,7 @@ __global__ void k_serial_begin(const MapRefs* refs, int G)
 // warp per instance), as the apply phase writes them
 __global__ void k_e4m3_copies(Instances inst, int n, int D)
 {
-    const float* Sm = scoring_master(inst, D);
+    const float* Sm = scoring_master(inst);
     const int Ds = scoring_dim(inst, D);
     for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += (gridDim.x * blockDim.x) >> 5)
         e4m3_copy_row(Sm + (size_t)k * Ds, Ds, inst.E8 + (size_t)k * Ds, inst.Er + k);
