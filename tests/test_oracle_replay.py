@@ -15,7 +15,11 @@ them and the map as the replay holds it, the replay recomputes:
     the voxel counts;
   - the fusion of Sec. III-C: over the existing members by ascending id,
     then the segments by ascending mask, the first highest Q wins (strict >);
-  - observations: a component's members' sum plus its segments.
+  - observations: a component's members' sum plus its segments;
+  - optionally the 26-neighbour overlap (an instance counts once per segment
+    voxel that it or one of the voxel's 26 neighbours carries) and a second
+    token grid (the gate compares association features, which travel with
+    the embedding through fusion).
 Every frame's representatives and counters, and the final map (voxels, their
 instances, parents, counts, Q, embeddings, observations), must equal the
 oracle's.  The float64 cosine takes every gate decision the oracle's exact
@@ -33,8 +37,14 @@ class Replay:
     def __init__(self, cfg):
         self.num, self.den = int(cfg["ov_num"]), int(cfg["ov_den"])
         self.tau = float(cfg["tau_cos"])
+        # options: the 26-neighbour overlap (reading N1) and a second token
+        # grid whose features drive the gate and travel with the embedding
+        # through fusion (reading T1)
+        self.dilate = bool(cfg.get("overlap_dilation", 0))
+        self.assoc = int(cfg.get("assoc_dim", 0)) > 0
         self.vox = {}          # voxel key -> instance id written when it was inserted
-        self.parent, self.count, self.Q, self.E, self.obs = [], [], [], [], []
+        self.at = {}           # voxel coordinates -> voxel key (dilation)
+        self.parent, self.count, self.Q, self.E, self.obs, self.A = [], [], [], [], [], []
 
     def root(self, i):
         while self.parent[i] != i:
@@ -58,12 +68,24 @@ class Replay:
         ov = {}
         for m in live:
             for k in seg[m]:
-                if k in self.vox:
-                    i = self.root(self.vox[k])
+                if self.dilate:
+                    c = oracle.unpack_key(k)
+                    near = set()
+                    for dx in (-1, 0, 1):
+                        for dy in (-1, 0, 1):
+                            for dz in (-1, 0, 1):
+                                kk = self.at.get((c[0] + dx, c[1] + dy, c[2] + dz))
+                                if kk is not None:
+                                    near.add(self.root(self.vox[kk]))
+                else:
+                    near = {self.root(self.vox[k])} if k in self.vox else set()
+                for i in near:
                     ov[(m, i)] = ov.get((m, i), 0) + 1
+        feat = "A" if self.assoc else "E"
+        mine = self.A if self.assoc else self.E
         edges = [(m, i) for (m, i), n in sorted(ov.items())
                  if n * self.den >= self.num * min(nv[m], self.count[i])
-                 and self.cos64(r["E"][m - 1], self.E[i]) >= self.tau]
+                 and self.cos64(r[feat][m - 1], mine[i]) >= self.tau]
         # components over segments ('s', m) and instances ('i', id)
         uf = {}
 
@@ -93,8 +115,9 @@ class Replay:
                 for x in range(len(self.parent)):
                     if self.parent[x] == i:
                         self.parent[x] = g
-            cands = [(self.Q[i], self.E[i]) for i in members]
-            cands += [(float(r["S"][m - 1][4]), r["E"][m - 1].copy()) for m in sorted(segs)]
+            cands = [(self.Q[i], self.E[i], self.A[i]) for i in members]
+            cands += [(float(r["S"][m - 1][4]), r["E"][m - 1].copy(), r["A"][m - 1].copy() if self.assoc else None)
+                      for m in sorted(segs)]
             best = 0
             for j in range(1, len(cands)):
                 if cands[j][0] > cands[best][0]:
@@ -104,7 +127,7 @@ class Replay:
             for i in members[1:]:
                 self.count[i] = 0
             self.count[g] = total
-            self.Q[g], self.E[g] = cands[best]
+            self.Q[g], self.E[g], self.A[g] = cands[best]
             self.obs[g] = obs
             for m in segs:
                 rep[m] = g
@@ -116,6 +139,7 @@ class Replay:
                 self.count.append(0)
                 self.Q.append(float(r["S"][m - 1][4]))
                 self.E.append(r["E"][m - 1].copy())
+                self.A.append(r["A"][m - 1].copy() if self.assoc else None)
                 self.obs.append(1)
                 rep[m] = g
                 new_ids += 1
@@ -128,6 +152,8 @@ class Replay:
         for k, m in owner.items():
             self.vox[k] = rep[m]
             self.count[rep[m]] += 1
+            if self.dilate:
+                self.at[oracle.unpack_key(k)] = k
         reps = np.array([rep.get(m, -1) for m in range(1, M + 1)], np.int32)
         return dict(rep=reps, nv=nv, live=len(live), new_instances=new_ids, merges=merges,
                     overlap_pairs=len(ov), active=len({i for (_, i) in ov}), new_voxels=len(owner))
@@ -157,11 +183,12 @@ def _replay(sc, idx, split=False, **kw):
     cfg = oracle.config_for_scene(sc, **kw)
     om = oracle.OracleMap(**cfg)
     rp = Replay(cfg)
+    at = fr.assoc_tokens(cfg["assoc_patch_h"], cfg["assoc_patch_w"], cfg["assoc_dim"]) if rp.assoc else None
     for i in range(len(fr)):
         depth, labels, tokens, pose, intr, M = oracle.frame_args(fr, i)
         if split:
             labels, M = _split_masks(labels, M, sc.max_masks, i)
-        r = om.integrate(depth, labels, tokens, pose, intr, M)
+        r = om.integrate(depth, labels, tokens, pose, intr, M, assoc_tokens=at[i] if rp.assoc else None)
         x = rp.frame(r, M)
         ctx = f"{sc.name} frame {idx[i]}"
         assert np.array_equal(r["rep"], x["rep"]), (ctx, r["rep"], x["rep"])
@@ -186,6 +213,8 @@ def _replay(sc, idx, split=False, **kw):
     for i in roots:
         assert np.float32(rp.Q[i]) == inst["Q"][i]
         assert np.array_equal(np.asarray(rp.E[i], np.float32).view(np.uint32), inst["E"][i].view(np.uint32))
+        if rp.assoc:
+            assert np.array_equal(np.asarray(rp.A[i], np.float32).view(np.uint32), inst["A"][i].view(np.uint32))
     return len(roots), sum(1 for i in range(n) if rp.parent[i] != i)
 
 
@@ -205,3 +234,17 @@ def test_replay_room_frames(stride):
     sc = synth.room_scene()
     live, merged = _replay(sc, list(range(0, 14 * stride, stride)))
     assert live >= 10
+
+
+def test_replay_with_neighbourhood_overlap():
+    # reading N1: an instance counts once per segment voxel when it labels
+    # the voxel or one of its 26 neighbours
+    live, merged = _replay(synth.tiny_scene(), list(range(20)), split=True, overlap_dilation=1)
+    assert merged > 0
+    _replay(synth.room_scene(), list(range(0, 70, 7)), overlap_dilation=1)
+
+
+def test_replay_with_a_second_token_grid():
+    # reading T1: the gate compares the association features, and fusion
+    # carries them with the embedding
+    _replay(synth.tiny_scene(), list(range(20)), split=True, assoc_dim=48, assoc_patch_h=4, assoc_patch_w=6)
