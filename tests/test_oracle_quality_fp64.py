@@ -176,3 +176,25 @@ def test_quality_terms_tiny_trajectory():
 def test_quality_terms_room_frames():
     sc = synth.room_scene()
     _compare(sc, list(range(0, 60, 12)), 1e-3)
+
+
+def test_oracle_fp64_pooling_twin_matches_numpy():
+    # the oracle's float64 pooling (the reference of every error statement
+    # about the fast pooled embedding) against numpy float64, on Room frames
+    sc = synth.room_scene()
+    fr = sc.render([0, 300])
+    for i in range(len(fr)):
+        F = fr.tokens[i]
+        M = int(fr.num_masks[i])
+        cov, npix = oracle.mask_coverage(fr.labels[i], sc.patch_h, sc.patch_w, M)
+        Dp, E = oracle.pool_f64(F, cov, npix, 1e-6)
+        D64, _ = _eq1_f64(F, 1e-6)
+        assert np.max(np.abs(Dp - D64)) < 1e-12
+        for m in range(M):
+            c = cov[m].astype(np.float64)
+            if c.sum() == 0:
+                continue
+            a = c * D64
+            w = a / a.sum()
+            e = w @ F.astype(np.float64)
+            assert np.linalg.norm(E[m] - e) <= 1e-12 * np.linalg.norm(e)
