@@ -233,8 +233,12 @@ disc_status disc_group_integrate(disc_group* group, disc_map* const* maps, int32
 disc_status disc_group_set_phase_timing(disc_group* group, int32_t enable);
 disc_status disc_group_phase_times(disc_group* group, double* ms, int64_t* launches, int64_t* calls,
                                    int32_t n);
+/* Kernels the group has launched since creation (graph nodes counted per
+ * replay), and the device bytes its scratch holds; 0 for a NULL group. */
 int64_t disc_group_kernel_launches(disc_group* group);
 int64_t disc_group_device_bytes(disc_group* group);
+/* Frees the group's streams, graphs and scratch; the maps it integrated stay
+ * valid.  Must not overlap a disc_group_integrate on the same group. */
 void disc_group_destroy(disc_group* group); /* NULL-safe */
 
 /* ---- Serving: a request loop over many resident maps ----------------------
@@ -297,6 +301,10 @@ disc_status disc_server_submit_query(disc_server* server, int32_t map_id, const 
 disc_status disc_server_wait(disc_server* server, int64_t ticket, disc_frame_stats* stats, int32_t* ids,
                              float* scores, double* latency_ms);
 
+/* The counters and latency percentiles of disc_server_report (out: caller
+ * memory); callable from any thread.  reset_stats zeroes the completed
+ * counts, busy and wall time and the latency samples (pending and resident
+ * bytes are states, not counts, and stay).  DISC_ERR_INVALID_ARG for NULL. */
 disc_status disc_server_stats(disc_server* server, disc_server_report* out);
 disc_status disc_server_reset_stats(disc_server* server);
 
