@@ -45,6 +45,7 @@ class Replay:
         self.vox = {}          # voxel key -> instance id written when it was inserted
         self.at = {}           # voxel coordinates -> voxel key (dilation)
         self.parent, self.count, self.Q, self.E, self.obs, self.A = [], [], [], [], [], []
+        self.cos_rejects = 0   # pairs past the overlap gate that the cosine gate stopped
 
     def root(self, i):
         while self.parent[i] != i:
@@ -83,9 +84,13 @@ class Replay:
                     ov[(m, i)] = ov.get((m, i), 0) + 1
         feat = "A" if self.assoc else "E"
         mine = self.A if self.assoc else self.E
-        edges = [(m, i) for (m, i), n in sorted(ov.items())
-                 if n * self.den >= self.num * min(nv[m], self.count[i])
-                 and self.cos64(r[feat][m - 1], mine[i]) >= self.tau]
+        edges = []
+        for (m, i), n in sorted(ov.items()):
+            if n * self.den >= self.num * min(nv[m], self.count[i]):
+                if self.cos64(r[feat][m - 1], mine[i]) >= self.tau:
+                    edges.append((m, i))
+                else:
+                    self.cos_rejects += 1
         # components over segments ('s', m) and instances ('i', id)
         uf = {}
 
@@ -215,6 +220,7 @@ def _replay(sc, idx, split=False, **kw):
         assert np.array_equal(np.asarray(rp.E[i], np.float32).view(np.uint32), inst["E"][i].view(np.uint32))
         if rp.assoc:
             assert np.array_equal(np.asarray(rp.A[i], np.float32).view(np.uint32), inst["A"][i].view(np.uint32))
+    _replay.last = rp
     return len(roots), sum(1 for i in range(n) if rp.parent[i] != i)
 
 
@@ -248,3 +254,36 @@ def test_replay_with_a_second_token_grid():
     # reading T1: the gate compares the association features, and fusion
     # carries them with the embedding
     _replay(synth.tiny_scene(), list(range(20)), split=True, assoc_dim=48, assoc_patch_h=4, assoc_patch_w=6)
+
+
+def _random_scene(seed):
+    # boxes and ellipsoids in pairs that touch, seen along a noisy orbit with
+    # noisy tokens: the cosine gate both passes and stops pairs the overlap
+    # gate lets through
+    from tests import scenes
+    rng = np.random.default_rng(seed)
+    prims, pid = [], 1
+    for _ in range(3):
+        c = rng.uniform([0.2, 0.2, 0.15], [1.8, 1.8, 0.4])
+        h = rng.uniform(0.1, 0.25, 3)
+        h2 = rng.uniform(0.1, 0.25, 3)
+        c2 = c + np.array([h[0] + h2[0] + 0.013, 0.0, 0.0])
+        prims.append((int(rng.integers(0, 2)), pid, tuple(c + 0.013), tuple(h)))
+        prims.append((0, pid + 1, tuple(c2 + 0.013), tuple(h2)))
+        pid += 2
+    poses = scenes.orbit((1.0, 1.0, 0.3), 2.2, 1.1, 14, start=float(rng.uniform(0, 6.28)))
+    return scenes.custom_scene(prims, poses, width=80, height=60, f=60.0, dim=64, patch=(6, 8), voxel=0.05,
+                               max_masks=8, seed=seed, token_noise=0.45, depth_noise=0.01)
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23, 24])
+def test_replay_random_scenes_with_noisy_tokens(seed):
+    _replay(_random_scene(seed), list(range(14)), split=(seed % 2 == 1))
+
+
+def test_random_scenes_exercise_the_cosine_gate():
+    total = 0
+    for seed in (21, 22, 23, 24):
+        _replay(_random_scene(seed), list(range(14)), split=(seed % 2 == 1))
+        total += _replay.last.cos_rejects
+    assert total > 0
