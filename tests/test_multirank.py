@@ -83,3 +83,22 @@ def test_reference_arm_prints_one_contract_line(monkeypatch):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_byte_model_of_the_dominant_kernel():
+    # the numerator of the benchmark's roofline: per frame, depth (fp32) and
+    # labels (u16) once, plus 44 B per unique (segment, voxel) pair (a 32 B
+    # segment slot, an 8 B entry key and a 4 B entry slot); summed over the
+    # frames of the timed batch.  Phases without a byte model report 0.
+    import bench
+    H, W, P, D, Kpad = 480, 640, 576, 768, 576
+    sts = [{"unique_seg_voxels": 20000, "new_voxels": 7000, "overlap_pairs": 30, "new_instances": 2,
+            "merges": 1}, {"unique_seg_voxels": 18000, "new_voxels": 6000, "overlap_pairs": 25,
+                           "new_instances": 0, "merges": 0}]
+    Ms = [40, 38]
+    assert bench.algorithmic_bytes("backproject", sts, H, W, P, D, Ms, Kpad) == \
+        2 * 6 * H * W + 44 * (20000 + 18000)
+    assert bench.algorithmic_bytes("token_stats", sts, H, W, P, D, Ms, Kpad) == 2 * 4 * P * D
+    assert bench.algorithmic_bytes("pool_gemm", sts, H, W, P, D, Ms, Kpad) == \
+        sum(4 * P * D + 4 * M * Kpad + 4 * M * D for M in Ms)
+    assert bench.algorithmic_bytes("union", sts, H, W, P, D, Ms, Kpad) == 0.0
