@@ -69,6 +69,9 @@ def parse():
                     help="steps of the same workload with the DBSCAN filter on (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--finalize", type=int, default=1,
+                    help="1: time the end-of-trajectory step on the main map once its frames are in")
+    ap.add_argument("--heatmap-calls", type=int, default=100, help="timed query-heatmap calls (0: skip)")
     ap.add_argument("--watchdog-s", type=float, default=600.0,
                     help="a run still going after this long prints the sections it finished and ends")
     return ap.parse_args()
@@ -518,8 +521,8 @@ def main():
     B, K, Wm = args.frames_per_step, args.steps, args.warmup
     # the line's sections as they finish (the watchdog prints what is here)
     state = {}
-    SECTIONS = ("dbscan", "assoc_grid", "dilation", "latency_ms", "phases_ms_per_frame", "roofline",
-                "cpu_baseline", "e2e", "batched", "served")
+    SECTIONS = ("dbscan", "assoc_grid", "dilation", "latency_ms", "finalize", "heatmap", "phases_ms_per_frame",
+                "roofline", "cpu_baseline", "e2e", "batched", "served")
 
     def assemble(unfinished=None):
         core = state.get("core")
@@ -721,9 +724,49 @@ def main():
         e1.synchronize()
         assert rc == 0, rc
         lat.append(e0.elapsed_time(e1))
-    gmap.close()
     state["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "frames": len(lat), "mode": "disc_integrate_frame, one frame per call"}
+
+    # the end-of-trajectory step (orphan merge and voxel-count filter) on the
+    # map the measured frames built, one synchronous call
+    fin = None
+    if args.finalize:
+        try:
+            nv_, nid_ = gmap.counts()
+            torch.cuda.synchronize()
+            t0_ = time.perf_counter()
+            rep_ = gmap.finalize(min_voxels=100)
+            fin_ms = (time.perf_counter() - t0_) * 1e3
+            fin = {"ms": fin_ms, "voxels": nv_, "instances": nid_, "voxels_per_s": nv_ / (fin_ms / 1e3),
+                   "min_voxels": 100, "report": rep_, "mode": "disc_map_finalize, one call, host clock"}
+        except Exception as ex:  # recorded, the rest of the line stands
+            fin = {"error": repr(ex)}
+    state["finalize"] = fin
+    gmap.close()
+
+    # the Fig. 2 query heatmap over one Room token grid (576 x 768 fp32)
+    heat = None
+    if args.heatmap_calls > 0:
+        try:
+            from paper_2603_03935_gb300 import query_heatmap
+            q_ = tokens[0][7].contiguous()
+            for _ in range(3):
+                query_heatmap(tokens[0], q_, stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.heatmap_calls):
+                query_heatmap(tokens[0], q_, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / args.heatmap_calls
+            heat = {"us_per_call": us, "calls": args.heatmap_calls, "grid": f"{P}x{D} fp32",
+                    "token_gb_per_s": P * D * 4 / (us * 1e-6) / 1e9,
+                    "mode": "disc_query_heatmap calls back to back on one stream, each synchronising "
+                            "(a call's latency; tokens L2-resident)"}
+        except Exception as ex:
+            heat = {"error": repr(ex)}
+    state["heatmap"] = heat
 
     # dominant single-kernel phase with a byte model, and its roofline (the
     # one-CTA union moves a few KB per frame and has none)
