@@ -107,8 +107,9 @@ typedef struct {
 
 typedef struct {
     int32_t width, height;
-    float fx, fy, cx, cy;
-    double T_world_cam[16];  /* row-major camera -> world */
+    float fx, fy, cx, cy;    /* pinhole intrinsics, pixels; finite, fx and fy non-zero */
+    double T_world_cam[16];  /* row-major camera -> world; its top three rows finite as fp32 (a frame
+                                with a non-finite intrinsic or pose is refused: DISC_ERR_INVALID_ARG) */
     const float* depth;      /* [H][W] metres; invalid = outside [z_min, z_max] or NaN */
     const uint16_t* labels;  /* [H][W] mask label, 0 = none, 1..num_masks */
     const void* tokens;      /* [Ph*Pw][D] row-major patch tokens (token_dtype) */

@@ -257,6 +257,12 @@ int oracle_integrate_frame(oracle_map* map, const oracle_frame* fr, oracle_repor
     if (H <= 0 || Wd <= 0 || (int64_t)H * Wd > (1 << 24) || M < 0 || M > 1023 || P > 16384 ||
         D > 4096 || !fr->depth || !fr->labels || !fr->tokens)
         return ORACLE_ERR_INVALID_ARG;
+    // a camera model and pose of finite numbers (the pose as it is rounded to fp32)
+    if (!std::isfinite(fr->fx) || !std::isfinite(fr->fy) || !std::isfinite(fr->cx) || !std::isfinite(fr->cy) ||
+        fr->fx == 0.0f || fr->fy == 0.0f)
+        return ORACLE_ERR_INVALID_ARG;
+    for (int i = 0; i < 12; i++)
+        if (!std::isfinite((float)fr->T_world_cam[i])) return ORACLE_ERR_INVALID_ARG;
     const float s = cfg.voxel_size;
     const int Da = cfg.assoc_dim, Pa = cfg.assoc_patch_h * cfg.assoc_patch_w;
     if (Da > 0) {

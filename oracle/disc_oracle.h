@@ -46,8 +46,8 @@ typedef struct {
 
 typedef struct {
     int32_t width, height;
-    float fx, fy, cx, cy;
-    double T_world_cam[16];    /* row-major camera->world */
+    float fx, fy, cx, cy;      /* finite, fx and fy non-zero */
+    double T_world_cam[16];    /* row-major camera->world; top three rows finite as fp32 */
     const float* depth;        /* [H][W] */
     const uint16_t* labels;    /* [H][W], 0 = none, 1..num_masks */
     const float* tokens;       /* [Ph*Pw][D] */

@@ -1047,7 +1047,12 @@ disc_status check_frame(const disc_map* m, const Runner& r, const disc_frame* f)
         return DISC_ERR_INVALID_ARG;
     if (f->num_masks < 0 || f->num_masks > m->cfg.max_masks || f->num_masks > r.Mmax) return DISC_ERR_INVALID_ARG;
     if (f->token_dtype != DISC_TOKENS_F32 && f->token_dtype != DISC_TOKENS_BF16) return DISC_ERR_INVALID_ARG;
-    if (!(f->fx != 0.0f) || !(f->fy != 0.0f)) return DISC_ERR_INVALID_ARG;
+    // a camera model and pose of finite numbers (the pose as it is rounded to fp32)
+    if (!std::isfinite(f->fx) || !std::isfinite(f->fy) || !std::isfinite(f->cx) || !std::isfinite(f->cy) ||
+        f->fx == 0.0f || f->fy == 0.0f)
+        return DISC_ERR_INVALID_ARG;
+    for (int i = 0; i < 12; i++)
+        if (!std::isfinite((float)f->T_world_cam[i])) return DISC_ERR_INVALID_ARG;
     if (m->cfg.assoc_dim > 0 && (!f->assoc_tokens || r.Da != m->cfg.assoc_dim || r.Pha != m->cfg.assoc_patch_h ||
                                  r.Pwa != m->cfg.assoc_patch_w))
         return DISC_ERR_INVALID_ARG;

@@ -502,3 +502,24 @@ def test_map_invariants_over_the_tiny_trajectory():
     cnt = np.bincount(ids, minlength=len(parent))
     assert np.array_equal(cnt, np.where(parent == np.arange(len(parent)), inst["count"], 0))
     assert len(np.unique(keys)) == len(keys)
+
+
+@pytest.mark.parametrize("bad", ["fx", "fy", "cx", "pose", "fx0"])
+def test_non_finite_camera_or_pose_is_refused(bad):
+    # a frame whose intrinsics or pose are not finite numbers (or whose focal
+    # length is zero) is refused before the map changes
+    H, W, D = 8, 8, 4
+    m = oracle.OracleMap(**oracle.default_config(D, 2, 2, 0.05, min_mask_pixels=1))
+    depth = np.full((H, W), 1.0, np.float32)
+    lab = np.ones((H, W), np.uint16)
+    F = np.ones((4, D), np.float32)
+    intr = {"fx": (np.nan, 8.0, 4.0, 4.0), "fy": (8.0, np.inf, 4.0, 4.0), "cx": (8.0, 8.0, np.nan, 4.0),
+            "pose": (8.0, 8.0, 4.0, 4.0), "fx0": (0.0, 8.0, 4.0, 4.0)}[bad]
+    pose = np.eye(4)
+    if bad == "pose":
+        pose[1, 3] = 1e39  # finite in fp64, infinite once rounded to fp32
+    with pytest.raises(RuntimeError):
+        m.integrate(depth, lab, F, pose, intr, 1)
+    assert m.voxels()[0].size == 0
+    m.integrate(depth, lab, F, np.eye(4), (8.0, 8.0, 4.0, 4.0), 1)  # a valid frame still integrates
+    assert m.voxels()[0].size > 0
