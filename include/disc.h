@@ -298,7 +298,9 @@ disc_status disc_server_submit_query(disc_server* server, int32_t map_id, const 
 
 /* Waits for a request and returns its status.  A frame fills stats
  * (nullable); a query fills ids and scores [nq][k] (nullable).  latency_ms
- * (nullable): submission to completion.  A ticket can be waited for once. */
+ * (nullable): submission to completion.  A ticket has one waiter: it can be
+ * waited for once, and a second wait on it, concurrent or later, returns
+ * DISC_ERR_INVALID_ARG. */
 disc_status disc_server_wait(disc_server* server, int64_t ticket, disc_frame_stats* stats, int32_t* ids,
                              float* scores, double* latency_ms);
 

@@ -2133,6 +2133,38 @@ disc_status disc_query_points(disc_map* m, const float* xyz, int64_t n, int32_t*
 }
 
 // checkpoint file: magic, config, counts, voxels (key, label), instance table
+// A checkpoint's arrays as the device code expects them:
+//   voxel keys packed (three 18-bit fields, below 2^54), hence never the
+//     table's empty marker, and pairwise distinct;
+//   voxel labels in [0, nid) (-1 too in a finalised map, whose dropped
+//     instances leave unlabelled voxels);
+//   parents in [0, nid) and flat (the parent of a parent is itself);
+//   voxel counts and observation counts non-negative;
+//   Q and every embedding entry finite, |entry| <= 1024 (a stored embedding
+//     is a weighted mean of tokens, which obey that bound).
+static bool checkpoint_contents_ok(const uint64_t* keys, const int32_t* ids, int64_t nv, const int32_t* parent,
+                                   const int64_t* count, const float* Q, const float* E, const int32_t* obs,
+                                   int32_t nid, int D, const float* A, int Da, bool finalized)
+{
+    for (int64_t i = 0; i < nv; i++) {
+        if (keys[i] >> 54) return false;
+        if (ids[i] >= nid || ids[i] < (finalized ? -1 : 0)) return false;
+    }
+    std::vector<uint64_t> sorted(keys, keys + nv);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return false;
+    auto entry_ok = [](float x) { return std::isfinite(x) && std::fabs(x) <= 1024.0f; };
+    for (int32_t i = 0; i < nid; i++) {
+        if (parent[i] < 0 || parent[i] >= nid || parent[parent[i]] != parent[i]) return false;
+        if (count[i] < 0 || obs[i] < 0 || !std::isfinite(Q[i])) return false;
+    }
+    for (size_t i = 0; i < (size_t)nid * D; i++)
+        if (!entry_ok(E[i])) return false;
+    for (size_t i = 0; A && i < (size_t)nid * Da; i++)
+        if (!entry_ok(A[i])) return false;
+    return true;
+}
+
 static const char kMagic[8] = {'D', 'I', 'S', 'C', 'M', 'A', 'P', '1'};
 static const char kMagicFinal[8] = {'D', 'I', 'S', 'C', 'M', 'A', 'P', 'F'};  // a finalised map
 
@@ -2221,6 +2253,13 @@ disc_status disc_map_load(const char* path, const disc_map_config* over, disc_ma
     std::fclose(fp);
     fp = nullptr;
     if (!ok) return DISC_ERR_INVALID_ARG;
+    // the contents too, before anything reaches a device: the kernels index
+    // the instance arrays with voxel labels and parents, and the voxel table
+    // needs distinct keys that differ from its empty marker
+    if (!checkpoint_contents_ok(keys.data(), ids.data(), nv, parent.data(), count.data(), Q.data(), E.data(),
+                                obs.data(), nid, D, Da > 0 ? A.data() : nullptr, Da,
+                                std::memcmp(magic, kMagicFinal, 8) == 0))
+        return DISC_ERR_INVALID_ARG;
     if (over) {
         c.cuda_stream = over->cuda_stream;
         c.device = over->device;

@@ -43,6 +43,7 @@ struct Request {
 
 struct Result {
     bool done = false;
+    bool claimed = false;  // a waiter holds this ticket (a ticket has one waiter)
     disc_status status = DISC_OK;
     disc_frame_stats stats{};
     std::vector<int32_t> ids;
@@ -435,7 +436,10 @@ disc_status disc_server_wait(disc_server* s, int64_t ticket, disc_frame_stats* s
     if (!s) return DISC_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->results.find(ticket);
-    if (it == s->results.end()) return DISC_ERR_INVALID_ARG;
+    // a ticket has one waiter: a second thread waiting on it (or on one
+    // already returned) is refused instead of sharing the entry
+    if (it == s->results.end() || it->second.claimed) return DISC_ERR_INVALID_ARG;
+    it->second.claimed = true;
     s->cv_done.wait(lk, [&] { return it->second.done; });
     Result& r = it->second;
     const disc_status st = r.status;

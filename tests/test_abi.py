@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -87,7 +88,7 @@ def test_corrupt_checkpoints_are_refused_before_any_allocation(libdisc, tmp_path
         return L.disc_map_load(str(p).encode(), None, ctypes.byref(h)), h.value
 
     nv, nid = 3, 2
-    body = bytes(12 * nv + nid * (4 + 8 + 4 + 4 * 8 + 4))
+    body = _checkpoint_body([5, 9, 2], [0, 1, 1], [0, 1], [1, 2], [0.5, 0.25], np.zeros((2, 8), np.float32), [1, 1])
     good = head + struct.pack("<qi", nv, nid) + body
     assert load(b"NOTAMAP1" + good[8:]) == (-1, None)              # magic
     assert load(good[:-1]) == (-1, None)                           # one byte short
@@ -103,3 +104,57 @@ def test_corrupt_checkpoints_are_refused_before_any_allocation(libdisc, tmp_path
         # the well-formed file passes every check and fails only at the device
         rc, h = load(good)
         assert rc != -1 and h is None
+
+
+def _checkpoint_body(keys, ids, parent, count, Q, E, obs):
+    """The arrays of a checkpoint file after its header, in file order."""
+    return b"".join([np.asarray(keys, np.uint64).tobytes(), np.asarray(ids, np.int32).tobytes(),
+                     np.asarray(parent, np.int32).tobytes(), np.asarray(count, np.int64).tobytes(),
+                     np.asarray(Q, np.float32).tobytes(), np.asarray(E, np.float32).tobytes(),
+                     np.asarray(obs, np.int32).tobytes()])
+
+
+def test_checkpoints_with_bad_contents_are_refused_before_any_allocation(libdisc, tmp_path):
+    # labels and parents index the instance arrays on the device and keys
+    # fill the voxel table: each bad value is refused on the host
+    import struct
+    from paper_2603_03935_gb300 import binding as b
+    L = b.lib()
+    c = b.Config(**b.config_default(embed_dim=8, patch_h=2, patch_w=2, max_width=8, max_height=8,
+                                    max_masks=4, voxel_capacity=1 << 10, instance_capacity=16))
+    E = np.zeros((2, 8), np.float32)
+    good = dict(keys=[5, 9, 2], ids=[0, 1, 1], parent=[0, 1], count=[1, 2], Q=[0.5, 0.25], E=E, obs=[1, 1])
+
+    def load(magic=b"DISCMAP1", **change):
+        a = dict(good, **change)
+        blob = magic + bytes(c) + struct.pack("<qi", len(a["keys"]), len(a["parent"])) + _checkpoint_body(**a)
+        p = tmp_path / "ck.bin"
+        p.write_bytes(blob)
+        h = ctypes.c_void_p()
+        return L.disc_map_load(str(p).encode(), None, ctypes.byref(h)), h.value
+
+    bad = [dict(ids=[0, 2, 1]),                       # label = nid
+           dict(ids=[0, -1, 1]),                      # unlabelled voxel in a map that is not final
+           dict(ids=[0, -2, 1]),
+           dict(parent=[0, 7]),                       # parent out of range
+           dict(parent=[-1, 1]),
+           dict(parent=[1, 0]),                       # not flat: the parent of 0's parent is not 0's parent
+           dict(count=[1, -3]),
+           dict(obs=[-1, 1]),
+           dict(Q=[np.nan, 0.25]),
+           dict(keys=[5, 0xFFFFFFFFFFFFFFFF, 2]),     # the table's empty marker
+           dict(keys=[5, 1 << 54, 2]),                # not a packed key
+           dict(keys=[5, 9, 5]),                      # repeated key
+           dict(E=np.full((2, 8), np.inf, np.float32)),
+           dict(E=np.full((2, 8), 2048.0, np.float32))]
+    for change in bad:
+        assert load(**change) == (-1, None), change
+    bad_final = dict(ids=[0, -2, 1])
+    assert load(b"DISCMAPF", **bad_final) == (-1, None)
+    import torch
+    if not torch.cuda.is_available():
+        # well-formed contents (a finalised map may hold unlabelled voxels)
+        # pass every check and fail only at the device
+        for magic, change in ((b"DISCMAP1", {}), (b"DISCMAPF", dict(ids=[0, -1, 1]))):
+            rc, h = load(magic, **change)
+            assert rc != -1 and h is None, (magic, change)

@@ -126,3 +126,79 @@ def test_same_frames_twice_give_the_same_bits(torch_dev):
     _same(out[0][0], out[1][0])
     for k in ("E", "E_fast", "W", "S", "cov"):
         assert np.array_equal(np.asarray(out[0][1][k]).view(np.uint8), np.asarray(out[1][1][k]).view(np.uint8)), k
+
+
+def _bad_intrinsics(sc, bad):
+    intr = [sc.fx, sc.fy, sc.cx, sc.cy]
+    pose_fix = None
+    if bad == "fx_nan":
+        intr[0] = float("nan")
+    elif bad == "fy_inf":
+        intr[1] = float("inf")
+    elif bad == "fx_zero":
+        intr[0] = 0.0
+    elif bad == "pose_1e39":
+        pose_fix = 1e39  # finite in fp64, infinite once rounded to fp32
+    return tuple(intr), pose_fix
+
+
+@pytest.mark.parametrize("bad", ["fx_nan", "fy_inf", "fx_zero", "pose_1e39"])
+def test_non_finite_camera_or_pose_is_refused_by_the_library(torch_dev, bad):
+    # a frame with a non-finite intrinsic or pose entry, or a zero focal
+    # length, is refused with DISC_ERR_INVALID_ARG before the map changes;
+    # the next valid frame integrates and the map ends equal to the oracle's
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, device_frame
+    sc = synth.tiny_scene()
+    fr = sc.render(range(3))
+    cfg = common.disc_cfg(sc)
+    gmap = DiscMap(**cfg)
+    gmap.integrate(_dframe(torch, dev, fr, 0))
+    before = _state(gmap)
+    intr, pose_fix = _bad_intrinsics(sc, bad)
+    pose = fr.poses[1].copy()
+    if pose_fix is not None:
+        pose[1, 3] = pose_fix
+    d = torch.from_numpy(fr.depth[1]).to(dev)
+    l = torch.from_numpy(fr.labels[1].view(np.int16)).to(dev)
+    t = torch.from_numpy(fr.tokens[1]).to(dev)
+    st = gmap.integrate(device_frame(d, l, t, pose, intr, fr.num_masks[1]), check=False)
+    assert st["rc"] == -1
+    after = _state(gmap)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    for k in before[2]:
+        assert np.array_equal(before[2][k], after[2][k]), k
+    # in a call of several frames, the frames before the bad one integrate
+    frames = [_dframe(torch, dev, fr, 1), device_frame(d, l, t, pose, intr, fr.num_masks[1])]
+    _, done, rc = gmap.integrate_frames(frames, check=False)
+    assert rc == -1 and done == 1
+    gmap.integrate(_dframe(torch, dev, fr, 2))
+    om = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    for i in range(3):
+        om.integrate(*oracle.frame_args(fr, i))
+    common.compare_maps(gmap, om, ctx=f"after a refused frame ({bad})")
+
+
+def test_non_finite_camera_in_a_group_stops_only_its_own_map(torch_dev):
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap, device_frame
+    scs = [synth.tiny_scene(seed=0), synth.tiny_scene(seed=5), synth.tiny_scene(seed=7)]
+    frs = [s.render(range(5)) for s in scs]
+    maps = [DiscMap(**common.disc_cfg(s)) for s in scs]
+    grp = DiscGroup(max_maps=3, frames_per_map=4, embed_dim=scs[0].dim, patch_h=scs[0].patch_h,
+                    patch_w=scs[0].patch_w, max_width=scs[0].width, max_height=scs[0].height,
+                    max_masks=scs[0].max_masks)
+    per = [[_dframe(torch, dev, fr, i) for i in range(5)] for fr in frs]
+    sc, fr = scs[1], frs[1]
+    d = torch.from_numpy(fr.depth[2]).to(dev)
+    l = torch.from_numpy(fr.labels[2].view(np.int16)).to(dev)
+    t = torch.from_numpy(fr.tokens[2]).to(dev)
+    per[1][2] = device_frame(d, l, t, fr.poses[2], (float("nan"), sc.fy, sc.cx, sc.cy), fr.num_masks[2])
+    stats, done, rc = grp.integrate(maps, per, check=False)
+    assert rc == -1
+    assert done == [5, 2, 5]
+    for g, (m, f) in enumerate(zip(maps, frs)):
+        om = oracle.OracleMap(**common.to_oracle_cfg(m.cfg))
+        for i in range(done[g]):
+            om.integrate(*oracle.frame_args(f, i))
+        common.compare_maps(m, om, ctx=f"map {g} after a refused frame in the group")
