@@ -135,6 +135,8 @@ typedef struct {
     int32_t max_probe;          /* longest hash probe of the frame */
     int32_t status;             /* disc_status of the frame */
     int32_t denoised_pixels;    /* pixels the DBSCAN filter removed */
+    int32_t scored_pairs;       /* (segment, instance) pairs past the overlap gate, cosine taken */
+    int32_t embedding_copies;   /* instance embeddings written (new instances, fusion winners) */
 } disc_frame_stats;
 
 /* Intermediates of the most recent frame, copied to caller host buffers (any
@@ -465,10 +467,15 @@ int64_t disc_map_kernel_launches(disc_map* map);
 /* Per-phase timing with CUDA events recorded on the map's stream around each
  * phase of every frame (off by default; enabling resets the totals).  Phases:
  * 0 clear, 1 token_stats (Eq. 1), 2 coverage, 3 weights, 4 pool_exact,
- * 5 pool_gemm -- one interval per batch each --, 6 backproject and 7 entries
- * (S_angle, |V_m|, lookup; then Q) -- one interval per chunk of 4 frames --,
- * and 8 overlap, 9 score, 10 union, 11 apply -- one interval per frame step
- * each.  With timing on, each batch is captured with event-record nodes and
+ * 5 pool_gemm -- one interval per batch each --, 6 dbscan, 7 backproject and
+ * 8 entries (S_angle, |V_m|; then Q) -- one interval per chunk of frames --,
+ * 13 lookup (every entry of the batch in the map as the batch starts),
+ * 14 associate (each map's frames in order: overlap pairs, gates, union,
+ * fusion, voxel counts), 15 commit (the batch's new voxels) -- one interval
+ * per batch each --, and, for maps with the neighbourhood overlap, 9 overlap,
+ * 10 score, 11 union, 12 apply -- one interval per frame step each (the
+ * entries phase then also looks the voxels up).  disc_phase_name(i) names
+ * phase i.  With timing on, each batch is captured with event-record nodes and
  * launched once as a graph.  ms/launches/calls: [n] accumulated device time,
  * kernels launched and timed intervals per phase (any may be NULL).  Kernel
  * launches count only the map's own calls (not group calls). */

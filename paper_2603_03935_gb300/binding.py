@@ -45,7 +45,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, c_i32) for k in ("valid_pixels", "dropped_pixels", "unique_seg_voxels", "new_voxels",
                                      "active_instances", "overlap_pairs", "new_instances", "merges",
                                      "live_segments", "borderline_rescored", "max_probe", "status",
-                                     "denoised_pixels")]
+                                     "denoised_pixels", "scored_pairs", "embedding_copies")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -467,7 +467,7 @@ class DiscMap:
         _check(lib().disc_map_set_phase_timing(self._h, 1 if enable else 0), "disc_map_set_phase_timing")
 
     def phase_times(self) -> dict:
-        n = 13
+        n = 16
         ms = np.zeros(n, np.float64)
         la = np.zeros(n, np.int64)
         ca = np.zeros(n, np.int64)
@@ -580,7 +580,7 @@ class DiscGroup:
         _check(lib().disc_group_set_phase_timing(self._h, 1 if enable else 0), "disc_group_set_phase_timing")
 
     def phase_times(self) -> dict:
-        n = 13
+        n = 16
         ms = np.zeros(n, np.float64)
         la = np.zeros(n, np.int64)
         ca = np.zeros(n, np.int64)

@@ -126,6 +126,9 @@ struct Runner {
     int hist_cap = 0;
     cudaStream_t stream_in = nullptr; // host-to-device copies of host inputs
     unsigned long long* d_room = nullptr;  // [2 Gmax] per map of a batch: voxel count, pairs of its frames
+    AbsentHash ah{};                  // voxels absent at a batch's start (k_lookup .. k_commit), grown on demand
+    uint64_t ah_cap = 0;
+    int* d_merged = nullptr;          // [Gmax] per map of a batch: some frame merged instances
     unsigned long long* h_room = nullptr;  // pinned copy of d_room
     cudaEvent_t ev_room = nullptr;
     cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {};  // staging set k filled / read by its last batch
@@ -409,6 +412,12 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         sc.slist = a.get<int32_t>((size_t)B * scap);
         sc.elab = a.get<int32_t>((size_t)B * scap);
         sc.smask = scap - 1;
+        sc.pkey = a.get<unsigned long long>((size_t)B * scap);
+        sc.pcnt = a.get<int32_t>((size_t)B * scap);
+        sc.plist = a.get<int32_t>((size_t)B * scap);
+        sc.aent = a.get<int32_t>((size_t)B * scap);
+        sc.aslot = a.get<int32_t>((size_t)B * scap);
+        sc.newcnt = a.get<int32_t>((size_t)B * MM);
         sc.ctr = a.get<FrameCounters>(B);
     }
     r.d_depth = a.get<float>((size_t)2 * B * npx);
@@ -416,6 +425,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     r.d_tokens = a.get<unsigned char>((size_t)2 * B * P * D * 4);
     r.d_gembed = a.get<float>((size_t)2 * B * D);
     r.d_room = a.get<unsigned long long>((size_t)2 * Gmax);
+    r.d_merged = a.get<int>((size_t)Gmax);
     if (r.Da) {
         // the second grid's view: the feature kernels' arrays at its sizes;
         // the counters are the primary slots' own
@@ -494,6 +504,9 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         CK(cudaMemsetAsync(sc.qexpm, 0, sizeof(int32_t) * (size_t)B * MM, s));
         CK(cudaMemsetAsync(sc.cov, 0, sizeof(int32_t) * (size_t)B * MM * P, s));
         CK(cudaMemsetAsync(sc.sslot, 0, sizeof(SegSlot) * B * scap, s));
+        CK(cudaMemsetAsync(sc.pkey, 0xff, sizeof(unsigned long long) * B * scap, s));
+        CK(cudaMemsetAsync(sc.pcnt, 0, sizeof(int32_t) * B * scap, s));
+        CK(cudaMemsetAsync(sc.newcnt, 0, sizeof(int32_t) * B * MM, s));
         CK(cudaMemsetAsync(sc.Efast, 0, sizeof(float) * (size_t)B * MM * D, s));
         CK(cudaMemsetAsync(sc.Ecan, 0, sizeof(float) * (size_t)B * MM * D, s));
         if (r.Da) {
@@ -600,6 +613,52 @@ disc_status ensure_dbscan(Runner& r)
     r.graphs.clear();
     r.shapes_seen.clear();
     return cuda_status(cudaStreamSynchronize(r.stream));
+}
+
+// The batch-wide hash of voxels absent at a batch's start, sized for `keys`
+// of them at load <= 1/2 (keys bounds the batch's unique (segment, voxel)
+// pairs); it grows when a batch could exceed it.  Captured graphs hold its
+// old pointers, so they are dropped on growth.
+disc_status ensure_absent(Runner& r, uint64_t keys)
+{
+    const uint64_t cap = next_pow2(std::max<uint64_t>(2 * keys, 1 << 16));
+    if (cap <= r.ah_cap) return DISC_OK;
+    CK(cudaStreamSynchronize(r.stream3));  // no batch of the runner is using the old one
+    CK(cudaStreamSynchronize(r.stream));
+    DevAlloc& a = r.mem;
+    if (r.ah.key) {
+        a.release(r.ah.key, sizeof(unsigned long long) * r.ah_cap);
+        a.release(r.ah.val, sizeof(int32_t) * r.ah_cap);
+        a.release(r.ah.list, sizeof(int32_t) * r.ah_cap);
+        a.release(r.ah.n, sizeof(int32_t));
+    }
+    r.ah = AbsentHash{};
+    r.ah_cap = 0;
+    for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
+    r.graphs.clear();
+    r.shapes_seen.clear();
+    AbsentHash h{};
+    h.key = a.get<unsigned long long>(cap);
+    h.val = a.get<int32_t>(cap);
+    h.list = a.get<int32_t>(cap);
+    h.n = a.get<int32_t>(1);
+    h.mask = cap - 1;
+    if (a.failed) {
+        a.failed = false;
+        if (h.key) a.release(h.key, sizeof(unsigned long long) * cap);
+        if (h.val) a.release(h.val, sizeof(int32_t) * cap);
+        if (h.list) a.release(h.list, sizeof(int32_t) * cap);
+        if (h.n) a.release(h.n, sizeof(int32_t));
+        return DISC_ERR_OOM;
+    }
+    CK(cudaMemsetAsync(h.key, 0, sizeof(unsigned long long) * cap, r.stream));
+    CK(cudaMemsetAsync(h.val, 0x7f, sizeof(int32_t) * cap, r.stream));  // 0x7f7f7f7f: above every (j << 9 | m)
+    CK(cudaMemsetAsync(h.n, 0, sizeof(int32_t), r.stream));
+    disc_status st = cuda_status(cudaStreamSynchronize(r.stream));
+    if (st != DISC_OK) return st;
+    r.ah = h;
+    r.ah_cap = cap;
+    return DISC_OK;
 }
 
 // ---- map tables --------------------------------------------------------------------
@@ -859,7 +918,9 @@ void reset_timing(Runner& r, bool enable)
 // the batch; bit COMBO_DBSCAN: some frame runs the DBSCAN filter; bit
 // COMBO_ASSOC: the feature kernels also run on the second grid's view
 constexpr int COMBO_DBSCAN = 1 << 6;
-constexpr int COMBO_ASSOC = 1 << 7;  // some frame's map has a second token grid
+constexpr int COMBO_ASSOC = 1 << 7;   // some frame's map has a second token grid
+constexpr int COMBO_DILATE = 1 << 8;  // some frame's map takes the neighbourhood overlap: the batch's
+                                      // frames run as four kernels each (overlap, score, union, apply)
 
 // slots [base, base + S) of set k (base > 0: the second half of a batch whose
 // halves wait for their own input copies)
@@ -901,14 +962,20 @@ int enqueue_stateless(Runner& r, int k, int S, int combos, cudaStream_t st, int 
             if (combos & COMBO_DBSCAN)
                 run_phase(r, PH_DBSCAN, st, [&] { return launch_dbscan(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
             run_phase(r, PH_BACKPROJECT, st, [&] { return launch_backproject(dfp, bs, f0, nb, r.Hmax, r.Wmax, st); });
-            run_phase(r, PH_ENTRIES, st, [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, st); });
+            run_phase(r, PH_ENTRIES, st,
+                      [&] { return launch_entries(dfp, bs, refs, f0, nb, Mmax, (combos & COMBO_DILATE) != 0, st); });
         }
         run_phase(r, PH_ENTRIES, st, [&] { return launch_quality(dfp, bs, S, st); });
     }
     return (int)(r.launches - before);
 }
 
-int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
+// The serial part of a batch of S slots over G maps (J frames per map).
+// Plain: every entry looked up at once, one CTA per map walks its frames
+// (k_associate), the new voxels committed at the end.  With the
+// neighbourhood overlap (COMBO_DILATE) each frame probes the map as its
+// predecessors left it: four kernels per frame.
+int enqueue_serial(Runner& r, int k, int S, int G, int J, int combos, cudaStream_t st)
 {
     const BatchScratch& bs = r.bs[k];
     const FrameParams* dfp = r.fps(k);
@@ -921,6 +988,18 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
     step.J = J;
     step.view = r.bsa[k];  // zero when the runner has no second grid
     step.cta_scale = r.cta_scale;
+    step.merged = r.d_merged;
+    if (!(combos & COMBO_DILATE)) {
+        step.j = 0;
+        run_phase(r, PH_LOOKUP, st, [&] { return launch_lookup(dfp, bs, step.refs, r.ah, S, st); });
+        run_phase(r, PH_ASSOCIATE, st, [&] { return launch_associate(dfp, bs, step, G, st); });
+        run_phase(r, PH_COMMIT, st, [&] {
+            const int n = launch_commit(bs, step, r.ah, G, st);
+            cudaMemsetAsync(r.ah.n, 0, sizeof(int32_t), st);  // the hash is empty again
+            return n;
+        });
+        return (int)(r.launches - before);
+    }
     run_phase(r, PH_OVERLAP, st, [&] { return launch_serial_begin(step.refs, G, st); });
     for (int j = 0; j < J; j++) {
         step.j = j;
@@ -932,7 +1011,7 @@ int enqueue_serial(Runner& r, int k, int G, int J, cudaStream_t st)
 
 long long graph_key(int part, int k, int S, int G, int J, int combos)
 {
-    return (((((((long long)S << 11) | G) << 9) | J) << 8 | combos) << 3) | (part << 1) | k;
+    return (((((((long long)S << 11) | G) << 9) | J) << 9 | combos) << 3) | (part << 1) | k;
 }
 
 // A part's kernel sequence captured once per shape and replayed.  A shape
@@ -1019,7 +1098,7 @@ bool launch_timed_graph(Runner& r, int k, int S, int G, int J, int combos)
         return false;
     }
     enqueue_stateless(r, k, S, combos, r.stream);
-    enqueue_serial(r, k, G, J, r.stream);
+    enqueue_serial(r, k, S, G, J, combos, r.stream);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if (cudaStreamEndCapture(r.stream, &graph) != cudaSuccess || !graph ||
@@ -1128,7 +1207,7 @@ struct CopyList {
 // Host inputs are staged in staging set `set` (copies collected in cl).
 // With a second grid, *outa receives the view of the frame on that grid (for
 // maps without one, an inert view: no tokens, no masks).
-disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int set, int slot, int g,
+disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int set, int slot, int g, int jpos,
                          FrameParams* out, FrameParams* outa, CopyList* cl)
 {
     const int P = r.P, D = r.D;
@@ -1165,6 +1244,7 @@ disc_status frame_params(Runner& r, const disc_map* m, const disc_frame* f, int 
     fp.min_px = std::max(1, m->cfg.min_mask_pixels);
     fp.token_bf16 = f->token_dtype == DISC_TOKENS_BF16;
     fp.map = g;
+    fp.jpos = jpos;
     fp.precision = m->cfg.precision;
     fp.dilate = m->cfg.overlap_dilation;
     fp.db_min_pts = m->cfg.dbscan_eps > 0.0f ? m->cfg.dbscan_min_pts : 0;
@@ -1245,6 +1325,8 @@ void to_stats(const FrameCounters& c, disc_frame_stats* s)
     s->max_probe = c.max_probe;
     s->status = c.err;
     s->denoised_pixels = c.denoised;
+    s->scored_pairs = c.n_scored;
+    s->embedding_copies = c.n_copies;
 }
 
 // The frames one call integrates into one map.
@@ -1274,6 +1356,10 @@ disc_status room_check(Runner& r, int k, int G, int J, std::vector<Work>& w, con
     CK(cudaMemcpyAsync(r.h_room, r.d_room, sizeof(unsigned long long) * 2 * G, cudaMemcpyDeviceToHost, sr));
     CK(cudaEventRecord(r.ev_room, sr));
     CK(cudaEventSynchronize(r.ev_room));
+    uint64_t pairs = 0;  // bounds the voxels absent at the batch start
+    for (int gi = 0; gi < G; gi++) pairs += r.h_room[2 * gi + 1];
+    disc_status sa = ensure_absent(r, pairs);
+    if (sa != DISC_OK) return sa;
     for (int gi = 0; gi < G; gi++) {
         disc_map* m = w[gl[gi]].m;
         const uint64_t need = r.h_room[2 * gi] + r.h_room[2 * gi + 1];
@@ -1309,7 +1395,13 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     // pipelined (calls of several batches): the runner's two streams start
     // after the caller's earlier work and the caller's stream waits for their
     // end; a single batch runs on the caller's stream
-    const bool pipe = !r.timing && nbatch > 1 && r.serial_sms > 0;
+    bool dilate = false;
+    for (const Work& wk : w) dilate |= wk.valid > 0 && wk.m->cfg.overlap_dilation != 0;
+    // the serial part of a plain batch runs on one SM per map, so the next
+    // batch's stateless part runs beside it on the other SMs (two streams,
+    // the serial one of highest priority); the four-kernels-per-frame form
+    // (neighbourhood overlap) overlaps only on SM partitions (serial_sms)
+    const bool pipe = !r.timing && nbatch > 1 && (r.serial_sms > 0 || !dilate);
     cudaStream_t sr = pipe ? r.stream3 : r.stream;  // serial part
     cudaStream_t ss = pipe ? r.stream2 : r.stream;  // stateless part
     // the input copies (and, pipelined, both parts) start after the caller's
@@ -1321,25 +1413,46 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(r.stream3, r.ev_join, 0));
     }
     if (s != DISC_OK) return s;
-    std::vector<unsigned char> blk(r.param_bytes);
     const bool one_graph = r.timing && !r.graphs_off;
+    // Batch b + 1's stateless part is enqueued after batch b's serial part:
+    // the serial kernel (one cluster of large-shared-memory CTAs per map)
+    // then takes its SMs first and the stateless part fills the rest.
+    // (Enqueued before it, the stateless kernels hold every SM and the
+    // serial kernel waits for them to drain: measured slower.)
     int hoff = 0;
-    for (int b = 0; b < nbatch && s == DISC_OK; b++) {
+    // One batch between its two halves of the loop below.
+    struct Pending {
+        int b = -1, k = 0, G = 0, J = 0, S = 0, combos = 0, hoff = 0;
+        std::vector<int> gl;       // works with frames in this batch
+        std::vector<size_t> mark;  // their history lengths before the batch
+        std::vector<unsigned char> blk;
+        bool copied = false, timed = false;
+    };
+    auto undo = [&](Pending& P) {
+        for (int gi = 0; gi < (int)P.gl.size(); gi++) w[P.gl[gi]].hist_idx.resize(P.mark[gi]);
+        P.b = -1;
+    };
+    // front: compose batch b, fill and upload its parameter block, copy its
+    // host inputs and enqueue its stateless part (or, timed, the whole batch)
+    auto front = [&](int b, Pending& P) -> disc_status {
+        P.b = -1;
         const int lo = b * r.Jmax;
-        std::vector<int> gl;  // works with frames in this batch
+        P.gl.clear();
         int J = 0, S = 0;
         for (int i = 0; i < (int)w.size(); i++) {
             const int cnt = std::min(r.Jmax, w[i].valid - lo);
             if (cnt <= 0) continue;
-            gl.push_back(i);
+            P.gl.push_back(i);
             J = std::max(J, cnt);
             S += cnt;
         }
-        const int G = (int)gl.size();
-        if (G == 0) break;
+        const int G = (int)P.gl.size();
+        if (G == 0) return DISC_OK;
         int combos = 0;
-        for (int gi = 0; gi < G && s == DISC_OK; gi++) {
-            Work& wk = w[gl[gi]];
+        uint64_t batch_px = 0;
+        disc_status st = DISC_OK;
+        for (int gi = 0; gi < G && st == DISC_OK; gi++) {
+            Work& wk = w[P.gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
             uint64_t px = 0;
             int64_t masks = 0;
@@ -1350,128 +1463,177 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 combos |= 1 << (3 * (f.token_dtype == DISC_TOKENS_BF16) + wk.m->cfg.precision);
                 if (wk.m->cfg.dbscan_eps > 0.0f) combos |= COMBO_DBSCAN;
                 if (wk.m->cfg.assoc_dim > 0) combos |= COMBO_ASSOC;
+                if (wk.m->cfg.overlap_dilation) combos |= COMBO_DILATE;
             }
-            // one graph of both parts (phase timing): room from the host bound;
-            // otherwise from the device between the parts (room_check)
-            if (one_graph) s = ensure_voxel_room(wk.m, px, sr);
-            if (s == DISC_OK) s = ensure_instance_room(wk.m, masks, sr);
+            // one graph of both parts (phase timing): room from the host
+            // bounds now; otherwise before the serial part (back)
+            if (one_graph) {
+                st = ensure_voxel_room(wk.m, px, sr);
+                if (st == DISC_OK) st = ensure_instance_room(wk.m, masks, sr);
+            }
+            batch_px += px;
         }
-        if (s != DISC_OK) break;
+        if (st == DISC_OK && one_graph) st = ensure_absent(r, batch_px);
+        if (st != DISC_OK) return st;
         // set k: its previous batch's serial part must be done before the
-        // stateless part of this batch overwrites the set (pipelined batches:
-        // stateless on stream2, serial on the runner's stream)
+        // stateless part of this batch overwrites the set
         const int k = r.cur;
         r.cur ^= 1;
-        if (pipe) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_serial[k], 0));
-        if (s != DISC_OK) break;
-        std::fill(blk.begin(), blk.end(), 0);
-        FrameParams* hfp = (FrameParams*)blk.data();
-        MapRefs* hrefs = (MapRefs*)(blk.data() + r.off_refs);
-        int* hslot = (int*)(blk.data() + r.off_slot);
-        int* hprev = (int*)(blk.data() + r.off_prev);
-        FrameParams* hfpa = r.Da ? (FrameParams*)(blk.data() + r.off_fpa) : nullptr;
+        if (pipe) CK(cudaStreamWaitEvent(ss, r.ev_serial[k], 0));
+        P.blk.assign(r.param_bytes, 0);
+        FrameParams* hfp = (FrameParams*)P.blk.data();
+        MapRefs* hrefs = (MapRefs*)(P.blk.data() + r.off_refs);
+        int* hslot = (int*)(P.blk.data() + r.off_slot);
+        int* hprev = (int*)(P.blk.data() + r.off_prev);
+        FrameParams* hfpa = r.Da ? (FrameParams*)(P.blk.data() + r.off_fpa) : nullptr;
         int slot = 0;
         CopyList cl[2];  // host inputs of the batch's first and second half
         // a batch that fails before its counters reach the call's history
         // leaves no history entries behind: its frames count as not done
-        std::vector<size_t> mark(G);
-        for (int gi = 0; gi < G; gi++) mark[gi] = w[gl[gi]].hist_idx.size();
-        auto undo = [&] {
-            for (int gi = 0; gi < G; gi++) w[gl[gi]].hist_idx.resize(mark[gi]);
-        };
+        P.mark.resize(G);
+        for (int gi = 0; gi < G; gi++) P.mark[gi] = w[P.gl[gi]].hist_idx.size();
+        P.b = b;
+        P.k = k;
+        P.G = G;
+        P.J = J;
+        P.S = S;
+        P.combos = combos;
+        P.hoff = hoff;
         // host inputs of this batch go to staging set k once the set's last
         // batch has read its inputs (its stateless part), on the input
         // stream, so they overlap the previous batch's kernels
-        s = cuda_status(cudaStreamWaitEvent(r.stream_in, r.ev_in_free[k], 0));
-        for (int gi = 0; gi < G && s == DISC_OK; gi++) {
-            Work& wk = w[gl[gi]];
+        st = cuda_status(cudaStreamWaitEvent(r.stream_in, r.ev_in_free[k], 0));
+        for (int gi = 0; gi < G && st == DISC_OK; gi++) {
+            Work& wk = w[P.gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
             hrefs[gi] = map_refs(wk.m);
             hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
-            for (int j = 0; j < cnt && s == DISC_OK; j++) {
-                s = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, hfp + slot, hfpa ? hfpa + slot : nullptr,
-                                 &cl[2 * slot >= S ? 1 : 0]);
+            for (int j = 0; j < cnt && st == DISC_OK; j++) {
+                st = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, j, hfp + slot, hfpa ? hfpa + slot : nullptr,
+                                  &cl[2 * slot >= S ? 1 : 0]);
                 hslot[gi * J + j] = slot;
                 wk.hist_idx.push_back(hoff + slot);
                 slot++;
             }
         }
+        hoff += S;
         // With host inputs (and not one timed graph), the batch's stateless
         // part runs in two halves: the second half's copies run while the
         // first half computes.
         const bool copied = !cl[0].empty() || !cl[1].empty();
-        const bool halves = copied && !(r.timing && !r.graphs_off) && S >= 8;
+        P.copied = copied;
+        const bool halves = copied && !one_graph && S >= 8;
         const int Sh = halves ? S / 2 : S;
         if (!halves) cl[0].append(cl[1]);
-        if (s == DISC_OK && copied) {
-            s = cl[0].issue(r.stream_in);
-            if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_ready[k], r.stream_in));
-            if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_ready[k], 0));
-            if (s == DISC_OK && halves) {
-                s = cl[1].issue(r.stream_in);
-                if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_in_half[k], r.stream_in));
+        if (st == DISC_OK && copied) {
+            st = cl[0].issue(r.stream_in);
+            if (st == DISC_OK) st = cuda_status(cudaEventRecord(r.ev_in_ready[k], r.stream_in));
+            if (st == DISC_OK) st = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_ready[k], 0));
+            if (st == DISC_OK && halves) {
+                st = cl[1].issue(r.stream_in);
+                if (st == DISC_OK) st = cuda_status(cudaEventRecord(r.ev_in_half[k], r.stream_in));
             }
-        }
-        if (s != DISC_OK) {
-            undo();
-            break;
         }
         // pageable source: the call returns once the block is staged
-        s = cuda_status(cudaMemcpyAsync(r.d_param[k], blk.data(), r.param_bytes, cudaMemcpyHostToDevice, ss));
-        if (s != DISC_OK) {
-            undo();
-            break;
-        }
-        if (r.timing && !r.graphs_off && launch_timed_graph(r, k, S, G, J, combos)) {
+        if (st == DISC_OK)
+            st = cuda_status(cudaMemcpyAsync(r.d_param[k], P.blk.data(), r.param_bytes, cudaMemcpyHostToDevice, ss));
+        if (st != DISC_OK) return st;
+        P.timed = one_graph && launch_timed_graph(r, k, S, G, J, combos);
+        if (P.timed) {
             // both parts with their phase events, one graph on the runner's stream
-            if (copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], r.stream));
+            if (copied) st = cuda_status(cudaEventRecord(r.ev_in_free[k], r.stream));
+            return st;
+        }
+        if (halves) {
+            st = run_part(r, graph_key(2, k, Sh, 0, 0, combos), ss,
+                          [&] { return enqueue_stateless(r, k, Sh, combos, ss); });
+            if (st == DISC_OK) st = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_half[k], 0));
+            if (st == DISC_OK)
+                st = run_part(r, graph_key(3, k, S - Sh, Sh, 0, combos), ss,  // keyed by its first slot too
+                              [&] { return enqueue_stateless(r, k, S - Sh, combos, ss, Sh); });
         } else {
-            if (halves) {
-                s = run_part(r, graph_key(2, k, Sh, 0, 0, combos), ss,
-                             [&] { return enqueue_stateless(r, k, Sh, combos, ss); });
-                if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(ss, r.ev_in_half[k], 0));
-                if (s == DISC_OK)
-                    s = run_part(r, graph_key(3, k, S - Sh, 0, 0, combos), ss,
-                                 [&] { return enqueue_stateless(r, k, S - Sh, combos, ss, Sh); });
-            } else {
-                s = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
-                             [&] { return enqueue_stateless(r, k, S, combos, ss); });
+            st = run_part(r, graph_key(0, k, S, 0, 0, combos), ss,
+                          [&] { return enqueue_stateless(r, k, S, combos, ss); });
+        }
+        if (st == DISC_OK && copied) st = cuda_status(cudaEventRecord(r.ev_in_free[k], ss));
+        if (st == DISC_OK && pipe) {
+            st = cuda_status(cudaEventRecord(r.ev_state[k], ss));
+            if (st == DISC_OK) st = cuda_status(cudaStreamWaitEvent(sr, r.ev_state[k], 0));
+        }
+        return st;
+    };
+    // back: room for the batch's new voxels and ids (the tables grow when
+    // they could pass their limits, and the batch's map pointers follow),
+    // its serial part, its counters to the call's history
+    auto back = [&](Pending& P) -> disc_status {
+        const int k = P.k, G = P.G, J = P.J, S = P.S, lo = P.b * r.Jmax;
+        disc_status st = DISC_OK;
+        if (!P.timed) {
+            MapRefs* hrefs = (MapRefs*)(P.blk.data() + r.off_refs);
+            bool moved = false;
+            for (int gi = 0; gi < G && st == DISC_OK; gi++) {
+                Work& wk = w[P.gl[gi]];
+                const int cnt = std::min(r.Jmax, wk.valid - lo);
+                int64_t masks = 0;
+                for (int j = 0; j < cnt; j++) masks += wk.frames[lo + j].num_masks;
+                st = ensure_instance_room(wk.m, masks, sr);
+                const MapRefs now = map_refs(wk.m);
+                if (std::memcmp(&now, &hrefs[gi], sizeof(MapRefs)) != 0) {
+                    hrefs[gi] = now;
+                    moved = true;
+                }
             }
-            if (s == DISC_OK && copied) s = cuda_status(cudaEventRecord(r.ev_in_free[k], ss));
-            if (s == DISC_OK && pipe) {
-                s = cuda_status(cudaEventRecord(r.ev_state[k], ss));
-                if (s == DISC_OK) s = cuda_status(cudaStreamWaitEvent(sr, r.ev_state[k], 0));
-            }
-            if (s == DISC_OK && !one_graph) s = room_check(r, k, G, J, w, gl, hrefs, sr);
-            if (s == DISC_OK)
-                s = run_part(r, graph_key(1, k, 0, G, J, 0), sr, [&] { return enqueue_serial(r, k, G, J, sr); });
+            if (st == DISC_OK && moved)
+                st = cuda_status(cudaMemcpyAsync(r.d_param[k] + r.off_refs, hrefs, sizeof(MapRefs) * G,
+                                                 cudaMemcpyHostToDevice, sr));
+            if (st == DISC_OK) st = room_check(r, k, G, J, w, P.gl, hrefs, sr);
+            if (st == DISC_OK)
+                st = run_part(r, graph_key(1, k, S, G, J, P.combos & COMBO_DILATE), sr,
+                              [&] { return enqueue_serial(r, k, S, G, J, P.combos, sr); });
         }
         // the batch's counters, in slot order, to the call's history
-        if (s == DISC_OK)
-            s = cuda_status(cudaMemcpyAsync(r.d_hist + hoff, r.bs[k].base.ctr, sizeof(FrameCounters) * S,
-                                            cudaMemcpyDeviceToDevice, sr));
-        if (s == DISC_OK && pipe) s = cuda_status(cudaEventRecord(r.ev_serial[k], sr));
-        if (s == DISC_OK) s = cuda_status(cudaGetLastError());
-        if (s != DISC_OK) {
-            undo();
-            break;
-        }
+        if (st == DISC_OK)
+            st = cuda_status(cudaMemcpyAsync(r.d_hist + P.hoff, r.bs[k].base.ctr, sizeof(FrameCounters) * S,
+                                             cudaMemcpyDeviceToDevice, sr));
+        if (st == DISC_OK && pipe) st = cuda_status(cudaEventRecord(r.ev_serial[k], sr));
+        if (st == DISC_OK) st = cuda_status(cudaGetLastError());
+        if (st != DISC_OK) return st;
         for (int gi = 0; gi < G; gi++) {
-            Work& wk = w[gl[gi]];
+            Work& wk = w[P.gl[gi]];
             const int cnt = std::min(r.Jmax, wk.valid - lo);
             for (int j = 0; j < cnt; j++) {
                 const disc_frame& f = wk.frames[lo + j];
-                if (one_graph) wk.m->used_upper += (uint64_t)f.width * f.height;
+                if (P.timed) wk.m->used_upper += (uint64_t)f.width * f.height;
                 wk.m->next_id_upper += f.num_masks;
             }
         }
         r.last_set = k;
         r.last_slot = S - 1;
-        const Work& wl = w[gl[G - 1]];
+        const Work& wl = w[P.gl[G - 1]];
         r.last_M = wl.frames[lo + std::min(r.Jmax, wl.valid - lo) - 1].num_masks;
         r.have_frame = true;
-        hoff += S;
+        return DISC_OK;
+    };
+    Pending cur, nxt;
+    if (nbatch > 0) {
+        s = front(0, cur);
+        if (s != DISC_OK && cur.b >= 0) undo(cur);
+    }
+    for (int b = 0; b < nbatch && s == DISC_OK && cur.b >= 0; b++) {
+        s = back(cur);
+        if (s != DISC_OK) {
+            undo(cur);
+            break;
+        }
+        const disc_status sn = b + 1 < nbatch ? front(b + 1, nxt) : DISC_OK;
+        if (sn != DISC_OK) {
+            if (nxt.b >= 0) undo(nxt);
+            s = sn;
+            break;
+        }
+        std::swap(cur, nxt);
+        nxt.b = -1;
     }
     if (pipe) {
         // the caller's stream continues after the call's work
@@ -2428,9 +2590,10 @@ disc_status disc_map_phase_times(disc_map* m, double* ms, int64_t* launches, int
 
 const char* disc_phase_name(int32_t i)
 {
-    static const char* names[PH_COUNT] = {"clear",     "token_stats", "coverage", "weights", "pool_exact",
+    static const char* names[PH_COUNT] = {"clear",     "token_stats", "coverage",    "weights", "pool_exact",
                                           "pool_gemm", "dbscan",      "backproject", "entries", "overlap",
-                                          "score",     "union",       "apply"};
+                                          "score",     "union",       "apply",       "lookup",  "associate",
+                                          "commit"};
     return (i >= 0 && i < PH_COUNT) ? names[i] : "";
 }
 

@@ -107,7 +107,8 @@ struct VoxelTable {              // open addressing, linear probing
 };
 
 struct Instances {
-    int32_t* parent;             // flat: parent[i] is always a root
+    int32_t* parent;             // flat between batches: parent[i] is always a root (inside a batch
+                                 // merges may leave chains, followed to the root)
     long long* count;            // voxels per root
     float* Q;
     float* E;                    // [cap][D] stored embedding
@@ -142,6 +143,10 @@ struct FrameCounters {
     int32_t denoised;            // pixels DBSCAN marked as noise
     int32_t db_left[2];          // DBSCAN points left to the warp-wide core / noise search
     int32_t db_cursor;           // DBSCAN cell ranges handed out
+    int32_t n_absent;            // entries whose voxel was absent from the map at the batch start
+    int32_t n_pre;               // distinct (segment, label) and (segment, earlier frame's segment) items
+    int32_t n_scored;            // (segment, instance) pairs that passed the overlap gate (cosine taken)
+    int32_t n_copies;            // embeddings written (new instances and fusion winners)
 };
 
 // One slot of the per-frame (segment, voxel) hash: one 32-byte sector.
@@ -188,6 +193,17 @@ struct Scratch {
     unsigned long long* sent;   // [scap] key of entry i (dense copy of the slot key)
     int32_t* elab;              // [scap] per entry: label at batch start, -1 absent
     unsigned long long smask;
+    // per-frame overlap items, counted over the whole batch before the frames
+    // run in order (one hash per slot, capacity scap, cleared slot by slot):
+    // key = mask << 33 | tag << 32 | x, tag 0: x = the voxel's label at the
+    // batch start; tag 1: x = j0 << 9 | m0, the voxel was first seen in the
+    // batch by frame j0 of the same map, its lowest segment there m0
+    unsigned long long* pkey;   // [scap] EMPTY = ~0
+    int32_t* pcnt;              // [scap] voxels of the item
+    int32_t* plist;             // [scap] used slots, in claim order
+    int32_t* aent;              // [scap] entries absent at the batch start
+    int32_t* aslot;             // [scap] and their slot in the batch's absent-voxel hash
+    int32_t* newcnt;            // [MM] voxels this frame inserts, by their lowest segment
     FrameCounters* ctr;
     // DBSCAN (Sec. III-A), allocated once a frame asks for it
     unsigned long long* dkey;   // [scap] (mask << 54 | cell); EMPTY = 0
@@ -243,6 +259,14 @@ struct BatchScratch {
         s.slist += f * scap;
         s.sent += f * scap;
         s.elab += f * scap;
+        if (s.pkey) {
+            s.pkey += f * scap;
+            s.pcnt += f * scap;
+            s.plist += f * scap;
+            s.aent += f * scap;
+            s.aslot += f * scap;
+            s.newcnt += f * sMM;
+        }
         s.ctr += f;
         if (s.dkey) {
             s.dkey += f * scap;
@@ -319,6 +343,20 @@ struct SerialStep {
     int j;                      // this step
     BatchScratch view;          // the second grid's features per slot (zero when the runner has none)
     int cta_scale;              // serial kernels' CTAs, in quarters of the default count (4 = default)
+    int* merged;                // [G] some frame of map g merged instances in this batch (k_associate)
+};
+
+// Voxels absent from their map when a batch starts, over all maps of the
+// batch: key (map + 1) << 54 | voxel key (never 0 = EMPTY), value the least
+// (frame position j << 9 | segment m) of the batch's segments that contain
+// the voxel.  Filled by k_lookup, read by k_absent, emptied by k_commit,
+// which inserts each voxel with its first frame's label.
+struct AbsentHash {
+    unsigned long long* key;    // [cap]
+    int32_t* val;               // [cap] above every (j << 9 | m) when empty
+    int32_t* list;              // [cap] used slots
+    int32_t* n;                 // [1] used slots
+    unsigned long long mask;    // cap - 1
 };
 
 // frame parameters passed by value
@@ -332,6 +370,7 @@ struct FrameParams {
     int32_t ov_num, ov_den, min_px;
     int32_t token_bf16;
     int32_t map;           // position of the frame's map in the batch (MapRefs index)
+    int32_t jpos;          // position of the frame among its map's frames in the batch
     int32_t precision;     // disc_precision of the fast pooled embedding and scoring
     int32_t dilate;        // overlap_dilation: 26-neighbour overlap
     int32_t assoc;         // the map has a second grid: association on its features

@@ -36,6 +36,7 @@ __global__ void k_slot_clear(BatchScratch bs, int D, int MM)
             sc.ang[i] = 0;
             sc.nvox[i] = 0;
             sc.segrep[i] = -1;
+            if (sc.newcnt) sc.newcnt[i] = 0;
         }
     }
 }
@@ -163,36 +164,36 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
             }
         }
     }
-    // Pixels of one warp with the same (mask, voxel) key are summed first:
-    // each 2^-32 fixed-point component v (|v| <= 2^32) splits exactly into
-    // v = (v >> 16) * 2^16 + (v & 0xffff), whose parts add in 32-bit integers
-    // for up to a whole tile.  One lane per key then updates the tile hash;
-    // the lane that claims a tile slot lists it.
-    const unsigned long long hk = keyed ? (((unsigned long long)lab << 54) | key) : 0ull;
-    const unsigned grp = __match_any_sync(0xffffffffu, hk);
-    unsigned part[6];
-#pragma unroll
-    for (int r = 0; r < 3; r++) {
-        part[2 * r] = (unsigned)(int)(nfix[r] >> 16);
-        part[2 * r + 1] = (unsigned)(nfix[r] & 0xffff);
-    }
-#pragma unroll
-    for (int r = 0; r < 6; r++) part[r] = __reduce_add_sync(grp, part[r]);
-    if (keyed && lane == __ffs(grp) - 1) {
+    // Every keyed pixel adds its normal to its (mask, voxel) slot of the
+    // tile's shared hash: each 2^-32 fixed-point component v (|v| <= 2^32)
+    // splits exactly into v = (v >> 16) * 2^16 + (v & 0xffff), whose parts
+    // add in 32-bit integers for up to a whole tile.  (Summing a warp's equal
+    // keys first with a warp match and reductions measured 27 against 16 us
+    // per frame: those warp instructions cost more than the shared-memory
+    // atomics they save.)  The pixel that claims a slot lists it.
+    if (keyed) {
+        const unsigned long long hk = ((unsigned long long)lab << 54) | key;
         // tile-level dedupe: at most BP_THREADS distinct keys in BP_SLOTS slots
         unsigned t = (unsigned)(mix64(hk) & (BP_SLOTS - 1));
         while (true) {
-            const unsigned long long prev = atomicCAS(&tkey[t], 0ull, hk);
-            if (prev == 0ull) {
-                tlist[atomicAdd(&tcount[2], 1)] = (unsigned short)t;
-                break;
+            const unsigned long long cur = tkey[t];
+            if (cur == hk) break;
+            if (cur == 0ull) {
+                const unsigned long long prev = atomicCAS(&tkey[t], 0ull, hk);
+                if (prev == 0ull) {
+                    tlist[atomicAdd(&tcount[2], 1)] = (unsigned short)t;
+                    break;
+                }
+                if (prev == hk) break;
             }
-            if (prev == hk) break;
             t = (t + 1) & (BP_SLOTS - 1);
         }
 #pragma unroll
-        for (int r = 0; r < 6; r++)
-            if (part[r]) atomicAdd((unsigned*)&tn[r][t], part[r]);
+        for (int r = 0; r < 3; r++) {
+            const unsigned hi = (unsigned)(int)(nfix[r] >> 16), lo = (unsigned)(nfix[r] & 0xffff);
+            if (hi) atomicAdd((unsigned*)&tn[2 * r][t], hi);
+            if (lo) atomicAdd((unsigned*)&tn[2 * r + 1][t], lo);
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -260,8 +261,10 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
 
 // ---- per unique (segment, voxel): Eq. 3 term, |V_m|, label at batch start ------
 // Per-segment sums gather in shared memory first (one global atomic per
-// block and segment).
-__global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs* refs, int f0)
+// block and segment).  lookup = 0: the labels are left to k_lookup, which
+// runs once the previous batch's voxels are in (this kernel then reads no
+// map state).
+__global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs* refs, int f0, int lookup)
 {
     extern __shared__ unsigned char ent_smem[];
     const FrameParams& fp = fps[f0 + blockIdx.y];
@@ -321,7 +324,7 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
                 atomicAdd((unsigned long long*)&s_ang[m - 1], (unsigned long long)tf);
                 atomicAdd(&s_nv[m - 1], 1);
             }
-            if (!valid) continue;
+            if (!valid || !lookup) continue;
             // label in the map at the start of the batch (-1: absent then)
             unsigned long long h = mix64(key) & vt.mask;
             int lab = -1, probes = 0;
@@ -385,10 +388,10 @@ int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, i
 }
 
 int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
-                   cudaStream_t st)
+                   bool lookup, cudaStream_t st)
 {
     const size_t smem = 12 * (size_t)std::max(Mmax, 1) + 16;
-    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, refs, f0);
+    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, refs, f0, lookup ? 1 : 0);
     return 1;
 }
 

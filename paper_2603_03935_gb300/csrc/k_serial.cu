@@ -44,8 +44,8 @@ __device__ __forceinline__ int vt_label(const VoxelTable& vt, unsigned long long
     return -1;
 }
 
-// one more voxel of segment-instance pair okey in the frame's pair hash
-__device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned long long okey)
+// cnt more voxels of segment-instance pair okey in the frame's pair hash
+__device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned long long okey, int cnt = 1)
 {
     unsigned long long t = mix64(okey) & ss.omask;
     for (unsigned long long pr = 0;; pr++) {
@@ -65,7 +65,7 @@ __device__ void add_pair(const Scratch& sc, const SerialScratch& ss, unsigned lo
             return;
         }
     }
-    atomicAdd(&ss.ocnt[t], 1);
+    atomicAdd(&ss.ocnt[t], cnt);
 }
 
 // Neighbourhood overlap (overlap_dilation): segment voxel `key` (label lab,
@@ -228,91 +228,166 @@ __device__ __forceinline__ float4 bf16x4_to_f32(uint2 v)
 
 // With a second grid (inst.A), the fast and exact features, their bounds and
 // the instance side all come from the association features (view scratch va).
-__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scratch& va, const SerialScratch& ss,
-                            const Instances& inst)
+struct GateFeatures {
+    const float* fast;    // [M][D] tensor-core pooled features
+    const float* exact;   // [M][D] exact pooled features
+    const float* bm;      // [M] sum_p w ||f_p|| (error-bound scale)
+    const float* Sm;      // [cap][D] instances' scoring master
+    int D;
+};
+
+__device__ __forceinline__ GateFeatures gate_features(const FrameParams& fp, const Scratch& sc, const Scratch& va,
+                                                      const Instances& inst)
+{
+    GateFeatures g;
+    g.D = scoring_dim(inst, fp.D);
+    g.Sm = scoring_master(inst);
+    g.fast = inst.A ? va.Efast : sc.Efast;
+    g.exact = inst.A ? va.Ecan : sc.Ecan;
+    g.bm = inst.A ? va.Bm : sc.Bm;
+    return g;
+}
+
+// The cosine gate of segment m against instance k, by one warp (all 32 lanes
+// call; every lane returns the decision).  The fast cosine takes the
+// tensor-core pooled feature and the instance's scoring copy; inside its
+// error band the pair is re-scored exactly (*border counts those).
+__device__ bool warp_cosine_gate(const FrameParams& fp, const GateFeatures& gf, const Instances& inst, int m, int k,
+                                 int* border)
 {
     const int lane = threadIdx.x & 31;
-    const int npairs = sc.ctr->n_pairs;
-    const int D = scoring_dim(inst, fp.D);
-    const float* Sm = scoring_master(inst);
-    const float* fast = inst.A ? va.Efast : sc.Efast;
-    const float* exact = inst.A ? va.Ecan : sc.Ecan;
-    const float* bm = inst.A ? va.Bm : sc.Bm;
-    int border = 0;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npairs; i += (gridDim.x * blockDim.x) >> 5) {
-        const int slot = ss.olist[i];
-        const unsigned long long okey = ss.okeys[slot];
-        const int m = (int)(okey >> 32) - 1;
-        const int k = (int)(okey & 0xffffffffu);
-        const long long ov = ss.ocnt[slot];
-        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
-        const long long denom = min((long long)sc.nvox[m], inst.count[k]);
-        if (ov * (long long)fp.ov_den < (long long)fp.ov_num * denom) continue;
-        const float* a = fast + (size_t)m * D;
-        const float* b = Sm + (size_t)k * D;
-        float dt = 0.0f, na = 0.0f, nb = 0.0f;
-        if (inst.Eb && (D & 3) == 0) {  // bf16 scoring copy: 8-byte rows of 4
-            const float4* a4 = (const float4*)a;
-            const uint2* b4 = (const uint2*)(inst.Eb + (size_t)k * D);
-            const int n4 = D >> 2;
-            for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
-                float4 xs[4];
-                uint2 ys[4];
+    const int D = gf.D;
+    const float* fast = gf.fast;
+    const float* exact = gf.exact;
+    const float* bm = gf.bm;
+    const float* Sm = gf.Sm;
+    const float* a = fast + (size_t)m * D;
+    const float* b = Sm + (size_t)k * D;
+    const float bmm = bm[m], erk = inst.Er ? inst.Er[k] : 0.0f;  // loaded beside the rows
+    float dt = 0.0f, na = 0.0f, nb = 0.0f;
+    if (inst.Eb && (D & 3) == 0) {  // bf16 scoring copy: 8-byte rows of 4
+        const float4* a4 = (const float4*)a;
+        const uint2* b4 = (const uint2*)(inst.Eb + (size_t)k * D);
+        const int n4 = D >> 2;
+        for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+            float4 xs[4];
+            uint2 ys[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int d = d0 + j * 32 + lane;
-                    xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    ys[j] = d < n4 ? b4[d] : make_uint2(0u, 0u);
-                }
+            for (int j = 0; j < 4; j++) {
+                const int d = d0 + j * 32 + lane;
+                xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ys[j] = d < n4 ? b4[d] : make_uint2(0u, 0u);
+            }
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const float4 x = xs[j], y = bf16x4_to_f32(ys[j]);
-                    dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
-                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-                    nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
-                }
+            for (int j = 0; j < 4; j++) {
+                const float4 x = xs[j], y = bf16x4_to_f32(ys[j]);
+                dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
             }
-        } else if (inst.E8 && (D & 3) == 0) {  // E4M3 scoring copy: 4-byte words of 4
-            const float4* a4 = (const float4*)a;
-            const uint32_t* b4 = (const uint32_t*)(inst.E8 + (size_t)k * D);
-            const int n4 = D >> 2;
-            for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
-                float4 xs[4];
-                uint32_t ys[4];
+        }
+    } else if (inst.E8 && (D & 3) == 0) {  // E4M3 scoring copy: 4-byte words of 4
+        const float4* a4 = (const float4*)a;
+        const uint32_t* b4 = (const uint32_t*)(inst.E8 + (size_t)k * D);
+        const int n4 = D >> 2;
+        for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+            float4 xs[4];
+            uint32_t ys[4];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int d = d0 + j * 32 + lane;
-                    xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    ys[j] = d < n4 ? b4[d] : 0u;
-                }
+            for (int j = 0; j < 4; j++) {
+                const int d = d0 + j * 32 + lane;
+                xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ys[j] = d < n4 ? b4[d] : 0u;
+            }
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const float4 x = xs[j];
-                    const float y0 = from_e4m3(ys[j] & 0xffu), y1 = from_e4m3((ys[j] >> 8) & 0xffu);
-                    const float y2 = from_e4m3((ys[j] >> 16) & 0xffu), y3 = from_e4m3(ys[j] >> 24);
-                    dt += x.x * y0 + x.y * y1 + x.z * y2 + x.w * y3;
-                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-                    nb += y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3;
-                }
+            for (int j = 0; j < 4; j++) {
+                const float4 x = xs[j];
+                const float y0 = from_e4m3(ys[j] & 0xffu), y1 = from_e4m3((ys[j] >> 8) & 0xffu);
+                const float y2 = from_e4m3((ys[j] >> 16) & 0xffu), y3 = from_e4m3(ys[j] >> 24);
+                dt += x.x * y0 + x.y * y1 + x.z * y2 + x.w * y3;
+                na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                nb += y0 * y0 + y1 * y1 + y2 * y2 + y3 * y3;
             }
-        } else if (inst.E8) {
-            const uint8_t* b8 = inst.E8 + (size_t)k * D;
-            for (int d = lane; d < D; d += 32) {
-                const float x = a[d], y = from_e4m3(b8[d]);
-                dt += x * y;
-                na += x * x;
-                nb += y * y;
+        }
+    } else if (inst.E8) {
+        const uint8_t* b8 = inst.E8 + (size_t)k * D;
+        for (int d = lane; d < D; d += 32) {
+            const float x = a[d], y = from_e4m3(b8[d]);
+            dt += x * y;
+            na += x * x;
+            nb += y * y;
+        }
+    } else if (inst.Eb) {
+        const uint16_t* bb = inst.Eb + (size_t)k * D;
+        for (int d = lane; d < D; d += 32) {
+            const float x = a[d], y = __uint_as_float((unsigned)bb[d] << 16);
+            dt += x * y;
+            na += x * x;
+            nb += y * y;
+        }
+    } else if ((D & 3) == 0 && D <= 1024) {  // 16-byte rows of up to 1024: every load in flight at once
+        const float4* a4 = (const float4*)a;
+        const float4* b4 = (const float4*)b;
+        const int n4 = D >> 2;
+        float4 xs[8], ys[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int d = j * 32 + lane;
+            xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ys[j] = d < n4 ? b4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float4 x = xs[j], y = ys[j];
+            dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+            na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+            nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+        }
+    } else if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads, 8 in flight per lane
+        const float4* a4 = (const float4*)a;
+        const float4* b4 = (const float4*)b;
+        const int n4 = D >> 2;
+        for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
+            float4 xs[4], ys[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int d = d0 + j * 32 + lane;
+                xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ys[j] = d < n4 ? b4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-        } else if (inst.Eb) {
-            const uint16_t* bb = inst.Eb + (size_t)k * D;
-            for (int d = lane; d < D; d += 32) {
-                const float x = a[d], y = __uint_as_float((unsigned)bb[d] << 16);
-                dt += x * y;
-                na += x * x;
-                nb += y * y;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float4 x = xs[j], y = ys[j];
+                dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+                nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
             }
-        } else if ((D & 3) == 0) {  // rows are 16-byte aligned: vector loads, 8 in flight per lane
-            const float4* a4 = (const float4*)a;
+        }
+    } else {
+        for (int d = lane; d < D; d += 32) {
+            const float x = a[d], y = b[d];
+            dt += x * y;
+            na += x * x;
+            nb += y * y;
+        }
+    }
+    dt = warp_sum(dt);
+    na = warp_sum(na);
+    nb = warp_sum(nb);
+    bool edge;
+    const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
+    // |cos(a, b') - cos(e, b)| <= 2 |a - e| / |a| + 2 |b' - b| / |b|, plus
+    // the fp32 arithmetic of cf; 10 % slack on the bounds
+    float band = (na > 0.0f) ? 2.2f * fp.eta * bmm / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
+    if (inst.Er) band += 2.2f * erk;
+    if (fabsf(cf - fp.tau) > band) {
+        edge = cf >= fp.tau;
+    } else {
+        // exact re-score with the exact pooled embedding
+        const float* ae = exact + (size_t)m * D;
+        long long xd = 0, xa = 0, xb = 0;
+        if ((D & 3) == 0) {  // all of a lane's loads in flight before the exact sums
+            const float4* a4 = (const float4*)ae;
             const float4* b4 = (const float4*)b;
             const int n4 = D >> 2;
             for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
@@ -325,77 +400,56 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scra
                 }
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
-                    const float4 x = xs[j], y = ys[j];
-                    dt += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
-                    na += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-                    nb += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+                    const float xv[4] = {xs[j].x, xs[j].y, xs[j].z, xs[j].w};
+                    const float yv[4] = {ys[j].x, ys[j].y, ys[j].z, ys[j].w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        xd += fix32f(__fmul_rn(xv[c], yv[c]), S_SQ);
+                        xa += fix32f(__fmul_rn(xv[c], xv[c]), S_SQ);
+                        xb += fix32f(__fmul_rn(yv[c], yv[c]), S_SQ);
+                    }
                 }
             }
         } else {
             for (int d = lane; d < D; d += 32) {
-                const float x = a[d], y = b[d];
-                dt += x * y;
-                na += x * x;
-                nb += y * y;
+                const float x = ae[d], y = b[d];
+                xd += fix32f(__fmul_rn(x, y), S_SQ);
+                xa += fix32f(__fmul_rn(x, x), S_SQ);
+                xb += fix32f(__fmul_rn(y, y), S_SQ);
             }
         }
-        dt = warp_sum(dt);
-        na = warp_sum(na);
-        nb = warp_sum(nb);
-        bool edge;
-        const float cf = (na > 0.0f && nb > 0.0f) ? dt / (sqrtf(na) * sqrtf(nb)) : 0.0f;
-        // |cos(a, b') - cos(e, b)| <= 2 |a - e| / |a| + 2 |b' - b| / |b|, plus
-        // the fp32 arithmetic of cf; 10 % slack on the bounds
-        float band = (na > 0.0f) ? 2.2f * fp.eta * bm[m] / sqrtf(na) + fp.dot_err + 1e-6f : 2.0f;
-        if (inst.Er) band += 2.2f * inst.Er[k];
-        if (fabsf(cf - fp.tau) > band) {
-            edge = cf >= fp.tau;
-        } else {
-            // exact re-score with the exact pooled embedding
-            const float* ae = exact + (size_t)m * D;
-            long long xd = 0, xa = 0, xb = 0;
-            if ((D & 3) == 0) {  // all of a lane's loads in flight before the exact sums
-                const float4* a4 = (const float4*)ae;
-                const float4* b4 = (const float4*)b;
-                const int n4 = D >> 2;
-                for (int d0 = 0; d0 < n4; d0 += 32 * 4) {
-                    float4 xs[4], ys[4];
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const int d = d0 + j * 32 + lane;
-                        xs[j] = d < n4 ? a4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        ys[j] = d < n4 ? b4[d] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        const float xv[4] = {xs[j].x, xs[j].y, xs[j].z, xs[j].w};
-                        const float yv[4] = {ys[j].x, ys[j].y, ys[j].z, ys[j].w};
-#pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            xd += fix32f(__fmul_rn(xv[c], yv[c]), S_SQ);
-                            xa += fix32f(__fmul_rn(xv[c], xv[c]), S_SQ);
-                            xb += fix32f(__fmul_rn(yv[c], yv[c]), S_SQ);
-                        }
-                    }
-                }
-            } else {
-                for (int d = lane; d < D; d += 32) {
-                    const float x = ae[d], y = b[d];
-                    xd += fix32f(__fmul_rn(x, y), S_SQ);
-                    xa += fix32f(__fmul_rn(x, x), S_SQ);
-                    xb += fix32f(__fmul_rn(y, y), S_SQ);
-                }
-            }
-            xd = warp_sum(xd);
-            xa = warp_sum(xa);
-            xb = warp_sum(xb);
-            float ce = 0.0f;
-            if (xa != 0 && xb != 0)
-                ce = __double2float_rn(__ddiv_rn(unfix(xd, S_SQ),
-                                                 __dmul_rn(__dsqrt_rn(unfix(xa, S_SQ)), __dsqrt_rn(unfix(xb, S_SQ)))));
-            edge = ce >= fp.tau;
-            border++;
-        }
+        xd = warp_sum(xd);
+        xa = warp_sum(xa);
+        xb = warp_sum(xb);
+        float ce = 0.0f;
+        if (xa != 0 && xb != 0)
+            ce = __double2float_rn(__ddiv_rn(unfix(xd, S_SQ),
+                                             __dmul_rn(__dsqrt_rn(unfix(xa, S_SQ)), __dsqrt_rn(unfix(xb, S_SQ)))));
+        edge = ce >= fp.tau;
+        (*border)++;
+    }
+    return edge;
+}
+
+// Warps w0, w0 + nw, ... of the launch take the pairs in turn.
+__device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scratch& va, const SerialScratch& ss,
+                            const Instances& inst, int w0, int nw)
+{
+    const int lane = threadIdx.x & 31;
+    const int npairs = sc.ctr->n_pairs;
+    const GateFeatures gf = gate_features(fp, sc, va, inst);
+    int border = 0, scored = 0;
+    for (int i = w0; i < npairs; i += nw) {
+        const int slot = ss.olist[i];
+        const unsigned long long okey = ss.okeys[slot];
+        const int m = (int)(okey >> 32) - 1;
+        const int k = (int)(okey & 0xffffffffu);
+        const long long ov = ss.ocnt[slot];
+        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
+        const long long denom = min((long long)sc.nvox[m], inst.count[k]);
+        if (ov * (long long)fp.ov_den < (long long)fp.ov_num * denom) continue;
+        scored++;
+        const bool edge = warp_cosine_gate(fp, gf, inst, m, k, &border);
         if (edge && lane == 0) {
             const int e = atomicAdd(ss.edge_n, 1);
             if (e < ss.edge_cap) {
@@ -407,13 +461,15 @@ __device__ void phase_score(const FrameParams& fp, const Scratch& sc, const Scra
         }
     }
     if (lane == 0 && border) atomicAdd(&sc.ctr->borderline, border);
+    if (lane == 0 && scored) atomicAdd(&sc.ctr->n_scored, scored);
 }
 
 // ---- union, new ids, merges, fusion (one block) ------------------------------------
 // Shared memory: a hash set of the frame's active roots (all overlap pairs)
 // that also hands out local indices to the roots that carry an edge, and
 // per-local-root arrays for the union-find and the fusion.  Every step runs
-// in parallel on shared memory except the new-id scan over the masks.
+// in parallel on shared memory.  Any block of a multiple of 32 threads, at
+// least MAX_MASKS, runs it.
 constexpr int UNION_THREADS = 256;
 constexpr int PAIR_CAP = 8192;             // distinct (segment, instance) overlaps per frame
 constexpr int EDGE_ROOT_CAP = 2048;        // distinct instances with an accepted edge per frame
@@ -454,12 +510,19 @@ __device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hv
     return (int)(hval[h] & ~UH_LOCAL);
 }
 
-__device__ void phase_union(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
-                            int* next_id, unsigned char* union_smem)
+// The frame's npairs overlap pairs give their roots through pair_root(i);
+// its nedge accepted edges are in ss.edge_m/k, or (edges_in_place) already in
+// the block's em/ek arrays.  uhash_cap: the root hash's slots in union_smem
+// (>= 2 * npairs); the layout is hkey, hval [uhash_cap], the per-root arrays
+// [EDGE_ROOT_CAP], em, ek [EDGE_CAP].
+template <class PairRoot>
+__device__ void union_frame(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
+                            int* next_id, unsigned char* union_smem, unsigned uhash_cap, int npairs, int nedge,
+                            bool edges_in_place, PairRoot pair_root)
 {
-    unsigned* hkey = (unsigned*)union_smem;           // [UHASH] root id
-    unsigned* hval = hkey + UHASH;                    // [UHASH] claimant edge, then UH_LOCAL | local index
-    int* gid = (int*)(hval + UHASH);                  // [EDGE_ROOT_CAP] local -> instance id
+    unsigned* hkey = (unsigned*)union_smem;           // [uhash_cap] root id
+    unsigned* hval = hkey + uhash_cap;                // [uhash_cap] claimant edge, then UH_LOCAL | local index
+    int* gid = (int*)(hval + uhash_cap);              // [EDGE_ROOT_CAP] local -> instance id
     int* uf = gid + EDGE_ROOT_CAP;                    // union-find over local indices
     int* best_src = uf + EDGE_ROOT_CAP;               // fusion winner per component
     float* best_q = (float*)(best_src + EDGE_ROOT_CAP);
@@ -472,12 +535,10 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     __shared__ int snv[MAX_MASKS];
     __shared__ float sq[MAX_MASKS];
     __shared__ int s_nroots, s_nloc, s_merges, s_new, s_ncopy, s_next;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, NT = blockDim.x;
     FrameCounters* ctr = sc.ctr;
     const int M = fp.M;
-    const int npairs = ctr->n_pairs;
-    const int nedge = min(*ss.edge_n, ss.edge_cap);
-    if (npairs > PAIR_CAP || nedge > EDGE_CAP) {
+    if (2u * (unsigned)npairs > uhash_cap || nedge > EDGE_CAP) {
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
         return;
     }
@@ -485,15 +546,15 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     while (hsize < 2u * (unsigned)npairs) hsize <<= 1;
     const unsigned hm = hsize - 1;
     // the edges, once, into shared memory (segment, root)
-    for (int e = tid; e < nedge; e += UNION_THREADS) {
+    for (int e = tid; e < nedge && !edges_in_place; e += NT) {
         em[e] = ss.edge_m[e];
         ek[e] = ss.edge_k[e];
     }
-    for (int i = tid; i < (int)hsize; i += UNION_THREADS) {
+    for (int i = tid; i < (int)hsize; i += NT) {
         hkey[i] = UH_EMPTY;
         hval[i] = UH_UNUSED;
     }
-    for (int m = tid; m < M; m += UNION_THREADS) {
+    for (int m = tid; m < M; m += NT) {
         anchor[m] = INT_MAX;
         snv[m] = sc.nvox[m];
         sq[m] = sc.S[5 * m + 4];
@@ -508,8 +569,8 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     }
     __syncthreads();
     // (1) active set: distinct roots of all overlap pairs
-    for (int i = tid; i < npairs; i += UNION_THREADS) {
-        const unsigned k = (unsigned)(ss.okeys[ss.olist[i]] & 0xffffffffu);
+    for (int i = tid; i < npairs; i += NT) {
+        const unsigned k = pair_root(i);
         unsigned h = uhash(k, hm);
         while (true) {
             const unsigned cur = hkey[h];
@@ -525,14 +586,14 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     __syncthreads();
     // (2) local indices for the roots that carry an edge: the first edge to
     //     claim a root's slot assigns the index
-    for (int e = tid; e < nedge; e += UNION_THREADS) {
+    for (int e = tid; e < nedge; e += NT) {
         const unsigned k = (unsigned)ek[e];
         unsigned h = uhash(k, hm);
         while (hkey[h] != k) h = (h + 1) & hm;
         atomicCAS(&hval[h], UH_UNUSED, (unsigned)e);
     }
     __syncthreads();
-    for (int e = tid; e < nedge; e += UNION_THREADS) {
+    for (int e = tid; e < nedge; e += NT) {
         const unsigned k = (unsigned)ek[e];
         unsigned h = uhash(k, hm);
         while (hkey[h] != k) h = (h + 1) & hm;
@@ -557,9 +618,9 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     //     root onto the segment's anchor; a hook always links the root with
     //     the larger instance id under the smaller one, so each set's root is
     //     its smallest instance id
-    for (int e = tid; e < nedge; e += UNION_THREADS) atomicMin(&anchor[em[e]], local_of(hkey, hval, hm, (unsigned)ek[e]));
+    for (int e = tid; e < nedge; e += NT) atomicMin(&anchor[em[e]], local_of(hkey, hval, hm, (unsigned)ek[e]));
     __syncthreads();
-    for (int e = tid; e < nedge; e += UNION_THREADS) {
+    for (int e = tid; e < nedge; e += NT) {
         int x = local_of(hkey, hval, hm, (unsigned)ek[e]);
         int y = anchor[em[e]];
         while (true) {
@@ -571,22 +632,22 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
         }
     }
     __syncthreads();
-    for (int x = tid; x < nloc; x += UNION_THREADS) uf[x] = uf_find(uf, x);  // stores only roots
+    for (int x = tid; x < nloc; x += NT) uf[x] = uf_find(uf, x);  // stores only roots
     __syncthreads();
-    for (int m = tid; m < M; m += UNION_THREADS) srep[m] = anchor[m] != INT_MAX ? gid[uf[anchor[m]]] : -1;
+    for (int m = tid; m < M; m += NT) srep[m] = anchor[m] != INT_MAX ? gid[uf[anchor[m]]] : -1;
     __syncthreads();
     // (4) new instances for live segments without an edge, in mask order:
     //     the id of mask m is next_id plus the number of such masks before it
-    //     (a block-wide exclusive scan; M <= UNION_THREADS)
+    //     (a block-wide exclusive scan; M <= MAX_MASKS <= NT)
     {
-        __shared__ int wtot[UNION_THREADS / 32];
+        __shared__ int wtot[32];
         const int lane = tid & 31, wid = tid >> 5;
         const bool want = tid < M && snv[tid] > 0 && srep[tid] < 0;
         const unsigned bal = __ballot_sync(0xffffffffu, want);
         if (lane == 0) wtot[wid] = __popc(bal);
         __syncthreads();
         int before = __popc(bal & ((1u << lane) - 1)), total = 0;
-        for (int w = 0; w < UNION_THREADS / 32; w++) {
+        for (int w = 0; w < (NT >> 5); w++) {
             before += w < wid ? wtot[w] : 0;
             total += wtot[w];
         }
@@ -613,7 +674,7 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     }
     __syncthreads();
     if (ctr->err) return;
-    for (int m = tid; m < M; m += UNION_THREADS) sc.segrep[m] = srep[m];
+    for (int m = tid; m < M; m += NT) sc.segrep[m] = srep[m];
     // (5) fusion per component: the candidates in the order (members by
     //     ascending id, then segments by ascending mask) keep the first one
     //     whose Q is the component's maximum (strict '>' while scanning):
@@ -625,32 +686,32 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
     int* obs = best_src;                                             // [nloc] observations
     unsigned long long* src_inst = (unsigned long long*)em;          // [nloc] (id << 32 | local) at the max
     int* src_seg = ek;                                               // [nloc] smallest mask at the max
-    for (int r = tid; r < nloc; r += UNION_THREADS) {
+    for (int r = tid; r < nloc; r += NT) {
         qmax[r] = 0u;
         obs[r] = 0;
         src_inst[r] = ~0ull;
         src_seg[r] = INT_MAX;
     }
     // the local root of each segment that joined a component
-    for (int m = tid; m < M; m += UNION_THREADS) snv[m] = anchor[m] != INT_MAX ? uf[anchor[m]] : -1;
+    for (int m = tid; m < M; m += NT) snv[m] = anchor[m] != INT_MAX ? uf[anchor[m]] : -1;
     __syncthreads();
-    for (int x = tid; x < nloc; x += UNION_THREADS) {
+    for (int x = tid; x < nloc; x += NT) {
         atomicMax(&qmax[uf[x]], f2key(qloc[x]));
         atomicAdd(&obs[uf[x]], oloc[x]);
     }
-    for (int m = tid; m < M; m += UNION_THREADS)
+    for (int m = tid; m < M; m += NT)
         if (snv[m] >= 0) {
             atomicMax(&qmax[snv[m]], f2key(sq[m]));
             atomicAdd(&obs[snv[m]], 1);
         }
     __syncthreads();
-    for (int x = tid; x < nloc; x += UNION_THREADS)
+    for (int x = tid; x < nloc; x += NT)
         if (qloc[x] == key2f(qmax[uf[x]]))
             atomicMin(&src_inst[uf[x]], ((unsigned long long)(unsigned)gid[x] << 32) | (unsigned)x);
-    for (int m = tid; m < M; m += UNION_THREADS)
+    for (int m = tid; m < M; m += NT)
         if (snv[m] >= 0 && sq[m] == key2f(qmax[snv[m]])) atomicMin(&src_seg[snv[m]], m);
     __syncthreads();
-    for (int r = tid; r < nloc; r += UNION_THREADS) {
+    for (int r = tid; r < nloc; r += NT) {
         if (uf[r] != r) continue;
         const int rep = gid[r];
         inst.n_obs[rep] = obs[r];
@@ -671,7 +732,7 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
         inst.Q[rep] = q;
     }
     // (6) merge members into their representative
-    for (int x = tid; x < nloc; x += UNION_THREADS) {
+    for (int x = tid; x < nloc; x += NT) {
         const int r = uf[x];
         if (r == x) continue;
         const int k = gid[x], rep = gid[r];
@@ -689,7 +750,18 @@ __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const Seri
         ctr->merges = s_merges;
         ctr->n_edges = nedge;
         ctr->next_id = s_next;
+        ctr->n_copies = s_ncopy;
     }
+}
+
+// The frame's pairs in the map's global pair hash, its edges in ss.edge_m/k.
+__device__ void phase_union(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
+                            int* next_id, unsigned char* union_smem)
+{
+    const int npairs = sc.ctr->n_pairs;
+    const int nedge = min(*ss.edge_n, ss.edge_cap);
+    union_frame(fp, sc, ss, inst, next_id, union_smem, UHASH, npairs, nedge, false,
+                [&](int i) { return (unsigned)(ss.okeys[ss.olist[i]] & 0xffffffffu); });
 }
 
 // One warp copies an embedding row (and writes its bf16 copy when tb is set).
@@ -863,7 +935,8 @@ __global__ void k_score(const FrameParams* fps, BatchScratch bs, SerialStep st)
     const MapRefs& R = st.refs[blockIdx.y];
     const SerialScratch ss = R.ss;
     const Instances inst = R.inst;
-    phase_score(fps[slot], bs.frame(slot), st.view.frame(slot), ss, inst);
+    phase_score(fps[slot], bs.frame(slot), st.view.frame(slot), ss, inst, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                (gridDim.x * blockDim.x) >> 5);
 }
 
 __global__ void __launch_bounds__(UNION_THREADS, 1) k_union(const FrameParams* fps, BatchScratch bs, SerialStep st)
@@ -896,6 +969,608 @@ __global__ void k_serial_begin(const MapRefs* refs, int G)
     if (g < G) {
         *refs[g].ss.edge_n = 0;
         *refs[g].ss.copy_n = 0;
+    }
+}
+
+// ==== The frame chain as one pass per batch ==========================================
+// The overlap histogram of frame j (Sec. III-B) counts, per segment m and
+// instance root k, the segment's voxels whose label resolves to k in the map
+// as frame j finds it.  A voxel of frame j is either
+//   (a) in the map when the batch starts: its label is known before any frame
+//       of the batch runs, only its root may change as earlier frames merge;
+//   (b) absent then, and first seen in this batch by an earlier frame j0 of
+//       the same map: that frame inserts it with the instance its lowest
+//       segment m0 joins (Sec. III-B, reading O11), known once frame j0 is
+//       associated;
+//   (c) absent until frame j itself: a new voxel of frame j (no overlap),
+//       owned by its lowest segment.
+// So the per-voxel work of the whole batch runs before the frames run in
+// order: k_lookup probes every (segment, voxel) entry of every frame in the
+// map as it stands at the batch start and gathers each absent voxel's first
+// (frame, segment) of the batch in one batch-wide hash; k_absent sorts the
+// absent entries into (b) and (c).  Each frame is left with a few hundred
+// to a few thousand items, (m, label) and (m, j0, m0), with voxel counts.
+// k_associate then runs each map's frames in order in one CTA (overlap pairs
+// from the items, the gates, the union, fusion and the voxel counts), and
+// k_commit inserts the batch's new voxels with their first frame's labels and
+// flattens the parent tables.  A frame that fails inserts nothing, and the
+// frames after it in its map are blocked.
+
+constexpr unsigned long long KEY54 = (1ull << 54) - 1;
+
+// The warp's lanes with `want` set add one voxel each to overlap item `key`
+// of the frame: lanes with the same key add together (one atomic per
+// distinct key of the warp).  All 32 lanes call.
+__device__ __forceinline__ void add_item_warp(const Scratch& sc, unsigned long long key, bool want)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, want);
+    if (!want) return;
+    const unsigned grp = __match_any_sync(act, key);
+    if ((int)(threadIdx.x & 31) != __ffs(grp) - 1) return;
+    unsigned long long t = mix64(key) & sc.smask;
+    for (unsigned long long pr = 0;; pr++) {
+        const unsigned long long cur = sc.pkey[t];
+        if (cur == key) break;
+        if (cur == EMPTY_KEY) {
+            const unsigned long long prev = atomicCAS(&sc.pkey[t], EMPTY_KEY, key);
+            if (prev == EMPTY_KEY) {
+                sc.plist[atomicAdd(&sc.ctr->n_pre, 1)] = (int)t;
+                break;
+            }
+            if (prev == key) break;
+        }
+        t = (t + 1) & sc.smask;
+        if (pr > sc.smask) {
+            set_err(sc.ctr, DISC_ERR_TABLE_FULL);
+            return;
+        }
+    }
+    atomicAdd(&sc.pcnt[t], __popc(grp));
+}
+
+// Warp-aggregated append: each lane with `want` gets a distinct index from
+// the counter; all 32 lanes call.
+__device__ __forceinline__ int warp_append(int* counter, bool want)
+{
+    const unsigned b = __ballot_sync(0xffffffffu, want);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && b) base = atomicAdd(counter, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(b & ((1u << lane) - 1));
+}
+
+// Every entry of every frame slot of the batch (block row = slot): its label
+// in the map at the batch start (tag-0 item), or, when absent, its slot in
+// the batch's absent-voxel hash, where the least (frame position, segment)
+// containing it is kept.
+__global__ void __launch_bounds__(256) k_lookup(const FrameParams* fps, BatchScratch bs, const MapRefs* refs,
+                                               AbsentHash ah)
+{
+    const int f = blockIdx.y;
+    const FrameParams& fp = fps[f];
+    const Scratch sc = bs.frame(f);
+    const int ne = sc.ctr->n_entries;
+    if (fp.M <= 0 || sc.ctr->err) return;  // a failed frame's items are never read
+    const VoxelTable vt = refs[fp.map].vt;
+    const unsigned long long gtag = (unsigned long long)(fp.map + 1) << 54;
+    const int lane = threadIdx.x & 31;
+    int maxp = 0;
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ne; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + lane;
+        const bool valid = i < ne;
+        const unsigned long long hk = valid ? sc.sent[i] : 0ull;
+        const int m = (int)(hk >> 54);
+        const unsigned long long key = hk & KEY54;
+        int lab = -1, at = -1;
+        bool claimed = false;
+        if (valid) {
+            unsigned long long h = mix64(key) & vt.mask;
+            for (int pr = 0;; pr++) {
+                const unsigned long long kk = vt.keys[h];
+                if (kk == key) { lab = vt.labels[h]; break; }
+                if (kk == EMPTY_KEY) break;
+                h = (h + 1) & vt.mask;
+                if (pr > (int)vt.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
+                maxp = max(maxp, pr + 1);
+            }
+            if (lab < 0) {
+                const unsigned long long ak = gtag | key;
+                unsigned long long t = mix64(ak) & ah.mask;
+                for (unsigned long long pr = 0;; pr++) {
+                    const unsigned long long cur = ah.key[t];
+                    if (cur == ak) break;
+                    if (cur == 0ull) {
+                        const unsigned long long prev = atomicCAS(&ah.key[t], 0ull, ak);
+                        if (prev == 0ull) { claimed = true; break; }
+                        if (prev == ak) break;
+                    }
+                    t = (t + 1) & ah.mask;
+                    if (pr > ah.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); t = ~0ull; break; }
+                }
+                if (t != ~0ull) {
+                    atomicMin(&ah.val[t], (fp.jpos << 9) | m);
+                    at = (int)t;
+                }
+            }
+        }
+        add_item_warp(sc, ((unsigned long long)m << 33) | (unsigned)lab, valid && lab >= 0);
+        const int li = warp_append(ah.n, claimed);
+        if (claimed) ah.list[li] = at;
+        const int ai = warp_append(&sc.ctr->n_absent, at >= 0);
+        if (at >= 0) {
+            sc.aent[ai] = i;
+            sc.aslot[ai] = at;
+        }
+    }
+    const int pm = __reduce_max_sync(0xffffffffu, maxp);
+    if (lane == 0 && pm > 0) atomicMax(&sc.ctr->max_probe, pm);
+}
+
+// Every entry absent at the batch start, once the batch-wide hash holds each
+// voxel's first (frame position j0, segment m0): j0 before this frame makes a
+// tag-1 item (m, j0 << 9 | m0); j0 this frame makes a new voxel, counted for
+// its owner m0 once (by the entry of m0 itself).
+__global__ void __launch_bounds__(256) k_absent(const FrameParams* fps, BatchScratch bs, AbsentHash ah)
+{
+    __shared__ int s_new[MAX_MASKS];
+    const int f = blockIdx.y;
+    const FrameParams& fp = fps[f];
+    const Scratch sc = bs.frame(f);
+    const int na = sc.ctr->n_absent;
+    if (fp.M <= 0 || sc.ctr->err || (int)(blockIdx.x * blockDim.x) >= na) return;  // uniform per block
+    for (int m = threadIdx.x; m < fp.M; m += blockDim.x) s_new[m] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int a0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); a0 < na; a0 += gridDim.x * blockDim.x) {
+        const int a = a0 + lane;
+        const bool valid = a < na;
+        int m = 0, pv = 0;
+        if (valid) {
+            m = (int)(sc.sent[sc.aent[a]] >> 54);
+            pv = ah.val[sc.aslot[a]];
+        }
+        const int j0 = pv >> 9, m0 = pv & 511;
+        add_item_warp(sc, ((unsigned long long)m << 33) | (1ull << 32) | (unsigned)pv, valid && j0 < fp.jpos);
+        if (valid && j0 == fp.jpos && m0 == m) atomicAdd(&s_new[m - 1], 1);
+    }
+    __syncthreads();
+    int tot = 0;
+    for (int m = threadIdx.x; m < fp.M; m += blockDim.x)
+        if (s_new[m]) {
+            atomicAdd(&sc.newcnt[m], s_new[m]);
+            tot += s_new[m];
+        }
+    tot = warp_sum(tot);
+    if (lane == 0 && tot) atomicAdd(&sc.ctr->n_new, tot);
+}
+
+// root of instance id x (parent chains may be longer than one step between
+// the merges of a batch and its k_commit).  A parent is never above its
+// child (a merge hooks an instance under the component's smallest id), so a
+// chain ends within one step per merging frame of the batch; the step limit
+// only keeps a damaged table from looping.
+__device__ __forceinline__ int find_root(const int32_t* parent, int x)
+{
+    for (int it = 0; it < (1 << 16); it++) {
+        const int p = parent[x];
+        if (p == x) break;
+        x = p;
+    }
+    return x;
+}
+
+// one thread reads a counter word another thread of the launch may have
+// written by an atomic; every thread then takes the same branch
+__device__ __forceinline__ int block_read(const int32_t* w)
+{
+    __shared__ int s_v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_v = *(volatile const int32_t*)w;
+    __syncthreads();
+    const int v = s_v;
+    __syncthreads();
+    return v;
+}
+
+constexpr int ASSOC_THREADS = 512;
+constexpr int APH = 4096;      // slots of the leader CTA's pair hash (shared memory)
+constexpr int APH_MAX = 3072;  // pairs it takes (load <= 3/4); a frame with more uses the map's global pair hash
+constexpr int ASSOC_CLUSTER_MAX = 8;
+static_assert((size_t)APH * 16 + (size_t)(2 * APH) * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8 <=
+                  UNION_SMEM, "shared-memory layout of k_associate");
+
+// ---- distributed shared memory of a thread-block cluster (inline PTX) ------------
+// Addresses are 32-bit shared::cluster addresses: a CTA's own shared-memory
+// offset mapped to the CTA of the given rank (mapa).
+__device__ __forceinline__ unsigned dsm_map(const void* local, unsigned rank)
+{
+    unsigned out;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ unsigned long long dsm_cas64(unsigned a, unsigned long long cmp, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "r"(a), "l"(cmp), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int dsm_add(unsigned a, int v)
+{
+    int old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void dsm_red_add(unsigned a, int v)
+{
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long dsm_ld64(unsigned a)
+{
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int dsm_ld32(unsigned a)
+{
+    int v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsm_st32(unsigned a, int v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size()
+{
+    unsigned n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+// every thread of every CTA of the cluster; shared-memory and global writes
+// before it are visible to the cluster after it (release / acquire)
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// A cluster of C CTAs per map of the batch (C = cluster size, 1 to 8)
+// walks the map's frames in order.  The leader CTA (rank 0) holds the
+// frame's pair hash, edge list and union state in its shared memory; the
+// other CTAs reach them through distributed shared memory.  Per frame:
+//   (1) every CTA resolves a share of the frame's items to (segment, root)
+//       pairs and counts them in the leader's pair hash;
+//   (2) every warp of the cluster takes a share of the pairs: each lane the
+//       overlap gate of one pair, then the warp the cosine gates of its
+//       lanes' passing pairs; accepted edges go to the leader's edge list;
+//   (3) the leader alone: union, new ids, merges and fusion winners;
+//   (4) every warp a share of the embedding copies; the leader the voxel
+//       counts of the frame's new voxels;
+// with a cluster barrier between the steps.  A frame with more pairs than
+// the leader's hash takes (APH_MAX) runs steps (1)-(3) on the leader alone
+// with the map's global pair hash.  Every branch that skips a cluster
+// barrier is taken by the whole cluster (its condition is read from the
+// leader after a barrier), so every CTA passes the same barriers.
+__global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParams* fps, BatchScratch bs,
+                                                                SerialStep st)
+{
+    extern __shared__ __align__(16) unsigned char union_smem[];
+    __shared__ int s_slot, s_blocked, s_np, s_ovf, s_ne, s_merged, s_err, s_nc;
+    const unsigned rank = cluster_rank(), C = cluster_size();
+    const bool leader = rank == 0;
+    const int g = blockIdx.x / C;
+    const MapRefs& R = st.refs[g];
+    const int tid = threadIdx.x, lane = tid & 31, NT = blockDim.x;
+    const int ct = (int)rank * NT + tid, CT = (int)C * NT;               // thread within the cluster
+    const int cw = (int)rank * (NT >> 5) + (tid >> 5), CW = (int)C * (NT >> 5);  // warp within the cluster
+    // the leader's step (1)-(3) state, laid out as in its union_smem:
+    // pair hash, then the union's region (root hash of 2 * APH slots,
+    // per-root arrays, edges)
+    unsigned long long* pk = (unsigned long long*)union_smem;  // [APH] (segment + 1) << 32 | root
+    int* pc = (int*)(pk + APH);                                 // [APH] voxels of the pair
+    int* pl = pc + APH;                                         // [APH] used slots
+    unsigned char* ureg = union_smem + (size_t)APH * 16;
+    int* em = (int*)(ureg + (size_t)(2 * APH) * 8 + (size_t)EDGE_ROOT_CAP * 24);
+    int* ek = em + EDGE_CAP;
+    const unsigned r_pk = dsm_map(pk, 0), r_pc = dsm_map(pc, 0), r_pl = dsm_map(pl, 0);
+    const unsigned r_em = dsm_map(em, 0), r_ek = dsm_map(ek, 0);
+    const unsigned r_slot = dsm_map(&s_slot, 0), r_blocked = dsm_map(&s_blocked, 0), r_np = dsm_map(&s_np, 0);
+    const unsigned r_ovf = dsm_map(&s_ovf, 0), r_ne = dsm_map(&s_ne, 0);
+    const unsigned r_err = dsm_map(&s_err, 0), r_nc = dsm_map(&s_nc, 0);
+    int2* cl = (int2*)union_smem;  // the frame's embedding copies (src, dst), staged over the pair hash
+    const unsigned r_cl = dsm_map(cl, 0);
+    if (leader && tid == 0) {
+        *R.ss.edge_n = 0;
+        *R.ss.copy_n = 0;
+        s_merged = 0;
+    }
+    for (int j = 0; j < st.J; j++) {
+        cluster_sync();  // the previous frame is done everywhere
+        if (leader) {
+            if (tid == 0) {
+                const int slot = st.slot_of[g * st.J + j];
+                int blocked = 0;
+                if (slot >= 0) {
+                    FrameCounters* c = bs.frame(slot).ctr;
+                    int prev = 0;
+                    if (j > 0) {
+                        const int ps = st.slot_of[g * st.J + j - 1];
+                        prev = ps >= 0 ? *(volatile int32_t*)&bs.frame(ps).ctr->err : 0;
+                    } else if (st.prev_hist[g] >= 0) {
+                        prev = st.hist[st.prev_hist[g]].err;
+                    }
+                    const int own = *(volatile int32_t*)&c->err;
+                    if (!own && prev) set_err(c, prev);
+                    blocked = own || prev;
+                }
+                s_slot = slot;
+                s_blocked = blocked;
+                s_np = 0;
+                s_ovf = 0;
+                s_ne = 0;
+            }
+            for (int i = tid; i < APH; i += NT) {
+                pk[i] = EMPTY_KEY;
+                pc[i] = 0;
+            }
+        }
+        cluster_sync();
+        const int slot = dsm_ld32(r_slot);
+        const bool blocked = dsm_ld32(r_blocked) != 0;
+        if (slot < 0) break;  // the whole cluster
+        const FrameParams& fp = fps[slot];
+        const Scratch sc = bs.frame(slot);
+        const int npre = sc.ctr->n_pre;
+        bool global_pairs = false;
+        if (!blocked) {
+            // (1) overlap pairs: each item's label resolved to its root now
+            //     (four items per thread in flight)
+            for (int i0 = ct; i0 < npre; i0 += 4 * CT) {
+                unsigned long long key[4];
+                int cnt[4], lab[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int i = i0 + u * CT;
+                    key[u] = EMPTY_KEY;
+                    cnt[u] = 0;
+                    if (i < npre) {
+                        const int ps = sc.plist[i];
+                        key[u] = sc.pkey[ps];
+                        cnt[u] = sc.pcnt[ps];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const unsigned x = (unsigned)key[u];
+                    lab[u] = -1;
+                    if (key[u] != EMPTY_KEY)
+                        lab[u] = ((key[u] >> 32) & 1ull)
+                                     ? bs.frame(st.slot_of[g * st.J + (int)(x >> 9)]).segrep[(x & 511u) - 1]
+                                     : (int)x;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (lab[u] < 0) continue;
+                    const unsigned long long okey = ((key[u] >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab[u]);
+                    unsigned h = (unsigned)(mix64(okey) & (APH - 1));
+                    for (int pr = 0;; pr++) {
+                        const unsigned long long cur = dsm_ld64(r_pk + 8u * h);
+                        if (cur == okey) break;
+                        if (cur == EMPTY_KEY) {
+                            const unsigned long long prev = dsm_cas64(r_pk + 8u * h, EMPTY_KEY, okey);
+                            if (prev == EMPTY_KEY) {
+                                const int at = dsm_add(r_np, 1);
+                                if (at < APH_MAX) dsm_st32(r_pl + 4u * at, (int)h);
+                                else dsm_st32(r_ovf, 1);
+                                break;
+                            }
+                            if (prev == okey) break;
+                        }
+                        h = (h + 1) & (APH - 1);
+                        if (pr >= APH) {
+                            dsm_st32(r_ovf, 1);
+                            break;
+                        }
+                    }
+                    dsm_red_add(r_pc + 4u * h, cnt[u]);
+                }
+            }
+            cluster_sync();
+            global_pairs = dsm_ld32(r_ovf) != 0;  // the whole cluster
+            if (global_pairs) {
+                // more pairs than the leader's hash takes: the leader alone,
+                // with the map's global pair hash, gates and union
+                if (leader) {
+                    for (int i = tid; i < npre; i += NT) {
+                        const int ps = sc.plist[i];
+                        const unsigned long long key = sc.pkey[ps];
+                        const unsigned x = (unsigned)key;
+                        const int lab = ((key >> 32) & 1ull)
+                                            ? bs.frame(st.slot_of[g * st.J + (int)(x >> 9)]).segrep[(x & 511u) - 1]
+                                            : (int)x;
+                        if (lab >= 0)
+                            add_pair(sc, R.ss, ((key >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab),
+                                     sc.pcnt[ps]);
+                    }
+                    if (!block_read(&sc.ctr->err))
+                        phase_score(fp, sc, st.view.frame(slot), R.ss, R.inst, tid >> 5, NT >> 5);
+                    if (!block_read(&sc.ctr->err)) phase_union(fp, sc, R.ss, R.inst, R.next_id, union_smem);
+                }
+            } else {
+                const int np = dsm_ld32(r_np);
+                if (leader && tid == 0) sc.ctr->n_pairs = np;
+                // (2) gates: each lane checks the overlap gate of one pair
+                //     (pairs dealt round robin over the cluster's warps), then
+                //     the warp takes the cosine gate of its passing pairs
+                const GateFeatures gf = gate_features(fp, sc, st.view.frame(slot), R.inst);
+                int border = 0, scored = 0;
+                for (int r0 = 0; r0 < np; r0 += CT) {
+                    const int i = r0 + lane * CW + cw;
+                    int m = 0, k = 0;
+                    bool pass = false;
+                    if (i < np) {
+                        const unsigned h = (unsigned)dsm_ld32(r_pl + 4u * i);
+                        const unsigned long long okey = dsm_ld64(r_pk + 8u * h);
+                        const long long ov = dsm_ld32(r_pc + 4u * h);
+                        m = (int)(okey >> 32) - 1;
+                        k = (int)(okey & 0xffffffffu);
+                        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
+                        const long long denom = min((long long)sc.nvox[m], R.inst.count[k]);
+                        pass = ov * (long long)fp.ov_den >= (long long)fp.ov_num * denom;
+                    }
+                    unsigned todo = __ballot_sync(0xffffffffu, pass);
+                    scored += __popc(todo);
+                    while (todo) {
+                        const int l = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int mm = __shfl_sync(0xffffffffu, m, l), kk = __shfl_sync(0xffffffffu, k, l);
+                        if (warp_cosine_gate(fp, gf, R.inst, mm, kk, &border) && lane == 0) {
+                            const int e = dsm_add(r_ne, 1);
+                            if (e < EDGE_CAP) {
+                                dsm_st32(r_em + 4u * e, mm);
+                                dsm_st32(r_ek + 4u * e, kk);
+                            } else {
+                                set_err(sc.ctr, DISC_ERR_CAPACITY);
+                            }
+                        }
+                    }
+                }
+                if (lane == 0 && border) atomicAdd(&sc.ctr->borderline, border);
+                if (lane == 0 && scored) atomicAdd(&sc.ctr->n_scored, scored);
+                cluster_sync();
+                // (3) union, new ids, merges, fusion winners: the leader
+                if (leader && !block_read(&sc.ctr->err))
+                    union_frame(fp, sc, R.ss, R.inst, R.next_id, ureg, 2 * APH, np, min(s_ne, EDGE_CAP), true,
+                                [&](int i) { return (unsigned)(pk[pl[i]] & 0xffffffffu); });
+            }
+            // the leader stages the frame's status and embedding copies for
+            // the cluster (the pair hash is no longer needed)
+            if (leader) {
+                __syncthreads();
+                const int err = *(volatile int32_t*)&sc.ctr->err;
+                const int nc = err ? 0 : min(*(volatile int32_t*)R.ss.copy_n, (int)(APH * 2));
+                for (int c = tid; c < nc; c += NT) cl[c] = make_int2(R.ss.copy_src[c], R.ss.copy_dst[c]);
+                if (tid == 0) {
+                    s_err = err;
+                    s_nc = nc;
+                }
+            }
+            cluster_sync();
+            // (4) the winners' embeddings (every warp of the cluster) and the
+            //     new voxels' counts (the leader)
+            if (!dsm_ld32(r_err)) {
+                const int D = fp.D;
+                const int nc = dsm_ld32(r_nc);
+                for (int c = cw; c < nc; c += CW) {
+                    const int src = dsm_ld32(r_cl + 8u * c), dst = dsm_ld32(r_cl + 8u * c + 4u);
+                    const Instances& inst = R.inst;
+                    const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
+                    if (inst.A) {
+                        const Scratch va = st.view.frame(slot);
+                        const int Da = inst.Da;
+                        const float* fa = src >= 0 ? inst.A + (size_t)src * Da : va.Ecan + (size_t)(-src - 1) * Da;
+                        copy_row(from, inst.E + (size_t)dst * D, nullptr, D, lane);
+                        copy_row(fa, inst.A + (size_t)dst * Da, inst.Eb ? inst.Eb + (size_t)dst * Da : nullptr, Da,
+                                 lane);
+                        if (inst.E8) e4m3_copy_row(fa, Da, inst.E8 + (size_t)dst * Da, inst.Er + dst);
+                    } else {
+                        copy_row(from, inst.E + (size_t)dst * D, inst.Eb ? inst.Eb + (size_t)dst * D : nullptr, D,
+                                 lane);
+                        if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)dst * D, inst.Er + dst);
+                    }
+                }
+                if (leader) {
+                    for (int m = tid; m < fp.M; m += NT) {
+                        const int n = sc.newcnt[m], rep = sc.segrep[m];
+                        if (n && rep >= 0) atomicAdd((unsigned long long*)&R.inst.count[rep], (unsigned long long)n);
+                    }
+                    if (tid == 0 && sc.ctr->merges > 0) s_merged = 1;
+                }
+            }
+        }
+        // empty the frame's item hash (and the global pair hash, if used)
+        if (global_pairs && leader) {
+            __syncthreads();
+            const int np = *(volatile int32_t*)&sc.ctr->n_pairs;
+            for (int i = tid; i < np; i += NT) {
+                const int t = R.ss.olist[i];
+                R.ss.okeys[t] = EMPTY_KEY;
+                R.ss.ocnt[t] = 0;
+            }
+        }
+        for (int i = ct; i < npre; i += CT) {
+            const int t = sc.plist[i];
+            sc.pkey[t] = EMPTY_KEY;
+            sc.pcnt[t] = 0;
+        }
+        if (leader && tid == 0) {
+            *R.ss.edge_n = 0;
+            *R.ss.copy_n = 0;
+        }
+    }
+    // no CTA leaves while another may still reach its shared memory
+    cluster_sync();
+    if (leader && tid == 0) st.merged[g] = s_merged;
+}
+
+// After the batch's frames: every voxel of the absent-voxel hash whose first
+// frame succeeded goes into its map with the instance that frame's lowest
+// segment joined; the hash is emptied on the way.  Then the parent table of
+// every map whose frames merged is flattened (each id to its root).
+__global__ void k_commit(BatchScratch bs, SerialStep st, AbsentHash ah, int G)
+{
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int n = *ah.n;
+    for (int i0 = gtid & ~31; i0 < n; i0 += gsz) {
+        const int i = i0 + lane;
+        int g = -1, lab = -1;
+        unsigned long long key = 0;
+        if (i < n) {
+            const int t = ah.list[i];
+            const unsigned long long ak = ah.key[t];
+            const int pv = ah.val[t];
+            ah.key[t] = 0ull;
+            ah.val[t] = INT_MAX;
+            g = (int)(ak >> 54) - 1;
+            key = ak & KEY54;
+            const int slot = st.slot_of[g * st.J + (pv >> 9)];
+            const Scratch sc = bs.frame(slot);
+            if (sc.ctr->err == 0) lab = sc.segrep[(pv & 511) - 1];
+        }
+        const bool ins = lab >= 0;
+        if (ins) {
+            const VoxelTable vt = st.refs[g].vt;
+            unsigned long long h = mix64(key) & vt.mask;
+            for (unsigned long long pr = 0;; pr++) {
+                const unsigned long long prev = atomicCAS(&vt.keys[h], EMPTY_KEY, key);
+                if (prev == EMPTY_KEY) {
+                    vt.labels[h] = lab;
+                    break;
+                }
+                h = (h + 1) & vt.mask;
+                if (pr > vt.mask) break;  // not reached: the batch's room was checked before it ran
+            }
+        }
+        // one count update per map of the warp
+        const unsigned act = __ballot_sync(0xffffffffu, ins);
+        if (ins) {
+            const unsigned grp = __match_any_sync(act, g);
+            if (lane == __ffs(grp) - 1) atomicAdd(st.refs[g].vt.used, (unsigned long long)__popc(grp));
+        }
+    }
+    for (int g = 0; g < G; g++) {
+        if (!st.merged[g]) continue;
+        const Instances inst = st.refs[g].inst;
+        const int nid = *st.refs[g].next_id;
+        for (int i = gtid; i < nid; i += gsz) inst.parent[i] = find_root(inst.parent, i);
     }
 }
 
@@ -974,9 +1649,83 @@ int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const Ser
     }
 }
 
+int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, const AbsentHash& ah, int S,
+                  cudaStream_t st)
+{
+    k_lookup<<<dim3(152, S), 256, 0, st>>>(fps, bs, refs, ah);
+    k_absent<<<dim3(38, S), 256, 0, st>>>(fps, bs, ah);
+    return 2;
+}
+
+// CTAs per map: a cluster of up to 8 when the maps leave SMs free (152 SMs,
+// one CTA each); checked once against what the device can co-schedule.
+static int g_assoc_max_cluster = -1;  // set once by set_serial_kernel_attrs
+
+static void probe_assoc_cluster()
+{
+    if (g_assoc_max_cluster < 0) {
+        int& max_c = g_assoc_max_cluster;
+        max_c = 1;
+        for (int c = ASSOC_CLUSTER_MAX; c > 1; c >>= 1) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(c);
+            cfg.blockDim = dim3(ASSOC_THREADS);
+            cfg.dynamicSmemBytes = UNION_SMEM;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, k_associate, &cfg) == cudaSuccess && n > 0) {
+                max_c = c;
+                break;
+            }
+            cudaGetLastError();
+        }
+    }
+}
+
+static int assoc_cluster(int G)
+{
+    int c = 1;
+    while (c * 2 <= g_assoc_max_cluster && (c * 2) * G <= 152) c *= 2;
+    return c;
+}
+
+int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s)
+{
+    const int c = assoc_cluster(G);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(G * c);
+    cfg.blockDim = dim3(ASSOC_THREADS);
+    cfg.dynamicSmemBytes = UNION_SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_associate, fps, bs, st);
+    return 1;
+}
+
+int launch_commit(const BatchScratch& bs, const SerialStep& st, const AbsentHash& ah, int G, cudaStream_t s)
+{
+    k_commit<<<152 * 2, 512, 0, s>>>(bs, st, ah, G);
+    return 1;
+}
+
 cudaError_t set_serial_kernel_attrs()
 {
     cudaError_t e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_associate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+    if (e == cudaSuccess) probe_assoc_cluster();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OV_SMEM);
     return e;
 }

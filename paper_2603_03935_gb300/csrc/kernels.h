@@ -31,6 +31,9 @@ enum Phase {
     PH_SCORE,         // per frame: geometry and cosine gates
     PH_UNION,         // per frame: union, new ids, merges, fusion (one CTA)
     PH_APPLY,         // per frame: embeddings, new voxels, parent flattening
+    PH_LOOKUP,        // every entry of the batch: label at the batch start, or first frame of the batch
+    PH_ASSOCIATE,     // one CTA per map: its frames in order (pairs, gates, union, fusion, counts)
+    PH_COMMIT,        // the batch's new voxels into the maps, parent tables flattened
     PH_COUNT
 };
 
@@ -52,7 +55,7 @@ int launch_backproject(const FrameParams* fps, const BatchScratch& bs, int f0, i
 // DBSCAN noise flags of frames [f0, f0 + nb) (frames without DBSCAN return at once)
 int launch_dbscan(const FrameParams* fps, const BatchScratch& bs, int f0, int nb, int H, int W, cudaStream_t st);
 int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, int f0, int nb, int Mmax,
-                   cudaStream_t st);
+                   bool lookup, cudaStream_t st);
 int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);
 // default frames per back-projection/entries/DBSCAN launch (their per-frame
 // hashes stay in L2); the runner's tuning may pick another
@@ -67,6 +70,16 @@ int launch_serial_begin(const MapRefs* refs, int G, cudaStream_t st);
 // 1 score, 2 union, 3 apply
 int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int phase,
                        cudaStream_t stream);
+
+// The frame chain as one pass per batch (k_serial.cu): lookup of every entry
+// of the batch's S slots in the maps as they stand (k_lookup, then k_absent);
+// each of the G maps' frames in order in one CTA (k_associate); the batch's
+// new voxels into the maps (k_commit).  The absent-voxel hash is empty
+// before k_lookup and after k_commit.
+int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, const AbsentHash& ah, int S,
+                  cudaStream_t st);
+int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s);
+int launch_commit(const BatchScratch& bs, const SerialStep& st, const AbsentHash& ah, int G, cudaStream_t s);
 
 size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);

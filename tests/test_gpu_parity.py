@@ -92,6 +92,33 @@ def test_host_inputs_in_batches_split_in_halves(torch_dev, batch):
     common.compare_maps(gmap, omap, ctx=f"host frames, batches of {batch} in halves")
 
 
+def test_host_input_halves_of_different_bases(torch_dev):
+    # calls of 16 and then 15 host frames: both split their batch in two
+    # halves whose second half has 8 frames, starting at slot 8 and at slot 7;
+    # each must replay its own captured launch sequence
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, host_frame
+    sc = synth.tiny_scene(num_frames=100)
+    sizes = [16, 16, 16, 16, 15, 15]
+    fr = sc.render(range(sum(sizes)))
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    frames = [host_frame(fr.depth[i], fr.labels[i], fr.tokens[i], fr.poses[i], intr, fr.num_masks[i])
+              for i in range(sum(sizes))]
+    cfg = common.disc_cfg(sc, batch_frames=16)
+    gmap = DiscMap(**cfg)
+    omap = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+    lo = 0
+    for n in sizes:
+        stats, done, rc = gmap.integrate_frames(frames[lo:lo + n])
+        assert rc == 0 and done == n
+        for j in range(n):
+            o = omap.integrate(*oracle.frame_args(fr, lo + j), report=True)
+            for gk, ok in common.COUNT_FIELDS:
+                assert stats[j][gk] == o[ok], f"frame {lo + j} {gk}: {stats[j][gk]} vs {o[ok]}"
+        lo += n
+    common.compare_maps(gmap, omap, ctx="host-input halves of different bases")
+
+
 def test_host_inputs_in_one_call_of_many_batches(torch_dev):
     # a whole trajectory from pinned host memory in one call: frames lie back
     # to back, so each batch's copies merge into one per input kind and run

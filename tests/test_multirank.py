@@ -86,19 +86,29 @@ def test_reference_arm_prints_one_contract_line(monkeypatch):
 
 
 def test_roofline_byte_model_of_the_dominant_kernel():
-    # the numerator of the benchmark's roofline: per frame, depth (fp32) and
-    # labels (u16) once, plus 44 B per unique (segment, voxel) pair (a 32 B
-    # segment slot, an 8 B entry key and a 4 B entry slot); summed over the
-    # frames of the timed batch.  Phases without a byte model report 0.
+    # the numerator of the benchmark's rooflines: per frame, depth (fp32) and
+    # labels (u16) once, the token grid once, 12 B per unique (segment, voxel)
+    # probe, 12 B per new voxel, one instance embedding per scored pair and
+    # one fp32 embedding per adopted segment; each phase is credited with its
+    # part; scratch (hash slots, lists) is not counted
     import bench
-    H, W, P, D, Kpad = 480, 640, 576, 768, 576
-    sts = [{"unique_seg_voxels": 20000, "new_voxels": 7000, "overlap_pairs": 30, "new_instances": 2,
-            "merges": 1}, {"unique_seg_voxels": 18000, "new_voxels": 6000, "overlap_pairs": 25,
-                           "new_instances": 0, "merges": 0}]
-    Ms = [40, 38]
-    assert bench.algorithmic_bytes("backproject", sts, H, W, P, D, Ms, Kpad) == \
-        2 * 6 * H * W + 44 * (20000 + 18000)
-    assert bench.algorithmic_bytes("token_stats", sts, H, W, P, D, Ms, Kpad) == 2 * 4 * P * D
-    assert bench.algorithmic_bytes("pool_gemm", sts, H, W, P, D, Ms, Kpad) == \
-        sum(4 * P * D + 4 * M * Kpad + 4 * M * D for M in Ms)
-    assert bench.algorithmic_bytes("union", sts, H, W, P, D, Ms, Kpad) == 0.0
+    H, W, P, D = 480, 640, 576, 768
+    sts = [{"unique_seg_voxels": 20000, "new_voxels": 7000, "overlap_pairs": 30, "scored_pairs": 12,
+            "embedding_copies": 2},
+           {"unique_seg_voxels": 18000, "new_voxels": 6000, "overlap_pairs": 25, "scored_pairs": 9,
+            "embedding_copies": 0}]
+    assert bench.algorithmic_bytes("backproject", sts, H, W, P, D) == 2 * 6 * H * W
+    assert bench.algorithmic_bytes("token_stats", sts, H, W, P, D) == 2 * 4 * P * D
+    assert bench.algorithmic_bytes("pool_gemm", sts, H, W, P, D, tok_b=2) == 2 * 2 * P * D
+    assert bench.algorithmic_bytes("lookup", sts, H, W, P, D) == 12 * (20000 + 18000)
+    assert bench.algorithmic_bytes("associate", sts, H, W, P, D, emb_b=1) == D * (12 + 9) + 4 * D * 2
+    assert bench.algorithmic_bytes("commit", sts, H, W, P, D) == 12 * (7000 + 6000)
+    assert bench.algorithmic_bytes("entries", sts, H, W, P, D) == 0.0
+    assert bench.algorithmic_bytes("entries", sts, H, W, P, D, lookup_in_entries=True) == 12 * (20000 + 18000)
+    assert bench.algorithmic_bytes("union", sts, H, W, P, D) == 0.0
+    # the step: the sum of the parts, each datum once
+    total = bench.step_bytes(sts[0], H, W, P, D)
+    assert total == 6 * H * W + 4 * P * D + 12 * 20000 + 12 * 7000 + 4 * D * 12 + 4 * D * 2
+    parts = sum(bench.algorithmic_bytes(ph, sts[:1], H, W, P, D)
+                for ph in ("backproject", "token_stats", "lookup", "associate", "commit"))
+    assert parts == total
