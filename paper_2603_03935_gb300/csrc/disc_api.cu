@@ -1797,6 +1797,7 @@ disc_status disc_map_create(const disc_map_config* cfg, disc_map_config* resolve
     ss.copy_dst = a.get<int32_t>(ss.copy_cap);
     ss.copy_src = a.get<int32_t>(ss.copy_cap);
     ss.copy_n = a.get<int32_t>(1);
+    ss.ureg = a.get<unsigned char>(union_region_bytes_full());
     disc_status st = DISC_OK;
     if (a.failed) st = DISC_ERR_OOM;
     if (st == DISC_OK) {

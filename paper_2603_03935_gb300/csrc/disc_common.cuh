@@ -304,6 +304,7 @@ struct SerialScratch {
     int32_t* copy_src;          // >= 0 instance id, < 0: segment -(m+1)
     int32_t* copy_n;            // [1]
     int32_t copy_cap;
+    unsigned char* ureg;        // a union region of the full capacities (frames past the shared ones)
 };
 
 // Everything the kernels need of one map's resident state.  A batch holds an

@@ -480,6 +480,7 @@ constexpr unsigned UH_EMPTY = 0xffffffffu;
 constexpr unsigned UH_UNUSED = 0xffffffffu;
 constexpr unsigned UH_LOCAL = 0x80000000u;
 constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8;
+static_assert(UNION_SMEM == (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8, "union layout");
 
 __device__ __forceinline__ unsigned uhash(unsigned k, unsigned mask) { return (unsigned)(mix64(k) & mask); }
 
@@ -510,26 +511,36 @@ __device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hv
     return (int)(hval[h] & ~UH_LOCAL);
 }
 
+// Bytes of a union region with the given capacities (layout below).
+__host__ __device__ constexpr size_t union_region_bytes(unsigned uhash_cap, int root_cap, int edge_cap)
+{
+    return (size_t)uhash_cap * 8 + (size_t)root_cap * 24 + (size_t)edge_cap * 8;
+}
+
 // The frame's npairs overlap pairs give their roots through pair_root(i);
 // its nedge accepted edges are in ss.edge_m/k, or (edges_in_place) already in
-// the block's em/ek arrays.  uhash_cap: the root hash's slots in union_smem
-// (>= 2 * npairs); the layout is hkey, hval [uhash_cap], the per-root arrays
-// [EDGE_ROOT_CAP], em, ek [EDGE_CAP].
+// the region's em/ek arrays.  The region (shared memory, or global memory
+// for frames beyond the shared capacities) holds hkey, hval [uhash_cap >=
+// 2 * npairs], the per-root arrays [root_cap], em, ek [edge_cap >= 2 *
+// root_cap... at least root_cap * 2 ints for the fusion step].  Past a
+// capacity the frame fails with DISC_ERR_CAPACITY, or, soft, the call
+// returns false before anything outside the region changed (the caller then
+// retries with larger capacities); otherwise it returns true.
 template <class PairRoot>
-__device__ void union_frame(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
-                            int* next_id, unsigned char* union_smem, unsigned uhash_cap, int npairs, int nedge,
-                            bool edges_in_place, PairRoot pair_root)
+__device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
+                            int* next_id, unsigned char* union_smem, unsigned uhash_cap, int root_cap, int edge_cap,
+                            bool soft, int npairs, int nedge, bool edges_in_place, PairRoot pair_root)
 {
     unsigned* hkey = (unsigned*)union_smem;           // [uhash_cap] root id
     unsigned* hval = hkey + uhash_cap;                // [uhash_cap] claimant edge, then UH_LOCAL | local index
-    int* gid = (int*)(hval + uhash_cap);              // [EDGE_ROOT_CAP] local -> instance id
-    int* uf = gid + EDGE_ROOT_CAP;                    // union-find over local indices
-    int* best_src = uf + EDGE_ROOT_CAP;               // fusion winner per component
-    float* best_q = (float*)(best_src + EDGE_ROOT_CAP);
-    float* qloc = best_q + EDGE_ROOT_CAP;             // Q of the local roots
-    int* oloc = (int*)(qloc + EDGE_ROOT_CAP);         // observations of the local roots
-    int* em = oloc + EDGE_ROOT_CAP;                   // [EDGE_CAP] edge segment
-    int* ek = em + EDGE_CAP;                          // [EDGE_CAP] edge instance id
+    int* gid = (int*)(hval + uhash_cap);              // [root_cap] local -> instance id
+    int* uf = gid + root_cap;                         // union-find over local indices
+    int* best_src = uf + root_cap;                    // fusion winner per component
+    float* best_q = (float*)(best_src + root_cap);
+    float* qloc = best_q + root_cap;                  // Q of the local roots
+    int* oloc = (int*)(qloc + root_cap);              // observations of the local roots
+    int* em = oloc + root_cap;                        // [edge_cap] edge segment
+    int* ek = em + edge_cap;                          // [edge_cap] edge instance id
     __shared__ int anchor[MAX_MASKS];                 // smallest local root of a segment's edges
     __shared__ int srep[MAX_MASKS];
     __shared__ int snv[MAX_MASKS];
@@ -538,9 +549,10 @@ __device__ void union_frame(const FrameParams& fp, const Scratch& sc, const Seri
     const int tid = threadIdx.x, NT = blockDim.x;
     FrameCounters* ctr = sc.ctr;
     const int M = fp.M;
-    if (2u * (unsigned)npairs > uhash_cap || nedge > EDGE_CAP) {
+    if (2u * (unsigned)npairs > uhash_cap || nedge > edge_cap) {
+        if (soft) return false;
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
-        return;
+        return true;
     }
     unsigned hsize = 64;
     while (hsize < 2u * (unsigned)npairs) hsize <<= 1;
@@ -599,7 +611,7 @@ __device__ void union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         while (hkey[h] != k) h = (h + 1) & hm;
         if (hval[h] == (unsigned)e) {
             const int x = atomicAdd(&s_nloc, 1);
-            if (x < EDGE_ROOT_CAP) {
+            if (x < root_cap) {
                 gid[x] = (int)k;
                 uf[x] = x;
                 qloc[x] = inst.Q[k];
@@ -610,9 +622,10 @@ __device__ void union_frame(const FrameParams& fp, const Scratch& sc, const Seri
     }
     __syncthreads();
     const int nloc = s_nloc;
-    if (nloc > EDGE_ROOT_CAP) {
+    if (nloc > root_cap) {
+        if (soft) return false;
         if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
-        return;
+        return true;
     }
     // (3) union of the instances one segment joins: every edge hooks its
     //     root onto the segment's anchor; a hook always links the root with
@@ -673,7 +686,7 @@ __device__ void union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         }
     }
     __syncthreads();
-    if (ctr->err) return;
+    if (ctr->err) return true;
     for (int m = tid; m < M; m += NT) sc.segrep[m] = srep[m];
     // (5) fusion per component: the candidates in the order (members by
     //     ascending id, then segments by ascending mask) keep the first one
@@ -752,15 +765,17 @@ __device__ void union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         ctr->next_id = s_next;
         ctr->n_copies = s_ncopy;
     }
+    return true;
 }
 
-// The frame's pairs in the map's global pair hash, its edges in ss.edge_m/k.
+// The frame's pairs in the map's global pair hash, its edges in ss.edge_m/k;
+// union_smem: a region of UNION_SMEM bytes (shared or global memory).
 __device__ void phase_union(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
                             int* next_id, unsigned char* union_smem)
 {
     const int npairs = sc.ctr->n_pairs;
     const int nedge = min(*ss.edge_n, ss.edge_cap);
-    union_frame(fp, sc, ss, inst, next_id, union_smem, UHASH, npairs, nedge, false,
+    union_frame(fp, sc, ss, inst, next_id, union_smem, UHASH, EDGE_ROOT_CAP, EDGE_CAP, false, npairs, nedge, false,
                 [&](int i) { return (unsigned)(ss.okeys[ss.olist[i]] & 0xffffffffu); });
 }
 
@@ -1174,11 +1189,16 @@ __device__ __forceinline__ int block_read(const int32_t* w)
 }
 
 constexpr int ASSOC_THREADS = 512;
-constexpr int APH = 4096;      // slots of the leader CTA's pair hash (shared memory)
-constexpr int APH_MAX = 3072;  // pairs it takes (load <= 3/4); a frame with more uses the map's global pair hash
+constexpr int APH = 2048;         // slots of the leader CTA's pair hash (shared memory)
+constexpr int APH_MAX = 1536;     // pairs it takes (load <= 3/4)
+constexpr int ASSOC_ROOTS = 512;  // instances with an accepted edge, in shared memory
+constexpr int ASSOC_EDGES = 1024; // accepted edges, in shared memory
+// A frame past one of these shared capacities runs steps (1)-(3) on the
+// leader alone with the map's global pair hash and union region.  The small
+// footprint lets the CTAs share SMs with the next batch's stateless kernels.
+constexpr size_t ASSOC_SMEM = (size_t)APH * 16 + union_region_bytes(2 * APH, ASSOC_ROOTS, ASSOC_EDGES);
 constexpr int ASSOC_CLUSTER_MAX = 8;
-static_assert((size_t)APH * 16 + (size_t)(2 * APH) * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8 <=
-                  UNION_SMEM, "shared-memory layout of k_associate");
+static_assert(ASSOC_EDGES >= 2 * ASSOC_ROOTS, "the fusion step overlays the edge arrays");
 
 // ---- distributed shared memory of a thread-block cluster (inline PTX) ------------
 // Addresses are 32-bit shared::cluster addresses: a CTA's own shared-memory
@@ -1277,14 +1297,15 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
     int* pc = (int*)(pk + APH);                                 // [APH] voxels of the pair
     int* pl = pc + APH;                                         // [APH] used slots
     unsigned char* ureg = union_smem + (size_t)APH * 16;
-    int* em = (int*)(ureg + (size_t)(2 * APH) * 8 + (size_t)EDGE_ROOT_CAP * 24);
-    int* ek = em + EDGE_CAP;
+    int* em = (int*)(ureg + (size_t)(2 * APH) * 8 + (size_t)ASSOC_ROOTS * 24);
+    int* ek = em + ASSOC_EDGES;
     const unsigned r_pk = dsm_map(pk, 0), r_pc = dsm_map(pc, 0), r_pl = dsm_map(pl, 0);
     const unsigned r_em = dsm_map(em, 0), r_ek = dsm_map(ek, 0);
     const unsigned r_slot = dsm_map(&s_slot, 0), r_blocked = dsm_map(&s_blocked, 0), r_np = dsm_map(&s_np, 0);
     const unsigned r_ovf = dsm_map(&s_ovf, 0), r_ne = dsm_map(&s_ne, 0);
     const unsigned r_err = dsm_map(&s_err, 0), r_nc = dsm_map(&s_nc, 0);
     int2* cl = (int2*)union_smem;  // the frame's embedding copies (src, dst), staged over the pair hash
+    constexpr int CL_CAP = APH * 2;
     const unsigned r_cl = dsm_map(cl, 0);
     if (leader && tid == 0) {
         *R.ss.edge_n = 0;
@@ -1384,26 +1405,7 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
             }
             cluster_sync();
             global_pairs = dsm_ld32(r_ovf) != 0;  // the whole cluster
-            if (global_pairs) {
-                // more pairs than the leader's hash takes: the leader alone,
-                // with the map's global pair hash, gates and union
-                if (leader) {
-                    for (int i = tid; i < npre; i += NT) {
-                        const int ps = sc.plist[i];
-                        const unsigned long long key = sc.pkey[ps];
-                        const unsigned x = (unsigned)key;
-                        const int lab = ((key >> 32) & 1ull)
-                                            ? bs.frame(st.slot_of[g * st.J + (int)(x >> 9)]).segrep[(x & 511u) - 1]
-                                            : (int)x;
-                        if (lab >= 0)
-                            add_pair(sc, R.ss, ((key >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab),
-                                     sc.pcnt[ps]);
-                    }
-                    if (!block_read(&sc.ctr->err))
-                        phase_score(fp, sc, st.view.frame(slot), R.ss, R.inst, tid >> 5, NT >> 5);
-                    if (!block_read(&sc.ctr->err)) phase_union(fp, sc, R.ss, R.inst, R.next_id, union_smem);
-                }
-            } else {
+            if (!global_pairs) {
                 const int np = dsm_ld32(r_np);
                 if (leader && tid == 0) sc.ctr->n_pairs = np;
                 // (2) gates: each lane checks the overlap gate of one pair
@@ -1433,29 +1435,57 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
                         const int mm = __shfl_sync(0xffffffffu, m, l), kk = __shfl_sync(0xffffffffu, k, l);
                         if (warp_cosine_gate(fp, gf, R.inst, mm, kk, &border) && lane == 0) {
                             const int e = dsm_add(r_ne, 1);
-                            if (e < EDGE_CAP) {
+                            if (e < ASSOC_EDGES) {
                                 dsm_st32(r_em + 4u * e, mm);
                                 dsm_st32(r_ek + 4u * e, kk);
-                            } else {
-                                set_err(sc.ctr, DISC_ERR_CAPACITY);
-                            }
+                            }  // more edges than the shared list holds: the global path below
                         }
                     }
                 }
                 if (lane == 0 && border) atomicAdd(&sc.ctr->borderline, border);
                 if (lane == 0 && scored) atomicAdd(&sc.ctr->n_scored, scored);
                 cluster_sync();
-                // (3) union, new ids, merges, fusion winners: the leader
-                if (leader && !block_read(&sc.ctr->err))
-                    union_frame(fp, sc, R.ss, R.inst, R.next_id, ureg, 2 * APH, np, min(s_ne, EDGE_CAP), true,
-                                [&](int i) { return (unsigned)(pk[pl[i]] & 0xffffffffu); });
+                // (3) union, new ids, merges, fusion winners: the leader, in
+                //     its shared memory unless a shared capacity is exceeded
+                if (leader) {
+                    bool done = s_ne <= ASSOC_EDGES;
+                    if (done && !block_read(&sc.ctr->err))
+                        done = union_frame(fp, sc, R.ss, R.inst, R.next_id, ureg, 2 * APH, ASSOC_ROOTS, ASSOC_EDGES,
+                                           true, np, s_ne, true, [&](int i) { return (unsigned)(pk[pl[i]] & 0xffffffffu); });
+                    if (!done && tid == 0) {  // steps (1)-(3) again on global memory
+                        sc.ctr->n_pairs = 0;
+                        sc.ctr->n_scored = 0;
+                        sc.ctr->borderline = 0;
+                    }
+                    global_pairs = !done;  // uniform in the leader
+                }
+            }
+            if (leader && global_pairs) {
+                // more pairs, edges or edge roots than the leader's shared
+                // memory holds: the leader alone, with the map's global pair
+                // hash and union region
+                __syncthreads();
+                for (int i = tid; i < npre; i += NT) {
+                    const int ps = sc.plist[i];
+                    const unsigned long long key = sc.pkey[ps];
+                    const unsigned x = (unsigned)key;
+                    const int lab = ((key >> 32) & 1ull)
+                                        ? bs.frame(st.slot_of[g * st.J + (int)(x >> 9)]).segrep[(x & 511u) - 1]
+                                        : (int)x;
+                    if (lab >= 0)
+                        add_pair(sc, R.ss, ((key >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab),
+                                 sc.pcnt[ps]);
+                }
+                if (!block_read(&sc.ctr->err))
+                    phase_score(fp, sc, st.view.frame(slot), R.ss, R.inst, tid >> 5, NT >> 5);
+                if (!block_read(&sc.ctr->err)) phase_union(fp, sc, R.ss, R.inst, R.next_id, R.ss.ureg);
             }
             // the leader stages the frame's status and embedding copies for
             // the cluster (the pair hash is no longer needed)
             if (leader) {
                 __syncthreads();
                 const int err = *(volatile int32_t*)&sc.ctr->err;
-                const int nc = err ? 0 : min(*(volatile int32_t*)R.ss.copy_n, (int)(APH * 2));
+                const int nc = err ? 0 : min(*(volatile int32_t*)R.ss.copy_n, CL_CAP);
                 for (int c = tid; c < nc; c += NT) cl[c] = make_int2(R.ss.copy_src[c], R.ss.copy_dst[c]);
                 if (tid == 0) {
                     s_err = err;
@@ -1495,7 +1525,8 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
                 }
             }
         }
-        // empty the frame's item hash (and the global pair hash, if used)
+        // empty the frame's item hash (and the global pair hash, if the
+        // leader used it)
         if (global_pairs && leader) {
             __syncthreads();
             const int np = *(volatile int32_t*)&sc.ctr->n_pairs;
@@ -1675,7 +1706,7 @@ static void probe_assoc_cluster()
             at[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(c);
             cfg.blockDim = dim3(ASSOC_THREADS);
-            cfg.dynamicSmemBytes = UNION_SMEM;
+            cfg.dynamicSmemBytes = ASSOC_SMEM;
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int n = 0;
@@ -1695,6 +1726,8 @@ static int assoc_cluster(int G)
     return c;
 }
 
+size_t union_region_bytes_full() { return UNION_SMEM; }
+
 int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s)
 {
     const int c = assoc_cluster(G);
@@ -1706,7 +1739,7 @@ int launch_associate(const FrameParams* fps, const BatchScratch& bs, const Seria
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(G * c);
     cfg.blockDim = dim3(ASSOC_THREADS);
-    cfg.dynamicSmemBytes = UNION_SMEM;
+    cfg.dynamicSmemBytes = ASSOC_SMEM;
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -1724,7 +1757,7 @@ cudaError_t set_serial_kernel_attrs()
 {
     cudaError_t e = cudaFuncSetAttribute(k_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_associate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UNION_SMEM);
+        e = cudaFuncSetAttribute(k_associate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ASSOC_SMEM);
     if (e == cudaSuccess) probe_assoc_cluster();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OV_SMEM);
     return e;

@@ -80,6 +80,8 @@ int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs*
                   cudaStream_t st);
 int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s);
 int launch_commit(const BatchScratch& bs, const SerialStep& st, const AbsentHash& ah, int G, cudaStream_t s);
+// bytes of the union region a map keeps in global memory (SerialScratch::ureg)
+size_t union_region_bytes_full();
 
 size_t coverage_smem_bytes(int max_masks, int Pw);
 size_t gemm_smem_bytes(int NT);

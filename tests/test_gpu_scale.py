@@ -11,6 +11,10 @@
   trajectory, submitted from several client threads into one server; every
   frame's counters and each final map equal the oracle's, and each query
   returns the top-k of the oracle's instances at that point.
+* Past the shared capacities: checkpoints whose instances are cut into many
+  small pieces make a frame join more edge roots or overlap more pairs than
+  the association kernel keeps in shared memory; the frame takes the map's
+  global pair hash and union region, with the same result as the oracle.
 """
 import threading
 
@@ -171,3 +175,71 @@ def test_served_maps_equal_the_oracle(torch_dev):
                             assert qids[r][j] == oids[r][j], f"map {g} query {r} rank {j}"
         common.compare_maps(srv.map(ids[g]), om, ctx=f"served map {g}")
     srv.close()
+
+
+def _split_state(omap, S):
+    """The oracle map's voxels with each instance cut into up to S pieces by
+    a hash of the voxel key (every piece its own instance with the parent's
+    embedding and Q): (keys, labels, parent, count, Q, E, n_obs)."""
+    keys, ids = omap.voxels()
+    inst = omap.instances()
+    h = (keys * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(40)
+    new = ids.astype(np.int64) * S + (h % np.uint64(S)).astype(np.int64)
+    uniq, inv = np.unique(new, return_inverse=True)
+    nid = len(uniq)
+    old = (uniq // S).astype(np.int64)
+    labels = inv.astype(np.int32)
+    return (keys, labels, np.arange(nid, dtype=np.int32), np.bincount(labels, minlength=nid).astype(np.int64),
+            inst["Q"][old].astype(np.float32), np.ascontiguousarray(inst["E"][old], np.float32),
+            np.ones(nid, np.int32))
+
+
+def _write_checkpoint(path, cfg, state):
+    import struct
+    from paper_2603_03935_gb300 import binding as b
+    keys, labels, parent, count, Q, E, obs = state
+    c = b.Config(**b.config_default(**cfg))
+    with open(path, "wb") as f:
+        f.write(b"DISCMAP1" + bytes(c) + struct.pack("<qi", len(keys), len(parent)))
+        for a, dt in ((keys, np.uint64), (labels, np.int32), (parent, np.int32), (count, np.int64), (Q, np.float32),
+                      (E, np.float32), (obs, np.int32)):
+            f.write(np.ascontiguousarray(a, dt).tobytes())
+
+
+@pytest.mark.parametrize("kind,S,before", [("tiny", 200, 10), ("room", 60, 8)])
+def test_frames_past_the_shared_capacities(torch_dev, tmp_path, kind, S, before):
+    # maps whose instances are cut into many small pieces: the next frame
+    # overlaps hundreds to thousands of them and its segments join most, so
+    # its edge roots (tiny: ~600) or its pairs (room: ~2000) pass what the
+    # association kernel keeps in shared memory and the frame runs on the
+    # map's global pair hash and union region; loaded through a checkpoint
+    # into the library and set into the oracle, both must agree
+    torch, dev = torch_dev
+    from paper_2603_03935_gb300 import DiscMap, device_frame
+    sc = synth.tiny_scene() if kind == "tiny" else synth.room_scene(num_frames=2000)
+    fr = sc.render(range(before + 2))
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 20, instance_capacity=1 << 14)
+    ocfg = common.to_oracle_cfg(cfg)
+    base = oracle.OracleMap(**ocfg)
+    for i in range(before):
+        base.integrate(*oracle.frame_args(fr, i))
+    state = _split_state(base, S)
+    omap = oracle.OracleMap(**ocfg)
+    omap.set_state(*state)
+    path = tmp_path / "split.ckpt"
+    _write_checkpoint(path, cfg, state)
+    gmap = DiscMap.load(path)
+    common.compare_maps(gmap, omap, ctx=f"{kind} split state loaded")
+    intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+    d = torch.from_numpy(fr.depth).to(dev)
+    l = torch.from_numpy(fr.labels.view(np.int16)).to(dev)
+    t = torch.from_numpy(fr.tokens).to(dev)
+    frames = [device_frame(d[j], l[j], t[j], fr.poses[j], intr, fr.num_masks[j]) for j in (before, before + 1)]
+    stats, done, rc = gmap.integrate_frames(frames)
+    assert rc == 0 and done == 2
+    for j in range(2):
+        o = omap.integrate(*oracle.frame_args(fr, before + j), report=True)
+        _counters_equal(stats[j], o, f"{kind} split frame {before + j}")
+        if j == 0:
+            assert o["merges"] > 512 if kind == "tiny" else o["overlap_pairs"] > 1536
+    common.compare_maps(gmap, omap, ctx=f"{kind} split, after two frames")
