@@ -1380,13 +1380,18 @@ disc_status room_check(Runner& r, int k, int G, int J, std::vector<Work>& w, con
 // those of the other maps.  Returns the first status that is not DISC_OK.
 disc_status run_call(Runner& r, std::vector<Work>& w)
 {
-    int total = 0, nbatch = 0;
+    int total = 0, most = 0;
     for (Work& wk : w) {
         wk.valid = 0;
         while (wk.valid < wk.n && check_frame(wk.m, r, wk.frames + wk.valid) == DISC_OK) wk.valid++;
         total += wk.valid;
-        nbatch = std::max(nbatch, (wk.valid + r.Jmax - 1) / r.Jmax);
+        most = std::max(most, wk.valid);
     }
+    // frames per map per batch: a call of one map that fits in one batch of
+    // 16 frames or more runs as two half batches, so that the second half's
+    // stateless kernels overlap the first half's frame chain
+    const int Jb = (!r.timing && w.size() == 1 && most >= 16 && most <= r.Jmax) ? (most + 1) / 2 : r.Jmax;
+    const int nbatch = (most + Jb - 1) / Jb;
     disc_status s = ensure_hist(r, std::max(total, 1));
     if (s != DISC_OK) return s;
     for (const Work& wk : w)
@@ -1436,11 +1441,11 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     // host inputs and enqueue its stateless part (or, timed, the whole batch)
     auto front = [&](int b, Pending& P) -> disc_status {
         P.b = -1;
-        const int lo = b * r.Jmax;
+        const int lo = b * Jb;
         P.gl.clear();
         int J = 0, S = 0;
         for (int i = 0; i < (int)w.size(); i++) {
-            const int cnt = std::min(r.Jmax, w[i].valid - lo);
+            const int cnt = std::min(Jb, w[i].valid - lo);
             if (cnt <= 0) continue;
             P.gl.push_back(i);
             J = std::max(J, cnt);
@@ -1453,7 +1458,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         disc_status st = DISC_OK;
         for (int gi = 0; gi < G && st == DISC_OK; gi++) {
             Work& wk = w[P.gl[gi]];
-            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            const int cnt = std::min(Jb, wk.valid - lo);
             uint64_t px = 0;
             int64_t masks = 0;
             for (int j = 0; j < cnt; j++) {
@@ -1505,7 +1510,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         st = cuda_status(cudaStreamWaitEvent(r.stream_in, r.ev_in_free[k], 0));
         for (int gi = 0; gi < G && st == DISC_OK; gi++) {
             Work& wk = w[P.gl[gi]];
-            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            const int cnt = std::min(Jb, wk.valid - lo);
             hrefs[gi] = map_refs(wk.m);
             hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
@@ -1567,14 +1572,14 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     // they could pass their limits, and the batch's map pointers follow),
     // its serial part, its counters to the call's history
     auto back = [&](Pending& P) -> disc_status {
-        const int k = P.k, G = P.G, J = P.J, S = P.S, lo = P.b * r.Jmax;
+        const int k = P.k, G = P.G, J = P.J, S = P.S, lo = P.b * Jb;
         disc_status st = DISC_OK;
         if (!P.timed) {
             MapRefs* hrefs = (MapRefs*)(P.blk.data() + r.off_refs);
             bool moved = false;
             for (int gi = 0; gi < G && st == DISC_OK; gi++) {
                 Work& wk = w[P.gl[gi]];
-                const int cnt = std::min(r.Jmax, wk.valid - lo);
+                const int cnt = std::min(Jb, wk.valid - lo);
                 int64_t masks = 0;
                 for (int j = 0; j < cnt; j++) masks += wk.frames[lo + j].num_masks;
                 st = ensure_instance_room(wk.m, masks, sr);
@@ -1601,7 +1606,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (st != DISC_OK) return st;
         for (int gi = 0; gi < G; gi++) {
             Work& wk = w[P.gl[gi]];
-            const int cnt = std::min(r.Jmax, wk.valid - lo);
+            const int cnt = std::min(Jb, wk.valid - lo);
             for (int j = 0; j < cnt; j++) {
                 const disc_frame& f = wk.frames[lo + j];
                 if (P.timed) wk.m->used_upper += (uint64_t)f.width * f.height;
@@ -1611,7 +1616,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         r.last_set = k;
         r.last_slot = S - 1;
         const Work& wl = w[P.gl[G - 1]];
-        r.last_M = wl.frames[lo + std::min(r.Jmax, wl.valid - lo) - 1].num_masks;
+        r.last_M = wl.frames[lo + std::min(Jb, wl.valid - lo) - 1].num_masks;
         r.have_frame = true;
         return DISC_OK;
     };

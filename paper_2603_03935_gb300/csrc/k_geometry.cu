@@ -261,7 +261,9 @@ __global__ void __launch_bounds__(BP_THREADS) k_backproject(const FrameParams* f
 
 // ---- per unique (segment, voxel): Eq. 3 term, |V_m|, label at batch start ------
 // Per-segment sums gather in shared memory first (one global atomic per
-// block and segment).  lookup = 0: the labels are left to k_lookup, which
+// block and segment).  Each term t (0 <= t <= 2^32 in 2^-32 fixed point)
+// adds as its two 16-bit halves in 32-bit shared atomics (64-bit shared
+// atomics are slower); a block's half sums stay below 2^31.  lookup = 0: the labels are left to k_lookup, which
 // runs once the previous batch's voxels are in (this kernel then reads no
 // map state).
 __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs* refs, int f0, int lookup)
@@ -270,10 +272,12 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
     const FrameParams& fp = fps[f0 + blockIdx.y];
     const Scratch sc = bs.frame(f0 + blockIdx.y);
     const VoxelTable vt = refs[fp.map].vt;
-    long long* s_ang = (long long*)ent_smem;         // [M]
-    int* s_nv = (int*)(s_ang + max(fp.M, 1));         // [M]
+    unsigned* s_hi = (unsigned*)ent_smem;             // [M] sum of the terms' high halves (t >> 16)
+    unsigned* s_lo = s_hi + max(fp.M, 1);             // [M] sum of their low halves (t & 0xffff)
+    int* s_nv = (int*)(s_lo + max(fp.M, 1));          // [M]
     for (int m = threadIdx.x; m < fp.M; m += blockDim.x) {
-        s_ang[m] = 0;
+        s_hi[m] = 0;
+        s_lo[m] = 0;
         s_nv[m] = 0;
     }
     __syncthreads();
@@ -313,15 +317,19 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
                 }
             }
             const long long tf = fix32f(term, S_VEC);
+            unsigned hi = (unsigned)(tf >> 16), lo = (unsigned)(tf & 0xffff);
             const int m0 = __shfl_sync(0xffffffffu, m, 0);
             if (__all_sync(0xffffffffu, valid && m == m0)) {
-                const long long sum = warp_sum(tf);
+                hi = __reduce_add_sync(0xffffffffu, hi);
+                lo = __reduce_add_sync(0xffffffffu, lo);
                 if (lane == 0) {
-                    atomicAdd((unsigned long long*)&s_ang[m0 - 1], (unsigned long long)sum);
+                    atomicAdd(&s_hi[m0 - 1], hi);
+                    atomicAdd(&s_lo[m0 - 1], lo);
                     atomicAdd(&s_nv[m0 - 1], 32);
                 }
             } else if (valid) {
-                atomicAdd((unsigned long long*)&s_ang[m - 1], (unsigned long long)tf);
+                if (hi) atomicAdd(&s_hi[m - 1], hi);
+                if (lo) atomicAdd(&s_lo[m - 1], lo);
                 atomicAdd(&s_nv[m - 1], 1);
             }
             if (!valid || !lookup) continue;
@@ -342,7 +350,8 @@ __global__ void k_entries(const FrameParams* fps, BatchScratch bs, const MapRefs
     __syncthreads();
     for (int m = threadIdx.x; m < fp.M; m += blockDim.x) {
         if (s_nv[m]) {
-            atomicAdd((unsigned long long*)&sc.ang[m], (unsigned long long)s_ang[m]);
+            const long long sum = (long long)s_hi[m] * 65536 + (long long)s_lo[m];
+            atomicAdd((unsigned long long*)&sc.ang[m], (unsigned long long)sum);
             atomicAdd(&sc.nvox[m], s_nv[m]);
         }
     }
@@ -391,7 +400,7 @@ int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs
                    bool lookup, cudaStream_t st)
 {
     const size_t smem = 12 * (size_t)std::max(Mmax, 1) + 16;
-    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, refs, f0, lookup ? 1 : 0);
+    k_entries<<<dim3(152 * 2, nb), 256, smem, st>>>(fps, bs, refs, f0, lookup ? 1 : 0);  // 3 x 4 B per mask
     return 1;
 }
 
