@@ -53,9 +53,17 @@ def parse():
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-frames", type=int, default=4, help="frames of each map per batch")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--same-maps", type=int, default=16,
+                    help="maps of the same-workload batched line (Room-scale 640x480 fp32, as the plain path; 0: skip)")
+    ap.add_argument("--same-frames", type=int, default=8, help="frames of each map per batch of that line")
+    ap.add_argument("--multistory-steps", type=int, default=8,
+                    help="timed 32-frame steps of the Multi-story configuration (0: skip)")
+    ap.add_argument("--tiny", type=int, default=1, help="1: time the Tiny configuration")
     ap.add_argument("--served-maps", type=int, default=32)
     ap.add_argument("--served-rates", default="4000,8000,12000,16000", help="offered frames/s, comma separated")
-    ap.add_argument("--served-seconds", type=float, default=1.0)
+    ap.add_argument("--served-repeats", type=int, default=2, help="measurements per offered rate")
+    ap.add_argument("--served-frames", type=int, default=96,
+                    help="frames of each served map's path; the measurements together take every frame once")
     ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
     ap.add_argument("--served-precision", type=int, default=2, help="0 fp32, 1 bf16, 2 fp8 e4m3")
     ap.add_argument("--precision", type=int, default=0,
@@ -351,10 +359,205 @@ def run_batched(args, torch, dev, stream, rank):
     return out
 
 
+SAME = "Batched, same per-frame work as the plain line: {G} independent Room-scale maps (10x8x3 m room, " \
+       "80 boxes/ellipsoids, 640x480 fp32 depth with 1% noise, 40 masks/frame, tokens 24x24x768 fp32, voxel " \
+       "2.5 cm, FP32), {J} frames of every map per group call, each map {W} frames into its own trajectory"
+
+
+def _device_frames(torch, dev, binding, sc, fr, idx, bf16=False):
+    """A ctypes Frame array over device copies of frames idx of fr (the
+    tensors are returned too, to keep them alive)."""
+    d = torch.from_numpy(fr.depth[idx]).to(dev)
+    l = torch.from_numpy(fr.labels[idx].view(np.int16)).to(dev)
+    t = torch.from_numpy(fr.tokens[idx]).to(dev)
+    if bf16:
+        t = t.to(torch.bfloat16).contiguous()
+    a = (binding.Frame * len(idx))()
+    for j, i in enumerate(idx):
+        f = a[j]
+        f.width, f.height = sc.width, sc.height
+        f.fx, f.fy, f.cx, f.cy = sc.fx, sc.fy, sc.cx, sc.cy
+        for q, v in enumerate(fr.poses[i].reshape(16)):
+            f.T_world_cam[q] = float(v)
+        f.depth, f.labels, f.tokens = d[j].data_ptr(), l[j].data_ptr(), t[j].data_ptr()
+        f.token_dtype = 1 if bf16 else 0
+        f.num_masks = int(fr.num_masks[i])
+        f.global_embed = None
+        f.inputs_on_device = 1
+    return a, (d, l, t)
+
+
+def run_same_workload_batched(args, torch, dev, stream, rank):
+    """The batched form on the plain line's workload: G Room-scale maps
+    (seeds 2.., FP32, fp32 tokens), each first integrating W frames of its
+    own trajectory untimed, then timed group calls of J frames per map."""
+    import synth
+    from paper_2603_03935_gb300 import DiscGroup, DiscMap, binding
+    from tests import common
+    G, J, T, W = args.same_maps, args.same_frames, 3, 32
+    scs = [synth.room_scene(seed=2 + 97 * rank + g) for g in range(G)]
+    maps = [DiscMap(**common.disc_cfg(s, voxel_capacity=1 << 22, instance_capacity=1 << 12,
+                                      cuda_stream=stream.cuda_stream, device=dev.index)) for s in scs]
+    grp = DiscGroup(max_maps=G, frames_per_map=J, embed_dim=scs[0].dim, patch_h=scs[0].patch_h,
+                    patch_w=scs[0].patch_w, max_width=scs[0].width, max_height=scs[0].height,
+                    max_masks=scs[0].max_masks, cuda_stream=stream.cuda_stream, device=dev.index)
+    sts = [(binding.Stats * J)() for _ in range(G)]
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    times, upd, pairs, newv = [], 0, 0, 0
+    for s in range((W + T * J) // J):
+        lo = s * J
+        frs = [sc.render(range(lo, lo + J)) for sc in scs]
+        arrs = [_device_frames(torch, dev, binding, sc, fr, list(range(J))) for sc, fr in zip(scs, frs)]
+        torch.cuda.synchronize()
+        timed = lo >= W
+        if timed:
+            flush.fill_(float(s))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        rc = grp.integrate_raw(maps, [a for a, _ in arrs], [J] * G, sts)
+        assert rc == 0, rc
+        if timed:
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for g in range(G):
+                for j in range(J):
+                    upd += sts[g][j].unique_seg_voxels
+                    pairs += sts[g][j].overlap_pairs
+                    newv += sts[g][j].new_voxels
+        del arrs
+    total_ms = float(np.sum(times))
+    nfr = T * G * J
+    out = {"workload": SAME.format(G=G, J=J, W=W), "frames_per_s": nfr / (total_ms / 1e3),
+           "voxel_updates_per_s": upd / (total_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
+           "steps": T, "ms_per_batch": total_ms / T,
+           "per_frame": {"voxel_updates": upd / nfr, "overlap_pairs": pairs / nfr, "new_voxels": newv / nfr},
+           "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                                "mode": "a frame's result is ready when its batch ends"}}
+    grp.close()
+    for m in maps:
+        m.close()
+    return out
+
+
+MULTISTORY = "Multi-story: 3 floors of 40x30 m, 1000 objects, 640x480 depth (to 20 m, 1% noise), up to 100 " \
+             "masks/frame, tokens 24x24x768 bf16, voxel 5 cm, a 2^27-slot voxel table, BF16 pooling and " \
+             "scoring with FP32 accumulation and exact re-score near the threshold"
+
+
+def run_multistory(args, torch, dev, stream, rank, cpu):
+    """The Multi-story configuration: 32-frame calls along its serpentine
+    path (device-resident bf16 tokens), two untimed warm-up steps, then the
+    timed steps; the oracle (bf16-rounded tokens, one host core) on its first
+    frames for about cpu_seconds."""
+    import oracle
+    import synth
+    from paper_2603_03935_gb300 import DiscMap, binding
+    from tests import common
+    B, K, Wm = 32, args.multistory_steps, 2
+    sc = synth.multistory_scene()
+    cfg = common.disc_cfg(sc, voxel_capacity=1 << 27, instance_capacity=1 << 14, precision=1,
+                          cuda_stream=stream.cuda_stream, device=dev.index)
+    m = DiscMap(**cfg)
+    stats = (binding.Stats * B)()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    times, upd, pairs, masks, cfr = [], 0, 0, 0, None
+    for s in range(Wm + K):
+        fr = sc.render(range(s * B, (s + 1) * B))
+        if s == 0:
+            cfr = fr
+        a, keep = _device_frames(torch, dev, binding, sc, fr, list(range(B)), bf16=True)
+        torch.cuda.synchronize()
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = m.integrate_frames_raw(a, B, stats)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        if s >= Wm:
+            times.append(e0.elapsed_time(e1))
+            upd += sum(stats[j].unique_seg_voxels for j in range(B))
+            pairs += sum(stats[j].overlap_pairs for j in range(B))
+            masks += int(fr.num_masks.sum())
+    nv, nid = m.counts()
+    m.close()
+    total_ms = float(np.sum(times))
+    out = {"workload": MULTISTORY, "frames_per_s": K * B / (total_ms / 1e3),
+           "voxel_updates_per_s": upd / (total_ms / 1e3), "frames": K * B, "first_frame": Wm * B,
+           "step_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                       "mode": "one 32-frame disc_integrate_frames call"},
+           "per_frame": {"voxel_updates": upd / (K * B), "overlap_pairs": pairs / (K * B), "masks": masks / (K * B)},
+           "map": {"voxels": nv, "instances": nid}}
+    if cpu and args.cpu_seconds > 0:
+        om = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+        t16 = torch.from_numpy(cfr.tokens).to(torch.bfloat16).float().numpy()
+        intr = (sc.fx, sc.fy, sc.cx, sc.cy)
+        t0 = time.perf_counter()
+        n = 0
+        while n < B and (n == 0 or time.perf_counter() - t0 < args.cpu_seconds):
+            om.integrate(cfr.depth[n], cfr.labels[n], t16[n], cfr.poses[n], intr, cfr.num_masks[n], report=False)
+            n += 1
+        dt = time.perf_counter() - t0
+        model, nproc = host_cpu()
+        out["cpu_baseline"] = {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle", "cpu_model": model,
+                               "nproc": nproc, "sample": f"frames 0..{n - 1} of the Multi-story path, fresh map"}
+    return out
+
+
+TINY = "Tiny: 4x4x3 m room with 4 boxes, 20 orbit frames of 64x48 (fx = fy = 50), <= 8 masks, tokens 8x6x512 " \
+       "fp32, voxel 5 cm, FP32"
+
+
+def run_tiny(args, torch, dev, stream, cpu):
+    """The Tiny configuration: its 20 frames in one call on a fresh map,
+    repeated; the oracle over the same 20 frames."""
+    import oracle
+    import synth
+    from paper_2603_03935_gb300 import DiscMap, binding
+    from tests import common
+    sc = synth.tiny_scene()
+    fr = sc.render(range(20))
+    a, keep = _device_frames(torch, dev, binding, sc, fr, list(range(20)))
+    cfg = common.disc_cfg(sc, cuda_stream=stream.cuda_stream, device=dev.index)
+    stats = (binding.Stats * 20)()
+    times = []
+    for r in range(8):
+        m = DiscMap(**cfg)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = m.integrate_frames_raw(a, 20, stats)
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        if r >= 3:
+            times.append(e0.elapsed_time(e1))
+        m.close()
+    ms = float(np.median(times))
+    out = {"workload": TINY, "frames_per_s": 20 / (ms / 1e3), "ms_per_trajectory": ms,
+           "mode": "one disc_integrate_frames call of the 20 frames on a fresh map (median of 5, after 3)"}
+    if cpu:
+        om_t = []
+        for r in range(3):
+            om = oracle.OracleMap(**common.to_oracle_cfg(cfg))
+            t0 = time.perf_counter()
+            for i in range(20):
+                om.integrate(*oracle.frame_args(fr, i), report=False)
+            om_t.append(time.perf_counter() - t0)
+        model, nproc = host_cpu()
+        out["cpu_baseline"] = {"value": 20 / float(np.median(om_t)), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                               "cpu_model": model, "nproc": nproc, "sample": "the 20 frames, fresh map, median of 3"}
+    return out
+
+
 SERVED = "Served: {G} resident room-scale maps of mixed size (320x240..640x480, 5-60 masks, bf16 tokens, " \
          "{prec} pooling and scoring), " \
-         "Poisson arrivals, integrate:query 9:1 (top-5 of 4 vectors), each map cycling through its {F} frames, " \
-         "4 client threads, continuous batching of up to {J} frames per map per batch"
+         "Poisson arrivals, integrate:query 9:1 (top-5 of 4 vectors), each map walking on along its own path " \
+         "({F} frames, none taken twice), 4 client threads, continuous batching of up to {J} frames per map per batch"
 
 
 def run_served(args, torch, dev, rank):
@@ -364,7 +567,7 @@ def run_served(args, torch, dev, rank):
     import threading
     from paper_2603_03935_gb300 import DiscServer, binding
     from tests import common
-    G, F, J = args.served_maps, 16, 4
+    G, F, J = args.served_maps, args.served_frames, 4
     scs = batched_scenes(G, 5000 + 97 * rank)
     frs = [sc.render(range(F)) for sc in scs]
     bf = []
@@ -380,35 +583,53 @@ def run_served(args, torch, dev, rank):
     ids = [srv.open_map(**common.disc_cfg(sc, voxel_capacity=1 << 21, instance_capacity=1 << 12,
                                           precision=args.served_precision)) for sc in scs]
     queries = [fr.tokens[0][:4] for fr in frs]
-    # warm-up: every map takes its frames once
+    # warm-up: every map takes its first 4 frames; the measured requests
+    # then walk on along each map's path from there
+    nxt = [0] * G
     for g in range(G):
-        for i in range(F):
+        for i in range(4):
             srv.wait_frame(srv.submit_frame(ids[g], bf[g][i]))
+        nxt[g] = 4
     rng = np.random.default_rng(11 + rank)
     out = []
-    for rate in [float(x) for x in args.served_rates.split(",") if x]:
-        n = int(rate / 0.9 * args.served_seconds)  # requests; 9 in 10 are frames
+    levels = [float(x) for x in args.served_rates.split(",") if x]
+    runs = [r for r in levels for _ in range(args.served_repeats)]
+    per_run = (F - 4) // len(runs)  # frames of each map per measurement: no frame is taken twice
+    for rate in runs:
+        # requests of this measurement: per_run frames of every map in a
+        # random order of maps, one query per nine frames at random places
+        # (9:1), Poisson arrivals
+        which = rng.permutation(np.repeat(np.arange(G), per_run))
+        qs = rng.integers(0, G, len(which) // 9)
+        n = len(which) + len(qs)
+        is_q = np.zeros(n, bool)
+        is_q[rng.choice(n, len(qs), replace=False)] = True
+        order = np.empty(n, np.int64)
+        order[~is_q] = which
+        order[is_q] = qs
+        which = order
         gaps = rng.exponential(1.0 / (rate / 0.9), n)
         when = np.cumsum(gaps)
-        which = rng.integers(0, G, n)
-        is_q = rng.random(n) < 0.1
-        nxt = [0] * G
         plan = []
         for r in range(n):
             g = int(which[r])
             if is_q[r]:
                 plan.append((when[r], g, -1))
             else:
-                plan.append((when[r], g, nxt[g] % F))
+                plan.append((when[r], g, nxt[g]))
                 nxt[g] += 1
         srv.reset_stats()
-        fail = []
+        fail, newv = [], []
 
         def client(c):
+            # client c submits the requests of maps g with g % 4 == c, so a
+            # map's frames go in in the order of its path
             tk = []
             t0 = start
-            for r in range(c, n, 4):
+            for r in range(n):
                 at, g, i = plan[r]
+                if g % 4 != c:
+                    continue
                 d = t0 + at - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
@@ -417,7 +638,12 @@ def run_served(args, torch, dev, rank):
                 else:
                     tk.append((False, srv.submit_frame(ids[g], bf[g][i])))
             for q, t in tk:
-                rc = srv.wait_query(t)[0] if q else srv.wait_frame(t)["rc"]
+                if q:
+                    rc = srv.wait_query(t)[0]
+                else:
+                    st_ = srv.wait_frame(t)
+                    rc = st_["rc"]
+                    newv.append(st_["new_voxels"])
                 if rc != 0:
                     fail.append(rc)
 
@@ -433,10 +659,19 @@ def run_served(args, torch, dev, rank):
                     "refused": len(fail), "refused_codes": sorted(set(fail))[:5],
                     "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "frames": rep["frames"],
                     "queries": rep["queries"], "batches": rep["batches"],
-                    "frames_per_batch": rep["frames"] / max(rep["batches"], 1)})
+                    "frames_per_batch": rep["frames"] / max(rep["batches"], 1),
+                    "new_voxels_per_frame": float(np.mean(newv)) if newv else 0.0})
     srv.close()
     prec = ("fp32", "bf16", "fp8 e4m3")[args.served_precision]
-    return {"workload": SERVED.format(G=G, F=F, J=J, prec=prec), "rates": out}
+    # the knee: the highest offered rate whose median achieved rate keeps up
+    # with 95 % of it
+    knee = 0.0
+    for rate in levels:
+        got = [o["frames_per_s"] for o in out if o["offered_frames_per_s"] == rate]
+        if got and float(np.median(got)) >= 0.95 * rate:
+            knee = rate
+    return {"workload": SERVED.format(G=G, F=F, J=J, prec=prec), "rates": out, "knee_offered_frames_per_s": knee,
+            "repeats": args.served_repeats}
 
 
 def run_reference(args, rank):
@@ -567,7 +802,8 @@ def main():
     # the line's sections as they finish (the watchdog prints what is here)
     state = {}
     SECTIONS = ("dbscan", "assoc_grid", "dilation", "latency_ms", "finalize", "heatmap", "phases_ms_per_frame",
-                "roofline", "roofline_step", "cpu_baseline", "e2e", "batched", "served")
+                "roofline", "roofline_step", "cpu_baseline", "e2e", "batched", "batched_same_workload", "tiny",
+                "multistory", "served")
 
     def assemble(unfinished=None):
         core = state.get("core")
@@ -892,6 +1128,11 @@ def main():
     # the batched and served forms last: their many maps and threads come
     # after every single-map measurement
     state["batched"] = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
+    state["batched_same_workload"] = (run_same_workload_batched(args, torch, dev, stream, rank)
+                                      if args.same_maps > 0 else None)
+    state["tiny"] = run_tiny(args, torch, dev, stream, rank == 0 and world == 1) if args.tiny else None
+    state["multistory"] = (run_multistory(args, torch, dev, stream, rank, rank == 0 and world == 1)
+                           if args.multistory_steps > 0 else None)
     state["served"] = run_served(args, torch, dev, rank) if args.served_maps > 0 else None
 
     if rank == 0:

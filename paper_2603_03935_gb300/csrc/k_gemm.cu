@@ -221,10 +221,27 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
     bool failed = false;
     int last_commit = -1;  // chunk of the most recent commit (same on all threads)
     const bool stall = g_gemm_stall != 0;  // uniform: read once
+    // Thread tid stages row d0 + tid of the F^T tile: its 32 tokens of the
+    // next chunk are loaded into registers while the current chunk is staged
+    // and multiplied, so token loads stay in flight across the loop.
+    auto load_chunk = [&](int c, float (&x)[GEMM_KC]) {
+        const int d = d0 + tid, p0 = c * GEMM_KC;
+#pragma unroll
+        for (int j = 0; j < GEMM_KC; j++) {
+            const int p = p0 + j;
+            x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
+        }
+    };
+    float xn[GEMM_KC];
+    if (nchunks > 0) load_chunk(0, xn);
 
     for (int c = 0; c < nchunks && !failed; c++) {
         const int s = c & 1;
         uint8_t* st = smem + s * STAGE;
+        float x[GEMM_KC];
+#pragma unroll
+        for (int j = 0; j < GEMM_KC; j++) x[j] = xn[j];
+        if (c + 1 < nchunks) load_chunk(c + 1, xn);
         if (c >= 2) {
             // the MMAs of chunk c-2 read this stage: wait for their commit
             bool ok = mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((c >> 1) - 1) & 1));
@@ -233,15 +250,8 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         const int p0 = c * GEMM_KC;
         if constexpr (F8) {
             // A: F^T tile in e4m3, thread tid owns row d0 + tid, 16 patches per
-            // 16 B; all loads first, then one exact multiply by 2^-a_p each
+            // 16 B; one exact multiply by 2^-a_p each
             {
-                const int d = d0 + tid;
-                float x[GEMM_KC];
-#pragma unroll
-                for (int j = 0; j < GEMM_KC; j++) {
-                    const int p = p0 + j;
-                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
-                }
                 const float4* qm = (const float4*)(sc.qmul + p0);  // zero past P
 #pragma unroll
                 for (int q4 = 0; q4 < GEMM_KC / 4; q4++) {
@@ -271,17 +281,11 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         } else if constexpr (BF) {
             // A: F^T tile in bf16, thread tid owns row d0 + tid, 8 patches per 16 B
             {
-                const int d = d0 + tid;
 #pragma unroll
                 for (int kq = 0; kq < GEMM_KC / 8; kq++) {
-                    float x[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        const int p = p0 + 8 * kq + j;
-                        x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
-                    }
-                    const uint4 v = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]),
-                                               pack_bf16(x[6], x[7]));
+                    const float* y = x + 8 * kq;
+                    const uint4 v = make_uint4(pack_bf16(y[0], y[1]), pack_bf16(y[2], y[3]), pack_bf16(y[4], y[5]),
+                                               pack_bf16(y[6], y[7]));
                     *(uint4*)(st + kq * A_LBO + tid * 16) = v;
                 }
             }
@@ -300,22 +304,16 @@ __global__ void __launch_bounds__(128, 1) k_pool_gemm(const FrameParams* fps, Ba
         } else {
         // A: F^T tile. Thread tid owns row r = tid (token dimension d0 + tid).
         {
-            const int d = d0 + tid;
             float* Ahi = (float*)st;
             float* Alo = (float*)(st + A_TILE_BYTES);
 #pragma unroll
             for (int kq = 0; kq < GEMM_KC / 4; kq++) {
-                float x[4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int p = p0 + 4 * kq + j;
-                    x[j] = (d < D && p < P) ? ldtok<T>(F, (size_t)p * D + d) : 0.0f;
-                }
+                const float* y = x + 4 * kq;
                 float4 hi, lo;
-                hi.x = tf32_rna(x[0]); lo.x = tf32_rna(x[0] - hi.x);
-                hi.y = tf32_rna(x[1]); lo.y = tf32_rna(x[1] - hi.y);
-                hi.z = tf32_rna(x[2]); lo.z = tf32_rna(x[2] - hi.z);
-                hi.w = tf32_rna(x[3]); lo.w = tf32_rna(x[3] - hi.w);
+                hi.x = tf32_rna(y[0]); lo.x = tf32_rna(y[0] - hi.x);
+                hi.y = tf32_rna(y[1]); lo.y = tf32_rna(y[1] - hi.y);
+                hi.z = tf32_rna(y[2]); lo.z = tf32_rna(y[2] - hi.z);
+                hi.w = tf32_rna(y[3]); lo.w = tf32_rna(y[3] - hi.w);
                 const uint32_t off = kq * A_LBO + tid * 16;
                 *(float4*)((uint8_t*)Ahi + off) = hi;
                 *(float4*)((uint8_t*)Alo + off) = lo;
