@@ -383,12 +383,18 @@ disc_status disc_debug_gemm_stall(int32_t device, int32_t on);
 /* ---- Launch schedule and autotuner -----------------------------------------
  * How a map's (or a group's) batches are cut into launches: the frames per
  * launch of the geometry kernels (back-projection, entries, DBSCAN), whose
- * per-frame hashes should stay in L2, and the CTA counts of the serial
- * kernels, which trade parallel probes against launch cost.  Neither changes
- * any result. */
+ * per-frame hashes should stay in L2; the CTA counts of the four serial
+ * kernels per frame of maps with the neighbourhood overlap; how many lanes
+ * look one voxel up in the table together (warp-cooperative probing: each
+ * round a group of probe_width lanes reads that many consecutive slots of the
+ * probe sequence); and how many CTAs (a thread-block cluster) carry one map's
+ * frames in the association kernel.  None changes any result. */
 typedef struct {
     int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 4) */
     int32_t serial_ctas;     /* serial kernels' CTAs in quarters of the default count, 1..32 (default 4) */
+    int32_t probe_width;     /* lanes per key of the voxel-table lookup: 1, 2, 4 or 8 (0 or 1: one lane) */
+    int32_t assoc_cluster;   /* CTAs per map in the association kernel: 0 (as many as the batch's maps leave
+                                SMs for, up to 8), or 1, 2, 4, 8 (capped by what the device co-schedules) */
 } disc_schedule;
 
 typedef struct {
@@ -402,7 +408,8 @@ disc_status disc_map_set_schedule(disc_map* map, const disc_schedule* schedule);
 disc_status disc_group_set_schedule(disc_group* group, const disc_schedule* schedule);
 
 /* Autotuner: times each candidate schedule (geometry_chunk in {2, 4, 8} x
- * serial_ctas in {2, 4, 8}) on the sample frames, integrated into fresh maps
+ * probe_width in {1, 2, 4} x assoc_cluster automatic or half of it) on the
+ * sample frames, integrated into fresh maps
  * with the given maps' configurations (created and destroyed here; the given
  * maps are not changed), two untimed passes then `reps` timed ones, and keeps
  * the fastest for the map or group.  report may be NULL. */

@@ -59,7 +59,7 @@ class GroupConfig(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32)]
+    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32), ("probe_width", c_i32), ("assoc_cluster", c_i32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -67,6 +67,7 @@ class TuneReport(ctypes.Structure):
 
     def as_dict(self):
         return {"geometry_chunk": int(self.best.geometry_chunk), "serial_ctas": int(self.best.serial_ctas),
+                "probe_width": int(self.best.probe_width), "assoc_cluster": int(self.best.assoc_cluster),
                 "best_ms": float(self.best_ms), "default_ms": float(self.default_ms),
                 "candidates": int(self.candidates)}
 
@@ -366,8 +367,9 @@ class DiscMap:
         """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
         return lib().disc_integrate_frames(self._h, arr, n, stats, None)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
-        _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0):
+        _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
+                                                                          assoc_cluster))),
                "disc_map_set_schedule")
 
     def autotune(self, frames, reps=3) -> dict:
@@ -535,8 +537,9 @@ class DiscGroup:
             if stats_arrays is not None else None
         return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4):
-        _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas))),
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0):
+        _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
+                                                                            assoc_cluster))),
                "disc_group_set_schedule")
 
     def autotune(self, maps, frame_arrays, counts, reps=3) -> dict:

@@ -149,6 +149,8 @@ struct Runner {
     // launch schedule (disc_*_set_schedule, disc_*_autotune)
     int geo_chunk = GEOMETRY_CHUNK;   // frames per back-projection / entries / DBSCAN launch
     int cta_scale = 4;                // serial kernels' CTAs in quarters of the default count
+    int probe_width = 1;              // lanes per key of the batch's voxel-table lookup
+    int assoc_cluster = 0;            // CTAs per map of the association kernel (0: automatic)
     bool graphs_off = false;
     std::map<long long, BatchGraph> graphs;
     std::map<long long, int> shapes_seen;  // batch shapes launched directly so far
@@ -991,8 +993,8 @@ int enqueue_serial(Runner& r, int k, int S, int G, int J, int combos, cudaStream
     step.merged = r.d_merged;
     if (!(combos & COMBO_DILATE)) {
         step.j = 0;
-        run_phase(r, PH_LOOKUP, st, [&] { return launch_lookup(dfp, bs, step.refs, r.ah, S, st); });
-        run_phase(r, PH_ASSOCIATE, st, [&] { return launch_associate(dfp, bs, step, G, st); });
+        run_phase(r, PH_LOOKUP, st, [&] { return launch_lookup(dfp, bs, step.refs, r.ah, S, r.probe_width, st); });
+        run_phase(r, PH_ASSOCIATE, st, [&] { return launch_associate(dfp, bs, step, G, r.assoc_cluster, st); });
         run_phase(r, PH_COMMIT, st, [&] {
             const int n = launch_commit(bs, step, r.ah, G, st);
             cudaMemsetAsync(r.ah.n, 0, sizeof(int32_t), st);  // the hash is empty again
@@ -2043,10 +2045,18 @@ disc_status set_schedule(Runner& r, const disc_schedule* sch)
 {
     if (!sch || sch->geometry_chunk < 1 || sch->geometry_chunk > 32 || sch->serial_ctas < 1 || sch->serial_ctas > 32)
         return DISC_ERR_INVALID_ARG;
-    if (r.geo_chunk == sch->geometry_chunk && r.cta_scale == sch->serial_ctas) return DISC_OK;
+    const int pw = sch->probe_width == 0 ? 1 : sch->probe_width;
+    if (pw != 1 && pw != 2 && pw != 4 && pw != 8) return DISC_ERR_INVALID_ARG;
+    const int ac = sch->assoc_cluster;
+    if (ac != 0 && ac != 1 && ac != 2 && ac != 4 && ac != 8) return DISC_ERR_INVALID_ARG;
+    if (r.geo_chunk == sch->geometry_chunk && r.cta_scale == sch->serial_ctas && r.probe_width == pw &&
+        r.assoc_cluster == ac)
+        return DISC_OK;
     CK(cudaStreamSynchronize(r.stream));
     r.geo_chunk = sch->geometry_chunk;
     r.cta_scale = sch->serial_ctas;
+    r.probe_width = pw;
+    r.assoc_cluster = ac;
     for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);  // captured with the old schedule
     r.graphs.clear();
     r.shapes_seen.clear();
@@ -2060,49 +2070,58 @@ disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
                      const std::vector<std::pair<const disc_frame*, int>>& frames, int reps, disc_tune_report* out)
 {
     if (reps < 1 || reps > 100) return DISC_ERR_INVALID_ARG;
-    const disc_schedule keep{r.geo_chunk, r.cta_scale};
+    const disc_schedule keep{r.geo_chunk, r.cta_scale, r.probe_width, r.assoc_cluster};
     disc_tune_report rep{};
     rep.best_ms = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     disc_status s = DISC_OK;
-    for (int geo : {4, 2, 8}) {  // the default first
-        for (int q : {4, 2, 8}) {
-            const disc_schedule cand{geo, q};
-            s = set_schedule(r, &cand);
-            double best = 1e300;
-            for (int pass = 0; pass < reps + 2 && s == DISC_OK; pass++) {
-                std::vector<disc_map*> maps(cfgs.size(), nullptr);
-                std::vector<Work> w(cfgs.size());
-                for (size_t i = 0; i < cfgs.size() && s == DISC_OK; i++) {
-                    disc_map_config c = *cfgs[i];
-                    c.cuda_stream = r.stream;
-                    s = disc_map_create(&c, nullptr, &maps[i]);
-                    w[i].m = maps[i];
-                    w[i].frames = frames[i].first;
-                    w[i].n = frames[i].second;
-                }
-                if (s == DISC_OK) {
-                    s = cuda_status(cudaEventRecord(e0, r.stream));
-                    if (s == DISC_OK) s = run_call(r, w);
-                    if (s == DISC_OK) s = cuda_status(cudaEventRecord(e1, r.stream));
-                    if (s == DISC_OK) s = cuda_status(cudaEventSynchronize(e1));
-                    float ms = 0.0f;
-                    if (s == DISC_OK) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
-                    if (s == DISC_OK && pass >= 2) best = std::min(best, (double)ms);
-                }
-                for (disc_map* m : maps) disc_map_destroy(m);
+    // frames per geometry launch x lanes per key of the lookup x CTAs per
+    // map of the association kernel (automatic, or the next smaller cluster)
+    const int auto_c = 0;
+    std::vector<disc_schedule> cands;
+    for (int geo : {4, 2, 8})  // the default first
+        for (int pw : {1, 2, 4})
+            for (int ac : {auto_c, -1}) cands.push_back(disc_schedule{geo, r.cta_scale, pw, ac});
+    for (disc_schedule cand : cands) {
+        if (cand.assoc_cluster < 0) {  // half the automatic cluster of these maps
+            int c = 1;
+            while (c * 2 <= 8 && (c * 2) * (int)cfgs.size() <= 152) c *= 2;
+            if (c == 1) continue;
+            cand.assoc_cluster = c / 2;
+        }
+        s = set_schedule(r, &cand);
+        double best = 1e300;
+        for (int pass = 0; pass < reps + 2 && s == DISC_OK; pass++) {
+            std::vector<disc_map*> maps(cfgs.size(), nullptr);
+            std::vector<Work> w(cfgs.size());
+            for (size_t i = 0; i < cfgs.size() && s == DISC_OK; i++) {
+                disc_map_config c = *cfgs[i];
+                c.cuda_stream = r.stream;
+                s = disc_map_create(&c, nullptr, &maps[i]);
+                w[i].m = maps[i];
+                w[i].frames = frames[i].first;
+                w[i].n = frames[i].second;
             }
-            if (s != DISC_OK) break;
-            rep.candidates++;
-            if (geo == 4 && q == 4) rep.default_ms = best;
-            if (best < rep.best_ms) {
-                rep.best_ms = best;
-                rep.best = cand;
+            if (s == DISC_OK) {
+                s = cuda_status(cudaEventRecord(e0, r.stream));
+                if (s == DISC_OK) s = run_call(r, w);
+                if (s == DISC_OK) s = cuda_status(cudaEventRecord(e1, r.stream));
+                if (s == DISC_OK) s = cuda_status(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                if (s == DISC_OK) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+                if (s == DISC_OK && pass >= 2) best = std::min(best, (double)ms);
             }
+            for (disc_map* m : maps) disc_map_destroy(m);
         }
         if (s != DISC_OK) break;
+        rep.candidates++;
+        if (cand.geometry_chunk == 4 && cand.probe_width == 1 && cand.assoc_cluster == 0) rep.default_ms = best;
+        if (best < rep.best_ms) {
+            rep.best_ms = best;
+            rep.best = cand;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

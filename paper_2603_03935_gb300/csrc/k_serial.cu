@@ -1055,10 +1055,45 @@ __device__ __forceinline__ int warp_append(int* counter, bool want)
     return base + __popc(b & ((1u << lane) - 1));
 }
 
+// Label of `key` in the voxel table (-1: absent), probed by the PW lanes of
+// an aligned lane group together (warp-cooperative probing): each round the
+// group loads PW consecutive slots of the probe sequence, and the first slot
+// in probe order that holds the key or is empty decides.  All lanes of a
+// group pass the same key and `active`; inactive groups return -1 at once.
+// *probes: slots passed before the deciding one; *full: no empty slot found.
+template <int PW>
+__device__ __forceinline__ int probe_label(const VoxelTable& vt, unsigned long long key, bool active, int* probes,
+                                           bool* full)
+{
+    *probes = 0;
+    *full = false;
+    if (!active) return -1;
+    const int lane = threadIdx.x & 31, base = lane & ~(PW - 1), sub = lane - base;
+    const unsigned gmask = (PW == 32 ? 0xffffffffu : ((1u << PW) - 1u)) << base;
+    const unsigned long long h = mix64(key) & vt.mask;
+    for (unsigned long long pr = 0; pr <= vt.mask; pr += PW) {
+        const unsigned long long slot = (h + pr + sub) & vt.mask;
+        const unsigned long long kk = vt.keys[slot];
+        const unsigned hit = (__ballot_sync(gmask, kk == key || kk == EMPTY_KEY) & gmask) >> base;
+        if (hit) {
+            const int first = __ffs(hit) - 1;
+            const bool found = __shfl_sync(gmask, kk == key, base + first);
+            int lab = -1;
+            if (found && sub == first) lab = vt.labels[slot];
+            *probes = (int)pr + first;
+            return found ? __shfl_sync(gmask, lab, base + first) : -1;
+        }
+    }
+    *full = true;
+    return -1;
+}
+
 // Every entry of every frame slot of the batch (block row = slot): its label
 // in the map at the batch start (tag-0 item), or, when absent, its slot in
 // the batch's absent-voxel hash, where the least (frame position, segment)
-// containing it is kept.
+// containing it is kept.  PW lanes look each entry up together (PW = 1: one
+// lane per entry); the group's first lane carries the entry afterwards.
+template <int PW>
 __global__ void __launch_bounds__(256) k_lookup(const FrameParams* fps, BatchScratch bs, const MapRefs* refs,
                                                AbsentHash ah)
 {
@@ -1070,46 +1105,43 @@ __global__ void __launch_bounds__(256) k_lookup(const FrameParams* fps, BatchScr
     const VoxelTable vt = refs[fp.map].vt;
     const unsigned long long gtag = (unsigned long long)(fp.map + 1) << 54;
     const int lane = threadIdx.x & 31;
+    constexpr int PER = 32 / PW;  // entries of a warp per round
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
     int maxp = 0;
-    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ne; i0 += gridDim.x * blockDim.x) {
-        const int i = i0 + lane;
+    for (int i0 = warp * PER; i0 < ne; i0 += nwarps * PER) {  // whole warps iterate together
+        const int i = i0 + lane / PW;
         const bool valid = i < ne;
+        const bool lead = valid && (lane & (PW - 1)) == 0;
         const unsigned long long hk = valid ? sc.sent[i] : 0ull;
         const int m = (int)(hk >> 54);
         const unsigned long long key = hk & KEY54;
-        int lab = -1, at = -1;
+        int probes;
+        bool full;
+        const int lab = probe_label<PW>(vt, key, valid, &probes, &full);
+        if (lead && full) set_err(sc.ctr, DISC_ERR_TABLE_FULL);
+        maxp = max(maxp, probes);
+        int at = -1;
         bool claimed = false;
-        if (valid) {
-            unsigned long long h = mix64(key) & vt.mask;
-            for (int pr = 0;; pr++) {
-                const unsigned long long kk = vt.keys[h];
-                if (kk == key) { lab = vt.labels[h]; break; }
-                if (kk == EMPTY_KEY) break;
-                h = (h + 1) & vt.mask;
-                if (pr > (int)vt.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); break; }
-                maxp = max(maxp, pr + 1);
+        if (lead && !full && lab < 0) {
+            const unsigned long long ak = gtag | key;
+            unsigned long long t = mix64(ak) & ah.mask;
+            for (unsigned long long pr = 0;; pr++) {
+                const unsigned long long cur = ah.key[t];
+                if (cur == ak) break;
+                if (cur == 0ull) {
+                    const unsigned long long prev = atomicCAS(&ah.key[t], 0ull, ak);
+                    if (prev == 0ull) { claimed = true; break; }
+                    if (prev == ak) break;
+                }
+                t = (t + 1) & ah.mask;
+                if (pr > ah.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); t = ~0ull; break; }
             }
-            if (lab < 0) {
-                const unsigned long long ak = gtag | key;
-                unsigned long long t = mix64(ak) & ah.mask;
-                for (unsigned long long pr = 0;; pr++) {
-                    const unsigned long long cur = ah.key[t];
-                    if (cur == ak) break;
-                    if (cur == 0ull) {
-                        const unsigned long long prev = atomicCAS(&ah.key[t], 0ull, ak);
-                        if (prev == 0ull) { claimed = true; break; }
-                        if (prev == ak) break;
-                    }
-                    t = (t + 1) & ah.mask;
-                    if (pr > ah.mask) { set_err(sc.ctr, DISC_ERR_TABLE_FULL); t = ~0ull; break; }
-                }
-                if (t != ~0ull) {
-                    atomicMin(&ah.val[t], (fp.jpos << 9) | m);
-                    at = (int)t;
-                }
+            if (t != ~0ull) {
+                atomicMin(&ah.val[t], (fp.jpos << 9) | m);
+                at = (int)t;
             }
         }
-        add_item_warp(sc, ((unsigned long long)m << 33) | (unsigned)lab, valid && lab >= 0);
+        add_item_warp(sc, ((unsigned long long)m << 33) | (unsigned)lab, lead && lab >= 0);
         const int li = warp_append(ah.n, claimed);
         if (claimed) ah.list[li] = at;
         const int ai = warp_append(&sc.ctr->n_absent, at >= 0);
@@ -1681,9 +1713,15 @@ int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const Ser
 }
 
 int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, const AbsentHash& ah, int S,
-                  cudaStream_t st)
+                  int probe_width, cudaStream_t st)
 {
-    k_lookup<<<dim3(152, S), 256, 0, st>>>(fps, bs, refs, ah);
+    const dim3 grid(152, S);
+    switch (probe_width) {
+        case 2: k_lookup<2><<<grid, 256, 0, st>>>(fps, bs, refs, ah); break;
+        case 4: k_lookup<4><<<grid, 256, 0, st>>>(fps, bs, refs, ah); break;
+        case 8: k_lookup<8><<<grid, 256, 0, st>>>(fps, bs, refs, ah); break;
+        default: k_lookup<1><<<grid, 256, 0, st>>>(fps, bs, refs, ah); break;
+    }
     k_absent<<<dim3(38, S), 256, 0, st>>>(fps, bs, ah);
     return 2;
 }
@@ -1719,18 +1757,23 @@ static void probe_assoc_cluster()
     }
 }
 
-static int assoc_cluster(int G)
+static int assoc_cluster(int G, int want)
 {
     int c = 1;
+    if (want > 0) {
+        while (c * 2 <= want && c * 2 <= g_assoc_max_cluster) c *= 2;
+        return c;
+    }
     while (c * 2 <= g_assoc_max_cluster && (c * 2) * G <= 152) c *= 2;
     return c;
 }
 
 size_t union_region_bytes_full() { return UNION_SMEM; }
 
-int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s)
+int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int cluster,
+                     cudaStream_t s)
 {
-    const int c = assoc_cluster(G);
+    const int c = assoc_cluster(G, cluster);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

@@ -76,9 +76,13 @@ int launch_serial_step(const FrameParams* fps, const BatchScratch& bs, const Ser
 // each of the G maps' frames in order in one CTA (k_associate); the batch's
 // new voxels into the maps (k_commit).  The absent-voxel hash is empty
 // before k_lookup and after k_commit.
+// probe_width: lanes per key in the voxel-table lookup (1, 2, 4, 8);
+// cluster: CTAs per map of the association kernel (0: as many as the maps
+// leave room for, up to 8; else 1, 2, 4 or 8, capped by the device)
 int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs* refs, const AbsentHash& ah, int S,
-                  cudaStream_t st);
-int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, cudaStream_t s);
+                  int probe_width, cudaStream_t st);
+int launch_associate(const FrameParams* fps, const BatchScratch& bs, const SerialStep& st, int G, int cluster,
+                     cudaStream_t s);
 int launch_commit(const BatchScratch& bs, const SerialStep& st, const AbsentHash& ah, int G, cudaStream_t s);
 // bytes of the union region a map keeps in global memory (SerialScratch::ureg)
 size_t union_region_bytes_full();
