@@ -197,10 +197,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "period_ms": self.period}
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from its committed ncu summary
-    (profiles/<kernel>_room_640x480.md), or None when there is none or the
-    kernel's source changed since the counters were taken."""
+def measured_traffic(kernel, frames_per_launch):
+    """DRAM bytes of one launch of `kernel` over frames_per_launch frames,
+    from its committed ncu summary (profiles/<kernel>_room_640x480.md: the
+    bytes of one captured launch over its frames, scaled per frame), or None
+    when there is none or the kernel's source changed since the counters were
+    taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}_room_640x480.md")
     try:
@@ -212,7 +214,7 @@ def measured_traffic(kernel):
         src = os.path.join(ROOT, kv["source"])
         if hashlib.sha256(open(src, "rb").read()).hexdigest() != kv["source_sha256"]:
             return None
-        return int(kv["traffic_bytes_per_launch"])
+        return int(kv["traffic_bytes_per_launch"]) / int(kv["frames_per_launch"]) * frames_per_launch
     except Exception:
         return None
 
@@ -1061,7 +1063,7 @@ def main():
     launch_ms = phases[dom]["ms"] / calls
     achieved = alg_total / (phases[dom]["ms"] / 1e3) / 1e9 if phases[dom]["ms"] > 0 and alg_total > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": measured_traffic(dom), "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": measured_traffic(dom, TB * B / calls), "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_total / calls, "launch_us": launch_ms * 1e3,
                 "launches_per_frame": calls / (TB * B)}
     # the whole step against the same peak: algorithmic bytes per frame (mean
