@@ -994,7 +994,10 @@ int enqueue_serial(Runner& r, int k, int S, int G, int J, int combos, cudaStream
     if (!(combos & COMBO_DILATE)) {
         step.j = 0;
         run_phase(r, PH_LOOKUP, st, [&] { return launch_lookup(dfp, bs, step.refs, r.ah, S, r.probe_width, st); });
-        run_phase(r, PH_ASSOCIATE, st, [&] { return launch_associate(dfp, bs, step, G, r.assoc_cluster, st); });
+        // on an SM partition (serial_sms) the chain runs one CTA per map: a
+        // cluster's CTAs must fit the partition's SMs together
+        const int cluster = r.green[0] ? 1 : r.assoc_cluster;
+        run_phase(r, PH_ASSOCIATE, st, [&] { return launch_associate(dfp, bs, step, G, cluster, st); });
         run_phase(r, PH_COMMIT, st, [&] {
             const int n = launch_commit(bs, step, r.ah, G, st);
             cudaMemsetAsync(r.ah.n, 0, sizeof(int32_t), st);  // the hash is empty again
