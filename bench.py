@@ -64,7 +64,12 @@ def parse():
     ap.add_argument("--served-repeats", type=int, default=2, help="measurements per offered rate")
     ap.add_argument("--served-frames", type=int, default=96,
                     help="frames of each served map's path; the measurements together take every frame once")
+    ap.add_argument("--batch-split", type=int, default=0,
+                    help="smaller batches per 32-frame call of the plain path (0: the library's automatic choice)")
     ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
+    ap.add_argument("--served-workers", type=int, default=2, help="batches the server runs at once")
+    ap.add_argument("--served-borrow", type=int, default=1,
+                    help="1: clients hand over pinned frames read in place; 0: the server copies each frame")
     ap.add_argument("--served-precision", type=int, default=2, help="0 fp32, 1 bf16, 2 fp8 e4m3")
     ap.add_argument("--precision", type=int, default=0,
                     help="fast pooling/scoring precision of the plain path: 0 fp32 (the Room-scale "
@@ -559,7 +564,8 @@ def run_tiny(args, torch, dev, stream, cpu):
 SERVED = "Served: {G} resident room-scale maps of mixed size (320x240..640x480, 5-60 masks, bf16 tokens, " \
          "{prec} pooling and scoring), " \
          "Poisson arrivals, integrate:query 9:1 (top-5 of 4 vectors), each map walking on along its own path " \
-         "({F} frames, none taken twice), 4 client threads, continuous batching of up to {J} frames per map per batch"
+         "({F} frames, none taken twice), 4 client threads, frame inputs {sub}, continuous batching of up to {J} " \
+         "frames per map per batch, {W} batches in flight"
 
 
 def run_served(args, torch, dev, rank):
@@ -574,10 +580,18 @@ def run_served(args, torch, dev, rank):
     frs = [sc.render(range(F)) for sc in scs]
     bf = []
     for sc, fr in zip(scs, frs):
-        t16 = torch.from_numpy(fr.tokens).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
-        bf.append([binding.host_frame(fr.depth[i], fr.labels[i], t16[i], fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy),
+        t16 = torch.from_numpy(fr.tokens).to(torch.bfloat16).view(torch.int16)
+        if args.served_borrow:
+            # the clients' frames sit in pinned host memory, read in place
+            dp = torch.from_numpy(fr.depth).pin_memory().numpy()
+            lp = torch.from_numpy(fr.labels.view(np.int16)).pin_memory().numpy().view(np.uint16)
+            tp = t16.pin_memory().numpy().view(np.uint16)
+        else:
+            dp, lp, tp = fr.depth, fr.labels, t16.numpy().view(np.uint16)
+        bf.append([binding.host_frame(dp[i], lp[i], tp[i], fr.poses[i], (sc.fx, sc.fy, sc.cx, sc.cy),
                                       fr.num_masks[i]) for i in range(F)])
-    srv = DiscServer(64 << 30, max_queue=1 << 16, max_maps=G, frames_per_map=J, embed_dim=scs[0].dim,
+    srv = DiscServer(64 << 30, max_queue=1 << 16, workers=args.served_workers, max_maps=G, frames_per_map=J,
+                     embed_dim=scs[0].dim,
                      patch_h=scs[0].patch_h, patch_w=scs[0].patch_w, max_width=max(s.width for s in scs),
                      max_height=max(s.height for s in scs), max_masks=max(s.max_masks for s in scs),
                      device=dev.index)
@@ -637,6 +651,8 @@ def run_served(args, torch, dev, rank):
                     time.sleep(d)
                 if i < 0:
                     tk.append((True, srv.submit_query(ids[g], queries[g], 5)))
+                elif args.served_borrow:
+                    tk.append((False, srv.submit_frame_borrowed(ids[g], bf[g][i])))
                 else:
                     tk.append((False, srv.submit_frame(ids[g], bf[g][i])))
             for q, t in tk:
@@ -661,6 +677,7 @@ def run_served(args, torch, dev, rank):
                     "refused": len(fail), "refused_codes": sorted(set(fail))[:5],
                     "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "frames": rep["frames"],
                     "queries": rep["queries"], "batches": rep["batches"],
+                    "worker_busy": rep["busy_ms"] / (1e3 * wall * max(args.served_workers, 1)),
                     "frames_per_batch": rep["frames"] / max(rep["batches"], 1),
                     "new_voxels_per_frame": float(np.mean(newv)) if newv else 0.0})
     srv.close()
@@ -672,7 +689,8 @@ def run_served(args, torch, dev, rank):
         got = [o["frames_per_s"] for o in out if o["offered_frames_per_s"] == rate]
         if got and float(np.median(got)) >= 0.95 * rate:
             knee = rate
-    return {"workload": SERVED.format(G=G, F=F, J=J, prec=prec), "rates": out, "knee_offered_frames_per_s": knee,
+    sub = "borrowed from pinned host memory" if args.served_borrow else "copied at submission"
+    return {"workload": SERVED.format(G=G, F=F, J=J, prec=prec, W=args.served_workers, sub=sub), "rates": out, "knee_offered_frames_per_s": knee,
             "repeats": args.served_repeats}
 
 
@@ -820,6 +838,7 @@ def main():
                           WORKLOAD.replace(", FP32", ", %s fast pooling and scoring (fp32 tokens)" %
                                            ("BF16", "FP8 E4M3")[args.precision - 1]),
                           "frames_per_step": B, "frames_timed": K * B,
+                          "batch_split": args.batch_split or "automatic",
                           "trajectory_frames": core["n_render"],
                           "l2": "flushed between timed steps (258 MB write)", "replicas": world},
                "voxel_updates_per_s": core["updates"] * world / (total_ms / 1e3),
@@ -858,6 +877,12 @@ def main():
     tokens = torch.from_numpy(fr.tokens).to(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
+    def plain_map(c):
+        m = DiscMap(**c)
+        if args.batch_split:
+            m.set_schedule(batch_split=args.batch_split)
+        return m
+
     def frame_array(lo, hi, on_device=True, host=None):
         n = hi - lo
         arr = (binding.Frame * n)()
@@ -884,7 +909,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    gmap = DiscMap(**cfg)
+    gmap = plain_map(cfg)
     for s in range(Wm):
         rc = gmap.integrate_frames_raw(steps[s], B, stats)
         assert rc == 0, rc
@@ -1085,7 +1110,7 @@ def main():
         hl = torch.from_numpy(fr.labels.view(np.int16)).pin_memory()
         ht = torch.from_numpy(fr.tokens).pin_memory()
         hsteps = [frame_array(s * B, (s + 1) * B, on_device=False, host=(hd, hl, ht)) for s in range(Wm + K)]
-        m2 = DiscMap(**cfg)
+        m2 = plain_map(cfg)
         for s in range(Wm):
             assert m2.integrate_frames_raw(hsteps[s], B, stats) == 0
         torch.cuda.synchronize()
@@ -1103,7 +1128,7 @@ def main():
         # the same K steps as one call (a trajectory handed over at once): the
         # copies of batch b + 1 overlap the kernels of batch b
         m2.close()
-        m3 = DiscMap(**cfg)
+        m3 = plain_map(cfg)
         for s in range(Wm):
             assert m3.integrate_frames_raw(hsteps[s], B, stats) == 0
         allf = frame_array(Wm * B, (Wm + K) * B, on_device=False, host=(hd, hl, ht))

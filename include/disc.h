@@ -246,35 +246,40 @@ void disc_group_destroy(disc_group* group); /* NULL-safe */
 
 /* ---- Serving: a request loop over many resident maps ----------------------
  * Clients (any host threads) submit integrate and query requests for maps the
- * server holds resident on the device.  A worker thread batches continuously:
- * each batch takes, for up to group.max_maps maps with work (oldest request
+ * server holds resident on the device.  Worker threads batch continuously,
+ * each with a group of its own: a worker's batch takes, for up to
+ * group.max_maps maps with work that no other batch holds (oldest request
  * first), the leading frames of each map's queue (up to
  * group.frames_per_map, stopping at the map's first query) and runs them as
- * one group call; requests arriving meanwhile join the next batch.  A query
+ * one group call; requests arriving meanwhile join a later batch.  With two
+ * workers one batch's input copies and stateless kernels run while the other
+ * batch's frame chain computes.  A map is in one batch at a time and a query
  * runs after the frames submitted before it on the same map and before those
  * after it, so every result equals the one of the same requests served alone.
- * Maps are admitted while the device memory of the group scratch and all open
- * maps stays within hbm_budget_bytes (the paper has no counterpart of this
- * layer). */
+ * Maps are admitted while the device memory of the workers' group scratch and
+ * all open maps stays within hbm_budget_bytes (the paper has no counterpart
+ * of this layer). */
 typedef struct disc_server disc_server; /* opaque */
 
 typedef struct {
     disc_group_config group;  /* batch shape and limits of every map */
     int64_t hbm_budget_bytes; /* admission limit for the group scratch plus the open maps */
     int32_t max_queue;        /* requests queued or running at most; more: DISC_ERR_BUDGET */
+    int32_t workers;          /* batches in flight at once, 1..4 (0: 2) */
 } disc_server_config;
 
 typedef struct {
     int64_t frames, queries, batches; /* completed since creation or the last reset */
     int64_t pending;                  /* requests queued or running */
-    int64_t resident_bytes;           /* group scratch + open maps at admission */
-    double busy_ms;                   /* host time inside batches */
+    int64_t resident_bytes;           /* the workers' group scratch + open maps at admission */
+    double busy_ms;                   /* host time inside batches, summed over the workers */
     double wall_ms;                   /* since creation or the last reset */
     double p50_ms, p99_ms;            /* frame latency, submission to completion */
 } disc_server_report;
 
-/* Creates the server and its worker thread.  DISC_ERR_BUDGET when the group
- * scratch alone passes the budget. */
+/* Creates the server, its worker threads and their groups.  DISC_ERR_BUDGET
+ * when the groups' scratch alone passes the budget; DISC_ERR_INVALID_ARG for
+ * workers outside 0..4. */
 disc_status disc_server_create(const disc_server_config* cfg, disc_server** out_server);
 
 /* Opens a map (cfg's embed_dim, patch grid and device equal to the group's;
@@ -293,6 +298,14 @@ disc_map* disc_server_map(disc_server* server, int32_t map_id);
  * are copied before the call returns.  *ticket identifies the request. */
 disc_status disc_server_submit_frame(disc_server* server, int32_t map_id, const disc_frame* frame,
                                      int64_t* ticket);
+
+/* As disc_server_submit_frame, but the inputs are not copied: the batch that
+ * takes the frame reads the caller's buffers in place (device memory, or host
+ * memory: pinned memory lets the copies run asynchronously).  They must stay
+ * allocated and unchanged until disc_server_wait has returned for the
+ * ticket. */
+disc_status disc_server_submit_frame_borrowed(disc_server* server, int32_t map_id, const disc_frame* frame,
+                                              int64_t* ticket);
 
 /* Queues a top-k query: queries [nq][D] host memory, copied before return. */
 disc_status disc_server_submit_query(disc_server* server, int32_t map_id, const float* queries, int32_t nq,
@@ -387,14 +400,19 @@ disc_status disc_debug_gemm_stall(int32_t device, int32_t on);
  * kernels per frame of maps with the neighbourhood overlap; how many lanes
  * look one voxel up in the table together (warp-cooperative probing: each
  * round a group of probe_width lanes reads that many consecutive slots of the
- * probe sequence); and how many CTAs (a thread-block cluster) carry one map's
- * frames in the association kernel.  None changes any result. */
+ * probe sequence); how many CTAs (a thread-block cluster) carry one map's
+ * frames in the association kernel; and into how many smaller batches a call
+ * whose frames fit one batch is cut, so that each smaller batch's stateless
+ * kernels run beside the frame chain of the one before it.  None changes any
+ * result. */
 typedef struct {
     int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 4) */
     int32_t serial_ctas;     /* serial kernels' CTAs in quarters of the default count, 1..32 (default 4) */
     int32_t probe_width;     /* lanes per key of the voxel-table lookup: 1, 2, 4 or 8 (0 or 1: one lane) */
     int32_t assoc_cluster;   /* CTAs per map in the association kernel: 0 (as many as the batch's maps leave
                                 SMs for, up to 8), or 1, 2, 4, 8 (capped by what the device co-schedules) */
+    int32_t batch_split;     /* smaller batches per call that fits one batch: 0 (2 for one map's calls of 16
+                                frames or more, else 1), or 1, 2, 4, 8; each keeps at least 4 frames */
 } disc_schedule;
 
 typedef struct {
@@ -408,8 +426,9 @@ disc_status disc_map_set_schedule(disc_map* map, const disc_schedule* schedule);
 disc_status disc_group_set_schedule(disc_group* group, const disc_schedule* schedule);
 
 /* Autotuner: times each candidate schedule (geometry_chunk in {2, 4, 8} x
- * probe_width in {1, 2, 4} x assoc_cluster automatic or half of it) on the
- * sample frames, integrated into fresh maps
+ * probe_width in {1, 2, 4} x assoc_cluster automatic or half of it, then the
+ * fastest of these with batch_split at each of {1, 2, 4} other than the
+ * automatic one) on the sample frames, integrated into fresh maps
  * with the given maps' configurations (created and destroyed here; the given
  * maps are not changed), two untimed passes then `reps` timed ones, and keeps
  * the fastest for the map or group.  report may be NULL. */

@@ -59,7 +59,8 @@ class GroupConfig(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32), ("probe_width", c_i32), ("assoc_cluster", c_i32)]
+    _fields_ = [("geometry_chunk", c_i32), ("serial_ctas", c_i32), ("probe_width", c_i32), ("assoc_cluster", c_i32),
+                ("batch_split", c_i32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -68,12 +69,13 @@ class TuneReport(ctypes.Structure):
     def as_dict(self):
         return {"geometry_chunk": int(self.best.geometry_chunk), "serial_ctas": int(self.best.serial_ctas),
                 "probe_width": int(self.best.probe_width), "assoc_cluster": int(self.best.assoc_cluster),
+                "batch_split": int(self.best.batch_split),
                 "best_ms": float(self.best_ms), "default_ms": float(self.default_ms),
                 "candidates": int(self.candidates)}
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("group", GroupConfig), ("hbm_budget_bytes", c_i64), ("max_queue", c_i32)]
+    _fields_ = [("group", GroupConfig), ("hbm_budget_bytes", c_i64), ("max_queue", c_i32), ("workers", c_i32)]
 
 
 class ServerReport(ctypes.Structure):
@@ -174,6 +176,7 @@ def lib():
         L.disc_server_map.argtypes = [c_vp, c_i32]
         L.disc_server_map.restype = c_vp
         L.disc_server_submit_frame.argtypes = [c_vp, c_i32, P(Frame), P(c_i64)]
+        L.disc_server_submit_frame_borrowed.argtypes = [c_vp, c_i32, P(Frame), P(c_i64)]
         L.disc_server_submit_query.argtypes = [c_vp, c_i32, c_vp, c_i32, c_i32, P(c_i64)]
         L.disc_server_wait.argtypes = [c_vp, c_i64, P(Stats), c_vp, c_vp, P(c_f64)]
         L.disc_server_stats.argtypes = [c_vp, P(ServerReport)]
@@ -367,9 +370,9 @@ class DiscMap:
         """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
         return lib().disc_integrate_frames(self._h, arr, n, stats, None)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0):
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
-                                                                          assoc_cluster))),
+                                                                          assoc_cluster, batch_split))),
                "disc_map_set_schedule")
 
     def autotune(self, frames, reps=3) -> dict:
@@ -537,9 +540,9 @@ class DiscGroup:
             if stats_arrays is not None else None
         return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0):
+    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
-                                                                            assoc_cluster))),
+                                                                            assoc_cluster, batch_split))),
                "disc_group_set_schedule")
 
     def autotune(self, maps, frame_arrays, counts, reps=3) -> dict:
@@ -596,13 +599,14 @@ class DiscGroup:
 class DiscServer:
     """Request loop over resident maps (disc_server_create ... disc_server_destroy)."""
 
-    def __init__(self, hbm_budget_bytes, max_queue=4096, **group):
+    def __init__(self, hbm_budget_bytes, max_queue=4096, workers=0, **group):
         c = ServerConfig()
         lib().disc_group_config_default(ctypes.byref(c.group))
         for k, v in group.items():
             setattr(c.group, k, v)
         c.hbm_budget_bytes = int(hbm_budget_bytes)
         c.max_queue = int(max_queue)
+        c.workers = int(workers)
         h = c_vp()
         _check(lib().disc_server_create(ctypes.byref(c), ctypes.byref(h)), "disc_server_create")
         self._h = h
@@ -647,6 +651,16 @@ class DiscServer:
         t = c_i64(0)
         _check(lib().disc_server_submit_frame(self._h, map_id, ctypes.byref(fr), ctypes.byref(t)),
                "disc_server_submit_frame")
+        return int(t.value)
+
+    def submit_frame_borrowed(self, map_id: int, frame) -> int:
+        """Queue a frame whose buffers the server reads in place: they (the
+        keepalive of `frame` included) must stay unchanged until the ticket's
+        wait returns."""
+        fr, _keep = frame
+        t = c_i64(0)
+        _check(lib().disc_server_submit_frame_borrowed(self._h, map_id, ctypes.byref(fr), ctypes.byref(t)),
+               "disc_server_submit_frame_borrowed")
         return int(t.value)
 
     def submit_frame_raw(self, map_id: int, fr) -> int:

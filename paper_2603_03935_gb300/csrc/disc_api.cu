@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include <cuda.h>
@@ -151,6 +152,7 @@ struct Runner {
     int cta_scale = 4;                // serial kernels' CTAs in quarters of the default count
     int probe_width = 1;              // lanes per key of the batch's voxel-table lookup
     int assoc_cluster = 0;            // CTAs per map of the association kernel (0: automatic)
+    int batch_split = 0;              // smaller batches per call that fits one (0: automatic)
     bool graphs_off = false;
     std::map<long long, BatchGraph> graphs;
     std::map<long long, int> shapes_seen;  // batch shapes launched directly so far
@@ -244,9 +246,12 @@ bool config_ok(const disc_map_config& c)
 }
 
 // kernel attributes (dynamic shared memory above 48 KB), once per process
+// (maps and groups may be created from several host threads at once)
 disc_status set_kernel_attrs()
 {
+    static std::mutex mu;
     static bool done = false;
+    std::lock_guard<std::mutex> lk(mu);
     if (done) return DISC_OK;
     cudaError_t e = set_feature_kernel_attrs(200 * 1024);
     if (e == cudaSuccess) e = set_gemm_kernel_attrs();
@@ -1392,10 +1397,13 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         total += wk.valid;
         most = std::max(most, wk.valid);
     }
-    // frames per map per batch: a call of one map that fits in one batch of
-    // 16 frames or more runs as two half batches, so that the second half's
-    // stateless kernels overlap the first half's frame chain
-    const int Jb = (!r.timing && w.size() == 1 && most >= 16 && most <= r.Jmax) ? (most + 1) / 2 : r.Jmax;
+    // frames per map per batch: a call that fits in one batch runs as
+    // batch_split smaller batches of at least 4 frames (automatic: two for one
+    // map's call of 16 frames or more, one for a group's), so that each one's
+    // stateless kernels overlap the frame chain of the one before
+    int pieces = r.batch_split > 0 ? r.batch_split : (w.size() == 1 && total >= 16 ? 2 : 1);
+    pieces = std::min(pieces, std::max(1, total / 4));
+    const int Jb = (!r.timing && pieces > 1 && most <= r.Jmax) ? (most + pieces - 1) / pieces : r.Jmax;
     const int nbatch = (most + Jb - 1) / Jb;
     disc_status s = ensure_hist(r, std::max(total, 1));
     if (s != DISC_OK) return s;
@@ -2052,14 +2060,17 @@ disc_status set_schedule(Runner& r, const disc_schedule* sch)
     if (pw != 1 && pw != 2 && pw != 4 && pw != 8) return DISC_ERR_INVALID_ARG;
     const int ac = sch->assoc_cluster;
     if (ac != 0 && ac != 1 && ac != 2 && ac != 4 && ac != 8) return DISC_ERR_INVALID_ARG;
+    const int bsp = sch->batch_split;
+    if (bsp != 0 && bsp != 1 && bsp != 2 && bsp != 4 && bsp != 8) return DISC_ERR_INVALID_ARG;
     if (r.geo_chunk == sch->geometry_chunk && r.cta_scale == sch->serial_ctas && r.probe_width == pw &&
-        r.assoc_cluster == ac)
+        r.assoc_cluster == ac && r.batch_split == bsp)
         return DISC_OK;
     CK(cudaStreamSynchronize(r.stream));
     r.geo_chunk = sch->geometry_chunk;
     r.cta_scale = sch->serial_ctas;
     r.probe_width = pw;
     r.assoc_cluster = ac;
+    r.batch_split = bsp;
     for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);  // captured with the old schedule
     r.graphs.clear();
     r.shapes_seen.clear();
@@ -2073,27 +2084,16 @@ disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
                      const std::vector<std::pair<const disc_frame*, int>>& frames, int reps, disc_tune_report* out)
 {
     if (reps < 1 || reps > 100) return DISC_ERR_INVALID_ARG;
-    const disc_schedule keep{r.geo_chunk, r.cta_scale, r.probe_width, r.assoc_cluster};
+    const disc_schedule keep{r.geo_chunk, r.cta_scale, r.probe_width, r.assoc_cluster, r.batch_split};
     disc_tune_report rep{};
     rep.best_ms = 1e300;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     disc_status s = DISC_OK;
-    // frames per geometry launch x lanes per key of the lookup x CTAs per
-    // map of the association kernel (automatic, or the next smaller cluster)
-    const int auto_c = 0;
-    std::vector<disc_schedule> cands;
-    for (int geo : {4, 2, 8})  // the default first
-        for (int pw : {1, 2, 4})
-            for (int ac : {auto_c, -1}) cands.push_back(disc_schedule{geo, r.cta_scale, pw, ac});
-    for (disc_schedule cand : cands) {
-        if (cand.assoc_cluster < 0) {  // half the automatic cluster of these maps
-            int c = 1;
-            while (c * 2 <= 8 && (c * 2) * (int)cfgs.size() <= 152) c *= 2;
-            if (c == 1) continue;
-            cand.assoc_cluster = c / 2;
-        }
+    // one candidate's best time over the timed passes
+    auto time_schedule = [&](const disc_schedule& cand) -> double {
+        if (s != DISC_OK) return 1e300;  // an earlier candidate failed
         s = set_schedule(r, &cand);
         double best = 1e300;
         for (int pass = 0; pass < reps + 2 && s == DISC_OK; pass++) {
@@ -2118,13 +2118,39 @@ disc_status autotune(Runner& r, const std::vector<const disc_map_config*>& cfgs,
             }
             for (disc_map* m : maps) disc_map_destroy(m);
         }
-        if (s != DISC_OK) break;
-        rep.candidates++;
-        if (cand.geometry_chunk == 4 && cand.probe_width == 1 && cand.assoc_cluster == 0) rep.default_ms = best;
-        if (best < rep.best_ms) {
-            rep.best_ms = best;
-            rep.best = cand;
+        if (s == DISC_OK) {
+            rep.candidates++;
+            if (best < rep.best_ms) {
+                rep.best_ms = best;
+                rep.best = cand;
+            }
         }
+        return best;
+    };
+    // frames per geometry launch x lanes per key of the lookup x CTAs per
+    // map of the association kernel (automatic, or the next smaller cluster),
+    // the automatic batch split
+    for (int geo : {4, 2, 8})  // the default first
+        for (int pw : {1, 2, 4})
+            for (int ac : {0, -1}) {
+                disc_schedule cand{geo, r.cta_scale, pw, ac, 0};
+                if (ac < 0) {  // half the automatic cluster of these maps
+                    int c = 1;
+                    while (c * 2 <= 8 && (c * 2) * (int)cfgs.size() <= 152) c *= 2;
+                    if (c == 1) continue;
+                    cand.assoc_cluster = c / 2;
+                }
+                const double ms = time_schedule(cand);
+                if (geo == 4 && pw == 1 && ac == 0) rep.default_ms = ms;
+            }
+    // then the fastest of these with each other batch split
+    const int auto_split = cfgs.size() == 1 ? 2 : 1;
+    const disc_schedule base = rep.best;
+    for (int bsp : {1, 2, 4}) {
+        if (bsp == auto_split) continue;
+        disc_schedule cand = base;
+        cand.batch_split = bsp;
+        time_schedule(cand);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -2,14 +2,16 @@
 // integrate and query requests from any host thread, continuous batching.
 //
 // Host orchestration only.  Every request is queued on its map in arrival
-// order.  One worker thread repeatedly forms a batch from what is pending:
-// for each map with work (oldest first, up to the group's maps per batch) the
-// leading frames of its queue up to the group's frames per map, stopping at
-// the map's first query.  Queries at the head of a queue run first, so a
-// query sees exactly the frames submitted before it.  The batch runs as one
-// group call (every kernel spans all its maps); requests that arrive
-// meanwhile join the next batch.  Maps are admitted against a device-memory
-// budget.
+// order.  Worker threads, each with a group of its own, repeatedly form a
+// batch from what is pending: for each map with work that no other batch
+// holds (oldest first, up to the group's maps per batch) the leading frames
+// of its queue up to the group's frames per map, stopping at the map's first
+// query.  Queries at the head of a queue run first, so a query sees exactly
+// the frames submitted before it.  The batch runs as one group call (every
+// kernel spans all its maps); requests that arrive meanwhile join a later
+// batch.  With two workers, one batch's host work, input copies and
+// stateless kernels overlap the other's frame chain.  Maps are admitted
+// against a device-memory budget.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -57,14 +59,14 @@ struct MapSlot {
     bool closing = false;
     int64_t bytes = 0;
     std::deque<Request> queue;
-    int64_t busy = 0;  // requests of this map inside the running batch
+    int64_t busy = 0;  // requests of this map inside a running batch (of one worker at a time)
 };
 
 }  // namespace
 
 struct disc_server {
     disc_server_config cfg;
-    disc_group* group = nullptr;
+    std::vector<disc_group*> groups;  // one per worker
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::vector<MapSlot> maps;
@@ -73,7 +75,7 @@ struct disc_server {
     int64_t pending = 0;
     int64_t resident = 0;  // device bytes: group scratch + open maps
     bool stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;
     // pinned staging blocks for frame inputs, reused
     std::vector<std::pair<unsigned char*, size_t>> free_blocks;
     // statistics
@@ -125,9 +127,13 @@ void finish(disc_server* s, const Request& r, disc_status st, const disc_frame_s
     }
 }
 
-void worker_loop(disc_server* s)
+// a map whose queue has work and that no batch holds
+bool takeable(const MapSlot& ms) { return ms.busy == 0 && !ms.queue.empty(); }
+
+void worker_loop(disc_server* s, int wi)
 {
     const int G = s->cfg.group.max_maps, J = s->cfg.group.frames_per_map;
+    disc_group* group = s->groups[wi];
     cudaSetDevice(s->cfg.group.device);
     while (true) {
         std::vector<int> gl;                       // maps of the batch
@@ -138,12 +144,21 @@ void worker_loop(disc_server* s)
         std::vector<disc_map*> qmaps;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || s->pending > 0; });
+            // work on a map that another worker's batch holds waits for that
+            // batch (its finish wakes the workers)
+            s->cv_work.wait(lk, [&] {
+                if (s->stop && s->pending == 0) return true;
+                for (const MapSlot& ms : s->maps)
+                    if (takeable(ms)) return true;
+                return false;
+            });
             if (s->stop && s->pending == 0) return;
+            std::vector<char> free(s->maps.size());
+            for (int i = 0; i < (int)s->maps.size(); i++) free[i] = s->maps[i].busy == 0;
             // queries at the head of a queue run before the batch
             for (int i = 0; i < (int)s->maps.size(); i++) {
                 MapSlot& ms = s->maps[i];
-                while (!ms.queue.empty() && ms.queue.front().is_query) {
+                while (free[i] && !ms.queue.empty() && ms.queue.front().is_query) {
                     queries.push_back({i, std::move(ms.queue.front())});
                     qmaps.push_back(ms.m);
                     ms.queue.pop_front();
@@ -153,7 +168,7 @@ void worker_loop(disc_server* s)
             // maps with frames waiting, oldest head first
             std::vector<std::pair<Clock::time_point, int>> order;
             for (int i = 0; i < (int)s->maps.size(); i++)
-                if (!s->maps[i].queue.empty() && !s->maps[i].queue.front().is_query)
+                if (free[i] && !s->maps[i].queue.empty() && !s->maps[i].queue.front().is_query)
                     order.push_back({s->maps[i].queue.front().t_submit, i});
             std::sort(order.begin(), order.end());
             for (auto& o : order) {
@@ -170,7 +185,8 @@ void worker_loop(disc_server* s)
                 frames.push_back(std::move(fr));
             }
         }
-        // queries (the maps' earlier frames are complete: batches are synchronous)
+        // queries (the maps' earlier frames are complete: a map is in one
+        // batch at a time and batches are synchronous)
         for (size_t qi = 0; qi < queries.size(); qi++) {
             auto& qr = queries[qi];
             const Request& r = qr.second;
@@ -182,7 +198,10 @@ void worker_loop(disc_server* s)
             s->maps[qr.first].busy--;
             s->pending--;
         }
-        if (!queries.empty()) s->cv_done.notify_all();
+        if (!queries.empty()) {
+            s->cv_done.notify_all();
+            s->cv_work.notify_all();  // their maps are free again
+        }
         if (gl.empty()) continue;
         // the batch: one group call over all its maps
         const int n = (int)gl.size();
@@ -200,7 +219,7 @@ void worker_loop(disc_server* s)
         }
         const auto tb = Clock::now();
         const disc_status gst =
-            disc_group_integrate(s->group, mp.data(), n, fptr.data(), cnt.data(), sptr.data(), done.data());
+            disc_group_integrate(group, mp.data(), n, fptr.data(), cnt.data(), sptr.data(), done.data());
         const double ms = std::chrono::duration<double, std::milli>(Clock::now() - tb).count();
         {
             // frames before a map's first failure are done, the failing frame
@@ -233,6 +252,7 @@ void worker_loop(disc_server* s)
             }
         }
         s->cv_done.notify_all();
+        s->cv_work.notify_all();  // the batch's maps are free for any worker
     }
 }
 
@@ -244,22 +264,28 @@ disc_status disc_server_create(const disc_server_config* cfg, disc_server** out)
 {
     if (!cfg || !out) return DISC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (cfg->max_queue <= 0 || cfg->hbm_budget_bytes <= 0) return DISC_ERR_INVALID_ARG;
+    if (cfg->max_queue <= 0 || cfg->hbm_budget_bytes <= 0 || cfg->workers < 0 || cfg->workers > 4)
+        return DISC_ERR_INVALID_ARG;
     disc_server* s = new disc_server();
     s->cfg = *cfg;
-    disc_status st = disc_group_create(&cfg->group, &s->group);
+    if (s->cfg.workers == 0) s->cfg.workers = 2;
+    disc_status st = DISC_OK;
+    for (int i = 0; i < s->cfg.workers && st == DISC_OK; i++) {
+        disc_group* g = nullptr;
+        st = disc_group_create(&cfg->group, &g);
+        if (st == DISC_OK) {
+            s->groups.push_back(g);
+            s->resident += disc_group_device_bytes(g);
+        }
+    }
+    if (st == DISC_OK && s->resident > cfg->hbm_budget_bytes) st = DISC_ERR_BUDGET;
     if (st != DISC_OK) {
+        for (disc_group* g : s->groups) disc_group_destroy(g);
         delete s;
         return st;
     }
-    s->resident = disc_group_device_bytes(s->group);
-    if (s->resident > cfg->hbm_budget_bytes) {
-        disc_group_destroy(s->group);
-        delete s;
-        return DISC_ERR_BUDGET;
-    }
     s->t0 = Clock::now();
-    s->worker = std::thread(worker_loop, s);
+    for (int i = 0; i < s->cfg.workers; i++) s->workers.emplace_back(worker_loop, s, i);
     *out = s;
     return DISC_OK;
 }
@@ -335,10 +361,35 @@ disc_status disc_server_close_map(disc_server* s, int32_t map_id)
     return DISC_OK;
 }
 
-disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_frame* f, int64_t* ticket)
+}  // extern "C"
+
+namespace {
+
+// Queue one frame.  borrow: the request keeps the caller's pointers (read
+// when its batch runs); otherwise the inputs are copied into a pinned block
+// of the server now.
+disc_status submit_frame(disc_server* s, int32_t map_id, const disc_frame* f, int64_t* ticket, bool borrow)
 {
     if (!s || !f || !ticket || !f->depth || !f->labels || !f->tokens || f->width <= 0 || f->height <= 0)
         return DISC_ERR_INVALID_ARG;
+    if (borrow) {
+        Request r;
+        r.t_submit = Clock::now();
+        r.frame = *f;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (map_id < 0 || map_id >= (int)s->maps.size() || !s->maps[map_id].open || s->maps[map_id].closing)
+                return DISC_ERR_INVALID_ARG;
+            if (s->pending >= s->cfg.max_queue) return DISC_ERR_BUDGET;
+            r.ticket = s->next_ticket++;
+            *ticket = r.ticket;
+            s->results[r.ticket];
+            s->maps[map_id].queue.push_back(std::move(r));
+            s->pending++;
+        }
+        s->cv_work.notify_one();
+        return DISC_OK;
+    }
     const disc_group_config& g = s->cfg.group;
     if (cudaSetDevice(g.device) != cudaSuccess) {
         cudaGetLastError();
@@ -403,6 +454,20 @@ disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_
     }
     s->cv_work.notify_one();
     return DISC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+disc_status disc_server_submit_frame(disc_server* s, int32_t map_id, const disc_frame* f, int64_t* ticket)
+{
+    return submit_frame(s, map_id, f, ticket, false);
+}
+
+disc_status disc_server_submit_frame_borrowed(disc_server* s, int32_t map_id, const disc_frame* f, int64_t* ticket)
+{
+    return submit_frame(s, map_id, f, ticket, true);
 }
 
 disc_status disc_server_submit_query(disc_server* s, int32_t map_id, const float* q, int32_t nq, int32_t k,
@@ -495,10 +560,11 @@ void disc_server_destroy(disc_server* s)
         s->stop = true;
     }
     s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (std::thread& t : s->workers)
+        if (t.joinable()) t.join();
     for (MapSlot& ms : s->maps)
         if (ms.m) disc_map_destroy(ms.m);
-    disc_group_destroy(s->group);
+    for (disc_group* g : s->groups) disc_group_destroy(g);
     for (auto& b : s->free_blocks) cudaFreeHost(b.first);
     delete s;
 }

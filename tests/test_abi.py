@@ -158,3 +158,16 @@ def test_checkpoints_with_bad_contents_are_refused_before_any_allocation(libdisc
         for magic, change in ((b"DISCMAP1", {}), (b"DISCMAPF", dict(ids=[0, -1, 1]))):
             rc, h = load(magic, **change)
             assert rc != -1 and h is None, (magic, change)
+
+
+def test_server_worker_count_is_checked_before_any_device_use(libdisc):
+    from paper_2603_03935_gb300 import binding as b
+    L = b.lib()
+    for workers in (-1, 5):
+        c = b.ServerConfig()
+        L.disc_group_config_default(ctypes.byref(c.group))
+        c.hbm_budget_bytes = 1 << 30
+        c.max_queue = 16
+        c.workers = workers
+        h = ctypes.c_void_p()
+        assert L.disc_server_create(ctypes.byref(c), ctypes.byref(h)) == -1 and h.value is None

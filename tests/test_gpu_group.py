@@ -178,17 +178,19 @@ def test_schedules_leave_results_unchanged_and_autotune_picks_one(torch_dev):
     omap = oracle.OracleMap(**common.to_oracle_cfg(common.disc_cfg(sc)))
     for i in range(16):
         omap.integrate(*oracle.frame_args(fr, i))
-    for geo, q, pw, ac in ((4, 4, 1, 0), (1, 1, 2, 1), (2, 8, 4, 2), (8, 2, 8, 8), (32, 32, 1, 4)):
-        m = DiscMap(**common.disc_cfg(sc, batch_frames=8))
-        m.set_schedule(geo, q, pw, ac)
-        _, done, rc = m.integrate_frames(frames)
-        assert rc == 0 and done == 16
-        common.compare_maps(m, omap, ctx=f"schedule {geo}/{q}/{pw}/{ac}")
+    for geo, q, pw, ac, bsp in ((4, 4, 1, 0, 0), (1, 1, 2, 1, 1), (2, 8, 4, 2, 2), (8, 2, 8, 8, 4),
+                                (32, 32, 1, 4, 8)):
+        for bf in (8, 16):  # a call of 16 frames: two batches, or one cut into bsp
+            m = DiscMap(**common.disc_cfg(sc, batch_frames=bf))
+            m.set_schedule(geo, q, pw, ac, bsp)
+            _, done, rc = m.integrate_frames(frames)
+            assert rc == 0 and done == 16
+            common.compare_maps(m, omap, ctx=f"schedule {geo}/{q}/{pw}/{ac}/{bsp}, batches of {bf}")
     m = DiscMap(**common.disc_cfg(sc, batch_frames=8))
     rep = m.autotune(frames[:8], reps=1)
-    assert rep["candidates"] == 18 and rep["best_ms"] <= rep["default_ms"]
+    assert rep["candidates"] == 20 and rep["best_ms"] <= rep["default_ms"]
     assert rep["geometry_chunk"] in (2, 4, 8) and rep["probe_width"] in (1, 2, 4)
-    assert rep["assoc_cluster"] in (0, 4)
+    assert rep["assoc_cluster"] in (0, 4) and rep["batch_split"] in (0, 1, 4)
     assert m.counts()[0] == 0
     _, done, rc = m.integrate_frames(frames)
     assert rc == 0
@@ -202,7 +204,7 @@ def test_schedules_leave_results_unchanged_and_autotune_picks_one(torch_dev):
     for i in range(4):
         arr[i] = frames[i][0]
     grep = grp.autotune([a, b], [arr, arr], [4, 4], reps=1)
-    assert grep["candidates"] == 18 and a.counts()[0] == 0 and b.counts()[0] == 0
+    assert grep["candidates"] == 20 and a.counts()[0] == 0 and b.counts()[0] == 0
     _, done, rc = grp.integrate([a, b], [frames, frames])
     assert rc == 0 and done == [16, 16]
     common.compare_maps(a, omap, ctx="tuned group, map a")

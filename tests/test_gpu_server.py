@@ -47,13 +47,13 @@ def _scenes():
     return [a, b, c, d]
 
 
-def _server(scs, budget=8 << 30, **kw):
+def _server(scs, budget=8 << 30, workers=0, **kw):
     from paper_2603_03935_gb300 import DiscServer
     g = dict(max_maps=len(scs), frames_per_map=2, embed_dim=scs[0].dim, patch_h=scs[0].patch_h,
              patch_w=scs[0].patch_w, max_width=max(s.width for s in scs), max_height=max(s.height for s in scs),
              max_masks=max(s.max_masks for s in scs))
     g.update(kw)
-    return DiscServer(budget, **g)
+    return DiscServer(budget, workers=workers, **g)
 
 
 def _same_map(a, b, ctx):
@@ -67,12 +67,16 @@ def _same_map(a, b, ctx):
     assert np.array_equal(ea["Q"].view(np.uint32), eb["Q"].view(np.uint32)), f"{ctx}: Q"
 
 
-def test_concurrent_clients_equal_each_map_alone(torch_dev):
+@pytest.mark.parametrize("workers,borrow", [(1, False), (2, False), (4, False), (2, True)])
+def test_concurrent_clients_equal_each_map_alone(torch_dev, workers, borrow):
+    # with several workers, batches of different maps run at once; a map is
+    # in one batch at a time, so every result still equals the map alone;
+    # borrowed frames are read in place when their batch runs
     from paper_2603_03935_gb300 import DiscMap
     scs = _scenes()
     nfr = [20, 14, 12, 10]
     frs = [s.render(range(n)) for s, n in zip(scs, nfr)]
-    srv = _server(scs)
+    srv = _server(scs, workers=workers)
     ids = [srv.open_map(**common.disc_cfg(s)) for s in scs]
     queries = [fr.tokens[0][:3] for fr in frs]  # three patch tokens of each map's first frame
     q_at = [n // 2 for n in nfr]                # each map is queried after half its frames
@@ -81,8 +85,13 @@ def test_concurrent_clients_equal_each_map_alone(torch_dev):
     def client(g):
         tickets = []
         tq = None
+        held = []  # borrowed inputs stay alive until their waits return
         for i in range(nfr[g]):
-            tickets.append(srv.submit_frame(ids[g], _hframe(frs[g], i)))
+            if borrow:
+                held.append(_hframe(frs[g], i))
+                tickets.append(srv.submit_frame_borrowed(ids[g], held[-1]))
+            else:
+                tickets.append(srv.submit_frame(ids[g], _hframe(frs[g], i)))
             if i + 1 == q_at[g]:
                 tq = srv.submit_query(ids[g], queries[g], 3)
         stats = [srv.wait_frame(t) for t in tickets]
