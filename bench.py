@@ -66,6 +66,8 @@ def parse():
                     help="frames of each served map's path; the measurements together take every frame once")
     ap.add_argument("--batch-split", type=int, default=0,
                     help="smaller batches per 32-frame call of the plain path (0: the library's automatic choice)")
+    ap.add_argument("--assoc-cluster", type=int, default=0,
+                    help="CTAs per map of the plain path's association kernel (0: automatic)")
     ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
     ap.add_argument("--served-workers", type=int, default=2, help="batches the server runs at once")
     ap.add_argument("--served-borrow", type=int, default=1,
@@ -839,6 +841,7 @@ def main():
                                            ("BF16", "FP8 E4M3")[args.precision - 1]),
                           "frames_per_step": B, "frames_timed": K * B,
                           "batch_split": args.batch_split or "automatic",
+                          "assoc_cluster": args.assoc_cluster or "automatic",
                           "trajectory_frames": core["n_render"],
                           "l2": "flushed between timed steps (258 MB write)", "replicas": world},
                "voxel_updates_per_s": core["updates"] * world / (total_ms / 1e3),
@@ -879,8 +882,8 @@ def main():
 
     def plain_map(c):
         m = DiscMap(**c)
-        if args.batch_split:
-            m.set_schedule(batch_split=args.batch_split)
+        if args.batch_split or args.assoc_cluster:
+            m.set_schedule(assoc_cluster=args.assoc_cluster, batch_split=args.batch_split)
         return m
 
     def frame_array(lo, hi, on_device=True, host=None):

@@ -422,8 +422,7 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
         sc.pkey = a.get<unsigned long long>((size_t)B * scap);
         sc.pcnt = a.get<int32_t>((size_t)B * scap);
         sc.plist = a.get<int32_t>((size_t)B * scap);
-        sc.aent = a.get<int32_t>((size_t)B * scap);
-        sc.aslot = a.get<int32_t>((size_t)B * scap);
+        sc.aent = a.get<int32_t>((size_t)B * 2 * scap);  // per slot: aent [scap], aslot [scap]
         sc.newcnt = a.get<int32_t>((size_t)B * MM);
         sc.ctr = a.get<FrameCounters>(B);
     }

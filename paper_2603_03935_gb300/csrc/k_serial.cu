@@ -511,36 +511,95 @@ __device__ __forceinline__ int local_of(const unsigned* hkey, const unsigned* hv
     return (int)(hval[h] & ~UH_LOCAL);
 }
 
-// Bytes of a union region with the given capacities (layout below).
-__host__ __device__ constexpr size_t union_region_bytes(unsigned uhash_cap, int root_cap, int edge_cap)
+// Bytes of a union region with the given capacities (layout in
+// UnionRegion); pre: with the arrays of values gathered before the union.
+__host__ __device__ constexpr size_t union_region_bytes(unsigned uhash_cap, int root_cap, int edge_cap,
+                                                        bool pre = false)
 {
-    return (size_t)uhash_cap * 8 + (size_t)root_cap * 24 + (size_t)edge_cap * 8;
+    return (size_t)uhash_cap * 8 + (size_t)root_cap * (pre ? 32 : 24) + (size_t)edge_cap * (pre ? 24 : 8);
 }
+
+// The arrays of a union region: the root hash, the per-local-root arrays
+// and the edge arrays; with `pre` also each local root's voxel count (cloc)
+// and, per edge, its instance's count, Q and observations as the gates read
+// them (ec, eq, eo), so the union issues no global load for them.
+struct UnionRegion {
+    unsigned* hkey;      // [uhash_cap] root id
+    unsigned* hval;      // [uhash_cap] claimant edge, then UH_LOCAL | local index
+    long long* cloc;     // [root_cap] voxel count of the local roots (pre)
+    int* gid;            // [root_cap] local -> instance id
+    int* uf;             // union-find over local indices
+    int* best_src;       // fusion winner per component
+    float* best_q;
+    float* qloc;         // Q of the local roots
+    int* oloc;           // observations of the local roots
+    long long* ec;       // [edge_cap] count of the edge's instance (pre)
+    int* em;             // [edge_cap] edge segment
+    int* ek;             // [edge_cap] edge instance id
+    float* eq;           // [edge_cap] Q of the edge's instance (pre)
+    int* eo;             // [edge_cap] observations of the edge's instance (pre)
+    __device__ __forceinline__ UnionRegion(unsigned char* base, unsigned uhash_cap, int root_cap, int edge_cap,
+                                           bool pre)
+    {
+        hkey = (unsigned*)base;
+        hval = hkey + uhash_cap;
+        cloc = pre ? (long long*)(hval + uhash_cap) : nullptr;
+        gid = pre ? (int*)(cloc + root_cap) : (int*)(hval + uhash_cap);
+        uf = gid + root_cap;
+        best_src = uf + root_cap;
+        best_q = (float*)(best_src + root_cap);
+        qloc = best_q + root_cap;
+        oloc = (int*)(qloc + root_cap);
+        ec = pre ? (long long*)(oloc + root_cap) : nullptr;
+        em = pre ? (int*)(ec + edge_cap) : oloc + root_cap;
+        ek = em + edge_cap;
+        eq = pre ? (float*)(ek + edge_cap) : nullptr;
+        eo = pre ? (int*)(eq + edge_cap) : nullptr;
+    }
+};
+
+// Per-segment inputs of the union read by the calling thread before the
+// union starts (thread t for segment t; the frame's M <= block size), and
+// what the union hands back to every thread when it completes.
+struct UnionPre {
+    int nv;       // nvox[t]
+    float q;      // the segment's Q
+    int nnew;     // voxels the frame inserts with segment t as their lowest segment
+    int next;     // the map's next instance id
+    int ok;       // out: the union completed without error
+    int ncopy;    // out: embedding copies it listed
+    int merges;   // out: instances it merged
+};
 
 // The frame's npairs overlap pairs give their roots through pair_root(i);
 // its nedge accepted edges are in ss.edge_m/k, or (edges_in_place) already in
-// the region's em/ek arrays.  The region (shared memory, or global memory
-// for frames beyond the shared capacities) holds hkey, hval [uhash_cap >=
-// 2 * npairs], the per-root arrays [root_cap], em, ek [edge_cap >= 2 *
-// root_cap... at least root_cap * 2 ints for the fusion step].  Past a
-// capacity the frame fails with DISC_ERR_CAPACITY, or, soft, the call
-// returns false before anything outside the region changed (the caller then
-// retries with larger capacities); otherwise it returns true.
+// the region's em/ek arrays (and, with pre, their instances' values in
+// ec/eq/eo).  The region (shared memory, or global memory for frames beyond
+// the shared capacities) is laid out as UnionRegion: hkey, hval [uhash_cap
+// >= 2 * npairs], the per-root arrays [root_cap], the edge arrays [edge_cap
+// >= 2 * root_cap: the fusion step lays root_cap 64-bit words over em].
+// pre: the calling thread's per-segment values, read before the union; the
+// union then also adds the frame's new voxels to their instances' counts.
+// Past a capacity the frame fails with DISC_ERR_CAPACITY, or, soft, the
+// call returns false before anything outside the region changed (the caller
+// then retries with larger capacities); otherwise it returns true.
 template <class PairRoot>
 __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const SerialScratch& ss, const Instances& inst,
                             int* next_id, unsigned char* union_smem, unsigned uhash_cap, int root_cap, int edge_cap,
-                            bool soft, int npairs, int nedge, bool edges_in_place, PairRoot pair_root)
+                            bool soft, int npairs, int nedge, bool edges_in_place, PairRoot pair_root,
+                            UnionPre* pre = nullptr)
 {
-    unsigned* hkey = (unsigned*)union_smem;           // [uhash_cap] root id
-    unsigned* hval = hkey + uhash_cap;                // [uhash_cap] claimant edge, then UH_LOCAL | local index
-    int* gid = (int*)(hval + uhash_cap);              // [root_cap] local -> instance id
-    int* uf = gid + root_cap;                         // union-find over local indices
-    int* best_src = uf + root_cap;                    // fusion winner per component
-    float* best_q = (float*)(best_src + root_cap);
-    float* qloc = best_q + root_cap;                  // Q of the local roots
-    int* oloc = (int*)(qloc + root_cap);              // observations of the local roots
-    int* em = oloc + root_cap;                        // [edge_cap] edge segment
-    int* ek = em + edge_cap;                          // [edge_cap] edge instance id
+    const UnionRegion U(union_smem, uhash_cap, root_cap, edge_cap, pre != nullptr);
+    unsigned* hkey = U.hkey;
+    unsigned* hval = U.hval;
+    int* gid = U.gid;
+    int* uf = U.uf;
+    int* best_src = U.best_src;
+    float* best_q = U.best_q;
+    float* qloc = U.qloc;
+    int* oloc = U.oloc;
+    int* em = U.em;
+    int* ek = U.ek;
     __shared__ int anchor[MAX_MASKS];                 // smallest local root of a segment's edges
     __shared__ int srep[MAX_MASKS];
     __shared__ int snv[MAX_MASKS];
@@ -566,10 +625,18 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         hkey[i] = UH_EMPTY;
         hval[i] = UH_UNUSED;
     }
-    for (int m = tid; m < M; m += NT) {
-        anchor[m] = INT_MAX;
-        snv[m] = sc.nvox[m];
-        sq[m] = sc.S[5 * m + 4];
+    if (pre) {
+        if (tid < M) {
+            anchor[tid] = INT_MAX;
+            snv[tid] = pre->nv;
+            sq[tid] = pre->q;
+        }
+    } else {
+        for (int m = tid; m < M; m += NT) {
+            anchor[m] = INT_MAX;
+            snv[m] = sc.nvox[m];
+            sq[m] = sc.S[5 * m + 4];
+        }
     }
     if (tid == 0) {
         s_nroots = 0;
@@ -577,23 +644,28 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         s_merges = 0;
         s_new = 0;
         s_ncopy = 0;
-        s_next = *next_id;
+        s_next = pre ? pre->next : *next_id;
     }
     __syncthreads();
-    // (1) active set: distinct roots of all overlap pairs
-    for (int i = tid; i < npairs; i += NT) {
-        const unsigned k = pair_root(i);
-        unsigned h = uhash(k, hm);
-        while (true) {
-            const unsigned cur = hkey[h];
-            if (cur == k) break;
-            if (cur == UH_EMPTY) {
-                const unsigned prev = atomicCAS(&hkey[h], UH_EMPTY, k);
-                if (prev == UH_EMPTY) { atomicAdd(&s_nroots, 1); break; }
-                if (prev == k) break;
+    // (1) active set: distinct roots of all overlap pairs (counted per warp)
+    {
+        int mine = 0;
+        for (int i = tid; i < npairs; i += NT) {
+            const unsigned k = pair_root(i);
+            unsigned h = uhash(k, hm);
+            while (true) {
+                const unsigned cur = hkey[h];
+                if (cur == k) break;
+                if (cur == UH_EMPTY) {
+                    const unsigned prev = atomicCAS(&hkey[h], UH_EMPTY, k);
+                    if (prev == UH_EMPTY) { mine++; break; }
+                    if (prev == k) break;
+                }
+                h = (h + 1) & hm;
             }
-            h = (h + 1) & hm;
         }
+        mine = warp_sum(mine);
+        if ((tid & 31) == 0 && mine) atomicAdd(&s_nroots, mine);
     }
     __syncthreads();
     // (2) local indices for the roots that carry an edge: the first edge to
@@ -614,8 +686,14 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
             if (x < root_cap) {
                 gid[x] = (int)k;
                 uf[x] = x;
-                qloc[x] = inst.Q[k];
-                oloc[x] = inst.n_obs[k];
+                if (pre) {
+                    qloc[x] = U.eq[e];
+                    oloc[x] = U.eo[e];
+                    U.cloc[x] = U.ec[e];
+                } else {
+                    qloc[x] = inst.Q[k];
+                    oloc[x] = inst.n_obs[k];
+                }
             }
             hval[h] = UH_LOCAL | (unsigned)x;
         }
@@ -665,9 +743,11 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
             total += wtot[w];
         }
         const int base = s_next;
-        if (base + total > inst.cap) {
+        if (base + total > inst.cap) {  // uniform: every thread summed the same counts
             if (tid == 0) set_err(ctr, DISC_ERR_CAPACITY);
-        } else if (want) {
+            return true;
+        }
+        if (want) {
             const int id = base + before, m = tid;
             srep[m] = id;
             inst.parent[id] = id;
@@ -677,8 +757,8 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
             ss.copy_dst[before] = id;
             ss.copy_src[before] = -(m + 1);
         }
-        __syncthreads();
-        if (tid == 0 && !ctr->err) {
+        __syncthreads();  // every thread has read s_next
+        if (tid == 0) {
             *next_id = base + total;
             s_next = base + total;
             s_new = total;
@@ -686,7 +766,6 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         }
     }
     __syncthreads();
-    if (ctr->err) return true;
     for (int m = tid; m < M; m += NT) sc.segrep[m] = srep[m];
     // (5) fusion per component: the candidates in the order (members by
     //     ascending id, then segments by ascending mask) keep the first one
@@ -744,16 +823,19 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         ss.copy_src[c] = src;
         inst.Q[rep] = q;
     }
-    // (6) merge members into their representative
+    // (6) merge members into their representative (then, with pre, the
+    //     frame's new voxels into their segment's instance)
     for (int x = tid; x < nloc; x += NT) {
         const int r = uf[x];
         if (r == x) continue;
         const int k = gid[x], rep = gid[r];
         inst.parent[k] = rep;
-        atomicAdd((unsigned long long*)&inst.count[rep], (unsigned long long)inst.count[k]);
+        atomicAdd((unsigned long long*)&inst.count[rep], (unsigned long long)(pre ? U.cloc[x] : inst.count[k]));
         inst.count[k] = 0;
         atomicAdd(&s_merges, 1);
     }
+    if (pre && tid < M && pre->nnew && srep[tid] >= 0)
+        atomicAdd((unsigned long long*)&inst.count[srep[tid]], (unsigned long long)pre->nnew);
     __syncthreads();
     if (tid == 0) {
         *ss.copy_n = s_ncopy;
@@ -764,6 +846,11 @@ __device__ bool union_frame(const FrameParams& fp, const Scratch& sc, const Seri
         ctr->n_edges = nedge;
         ctr->next_id = s_next;
         ctr->n_copies = s_ncopy;
+    }
+    if (pre) {
+        pre->ok = 1;
+        pre->ncopy = s_ncopy;
+        pre->merges = s_merges;
     }
     return true;
 }
@@ -1192,6 +1279,26 @@ __global__ void __launch_bounds__(256) k_absent(const FrameParams* fps, BatchScr
     if (lane == 0 && tot) atomicAdd(&sc.ctr->n_new, tot);
 }
 
+// Every slot's overlap items, once k_absent is done: the hash slots listed
+// in plist become dense (key, count) arrays in claim order (ikey over the
+// free aent | aslot, icnt over plist itself: each thread reads plist[i]
+// before it writes icnt[i]), and the hash is emptied for the slot's next
+// batch.  Items of a failed frame are emptied as well.
+__global__ void __launch_bounds__(256) k_items(BatchScratch bs)
+{
+    const Scratch sc = bs.frame(blockIdx.y);
+    const int n = sc.ctr->n_pre;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = sc.plist[i];
+        const unsigned long long key = sc.pkey[t];
+        const int cnt = sc.pcnt[t];
+        sc.pkey[t] = EMPTY_KEY;
+        sc.pcnt[t] = 0;
+        sc.ikey[i] = key;
+        sc.icnt[i] = cnt;
+    }
+}
+
 // root of instance id x (parent chains may be longer than one step between
 // the merges of a batch and its k_commit).  A parent is never above its
 // child (a merge hooks an instance under the component's smallest id), so a
@@ -1223,12 +1330,12 @@ __device__ __forceinline__ int block_read(const int32_t* w)
 constexpr int ASSOC_THREADS = 512;
 constexpr int APH = 2048;         // slots of the leader CTA's pair hash (shared memory)
 constexpr int APH_MAX = 1536;     // pairs it takes (load <= 3/4)
-constexpr int ASSOC_ROOTS = 512;  // instances with an accepted edge, in shared memory
-constexpr int ASSOC_EDGES = 1024; // accepted edges, in shared memory
+constexpr int ASSOC_ROOTS = 256;  // instances with an accepted edge, in shared memory
+constexpr int ASSOC_EDGES = 512;  // accepted edges, in shared memory
 // A frame past one of these shared capacities runs steps (1)-(3) on the
 // leader alone with the map's global pair hash and union region.  The small
 // footprint lets the CTAs share SMs with the next batch's stateless kernels.
-constexpr size_t ASSOC_SMEM = (size_t)APH * 16 + union_region_bytes(2 * APH, ASSOC_ROOTS, ASSOC_EDGES);
+constexpr size_t ASSOC_SMEM = (size_t)APH * 16 + union_region_bytes(2 * APH, ASSOC_ROOTS, ASSOC_EDGES, true);
 constexpr int ASSOC_CLUSTER_MAX = 8;
 static_assert(ASSOC_EDGES >= 2 * ASSOC_ROOTS, "the fusion step overlays the edge arrays");
 
@@ -1274,6 +1381,10 @@ __device__ __forceinline__ void dsm_st32(unsigned a, int v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
+__device__ __forceinline__ void dsm_st64(unsigned a, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
 __device__ __forceinline__ unsigned cluster_rank()
 {
     unsigned r;
@@ -1292,29 +1403,44 @@ __device__ __forceinline__ void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
+// the two halves of cluster_sync: between them a thread may read what no
+// other thread of the cluster writes in this phase
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 // A cluster of C CTAs per map of the batch (C = cluster size, 1 to 8)
 // walks the map's frames in order.  The leader CTA (rank 0) holds the
-// frame's pair hash, edge list and union state in its shared memory; the
-// other CTAs reach them through distributed shared memory.  Per frame:
+// frame's pair hash, scored-pair list, edge list and union state in its
+// shared memory; the other CTAs reach them through distributed shared
+// memory.  Per frame:
 //   (1) every CTA resolves a share of the frame's items to (segment, root)
 //       pairs and counts them in the leader's pair hash;
-//   (2) every warp of the cluster takes a share of the pairs: each lane the
-//       overlap gate of one pair, then the warp the cosine gates of its
-//       lanes' passing pairs; accepted edges go to the leader's edge list;
-//   (3) the leader alone: union, new ids, merges and fusion winners;
+//   (2) every thread of the cluster checks the overlap gate of one pair and
+//       appends a passing pair to the scored list; then every warp takes the
+//       cosine gate of one scored pair (so no warp scores several while
+//       others idle); accepted edges go to the leader's edge list;
+//   (3) the leader alone: union, new ids, merges and fusion winners; then it
+//       stages the frame's status and copy count and empties its pair hash;
 //   (4) every warp a share of the embedding copies; the leader the voxel
 //       counts of the frame's new voxels;
-// with a cluster barrier between the steps.  A frame with more pairs than
-// the leader's hash takes (APH_MAX) runs steps (1)-(3) on the leader alone
-// with the map's global pair hash.  Every branch that skips a cluster
-// barrier is taken by the whole cluster (its condition is read from the
-// leader after a barrier), so every CTA passes the same barriers.
+// with a cluster barrier after (1), after each half of (2) and after (3).
+// Step (4) needs no barrier before the next frame's step (1): that step
+// touches only the leader's emptied hash, and the next barrier orders the
+// copies before the next gates read the embeddings.  The status and copy
+// count alternate between two words by frame parity, so the leader may
+// stage the next frame's while a slower CTA still reads this frame's.  A
+// frame with more pairs than the leader's hash takes (APH_MAX), or more
+// edges or edge roots than its union region holds, runs steps (1)-(3) on the
+// leader alone with the map's global pair hash.  Every branch that skips a
+// cluster barrier is taken by the whole cluster (its condition is read from
+// global memory written before the launch, or from the leader after a
+// barrier), so every CTA passes the same barriers.
 __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParams* fps, BatchScratch bs,
                                                                 SerialStep st)
 {
     extern __shared__ __align__(16) unsigned char union_smem[];
-    __shared__ int s_slot, s_blocked, s_np, s_ovf, s_ne, s_merged, s_err, s_nc;
+    __shared__ int s_np, s_ovf, s_ne, s_nsc, s_merged;
+    __shared__ int s_err[2], s_nc[2];  // by frame parity
     const unsigned rank = cluster_rank(), C = cluster_size();
     const bool leader = rank == 0;
     const int g = blockIdx.x / C;
@@ -1324,65 +1450,54 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
     const int cw = (int)rank * (NT >> 5) + (tid >> 5), CW = (int)C * (NT >> 5);  // warp within the cluster
     // the leader's step (1)-(3) state, laid out as in its union_smem:
     // pair hash, then the union's region (root hash of 2 * APH slots,
-    // per-root arrays, edges)
+    // per-root arrays, edges); the scored pairs (segment, instance) sit over
+    // the root hash, which the union fills only after the gates
     unsigned long long* pk = (unsigned long long*)union_smem;  // [APH] (segment + 1) << 32 | root
     int* pc = (int*)(pk + APH);                                 // [APH] voxels of the pair
     int* pl = pc + APH;                                         // [APH] used slots
     unsigned char* ureg = union_smem + (size_t)APH * 16;
-    int* em = (int*)(ureg + (size_t)(2 * APH) * 8 + (size_t)ASSOC_ROOTS * 24);
-    int* ek = em + ASSOC_EDGES;
-    const unsigned r_pk = dsm_map(pk, 0), r_pc = dsm_map(pc, 0), r_pl = dsm_map(pl, 0);
-    const unsigned r_em = dsm_map(em, 0), r_ek = dsm_map(ek, 0);
-    const unsigned r_slot = dsm_map(&s_slot, 0), r_blocked = dsm_map(&s_blocked, 0), r_np = dsm_map(&s_np, 0);
-    const unsigned r_ovf = dsm_map(&s_ovf, 0), r_ne = dsm_map(&s_ne, 0);
-    const unsigned r_err = dsm_map(&s_err, 0), r_nc = dsm_map(&s_nc, 0);
-    int2* cl = (int2*)union_smem;  // the frame's embedding copies (src, dst), staged over the pair hash
-    constexpr int CL_CAP = APH * 2;
-    const unsigned r_cl = dsm_map(cl, 0);
-    if (leader && tid == 0) {
-        *R.ss.edge_n = 0;
-        *R.ss.copy_n = 0;
-        s_merged = 0;
-    }
-    for (int j = 0; j < st.J; j++) {
-        cluster_sync();  // the previous frame is done everywhere
-        if (leader) {
-            if (tid == 0) {
-                const int slot = st.slot_of[g * st.J + j];
-                int blocked = 0;
-                if (slot >= 0) {
-                    FrameCounters* c = bs.frame(slot).ctr;
-                    int prev = 0;
-                    if (j > 0) {
-                        const int ps = st.slot_of[g * st.J + j - 1];
-                        prev = ps >= 0 ? *(volatile int32_t*)&bs.frame(ps).ctr->err : 0;
-                    } else if (st.prev_hist[g] >= 0) {
-                        prev = st.hist[st.prev_hist[g]].err;
-                    }
-                    const int own = *(volatile int32_t*)&c->err;
-                    if (!own && prev) set_err(c, prev);
-                    blocked = own || prev;
-                }
-                s_slot = slot;
-                s_blocked = blocked;
-                s_np = 0;
-                s_ovf = 0;
-                s_ne = 0;
-            }
-            for (int i = tid; i < APH; i += NT) {
-                pk[i] = EMPTY_KEY;
-                pc[i] = 0;
-            }
+    int2* sp = (int2*)ureg;                                     // [APH_MAX] scored pairs
+    const UnionRegion U(ureg, 2 * APH, ASSOC_ROOTS, ASSOC_EDGES, true);
+    static_assert((size_t)APH_MAX * 8 <= (size_t)(2 * APH) * 8, "scored pairs fit over the root hash");
+    const unsigned r_pk = dsm_map(pk, 0), r_pc = dsm_map(pc, 0), r_pl = dsm_map(pl, 0), r_sp = dsm_map(sp, 0);
+    const unsigned r_em = dsm_map(U.em, 0), r_ek = dsm_map(U.ek, 0), r_ec = dsm_map(U.ec, 0);
+    const unsigned r_eq = dsm_map(U.eq, 0), r_eo = dsm_map(U.eo, 0);
+    const unsigned r_np = dsm_map(&s_np, 0), r_ovf = dsm_map(&s_ovf, 0), r_ne = dsm_map(&s_ne, 0);
+    const unsigned r_nsc = dsm_map(&s_nsc, 0), r_err = dsm_map(&s_err[0], 0), r_nc = dsm_map(&s_nc[0], 0);
+    if (leader) {
+        for (int i = tid; i < APH; i += NT) {
+            pk[i] = EMPTY_KEY;
+            pc[i] = 0;
         }
-        cluster_sync();
-        const int slot = dsm_ld32(r_slot);
-        const bool blocked = dsm_ld32(r_blocked) != 0;
-        if (slot < 0) break;  // the whole cluster
+        if (tid == 0) {
+            *R.ss.edge_n = 0;
+            *R.ss.copy_n = 0;
+            s_merged = 0;
+            s_np = s_ovf = s_ne = s_nsc = 0;
+            s_err[0] = s_err[1] = 0;
+            s_nc[0] = s_nc[1] = 0;
+        }
+    }
+    cluster_sync();
+    for (int j = 0; j < st.J; j++) {
+        const int slot = st.slot_of[g * st.J + j];  // the same for the whole cluster
+        if (slot < 0) break;
+        const int par = j & 1;
         const FrameParams& fp = fps[slot];
         const Scratch sc = bs.frame(slot);
-        const int npre = sc.ctr->n_pre;
+        // blocked: the frame's own error (set before the launch), or its
+        // predecessor's status (staged by the leader before the last barrier)
+        const int prev = j > 0 ? dsm_ld32(r_err + 4u * (par ^ 1))
+                               : (st.prev_hist[g] >= 0 ? st.hist[st.prev_hist[g]].err : 0);
+        const int own = *(volatile const int32_t*)&sc.ctr->err;
+        const bool blocked = own || prev;
+        if (leader && tid == 0 && !own && prev) set_err(sc.ctr, prev);
         bool global_pairs = false;
+        // the leader's per-segment union inputs; up.ok: the union completed
+        // (and added the frame's new voxels to the counts)
+        UnionPre up{};
         if (!blocked) {
+            const int npre = sc.ctr->n_pre;
             // (1) overlap pairs: each item's label resolved to its root now
             //     (four items per thread in flight)
             for (int i0 = ct; i0 < npre; i0 += 4 * CT) {
@@ -1391,13 +1506,8 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const int i = i0 + u * CT;
-                    key[u] = EMPTY_KEY;
-                    cnt[u] = 0;
-                    if (i < npre) {
-                        const int ps = sc.plist[i];
-                        key[u] = sc.pkey[ps];
-                        cnt[u] = sc.pcnt[ps];
-                    }
+                    key[u] = i < npre ? sc.ikey[i] : EMPTY_KEY;
+                    cnt[u] = i < npre ? sc.icnt[i] : 0;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
@@ -1413,19 +1523,15 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
                     if (lab[u] < 0) continue;
                     const unsigned long long okey = ((key[u] >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab[u]);
                     unsigned h = (unsigned)(mix64(okey) & (APH - 1));
-                    for (int pr = 0;; pr++) {
-                        const unsigned long long cur = dsm_ld64(r_pk + 8u * h);
-                        if (cur == okey) break;
-                        if (cur == EMPTY_KEY) {
-                            const unsigned long long prev = dsm_cas64(r_pk + 8u * h, EMPTY_KEY, okey);
-                            if (prev == EMPTY_KEY) {
-                                const int at = dsm_add(r_np, 1);
-                                if (at < APH_MAX) dsm_st32(r_pl + 4u * at, (int)h);
-                                else dsm_st32(r_ovf, 1);
-                                break;
-                            }
-                            if (prev == okey) break;
+                    for (int pr = 0;; pr++) {  // claim or find in one round trip per slot
+                        const unsigned long long prv = dsm_cas64(r_pk + 8u * h, EMPTY_KEY, okey);
+                        if (prv == EMPTY_KEY) {
+                            const int at = dsm_add(r_np, 1);
+                            if (at < APH_MAX) dsm_st32(r_pl + 4u * at, (int)h);
+                            else dsm_st32(r_ovf, 1);
+                            break;
                         }
+                        if (prv == okey) break;
                         h = (h + 1) & (APH - 1);
                         if (pr >= APH) {
                             dsm_st32(r_ovf, 1);
@@ -1439,14 +1545,11 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
             global_pairs = dsm_ld32(r_ovf) != 0;  // the whole cluster
             if (!global_pairs) {
                 const int np = dsm_ld32(r_np);
-                if (leader && tid == 0) sc.ctr->n_pairs = np;
-                // (2) gates: each lane checks the overlap gate of one pair
-                //     (pairs dealt round robin over the cluster's warps), then
-                //     the warp takes the cosine gate of its passing pairs
-                const GateFeatures gf = gate_features(fp, sc, st.view.frame(slot), R.inst);
-                int border = 0, scored = 0;
-                for (int r0 = 0; r0 < np; r0 += CT) {
-                    const int i = r0 + lane * CW + cw;
+                // (2a) overlap gate of pair i by thread i of the cluster:
+                //      |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den;
+                //      passing pairs to the scored list (one slot claim per warp)
+                for (int w0 = ct & ~31; w0 < np; w0 += CT) {  // whole warps iterate together
+                    const int i = w0 + lane;
                     int m = 0, k = 0;
                     bool pass = false;
                     if (i < np) {
@@ -1455,35 +1558,67 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
                         const long long ov = dsm_ld32(r_pc + 4u * h);
                         m = (int)(okey >> 32) - 1;
                         k = (int)(okey & 0xffffffffu);
-                        // overlap coefficient |V_m & V_k| / min(|V_m|, |V_k|) >= ov_num / ov_den
                         const long long denom = min((long long)sc.nvox[m], R.inst.count[k]);
                         pass = ov * (long long)fp.ov_den >= (long long)fp.ov_num * denom;
                     }
-                    unsigned todo = __ballot_sync(0xffffffffu, pass);
-                    scored += __popc(todo);
-                    while (todo) {
-                        const int l = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int mm = __shfl_sync(0xffffffffu, m, l), kk = __shfl_sync(0xffffffffu, k, l);
-                        if (warp_cosine_gate(fp, gf, R.inst, mm, kk, &border) && lane == 0) {
-                            const int e = dsm_add(r_ne, 1);
-                            if (e < ASSOC_EDGES) {
-                                dsm_st32(r_em + 4u * e, mm);
-                                dsm_st32(r_ek + 4u * e, kk);
-                            }  // more edges than the shared list holds: the global path below
-                        }
+                    const unsigned b = __ballot_sync(0xffffffffu, pass);
+                    int base = 0;
+                    if (lane == 0 && b) base = dsm_add(r_nsc, __popc(b));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (pass) {
+                        const unsigned at = (unsigned)(base + __popc(b & ((1u << lane) - 1)));
+                        dsm_st32(r_sp + 8u * at, m);
+                        dsm_st32(r_sp + 8u * at + 4u, k);
+                    }
+                }
+                cluster_sync();
+                const int nsc = dsm_ld32(r_nsc);
+                if (leader && tid == 0) {
+                    sc.ctr->n_pairs = np;
+                    sc.ctr->n_scored = nsc;
+                }
+                // (2b) cosine gate of scored pair s by warp s of the cluster
+                const GateFeatures gf = gate_features(fp, sc, st.view.frame(slot), R.inst);
+                int border = 0;
+                for (int q = cw; q < nsc; q += CW) {
+                    const int mm = dsm_ld32(r_sp + 8u * q), kk = dsm_ld32(r_sp + 8u * q + 4u);
+                    // the instance's values the union needs, read beside the gate
+                    const long long ck = lane == 0 ? R.inst.count[kk] : 0;
+                    const float qk = lane == 0 ? R.inst.Q[kk] : 0.0f;
+                    const int ok = lane == 0 ? R.inst.n_obs[kk] : 0;
+                    if (warp_cosine_gate(fp, gf, R.inst, mm, kk, &border) && lane == 0) {
+                        const int e = dsm_add(r_ne, 1);
+                        if (e < ASSOC_EDGES) {
+                            dsm_st32(r_em + 4u * e, mm);
+                            dsm_st32(r_ek + 4u * e, kk);
+                            dsm_st64(r_ec + 8u * e, (unsigned long long)ck);
+                            dsm_st32(r_eq + 4u * e, __float_as_int(qk));
+                            dsm_st32(r_eo + 4u * e, ok);
+                        }  // more edges than the shared list holds: the global path below
                     }
                 }
                 if (lane == 0 && border) atomicAdd(&sc.ctr->borderline, border);
-                if (lane == 0 && scored) atomicAdd(&sc.ctr->n_scored, scored);
-                cluster_sync();
+                // the leader reads its segments' values for the union while
+                // the cluster arrives (nothing in the cluster writes them)
+                cluster_arrive();
+                if (leader) {
+                    if (tid < fp.M) {
+                        up.nv = sc.nvox[tid];
+                        up.q = sc.S[5 * tid + 4];
+                        up.nnew = sc.newcnt[tid];
+                    }
+                    up.next = *(volatile const int*)R.next_id;
+                }
+                cluster_wait();
                 // (3) union, new ids, merges, fusion winners: the leader, in
                 //     its shared memory unless a shared capacity is exceeded
                 if (leader) {
                     bool done = s_ne <= ASSOC_EDGES;
-                    if (done && !block_read(&sc.ctr->err))
+                    if (done && !block_read(&sc.ctr->err)) {
                         done = union_frame(fp, sc, R.ss, R.inst, R.next_id, ureg, 2 * APH, ASSOC_ROOTS, ASSOC_EDGES,
-                                           true, np, s_ne, true, [&](int i) { return (unsigned)(pk[pl[i]] & 0xffffffffu); });
+                                           true, np, s_ne, true, [&](int i) { return (unsigned)(pk[pl[i]] & 0xffffffffu); },
+                                           &up);
+                    }
                     if (!done && tid == 0) {  // steps (1)-(3) again on global memory
                         sc.ctr->n_pairs = 0;
                         sc.ctr->n_scored = 0;
@@ -1498,80 +1633,74 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
                 // hash and union region
                 __syncthreads();
                 for (int i = tid; i < npre; i += NT) {
-                    const int ps = sc.plist[i];
-                    const unsigned long long key = sc.pkey[ps];
+                    const unsigned long long key = sc.ikey[i];
                     const unsigned x = (unsigned)key;
                     const int lab = ((key >> 32) & 1ull)
                                         ? bs.frame(st.slot_of[g * st.J + (int)(x >> 9)]).segrep[(x & 511u) - 1]
                                         : (int)x;
                     if (lab >= 0)
-                        add_pair(sc, R.ss, ((key >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab),
-                                 sc.pcnt[ps]);
+                        add_pair(sc, R.ss, ((key >> 33) << 32) | (unsigned)find_root(R.inst.parent, lab), sc.icnt[i]);
                 }
                 if (!block_read(&sc.ctr->err))
                     phase_score(fp, sc, st.view.frame(slot), R.ss, R.inst, tid >> 5, NT >> 5);
                 if (!block_read(&sc.ctr->err)) phase_union(fp, sc, R.ss, R.inst, R.next_id, R.ss.ureg);
-            }
-            // the leader stages the frame's status and embedding copies for
-            // the cluster (the pair hash is no longer needed)
-            if (leader) {
+                // empty the global pair hash
                 __syncthreads();
-                const int err = *(volatile int32_t*)&sc.ctr->err;
-                const int nc = err ? 0 : min(*(volatile int32_t*)R.ss.copy_n, CL_CAP);
-                for (int c = tid; c < nc; c += NT) cl[c] = make_int2(R.ss.copy_src[c], R.ss.copy_dst[c]);
-                if (tid == 0) {
-                    s_err = err;
-                    s_nc = nc;
-                }
-            }
-            cluster_sync();
-            // (4) the winners' embeddings (every warp of the cluster) and the
-            //     new voxels' counts (the leader)
-            if (!dsm_ld32(r_err)) {
-                const int D = fp.D;
-                const int nc = dsm_ld32(r_nc);
-                for (int c = cw; c < nc; c += CW) {
-                    const int src = dsm_ld32(r_cl + 8u * c), dst = dsm_ld32(r_cl + 8u * c + 4u);
-                    const Instances& inst = R.inst;
-                    const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
-                    if (inst.A) {
-                        const Scratch va = st.view.frame(slot);
-                        const int Da = inst.Da;
-                        const float* fa = src >= 0 ? inst.A + (size_t)src * Da : va.Ecan + (size_t)(-src - 1) * Da;
-                        copy_row(from, inst.E + (size_t)dst * D, nullptr, D, lane);
-                        copy_row(fa, inst.A + (size_t)dst * Da, inst.Eb ? inst.Eb + (size_t)dst * Da : nullptr, Da,
-                                 lane);
-                        if (inst.E8) e4m3_copy_row(fa, Da, inst.E8 + (size_t)dst * Da, inst.Er + dst);
-                    } else {
-                        copy_row(from, inst.E + (size_t)dst * D, inst.Eb ? inst.Eb + (size_t)dst * D : nullptr, D,
-                                 lane);
-                        if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)dst * D, inst.Er + dst);
-                    }
-                }
-                if (leader) {
-                    for (int m = tid; m < fp.M; m += NT) {
-                        const int n = sc.newcnt[m], rep = sc.segrep[m];
-                        if (n && rep >= 0) atomicAdd((unsigned long long*)&R.inst.count[rep], (unsigned long long)n);
-                    }
-                    if (tid == 0 && sc.ctr->merges > 0) s_merged = 1;
+                const int np = *(volatile int32_t*)&sc.ctr->n_pairs;
+                for (int i = tid; i < np; i += NT) {
+                    const int t = R.ss.olist[i];
+                    R.ss.okeys[t] = EMPTY_KEY;
+                    R.ss.ocnt[t] = 0;
                 }
             }
         }
-        // empty the frame's item hash (and the global pair hash, if the
-        // leader used it)
-        if (global_pairs && leader) {
+        // the leader closes the frame: its status and copy count for step (4)
+        // and the next frame, its pair hash emptied for the next frame
+        if (leader) {
             __syncthreads();
-            const int np = *(volatile int32_t*)&sc.ctr->n_pairs;
-            for (int i = tid; i < np; i += NT) {
-                const int t = R.ss.olist[i];
-                R.ss.okeys[t] = EMPTY_KEY;
-                R.ss.ocnt[t] = 0;
+            const int err = up.ok ? 0 : *(volatile int32_t*)&sc.ctr->err;
+            const int nc = up.ok ? up.ncopy : err ? 0 : *(volatile int32_t*)R.ss.copy_n;
+            for (int i = tid; i < APH; i += NT) {
+                pk[i] = EMPTY_KEY;
+                pc[i] = 0;
+            }
+            if (tid == 0) {
+                s_err[par] = err;
+                s_nc[par] = nc;
+                s_np = s_ovf = s_ne = s_nsc = 0;
             }
         }
-        for (int i = ct; i < npre; i += CT) {
-            const int t = sc.plist[i];
-            sc.pkey[t] = EMPTY_KEY;
-            sc.pcnt[t] = 0;
+        cluster_sync();
+        // (4) the winners' embeddings (every warp of the cluster) and the
+        //     new voxels' counts (the leader)
+        if (!dsm_ld32(r_err + 4u * par)) {
+            const int D = fp.D;
+            const int nc = dsm_ld32(r_nc + 4u * par);
+            // from the cluster's last warp down: the first warps take the
+            // next frame's items, so the two run side by side
+            for (int c = CW - 1 - cw; c < nc; c += CW) {
+                const int src = R.ss.copy_src[c], dst = R.ss.copy_dst[c];
+                const Instances& inst = R.inst;
+                const float* from = src >= 0 ? inst.E + (size_t)src * D : sc.Ecan + (size_t)(-src - 1) * D;
+                if (inst.A) {
+                    const Scratch va = st.view.frame(slot);
+                    const int Da = inst.Da;
+                    const float* fa = src >= 0 ? inst.A + (size_t)src * Da : va.Ecan + (size_t)(-src - 1) * Da;
+                    copy_row(from, inst.E + (size_t)dst * D, nullptr, D, lane);
+                    copy_row(fa, inst.A + (size_t)dst * Da, inst.Eb ? inst.Eb + (size_t)dst * Da : nullptr, Da, lane);
+                    if (inst.E8) e4m3_copy_row(fa, Da, inst.E8 + (size_t)dst * Da, inst.Er + dst);
+                } else {
+                    copy_row(from, inst.E + (size_t)dst * D, inst.Eb ? inst.Eb + (size_t)dst * D : nullptr, D, lane);
+                    if (inst.E8) e4m3_copy_row(from, D, inst.E8 + (size_t)dst * D, inst.Er + dst);
+                }
+            }
+            if (leader) {
+                for (int m = tid; m < fp.M && !up.ok; m += NT) {
+                    const int n = sc.newcnt[m], rep = sc.segrep[m];
+                    if (n && rep >= 0) atomicAdd((unsigned long long*)&R.inst.count[rep], (unsigned long long)n);
+                }
+                if (tid == 0 && (up.ok ? up.merges : sc.ctr->merges) > 0) s_merged = 1;
+            }
         }
         if (leader && tid == 0) {
             *R.ss.edge_n = 0;
@@ -1723,7 +1852,8 @@ int launch_lookup(const FrameParams* fps, const BatchScratch& bs, const MapRefs*
         default: k_lookup<1><<<grid, 256, 0, st>>>(fps, bs, refs, ah); break;
     }
     k_absent<<<dim3(38, S), 256, 0, st>>>(fps, bs, ah);
-    return 2;
+    k_items<<<dim3(16, S), 256, 0, st>>>(bs);
+    return 3;
 }
 
 // CTAs per map: a cluster of up to 8 when the maps leave SMs free (152 SMs,
