@@ -394,33 +394,6 @@ struct FrameParams {
 };
 
 // ---- Sec. III-A: world point of pixel (u, v) at depth z -------------------------
-// The camera of a frame held in registers: the same arithmetic as
-// world_point, without re-reading the frame's parameters per point.
-struct CameraPose {
-    float cx, cy, inv_fx, inv_fy, R[9], t[3];
-    __device__ __forceinline__ explicit CameraPose(const FrameParams& fp)
-    {
-        cx = fp.cx;
-        cy = fp.cy;
-        inv_fx = fp.inv_fx;
-        inv_fy = fp.inv_fy;
-#pragma unroll
-        for (int i = 0; i < 9; i++) R[i] = fp.R[i];
-#pragma unroll
-        for (int i = 0; i < 3; i++) t[i] = fp.t[i];
-    }
-    __device__ __forceinline__ void world_point(int u, int v, float z, float p[3]) const
-    {
-        const float xc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), cx), z), inv_fx);
-        const float yc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), cy), z), inv_fy);
-#pragma unroll
-        for (int r = 0; r < 3; r++)
-            p[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(R[3 * r], xc), __fmul_rn(R[3 * r + 1], yc)),
-                                       __fmul_rn(R[3 * r + 2], z)),
-                             t[r]);
-    }
-};
-
 __device__ __forceinline__ void world_point(const FrameParams& fp, int u, int v, float z, float p[3])
 {
     float xc = __fmul_rn(__fmul_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fp.cx), z), fp.inv_fx);

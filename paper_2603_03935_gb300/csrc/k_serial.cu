@@ -482,7 +482,13 @@ constexpr unsigned UH_LOCAL = 0x80000000u;
 constexpr size_t UNION_SMEM = (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8;
 static_assert(UNION_SMEM == (size_t)UHASH * 8 + (size_t)EDGE_ROOT_CAP * 24 + (size_t)EDGE_CAP * 8, "union layout");
 
-__device__ __forceinline__ unsigned uhash(unsigned k, unsigned mask) { return (unsigned)(mix64(k) & mask); }
+// slot of root id k in the union's root hash (32-bit multiplicative mix)
+__device__ __forceinline__ unsigned uhash(unsigned k, unsigned mask)
+{
+    unsigned h = k * 0x9E3779B1u;
+    h ^= h >> 15;
+    return h & mask;
+}
 
 // float <-> unsigned key with the same order (for atomicMax over floats)
 __device__ __forceinline__ unsigned f2key(float x)
@@ -1444,8 +1450,15 @@ __global__ void __launch_bounds__(ASSOC_THREADS, 1) k_associate(const FrameParam
     const unsigned rank = cluster_rank(), C = cluster_size();
     const bool leader = rank == 0;
     const int g = blockIdx.x / C;
-    const MapRefs& R = st.refs[g];
     const int tid = threadIdx.x, lane = tid & 31, NT = blockDim.x;
+    // the map's table pointers, in shared memory: read there, they are never
+    // reloaded from global memory after the kernel's own global stores
+    __shared__ MapRefs s_refs;
+    static_assert(sizeof(MapRefs) % 8 == 0, "copied in 8-byte words");
+    for (int i = tid; i < (int)(sizeof(MapRefs) / 8); i += NT)
+        ((unsigned long long*)&s_refs)[i] = ((const unsigned long long*)&st.refs[g])[i];
+    __syncthreads();
+    const MapRefs& R = s_refs;
     const int ct = (int)rank * NT + tid, CT = (int)C * NT;               // thread within the cluster
     const int cw = (int)rank * (NT >> 5) + (tid >> 5), CW = (int)C * (NT >> 5);  // warp within the cluster
     // the leader's step (1)-(3) state, laid out as in its union_smem:
