@@ -1151,6 +1151,7 @@ def main():
                "h2d_bytes_per_step": B * (H * W_ * 6 + P * D * 4),
                "d2h_bytes_per_step": B * 64,
                "calls": "one disc_integrate_frames call per step (32 frames), host buffers, synchronous",
+               "call_ms": {"p50": float(np.median(et)), "min": float(np.min(et)), "max": float(np.max(et))},
                "one_call_trajectory": {"value": whole_job_rate(K * B, world, traj_ms), "unit": "frames/s",
                                        "frames": K * B}}
     state["e2e"] = e2e

@@ -251,9 +251,11 @@ void disc_group_destroy(disc_group* group); /* NULL-safe */
  * group.max_maps maps with work that no other batch holds (oldest request
  * first), the leading frames of each map's queue (up to
  * group.frames_per_map, stopping at the map's first query) and runs them as
- * one group call; requests arriving meanwhile join a later batch.  With two
- * workers one batch's input copies and stateless kernels run while the other
- * batch's frame chain computes.  A map is in one batch at a time and a query
+ * one group call; requests arriving meanwhile join a later batch.  While
+ * other workers wait for work, a worker takes only its share of the free
+ * maps (their number over the waiting workers plus one), so under a full
+ * load batches stay in flight side by side: one batch's input copies and
+ * stateless kernels run while another's frame chain computes.  A map is in one batch at a time and a query
  * runs after the frames submitted before it on the same map and before those
  * after it, so every result equals the one of the same requests served alone.
  * Maps are admitted while the device memory of the workers' group scratch and

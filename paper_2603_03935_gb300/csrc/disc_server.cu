@@ -73,6 +73,7 @@ struct disc_server {
     std::map<int64_t, Result> results;
     int64_t next_ticket = 1;
     int64_t pending = 0;
+    int waiting = 0;  // workers waiting for work
     int64_t resident = 0;  // device bytes: group scratch + open maps
     bool stop = false;
     std::vector<std::thread> workers;
@@ -146,12 +147,14 @@ void worker_loop(disc_server* s, int wi)
             std::unique_lock<std::mutex> lk(s->mu);
             // work on a map that another worker's batch holds waits for that
             // batch (its finish wakes the workers)
+            s->waiting++;
             s->cv_work.wait(lk, [&] {
                 if (s->stop && s->pending == 0) return true;
                 for (const MapSlot& ms : s->maps)
                     if (takeable(ms)) return true;
                 return false;
             });
+            s->waiting--;
             if (s->stop && s->pending == 0) return;
             std::vector<char> free(s->maps.size());
             for (int i = 0; i < (int)s->maps.size(); i++) free[i] = s->maps[i].busy == 0;
@@ -171,8 +174,11 @@ void worker_loop(disc_server* s, int wi)
                 if (free[i] && !s->maps[i].queue.empty() && !s->maps[i].queue.front().is_query)
                     order.push_back({s->maps[i].queue.front().t_submit, i});
             std::sort(order.begin(), order.end());
+            // a fair share of the free maps when other workers wait, so that
+            // batches stay in flight side by side under a full load
+            const int share = std::min<int>(G, ((int)order.size() + s->waiting) / (s->waiting + 1));
             for (auto& o : order) {
-                if ((int)gl.size() == G) break;
+                if ((int)gl.size() == std::max(share, 1)) break;
                 MapSlot& ms = s->maps[o.second];
                 std::vector<Request> fr;
                 while ((int)fr.size() < J && !ms.queue.empty() && !ms.queue.front().is_query) {
@@ -184,6 +190,7 @@ void worker_loop(disc_server* s, int wi)
                 mp.push_back(ms.m);
                 frames.push_back(std::move(fr));
             }
+            if ((int)gl.size() < (int)order.size() && s->waiting > 0) s->cv_work.notify_one();  // the rest
         }
         // queries (the maps' earlier frames are complete: a map is in one
         // batch at a time and batches are synchronous)
