@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-frames", type=int, default=4, help="frames of each map per batch")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--batched-history", default="0,16,64,256",
+                    help="frames each batched map integrates before the timed frames, cycling over the maps")
     ap.add_argument("--same-maps", type=int, default=16,
                     help="maps of the same-workload batched line (Room-scale 640x480 fp32, as the plain path; 0: skip)")
     ap.add_argument("--same-frames", type=int, default=8, help="frames of each map per batch of that line")
-    ap.add_argument("--multistory-steps", type=int, default=8,
+    ap.add_argument("--multistory-steps", type=int, default=16,
                     help="timed 32-frame steps of the Multi-story configuration (0: skip)")
     ap.add_argument("--tiny", type=int, default=1, help="1: time the Tiny configuration")
     ap.add_argument("--served-maps", type=int, default=32)
@@ -66,6 +68,8 @@ def parse():
                     help="frames of each served map's path; the measurements together take every frame once")
     ap.add_argument("--batch-split", type=int, default=0,
                     help="smaller batches per 32-frame call of the plain path (0: the library's automatic choice)")
+    ap.add_argument("--table-log2", type=int, default=25,
+                    help="initial voxel-table slots of the plain path's map, as a power of two")
     ap.add_argument("--assoc-cluster", type=int, default=0,
                     help="CTAs per map of the plain path's association kernel (0: automatic)")
     ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
@@ -280,7 +284,8 @@ def host_cpu():
 
 
 BATCHED = "Batched: {G} independent room-scale maps of uneven size (320x240..640x480 frames, 20-120 objects, " \
-          "5-60 masks/frame, voxel 2.5 cm), bf16 tokens 24x24x768, {J} frames of every map per batch"
+          "5-60 masks/frame, voxel 2.5 cm; {hist} frames of history before the timed frames, cycling over the " \
+          "maps), bf16 tokens 24x24x768, {J} frames of every map per batch"
 
 
 def batched_scenes(G, seed0):
@@ -301,8 +306,10 @@ def run_batched(args, torch, dev, stream, rank):
     from tests import common
     G, J, T = args.batched_maps, args.batched_frames, args.batched_steps
     scs = batched_scenes(G, 1000 + 97 * rank)
+    hist = [int(x) for x in args.batched_history.split(",") if x] or [0]
+    hg = [hist[g % len(hist)] for g in range(G)]  # frames each map integrated before the timed frames
     nf = (1 + T) * J
-    frs = [s.render(range(nf)) for s in scs]
+    frs = [s.render(range(h, h + nf)) for s, h in zip(scs, hg)]
     dd = [torch.from_numpy(f.depth).to(dev) for f in frs]
     ll = [torch.from_numpy(f.labels.view(np.int16)).to(dev) for f in frs]
     tt = [torch.from_numpy(f.tokens).to(dev).to(torch.bfloat16).contiguous() for f in frs]
@@ -311,6 +318,23 @@ def run_batched(args, torch, dev, stream, rank):
                     patch_w=scs[0].patch_w, max_width=max(s.width for s in scs),
                     max_height=max(s.height for s in scs), max_masks=max(s.max_masks for s in scs),
                     cuda_stream=stream.cuda_stream, device=dev.index)
+    # history: each map first integrates the start of its own path (untimed,
+    # through the group, 32 frames of every map with history per call), so
+    # the maps enter the measurement at uneven sizes
+    for lo in range(0, max(hg), 32):
+        part = [g for g in range(G) if hg[g] > lo]
+        keep, arrs, cnts = [], [], []
+        for g in part:
+            hf = scs[g].render(range(lo, min(hg[g], lo + 32)))
+            a, k = _device_frames(torch, dev, binding, scs[g], hf, range(len(hf.depth)), bf16=True)
+            keep.append(k)
+            arrs.append(a)
+            cnts.append(len(hf.depth))
+        hst = [(binding.Stats * 32)() for _ in part]
+        rc = grp.integrate_raw([maps[g] for g in part], arrs, cnts, hst)
+        assert rc == 0, rc
+    torch.cuda.synchronize()
+    vox0 = [m.counts()[0] for m in maps]
 
     def arrays(lo):
         out = []
@@ -354,7 +378,8 @@ def run_batched(args, torch, dev, stream, rank):
         times.append(e0.elapsed_time(e1))
         upd += sum(sts[g][j].unique_seg_voxels for g in range(G) for j in range(J))
     total_ms = float(np.sum(times))
-    out = {"workload": BATCHED.format(G=G, J=J), "frames_per_s": T * G * J / (total_ms / 1e3),
+    out = {"workload": BATCHED.format(G=G, J=J, hist=args.batched_history), "frames_per_s": T * G * J / (total_ms / 1e3),
+           "map_voxels_at_start": {"min": int(min(vox0)), "median": int(np.median(vox0)), "max": int(max(vox0))},
            "voxel_updates_per_s": upd / (total_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
            "steps": T, "ms_per_batch": total_ms / T,
            "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
@@ -842,6 +867,7 @@ def main():
                           "frames_per_step": B, "frames_timed": K * B,
                           "batch_split": args.batch_split or "automatic",
                           "assoc_cluster": args.assoc_cluster or "automatic",
+                          "voxel_table_slots": 1 << args.table_log2,
                           "trajectory_frames": core["n_render"],
                           "l2": "flushed between timed steps (258 MB write)", "replicas": world},
                "voxel_updates_per_s": core["updates"] * world / (total_ms / 1e3),
@@ -869,6 +895,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     cfg = room_cfg(scene)
+    cfg["voxel_capacity"] = 1 << args.table_log2
     if args.batch_frames > 0:
         cfg["batch_frames"] = args.batch_frames
     cfg["serial_sms"] = args.serial_sms

@@ -1604,7 +1604,31 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             if (st == DISC_OK && moved)
                 st = cuda_status(cudaMemcpyAsync(r.d_param[k] + r.off_refs, hrefs, sizeof(MapRefs) * G,
                                                  cudaMemcpyHostToDevice, sr));
-            if (st == DISC_OK) st = room_check(r, k, G, J, w, P.gl, hrefs, sr);
+            // Room without a round trip when the host bound suffices: a batch
+            // inserts at most one voxel per pixel of its frames, so each
+            // map's count stays below its bound plus the batch's pixels, and
+            // the absent-voxel hash below the batch's pixels (sized so at most
+            // kAbsentPixelCap slots).  Otherwise the exact counts come back
+            // (room_check) and set the bounds anew.
+            constexpr uint64_t kAbsentPixelCap = 1ull << 25;
+            bool fast = st == DISC_OK;
+            uint64_t batch_px = 0;
+            std::vector<uint64_t> px(G, 0);
+            for (int gi = 0; gi < G; gi++) {
+                Work& wk = w[P.gl[gi]];
+                const int cnt = std::min(Jb, wk.valid - lo);
+                for (int j = 0; j < cnt; j++) px[gi] += (uint64_t)wk.frames[lo + j].width * wk.frames[lo + j].height;
+                batch_px += px[gi];
+                const disc_map* m = wk.m;
+                fast = fast && (double)(m->used_upper + px[gi]) <= (double)m->cfg.max_load * (double)(m->vt.mask + 1);
+            }
+            fast = fast && next_pow2(std::max<uint64_t>(2 * batch_px, 1 << 16)) <= kAbsentPixelCap;
+            if (fast) {
+                st = ensure_absent(r, batch_px);
+                for (int gi = 0; gi < G && st == DISC_OK; gi++) w[P.gl[gi]].m->used_upper += px[gi];
+            } else if (st == DISC_OK) {
+                st = room_check(r, k, G, J, w, P.gl, hrefs, sr);
+            }
             if (st == DISC_OK)
                 st = run_part(r, graph_key(1, k, S, G, J, P.combos & COMBO_DILATE), sr,
                               [&] { return enqueue_serial(r, k, S, G, J, P.combos, sr); });
@@ -1658,6 +1682,13 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         cudaStreamWaitEvent(r.stream, r.ev_join, 0);
     }
     std::vector<FrameCounters> c(std::max(hoff, 1));
+    // every map's exact voxel count once the call's work is done, into the
+    // pinned room buffer: the next call's host bounds start from it
+    const int nread = std::min<int>((int)w.size(), 2 * r.Gmax);
+    for (int i = 0; i < nread; i++)
+        if (cudaMemcpyAsync(r.h_room + i, w[i].m->vt.used, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            r.stream) != cudaSuccess)
+            cudaGetLastError();
     if (hoff > 0) {
         disc_status s2 = cuda_status(
             cudaMemcpyAsync(c.data(), r.d_hist, sizeof(FrameCounters) * hoff, cudaMemcpyDeviceToHost, r.stream));
@@ -1671,6 +1702,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     s3 = cuda_status(cudaStreamSynchronize(r.stream_in));
     if (s == DISC_OK) s = s3;
     collect_timing(r);
+    if (s == DISC_OK)
+        for (int i = 0; i < nread; i++) w[i].m->used_upper = (uint64_t)r.h_room[i];
     disc_status first = s;
     for (Work& wk : w) {
         int exact_next_id = -1;  // frames without masks skip the kernel that records it
