@@ -68,7 +68,7 @@ def parse():
                     help="frames of each served map's path; the measurements together take every frame once")
     ap.add_argument("--batch-split", type=int, default=0,
                     help="smaller batches per 32-frame call of the plain path (0: the library's automatic choice)")
-    ap.add_argument("--table-log2", type=int, default=25,
+    ap.add_argument("--table-log2", type=int, default=26,
                     help="initial voxel-table slots of the plain path's map, as a power of two")
     ap.add_argument("--assoc-cluster", type=int, default=0,
                     help="CTAs per map of the plain path's association kernel (0: automatic)")
@@ -299,16 +299,42 @@ def batched_scenes(G, seed0):
                              n_objects=objs[g % 5], max_masks=masks[g % 6]) for g in range(G)]
 
 
+def _group_async_steps(torch, stream, binding, grp, maps, steps, J, flush):
+    """Time steps (per step a list of per-map Frame arrays of J frames) as
+    disc_group_integrate_async calls in one timed region, the L2 flush
+    enqueued between the steps; returns (ms, unique segment-voxel pairs)."""
+    G, T = len(maps), len(steps)
+    sts = [[(binding.Stats * J)() for _ in range(G)] for _ in range(T)]
+    done = [(ctypes.c_int32 * G)() for _ in range(T)]
+    res = [ctypes.c_int32(1) for _ in range(T)]
+    flush.fill_(-1.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(T):
+        if s:
+            flush.fill_(float(s))
+        rc = grp.integrate_async_raw(maps, steps[s], [J] * G, sts[s], done[s], res[s])
+        assert rc == 0, rc
+    rc = grp.wait()
+    e1.record(stream)
+    e1.synchronize()
+    assert rc == 0 and all(r.value == 0 for r in res) and all(list(d) == [J] * G for d in done), rc
+    upd = sum(sts[s][g][j].unique_seg_voxels for s in range(T) for g in range(G) for j in range(J))
+    return e0.elapsed_time(e1), upd
+
+
 def run_batched(args, torch, dev, stream, rank):
-    """The batched form: every map's frames j..j+J of a step in one group call
-    (disc_group_integrate), device-resident bf16 inputs."""
+    """The batched form: every map's frames j..j+J of a step in one group call,
+    device-resident bf16 inputs; timed as asynchronous calls
+    (disc_group_integrate_async), then as synchronous ones for the latency."""
     from paper_2603_03935_gb300 import DiscGroup, DiscMap, binding
     from tests import common
     G, J, T = args.batched_maps, args.batched_frames, args.batched_steps
     scs = batched_scenes(G, 1000 + 97 * rank)
     hist = [int(x) for x in args.batched_history.split(",") if x] or [0]
     hg = [hist[g % len(hist)] for g in range(G)]  # frames each map integrated before the timed frames
-    nf = (1 + T) * J
+    nf = (1 + 2 * T) * J
     frs = [s.render(range(h, h + nf)) for s, h in zip(scs, hg)]
     dd = [torch.from_numpy(f.depth).to(dev) for f in frs]
     ll = [torch.from_numpy(f.labels.view(np.int16)).to(dev) for f in frs]
@@ -356,7 +382,7 @@ def run_batched(args, torch, dev, stream, rank):
             out.append(a)
         return out
 
-    steps = [arrays(s * J) for s in range(1 + T)]
+    steps = [arrays(s * J) for s in range(1 + 2 * T)]
     sts = [(binding.Stats * J)() for _ in range(G)]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     # the launch schedule the autotuner picks on the first step's frames
@@ -365,8 +391,13 @@ def run_batched(args, torch, dev, stream, rank):
     l0 = grp.kernel_launches()
     assert grp.integrate_raw(maps, steps[0], [J] * G, sts) == 0
     torch.cuda.synchronize()
-    times, upd = [], 0
-    for s in range(1, 1 + T):
+    # the timed steps as asynchronous group calls (a batch's frame chains
+    # overlap the next batch's per-frame kernels), one timed region
+    async_ms, upd = _group_async_steps(torch, stream, binding, grp, maps, steps[1:1 + T], J, flush)
+    # the next T steps of every map as synchronous calls, each timed alone:
+    # a frame's result is ready when its call returns (the latency figures)
+    times = []
+    for s in range(1 + T, 1 + 2 * T):
         flush.fill_(float(s))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -376,15 +407,18 @@ def run_batched(args, torch, dev, stream, rank):
         e1.synchronize()
         assert rc == 0, rc
         times.append(e0.elapsed_time(e1))
-        upd += sum(sts[g][j].unique_seg_voxels for g in range(G) for j in range(J))
     total_ms = float(np.sum(times))
-    out = {"workload": BATCHED.format(G=G, J=J, hist=args.batched_history), "frames_per_s": T * G * J / (total_ms / 1e3),
+    out = {"workload": BATCHED.format(G=G, J=J, hist=args.batched_history),
+           "frames_per_s": T * G * J / (async_ms / 1e3),
+           "mode": "one disc_group_integrate_async call per batch, disc_group_wait after the last; one timed region",
+           "sync_calls": {"frames_per_s": T * G * J / (total_ms / 1e3),
+                          "mode": "one synchronous disc_group_integrate call per batch, each timed alone"},
            "map_voxels_at_start": {"min": int(min(vox0)), "median": int(np.median(vox0)), "max": int(max(vox0))},
-           "voxel_updates_per_s": upd / (total_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
-           "steps": T, "ms_per_batch": total_ms / T,
+           "voxel_updates_per_s": upd / (async_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
+           "steps": T, "ms_per_batch": async_ms / T,
            "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
                                 "mode": "a frame's result is ready when its batch ends"},
-           "gpu_launches_per_batch": (grp.kernel_launches() - l0) // (1 + T),
+           "gpu_launches_per_batch": (grp.kernel_launches() - l0) // (1 + 2 * T),
            "schedule": tune,
            "device_gb": (grp.device_bytes() + sum(m.device_bytes() for m in maps)) / 1e9}
     grp.close()
@@ -424,7 +458,9 @@ def _device_frames(torch, dev, binding, sc, fr, idx, bf16=False):
 def run_same_workload_batched(args, torch, dev, stream, rank):
     """The batched form on the plain line's workload: G Room-scale maps
     (seeds 2.., FP32, fp32 tokens), each first integrating W frames of its
-    own trajectory untimed, then timed group calls of J frames per map."""
+    own trajectory untimed, then T group calls of J frames per map timed as
+    asynchronous calls in one region, then T more as synchronous calls, each
+    timed alone."""
     import synth
     from paper_2603_03935_gb300 import DiscGroup, DiscMap, binding
     from tests import common
@@ -437,38 +473,50 @@ def run_same_workload_batched(args, torch, dev, stream, rank):
                     max_masks=scs[0].max_masks, cuda_stream=stream.cuda_stream, device=dev.index)
     sts = [(binding.Stats * J)() for _ in range(G)]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    times, upd, pairs, newv = [], 0, 0, 0
-    for s in range((W + T * J) // J):
-        lo = s * J
+
+    def step(lo):
         frs = [sc.render(range(lo, lo + J)) for sc in scs]
-        arrs = [_device_frames(torch, dev, binding, sc, fr, list(range(J))) for sc, fr in zip(scs, frs)]
+        return [_device_frames(torch, dev, binding, sc, fr, list(range(J))) for sc, fr in zip(scs, frs)]
+
+    for lo in range(0, W, J):  # untimed: the maps' first W frames
+        arrs = step(lo)
+        assert grp.integrate_raw(maps, [a for a, _ in arrs], [J] * G, sts) == 0
+        del arrs
+    timed = [step(W + s * J) for s in range(T)]  # resident before the timed region
+    torch.cuda.synchronize()
+    async_ms, upd = _group_async_steps(torch, stream, binding, grp, maps, [[a for a, _ in st] for st in timed], J,
+                                       flush)
+    del timed
+    times, pairs, newv, supd = [], 0, 0, 0
+    for s in range(T, 2 * T):
+        arrs = step(W + s * J)
         torch.cuda.synchronize()
-        timed = lo >= W
-        if timed:
-            flush.fill_(float(s))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        flush.fill_(float(s))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         rc = grp.integrate_raw(maps, [a for a, _ in arrs], [J] * G, sts)
+        e1.record(stream)
+        e1.synchronize()
         assert rc == 0, rc
-        if timed:
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            for g in range(G):
-                for j in range(J):
-                    upd += sts[g][j].unique_seg_voxels
-                    pairs += sts[g][j].overlap_pairs
-                    newv += sts[g][j].new_voxels
+        times.append(e0.elapsed_time(e1))
+        for g in range(G):
+            for j in range(J):
+                supd += sts[g][j].unique_seg_voxels
+                pairs += sts[g][j].overlap_pairs
+                newv += sts[g][j].new_voxels
         del arrs
     total_ms = float(np.sum(times))
     nfr = T * G * J
-    out = {"workload": SAME.format(G=G, J=J, W=W), "frames_per_s": nfr / (total_ms / 1e3),
-           "voxel_updates_per_s": upd / (total_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
-           "steps": T, "ms_per_batch": total_ms / T,
-           "per_frame": {"voxel_updates": upd / nfr, "overlap_pairs": pairs / nfr, "new_voxels": newv / nfr},
+    out = {"workload": SAME.format(G=G, J=J, W=W), "frames_per_s": nfr / (async_ms / 1e3),
+           "mode": "one disc_group_integrate_async call per batch, disc_group_wait after the last; one timed region",
+           "sync_calls": {"frames_per_s": nfr / (total_ms / 1e3),
+                          "mode": "the next batches as synchronous disc_group_integrate calls, each timed alone"},
+           "voxel_updates_per_s": upd / (async_ms / 1e3), "maps": G, "frames_per_map_per_batch": J,
+           "steps": T, "ms_per_batch": async_ms / T,
+           "per_frame": {"voxel_updates": supd / nfr, "overlap_pairs": pairs / nfr, "new_voxels": newv / nfr},
            "frame_latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
-                                "mode": "a frame's result is ready when its batch ends"}}
+                                "mode": "a frame's result is ready when its (synchronous) batch ends"}}
     grp.close()
     for m in maps:
         m.close()
@@ -848,7 +896,8 @@ def main():
     B, K, Wm = args.frames_per_step, args.steps, args.warmup
     # the line's sections as they finish (the watchdog prints what is here)
     state = {}
-    SECTIONS = ("dbscan", "assoc_grid", "dilation", "latency_ms", "finalize", "heatmap", "phases_ms_per_frame",
+    SECTIONS = ("sync_calls", "dbscan", "assoc_grid", "dilation", "latency_ms", "finalize", "heatmap",
+                "phases_ms_per_frame",
                 "roofline", "roofline_step", "cpu_baseline", "e2e", "batched", "batched_same_workload", "tiny",
                 "multistory", "served")
 
@@ -950,24 +999,32 @@ def main():
     time.sleep(0.5)  # the sampler is running by now
     launches0 = gmap.kernel_launches()
     wall0 = time.time()
-    times = []
-    updates = 0
-    new_vox = 0
-    for s in range(Wm, Wm + K):
-        flush.fill_(float(s))           # L2 flush between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rc = gmap.integrate_frames_raw(steps[s], B, stats)
-        e1.record(stream)
-        e1.synchronize()
+    # K steps, each one disc_integrate_frames_async call of B frames: a
+    # step's last frames associate while the next step's per-frame kernels
+    # run (two calls unfinished at most).  One timed region from before the
+    # first call to the end of the last (disc_map_wait), with the L2 flush
+    # enqueued between the steps inside it.
+    astats = [(binding.Stats * B)() for _ in range(K)]
+    adone = [ctypes.c_int32(-1) for _ in range(K)]
+    ares = [ctypes.c_int32(1) for _ in range(K)]
+    flush.fill_(float(Wm))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i, s in enumerate(range(Wm, Wm + K)):
+        if i:
+            flush.fill_(float(s))       # L2 flush between timed steps
+        rc = gmap.integrate_frames_async_raw(steps[s], B, astats[i], adone[i], ares[i])
         assert rc == 0, rc
-        times.append(e0.elapsed_time(e1))
-        updates += sum(stats[j].unique_seg_voxels for j in range(B))
-        new_vox += sum(stats[j].new_voxels for j in range(B))
+    rc = gmap.wait()
+    e1.record(stream)
+    e1.synchronize()
+    assert rc == 0 and all(r.value == 0 for r in ares) and all(d.value == B for d in adone), rc
+    updates = sum(astats[i][j].unique_seg_voxels for i in range(K) for j in range(B))
+    new_vox = sum(astats[i][j].new_voxels for i in range(K) for j in range(B))
     launches = gmap.kernel_launches() - launches0
     clocks.mark(wall0, time.time())
-    total_ms = max_over_ranks(float(np.sum(times)), world, dev)
+    total_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     clk = clocks.stop()
     frames_all = K * B * world
     state["core"] = {"total_ms": total_ms, "updates": updates, "new_vox": new_vox, "launches": launches,
@@ -999,6 +1056,12 @@ def main():
         vmap.close()
         return nf / (dt_ms / 1e3), nf, {k_: v_ / nf for k_, v_ in sums.items()}
 
+    # the same steps as synchronous calls on a fresh map, each timed alone
+    # (the call returns once its frames are done; L2 flushed before each)
+    fps_sync, nf_sync, _ = variant({}, K)
+    state["sync_calls"] = {"frames_per_s": whole_job_rate(nf_sync, world, nf_sync / fps_sync * 1e3),
+                           "frames": nf_sync,
+                           "mode": "one synchronous disc_integrate_frames call per step, each step timed alone"}
     # the same workload with the Sec. III-A DBSCAN filter on (eps 5 cm, 10 points)
     dbscan = None
     if args.dbscan_steps > 0:
@@ -1140,6 +1203,33 @@ def main():
         hl = torch.from_numpy(fr.labels.view(np.int16)).pin_memory()
         ht = torch.from_numpy(fr.tokens).pin_memory()
         hsteps = [frame_array(s * B, (s + 1) * B, on_device=False, host=(hd, hl, ht)) for s in range(Wm + K)]
+        # one asynchronous call per step, as the plain line: the H2D copies
+        # of a step's inputs (pinned host memory) and the read-back of its
+        # counters are inside the timed region, and overlap the kernels of
+        # the step before
+        m1 = plain_map(cfg)
+        for s in range(Wm):
+            assert m1.integrate_frames_raw(hsteps[s], B, stats) == 0
+        hst = [(binding.Stats * B)() for _ in range(K)]
+        hdone = [ctypes.c_int32(-1) for _ in range(K)]
+        hres = [ctypes.c_int32(1) for _ in range(K)]
+        torch.cuda.synchronize()
+        flush.fill_(float(Wm))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, s in enumerate(range(Wm, Wm + K)):
+            if i:
+                flush.fill_(float(s))
+            rc = m1.integrate_frames_async_raw(hsteps[s], B, hst[i], hdone[i], hres[i])
+            assert rc == 0, rc
+        rc = m1.wait()
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0 and all(r.value == 0 for r in hres) and all(d.value == B for d in hdone), rc
+        async_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        m1.close()
+        # the same steps as synchronous calls, each timed alone
         m2 = plain_map(cfg)
         for s in range(Wm):
             assert m2.integrate_frames_raw(hsteps[s], B, stats) == 0
@@ -1174,11 +1264,15 @@ def main():
         traj_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         m3.close()
         e2e_ms = max_over_ranks(float(np.sum(et)), world, dev)
-        e2e = {"value": whole_job_rate(K * B, world, e2e_ms), "unit": "frames/s",
+        e2e = {"value": whole_job_rate(K * B, world, async_ms), "unit": "frames/s",
                "h2d_bytes_per_step": B * (H * W_ * 6 + P * D * 4),
                "d2h_bytes_per_step": B * 64,
-               "calls": "one disc_integrate_frames call per step (32 frames), host buffers, synchronous",
-               "call_ms": {"p50": float(np.median(et)), "min": float(np.min(et)), "max": float(np.max(et))},
+               "calls": "one disc_integrate_frames_async call per step (32 frames) from pinned host buffers, "
+                        "disc_map_wait after the last; one timed region",
+               "sync_calls": {"value": whole_job_rate(K * B, world, e2e_ms), "unit": "frames/s",
+                              "mode": "one synchronous disc_integrate_frames call per step, each timed alone",
+                              "call_ms": {"p50": float(np.median(et)), "min": float(np.min(et)),
+                                          "max": float(np.max(et))}},
                "one_call_trajectory": {"value": whole_job_rate(K * B, world, traj_ms), "unit": "frames/s",
                                        "frames": K * B}}
     state["e2e"] = e2e

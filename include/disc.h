@@ -187,6 +187,36 @@ disc_status disc_integrate_frame(disc_map* map, const disc_frame* frame, disc_fr
 disc_status disc_integrate_frames(disc_map* map, const disc_frame* frames, int32_t n,
                                   disc_frame_stats* stats, int32_t* n_done);
 
+/* Asynchronous form of disc_integrate_frames (the paper integrates a stream
+ * of frames; this lets the next call's frames start while the last frames of
+ * the previous call still associate, Sec. III-B, so the map's frame chain and
+ * the next frames' per-frame kernels share the GPU).  The call enqueues the
+ * frames and returns DISC_OK without waiting for them; it is finished later
+ * by disc_map_wait, by a third asynchronous call on the map (at most two stay
+ * unfinished; the oldest is finished first), or by any other call on the map,
+ * which sees the map after every earlier call.  When a call is finished its
+ * results are written: stats (nullable, n entries), *n_done (nullable) and
+ * *result (nullable, the status disc_integrate_frames would have returned).
+ * Until then the caller keeps stats, n_done and result valid, and the
+ * frames' input buffers (host or device) unchanged; the disc_frame array
+ * itself is read before the call returns.  Frames run in call order: a frame
+ * that fails on the device stops every later frame of the map, in this call
+ * and in calls enqueued while it was unfinished (their *result is that
+ * error).  A frame that fails the host checks, and a map whose calls cannot
+ * overlap (phase timing on, or the neighbourhood overlap without serial_sms),
+ * make the call run synchronously: earlier calls finish first and the results
+ * are written before it returns, with the status also returned.  Work on the
+ * map's stream is not made to wait for an unfinished call.  Errors returned
+ * directly: DISC_ERR_INVALID_ARG (bad arguments, a finalised map), and the
+ * synchronous cases' statuses. */
+disc_status disc_integrate_frames_async(disc_map* map, const disc_frame* frames, int32_t n,
+                                        disc_frame_stats* stats, int32_t* n_done, disc_status* result);
+
+/* Finishes the unfinished asynchronous calls that hold the map (its own, or a
+ * group's: then every call of that group), oldest first, writing their
+ * results.  Returns the first of their statuses that is not DISC_OK. */
+disc_status disc_map_wait(disc_map* map);
+
 /* ---- Groups: many maps integrated side by side --------------------------
  * A group owns the scratch of one batch over up to max_maps maps with up to
  * frames_per_map frames each (the paper has no counterpart: it processes one
@@ -232,6 +262,22 @@ disc_status disc_group_integrate(disc_group* group, disc_map* const* maps, int32
                                  const disc_frame* const* frames, const int32_t* counts,
                                  disc_frame_stats* const* stats, int32_t* n_done);
 
+/* Asynchronous form of disc_group_integrate, with the semantics of
+ * disc_integrate_frames_async: the batch's frame chains overlap the next
+ * call's per-frame kernels.  stats[i] (the arrays, not the outer array),
+ * n_done [n_maps] and result stay valid until the call is finished, by
+ * disc_group_wait, a third asynchronous call on the group, another call on
+ * the group, or any call on one of its maps (disc_map_wait finishes every
+ * call of the group).  A map whose earlier asynchronous calls are held by
+ * another runner (its own, or another group) has them finished first. */
+disc_status disc_group_integrate_async(disc_group* group, disc_map* const* maps, int32_t n_maps,
+                                       const disc_frame* const* frames, const int32_t* counts,
+                                       disc_frame_stats* const* stats, int32_t* n_done, disc_status* result);
+
+/* Finishes the group's unfinished asynchronous calls, oldest first, writing
+ * their results; returns the first of their statuses that is not DISC_OK. */
+disc_status disc_group_wait(disc_group* group);
+
 /* Per-phase timing of the group's batches (as disc_map_set_phase_timing). */
 disc_status disc_group_set_phase_timing(disc_group* group, int32_t enable);
 disc_status disc_group_phase_times(disc_group* group, double* ms, int64_t* launches, int64_t* calls,
@@ -241,7 +287,8 @@ disc_status disc_group_phase_times(disc_group* group, double* ms, int64_t* launc
 int64_t disc_group_kernel_launches(disc_group* group);
 int64_t disc_group_device_bytes(disc_group* group);
 /* Frees the group's streams, graphs and scratch; the maps it integrated stay
- * valid.  Must not overlap a disc_group_integrate on the same group. */
+ * valid (its unfinished asynchronous calls are finished first).  Must not
+ * overlap a disc_group_integrate on the same group. */
 void disc_group_destroy(disc_group* group); /* NULL-safe */
 
 /* ---- Serving: a request loop over many resident maps ----------------------
@@ -514,6 +561,8 @@ const char* disc_phase_name(int32_t phase);
 /* Device memory held by the map, bytes. */
 int64_t disc_map_device_bytes(disc_map* map);
 
+/* Frees the map; its unfinished asynchronous calls (and those of a group
+ * call that holds it) are finished first, writing their results. */
 void disc_map_destroy(disc_map* map); /* NULL-safe */
 const char* disc_status_str(int32_t status);
 

@@ -115,6 +115,8 @@ def lib():
         L.disc_map_create.argtypes = [P(Config), P(Config), P(c_vp)]
         L.disc_integrate_frame.argtypes = [c_vp, P(Frame), P(Stats)]
         L.disc_integrate_frames.argtypes = [c_vp, P(Frame), c_i32, P(Stats), P(c_i32)]
+        L.disc_integrate_frames_async.argtypes = [c_vp, P(Frame), c_i32, P(Stats), P(c_i32), P(c_i32)]
+        L.disc_map_wait.argtypes = [c_vp]
         L.disc_map_last_frame.argtypes = [c_vp, P(Report)]
         L.disc_query_topk.argtypes = [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp]
         L.disc_query_points.argtypes = [c_vp, c_vp, c_i64, c_vp]
@@ -161,6 +163,8 @@ def lib():
         L.disc_group_config_default.restype = None
         L.disc_group_create.argtypes = [P(GroupConfig), P(c_vp)]
         L.disc_group_integrate.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]
+        L.disc_group_integrate_async.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, P(c_i32)]
+        L.disc_group_wait.argtypes = [c_vp]
         L.disc_group_set_phase_timing.argtypes = [c_vp, c_i32]
         L.disc_group_phase_times.argtypes = [c_vp, c_vp, c_vp, c_vp, c_i32]
         L.disc_group_kernel_launches.argtypes = [c_vp]
@@ -189,7 +193,8 @@ def lib():
                   "disc_group_integrate", "disc_group_set_phase_timing", "disc_group_phase_times",
                   "disc_server_create", "disc_server_open_map", "disc_server_close_map", "disc_server_submit_frame",
                   "disc_server_submit_query", "disc_server_wait", "disc_server_stats", "disc_server_reset_stats",
-                  "disc_map_finalize"):
+                  "disc_map_finalize", "disc_integrate_frames_async", "disc_map_wait",
+                  "disc_group_integrate_async", "disc_group_wait"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -310,6 +315,27 @@ def query_heatmap(tokens, query, eps=1e-6, stream=None):
     return heat
 
 
+class AsyncFrames:
+    """The pending results of one disc_integrate_frames_async call: the
+    counters, frames done and status, valid once the call is finished."""
+
+    def __init__(self, gmap, frames, n):
+        self.map = gmap
+        self.keep = frames  # the frames' input buffers stay alive with the handle
+        self.stats = (Stats * max(n, 1))()
+        self.done = c_i32(0)
+        self.rc = c_i32(0)
+        self.n = n
+
+    def result(self, check: bool = True):
+        """Wait for the map's asynchronous calls, then (stats dicts, frames
+        done, status), as integrate_frames returns them."""
+        self.map.wait()
+        if check:
+            _check(self.rc.value, "disc_integrate_frames_async")
+        return [self.stats[i].as_dict() for i in range(self.n)], int(self.done.value), int(self.rc.value)
+
+
 class DiscMap:
     """One map resident on one GPU (disc_map_create ... disc_map_destroy)."""
 
@@ -338,7 +364,7 @@ class DiscMap:
     def close(self):
         h = getattr(self, "_h", None)
         if h and getattr(self, "_owned", True):
-            lib().disc_map_destroy(h)
+            lib().disc_map_destroy(h)  # finishes the map's asynchronous calls first
         self._h = None
 
     __del__ = close
@@ -369,6 +395,39 @@ class DiscMap:
     def integrate_frames_raw(self, arr, n, stats):
         """Pre-built ctypes arrays (no per-call marshalling); returns the status."""
         return lib().disc_integrate_frames(self._h, arr, n, stats, None)
+
+    def integrate_frames_async_raw(self, arr, n, stats, n_done=None, result=None):
+        """disc_integrate_frames_async on pre-built ctypes arrays.  stats (a
+        Stats array), n_done and result (c_int32 objects, or None) are written
+        when the call is finished; the caller keeps them and the frames'
+        input buffers alive until then.  Returns the status of the call."""
+        return lib().disc_integrate_frames_async(self._h, arr, n, stats,
+                                                 None if n_done is None else ctypes.byref(n_done),
+                                                 None if result is None else ctypes.byref(result))
+
+    def integrate_frames_async(self, frames) -> "AsyncFrames":
+        """Enqueue frames (a list of (Frame, keepalive)) and return at once;
+        AsyncFrames.result() waits and gives what integrate_frames gives."""
+        n = len(frames)
+        arr = (Frame * n)()
+        for i, (fr, _k) in enumerate(frames):
+            arr[i] = fr
+        h = AsyncFrames(self, frames, n)
+        rc = self.integrate_frames_async_raw(arr, n, h.stats, h.done, h.rc)
+        _check(rc, "disc_integrate_frames_async")
+        # the library writes into the handle when the call is finished, which
+        # may be as late as the map's destruction: the map holds it till then
+        if not hasattr(self, "_pending"):
+            self._pending = []
+        self._pending.append(h)
+        return h
+
+    def wait(self) -> int:
+        """disc_map_wait: finish the map's asynchronous calls; returns the
+        first status among them that is not DISC_OK (0 if none)."""
+        rc = lib().disc_map_wait(self._h)
+        self._pending = []
+        return rc
 
     def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
@@ -539,6 +598,23 @@ class DiscGroup:
         hs = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in stats_arrays]) \
             if stats_arrays is not None else None
         return lib().disc_group_integrate(self._h, hm, n, hf, hc, hs, n_done)
+
+    def integrate_async_raw(self, maps, frame_arrays, counts, stats_arrays=None, n_done=None, result=None):
+        """disc_group_integrate_async; stats_arrays, n_done (a c_int32 array)
+        and result (a c_int32) are written when the call is finished and must
+        stay alive until then.  Returns the status of the call."""
+        n = len(maps)
+        hm = (c_vp * n)(*[m._h.value for m in maps])
+        hf = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in frame_arrays])
+        hc = (c_i32 * n)(*counts)
+        hs = (c_vp * n)(*[ctypes.cast(a, c_vp).value if a is not None else None for a in stats_arrays]) \
+            if stats_arrays is not None else None
+        return lib().disc_group_integrate_async(self._h, hm, n, hf, hc, hs, n_done,
+                                                None if result is None else ctypes.byref(result))
+
+    def wait(self) -> int:
+        """disc_group_wait: finish the group's asynchronous calls."""
+        return lib().disc_group_wait(self._h)
 
     def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,

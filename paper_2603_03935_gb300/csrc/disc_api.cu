@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -96,6 +97,33 @@ struct BatchGraph {
     int kernels = 0;
 };
 
+// The frames one call integrates into one map.
+struct Work {
+    disc_map* m = nullptr;
+    const disc_frame* frames = nullptr;
+    int n = 0;                        // frames asked for
+    int valid = 0;                    // leading frames that pass the host checks
+    disc_frame_stats* stats = nullptr;
+    int done = 0;                     // frames integrated
+    disc_status status = DISC_OK;     // first failure of this map
+    std::vector<int> hist_idx;        // counters of each enqueued frame in the call's history
+    int prev_idx = -1;                // history entry of the map's last frame in an unfinished
+                                      // asynchronous call (its first frame waits on that one's status)
+};
+
+// An asynchronous call whose work may still be on the device.  A runner
+// holds at most two; each writes its counters to its own half (region) of
+// the history buffer, and its results reach the caller's pointers when it
+// is finished (finish_oldest).
+struct AsyncCall {
+    std::vector<Work> w;
+    int region = 0;
+    std::vector<uint64_t> px_mark;    // per map: its px_total when the call was enqueued
+    std::vector<int64_t> masks_mark;  // per map: its masks_total then
+    int32_t* n_done = nullptr;        // the caller's outputs (one n_done per map)
+    disc_status* result = nullptr;
+};
+
 // What one batch of frame slots needs besides the maps themselves: the
 // slots' scratch, the per-batch parameter block, input staging, the per-frame
 // counters of the running call, captured launch sequences and phase timing.
@@ -123,8 +151,12 @@ struct Runner {
     size_t off_refs = 0, off_slot = 0, off_prev = 0, param_bytes = 0;
     cudaEvent_t ev_state[2] = {}, ev_serial[2] = {};  // stateless / serial part of the set's last batch done
     int cur = 0;                                        // set of the next batch
-    FrameCounters* d_hist = nullptr;  // [hist_cap] per-frame counters of one call
-    int hist_cap = 0;
+    FrameCounters* d_hist = nullptr;  // [2 hist_cap] per-frame counters: a synchronous call uses the
+    int hist_cap = 0;                 // first half, asynchronous calls alternate between the halves
+    FrameCounters* h_hist = nullptr;  // pinned [2 hist_cap]: asynchronous calls' counters
+    unsigned long long* h_used = nullptr;  // pinned [2 Gmax]: their maps' voxel counts at the end
+    cudaEvent_t ev_done[2] = {};      // an asynchronous call's work done, by history half
+    std::deque<AsyncCall> pend;       // unfinished asynchronous calls, oldest first (at most two)
     cudaStream_t stream_in = nullptr; // host-to-device copies of host inputs
     unsigned long long* d_room = nullptr;  // [2 Gmax] per map of a batch: voxel count, pairs of its frames
     AbsentHash ah{};                  // voxels absent at a batch's start (k_lookup .. k_commit), grown on demand
@@ -192,6 +224,11 @@ struct disc_map {
     // host-side bounds that avoid a synchronisation per frame
     uint64_t used_upper = 0;
     int64_t next_id_upper = 0;
+    uint64_t px_total = 0;      // pixels of every frame enqueued on the map (bounds its new voxels)
+    int64_t masks_total = 0;    // masks of every frame enqueued (bounds the ids handed out)
+    Runner* pend_run = nullptr; // the runner holding the map's unfinished asynchronous calls
+    int pend_calls = 0;         // how many of them
+    int pend_last = -1;         // history entry of the map's last frame in them
     Runner* run = nullptr;  // created by the map's first own integration call
     bool timing_wanted = false;
     unsigned char* qscratch = nullptr;  // query buffers, grown on demand and kept
@@ -490,7 +527,9 @@ disc_status runner_init(Runner& r, int device, cudaStream_t stream, int D, int P
     CK(cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&r.stream_in, cudaStreamNonBlocking));
     CK(cudaHostAlloc(&r.h_room, sizeof(unsigned long long) * 2 * Gmax, cudaHostAllocDefault));
+    CK(cudaHostAlloc(&r.h_used, sizeof(unsigned long long) * 2 * Gmax, cudaHostAllocDefault));
     CK(cudaEventCreateWithFlags(&r.ev_room, cudaEventDisableTiming));
+    for (int k = 0; k < 2; k++) CK(cudaEventCreateWithFlags(&r.ev_done[k], cudaEventDisableTiming));
     for (int k = 0; k < 2; k++) {
         CK(cudaEventCreateWithFlags(&r.ev_in_ready[k], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&r.ev_in_half[k], cudaEventDisableTiming));
@@ -544,6 +583,14 @@ void runner_release(Runner& r)
     r.ev_room = nullptr;
     if (r.h_room) cudaFreeHost(r.h_room);
     r.h_room = nullptr;
+    if (r.h_used) cudaFreeHost(r.h_used);
+    r.h_used = nullptr;
+    if (r.h_hist) cudaFreeHost(r.h_hist);
+    r.h_hist = nullptr;
+    for (int k = 0; k < 2; k++) {
+        if (r.ev_done[k]) cudaEventDestroy(r.ev_done[k]);
+        r.ev_done[k] = nullptr;
+    }
     for (int i = 0; i < 2; i++) {
         if (r.green[i]) green_api().destroy(r.green[i]);
         r.green[i] = nullptr;
@@ -563,20 +610,27 @@ void runner_release(Runner& r)
     r.mem.free_all();
 }
 
+// The history buffer for calls of up to n frames (in each of its halves).
+// Growing it replaces the buffer: no asynchronous call may be unfinished.
 disc_status ensure_hist(Runner& r, int n)
 {
     if (n <= r.hist_cap) return DISC_OK;
-    if (r.d_hist) r.mem.release(r.d_hist, sizeof(FrameCounters) * r.hist_cap);
+    if (r.d_hist) r.mem.release(r.d_hist, sizeof(FrameCounters) * 2 * r.hist_cap);
+    if (r.h_hist) cudaFreeHost(r.h_hist);
+    r.h_hist = nullptr;
     // captured sequences hold the old pointer
     for (auto& kv : r.graphs) cudaGraphExecDestroy(kv.second.exec);
     r.graphs.clear();
     r.shapes_seen.clear();
     const int cap = std::max(n, 2 * r.hist_cap);
-    r.d_hist = r.mem.get<FrameCounters>(cap);
-    if (r.mem.failed) {
+    r.d_hist = r.mem.get<FrameCounters>((size_t)2 * cap);
+    if (r.mem.failed || cudaHostAlloc(&r.h_hist, sizeof(FrameCounters) * 2 * cap, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        if (r.d_hist) r.mem.release(r.d_hist, sizeof(FrameCounters) * 2 * cap);
         r.mem.failed = false;
         r.hist_cap = 0;
         r.d_hist = nullptr;
+        r.h_hist = nullptr;
         return DISC_ERR_OOM;
     }
     r.hist_cap = cap;
@@ -1338,18 +1392,6 @@ void to_stats(const FrameCounters& c, disc_frame_stats* s)
     s->embedding_copies = c.n_copies;
 }
 
-// The frames one call integrates into one map.
-struct Work {
-    disc_map* m = nullptr;
-    const disc_frame* frames = nullptr;
-    int n = 0;                        // frames asked for
-    int valid = 0;                    // leading frames that pass the host checks
-    disc_frame_stats* stats = nullptr;
-    int done = 0;                     // frames integrated
-    disc_status status = DISC_OK;     // first failure of this map
-    std::vector<int> hist_idx;        // counters of each enqueued frame in the call's history
-};
-
 // Between a batch's stateless and serial parts (on the serial stream, after
 // the stateless part): each map's exact voxel count and the unique (segment,
 // voxel) pairs of its frames, which bound the voxels the batch inserts, come
@@ -1387,8 +1429,15 @@ disc_status room_check(Runner& r, int k, int G, int J, std::vector<Work>& w, con
 // map; the maps of a batch run side by side, each map's frames in order.  A
 // frame that fails stops the later frames of its map (on the device), not
 // those of the other maps.  Returns the first status that is not DISC_OK.
-disc_status run_call(Runner& r, std::vector<Work>& w)
+// With `async` (an asynchronous call, its history half chosen by the
+// caller) a call whose work can overlap later calls returns as soon as it is
+// enqueued, with *queued set: its counters and voxel counts come back on the
+// serial stream and ev_done[async->region] marks the end of its work, and
+// finish_oldest hands out its results.  Otherwise (or when enqueueing
+// fails) it completes before returning, as a synchronous call does.
+disc_status run_call(Runner& r, std::vector<Work>& w, const AsyncCall* async = nullptr, bool* queued = nullptr)
 {
+    if (queued) *queued = false;
     int total = 0, most = 0;
     for (Work& wk : w) {
         wk.valid = 0;
@@ -1418,7 +1467,9 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     // batch's stateless part runs beside it on the other SMs (two streams,
     // the serial one of highest priority); the four-kernels-per-frame form
     // (neighbourhood overlap) overlaps only on SM partitions (serial_sms)
-    const bool pipe = !r.timing && nbatch > 1 && (r.serial_sms > 0 || !dilate);
+    const bool can_pipe = !r.timing && (r.serial_sms > 0 || !dilate);
+    const bool pipe = can_pipe && (nbatch > 1 || async);
+    const bool queue = async && can_pipe;  // returns once enqueued
     cudaStream_t sr = pipe ? r.stream3 : r.stream;  // serial part
     cudaStream_t ss = pipe ? r.stream2 : r.stream;  // stateless part
     // the input copies (and, pipelined, both parts) start after the caller's
@@ -1436,7 +1487,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
     // then takes its SMs first and the stateless part fills the rest.
     // (Enqueued before it, the stateless kernels hold every SM and the
     // serial kernel waits for them to drain: measured slower.)
-    int hoff = 0;
+    const int hbase = async ? async->region * r.hist_cap : 0;  // the call's half of the history
+    int hoff = hbase;
     // One batch between its two halves of the loop below.
     struct Pending {
         int b = -1, k = 0, G = 0, J = 0, S = 0, combos = 0, hoff = 0;
@@ -1524,7 +1576,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
             Work& wk = w[P.gl[gi]];
             const int cnt = std::min(Jb, wk.valid - lo);
             hrefs[gi] = map_refs(wk.m);
-            hprev[gi] = wk.hist_idx.empty() ? -1 : wk.hist_idx.back();
+            hprev[gi] = wk.hist_idx.empty() ? wk.prev_idx : wk.hist_idx.back();
             for (int j = 0; j < J; j++) hslot[gi * J + j] = -1;
             for (int j = 0; j < cnt && st == DISC_OK; j++) {
                 st = frame_params(r, wk.m, wk.frames + lo + j, k, slot, gi, j, hfp + slot, hfpa ? hfpa + slot : nullptr,
@@ -1647,6 +1699,8 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
                 const disc_frame& f = wk.frames[lo + j];
                 if (P.timed) wk.m->used_upper += (uint64_t)f.width * f.height;
                 wk.m->next_id_upper += f.num_masks;
+                wk.m->px_total += (uint64_t)f.width * f.height;
+                wk.m->masks_total += f.num_masks;
             }
         }
         r.last_set = k;
@@ -1676,6 +1730,23 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         std::swap(cur, nxt);
         nxt.b = -1;
     }
+    if (queue && s == DISC_OK) {
+        // every map's exact voxel count and the call's counters come back
+        // behind its last batch; the caller's stream is not made to wait
+        const int nu = std::min<int>((int)w.size(), r.Gmax);
+        unsigned long long* hu = r.h_used + (size_t)async->region * r.Gmax;
+        for (int i = 0; i < nu && s == DISC_OK; i++)
+            s = cuda_status(cudaMemcpyAsync(hu + i, w[i].m->vt.used, sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, r.stream3));
+        if (s == DISC_OK && hoff > hbase)
+            s = cuda_status(cudaMemcpyAsync(r.h_hist + hbase, r.d_hist + hbase, sizeof(FrameCounters) * (hoff - hbase),
+                                            cudaMemcpyDeviceToHost, r.stream3));
+        if (s == DISC_OK) s = cuda_status(cudaEventRecord(r.ev_done[async->region], r.stream3));
+        if (s == DISC_OK) {
+            *queued = true;
+            return DISC_OK;
+        }
+    }
     if (pipe) {
         // the caller's stream continues after the call's work
         cudaEventRecord(r.ev_join, r.stream3);
@@ -1689,9 +1760,10 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         if (cudaMemcpyAsync(r.h_room + i, w[i].m->vt.used, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                             r.stream) != cudaSuccess)
             cudaGetLastError();
-    if (hoff > 0) {
-        disc_status s2 = cuda_status(
-            cudaMemcpyAsync(c.data(), r.d_hist, sizeof(FrameCounters) * hoff, cudaMemcpyDeviceToHost, r.stream));
+    if (hoff > hbase) {
+        disc_status s2 = cuda_status(cudaMemcpyAsync(c.data() + hbase, r.d_hist + hbase,
+                                                     sizeof(FrameCounters) * (hoff - hbase), cudaMemcpyDeviceToHost,
+                                                     r.stream));
         if (s == DISC_OK) s = s2;
     }
     disc_status s3 = cuda_status(cudaStreamSynchronize(r.stream));
@@ -1709,7 +1781,7 @@ disc_status run_call(Runner& r, std::vector<Work>& w)
         int exact_next_id = -1;  // frames without masks skip the kernel that records it
         wk.done = 0;
         wk.status = DISC_OK;
-        for (size_t i = 0; i < wk.hist_idx.size() && hoff > 0; i++) {
+        for (size_t i = 0; i < wk.hist_idx.size() && hoff > hbase; i++) {
             const FrameCounters& fc = c[wk.hist_idx[i]];
             if (wk.stats) to_stats(fc, wk.stats + i);
             if (wk.status != DISC_OK) continue;
@@ -1746,10 +1818,125 @@ disc_status map_runner(disc_map* m)
     return DISC_OK;
 }
 
+// Finish the runner's oldest asynchronous call: wait for its work, hand its
+// per-frame counters, frames done and status to the caller's pointers, and
+// tighten its maps' host bounds: the exact voxel count and next id at its end
+// plus what the calls enqueued after it may add (a voxel per pixel, an id per
+// mask).  Returns the call's status.
+disc_status finish_oldest(Runner& r)
+{
+    AsyncCall a = std::move(r.pend.front());
+    r.pend.pop_front();
+    const disc_status s = cuda_status(cudaEventSynchronize(r.ev_done[a.region]));
+    const unsigned long long* hu = r.h_used + (size_t)a.region * r.Gmax;
+    disc_status first = s;
+    for (size_t i = 0; i < a.w.size(); i++) {
+        Work& wk = a.w[i];
+        disc_map* m = wk.m;
+        int exact_next_id = -1;
+        wk.done = 0;
+        wk.status = DISC_OK;
+        for (size_t j = 0; j < wk.hist_idx.size() && s == DISC_OK; j++) {
+            const FrameCounters& fc = r.h_hist[wk.hist_idx[j]];
+            if (wk.stats) to_stats(fc, wk.stats + j);
+            if (wk.status != DISC_OK) continue;
+            if (fc.err != 0) {
+                wk.status = (disc_status)fc.err;
+                continue;
+            }
+            exact_next_id = std::max(exact_next_id, fc.next_id);
+            wk.done++;
+        }
+        if (s == DISC_OK) {
+            if ((int)i < r.Gmax)
+                m->used_upper = std::min<uint64_t>(m->used_upper, (uint64_t)hu[i] + (m->px_total - a.px_mark[i]));
+            if (exact_next_id > 0)
+                m->next_id_upper =
+                    std::min<int64_t>(m->next_id_upper, (int64_t)exact_next_id + (m->masks_total - a.masks_mark[i]));
+        }
+        if (wk.status == DISC_OK && s != DISC_OK && wk.done < wk.valid) wk.status = s;
+        if (first == DISC_OK) first = wk.status;
+        if (a.n_done) a.n_done[i] = wk.done;
+        if (--m->pend_calls <= 0) {
+            m->pend_calls = 0;
+            m->pend_run = nullptr;
+            m->pend_last = -1;
+        }
+    }
+    if (a.result) *a.result = first;
+    return first;
+}
+
+// Finish every asynchronous call of the runner, oldest first; returns the
+// first status that is not DISC_OK.
+disc_status finish_all(Runner& r)
+{
+    disc_status first = DISC_OK;
+    while (!r.pend.empty()) {
+        const disc_status s = finish_oldest(r);
+        if (first == DISC_OK) first = s;
+    }
+    return first;
+}
+
+// Finish the unfinished asynchronous calls that hold the map (its own or a
+// group's), so that what follows sees the map after them.
+disc_status wait_pending(disc_map* m)
+{
+    return m->pend_run ? finish_all(*m->pend_run) : DISC_OK;
+}
+
+// Enqueue an asynchronous call of the works on runner r (at most two stay
+// unfinished: a third finishes the oldest first).  A call with a frame that
+// fails the host checks, or one that cannot overlap later calls, runs
+// synchronously after the earlier calls have finished, and its results are
+// written before returning.
+disc_status enqueue_async(Runner& r, std::vector<Work>&& w, int32_t* n_done, disc_status* result)
+{
+    int64_t frames = 0;
+    bool ok = true;
+    for (Work& wk : w) {
+        if (wk.m->pend_run && wk.m->pend_run != &r) finish_all(*wk.m->pend_run);
+        frames += wk.n;
+        for (int i = 0; i < wk.n && ok; i++) ok = check_frame(wk.m, r, wk.frames + i) == DISC_OK;
+    }
+    // calls that cannot overlap run on the caller's stream, after every
+    // earlier call has finished
+    bool dilate = false;
+    for (const Work& wk : w) dilate |= wk.n > 0 && wk.m->cfg.overlap_dilation != 0;
+    const bool overlap = !r.timing && (r.serial_sms > 0 || !dilate);
+    if (!ok || !overlap || frames > r.hist_cap) finish_all(r);
+    while (r.pend.size() >= 2) finish_oldest(r);
+    AsyncCall a;
+    a.region = r.pend.empty() ? 0 : (r.pend.back().region ^ 1);
+    a.n_done = n_done;
+    a.result = result;
+    a.w = std::move(w);
+    for (Work& wk : a.w) wk.prev_idx = wk.m->pend_run == &r ? wk.m->pend_last : -1;
+    bool queued = false;
+    const disc_status s = run_call(r, a.w, ok && overlap ? &a : nullptr, &queued);
+    if (!queued) {
+        for (size_t i = 0; i < a.w.size() && n_done; i++) n_done[i] = a.w[i].done;
+        if (result) *result = s;
+        return s;
+    }
+    for (Work& wk : a.w) {
+        disc_map* m = wk.m;
+        a.px_mark.push_back(m->px_total);
+        a.masks_mark.push_back(m->masks_total);
+        m->pend_run = &r;
+        m->pend_calls++;
+        if (!wk.hist_idx.empty()) m->pend_last = wk.hist_idx.back();
+    }
+    r.pend.push_back(std::move(a));
+    return DISC_OK;
+}
+
 disc_status integrate(disc_map* m, const disc_frame* frames, int n, disc_frame_stats* stats, int* n_done)
 {
     if (n_done) *n_done = 0;
     if (m->finalized) return DISC_ERR_INVALID_ARG;
+    wait_pending(m);
     disc_status s = map_runner(m);
     if (s != DISC_OK) return s;
     std::vector<Work> w(1);
@@ -1883,6 +2070,7 @@ void disc_map_destroy(disc_map* m)
 {
     if (!m) return;
     cudaSetDevice(m->cfg.device);
+    wait_pending(m);
     cudaStreamSynchronize(m->stream);
     if (m->run) {
         runner_release(*m->run);
@@ -1910,10 +2098,38 @@ disc_status disc_integrate_frames(disc_map* m, const disc_frame* frames, int32_t
     return integrate(m, frames, n, stats, n_done);
 }
 
+disc_status disc_integrate_frames_async(disc_map* m, const disc_frame* frames, int32_t n, disc_frame_stats* stats,
+                                        int32_t* n_done, disc_status* result)
+{
+    if (!m || (n > 0 && !frames) || n < 0 || m->finalized) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    if (n == 0) {
+        if (n_done) *n_done = 0;
+        if (result) *result = DISC_OK;
+        return DISC_OK;
+    }
+    disc_status s = map_runner(m);
+    if (s != DISC_OK) return s;
+    std::vector<Work> w(1);
+    w[0].m = m;
+    w[0].frames = frames;
+    w[0].n = n;
+    w[0].stats = stats;
+    return enqueue_async(*m->run, std::move(w), n_done, result);
+}
+
+disc_status disc_map_wait(disc_map* m)
+{
+    if (!m) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(m->cfg.device));
+    return wait_pending(m);
+}
+
 disc_status disc_map_last_frame(disc_map* m, disc_frame_report* r)
 {
     if (!m || !r) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const Runner* run = m->run;
     const bool have = run && run->have_frame;
@@ -2062,12 +2278,52 @@ disc_status disc_group_integrate(disc_group* g, disc_map* const* maps, int32_t n
     }
     if (n_maps == 0) return DISC_OK;
     CK(cudaSetDevice(g->cfg.device));
+    // earlier asynchronous calls of the group or of its maps finish first
+    finish_all(g->run);
+    for (int i = 0; i < n_maps; i++) wait_pending(maps[i]);
     // the maps' own streams may still hold work of earlier calls
     for (int i = 0; i < n_maps; i++) CK(cudaStreamSynchronize(maps[i]->stream));
     disc_status s = run_call(g->run, w);
     if (n_done)
         for (int i = 0; i < n_maps; i++) n_done[i] = w[i].done;
     return s;
+}
+
+disc_status disc_group_integrate_async(disc_group* g, disc_map* const* maps, int32_t n_maps,
+                                       const disc_frame* const* frames, const int32_t* counts,
+                                       disc_frame_stats* const* stats, int32_t* n_done, disc_status* result)
+{
+    if (!g || n_maps < 0 || n_maps > g->cfg.max_maps || (n_maps > 0 && (!maps || !frames || !counts)))
+        return DISC_ERR_INVALID_ARG;
+    std::vector<Work> w(n_maps);
+    for (int i = 0; i < n_maps; i++) {
+        disc_map* m = maps[i];
+        if (!m || counts[i] < 0 || (counts[i] > 0 && !frames[i])) return DISC_ERR_INVALID_ARG;
+        if (m->cfg.device != g->cfg.device || m->D != g->cfg.embed_dim || m->cfg.patch_h != g->cfg.patch_h ||
+            m->cfg.patch_w != g->cfg.patch_w)
+            return DISC_ERR_INVALID_ARG;
+        for (int k = 0; k < i; k++)
+            if (maps[k] == m) return DISC_ERR_INVALID_ARG;  // one entry per map
+        if (m->finalized) return DISC_ERR_INVALID_ARG;
+        w[i].m = m;
+        w[i].frames = frames[i];
+        w[i].n = counts[i];
+        w[i].stats = stats ? stats[i] : nullptr;
+    }
+    if (n_maps == 0) {
+        if (result) *result = DISC_OK;
+        return DISC_OK;
+    }
+    CK(cudaSetDevice(g->cfg.device));
+    for (int i = 0; i < n_maps; i++) CK(cudaStreamSynchronize(maps[i]->stream));
+    return enqueue_async(g->run, std::move(w), n_done, result);
+}
+
+disc_status disc_group_wait(disc_group* g)
+{
+    if (!g) return DISC_ERR_INVALID_ARG;
+    CK(cudaSetDevice(g->cfg.device));
+    return finish_all(g->run);
 }
 
 // ---- test hooks: failures made on the host, waits that run out ---------------
@@ -2201,6 +2457,7 @@ disc_status disc_map_set_schedule(disc_map* m, const disc_schedule* sch)
 {
     if (!m || !sch) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     disc_status s = map_runner(m);
     return s != DISC_OK ? s : set_schedule(*m->run, sch);
 }
@@ -2209,6 +2466,7 @@ disc_status disc_group_set_schedule(disc_group* g, const disc_schedule* sch)
 {
     if (!g || !sch) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(g->cfg.device));
+    finish_all(g->run);
     return set_schedule(g->run, sch);
 }
 
@@ -2218,6 +2476,7 @@ disc_status disc_map_autotune(disc_map* m, const disc_frame* frames, int32_t n, 
     CK(cudaSetDevice(m->cfg.device));
     disc_status s = map_runner(m);
     if (s != DISC_OK) return s;
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     return autotune(*m->run, {&m->cfg}, {{frames, n}}, reps, report);
 }
@@ -2234,6 +2493,8 @@ disc_status disc_group_autotune(disc_group* g, disc_map* const* maps, int32_t n_
         fr.push_back({frames[i], counts[i]});
     }
     CK(cudaSetDevice(g->cfg.device));
+    finish_all(g->run);
+    for (int i = 0; i < n_maps; i++) wait_pending(maps[i]);
     return autotune(g->run, cfgs, fr, reps, report);
 }
 
@@ -2241,6 +2502,7 @@ void disc_group_destroy(disc_group* g)
 {
     if (!g) return;
     cudaSetDevice(g->cfg.device);
+    finish_all(g->run);
     cudaStream_t st = g->run.stream;
     runner_release(g->run);
     if (g->own_stream) cudaStreamDestroy(st);
@@ -2255,6 +2517,7 @@ disc_status disc_group_set_phase_timing(disc_group* g, int32_t enable)
 {
     if (!g) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(g->cfg.device));
+    finish_all(g->run);
     CK(cudaStreamSynchronize(g->run.stream));
     reset_timing(g->run, enable != 0);
     return DISC_OK;
@@ -2275,6 +2538,7 @@ disc_status disc_map_counts(disc_map* m, int64_t* nv, int32_t* nid)
 {
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     if (nv) *nv = (int64_t)read_used(m, m->stream);
     if (nid) *nid = read_next_id(m, m->stream);
@@ -2285,6 +2549,7 @@ disc_status disc_map_export_voxels(disc_map* m, uint64_t* keys, int32_t* ids, in
 {
     if (!m || (cap > 0 && (!keys || !ids))) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const uint64_t tc = m->vt.mask + 1;
     std::vector<unsigned long long> k(tc);
@@ -2310,6 +2575,7 @@ disc_status disc_map_export_assoc(disc_map* m, float* A, int32_t cap)
 {
     if (!m || !A || m->cfg.assoc_dim <= 0) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const int n = read_next_id(m, m->stream);
     if (n > cap) return DISC_ERR_INVALID_ARG;
@@ -2322,6 +2588,7 @@ disc_status disc_map_export_instances(disc_map* m, int32_t* parent, int64_t* cou
 {
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const int n = read_next_id(m, m->stream);
     if (n > cap) return DISC_ERR_INVALID_ARG;
@@ -2339,6 +2606,7 @@ disc_status disc_query_topk(disc_map* m, const float* q, int32_t nq, int32_t k, 
     if (!m || nq < 0 || k <= 0 || (nq > 0 && (!q || !ids || !scores))) return DISC_ERR_INVALID_ARG;
     if (nq == 0) return DISC_OK;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const int nid = read_next_id(m, m->stream);
     const int D = m->D;
@@ -2369,6 +2637,7 @@ disc_status disc_query_points(disc_map* m, const float* xyz, int64_t n, int32_t*
     if (!m || n < 0 || (n > 0 && (!xyz || !ids))) return DISC_ERR_INVALID_ARG;
     if (n == 0) return DISC_OK;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     const size_t b_x = align256(sizeof(float) * 3 * (size_t)n);
     unsigned char* base = query_scratch(m, b_x + sizeof(int) * (size_t)n);
     if (!base) return DISC_ERR_OOM;
@@ -2582,6 +2851,7 @@ disc_status disc_map_finalize(disc_map* m, const disc_finalize_config* cfg, disc
     if (!m || !cfg || cfg->contact_den <= 0 || cfg->contact_num < 0 || cfg->min_voxels < 0) return DISC_ERR_INVALID_ARG;
     if (m->finalized) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     const int nid = read_next_id(m, m->stream);
     cudaStream_t st = m->stream;
@@ -2657,6 +2927,7 @@ disc_status disc_map_set_phase_timing(disc_map* m, int32_t enable)
 {
     if (!m) return DISC_ERR_INVALID_ARG;
     CK(cudaSetDevice(m->cfg.device));
+    wait_pending(m);
     CK(cudaStreamSynchronize(m->stream));
     m->timing_wanted = enable != 0;
     if (m->run) reset_timing(*m->run, enable != 0);
