@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--assoc-cluster", type=int, default=0,
                     help="CTAs per map of the plain path's association kernel (0: automatic)")
     ap.add_argument("--geometry-chunk", type=int, default=0,
-                    help="frames per back-projection launch of the plain path (0: the library's default, 4)")
+                    help="frames per back-projection launch of the plain path (0: the library's default, 8)")
     ap.add_argument("--batched-tune", type=int, default=1, help="1: autotune the group's launch schedule first")
     ap.add_argument("--served-workers", type=int, default=2, help="batches the server runs at once")
     ap.add_argument("--served-borrow", type=int, default=1,
@@ -917,7 +917,7 @@ def main():
                           "frames_per_step": B, "frames_timed": K * B,
                           "batch_split": args.batch_split or "automatic",
                           "assoc_cluster": args.assoc_cluster or "automatic",
-                          "geometry_chunk": args.geometry_chunk or 4,
+                          "geometry_chunk": args.geometry_chunk or 8,
                           "voxel_table_slots": 1 << args.table_log2,
                           "trajectory_frames": core["n_render"],
                           "l2": "flushed between timed steps (258 MB write)", "replicas": world},
@@ -961,7 +961,7 @@ def main():
     def plain_map(c):
         m = DiscMap(**c)
         if args.batch_split or args.assoc_cluster or args.geometry_chunk:
-            m.set_schedule(geometry_chunk=args.geometry_chunk or 4, assoc_cluster=args.assoc_cluster,
+            m.set_schedule(geometry_chunk=args.geometry_chunk or 8, assoc_cluster=args.assoc_cluster,
                            batch_split=args.batch_split)
         return m
 

@@ -455,13 +455,14 @@ disc_status disc_debug_gemm_stall(int32_t device, int32_t on);
  * kernels run beside the frame chain of the one before it.  None changes any
  * result. */
 typedef struct {
-    int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 4) */
+    int32_t geometry_chunk;  /* frames per geometry launch, 1..32 (default 8) */
     int32_t serial_ctas;     /* serial kernels' CTAs in quarters of the default count, 1..32 (default 4) */
     int32_t probe_width;     /* lanes per key of the voxel-table lookup: 1, 2, 4 or 8 (0 or 1: one lane) */
     int32_t assoc_cluster;   /* CTAs per map in the association kernel: 0 (as many as the batch's maps leave
                                 SMs for, up to 8), or 1, 2, 4, 8 (capped by what the device co-schedules) */
-    int32_t batch_split;     /* smaller batches per call that fits one batch: 0 (2 for one map's calls of 16
-                                frames or more, else 1), or 1, 2, 4, 8; each keeps at least 4 frames */
+    int32_t batch_split;     /* smaller batches per call that fits one batch: 0 (2 for one map's synchronous
+                                calls of 16 frames or more, else 1: an asynchronous call's frame chain
+                                already overlaps the next call), or 1, 2, 4, 8; each keeps at least 4 frames */
 } disc_schedule;
 
 typedef struct {

@@ -429,7 +429,7 @@ class DiscMap:
         self._pending = []
         return rc
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
+    def set_schedule(self, geometry_chunk=8, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_map_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
                                                                           assoc_cluster, batch_split))),
                "disc_map_set_schedule")
@@ -616,7 +616,7 @@ class DiscGroup:
         """disc_group_wait: finish the group's asynchronous calls."""
         return lib().disc_group_wait(self._h)
 
-    def set_schedule(self, geometry_chunk=4, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
+    def set_schedule(self, geometry_chunk=8, serial_ctas=4, probe_width=1, assoc_cluster=0, batch_split=0):
         _check(lib().disc_group_set_schedule(self._h, ctypes.byref(Schedule(geometry_chunk, serial_ctas, probe_width,
                                                                             assoc_cluster, batch_split))),
                "disc_group_set_schedule")

@@ -59,7 +59,7 @@ int launch_entries(const FrameParams* fps, const BatchScratch& bs, const MapRefs
 int launch_quality(const FrameParams* fps, const BatchScratch& bs, int B, cudaStream_t st);
 // default frames per back-projection/entries/DBSCAN launch (their per-frame
 // hashes stay in L2); the runner's tuning may pick another
-constexpr int GEOMETRY_CHUNK = 4;
+constexpr int GEOMETRY_CHUNK = 8;
 
 // start of a batch's serial part: every map's edge and copy counters to zero
 int launch_e4m3_copies(const Instances& inst, int n, int D, cudaStream_t st);
