@@ -1277,7 +1277,7 @@ def main():
         e2e_ms = max_over_ranks(float(np.sum(et)), world, dev)
         e2e = {"value": whole_job_rate(K * B, world, async_ms), "unit": "frames/s",
                "h2d_bytes_per_step": B * (H * W_ * 6 + P * D * 4),
-               "d2h_bytes_per_step": B * 64,
+               "d2h_bytes_per_step": B * 96 + 8,  # per frame its 96-byte counters, and the map's voxel count
                "calls": "one disc_integrate_frames_async call per step (32 frames) from pinned host buffers, "
                         "disc_map_wait after the last; one timed region",
                "sync_calls": {"value": whole_job_rate(K * B, world, e2e_ms), "unit": "frames/s",
