@@ -28,7 +28,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("disc_map_create", "disc_integrate_frame", "disc_integrate_frames", "disc_query_topk",
                      "disc_query_points", "disc_map_destroy", "disc_map_export_voxels", "disc_map_save",
-                     "disc_map_load"):
+                     "disc_map_load", "disc_integrate_frames_async", "disc_map_wait", "disc_group_integrate_async",
+                     "disc_group_wait"):
         assert required in names
 
 
@@ -51,6 +52,18 @@ def test_host_only_entry_points(libdisc):
         key = pkg.pack_key(*k)
         assert oracle.unpack_key(key) == k
     assert pkg.pack_key(1, 2, 3) == oracle.point_key(1.01, 2.01, 3.01, 1.0)
+
+
+def test_asynchronous_entry_points_refuse_bad_arguments_without_a_device(libdisc):
+    # argument checks come before any device call, so they run here
+    from paper_2603_03935_gb300 import binding as b
+    L = b.lib()
+    res, done = ctypes.c_int32(7), ctypes.c_int32(7)
+    assert L.disc_integrate_frames_async(None, None, 0, None, ctypes.byref(done), ctypes.byref(res)) == -1
+    assert L.disc_map_wait(None) == -1
+    assert L.disc_group_integrate_async(None, None, 0, None, None, None, None, ctypes.byref(res)) == -1
+    assert L.disc_group_wait(None) == -1
+    assert (res.value, done.value) == (7, 7)  # nothing was enqueued, nothing written
 
 
 def test_product_path_refuses_to_run_without_the_library(tmp_path, monkeypatch):
