@@ -19,10 +19,12 @@
  *   - Status codes only; nothing throws across the ABI.  A frame is all or
  *     nothing: when integration fails the map keeps its pre-frame state.
  *   - The caller owns every buffer it passes; the map owns its device state.
- *     Inputs must stay valid until the call returns.
+ *     Inputs must stay valid until the call returns (for the asynchronous
+ *     integration calls: until the call is finished, see
+ *     disc_integrate_frames_async).
  *   - Work is ordered on the map's CUDA stream (config.cuda_stream, or a
  *     stream the map creates).  Every call returns after its results are on
- *     the host unless stated otherwise.
+ *     the host unless stated otherwise (the *_async calls).
  *   - One host thread per map at a time; different maps are independent.
  *   - Instance ids are resolved roots (the smallest id of a merged group);
  *     -1 means "none".
