@@ -120,6 +120,17 @@ def max_over_ranks(value: float, world: int, device) -> float:
     return float(t.item())
 
 
+def guarded(name, fn):
+    """A section of the line after the main measurement: its result, or an
+    {"error": ...} entry if it raises, so that the line still carries every
+    section that finished."""
+    try:
+        return fn()
+    except Exception as ex:  # recorded, the rest of the line stands
+        print(f"bench: section {name} failed: {ex!r}", file=sys.stderr, flush=True)
+        return {"error": repr(ex)}
+
+
 def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time (weak scaling: every rank does the same work)."""
@@ -1208,8 +1219,7 @@ def main():
     state["cpu_baseline"] = cpu_baseline(scene, fr, args.cpu_seconds, Wm * B) if rank == 0 and world == 1 else None
 
     # end to end through the C ABI with pinned host buffers (H2D inside)
-    e2e = None
-    if not args.no_e2e:
+    def run_e2e():
         hd = torch.from_numpy(fr.depth).pin_memory()
         hl = torch.from_numpy(fr.labels.view(np.int16)).pin_memory()
         ht = torch.from_numpy(fr.tokens).pin_memory()
@@ -1286,17 +1296,25 @@ def main():
                                           "max": float(np.max(et))}},
                "one_call_trajectory": {"value": whole_job_rate(K * B, world, traj_ms), "unit": "frames/s",
                                        "frames": K * B}}
-    state["e2e"] = e2e
+        return e2e
+
+    # (with several ranks a failure would leave the others in a collective: not caught there)
+    state["e2e"] = None if args.no_e2e else (guarded("e2e", run_e2e) if world == 1 else run_e2e())
 
     # the batched and served forms last: their many maps and threads come
     # after every single-map measurement
-    state["batched"] = run_batched(args, torch, dev, stream, rank) if args.batched_maps > 0 else None
-    state["batched_same_workload"] = (run_same_workload_batched(args, torch, dev, stream, rank)
-                                      if args.same_maps > 0 else None)
-    state["tiny"] = run_tiny(args, torch, dev, stream, rank == 0 and world == 1) if args.tiny else None
-    state["multistory"] = (run_multistory(args, torch, dev, stream, rank, rank == 0 and world == 1)
-                           if args.multistory_steps > 0 else None)
-    state["served"] = run_served(args, torch, dev, rank) if args.served_maps > 0 else None
+    # (no collective inside them: a failure is recorded and the other ranks go on)
+    state["batched"] = (guarded("batched", lambda: run_batched(args, torch, dev, stream, rank))
+                        if args.batched_maps > 0 else None)
+    state["batched_same_workload"] = (
+        guarded("batched_same_workload", lambda: run_same_workload_batched(args, torch, dev, stream, rank))
+        if args.same_maps > 0 else None)
+    state["tiny"] = (guarded("tiny", lambda: run_tiny(args, torch, dev, stream, rank == 0 and world == 1))
+                     if args.tiny else None)
+    state["multistory"] = (
+        guarded("multistory", lambda: run_multistory(args, torch, dev, stream, rank, rank == 0 and world == 1))
+        if args.multistory_steps > 0 else None)
+    state["served"] = guarded("served", lambda: run_served(args, torch, dev, rank)) if args.served_maps > 0 else None
 
     if rank == 0:
         line = assemble()

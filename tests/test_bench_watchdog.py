@@ -2,7 +2,7 @@
 process): a run that outlives its budget prints the sections it finished,
 the rest marked unfinished, and exits 0; without the main measurement it
 prints nothing and exits 1; a run that finishes first prints exactly one
-line."""
+line; a section that raises is recorded as an error entry."""
 import json
 import os
 import subprocess
@@ -48,3 +48,15 @@ def test_finished_run_prints_once():
     rc, lines = _run("finish")
     assert rc == 0 and len(lines) == 2 and json.loads(lines[0]) == {"value": 1.0, "served": {"p99_ms": 1.0}}
     assert lines[1] == "still here"
+
+
+def test_a_failing_section_is_recorded_and_the_line_goes_on():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def boom():
+        raise RuntimeError("section failed")
+
+    assert bench.guarded("served", lambda: {"p99_ms": 1.0}) == {"p99_ms": 1.0}
+    out = bench.guarded("served", boom)
+    assert set(out) == {"error"} and "section failed" in out["error"]
